@@ -1,0 +1,521 @@
+"""Seeded synthetic grasp scenes: the inputs shared by the CUDA path, the oracle and the tests.
+
+This module only builds geometry, material parameters and kinematic schedules. It holds none
+of the simulator's arithmetic (no energies, distances, CCD or solves), so both the CUDA path and
+the CPU oracle can be fed from it without sharing any of the method.
+
+The paper's assets (UMI/LEAP meshes, DexGraspNet objects) are not available, so every scene is
+a procedural stand-in with the shapes, sizes and parameter ranges of the grasp-validation
+workload of Sec. III-D (dt, kappa, dhat, eps_v) and the domain randomisation of Sec. III-B
+(Young's modulus, friction coefficient and object scale drawn per environment).
+
+Env dict layout (all arrays numpy, C-contiguous):
+
+    soft:    list of {verts (n,3) f64, tets (m,4) i32, tris (f,3) i32 outward,
+                      E, nu, rho (floats), kin (n,) u8: 1 = vertex driven by the schedule}
+    affine:  list of {verts (n,3) f64 rest surface, tris (f,3) i32 outward, rho,
+                      q0 (12,) f64, qdot0 (12,) f64, kinematic (bool)}
+    mu:      friction coefficient of the environment
+    gravity: (n_steps,) u8, 1 = gravity acts during that step
+    targets: (n_steps, n_soft + n_affine, 12) f64 — for each step s the affine map
+             q = (p, a1, a2, a3) that a kinematic body (or a soft body's kinematic vertices,
+             mapped from their initial positions) must reach at the end of step s.
+
+Affine coordinates q = (p, a1, a2, a3) place a rest point xb at p + xb[0] a1 + xb[1] a2 + xb[2] a3
+(the a_i are the columns of A).
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+BASE_SEED = 20250306
+MASK64 = (1 << 64) - 1
+
+IDENTITY_Q = np.array([0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1], dtype=np.float64)
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea & Flood 2014): a counter-based 64-bit generator."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+    def uniform_array(self, n: int, lo: float, hi: float) -> np.ndarray:
+        return np.array([self.uniform(lo, hi) for _ in range(n)], dtype=np.float64)
+
+    def randint(self, lo: int, hi: int) -> int:
+        """Integer in [lo, hi)."""
+        return lo + int(self.uniform() * (hi - lo)) % max(hi - lo, 1)
+
+    def normal(self) -> float:
+        u1 = max(self.uniform(), 1e-300)
+        u2 = self.uniform()
+        return math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+
+
+# --------------------------------------------------------------------------- meshes
+
+def _orient_tets(verts: np.ndarray, tets: np.ndarray) -> np.ndarray:
+    """Swap two vertices of every tet whose rest orientation is negative."""
+    a, b, c, d = (verts[tets[:, i]] for i in range(4))
+    det = np.einsum("ij,ij->i", np.cross(b - a, c - a), d - a)
+    tets = tets.copy()
+    neg = det < 0
+    tets[neg, 2], tets[neg, 3] = tets[neg, 3].copy(), tets[neg, 2].copy()
+    return tets
+
+
+def kuhn_grid(nx: int, ny: int, nz: int, lo, hi, cell_mask: np.ndarray | None = None):
+    """Box [lo, hi] split into nx*ny*nz cells, each cut into 6 Kuhn tets along its main diagonal.
+
+    cell_mask[i, j, k] == False removes that cell. Unused vertices are dropped.
+    Returns (verts (n,3) f64, tets (m,4) i32, grid_index (n,3) i32 of each kept vertex).
+    """
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    gi, gj, gk = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    grid = np.stack([gi.ravel(), gj.ravel(), gk.ravel()], axis=1)
+    verts = lo + (hi - lo) * grid / np.array([nx, ny, nz], dtype=np.float64)
+
+    def vid(i, j, k):
+        return (i * (ny + 1) + j) * (nz + 1) + k
+
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for i in range(nx):
+        for j in range(ny):
+            for k in range(nz):
+                if cell_mask is not None and not cell_mask[i, j, k]:
+                    continue
+                for p in perms:
+                    c = [i, j, k]
+                    path = [tuple(c)]
+                    for ax in p:
+                        c[ax] += 1
+                        path.append(tuple(c))
+                    tets.append([vid(*q) for q in path])
+    tets = np.asarray(tets, dtype=np.int64)
+    used = np.unique(tets)
+    remap = -np.ones(len(verts), dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    verts = verts[used]
+    grid = grid[used]
+    tets = remap[tets]
+    tets = _orient_tets(verts, tets)
+    return verts, tets.astype(np.int32), grid.astype(np.int32)
+
+
+def boundary_tris(verts: np.ndarray, tets: np.ndarray) -> np.ndarray:
+    """Faces used by exactly one tet, oriented so that the normal points out of that tet."""
+    faces = {}
+    for t in tets:
+        for f, opp in (((t[1], t[2], t[3]), t[0]), ((t[0], t[2], t[3]), t[1]),
+                       ((t[0], t[1], t[3]), t[2]), ((t[0], t[1], t[2]), t[3])):
+            key = tuple(sorted(f))
+            if key in faces:
+                faces[key] = None
+            else:
+                faces[key] = (f, opp)
+    out = []
+    for v in faces.values():
+        if v is None:
+            continue
+        (a, b, c), d = v
+        n = np.cross(verts[b] - verts[a], verts[c] - verts[a])
+        if np.dot(n, verts[d] - verts[a]) > 0:
+            b, c = c, b
+        out.append((a, b, c))
+    out.sort()
+    return np.asarray(out, dtype=np.int32)
+
+
+def box_surface(half_extents) -> tuple[np.ndarray, np.ndarray]:
+    """Closed, outward-oriented 8-vertex 12-triangle box centred at the origin."""
+    hx, hy, hz = half_extents
+    v = np.array([[sx * hx, sy * hy, sz * hz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)])
+    quads = [(0, 1, 3, 2), (4, 6, 7, 5), (0, 4, 5, 1), (2, 3, 7, 6), (0, 2, 6, 4), (1, 5, 7, 3)]
+    tris = []
+    for a, b, c, d in quads:
+        tris += [(a, b, c), (a, c, d)]
+    tris = np.asarray(tris, dtype=np.int64)
+    # orient outward
+    cen = v.mean(axis=0)
+    for t in tris:
+        n = np.cross(v[t[1]] - v[t[0]], v[t[2]] - v[t[0]])
+        if np.dot(n, v[t[0]] - cen) < 0:
+            t[1], t[2] = t[2], t[1]
+    return v.astype(np.float64), tris.astype(np.int32)
+
+
+def convex_hull_surface(points: np.ndarray) -> np.ndarray:
+    """Outward triangles of the convex hull (qhull via scipy, used only to build inputs)."""
+    from scipy.spatial import ConvexHull
+
+    hull = ConvexHull(points)
+    tris = hull.simplices.astype(np.int64).copy()
+    cen = points[hull.vertices].mean(axis=0)
+    for t in tris:
+        n = np.cross(points[t[1]] - points[t[0]], points[t[2]] - points[t[0]])
+        if np.dot(n, points[t[0]] - cen) < 0:
+            t[1], t[2] = t[2], t[1]
+    used = np.unique(tris)
+    remap = -np.ones(len(points), dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    return points[used].copy(), remap[tris].astype(np.int32)
+
+
+def subdivide_midpoint(verts: np.ndarray, tris: np.ndarray):
+    """One 1->4 midpoint subdivision (the surface geometry does not change)."""
+    verts = [tuple(v) for v in verts]
+    mid = {}
+    out = []
+
+    def m(a, b):
+        key = (min(a, b), max(a, b))
+        if key not in mid:
+            mid[key] = len(verts)
+            va, vb = verts[a], verts[b]
+            verts.append(tuple(0.5 * (x + y) for x, y in zip(va, vb)))
+        return mid[key]
+
+    for a, b, c in tris:
+        ab, bc, ca = m(a, b), m(b, c), m(c, a)
+        out += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]
+    return np.asarray(verts, dtype=np.float64), np.asarray(out, dtype=np.int32)
+
+
+def star_ball(rng: SplitMix64, n: int, r0: float, n_harm: int = 3, amp: float = 0.15):
+    """Star-shaped soft object: a Kuhn-gridded ball, radially warped by seeded low harmonics."""
+    lo = np.array([-1.0, -1.0, -1.0])
+    hi = np.array([1.0, 1.0, 1.0])
+    c = (np.arange(n) + 0.5) / n * 2.0 - 1.0
+    ci, cj, ck = np.meshgrid(c, c, c, indexing="ij")
+    mask = (ci ** 2 + cj ** 2 + ck ** 2) <= 1.0
+    verts, tets, _ = kuhn_grid(n, n, n, lo, hi, mask)
+    coeffs = [(rng.uniform(-amp, amp), rng.normal(), rng.normal(), rng.normal()) for _ in range(n_harm)]
+    r = np.linalg.norm(verts, axis=1)
+    dirs = verts / np.maximum(r[:, None], 1e-12)
+    scale = np.ones(len(verts))
+    for a, kx, ky, kz in coeffs:
+        k = np.array([kx, ky, kz])
+        k = k / max(np.linalg.norm(k), 1e-12)
+        scale += a * (dirs @ k) ** 2
+    verts = verts * (r0 * scale)[:, None]
+    return verts, tets
+
+
+# ----------------------------------------------------------------------- parameters
+
+def scene_params(dt: float, dhat: float = 1e-3, kappa: float = 3e6, eps_v: float = 1e-3,
+                 newton_tol: float | None = None, pcg_rel_tol: float = 1e-4,
+                 max_newton: int = 100, max_ls: int = 40, max_pcg: int = 1000,
+                 kappa_affine: float = 1e8, gravity=(0.0, 0.0, -9.8)) -> dict:
+    """Solver parameters. Defaults follow Sec. III-D: kappa = 3e6 kg/s^2, dhat = 1e-3 m,
+    eps_v = 1e-3 m/s, at most 100 Newton iterations; the Newton tolerance defaults to
+    1e-2 * dt in m/s on the infinity norm of the Newton step divided by dt."""
+    return dict(dt=float(dt), dhat=float(dhat), kappa=float(kappa), eps_v=float(eps_v),
+                newton_tol=float(1e-2 * dt if newton_tol is None else newton_tol),
+                pcg_rel_tol=float(pcg_rel_tol), max_newton=int(max_newton), max_ls=int(max_ls),
+                max_pcg=int(max_pcg), kappa_affine=float(kappa_affine),
+                gravity=tuple(float(g) for g in gravity))
+
+
+def parity_params(params: dict) -> dict:
+    """Tight solve settings for trajectory parity: Newton tolerance x1e-3, PCG to 1e-12."""
+    p = dict(params)
+    p["newton_tol"] = params["newton_tol"] * 1e-3
+    p["pcg_rel_tol"] = 1e-12
+    p["max_pcg"] = max(params["max_pcg"], 20000)
+    return p
+
+
+def _translation_q(p) -> np.ndarray:
+    q = IDENTITY_Q.copy()
+    q[:3] = p
+    return q
+
+
+# -------------------------------------------------------------------- configurations
+
+def cube_squeeze_env(env_id: int = 0, base_seed: int = BASE_SEED, n_steps: int = 100,
+                     close_steps: int | None = None, dt: float = 0.01, dhat: float = 1e-3,
+                     mu: float = 0.5, cells: int = 4, size: float = 0.05,
+                     E: float = 1e5, nu: float = 0.4, rho: float = 1000.0,
+                     close_speed: float = 0.01, lift_speed: float = 0.02) -> dict:
+    """Soft 0.05 m cube (5x5x5 vertices, 384 Kuhn tets) squeezed by two kinematic rigid plates.
+
+    Plates start 1.5*dhat from the faces, close at `close_speed` with gravity off, then lift at
+    `lift_speed` with gravity on (the gravity gating of the grasp protocol, Sec. III-D).
+    Vertices get a seeded jitter U(-1e-5, 1e-5) m.
+    """
+    rng = SplitMix64(base_seed + env_id)
+    h = size / 2
+    verts, tets, _ = kuhn_grid(cells, cells, cells, (-h, -h, -h), (h, h, h))
+    verts = verts + rng.uniform_array(verts.size, -1e-5, 1e-5).reshape(verts.shape)
+    tris = boundary_tris(verts, tets)
+    gap = 1.5 * dhat
+    pt = 0.005  # plate half thickness
+    pv, ptris = box_surface((pt, 0.04, 0.04))
+    xmax = verts[:, 0].max()
+    xmin = verts[:, 0].min()
+    pl = dict(verts=pv, tris=ptris, rho=1000.0, q0=_translation_q((xmax + gap + pt, 0, 0)),
+              qdot0=np.zeros(12), kinematic=True)
+    pr = dict(verts=pv.copy(), tris=ptris.copy(), rho=1000.0,
+              q0=_translation_q((xmin - gap - pt, 0, 0)), qdot0=np.zeros(12), kinematic=True)
+    if close_steps is None:
+        close_steps = n_steps // 2
+    targets = np.zeros((n_steps, 3, 12))
+    gravity = np.zeros(n_steps, dtype=np.uint8)
+    for s in range(n_steps):
+        nc = min(s + 1, close_steps)
+        nl = max(s + 1 - close_steps, 0)
+        dx = close_speed * dt * nc
+        dz = lift_speed * dt * nl
+        targets[s, 0] = IDENTITY_Q
+        targets[s, 1] = _translation_q((xmax + gap + pt - dx, 0, dz))
+        targets[s, 2] = _translation_q((xmin - gap - pt + dx, 0, dz))
+        gravity[s] = 1 if s >= close_steps else 0
+    soft = dict(verts=verts, tets=tets, tris=tris, E=E, nu=nu, rho=rho,
+                kin=np.zeros(len(verts), dtype=np.uint8))
+    return dict(soft=[soft], affine=[pl, pr], mu=mu, gravity=gravity, targets=targets)
+
+
+def finger_pad(rng: SplitMix64, side: int, inner_x: float, E: float, nu: float,
+               rho: float = 1100.0, n=(6, 8, 18), thick=0.015, width=0.04, height=0.08,
+               taper=0.35, n_cutouts=3):
+    """Tapered soft finger pad on a Kuhn grid with seeded rectangular cutouts.
+
+    side=+1 puts the pad at x >= inner_x (flat contact face at x = inner_x), side=-1 mirrors it.
+    The outermost vertex layer is kinematic (driven by the gripper).
+    """
+    nx, ny, nz = n
+    mask = np.ones((nx, ny, nz), dtype=bool)
+    for _ in range(n_cutouts):
+        i0 = rng.randint(1, nx - 2)
+        i1 = min(i0 + rng.randint(1, 3), nx - 1)
+        j0 = rng.randint(0, ny - 2)
+        j1 = min(j0 + rng.randint(2, 5), ny)
+        k0 = rng.randint(1, nz - 4)
+        k1 = min(k0 + rng.randint(2, 6), nz - 1)
+        mask[i0:i1, j0:j1, k0:k1] = False
+    verts, tets, grid = kuhn_grid(nx, ny, nz, (0, -width / 2, -height / 2), (thick, width / 2, height / 2), mask)
+    # taper: the pad thins linearly towards its top; the contact face x=0 stays flat.
+    zrel = (verts[:, 2] + height / 2) / height
+    verts[:, 0] *= 1.0 - taper * zrel
+    kin = (grid[:, 0] == nx).astype(np.uint8)
+    verts[:, 0] = inner_x + verts[:, 0] if side > 0 else -inner_x - verts[:, 0]
+    tets = _orient_tets(verts, tets.astype(np.int64)).astype(np.int32)
+    tris = boundary_tris(verts, tets)
+    return dict(verts=verts, tets=tets, tris=tris, E=E, nu=nu, rho=rho, kin=kin)
+
+
+def hull_object(rng: SplitMix64, n_points: int = 200, dmin: float = 0.03, dmax: float = 0.08,
+                subdivide: bool = True):
+    """Convex hull of seeded points on an ellipsoid whose per-axis diameters are U(dmin, dmax);
+    one midpoint subdivision brings 200 hull points to 1584 triangles."""
+    radii = np.array([rng.uniform(dmin, dmax) / 2 for _ in range(3)])
+    pts = []
+    for _ in range(n_points):
+        d = np.array([rng.normal(), rng.normal(), rng.normal()])
+        d /= max(np.linalg.norm(d), 1e-12)
+        pts.append(d * radii)
+    pts = np.asarray(pts)
+    verts, tris = convex_hull_surface(pts)
+    if subdivide:
+        verts, tris = subdivide_midpoint(verts, tris)
+    return verts, tris
+
+
+def pad_grasp_env(env_id: int = 0, base_seed: int = BASE_SEED, n_steps: int = 300,
+                  close_steps: int = 100, dt: float = 0.005, dhat: float = 1e-3,
+                  squeeze: float = 2e-3, lift: float = 0.1, pad_cells=(6, 8, 18),
+                  object_points: int = 200) -> dict:
+    """Two soft wedge finger pads (~5k tets each, E=2e5 Pa, nu=0.45) grasping a rigid affine
+    hull object (density U(500,1500)); mu ~ U(0.3, 0.8). Close with gravity off, then lift
+    0.1 m with gravity on."""
+    rng = SplitMix64(base_seed + env_id)
+    mu = rng.uniform(0.3, 0.8)
+    ov, otris = hull_object(rng, object_points)
+    rho_o = rng.uniform(500.0, 1500.0)
+    gap = 1.5 * dhat
+    xr = ov[:, 0].max() + gap
+    xl = -ov[:, 0].min() + gap
+    pad_r = finger_pad(rng, +1, xr, 2e5, 0.45, n=pad_cells)
+    pad_l = finger_pad(rng, -1, xl, 2e5, 0.45, n=pad_cells)
+    obj = dict(verts=ov, tris=otris, rho=rho_o, q0=IDENTITY_Q.copy(), qdot0=np.zeros(12), kinematic=False)
+    close_speed_r = (gap + squeeze) / (close_steps * dt)
+    lift_steps = max(n_steps - close_steps, 1)
+    lift_speed = lift / (lift_steps * dt)
+    targets = np.zeros((n_steps, 3, 12))
+    gravity = np.zeros(n_steps, dtype=np.uint8)
+    for s in range(n_steps):
+        nc = min(s + 1, close_steps)
+        nl = max(s + 1 - close_steps, 0)
+        dx = close_speed_r * dt * nc
+        dz = lift_speed * dt * nl
+        targets[s, 0] = _translation_q((-dx, 0, dz))
+        targets[s, 1] = _translation_q((dx, 0, dz))
+        targets[s, 2] = IDENTITY_Q
+        gravity[s] = 1 if s >= close_steps else 0
+    return dict(soft=[pad_r, pad_l], affine=[obj], mu=mu, gravity=gravity, targets=targets)
+
+
+def soft_object_grasp_env(env_id: int, base_seed: int = BASE_SEED, n_steps: int = 100,
+                          close_steps: int = 50, dt: float = 0.005, dhat: float = 1e-3,
+                          tets_lo: int = 2000, tets_hi: int = 60000, bimanual: bool | None = None,
+                          squeeze: float = 1.5e-3, lift: float = 0.05) -> dict:
+    """Uneven-batch scene: a star-shaped soft object of log-uniform size in [tets_lo, tets_hi]
+    held by rigid kinematic plates (one pair, or two pairs when bimanual)."""
+    rng = SplitMix64(base_seed + env_id)
+    target_tets = math.exp(rng.uniform(math.log(tets_lo), math.log(tets_hi)))
+    # a Kuhn ball of n^3 cells keeps about (pi/6) n^3 cells, 6 tets each
+    n = max(4, int(round((target_tets / (6 * math.pi / 6)) ** (1 / 3))))
+    r0 = rng.uniform(0.02, 0.04)
+    verts, tets = star_ball(rng, n, r0)
+    tris = boundary_tris(verts, tets)
+    E = math.exp(rng.uniform(math.log(1e4), math.log(1e6)))
+    nu = rng.uniform(0.3, 0.45)
+    mu = rng.uniform(0.3, 0.8)
+    if bimanual is None:
+        bimanual = rng.uniform() < 0.25
+    soft = dict(verts=verts, tets=tets, tris=tris, E=E, nu=nu, rho=1000.0,
+                kin=np.zeros(len(verts), dtype=np.uint8))
+    gap = 1.5 * dhat
+    pt = 0.004
+    pv, ptris = box_surface((pt, 0.05, 0.05))
+    axes = [0, 1] if bimanual else [0]
+    plates = []
+    for ax in axes:
+        for sgn in (+1, -1):
+            ext = verts[:, ax].max() if sgn > 0 else -verts[:, ax].min()
+            c = np.zeros(3)
+            c[ax] = sgn * (ext + gap + pt)
+            q0 = _translation_q(c)
+            if ax == 1:  # plate rotated so its thin axis is y: A maps rest x to world y
+                q0[3:12] = [0, 1, 0, -1, 0, 0, 0, 0, 1]
+            plates.append((ax, sgn, q0))
+    if bimanual:
+        # make the y plates shorter in x so the two pairs do not touch each other
+        pv_y, ptris_y = box_surface((pt, 0.012, 0.05))
+    speed = (gap + squeeze) / (close_steps * dt)
+    lift_speed = lift / (max(n_steps - close_steps, 1) * dt)
+    affine = []
+    targets = np.zeros((n_steps, 1 + len(plates), 12))
+    for b, (ax, sgn, q0) in enumerate(plates):
+        v, t = (pv_y, ptris_y) if ax == 1 else (pv, ptris)
+        affine.append(dict(verts=v.copy(), tris=t.copy(), rho=1000.0, q0=q0, qdot0=np.zeros(12), kinematic=True))
+        for s in range(n_steps):
+            nc = min(s + 1, close_steps)
+            nl = max(s + 1 - close_steps, 0)
+            q = q0.copy()
+            q[ax] -= sgn * speed * dt * nc
+            q[2] += lift_speed * dt * nl
+            targets[s, 1 + b] = q
+    targets[:, 0] = IDENTITY_Q
+    gravity = (np.arange(n_steps) >= close_steps).astype(np.uint8)
+    return dict(soft=[soft], affine=affine, mu=mu, gravity=gravity, targets=targets)
+
+
+# ---------------------------------------------------------------- small test scenes
+
+def single_tet_env(n_steps: int = 1, offset=(0.0, 0.0, 0.0)) -> dict:
+    """One free tet with no contact partner (free-fall and elasticity checks)."""
+    v = np.array([[0, 0, 0], [0.01, 0, 0], [0, 0.01, 0], [0, 0, 0.01]], dtype=np.float64) + np.asarray(offset)
+    tets = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    tris = boundary_tris(v, tets)
+    soft = dict(verts=v, tets=tets, tris=tris, E=1e5, nu=0.4, rho=1000.0, kin=np.zeros(4, dtype=np.uint8))
+    return dict(soft=[soft], affine=[], mu=0.0, gravity=np.ones(n_steps, dtype=np.uint8),
+                targets=np.tile(IDENTITY_Q, (n_steps, 1, 1)))
+
+
+def _rot_y(deg: float) -> np.ndarray:
+    th = math.radians(deg)
+    return np.array([[math.cos(th), 0, math.sin(th)], [0, 1, 0], [-math.sin(th), 0, math.cos(th)]])
+
+
+def _q_from(R: np.ndarray, p) -> np.ndarray:
+    q = IDENTITY_Q.copy()
+    q[:3] = p
+    q[3:6], q[6:9], q[9:12] = R[:, 0], R[:, 1], R[:, 2]
+    return q
+
+
+def ground_triangle(L: float = 0.2):
+    """One large triangle in the z=0 plane covering [-L, L]^2 (a one-sided kinematic ground:
+    a body touching it meets exactly one triangle and none of its edges)."""
+    v = np.array([[-L, -L, 0.0], [3 * L, -L, 0.0], [-L, 3 * L, 0.0]])
+    return v, np.array([[0, 1, 2]], dtype=np.int32)
+
+
+def resting_env(body: str = "tet", n_steps: int = 100, mu: float = 0.0, incline_deg: float = 0.0,
+                dhat: float = 1e-3, gap: float | None = None, size: float = 0.02, E: float = 1e6,
+                rho: float = 1000.0, cells: int = 2) -> dict:
+    """A body resting under gravity on a fixed ground triangle inclined about the y axis.
+
+    body = "tet": one tet with a horizontal base and its apex over the base centroid;
+    "block": a soft Kuhn block; "rigid": a free affine box.
+    """
+    if gap is None:
+        gap = 0.5 * dhat
+    R = _rot_y(incline_deg)
+    gv, gt = ground_triangle()
+    ground = dict(verts=gv, tris=gt, rho=1000.0, q0=_q_from(R, (0, 0, 0)), qdot0=np.zeros(12), kinematic=True)
+    h = size / 2
+    if body == "rigid":
+        bv, bt = box_surface((h, h, h))
+        q0 = _q_from(R, R @ np.array([0, 0, h + gap]))
+        obj = dict(verts=bv, tris=bt, rho=rho, q0=q0, qdot0=np.zeros(12), kinematic=False)
+        targets = np.zeros((n_steps, 2, 12))
+        targets[:, 0] = q0
+        targets[:, 1] = ground["q0"]
+        return dict(soft=[], affine=[obj, ground], mu=mu, gravity=np.ones(n_steps, dtype=np.uint8),
+                    targets=targets)
+    if body == "tet":
+        r = size / 2
+        base = np.array([[r * math.cos(a), r * math.sin(a), 0.0] for a in (0.3, 0.3 + 2 * math.pi / 3, 0.3 + 4 * math.pi / 3)])
+        verts = np.vstack([base, [[0.0, 0.0, size]]]) + np.array([0, 0, gap])
+        tets = _orient_tets(verts, np.array([[0, 1, 2, 3]])).astype(np.int32)
+    else:
+        verts, tets, _ = kuhn_grid(cells, cells, cells, (-h, -h, 0.0), (h, h, size))
+        verts = verts + np.array([0, 0, gap])
+    verts = verts @ R.T
+    tris = boundary_tris(verts, tets)
+    soft = dict(verts=verts, tets=tets, tris=tris, E=E, nu=0.3, rho=rho, kin=np.zeros(len(verts), dtype=np.uint8))
+    targets = np.zeros((n_steps, 2, 12))
+    targets[:, 0] = IDENTITY_Q
+    targets[:, 1] = ground["q0"]
+    return dict(soft=[soft], affine=[ground], mu=mu, gravity=np.ones(n_steps, dtype=np.uint8), targets=targets)
+
+
+def spinning_body_env(n_steps: int = 20, omega=(0.0, 0.0, 20.0)) -> dict:
+    """A free rigid box spinning in free flight with gravity off (A A^T stays close to I)."""
+    bv, btris = box_surface((0.02, 0.01, 0.005))
+    q0 = IDENTITY_Q.copy()
+    w = np.asarray(omega, dtype=np.float64)
+    W = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+    Adot = W  # d/dt of A at A = I
+    qdot0 = np.zeros(12)
+    qdot0[3:6], qdot0[6:9], qdot0[9:12] = Adot[:, 0], Adot[:, 1], Adot[:, 2]
+    body = dict(verts=bv, tris=btris, rho=800.0, q0=q0, qdot0=qdot0, kinematic=False)
+    return dict(soft=[], affine=[body], mu=0.0, gravity=np.zeros(n_steps, dtype=np.uint8),
+                targets=np.tile(IDENTITY_Q, (n_steps, 1, 1)))
+
+
+def env_sizes(env: dict) -> dict:
+    """Counts used to size buffers and to report workloads."""
+    nv = sum(len(s["verts"]) for s in env["soft"])
+    nt = sum(len(s["tets"]) for s in env["soft"])
+    ntri = sum(len(s["tris"]) for s in env["soft"]) + sum(len(a["tris"]) for a in env["affine"])
+    return dict(soft_verts=nv, tets=nt, tris=ntri, bodies=len(env["affine"]),
+                dofs=3 * nv + 12 * len(env["affine"]), steps=len(env["gravity"]))

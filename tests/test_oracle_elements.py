@@ -1,0 +1,360 @@
+"""Pins of the CPU oracle's element-level functions against closed forms, brute force,
+finite differences and independent library routines (no GPU)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+from oracle import oracle as O
+from paper_2503_05020_b300 import scenes as S
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+RNG = np.random.default_rng(1234)
+
+
+def rand_rotation(rng):
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def lame(E, nu):
+    return E / (2 * (1 + nu)), E * nu / ((1 + nu) * (1 - 2 * nu))
+
+
+# ------------------------------------------------------------------ paper parameters
+def test_paper_parameters_are_defaults():
+    """Sec. III-D fixes dt, kappa, dhat, eps_v and the Newton cap; the defaults must match."""
+    g = json.load(open(os.path.join(HERE, "golden", "paper_parameters.json")))
+    p = S.scene_params(g["dt"])
+    assert p["kappa"] == g["kappa"] and p["dhat"] == g["dhat"] and p["eps_v"] == g["eps_v"]
+    assert p["max_newton"] == g["max_newton"]
+    assert abs(np.linalg.norm(p["gravity"]) - g["gravity_magnitude"]) < 1e-12
+
+
+# ------------------------------------------------------------------ Neo-Hookean
+def test_neo_hookean_zero_for_rotations():
+    mu, lam = lame(1e5, 0.4)
+    for _ in range(5):
+        R = rand_rotation(RNG)
+        psi, P, H = O.neo_hookean(R, mu, lam)
+        assert abs(psi) < 1e-9 * mu
+        assert np.abs(P).max() < 1e-9 * mu
+
+
+def test_neo_hookean_small_strain_is_linear_elasticity():
+    """Psi(I + eps) -> mu |eps|^2 + lam/2 tr(eps)^2 for a small symmetric strain."""
+    mu, lam = lame(2e5, 0.45)
+    e = RNG.normal(size=(3, 3))
+    e = 0.5 * (e + e.T)
+    for s in (1e-3, 1e-4):
+        eps = s * e
+        psi, _, _ = O.neo_hookean(np.eye(3) + eps, mu, lam)
+        lin = mu * np.sum(eps * eps) + 0.5 * lam * np.trace(eps) ** 2
+        assert abs(psi - lin) / lin < 20 * s
+
+
+def test_neo_hookean_derivatives_match_finite_differences():
+    mu, lam = lame(1e5, 0.3)
+    F = np.eye(3) + 0.2 * RNG.normal(size=(3, 3))
+    assert np.linalg.det(F) > 0
+    psi, P, H = O.neo_hookean(F, mu, lam)
+    h = 1e-6
+    Pfd = np.zeros(9)
+    Hfd = np.zeros((9, 9))
+    for i in range(9):
+        d = np.zeros(9)
+        d[i] = h
+        pp, Pp, _ = O.neo_hookean(F.ravel() + d, mu, lam)
+        pm, Pm, _ = O.neo_hookean(F.ravel() - d, mu, lam)
+        Pfd[i] = (pp - pm) / (2 * h)
+        Hfd[i] = (Pp - Pm) / (2 * h)
+    assert np.allclose(P, Pfd, rtol=1e-6, atol=1e-6 * mu)
+    assert np.allclose(H, Hfd, rtol=1e-5, atol=1e-5 * mu)
+    assert np.allclose(H, H.T, atol=1e-9 * mu)
+
+
+# ------------------------------------------------------------------ PSD projection
+def test_psd_projection_matches_numpy_eigh():
+    for n in (3, 9, 12):
+        A = RNG.normal(size=(n, n))
+        A = A + A.T
+        P = O.project_psd(A)
+        w, V = np.linalg.eigh(A)
+        ref = (V * np.maximum(w, 0)) @ V.T
+        assert np.allclose(P, ref, atol=1e-12 * np.abs(A).max())
+        assert np.linalg.eigvalsh(P).min() > -1e-12 * np.abs(A).max()
+
+
+def test_psd_projection_keeps_psd_matrix():
+    B = RNG.normal(size=(12, 12))
+    A = B @ B.T
+    assert np.allclose(O.project_psd(A), A, atol=1e-12 * np.abs(A).max())
+
+
+def test_jacobi_eigenvalues_match_numpy():
+    A = RNG.normal(size=(9, 9))
+    A = A + A.T
+    w, V = O.eigh(A)
+    assert np.allclose(np.sort(w), np.linalg.eigvalsh(A), atol=1e-12 * np.abs(A).max())
+    assert np.allclose(V.T @ V, np.eye(9), atol=1e-12)
+
+
+# ------------------------------------------------------------------ barrier
+def test_barrier_closed_form_and_smoothness_at_dhat():
+    dhat = 1e-3
+    b, b1, b2 = O.barrier(dhat, dhat)
+    assert b == 0 and b1 == 0 and b2 == 0  # C2 at dhat
+    assert np.all(O.barrier(2 * dhat, dhat) == 0)
+    b, _, _ = O.barrier(dhat / 2, dhat)
+    assert math.isclose(b, (dhat / 2) ** 2 * math.log(2), rel_tol=1e-14)
+    for d in (1e-6, 1e-5, 3e-4, 9e-4):
+        b, b1, b2 = O.barrier(d, dhat)
+        h = d * 1e-5
+        bp, bm = O.barrier(d + h, dhat), O.barrier(d - h, dhat)
+        assert b > 0 and b1 < 0 and b2 > 0
+        assert math.isclose(b1, (bp[0] - bm[0]) / (2 * h), rel_tol=1e-6)
+        assert math.isclose(b2, (bp[1] - bm[1]) / (2 * h), rel_tol=1e-6)
+    assert O.barrier(1e-12, dhat)[0] > O.barrier(1e-9, dhat)[0] > O.barrier(1e-6, dhat)[0]
+
+
+# ------------------------------------------------------------------ distances
+def brute_pt(x):
+    p, a, b, c = x[0:3], x[3:6], x[6:9], x[9:12]
+    u = np.linspace(0, 1, 201)
+    U, V = np.meshgrid(u, u)
+    m = U + V <= 1
+    Q = a + U[m, None] * (b - a) + V[m, None] * (c - a)
+    k = np.argmin(((Q - p) ** 2).sum(1))
+    x0 = np.array([U[m][k], V[m][k]])
+    f = lambda z: np.sum((a + z[0] * (b - a) + z[1] * (c - a) - p) ** 2)
+    r = minimize(f, x0, method="SLSQP", bounds=[(0, 1), (0, 1)],
+                 constraints=[{"type": "ineq", "fun": lambda z: 1 - z[0] - z[1]}], options={"ftol": 1e-30, "maxiter": 500})
+    return min(r.fun, f(x0))
+
+
+def brute_ee(x):
+    a0, a1, b0, b1 = x[0:3], x[3:6], x[6:9], x[9:12]
+    u = np.linspace(0, 1, 201)
+    U, V = np.meshgrid(u, u)
+    A = a0 + U.ravel()[:, None] * (a1 - a0)
+    B = b0 + V.ravel()[:, None] * (b1 - b0)
+    k = np.argmin(((A - B) ** 2).sum(1))
+    f = lambda z: np.sum((a0 + z[0] * (a1 - a0) - b0 - z[1] * (b1 - b0)) ** 2)
+    x0 = np.array([U.ravel()[k], V.ravel()[k]])
+    r = minimize(f, x0, method="L-BFGS-B", bounds=[(0, 1), (0, 1)], options={"ftol": 1e-30, "gtol": 1e-30})
+    return min(r.fun, f(x0))
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_distance_matches_brute_force(kind):
+    seen = set()
+    for _ in range(300):
+        x = RNG.normal(size=12) * 0.01
+        d2, t, _, _ = O.pair_dist2(kind, x)
+        ref = brute_pt(x) if kind == 0 else brute_ee(x)
+        seen.add(t)
+        assert abs(d2 - ref) <= 1e-9 * max(ref, 1e-12), (kind, t, d2, ref)
+    assert len(seen) >= (6 if kind == 0 else 7)  # most region types were exercised
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_distance_derivatives_match_finite_differences(kind):
+    for _ in range(40):
+        x = RNG.normal(size=12) * 0.01
+        d2, t, g, H = O.pair_dist2(kind, x)
+        h = 1e-8
+        for i in range(12):
+            e = np.zeros(12)
+            e[i] = h
+            fp = O.pair_dist2_typed(kind, t, x + e)
+            fm = O.pair_dist2_typed(kind, t, x - e)
+            assert abs((fp - fm) / (2 * h) - g[i]) <= 1e-6 * max(np.abs(g).max(), 1e-12)
+        # Hessian by differences of the AD gradient at fixed type
+        for i in range(12):
+            e = np.zeros(12)
+            e[i] = 1e-7
+            _, tp, gp, _ = O.pair_dist2(kind, x + e)
+            _, tm, gm, _ = O.pair_dist2(kind, x - e)
+            if tp != t or tm != t:
+                continue
+            assert np.allclose((gp - gm) / 2e-7, H[i], atol=1e-5 * max(np.abs(H).max(), 1e-12))
+
+
+def test_pt_distance_continuous_across_regions():
+    """On the boundary between two regions both typed formulas give the same distance."""
+    a, b, c = np.array([0.0, 0, 0]), np.array([1.0, 0, 0]), np.array([0.0, 1, 0])
+    # point above the edge ab, exactly on the plane through ab perpendicular to the face
+    p = np.array([0.3, 0.0, 0.4])
+    x = np.concatenate([p, a, b, c])
+    d_face = O.pair_dist2_typed(0, 6, x)
+    d_edge = O.pair_dist2_typed(0, 3, x)
+    assert math.isclose(d_face, d_edge, rel_tol=1e-14)
+    # beyond vertex b, on the boundary of the vertex and edge regions
+    p = np.array([1.0, -0.2, 0.1])
+    x = np.concatenate([p, a, b, c])
+    assert math.isclose(O.pair_dist2_typed(0, 1, x), O.pair_dist2_typed(0, 3, x), rel_tol=1e-14)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_closest_point_coefficients(kind):
+    for _ in range(100):
+        x = RNG.normal(size=12) * 0.01
+        d2, _, _, _ = O.pair_dist2(kind, x)
+        c, n = O.pair_closest(kind, x)
+        diff = sum(c[i] * x[3 * i:3 * i + 3] for i in range(4))
+        assert math.isclose(np.linalg.norm(diff), math.sqrt(d2), rel_tol=1e-8)
+        assert np.allclose(diff / np.linalg.norm(diff), n, atol=1e-8)
+        assert abs(c.sum()) < 1e-12  # a rigid translation has no relative displacement
+
+
+# ------------------------------------------------------------------ EE mollifier, contact energy
+def test_mollifier_continuity_and_limits():
+    a0, a1 = np.array([0.0, 0, 0]), np.array([1.0, 0, 0])
+    eps = 0.01
+    perpendicular = np.concatenate([a0, a1, [0.5, -0.5, 0.1], [0.5, 0.5, 0.1]])
+    parallel = np.concatenate([a0, a1, [0.0, 0.0, 0.1], [1.0, 0.0, 0.1]])
+    assert O.mollifier(perpendicular, eps) == 1.0
+    assert O.mollifier(parallel, eps) == 0.0
+    # continuity across c = eps: |a x b|^2 = sin^2(th) for unit edges
+    th = math.asin(math.sqrt(eps))
+    for d in (-1e-9, 1e-9):
+        b1 = np.array([0.5 + math.cos(th + d), math.sin(th + d), 0.1])
+        x = np.concatenate([a0, a1, [0.5, 0, 0.1], b1])
+        assert abs(O.mollifier(x, eps) - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_contact_barrier_derivatives_match_finite_differences(kind):
+    dhat, kappa = 1e-3, 3e6
+    n_checked = 0
+    while n_checked < 10:
+        x = RNG.normal(size=12) * 1e-3
+        d2, t, _, _ = O.pair_dist2(kind, x)
+        if not (1e-8 < d2 < (0.9 * dhat) ** 2):
+            continue
+        eps = 1e-3 * np.sum((x[3:6] - x[0:3]) ** 2) * np.sum((x[9:12] - x[6:9]) ** 2) if kind else 0.0
+        E, g, H = O.contact_barrier(kind, x, dhat, kappa, eps)
+        h = 1e-10
+        for i in range(12):
+            e = np.zeros(12)
+            e[i] = h
+            _, t2, _, _ = O.pair_dist2(kind, x + e)
+            _, t3, _, _ = O.pair_dist2(kind, x - e)
+            if t2 != t or t3 != t:
+                continue
+            Ep, gp, _ = O.contact_barrier(kind, x + e, dhat, kappa, eps)
+            Em, gm, _ = O.contact_barrier(kind, x - e, dhat, kappa, eps)
+            assert abs((Ep - Em) / (2 * h) - g[i]) <= 1e-5 * np.abs(g).max()
+            assert np.allclose((gp - gm) / (2 * h), H[i], atol=1e-4 * np.abs(H).max())
+        n_checked += 1
+
+
+# ------------------------------------------------------------------ friction smoothing
+def test_friction_f0_is_c1_and_matches_limits():
+    eh = 1e-5
+    f_lo = O.friction_f(eh * (1 - 1e-12), eh)
+    f_hi = O.friction_f(eh * (1 + 1e-12), eh)
+    assert math.isclose(f_lo[0], f_hi[0], rel_tol=1e-9) and math.isclose(f_lo[1], f_hi[1], abs_tol=1e-9)
+    f0 = O.friction_f(0.0, eh)
+    assert math.isclose(f0[0], eh / 3, rel_tol=1e-15) and f0[1] == 0.0
+    for y in (0.1 * eh, 0.5 * eh, 0.9 * eh):
+        h = 1e-6 * eh
+        fp, fm = O.friction_f(y + h, eh), O.friction_f(y - h, eh)
+        f = O.friction_f(y, eh)
+        assert math.isclose(f[1], (fp[0] - fm[0]) / (2 * h), rel_tol=1e-6)
+        assert math.isclose(f[2], (fp[1] - fm[1]) / (2 * h), rel_tol=1e-6)
+        assert 0 < f[1] <= 1
+
+
+# ------------------------------------------------------------------ ACCD
+def true_toi(kind, x, p, n=20001):
+    ts = np.linspace(0, 1, n)
+    ds = np.array([O.pair_dist2(kind, x + t * p)[0] for t in ts])
+    hit = np.nonzero(ds <= 0)[0]
+    if len(hit):
+        return ts[hit[0]]
+    # refine the minimum by bisection on the sign of d^2 - tiny
+    k = np.argmin(ds)
+    return 1.0 if ds[k] > 1e-24 else ts[k]
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_accd_is_conservative_against_bisection(kind):
+    n_hit = 0
+    for trial in range(120):
+        x = RNG.normal(size=12) * 0.01
+        d2 = O.pair_dist2(kind, x)[0]
+        if d2 < 1e-8:
+            continue
+        # aim the first primitive at the second so that many trials collide
+        p = RNG.normal(size=12) * 0.01
+        target = x[6:9] if kind == 0 else 0.5 * (x[6:9] + x[9:12])
+        src = x[0:3] if kind == 0 else 0.5 * (x[0:3] + x[3:6])
+        shift = 2.0 * (target - src) * RNG.uniform(0.5, 1.5)
+        for i in range(2 if kind else 1):
+            p[3 * i:3 * i + 3] += shift
+        t, it = O.accd(kind, x, p)
+        assert 0 < t <= 1
+        d_at = O.pair_dist2(kind, x + t * p)[0]
+        assert d_at > 0
+        # no contact before t: sample the path densely
+        for s in np.linspace(0, t, 200):
+            assert O.pair_dist2(kind, x + s * p)[0] > 0
+        if t < 1:
+            n_hit += 1
+            # and not grossly conservative: the gap left is about s*d at the reported time
+            dist_t = math.sqrt(d_at)
+            assert dist_t <= math.sqrt(d2)
+    assert n_hit >= 10
+
+
+def test_accd_returns_one_without_contact():
+    x = np.array([0, 0, 0.1, 0, 0, 0, 1, 0, 0, 0, 1, 0], dtype=float)
+    p = np.zeros(12)
+    p[0:3] = [0.1, 0.1, 0.0]  # slides parallel to the triangle, never touches
+    t, _ = O.accd(0, x, p)
+    assert t == 1.0
+    t, it = O.accd(0, x, np.zeros(12))
+    assert t == 1.0 and it == 0
+
+
+def test_accd_head_on_toi():
+    """A point falling straight onto a triangle: contact at t* = 0.1/0.2 = 0.5; ACCD stops
+    just before it, leaving at least the s = 0.1 fraction of the initial gap."""
+    x = np.array([0.2, 0.2, 0.1, 0, 0, 0, 1, 0, 0, 0, 1, 0], dtype=float)
+    p = np.zeros(12)
+    p[2] = -0.2
+    t, _ = O.accd(0, x, p)
+    assert 0.45 - 1e-12 <= t < 0.5
+    assert O.pair_dist2(0, x + t * p)[0] ** 0.5 >= 0.1 * 0.1 * 0.99
+
+
+# ------------------------------------------------------------------ mass properties
+def test_box_mass_properties_closed_form():
+    hx, hy, hz = 0.03, 0.02, 0.01
+    v, t = S.box_surface((hx, hy, hz))
+    c = np.array([0.1, -0.2, 0.05])
+    rho = 700.0
+    M, vol = O.mass_properties(v + c, t, rho)
+    V = 8 * hx * hy * hz
+    m = rho * V
+    assert math.isclose(vol, V, rel_tol=1e-12)
+    assert math.isclose(M[0, 0], m, rel_tol=1e-12)
+    assert np.allclose(M[0, 1:], m * c, rtol=1e-12)
+    second = m * (np.diag([hx * hx, hy * hy, hz * hz]) / 3.0) + m * np.outer(c, c)
+    assert np.allclose(M[1:, 1:], second, rtol=1e-11, atol=1e-16)
+    assert np.allclose(M, M.T)
+
+
+def test_hull_mass_positive_definite():
+    rng = S.SplitMix64(7)
+    v, t = S.hull_object(rng, 200)
+    M, vol = O.mass_properties(v, t, 1000.0)
+    assert vol > 0 and np.linalg.eigvalsh(M).min() > 0
+    assert len(t) == 1584

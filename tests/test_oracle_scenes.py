@@ -1,0 +1,208 @@
+"""Scene-level pins of the CPU oracle: closed-form motions, static equilibrium, friction limits,
+rigidity, finite-difference gradients and the stepping invariants (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_05020_b300 import scenes as S
+
+G = 9.8
+
+
+def test_free_fall_matches_implicit_euler_closed_form():
+    """No contact, rigid translation: v_{n+1} = v_n + h g and x_{n+1} = x_n + h v_{n+1}."""
+    h = 0.01
+    p = S.scene_params(h)
+    env = S.single_tet_env(n_steps=10)
+    e = O.OracleEnv(p, env)
+    x0, _ = e.state()
+    assert e.step(10) == "DONE"
+    x, v = e.state()
+    vz = 0.0
+    z = 0.0
+    for _ in range(10):
+        vz = vz - h * G
+        z = z + h * vz
+    assert np.allclose(v.reshape(-1, 3)[:, 2], vz, rtol=1e-9)
+    assert np.allclose((x - x0).reshape(-1, 3)[:, 2], z, rtol=1e-9)
+    assert np.allclose((x - x0).reshape(-1, 3)[:, :2], 0, atol=1e-12)
+
+
+@pytest.mark.parametrize("body", ["tet", "rigid", "block"])
+def test_resting_body_contact_forces_balance_weight(body):
+    """Static equilibrium on a ground triangle: sum of kappa |b'(d_k)| = m g (barrier in N)."""
+    p = S.scene_params(0.01, newton_tol=1e-8)
+    env = S.resting_env(body, n_steps=150)
+    e = O.OracleEnv(p, env)
+    assert e.step(150) == "DONE"
+    x, v = e.state()
+    _, d2 = e.contacts(x)
+    assert len(d2) >= 3 and np.all(np.sqrt(d2) < p["dhat"]) and np.all(d2 > 0)
+    F = sum(p["kappa"] * abs(O.barrier(math.sqrt(q), p["dhat"])[1]) for q in d2)
+    if body == "rigid":
+        M, vol = e.body_mass(0)
+        m = M[0, 0]
+    else:
+        m = e.soft_mass(len(env["soft"][0]["verts"])).sum()
+    tol = 5e-5 if body == "block" else 1e-5
+    assert abs(F / (m * G) - 1) < tol
+
+
+def _slope_velocity(e, env, incline_deg):
+    x, v = e.state()
+    th = math.radians(incline_deg)
+    down = np.array([math.cos(th), 0, -math.sin(th)])  # direction of steepest descent
+    return float(v[0:3] @ down)
+
+
+@pytest.mark.slow
+def test_incline_stick_and_slip():
+    """Rigid box on a 20 deg incline: mu > tan(th) sticks (creep below eps_v); mu < tan(th)
+    slides with acceleration g (sin th - mu cos th). A tight Newton tolerance is used because
+    the normal forces that friction lags are only as accurate as the force residual, and a
+    step-size stopping rule leaves large residuals against the stiff barrier."""
+    th = 20.0
+    p = S.scene_params(0.01, newton_tol=1e-8)
+    env = S.resting_env("rigid", n_steps=60, mu=0.5, incline_deg=th)
+    e = O.OracleEnv(p, env)
+    assert e.step(60) == "DONE"
+    assert abs(_slope_velocity(e, env, th)) < p["eps_v"]
+    mu = 0.2
+    env = S.resting_env("rigid", n_steps=60, mu=mu, incline_deg=th)
+    e = O.OracleEnv(p, env)
+    e.step(20)
+    v20 = _slope_velocity(e, env, th)
+    e.step(30)
+    v50 = _slope_velocity(e, env, th)
+    a = (v50 - v20) / (30 * 0.01)
+    ref = G * (math.sin(math.radians(th)) - mu * math.cos(math.radians(th)))
+    assert abs(a / ref - 1) < 0.02
+
+
+def test_spinning_body_stays_rigid():
+    p = S.scene_params(0.01)
+    env = S.spinning_body_env(n_steps=20, omega=(0, 0, 20.0))
+    e = O.OracleEnv(p, env)
+    assert e.step(20) == "DONE"
+    x, _ = e.state()
+    A = np.stack([x[3:6], x[6:9], x[9:12]], axis=1)
+    assert np.abs(A @ A.T - np.eye(3)).max() < 1e-3
+    # it did rotate: about 20 rad/s * 0.2 s = 4 rad, up to implicit-Euler damping
+    ang = math.atan2(A[1, 0], A[0, 0])
+    assert abs(ang) > 0.3
+
+
+def _fd_check(e, q, idx, rel=1e-5):
+    E, g = e.eval(q)
+    scale = np.abs(g).max()
+    for i in idx:
+        h = 1e-8 if i < e.ndof else 1e-8
+        qp = q.copy()
+        qm = q.copy()
+        qp[i] += h
+        qm[i] -= h
+        fd = (e.eval(qp, grad=False) - e.eval(qm, grad=False)) / (2 * h)
+        assert abs(fd - g[i]) <= rel * scale + 1e-9 * abs(g[i]), (i, fd, g[i], scale)
+
+
+def test_env_gradient_matches_finite_differences_with_contact_and_friction():
+    """Whole incremental potential (inertia, Neo-Hookean, barrier, lagged friction, affine
+    inertia/orthogonality) against central differences at a state with active contacts."""
+    p = S.scene_params(0.01)
+    env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+    e = O.OracleEnv(p, env)
+    e.step(30)  # plates in contact, lifting phase (gravity and friction active)
+    x, v = e.state()
+    c, _ = e.contacts(x)
+    assert len(c) > 10
+    rng = np.random.default_rng(0)
+    q = x + rng.normal(size=x.size) * 1e-6
+    # pick DOFs of surface vertices touching the plates plus random ones
+    idx = sorted(set(rng.choice(e.ndof, 40, replace=False).tolist()) | {0, 1, 2})
+    _fd_check(e, q, idx)
+
+
+def test_env_gradient_fd_rigid_body_terms():
+    p = S.scene_params(0.01)
+    env = S.resting_env("rigid", n_steps=30, mu=0.4, incline_deg=10)
+    e = O.OracleEnv(p, env)
+    e.step(20)
+    x, _ = e.state()
+    q = x.copy()
+    q[3:12] += np.random.default_rng(1).normal(size=9) * 1e-4  # break orthogonality a little
+    _fd_check(e, q, list(range(12)))
+
+
+def test_hessian_is_symmetric_psd():
+    p = S.scene_params(0.01)
+    env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+    e = O.OracleEnv(p, env)
+    e.step(25)
+    x, _ = e.state()
+    H = e.hessian(x)
+    assert np.allclose(H, H.T, atol=1e-12 * np.abs(H).max())
+    # free block (soft DOFs): PSD up to round-off
+    n = 3 * 125
+    w = np.linalg.eigvalsh(H[:n, :n])
+    assert w.min() > -1e-10 * w.max()
+
+
+def test_line_search_energy_is_monotone():
+    """Within each step, every unconstrained Newton iteration does not increase the energy."""
+    p = S.scene_params(0.01)
+    env = S.cube_squeeze_env(0, n_steps=30, close_steps=15)
+    e = O.OracleEnv(p, env)
+    e.trace(True)
+    assert e.step(30) == "DONE"
+    tr = e.trace_energies()
+    n_checked = 0
+    for k in range(len(tr) - 1):
+        s, it, constrained, E = tr[k]
+        s2, it2, _, E2 = tr[k + 1]
+        if s2 == s and it2 == it + 1 and constrained == 0:
+            assert E2 <= E
+            n_checked += 1
+    assert n_checked > 10
+
+
+def test_constraint_candidates_are_conservative():
+    """Every non-excluded pair closer than dhat appears among the dhat/2-inflated candidates."""
+    p = S.scene_params(0.01)
+    env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+    e = O.OracleEnv(p, env)
+    e.step(25)
+    x, _ = e.state()
+    cand = {tuple(r) for r in e.candidates(x)}
+    contacts, d2 = e.contacts(x)
+    assert len(contacts) > 0
+    for r in contacts:
+        assert (r[0], r[1], r[2]) in cand
+    assert np.all(d2 < p["dhat"] ** 2)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mu, lifts", [(0.5, True), (0.0, False)])
+def test_cube_grasp_lift_outcome_and_invariants(mu, lifts):
+    """Plates squeeze the cube with gravity off, then lift with gravity on: with friction the
+    cube follows the plates up; without friction it is not lifted. No intersection and no
+    inverted tet at any checked step."""
+    p = S.scene_params(0.01)
+    env = S.cube_squeeze_env(0, n_steps=50, close_steps=30, mu=mu)
+    e = O.OracleEnv(p, env)
+    x0, _ = e.state()
+    z0 = x0[: 3 * 125].reshape(-1, 3)[:, 2].mean()
+    for s in range(5):
+        e.step(10)
+        x, _ = e.state()
+        inv = e.invariants(x)
+        assert inv["intersections"] == 0 and inv["inverted"] == 0 and inv["min_dist"] > 0
+    assert e.status()["status"] == "DONE"
+    x, _ = e.state()
+    dz = x[: 3 * 125].reshape(-1, 3)[:, 2].mean() - z0
+    plate_dz = 20 * 0.01 * 0.02
+    if lifts:
+        assert abs(dz - plate_dz) < 0.1 * plate_dz
+    else:
+        assert dz < 0.2 * plate_dz
