@@ -1,0 +1,182 @@
+/*
+ * ipc.h — C ABI of the B300-native multi-environment IPC stepper.
+ *
+ * The library advances a batch of independent grasp environments with Incremental Potential
+ * Contact (GRIP, arXiv 2503.05020, Sec. II-C: barrier augmentation, CCD and a projected Newton
+ * solver with a step-size filter; Sec. III-A: the environments are isolated in collision
+ * detection and step-size filtering, each one stops on its own criterion and is frozen, and a
+ * failed environment is detected and excluded; Sec. III-D: dt, kappa, dhat, eps_v, FP64 and at
+ * most 100 Newton iterations). Soft bodies are Neo-Hookean tet meshes; rigid parts are 12-DOF
+ * affine bodies (Sec. I, IPC coupled with affine body dynamics).
+ *
+ * Conventions
+ *  - Every function returns an ipc_status; on error, ipc_last_error() returns a message that
+ *    stays valid until the next call on the same host thread.
+ *  - All descriptor arrays are HOST pointers. They are copied during the call; the caller keeps
+ *    ownership and may free them on return.
+ *  - Output buffers are HOST pointers owned by the caller. When a buffer is too small the call
+ *    returns IPC_ERR_ARG and *written (if not NULL) gets the required byte count.
+ *  - Device memory is allocated by the library (cudaMalloc on the scene's device) and released
+ *    by ipc_scene_destroy. Work is issued on the scene's stream (borrowed, or created when the
+ *    descriptor passes NULL). ipc_step returns after the step's work has completed.
+ *  - A scene is not thread-safe: use one scene per host thread.
+ *  - Layout of an environment's DOF vector ("DOFs"): the vertices of its soft bodies in the
+ *    order they were given (x, y, z each, metres), then for each affine body its 12 affine
+ *    coordinates q = (p, a1, a2, a3) where a rest point xb sits at p + xb0*a1 + xb1*a2 + xb2*a3.
+ */
+#ifndef IPC_B300_H
+#define IPC_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ipc_scene ipc_scene;
+
+typedef enum {
+  IPC_OK = 0,
+  IPC_ERR_ARG = 1,            /* bad argument, unknown env id, output buffer too small */
+  IPC_ERR_OOM = 2,            /* device allocation failed */
+  IPC_ERR_BUDGET = 3,         /* the env would exceed the scene's HBM budget (admission) */
+  IPC_ERR_CUDA = 4,           /* a CUDA call failed; the message names it */
+  IPC_ERR_INIT_INTERSECT = 5, /* initial state has a touching or intersecting pair: IPC needs an
+                                 intersection-free start (Sec. III-C) */
+  IPC_ERR_INIT_INVERTED = 6,  /* a tet has non-positive rest or initial volume */
+  IPC_ERR_NO_ENV = 7,         /* the scene holds no environment */
+  IPC_ERR_INTERNAL = 8        /* an internal capacity or traversal limit was hit */
+} ipc_status;
+
+typedef enum { IPC_FP64 = 0, IPC_MIXED = 1 } ipc_precision;
+
+/* Solver parameters shared by every environment of a scene (Sec. III-D gives dt = 0.01 s,
+ * kappa = 3e6 kg/s^2, dhat = 1e-3 m, eps_v = 1e-3 m/s, 100 Newton iterations, FP64). */
+typedef struct {
+  double dt;             /* time step h (s) */
+  double dhat;           /* barrier activation distance (m) */
+  double kappa;          /* barrier stiffness (kg/s^2) */
+  double eps_v;          /* friction static/dynamic transition speed (m/s) */
+  double newton_tol;     /* converged when ||p||_inf / h < newton_tol (m/s) */
+  double pcg_rel_tol;    /* PCG stops at ||r|| <= pcg_rel_tol ||b|| */
+  double kappa_affine;   /* affine-body orthogonality stiffness (Pa) */
+  double gravity[3];     /* m/s^2 */
+  int32_t max_newton;    /* Newton iterations per step before the env is marked FAILED */
+  int32_t max_ls_halvings; /* line-search halvings before the env is marked FAILED */
+  int32_t max_pcg_iters; /* PCG iteration cap per solve */
+  int32_t precision;     /* ipc_precision */
+  uint64_t hbm_budget_bytes; /* 0 = no admission limit */
+  int32_t device;        /* CUDA device ordinal */
+  int32_t pad;
+  void* cuda_stream;     /* cudaStream_t to borrow, or NULL for a library-owned stream */
+} ipc_scene_desc;
+
+/* Soft body: a Neo-Hookean tet mesh. verts: n_verts*3 doubles (rest = initial positions);
+ * tets: n_tets*4 int32 with positive rest orientation; tris: n_tris*3 int32 outward surface
+ * triangles (vertex indices of this body); kinematic: n_verts bytes, 1 = the vertex follows the
+ * schedule (may be NULL). */
+typedef struct {
+  int32_t n_verts, n_tets, n_tris, pad;
+  const double* verts;
+  const int32_t* tets;
+  const int32_t* tris;
+  const uint8_t* kinematic;
+  double youngs, poisson, density;
+} ipc_soft_body_desc;
+
+/* Affine body: closed outward rest surface (n_verts*3 doubles, n_tris*3 int32), density,
+ * initial coordinates q0 and rates qdot0 (12 each). A kinematic body follows the schedule. */
+typedef struct {
+  int32_t n_verts, n_tris, kinematic, pad;
+  const double* verts;
+  const int32_t* tris;
+  double density;
+  double q0[12];
+  double qdot0[12];
+} ipc_affine_body_desc;
+
+/* One environment. gravity_on: n_steps bytes (gravity acts during step s when 1).
+ * targets: n_steps * (n_soft + n_affine) * 12 doubles: for step s and body b (soft bodies
+ * first) the affine map the body's kinematic vertices (soft, applied to their initial
+ * positions) or the kinematic affine body itself must reach at the end of step s. */
+typedef struct {
+  int32_t n_soft, n_affine, n_steps, pad;
+  const ipc_soft_body_desc* soft;
+  const ipc_affine_body_desc* affine;
+  double friction_mu;
+  const uint8_t* gravity_on;
+  const double* targets;
+} ipc_env_desc;
+
+typedef enum {
+  IPC_Q_DOFS = 0,        /* double[ndof]: current DOFs */
+  IPC_Q_VELOCITIES = 1,  /* double[ndof]: current DOF rates */
+  IPC_Q_STATUS = 2,      /* int32[4]: status (0 ACTIVE, 1 DONE, 2 FAILED), reason (0 none,
+                            1 Newton cap, 2 line search, 3 non-finite), steps done, next step */
+  IPC_Q_STATS = 3,       /* int64[5]: Newton iterations, PCG iterations, line-search halvings,
+                            steps, ACCD iterations (cumulative) */
+  IPC_Q_CANDIDATES = 4,  /* int32[n][3]: (kind 0 = point-triangle / 1 = edge-edge, i, j) of the
+                            dhat/2-inflated box candidates at the current DOFs, env-local
+                            surface-vertex / triangle / edge indices, sorted */
+  IPC_Q_CONTACTS = 5,    /* int32[n][4]: (kind, i, j, distance type) of candidates closer than
+                            dhat, sorted like CANDIDATES */
+  IPC_Q_POINTS = 6,      /* double[n_points][3]: world positions of all surface-capable points
+                            (soft vertices, then affine rest vertices mapped by q) */
+  IPC_Q_SIZES = 7,       /* int64[8]: ndof, points, surface vertices, edges, triangles, tets,
+                            bodies, steps */
+  IPC_Q_INTERSECTIONS = 8 /* int64[2]: segment-triangle intersections, inverted tets */
+} ipc_query_kind;
+
+/* Create / destroy a scene on desc->device. */
+ipc_status ipc_scene_create(const ipc_scene_desc* desc, ipc_scene** out);
+ipc_status ipc_scene_destroy(ipc_scene* scene);
+
+/* Add an environment (copied). Rejects inverted tets (IPC_ERR_INIT_INVERTED), an initial
+ * state with a touching or crossing pair (IPC_ERR_INIT_INTERSECT; checked when the batch is
+ * next laid out on the device, i.e. at the next ipc_step / query), and an env whose estimated
+ * device bytes do not fit the remaining HBM budget (IPC_ERR_BUDGET). */
+ipc_status ipc_env_add(ipc_scene* scene, const ipc_env_desc* env, int32_t* env_id);
+/* Remove an environment; its slot and memory are reused. */
+ipc_status ipc_env_remove(ipc_scene* scene, int32_t env_id);
+
+/* Advance every ACTIVE environment by up to n_steps time steps (Sec. III-A: each env has its
+ * own step size, stopping test and failure state; a failure never fails the call). */
+ipc_status ipc_step(ipc_scene* scene, int32_t n_steps);
+
+/* Copy one result of one environment into out (host). */
+ipc_status ipc_query(ipc_scene* scene, int32_t env_id, int32_t kind, void* out, size_t out_bytes,
+                     size_t* written);
+
+/* Overwrite an environment's state: DOFs x and rates v (ndof doubles each, host) and the index
+ * of its next step. Used for checkpoint/resume and for parity checks. */
+ipc_status ipc_env_set_state(ipc_scene* scene, int32_t env_id, const double* x, const double* v,
+                             int32_t step);
+
+/* Incremental potential and its gradient at DOFs q (host, ndof doubles) for the env's next
+ * step, taking its current state as x^t (predicted positions and friction lagged at x^t).
+ * grad may be NULL. Diagnostic entry point (parity checks); it recomputes the step set-up. */
+ipc_status ipc_eval(ipc_scene* scene, int32_t env_id, const double* q, double* energy,
+                    double* grad);
+
+/* Streaming schedule: overwrite, for every ACTIVE env (in env-id order of the ids returned by
+ * ipc_env_add), the kinematic targets of its next step from a host array laid out as
+ * [env][body][12]. bytes must equal 12*8*sum over active envs of their body counts. */
+ipc_status ipc_set_next_targets(ipc_scene* scene, const double* targets, size_t bytes);
+
+/* Copy the DOFs of every ACTIVE-or-finished env, in env-id order, into one host array. */
+ipc_status ipc_get_all_dofs(ipc_scene* scene, double* out, size_t out_bytes, size_t* written);
+
+/* Estimated device bytes an env would hold (used for admission control). */
+ipc_status ipc_env_estimate_bytes(const ipc_env_desc* env, int32_t precision, uint64_t* bytes);
+
+/* Number of kernel launches issued by this scene since creation (instrumentation). */
+ipc_status ipc_launch_count(ipc_scene* scene, int64_t* count);
+
+const char* ipc_last_error(void);
+const char* ipc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPC_B300_H */

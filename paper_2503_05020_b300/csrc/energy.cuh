@@ -1,0 +1,427 @@
+// Energy stencils of the incremental potential
+//   E(x) = 1/2 |x - x~|_M^2 + h^2 [ sum_tets V Psi(F) + sum_bodies kappa_A V |A A^T - I|^2
+//                                  + kappa sum_k e_k b(d_k) + sum_k mu lambda_k f0(|P_k rel_k|) ]
+// (IPC 2020 incremental potential with the affine-body orthogonality term of Lan et al. 2022),
+// each written per element so that one thread owns one tet, body or contact. Outputs are
+// per-element energies, gradients and PSD-projected Hessians; a later pass gathers them in a
+// fixed order (deterministic, no atomics on values).
+#pragma once
+#include "common.cuh"
+#include "geometry.cuh"
+
+enum { MODE_ENERGY = 0, MODE_GRAD = 1, MODE_HESS = 2 };
+
+struct StepConst {
+  double h, dhat, kappa, eps_v, kappa_affine;
+  double g[3];
+};
+
+// ----------------------------------------------------------------- point positions
+// soft point: its node; affine point: ((p + xb0 a1) + xb1 a2) + xb2 a3, rounded as written.
+__global__ void k_points(int n_pts, const int* __restrict__ pt_node, const double* __restrict__ pt_xb,
+                         const int* __restrict__ body_node, const double* __restrict__ q, double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pts) return;
+  int nd = pt_node[i];
+  if (nd >= 0) {
+    out[3 * i] = q[3 * nd];
+    out[3 * i + 1] = q[3 * nd + 1];
+    out[3 * i + 2] = q[3 * nd + 2];
+  } else {
+    const double* b = q + 3 * (long)body_node[-1 - nd];
+    double x0 = pt_xb[3 * i], x1 = pt_xb[3 * i + 1], x2 = pt_xb[3 * i + 2];
+    for (int k = 0; k < 3; ++k) {
+      double r = add_mul_rn(b[k], x0, b[3 + k]);
+      r = add_mul_rn(r, x1, b[6 + k]);
+      r = add_mul_rn(r, x2, b[9 + k]);
+      out[3 * i + k] = r;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- Neo-Hookean tets
+// Analytic eigensystem of d2Psi/dF2 (Smith, de Goes & Kim 2019) for
+// Psi = mu/2 (|F|^2 - 3) - mu ln J + lam/2 (ln J)^2 with F = U diag(s) V^T:
+//   scaling modes: eigenpairs of A_ii = mu + (mu - lam lnJ + lam)/s_i^2, A_ij = lam/(s_i s_j),
+//   twist (i,j):   mu + (lam lnJ - mu)/(s_i s_j),  U (e_i e_j^T - e_j e_i^T) V^T / sqrt 2,
+//   flip (i,j):    mu + (mu - lam lnJ)/(s_i s_j),  U (e_i e_j^T + e_j e_i^T) V^T / sqrt 2.
+// Negative eigenvalues are dropped (projected Newton); the 12x12 Hessian is
+// h^2 V sum_m lam_m^+ w_m w_m^T with w_m[a] = Q_m b_a (b_a: shape-function gradients).
+template <int MODE>
+__global__ void k_elastic(int n_tets, const int4* __restrict__ tets, const double* __restrict__ prm,
+                          const int* __restrict__ tenv, const uint8_t* __restrict__ act, const double* __restrict__ q,
+                          double h2, double* __restrict__ tE, double* __restrict__ tg, double* __restrict__ tH,
+                          int* __restrict__ env_bad) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tets) return;
+  int e = tenv[t];
+  if (!act[e]) return;
+  int4 T = tets[t];
+  const double* P = prm + 12 * (long)t;
+  d3 x0 = ld3(q, T.x), x1 = ld3(q, T.y), x2 = ld3(q, T.z), x3 = ld3(q, T.w);
+  d3 c1 = x1 - x0, c2 = x2 - x0, c3 = x3 - x0;
+  double Bm[9];
+  for (int i = 0; i < 9; ++i) Bm[i] = P[i];
+  double vol = P[9], mu = P[10], lam = P[11];
+  // F = Ds Dm^-1, Ds columns = c1, c2, c3
+  double F[9];
+  const d3 Cc[3] = {c1, c2, c3};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      F[3 * r + c] = comp(Cc[0], r) * Bm[c] + comp(Cc[1], r) * Bm[3 + c] + comp(Cc[2], r) * Bm[6 + c];
+  double cof[9];
+  cof[0] = F[4] * F[8] - F[5] * F[7];
+  cof[1] = F[5] * F[6] - F[3] * F[8];
+  cof[2] = F[3] * F[7] - F[4] * F[6];
+  cof[3] = F[2] * F[7] - F[1] * F[8];
+  cof[4] = F[0] * F[8] - F[2] * F[6];
+  cof[5] = F[1] * F[6] - F[0] * F[7];
+  cof[6] = F[1] * F[5] - F[2] * F[4];
+  cof[7] = F[2] * F[3] - F[0] * F[5];
+  cof[8] = F[0] * F[4] - F[1] * F[3];
+  double J = F[0] * cof[0] + F[1] * cof[1] + F[2] * cof[2];
+  if (!(J > 0.0)) {
+    env_bad[e] = 1;
+    tE[t] = 0.0;
+    return;
+  }
+  double lnJ = log(J);
+  double tr = 0.0;
+  for (int i = 0; i < 9; ++i) tr += F[i] * F[i];
+  double w = h2 * vol;
+  tE[t] = w * (0.5 * mu * (tr - 3.0) - mu * lnJ + 0.5 * lam * lnJ * lnJ);
+  if (MODE == MODE_ENERGY) return;
+  // shape-function gradients b_a (rows): b1..b3 = rows of Dm^-1, b0 = -(b1 + b2 + b3)
+  d3 b[4];
+  b[1] = mk3(Bm[0], Bm[1], Bm[2]);
+  b[2] = mk3(Bm[3], Bm[4], Bm[5]);
+  b[3] = mk3(Bm[6], Bm[7], Bm[8]);
+  b[0] = mk3(-(Bm[0] + Bm[3] + Bm[6]), -(Bm[1] + Bm[4] + Bm[7]), -(Bm[2] + Bm[5] + Bm[8]));
+  // first Piola-Kirchhoff stress P = mu F + (lam lnJ - mu) cof(F) / J
+  double kk = (lam * lnJ - mu) / J;
+  double Pk[9];
+  for (int i = 0; i < 9; ++i) Pk[i] = mu * F[i] + kk * cof[i];
+  for (int a = 0; a < 4; ++a) {
+    d3 ga = mk3(Pk[0] * b[a].x + Pk[1] * b[a].y + Pk[2] * b[a].z, Pk[3] * b[a].x + Pk[4] * b[a].y + Pk[5] * b[a].z,
+                Pk[6] * b[a].x + Pk[7] * b[a].y + Pk[8] * b[a].z);
+    tg[12 * (long)t + 3 * a] = w * ga.x;
+    tg[12 * (long)t + 3 * a + 1] = w * ga.y;
+    tg[12 * (long)t + 3 * a + 2] = w * ga.z;
+  }
+  if (MODE == MODE_GRAD) return;
+  // SVD through the eigen-decomposition of F^T F
+  double C[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) C[3 * r + c] = F[r] * F[c] + F[3 + r] * F[3 + c] + F[6 + r] * F[6 + c];
+  double s2[3], V[9];
+  eig_sym3(C, s2, V);
+  double s[3];
+  for (int i = 0; i < 3; ++i) s[i] = sqrt(fmax(s2[i], 1e-300));
+  double U[9];  // U = F V diag(1/s)
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      U[3 * r + c] = (F[3 * r] * V[c] + F[3 * r + 1] * V[3 + c] + F[3 * r + 2] * V[6 + c]) / s[c];
+  // c_a = V^T b_a
+  d3 cb[4];
+  for (int a = 0; a < 4; ++a)
+    cb[a] = mk3(V[0] * b[a].x + V[3] * b[a].y + V[6] * b[a].z, V[1] * b[a].x + V[4] * b[a].y + V[7] * b[a].z,
+                V[2] * b[a].x + V[5] * b[a].y + V[8] * b[a].z);
+  double Hb[90];
+  for (int i = 0; i < 90; ++i) Hb[i] = 0.0;
+  // accumulate lam * w w^T over the 10 upper 3x3 blocks; w_a = U m_a where m_a = M c_a
+  auto add_mode = [&](double lm, const d3* m) {
+    if (!(lm > 0.0)) return;
+    d3 wv[4];
+    for (int a = 0; a < 4; ++a)
+      wv[a] = mk3(U[0] * m[a].x + U[1] * m[a].y + U[2] * m[a].z, U[3] * m[a].x + U[4] * m[a].y + U[5] * m[a].z,
+                  U[6] * m[a].x + U[7] * m[a].y + U[8] * m[a].z);
+    int blk = 0;
+    for (int a = 0; a < 4; ++a)
+      for (int bb = a; bb < 4; ++bb, ++blk)
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c) Hb[9 * blk + 3 * r + c] += lm * comp(wv[a], r) * comp(wv[bb], c);
+  };
+  // scaling modes
+  double A[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      A[3 * i + j] = (i == j) ? mu + (mu - lam * lnJ + lam) / (s[i] * s[i]) : lam / (s[i] * s[j]);
+  double la[3], av[9];
+  eig_sym3(A, la, av);
+  for (int k = 0; k < 3; ++k) {
+    d3 m[4];
+    for (int a = 0; a < 4; ++a) m[a] = mk3(av[k] * cb[a].x, av[3 + k] * cb[a].y, av[6 + k] * cb[a].z);
+    add_mode(la[k], m);
+  }
+  // twist and flip modes of each pair
+  const double r2 = 0.70710678118654752440;
+  for (int pr = 0; pr < 3; ++pr) {
+    int i = pr == 2 ? 0 : pr, j = pr == 2 ? 2 : pr + 1;
+    double ss = s[i] * s[j];
+    double lt = mu + (lam * lnJ - mu) / ss, lf = mu + (mu - lam * lnJ) / ss;
+    d3 mt[4], mf[4];
+    for (int a = 0; a < 4; ++a) {
+      double ci = comp(cb[a], i), cj = comp(cb[a], j);
+      double vt[3] = {0, 0, 0}, vf[3] = {0, 0, 0};
+      // (e_i e_j^T -/+ e_j e_i^T) c = e_i c_j -/+ e_j c_i
+      vt[i] = r2 * cj;
+      vt[j] = -r2 * ci;
+      vf[i] = r2 * cj;
+      vf[j] = r2 * ci;
+      mt[a] = mk3(vt[0], vt[1], vt[2]);
+      mf[a] = mk3(vf[0], vf[1], vf[2]);
+    }
+    add_mode(lt, mt);
+    add_mode(lf, mf);
+  }
+  for (int i = 0; i < 90; ++i) tH[90 * (long)t + i] = w * Hb[i];
+}
+
+// ----------------------------------------------------------------- affine bodies
+// Inertia 1/2 (q - q~)^T (M4 x I3) (q - q~) and orthogonality h^2 kappa_A V |A A^T - I|_F^2,
+// A[r][c] = q[3 + 3c + r]. d2/dA2 of |S|^2, S = A A^T - I, is
+// 4 [d_km (A^T A)_nl + A_kn A_ml + S_km d_ln] at (kl, mn); it is projected to PSD.
+template <int MODE>
+__global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int* __restrict__ benv,
+                         const uint8_t* __restrict__ bkin, const double* __restrict__ M4, const double* __restrict__ bvol,
+                         const uint8_t* __restrict__ act, const double* __restrict__ q, const double* __restrict__ qt,
+                         double h2kA, double* __restrict__ bE, double* __restrict__ bg, double* __restrict__ bH) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_bodies) return;
+  int e = benv[b];
+  if (!act[e]) return;
+  if (bkin[b]) {
+    bE[b] = 0.0;
+    if (MODE >= MODE_GRAD)
+      for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = 0.0;
+    if (MODE == MODE_HESS)
+      for (int i = 0; i < 144; ++i) bH[144 * (long)b + i] = (i % 13 == 0) ? 1.0 : 0.0;
+    return;
+  }
+  const double* Q = q + 3 * (long)bnode[b];
+  const double* Qt = qt + 3 * (long)bnode[b];
+  const double* M = M4 + 16 * (long)b;
+  double dq[12];
+  for (int i = 0; i < 12; ++i) dq[i] = Q[i] - Qt[i];
+  double Ein = 0.0, g[12];
+  for (int I = 0; I < 4; ++I)
+    for (int k = 0; k < 3; ++k) {
+      double s = 0.0;
+      for (int Jn = 0; Jn < 4; ++Jn) s += M[4 * I + Jn] * dq[3 * Jn + k];
+      g[3 * I + k] = s;
+      Ein += 0.5 * dq[3 * I + k] * s;
+    }
+  double A[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) A[3 * r + c] = Q[3 + 3 * c + r];
+  double S[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      S[3 * i + j] = A[3 * i] * A[3 * j] + A[3 * i + 1] * A[3 * j + 1] + A[3 * i + 2] * A[3 * j + 2] - (i == j ? 1.0 : 0.0);
+  double f = 0.0;
+  for (int i = 0; i < 9; ++i) f += S[i] * S[i];
+  double wk = h2kA * bvol[b];
+  bE[b] = Ein + wk * f;
+  if (MODE == MODE_ENERGY) return;
+  // gradient of |S|^2 wrt A: 4 S A
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      double sa = S[3 * k] * A[l] + S[3 * k + 1] * A[3 + l] + S[3 * k + 2] * A[6 + l];
+      g[3 + 3 * l + k] += wk * 4.0 * sa;
+    }
+  for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = g[i];
+  if (MODE == MODE_GRAD) return;
+  double Ho[81];
+  double AtA[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) AtA[3 * i + j] = A[i] * A[j] + A[3 + i] * A[3 + j] + A[6 + i] * A[6 + j];
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l)
+      for (int m = 0; m < 3; ++m)
+        for (int n = 0; n < 3; ++n) {
+          double v = A[3 * k + n] * A[3 * m + l];
+          if (k == m) v += AtA[3 * n + l];
+          if (l == n) v += S[3 * k + m];
+          Ho[(3 * k + l) * 9 + 3 * m + n] = 4.0 * v;
+        }
+  project_psd_jacobi<9>(Ho);
+  double* Hout = bH + 144 * (long)b;
+  for (int I = 0; I < 4; ++I)
+    for (int Jn = 0; Jn < 4; ++Jn)
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) Hout[(3 * I + k) * 12 + 3 * Jn + l] = (k == l) ? M[4 * I + Jn] : 0.0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l)
+      for (int m = 0; m < 3; ++m)
+        for (int n = 0; n < 3; ++n) {
+          int qi = 3 + 3 * l + k, qj = 3 + 3 * n + m;
+          Hout[qi * 12 + qj] += wk * Ho[(3 * k + l) * 9 + 3 * m + n];
+        }
+}
+
+// ----------------------------------------------------------------- contacts (barrier)
+struct ContactRec {
+  int pts[4];
+  int kind, type, env, cand;
+  double eps_x;
+};
+
+// h^2 kappa e(c) b(d) with PSD-projected Hessian; d = sqrt(s), grad b = b'/(2d) grad s,
+// hess b = (b''/(4 d^2) - b'/(4 d^3)) grad s grad s^T + b'/(2d) hess s.
+template <int MODE>
+__global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
+                          const double* __restrict__ ptx, double h2, double dhat, double kappa, double* __restrict__ sE,
+                          double* __restrict__ sg, double* __restrict__ sH) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_ct) return;
+  ContactRec c = ct[k];
+  if (!act[c.env]) return;
+  d3 X[4];
+  for (int i = 0; i < 4; ++i) X[i] = ld3(ptx, c.pts[i]);
+  double s, gs[12], Hs[78];
+  if (MODE == MODE_ENERGY) {
+    s = typed_d2(c.kind, c.type, X);
+  } else {
+    d2_derivs(c.kind, c.type, X, &s, gs, Hs);
+  }
+  double d = sqrt(s);
+  double b, b1, b2;
+  barrier3(d, dhat, &b, &b1, &b2);
+  double m = 1.0, m1 = 0.0, m2 = 0.0, cc = 0.0, gc[12], Hc[78];
+  if (c.kind == 1) {
+    double P[12], N, Ng[12], Nh[78];
+    for (int i = 0; i < 4; ++i) {
+      P[3 * i] = X[i].x;
+      P[3 * i + 1] = X[i].y;
+      P[3 * i + 2] = X[i].z;
+    }
+    if (MODE == MODE_ENERGY) {
+      d3 n = cross(X[1] - X[0], X[3] - X[2]);
+      cc = dot(n, n);
+    } else {
+      ee_poly(P, P + 3, P + 6, P + 9, &N, Ng, Nh, &cc, gc, Hc);
+    }
+    if (cc < c.eps_x) {
+      double r = cc / c.eps_x;
+      m = -r * r + 2.0 * r;
+      m1 = (-2.0 * r + 2.0) / c.eps_x;
+      m2 = -2.0 / (c.eps_x * c.eps_x);
+    }
+  }
+  double scale = h2 * kappa;
+  sE[k] = scale * m * b;
+  if (MODE == MODE_ENERGY) return;
+  double gb[12], kb = b1 / (2.0 * d);
+  for (int i = 0; i < 12; ++i) gb[i] = kb * gs[i];
+  double gm[12];
+  for (int i = 0; i < 12; ++i) gm[i] = c.kind == 1 ? m1 * gc[i] : 0.0;
+  for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = scale * (m * gb[i] + b * gm[i]);
+  if (MODE == MODE_GRAD) return;
+  double H[144];
+  double ka = b2 / (4.0 * d * d) - b1 / (4.0 * d * d * d);
+  for (int i = 0; i < 12; ++i)
+    for (int j = i; j < 12; ++j) {
+      int u = up_idx(i, j, 12);
+      double hb = ka * gs[i] * gs[j] + kb * Hs[u];
+      double v = m * hb;
+      if (c.kind == 1) v += b * (m2 * gc[i] * gc[j] + m1 * Hc[u]) + gm[i] * gb[j] + gb[i] * gm[j];
+      H[12 * i + j] = scale * v;
+      H[12 * j + i] = scale * v;
+    }
+  project_psd_jacobi<12>(H);
+  for (int i = 0; i < 12; ++i)
+    for (int j = i; j < 12; ++j) sH[78 * (long)k + up_idx(i, j, 12)] = H[12 * i + j];
+}
+
+// ----------------------------------------------------------------- lagged friction
+struct FrictionRec {
+  int pts[4];
+  int env, pad;
+  double c[4];
+  double n[3];
+  double mu_lambda;
+};
+
+// h^2 mu lambda f0(|u|), u = P rel, rel = sum_i c_i (x_i - x_i^t), P = I - n n^T; gradient
+// c_i a u and Hessian c_i c_j (a P + b u u^T) with a = f1/y, b = (f1' y - f1)/y^3 (PSD for the
+// IPC smoothing f0; at y = 0, a = 2/(eps_v h) and the u u^T term vanishes).
+template <int MODE>
+__global__ void k_friction(int n_fr, const FrictionRec* __restrict__ fr, const uint8_t* __restrict__ act,
+                           const double* __restrict__ ptx, const double* __restrict__ ptx_t, double h2, double eh,
+                           double* __restrict__ sE, double* __restrict__ sg, double* __restrict__ sH) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_fr) return;
+  FrictionRec f = fr[k];
+  if (!act[f.env]) return;
+  d3 rel = mk3(0, 0, 0);
+  for (int i = 0; i < 4; ++i) rel = rel + f.c[i] * (ld3(ptx, f.pts[i]) - ld3(ptx_t, f.pts[i]));
+  d3 n = mk3(f.n[0], f.n[1], f.n[2]);
+  d3 u = rel - dot(n, rel) * n;
+  double y = sqrt(dot(u, u));
+  double f0, f1, f2;
+  if (y < eh) {
+    f0 = -y * y * y / (3.0 * eh * eh) + y * y / eh + eh / 3.0;
+    f1 = -y * y / (eh * eh) + 2.0 * y / eh;
+    f2 = -2.0 * y / (eh * eh) + 2.0 / eh;
+  } else {
+    f0 = y;
+    f1 = 1.0;
+    f2 = 0.0;
+  }
+  double s = h2 * f.mu_lambda;
+  sE[k] = s * f0;
+  if (MODE == MODE_ENERGY) return;
+  double a = y > 0.0 ? f1 / y : 2.0 / eh;
+  double bc = y > 0.0 ? (f2 * y - f1) / (y * y * y) : 0.0;
+  for (int i = 0; i < 4; ++i) {
+    sg[12 * (long)k + 3 * i] = s * f.c[i] * a * u.x;
+    sg[12 * (long)k + 3 * i + 1] = s * f.c[i] * a * u.y;
+    sg[12 * (long)k + 3 * i + 2] = s * f.c[i] * a * u.z;
+  }
+  if (MODE == MODE_GRAD) return;
+  double M[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) M[3 * r + c] = a * ((r == c ? 1.0 : 0.0) - f.n[r] * f.n[c]) + bc * comp(u, r) * comp(u, c);
+  for (int i = 0; i < 12; ++i)
+    for (int j = i; j < 12; ++j)
+      sH[78 * (long)k + up_idx(i, j, 12)] = s * f.c[i / 3] * f.c[j / 3] * M[3 * (i % 3) + (j % 3)];
+}
+
+// ----------------------------------------------------------------- per-env energy sums
+// One block per env; every sub-range is summed by a fixed-order tree. Dynamic lists (contacts,
+// friction) are env-sorted; their env ranges are found by binary search.
+DEV int lower_env(const int* envs, int lo, int hi, int e) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (envs[mid] < e) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+struct EnergyLists {
+  const double* nodeE; const int* node_off;     // soft-node inertia per node
+  const double* tetE; const int* tet_off;
+  const double* bodyE; const int* body_off;
+  const double* stE; const int* st_env; int n_pt, n_ee, n_frpt, n_fr;  // stencils: [pt|ee|frpt|free]
+};
+__global__ void k_env_energy(int n_env, EnergyLists L, const uint8_t* __restrict__ act, double* __restrict__ out) {
+  __shared__ double sh[256];
+  int e = blockIdx.x;
+  if (!act[e]) return;
+  double acc = 0.0;
+  auto range_sum = [&](const double* v, int b, int en) {
+    double s = 0.0;
+    for (int i = b + threadIdx.x; i < en; i += blockDim.x) s += v[i];
+    return block_sum(s, sh);
+  };
+  acc += range_sum(L.nodeE, L.node_off[e], L.node_off[e + 1]);
+  acc += range_sum(L.tetE, L.tet_off[e], L.tet_off[e + 1]);
+  acc += range_sum(L.bodyE, L.body_off[e], L.body_off[e + 1]);
+  int bounds[5] = {0, L.n_pt, L.n_pt + L.n_ee, L.n_pt + L.n_ee + L.n_frpt, L.n_pt + L.n_ee + L.n_fr};
+  for (int r = 0; r < 4; ++r) {
+    int b = lower_env(L.st_env, bounds[r], bounds[r + 1], e);
+    int en = lower_env(L.st_env, bounds[r], bounds[r + 1], e + 1);
+    acc += range_sum(L.stE, b, en);
+  }
+  if (threadIdx.x == 0) out[e] = acc;
+}

@@ -1,0 +1,1449 @@
+// Host side of the B300 multi-environment IPC stepper: environment records, the flattened
+// device layout of a batch, and the batched Newton loop (Sec. III-A: per-env collision
+// isolation, step size, stopping and failure). Every numerical stage runs in the kernels of
+// the included headers; the host sequences launches, sizes buffers and polls small counters.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ipc.h"
+#include "common.cuh"
+#include "geometry.cuh"
+#include "lbvh.cuh"
+#include "energy.cuh"
+#include "solver.cuh"
+#include "kernels_misc.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+struct IpcError {
+  ipc_status st;
+  std::string msg;
+};
+[[noreturn]] void fail_with(ipc_status st, const std::string& m) { throw IpcError{st, m}; }
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) fail_with(IPC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t m) {  // exact (re)allocation, contents undefined
+    release();
+    if (m == 0) m = 1;
+    cudaError_t e = cudaMalloc(&p, m * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      fail_with(IPC_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    n = m;
+  }
+  void ensure(size_t m) {  // grow-only, contents not preserved
+    if (m <= n && p) return;
+    alloc(std::max(m, (size_t)(n * 3 / 2 + 64)));
+  }
+  void upload(const std::vector<T>& v, cudaStream_t s) {
+    alloc(v.size());
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  void zero(cudaStream_t s, size_t m = (size_t)-1) {
+    if (p) CK(cudaMemsetAsync(p, 0, std::min(m, n) * sizeof(T), s));
+  }
+};
+
+// ---------------------------------------------------------------- host environment record
+struct HostEnv {
+  int id = -1;
+  // copies of the descriptor
+  struct Soft {
+    std::vector<double> verts;
+    std::vector<int> tets, tris;
+    std::vector<uint8_t> kin;
+    double E, nu, rho;
+  };
+  struct Aff {
+    std::vector<double> verts;
+    std::vector<int> tris;
+    double rho;
+    double q0[12], qdot0[12];
+    int kin;
+  };
+  std::vector<Soft> soft;
+  std::vector<Aff> aff;
+  double mu = 0;
+  int n_steps = 0;
+  std::vector<uint8_t> grav;
+  std::vector<double> targets;
+  // derived (env-local)
+  int nsv_verts = 0, nbodies = 0, ntets = 0, ndof = 0;
+  std::vector<int> tet_nodes;        // 4 per tet, env-local nodes
+  std::vector<double> tet_prm;       // 12 per tet
+  std::vector<double> mass;          // per soft node
+  std::vector<uint8_t> node_kin;     // per soft node
+  std::vector<int> node_handle;      // per node (soft + 4 per body)
+  std::vector<double> X0;            // per soft node
+  std::vector<double> M4, bvol, bbox;  // per body
+  // points: env-local node (soft) or -1-body
+  std::vector<int> pt_node;
+  std::vector<double> pt_xb, pt_rest;
+  std::vector<int> pt_body;  // affine body index (local) or -1 - soft body index
+  std::vector<uint8_t> pt_kin;
+  std::vector<int> sv, edges, tris;  // point ids
+  std::vector<double> edge_rest2;
+  // state
+  std::vector<double> x, v;
+  int step = 0, status = ST_ACTIVE, reason = FAIL_NONE;
+  long long stats[5] = {0, 0, 0, 0, 0};
+  bool checked = false;  // initial intersection check done
+  uint64_t est_bytes = 0;
+};
+
+uint64_t estimate_bytes(const HostEnv& h, int precision) {
+  uint64_t nn = h.nsv_verts + 4 * h.nbodies;
+  uint64_t hb = precision == IPC_MIXED ? 4 : 8;
+  uint64_t b = nn * (24 * 14 + 72) + (uint64_t)h.ntets * (96 + 16 + 96 + 90 * 8 + 64) + nn * 15 * (9 * hb + 8);
+  uint64_t np = h.pt_node.size(), nprim = h.tris.size() / 3 + h.edges.size() / 2 + h.sv.size();
+  b += np * 96 + nprim * 4 * 64 + 4096 * (78 * 8 + 200);  // contact capacity estimate
+  b += (uint64_t)h.targets.size() * 8;
+  return b;
+}
+
+void build_env(HostEnv& h, const ipc_env_desc* D) {
+  if (!D || D->n_steps <= 0 || (D->n_soft + D->n_affine) <= 0) fail_with(IPC_ERR_ARG, "env: empty or no steps");
+  if (!D->gravity_on || !D->targets) fail_with(IPC_ERR_ARG, "env: gravity_on and targets are required");
+  h.mu = D->friction_mu;
+  h.n_steps = D->n_steps;
+  h.grav.assign(D->gravity_on, D->gravity_on + D->n_steps);
+  int nh = D->n_soft + D->n_affine;
+  h.targets.assign(D->targets, D->targets + (size_t)D->n_steps * nh * 12);
+  int nsv = 0;
+  for (int b = 0; b < D->n_soft; ++b) {
+    const ipc_soft_body_desc& S = D->soft[b];
+    if (S.n_verts <= 0 || S.n_tets <= 0 || !S.verts || !S.tets) fail_with(IPC_ERR_ARG, "soft body: empty");
+    HostEnv::Soft s;
+    s.verts.assign(S.verts, S.verts + 3 * S.n_verts);
+    s.tets.assign(S.tets, S.tets + 4 * S.n_tets);
+    if (S.n_tris > 0) s.tris.assign(S.tris, S.tris + 3 * S.n_tris);
+    s.kin.assign(S.n_verts, 0);
+    if (S.kinematic) s.kin.assign(S.kinematic, S.kinematic + S.n_verts);
+    s.E = S.youngs;
+    s.nu = S.poisson;
+    s.rho = S.density;
+    for (int i : s.tets)
+      if (i < 0 || i >= S.n_verts) fail_with(IPC_ERR_ARG, "soft body: tet index out of range");
+    for (int i : s.tris)
+      if (i < 0 || i >= S.n_verts) fail_with(IPC_ERR_ARG, "soft body: triangle index out of range");
+    nsv += S.n_verts;
+    h.soft.push_back(std::move(s));
+  }
+  for (int b = 0; b < D->n_affine; ++b) {
+    const ipc_affine_body_desc& A = D->affine[b];
+    if (A.n_verts <= 0 || A.n_tris <= 0) fail_with(IPC_ERR_ARG, "affine body: empty surface");
+    HostEnv::Aff a;
+    a.verts.assign(A.verts, A.verts + 3 * A.n_verts);
+    a.tris.assign(A.tris, A.tris + 3 * A.n_tris);
+    for (int i : a.tris)
+      if (i < 0 || i >= A.n_verts) fail_with(IPC_ERR_ARG, "affine body: triangle index out of range");
+    a.rho = A.density;
+    std::memcpy(a.q0, A.q0, sizeof(a.q0));
+    std::memcpy(a.qdot0, A.qdot0, sizeof(a.qdot0));
+    a.kin = A.kinematic;
+    h.aff.push_back(std::move(a));
+  }
+  h.nsv_verts = nsv;
+  h.nbodies = D->n_affine;
+  h.ndof = 3 * nsv + 12 * D->n_affine;
+  h.x.assign(h.ndof, 0.0);
+  h.v.assign(h.ndof, 0.0);
+  h.mass.assign(nsv, 0.0);
+  h.node_kin.assign(nsv, 0);
+  h.X0.assign(3 * nsv, 0.0);
+  h.node_handle.assign(nsv + 4 * D->n_affine, 0);
+  // soft: rest shape matrices, volumes, Lame parameters, lumped masses
+  int off = 0;
+  for (size_t b = 0; b < h.soft.size(); ++b) {
+    auto& s = h.soft[b];
+    double mu = s.E / (2.0 * (1.0 + s.nu)), lam = s.E * s.nu / ((1.0 + s.nu) * (1.0 - 2.0 * s.nu));
+    int nv = (int)s.verts.size() / 3;
+    for (int i = 0; i < nv; ++i) {
+      for (int k = 0; k < 3; ++k) {
+        h.x[3 * (off + i) + k] = s.verts[3 * i + k];
+        h.X0[3 * (off + i) + k] = s.verts[3 * i + k];
+      }
+      h.node_kin[off + i] = s.kin[i] ? 1 : 0;
+      h.node_handle[off + i] = (int)b;
+    }
+    int nt = (int)s.tets.size() / 4;
+    for (int t = 0; t < nt; ++t) {
+      const double* X[4];
+      for (int k = 0; k < 4; ++k) X[k] = &s.verts[3 * s.tets[4 * t + k]];
+      double Dm[9];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Dm[3 * r + c] = X[c + 1][r] - X[0][r];
+      double det = Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
+                   Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
+      if (!(det > 0.0)) fail_with(IPC_ERR_INIT_INVERTED, "a tet has non-positive rest volume");
+      double inv[9] = {(Dm[4] * Dm[8] - Dm[5] * Dm[7]) / det, (Dm[2] * Dm[7] - Dm[1] * Dm[8]) / det,
+                       (Dm[1] * Dm[5] - Dm[2] * Dm[4]) / det, (Dm[5] * Dm[6] - Dm[3] * Dm[8]) / det,
+                       (Dm[0] * Dm[8] - Dm[2] * Dm[6]) / det, (Dm[2] * Dm[3] - Dm[0] * Dm[5]) / det,
+                       (Dm[3] * Dm[7] - Dm[4] * Dm[6]) / det, (Dm[1] * Dm[6] - Dm[0] * Dm[7]) / det,
+                       (Dm[0] * Dm[4] - Dm[1] * Dm[3]) / det};
+      double vol = det / 6.0;
+      for (int k = 0; k < 4; ++k) h.tet_nodes.push_back(off + s.tets[4 * t + k]);
+      for (int k = 0; k < 9; ++k) h.tet_prm.push_back(inv[k]);
+      h.tet_prm.push_back(vol);
+      h.tet_prm.push_back(mu);
+      h.tet_prm.push_back(lam);
+      for (int k = 0; k < 4; ++k) h.mass[off + s.tets[4 * t + k]] += s.rho * vol / 4.0;
+    }
+    off += nv;
+  }
+  h.ntets = (int)h.tet_nodes.size() / 4;
+  // affine bodies: mass matrix from the closed surface (divergence theorem), rest bbox
+  for (size_t b = 0; b < h.aff.size(); ++b) {
+    auto& a = h.aff[b];
+    double I0 = 0, I1[3] = {0, 0, 0}, I2[9] = {0};
+    int nt = (int)a.tris.size() / 3;
+    for (int f = 0; f < nt; ++f) {
+      const double* A = &a.verts[3 * a.tris[3 * f]];
+      const double* B = &a.verts[3 * a.tris[3 * f + 1]];
+      const double* Cc = &a.verts[3 * a.tris[3 * f + 2]];
+      double det = A[0] * (B[1] * Cc[2] - B[2] * Cc[1]) - A[1] * (B[0] * Cc[2] - B[2] * Cc[0]) +
+                   A[2] * (B[0] * Cc[1] - B[1] * Cc[0]);
+      double s[3] = {A[0] + B[0] + Cc[0], A[1] + B[1] + Cc[1], A[2] + B[2] + Cc[2]};
+      I0 += det / 6.0;
+      for (int i = 0; i < 3; ++i) I1[i] += det * s[i] / 24.0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) I2[3 * i + j] += det * (A[i] * A[j] + B[i] * B[j] + Cc[i] * Cc[j] + s[i] * s[j]) / 120.0;
+    }
+    double M[16];
+    M[0] = a.rho * I0;
+    for (int i = 0; i < 3; ++i) M[1 + i] = M[4 * (1 + i)] = a.rho * I1[i];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) M[4 * (1 + i) + 1 + j] = a.rho * I2[3 * i + j];
+    if (!a.kin && !(I0 > 0.0)) fail_with(IPC_ERR_ARG, "affine body: surface encloses no volume (not closed / inward)");
+    for (int i = 0; i < 16; ++i) h.M4.push_back(M[i]);
+    h.bvol.push_back(I0);
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (size_t i = 0; i < a.verts.size() / 3; ++i)
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], a.verts[3 * i + k]);
+        hi[k] = std::max(hi[k], a.verts[3 * i + k]);
+      }
+    for (int k = 0; k < 3; ++k) h.bbox.push_back(lo[k]);
+    for (int k = 0; k < 3; ++k) h.bbox.push_back(hi[k]);
+    int dof = 3 * nsv + 12 * (int)b;
+    for (int k = 0; k < 12; ++k) {
+      h.x[dof + k] = a.q0[k];
+      h.v[dof + k] = a.qdot0[k];
+    }
+    for (int k = 0; k < 4; ++k) h.node_handle[nsv + 4 * b + k] = (int)h.soft.size() + (int)b;
+  }
+  // points, triangles, surface vertices, edges
+  std::vector<int> soft_off, aff_off;
+  off = 0;
+  for (size_t b = 0; b < h.soft.size(); ++b) {
+    soft_off.push_back((int)h.pt_node.size());
+    int nv = (int)h.soft[b].verts.size() / 3;
+    for (int i = 0; i < nv; ++i) {
+      h.pt_node.push_back(off + i);
+      for (int k = 0; k < 3; ++k) {
+        h.pt_xb.push_back(0.0);
+        h.pt_rest.push_back(h.soft[b].verts[3 * i + k]);
+      }
+      h.pt_body.push_back(-1 - (int)b);
+      h.pt_kin.push_back(h.soft[b].kin[i] ? 1 : 0);
+    }
+    off += nv;
+  }
+  for (size_t b = 0; b < h.aff.size(); ++b) {
+    aff_off.push_back((int)h.pt_node.size());
+    int nv = (int)h.aff[b].verts.size() / 3;
+    for (int i = 0; i < nv; ++i) {
+      h.pt_node.push_back(-1 - (int)b);
+      for (int k = 0; k < 3; ++k) {
+        h.pt_xb.push_back(h.aff[b].verts[3 * i + k]);
+        h.pt_rest.push_back(h.aff[b].verts[3 * i + k]);
+      }
+      h.pt_body.push_back((int)b);
+      h.pt_kin.push_back(h.aff[b].kin ? 1 : 0);
+    }
+  }
+  for (size_t b = 0; b < h.soft.size(); ++b)
+    for (int v : h.soft[b].tris) h.tris.push_back(soft_off[b] + v);
+  for (size_t b = 0; b < h.aff.size(); ++b)
+    for (int v : h.aff[b].tris) h.tris.push_back(aff_off[b] + v);
+  std::vector<int> sv(h.tris);
+  std::sort(sv.begin(), sv.end());
+  sv.erase(std::unique(sv.begin(), sv.end()), sv.end());
+  h.sv = sv;
+  std::vector<std::pair<int, int>> ed;
+  for (size_t f = 0; f < h.tris.size() / 3; ++f)
+    for (int k = 0; k < 3; ++k) {
+      int a = h.tris[3 * f + k], b = h.tris[3 * f + (k + 1) % 3];
+      ed.push_back({std::min(a, b), std::max(a, b)});
+    }
+  std::sort(ed.begin(), ed.end());
+  ed.erase(std::unique(ed.begin(), ed.end()), ed.end());
+  for (auto& e : ed) {
+    h.edges.push_back(e.first);
+    h.edges.push_back(e.second);
+    double s = 0;
+    for (int k = 0; k < 3; ++k) {
+      double d = h.pt_rest[3 * e.first + k] - h.pt_rest[3 * e.second + k];
+      s += d * d;
+    }
+    h.edge_rest2.push_back(s);
+  }
+}
+
+}  // namespace
+
+// per-env PCG iteration counts into the statistics
+__global__ void k_add_stats(int n_env, const long long* __restrict__ it, long long* __restrict__ stats) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n_env) stats[5 * e + STAT_PCG] += it[e];
+}
+
+// ==================================================================== the scene
+struct ipc_scene {
+  ipc_scene_desc desc;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  std::map<int, HostEnv> envs;
+  int next_id = 0;
+  bool dirty = true;
+  uint64_t used_bytes = 0;
+  long long launches = 0;
+
+  // ---------------- layout sizes
+  int E = 0, NN = 0, NB = 0, NT = 0, NP = 0, NSV = 0, NED = 0, NTR = 0, NTILE = 0, NNZB = 0;
+  std::vector<int> ids;  // layout index -> env id
+  std::vector<int> h_node_off, h_tet_off, h_pt_off, h_sv_off, h_ed_off, h_tri_off, h_body_off, h_tile_off;
+  // ---------------- device arrays (static per layout)
+  DBuf<int> node_off, tet_off, body_off, nsteps, grav_off, nh, tile_env, tile_kind, tile_begin, tile_end, tile_off;
+  DBuf<long> sched_off;
+  DBuf<double> env_mu, sched;
+  DBuf<uint8_t> grav;
+  DBuf<int> node_env, node_body, node_handle, body_node, body_env;
+  DBuf<uint8_t> node_kin, body_kin;
+  DBuf<double> node_mass, X0, M4, bvol, bbox;
+  DBuf<int4> tets;
+  DBuf<double> tet_prm;
+  DBuf<int> tet_env;
+  DBuf<int> pt_node, pt_body, pt_env;
+  DBuf<double> pt_xb;
+  DBuf<uint8_t> pt_kin;
+  DBuf<int> sv_pt, sv_env, ed_pt, ed_env, tri_pt, tri_env;
+  DBuf<double> ed_rest2;
+  DBuf<int> bsr_ptr, bsr_col, blk_row, bsr_diag, blk_ptr, blk_src, nt_ptr, nt_src;
+  // ---------------- state
+  DBuf<double> x, v, xt, xtilde, xtarget, xtrial, p, pbar, grad;
+  DBuf<double> ptx, ptx_t, ptp, pte;
+  // env control
+  DBuf<int> e_status, e_reason, e_step, e_constrained, e_bad, e_nanp, e_halv, e_newton_it, e_count;
+  DBuf<uint8_t> e_stepping, e_iter, e_ls, e_accept, e_sel, e_all;
+  DBuf<double> e_E0, e_Et, e_alpha;
+  DBuf<unsigned long long> e_alpha_bits, e_pnorm_bits, e_inter, e_inv;
+  DBuf<long long> e_stats;
+  // energies / stencils
+  DBuf<double> nodeE, tetE, tet_g, tet_H, bodyE, body_g, body_H;
+  DBuf<double> bsr_val, Ps, Pb;
+  DBuf<double> pcg_r, pcg_z, pcg_d, pcg_y, pcg_x, part_a, part_b, part_c, pcg_rz, pcg_bb;
+  DBuf<int> pcg_it, pcg_active;
+  DBuf<uint8_t> pcg_run;
+  // trees
+  struct TreeBufs {
+    DBuf<double> pbox, nbox;
+    DBuf<unsigned long long> keys, keys2;
+    DBuf<unsigned> vals, vals2;
+    DBuf<int> child, parent, range, root, flags, hist;
+    DBuf<unsigned long long> emin, emax;
+    int n = 0;
+    bool built = false;
+  } ttri, tedge;
+  // candidates / contacts
+  DBuf<int> cnt_pt, off_pt, cnt_ee, off_ee, cand_j, nflag, noff, scan_tmp, overflow;
+  DBuf<ContactRec> ct_tmp, ct;
+  DBuf<FrictionRec> fr;
+  int n_pt = 0, n_ee = 0, n_ct = 0, n_ct_pt = 0, n_fr = 0, n_fr_pt = 0;
+  DBuf<int> st_pts, st_env, st_cnt, st_off, ns_ptr, ns_src, ns_cnt;
+  DBuf<unsigned long long> st_keys, st_keys2;
+  DBuf<unsigned> st_vals, st_vals2;
+  DBuf<double> sE, sg, sH, st_t;
+  DBuf<long long> pcg_iters;
+  DBuf<int> st_hist, root_off_tri, root_off_ed;
+  // pinned host scratch
+  int* hpin = nullptr;
+
+  ~ipc_scene() {
+    if (hpin) cudaFreeHost(hpin);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+
+  // ------------------------------------------------------------------ launch helpers
+  template <class K, class... Args>
+  void launch(K kern, long n_threads, int block, Args... args) {
+    if (n_threads <= 0) return;
+    long grid = (n_threads + block - 1) / block;
+    kern<<<(unsigned)grid, block, 0, stream>>>(args...);
+    ++launches;
+    CK(cudaGetLastError());
+  }
+  template <class K, class... Args>
+  void launch_grid(K kern, long grid, int block, Args... args) {
+    if (grid <= 0) return;
+    kern<<<(unsigned)grid, block, 0, stream>>>(args...);
+    ++launches;
+    CK(cudaGetLastError());
+  }
+  int read_int(const int* dptr) {
+    CK(cudaMemcpyAsync(hpin, dptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    return *hpin;
+  }
+  int count_flags(const uint8_t* f) {
+    launch_grid(k_count_flags, 1, 256, E, f, e_count.p);
+    return read_int(e_count.p);
+  }
+  // exclusive scan of n ints into out[0..n] (out[n] = total); returns total (sync)
+  int scan(const int* in, int n, int* out, bool read_total = true) {
+    if (n <= 0) {
+      CK(cudaMemsetAsync(out, 0, sizeof(int), stream));
+      return 0;
+    }
+    int nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    scan_tmp.ensure(nb + 1);
+    launch_grid(k_scan_block_sums, nb, SCAN_BLOCK, in, n, scan_tmp.p);
+    launch_grid(k_scan_sums, 1, SCAN_BLOCK, scan_tmp.p, nb);
+    launch_grid(k_scan_apply, nb, SCAN_BLOCK, in, n, (const int*)scan_tmp.p, out);
+    return read_total ? read_int(out + n) : 0;
+  }
+  // stable sort of (key, value) pairs over key bits [0, bits)
+  void radix_sort(DBuf<unsigned long long>& k, DBuf<unsigned>& v, DBuf<unsigned long long>& k2, DBuf<unsigned>& v2,
+                  DBuf<int>& hist, int n, int bits) {
+    if (n <= 1) return;
+    int nblk = (n + RS_TILE - 1) / RS_TILE;
+    hist.ensure(256 * nblk + 1);
+    k2.ensure(n);
+    v2.ensure(n);
+    for (int shift = 0; shift < bits; shift += 8) {
+      launch_grid(k_rs_hist, nblk, RS_THREADS, (const unsigned long long*)k.p, n, shift, nblk, hist.p);
+      scan(hist.p, 256 * nblk, hist.p, false);  // in place is safe: apply reads 'in' block-locally first
+      launch_grid(k_rs_scatter, nblk, RS_THREADS, (const unsigned long long*)k.p, (const unsigned*)v.p, k2.p, v2.p, n,
+                  shift, nblk, (const int*)hist.p);
+      std::swap(k.p, k2.p);
+      std::swap(k.n, k2.n);
+      std::swap(v.p, v2.p);
+      std::swap(v.n, v2.n);
+    }
+  }
+
+  Layout layout() const {
+    return Layout{node_env.p, node_body.p, node_kin.p, node_mass.p, body_node.p, body_kin.p, pt_node.p, pt_xb.p};
+  }
+  Tiles tiles() const { return Tiles{tile_env.p, tile_kind.p, tile_begin.p, tile_end.p, tile_off.p}; }
+  EnvCtl ctl() {
+    return EnvCtl{e_status.p, e_reason.p, e_step.p, nsteps.p, e_stepping.p, e_iter.p, e_ls.p, e_accept.p,
+                  e_constrained.p, e_bad.p, e_nanp.p, e_halv.p, e_newton_it.p, e_E0.p, e_Et.p, e_alpha.p,
+                  e_alpha_bits.p, e_pnorm_bits.p, e_stats.p, e_count.p};
+  }
+  Sched sched_view() const {
+    return Sched{sched.p, grav.p, sched_off.p, grav_off.p, nh.p, node_handle.p, X0.p};
+  }
+  PtInfo ptinfo() const { return PtInfo{pt_body.p, pt_kin.p}; }
+  Tree tree(TreeBufs& T) const { return Tree{T.n, T.vals.p, T.child.p, T.nbox.p, T.root.p}; }
+
+  // ------------------------------------------------------------------ layout
+  void pull_state() {
+    // copy the device state of the current layout back into the env records
+    if (ids.empty()) return;
+    std::vector<double> hx(3 * (size_t)NN), hv(3 * (size_t)NN);
+    std::vector<int> st(E), rs(E), sp(E);
+    std::vector<long long> stats(5 * (size_t)E);
+    CK(cudaMemcpyAsync(hx.data(), x.p, hx.size() * 8, cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(hv.data(), v.p, hv.size() * 8, cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(st.data(), e_status.p, E * 4, cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(rs.data(), e_reason.p, E * 4, cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(sp.data(), e_step.p, E * 4, cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(stats.data(), e_stats.p, E * 40, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    for (int li = 0; li < E; ++li) {
+      auto it = envs.find(ids[li]);
+      if (it == envs.end()) continue;
+      HostEnv& h = it->second;
+      size_t o = 3 * (size_t)h_node_off[li];
+      std::copy(hx.begin() + o, hx.begin() + o + h.ndof, h.x.begin());
+      std::copy(hv.begin() + o, hv.begin() + o + h.ndof, h.v.begin());
+      h.status = st[li];
+      h.reason = rs[li];
+      h.step = sp[li];
+      for (int k = 0; k < 5; ++k) h.stats[k] = stats[5 * li + k];
+    }
+  }
+
+  void commit() {
+    if (!dirty) return;
+    if (envs.empty()) fail_with(IPC_ERR_NO_ENV, "scene holds no environment");
+    CK(cudaSetDevice(device));
+    pull_state();
+    ids.clear();
+    for (auto& kv : envs) ids.push_back(kv.first);
+    E = (int)ids.size();
+    std::vector<int> node_off_h{0}, tet_off_h{0}, pt_off_h{0}, sv_off_h{0}, ed_off_h{0}, tri_off_h{0}, body_off_h{0};
+    std::vector<int> nsteps_h, grav_off_h, nh_h;
+    std::vector<long> sched_off_h;
+    std::vector<double> mu_h, sched_h;
+    std::vector<uint8_t> grav_h;
+    std::vector<int> node_env_h, node_body_h, node_handle_h, body_node_h, body_env_h;
+    std::vector<uint8_t> node_kin_h, body_kin_h, pt_kin_h;
+    std::vector<double> node_mass_h, X0_h, M4_h, bvol_h, bbox_h, tet_prm_h, pt_xb_h, ed_rest2_h, x_h, v_h;
+    std::vector<int4> tets_h;
+    std::vector<int> tet_env_h, pt_node_h, pt_body_h, pt_env_h, sv_pt_h, sv_env_h, ed_pt_h, ed_env_h, tri_pt_h, tri_env_h;
+    std::vector<int> status_h, reason_h, step_h;
+    std::vector<long long> stats_h;
+    int body_base = 0, soft_body_base = 0;
+    for (int li = 0; li < E; ++li) {
+      HostEnv& h = envs[ids[li]];
+      int n0 = node_off_h.back(), p0 = pt_off_h.back(), t0 = tet_off_h.back(), b0 = body_off_h.back();
+      int nsv = h.nsv_verts;
+      // nodes: soft vertices, then 4 per body
+      for (int i = 0; i < nsv; ++i) {
+        node_env_h.push_back(li);
+        node_body_h.push_back(-1);
+        node_kin_h.push_back(h.node_kin[i]);
+        node_mass_h.push_back(h.mass[i]);
+        node_handle_h.push_back(h.node_handle[i]);
+        for (int k = 0; k < 3; ++k) X0_h.push_back(h.X0[3 * i + k]);
+      }
+      for (int b = 0; b < h.nbodies; ++b) {
+        body_node_h.push_back(n0 + nsv + 4 * b);
+        body_env_h.push_back(li);
+        body_kin_h.push_back(h.aff[b].kin ? 1 : 0);
+        for (int k = 0; k < 16; ++k) M4_h.push_back(h.M4[16 * b + k]);
+        bvol_h.push_back(h.bvol[b]);
+        for (int k = 0; k < 6; ++k) bbox_h.push_back(h.bbox[6 * b + k]);
+        for (int k = 0; k < 4; ++k) {
+          node_env_h.push_back(li);
+          node_body_h.push_back(b0 + b);
+          node_kin_h.push_back(0);
+          node_mass_h.push_back(0.0);
+          node_handle_h.push_back(h.node_handle[nsv + 4 * b + k]);
+          for (int q = 0; q < 3; ++q) X0_h.push_back(0.0);
+        }
+      }
+      for (double d : h.x) x_h.push_back(d);
+      for (double d : h.v) v_h.push_back(d);
+      for (int t = 0; t < h.ntets; ++t) {
+        tets_h.push_back(make_int4(n0 + h.tet_nodes[4 * t], n0 + h.tet_nodes[4 * t + 1], n0 + h.tet_nodes[4 * t + 2],
+                                   n0 + h.tet_nodes[4 * t + 3]));
+        tet_env_h.push_back(li);
+        for (int k = 0; k < 12; ++k) tet_prm_h.push_back(h.tet_prm[12 * t + k]);
+      }
+      for (size_t i = 0; i < h.pt_node.size(); ++i) {
+        int nd = h.pt_node[i];
+        pt_node_h.push_back(nd >= 0 ? n0 + nd : -1 - (b0 + (-1 - nd)));
+        int pb = h.pt_body[i];
+        pt_body_h.push_back(pb >= 0 ? b0 + pb : -1 - (soft_body_base + (-1 - pb)));
+        pt_kin_h.push_back(h.pt_kin[i]);
+        pt_env_h.push_back(li);
+        for (int k = 0; k < 3; ++k) pt_xb_h.push_back(h.pt_xb[3 * i + k]);
+      }
+      for (int s : h.sv) {
+        sv_pt_h.push_back(p0 + s);
+        sv_env_h.push_back(li);
+      }
+      for (size_t e = 0; e < h.edges.size() / 2; ++e) {
+        ed_pt_h.push_back(p0 + h.edges[2 * e]);
+        ed_pt_h.push_back(p0 + h.edges[2 * e + 1]);
+        ed_env_h.push_back(li);
+        ed_rest2_h.push_back(h.edge_rest2[e]);
+      }
+      for (size_t f = 0; f < h.tris.size() / 3; ++f) {
+        for (int k = 0; k < 3; ++k) tri_pt_h.push_back(p0 + h.tris[3 * f + k]);
+        tri_env_h.push_back(li);
+      }
+      nsteps_h.push_back(h.n_steps);
+      grav_off_h.push_back((int)grav_h.size());
+      grav_h.insert(grav_h.end(), h.grav.begin(), h.grav.end());
+      nh_h.push_back((int)(h.soft.size() + h.aff.size()));
+      sched_off_h.push_back((long)sched_h.size());
+      sched_h.insert(sched_h.end(), h.targets.begin(), h.targets.end());
+      mu_h.push_back(h.mu);
+      status_h.push_back(h.status);
+      reason_h.push_back(h.reason);
+      step_h.push_back(h.step);
+      for (int k = 0; k < 5; ++k) stats_h.push_back(h.stats[k]);
+      node_off_h.push_back(n0 + nsv + 4 * h.nbodies);
+      tet_off_h.push_back(t0 + h.ntets);
+      pt_off_h.push_back(p0 + (int)h.pt_node.size());
+      sv_off_h.push_back(sv_off_h.back() + (int)h.sv.size());
+      ed_off_h.push_back(ed_off_h.back() + (int)h.edges.size() / 2);
+      tri_off_h.push_back(tri_off_h.back() + (int)h.tris.size() / 3);
+      body_off_h.push_back(b0 + h.nbodies);
+      body_base += h.nbodies;
+      soft_body_base += (int)h.soft.size();
+    }
+    NN = node_off_h.back();
+    NT = tet_off_h.back();
+    NP = pt_off_h.back();
+    NSV = sv_off_h.back();
+    NED = ed_off_h.back();
+    NTR = tri_off_h.back();
+    NB = body_off_h.back();
+    h_node_off = node_off_h;
+    h_tet_off = tet_off_h;
+    h_pt_off = pt_off_h;
+    h_sv_off = sv_off_h;
+    h_ed_off = ed_off_h;
+    h_tri_off = tri_off_h;
+    h_body_off = body_off_h;
+    // tiles: per env, soft-node tiles then body tiles
+    std::vector<int> te, tk, tb, tn, toff{0};
+    for (int li = 0; li < E; ++li) {
+      int n0 = node_off_h[li];
+      int nsv = envs[ids[li]].nsv_verts;
+      for (int s = 0; s < nsv; s += TILE) {
+        te.push_back(li);
+        tk.push_back(0);
+        tb.push_back(n0 + s);
+        tn.push_back(n0 + std::min(nsv, s + TILE));
+      }
+      for (int s = body_off_h[li]; s < body_off_h[li + 1]; s += TILE) {
+        te.push_back(li);
+        tk.push_back(1);
+        tb.push_back(s);
+        tn.push_back(std::min(body_off_h[li + 1], s + TILE));
+      }
+      toff.push_back((int)te.size());
+    }
+    NTILE = (int)te.size();
+    h_tile_off = toff;
+    // BSR pattern of the soft nodes from the tets, gather lists for blocks and gradients
+    std::vector<std::vector<int>> adj(NN);
+    for (int t = 0; t < NT; ++t) {
+      int n4[4] = {tets_h[t].x, tets_h[t].y, tets_h[t].z, tets_h[t].w};
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) adj[n4[a]].push_back(n4[b]);
+    }
+    std::vector<int> bptr{0}, bcol, brow, bdiag(NN, -1);
+    for (int i = 0; i < NN; ++i) {
+      auto& a = adj[i];
+      std::sort(a.begin(), a.end());
+      a.erase(std::unique(a.begin(), a.end()), a.end());
+      for (int j : a) {
+        if (j == i) bdiag[i] = (int)bcol.size();
+        bcol.push_back(j);
+        brow.push_back(i);
+      }
+      if (node_body_h[i] < 0 && a.empty()) {  // isolated soft vertex: diagonal mass block only
+        bdiag[i] = (int)bcol.size();
+        bcol.push_back(i);
+        brow.push_back(i);
+      }
+      bptr.push_back((int)bcol.size());
+    }
+    NNZB = (int)bcol.size();
+    std::vector<int> bcnt(NNZB + 1, 0), ntcnt(NN + 1, 0);
+    auto find_blk = [&](int r, int c) {
+      auto b = bcol.begin() + bptr[r], e = bcol.begin() + bptr[r + 1];
+      return (int)(std::lower_bound(b, e, c) - bcol.begin());
+    };
+    std::vector<std::pair<int, int>> contrib;  // (block, src) in tet order
+    contrib.reserve((size_t)16 * NT);
+    for (int t = 0; t < NT; ++t) {
+      int n4[4] = {tets_h[t].x, tets_h[t].y, tets_h[t].z, tets_h[t].w};
+      for (int a = 0; a < 4; ++a) {
+        ntcnt[n4[a] + 1]++;
+        for (int b = 0; b < 4; ++b) contrib.push_back({find_blk(n4[a], n4[b]), 16 * t + 4 * a + b});
+      }
+    }
+    std::stable_sort(contrib.begin(), contrib.end(),
+                     [](const std::pair<int, int>& u, const std::pair<int, int>& w) { return u.first < w.first; });
+    std::vector<int> blkptr(NNZB + 1, 0), blksrc;
+    blksrc.reserve(contrib.size());
+    for (auto& c : contrib) {
+      blkptr[c.first + 1]++;
+      blksrc.push_back(c.second);
+    }
+    for (int k = 0; k < NNZB; ++k) blkptr[k + 1] += blkptr[k];
+    for (int i = 0; i < NN; ++i) ntcnt[i + 1] += ntcnt[i];
+    std::vector<int> ntsrc(4 * (size_t)NT), fillp(ntcnt.begin(), ntcnt.end() - 1);
+    for (int t = 0; t < NT; ++t) {
+      int n4[4] = {tets_h[t].x, tets_h[t].y, tets_h[t].z, tets_h[t].w};
+      for (int a = 0; a < 4; ++a) ntsrc[fillp[n4[a]]++] = 4 * t + a;
+    }
+    // ---------- upload
+    cudaStream_t s = stream;
+    node_off.upload(node_off_h, s);
+    tet_off.upload(tet_off_h, s);
+    body_off.upload(body_off_h, s);
+    nsteps.upload(nsteps_h, s);
+    grav_off.upload(grav_off_h, s);
+    nh.upload(nh_h, s);
+    sched_off.upload(sched_off_h, s);
+    env_mu.upload(mu_h, s);
+    sched.upload(sched_h, s);
+    grav.upload(grav_h, s);
+    node_env.upload(node_env_h, s);
+    node_body.upload(node_body_h, s);
+    node_handle.upload(node_handle_h, s);
+    node_kin.upload(node_kin_h, s);
+    node_mass.upload(node_mass_h, s);
+    X0.upload(X0_h, s);
+    body_node.upload(body_node_h, s);
+    body_env.upload(body_env_h, s);
+    body_kin.upload(body_kin_h, s);
+    M4.upload(M4_h, s);
+    bvol.upload(bvol_h, s);
+    bbox.upload(bbox_h, s);
+    tets.upload(tets_h, s);
+    tet_prm.upload(tet_prm_h, s);
+    tet_env.upload(tet_env_h, s);
+    pt_node.upload(pt_node_h, s);
+    pt_body.upload(pt_body_h, s);
+    pt_env.upload(pt_env_h, s);
+    pt_kin.upload(pt_kin_h, s);
+    pt_xb.upload(pt_xb_h, s);
+    sv_pt.upload(sv_pt_h, s);
+    sv_env.upload(sv_env_h, s);
+    ed_pt.upload(ed_pt_h, s);
+    ed_env.upload(ed_env_h, s);
+    ed_rest2.upload(ed_rest2_h, s);
+    tri_pt.upload(tri_pt_h, s);
+    tri_env.upload(tri_env_h, s);
+    tile_env.upload(te, s);
+    tile_kind.upload(tk, s);
+    tile_begin.upload(tb, s);
+    tile_end.upload(tn, s);
+    tile_off.upload(toff, s);
+    root_off_tri.upload(tri_off_h, s);
+    root_off_ed.upload(ed_off_h, s);
+    bsr_ptr.upload(bptr, s);
+    bsr_col.upload(bcol, s);
+    blk_row.upload(brow, s);
+    bsr_diag.upload(bdiag, s);
+    blk_ptr.upload(blkptr, s);
+    blk_src.upload(blksrc, s);
+    nt_ptr.upload(ntcnt, s);
+    nt_src.upload(ntsrc, s);
+    x.upload(x_h, s);
+    v.upload(v_h, s);
+    size_t n3 = 3 * (size_t)NN;
+    for (DBuf<double>* b : {&xt, &xtilde, &xtarget, &xtrial, &p, &pbar, &grad, &pcg_r, &pcg_z, &pcg_d, &pcg_y, &pcg_x})
+      b->alloc(n3);
+    xtarget.zero(s);
+    for (DBuf<double>* b : {&ptx, &ptx_t, &ptp, &pte}) b->alloc(3 * (size_t)NP);
+    e_status.upload(status_h, s);
+    e_reason.upload(reason_h, s);
+    e_step.upload(step_h, s);
+    e_stats.upload(stats_h, s);
+    for (DBuf<int>* b : {&e_constrained, &e_bad, &e_nanp, &e_halv, &e_newton_it}) b->alloc(E);
+    e_count.alloc(4);
+    for (DBuf<uint8_t>* b : {&e_stepping, &e_iter, &e_ls, &e_accept, &e_sel, &e_all}) {
+      b->alloc(E);
+      b->zero(s);
+    }
+    launch(k_fill_u8, E, 256, E, e_all.p, (uint8_t)1);
+    for (DBuf<double>* b : {&e_E0, &e_Et, &e_alpha}) b->alloc(E);
+    for (DBuf<unsigned long long>* b : {&e_alpha_bits, &e_pnorm_bits, &e_inter, &e_inv}) b->alloc(E);
+    nodeE.alloc(NN);
+    tetE.alloc(NT);
+    tet_g.alloc(12 * (size_t)NT);
+    tet_H.alloc(90 * (size_t)NT);
+    bodyE.alloc(NB);
+    body_g.alloc(12 * (size_t)NB);
+    body_H.alloc(144 * (size_t)NB);
+    bsr_val.alloc(9 * (size_t)NNZB);
+    Ps.alloc(9 * (size_t)NN);
+    Pb.alloc(144 * (size_t)NB);
+    for (DBuf<double>* b : {&part_a, &part_b, &part_c}) b->alloc(NTILE);
+    pcg_rz.alloc(2 * (size_t)E);
+    pcg_bb.alloc(E);
+    pcg_it.alloc(E);
+    pcg_run.alloc(E);
+    pcg_active.alloc(1);
+    cnt_pt.alloc(NSV + 1);
+    off_pt.alloc(NSV + 1);
+    cnt_ee.alloc(NED + 1);
+    off_ee.alloc(NED + 1);
+    overflow.alloc(1);
+    overflow.zero(s);
+    ns_ptr.alloc(NN + 1);
+    ns_cnt.alloc(NN + 1);
+    ttri.built = tedge.built = false;
+    ttri.n = NTR;
+    tedge.n = NED;
+    n_ct = n_ct_pt = n_fr = n_fr_pt = n_pt = n_ee = 0;
+    CK(cudaStreamSynchronize(s));
+    dirty = false;
+    initial_checks();
+  }
+
+  // ------------------------------------------------------------------ BVH
+  void tree_build(TreeBufs& T, const int* prim_pt, int nv, const int* prim_env, const int* prim_off) {
+    int n = T.n;
+    T.pbox.ensure(6 * (size_t)std::max(n, 1));
+    T.nbox.ensure(6 * (size_t)std::max(2 * n - 1, 1));
+    T.keys.ensure(std::max(n, 1));
+    T.vals.ensure(std::max(n, 1));
+    T.child.ensure(2 * (size_t)std::max(n, 1));
+    T.parent.ensure(std::max(2 * n - 1, 1));
+    T.range.ensure(2 * (size_t)std::max(n, 1));
+    T.root.ensure(E);
+    T.flags.ensure(std::max(n, 1));
+    T.emin.ensure(3 * (size_t)E);
+    T.emax.ensure(3 * (size_t)E);
+    if (n == 0) {
+      CK(cudaMemsetAsync(T.root.p, 0xff, E * sizeof(int), stream));
+      T.built = true;
+      return;
+    }
+    if (nv == 3) launch(k_prim_boxes<3>, n, 256, n, prim_pt, (const double*)ptx.p, (const double*)nullptr, 0.0, T.pbox.p);
+    else launch(k_prim_boxes<2>, n, 256, n, prim_pt, (const double*)ptx.p, (const double*)nullptr, 0.0, T.pbox.p);
+    CK(cudaMemsetAsync(T.emin.p, 0xff, 3 * E * sizeof(unsigned long long), stream));
+    CK(cudaMemsetAsync(T.emax.p, 0, 3 * E * sizeof(unsigned long long), stream));
+    launch(k_env_bounds, n, 256, (const double*)T.pbox.p, prim_env, n, T.emin.p, T.emax.p);
+    launch(k_morton, n, 256, (const double*)T.pbox.p, prim_env, n, (const unsigned long long*)T.emin.p,
+           (const unsigned long long*)T.emax.p, T.keys.p, T.vals.p);
+    int env_bits = 1;
+    while ((1 << env_bits) < E) ++env_bits;
+    radix_sort(T.keys, T.vals, T.keys2, T.vals2, T.hist, n, 32 + env_bits);
+    CK(cudaMemsetAsync(T.root.p, 0xff, E * sizeof(int), stream));
+    if (n == 1) {
+      int m1 = -1;
+      CK(cudaMemcpyAsync(T.parent.p, &m1, sizeof(int), cudaMemcpyHostToDevice, stream));
+    }
+    launch(k_karras, n - 1, 256, (const unsigned long long*)T.keys.p, n, T.child.p, T.parent.p, T.range.p);
+    launch(k_env_roots, std::max(n - 1, E), 256, n, (const int*)T.range.p, prim_off, E, prim_env, T.root.p);
+    T.built = true;
+  }
+  void tree_refit(TreeBufs& T) {
+    if (T.n == 0) return;
+    CK(cudaMemsetAsync(T.flags.p, 0, T.n * sizeof(int), stream));
+    launch(k_refit, T.n, 256, T.n, (const unsigned*)T.vals.p, (const double*)T.pbox.p, (const int*)T.child.p,
+           (const int*)T.parent.p, T.nbox.p, T.flags.p);
+  }
+  // build both trees at the current ptx
+  void build_trees() {
+    tree_build(ttri, tri_pt.p, 3, tri_env.p, root_off_tri.p);
+    tree_build(tedge, ed_pt.p, 2, ed_env.p, root_off_ed.p);
+  }
+  // primitive boxes at ptx (r) or swept to pte (r = 0), then refit
+  void boxes_and_refit(const double* end, double r) {
+    launch(k_prim_boxes<3>, NTR, 256, NTR, (const int*)tri_pt.p, (const double*)ptx.p, end, r, ttri.pbox.p);
+    launch(k_prim_boxes<2>, NED, 256, NED, (const int*)ed_pt.p, (const double*)ptx.p, end, r, tedge.pbox.p);
+    tree_refit(ttri);
+    tree_refit(tedge);
+  }
+  void check_overflow() {
+    if (read_int(overflow.p)) {
+      overflow.zero(stream);
+      fail_with(IPC_ERR_INTERNAL, "BVH traversal stack overflow");
+    }
+  }
+
+  // ------------------------------------------------------------------ constraint set
+  // contacts (d < dhat) of the envs in act at positions ptx (already computed)
+  void constraint_set(const uint8_t* act) {
+    double r = 0.5 * desc.dhat;
+    boxes_and_refit(nullptr, r);
+    CandOut o{cnt_pt.p, nullptr, nullptr, overflow.p};
+    launch(k_trav_pt<TRAV_COUNT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
+           (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), o, (const double*)nullptr, ctl());
+    CandOut oe{cnt_ee.p, nullptr, nullptr, overflow.p};
+    launch(k_trav_ee<TRAV_COUNT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+           (const double*)tedge.pbox.p, tree(tedge), ptinfo(), oe, (const double*)nullptr, (const double*)nullptr, ctl());
+    n_pt = scan(cnt_pt.p, NSV, off_pt.p);
+    n_ee = scan(cnt_ee.p, NED, off_ee.p);
+    check_overflow();
+    int nc = n_pt + n_ee;
+    cand_j.ensure(nc + 1);
+    CandOut f{nullptr, off_pt.p, cand_j.p, overflow.p};
+    launch(k_trav_pt<TRAV_FILL>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
+           (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), f, (const double*)nullptr, ctl());
+    CandOut fe{nullptr, off_ee.p, cand_j.p + n_pt, overflow.p};
+    launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+           (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr, ctl());
+    nflag.ensure(nc + 1);
+    noff.ensure(nc + 1);
+    ct_tmp.ensure(nc + 1);
+    double dh2 = desc.dhat * desc.dhat;
+    launch(k_narrow, nc, 128, n_pt, n_ee, (const int*)off_pt.p, NSV, (const int*)off_ee.p, NED, (const int*)cand_j.p,
+           (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p, (const int*)ed_env.p,
+           (const double*)ptx.p, dh2, nflag.p, ct_tmp.p, (const double*)ed_rest2.p);
+    n_ct = scan(nflag.p, nc, noff.p);
+    n_ct_pt = n_pt > 0 ? read_int(noff.p + n_pt) : 0;
+    ct.ensure(n_ct + 1);
+    launch(k_compact_contacts, nc, 256, nc, (const int*)nflag.p, (const int*)noff.p, (const ContactRec*)ct_tmp.p, ct.p);
+  }
+  void stencil_table() {
+    int ns = n_ct + n_fr;
+    st_pts.ensure(4 * (size_t)ns + 4);
+    st_env.ensure(ns + 1);
+    sE.ensure(ns + 1);
+    sg.ensure(12 * (size_t)ns + 12);
+    sH.ensure(78 * (size_t)ns + 78);
+    st_t.ensure(12 * (size_t)ns + 12);
+    launch(k_stencil_table, ns, 256, n_ct, n_fr, (const ContactRec*)ct.p, (const FrictionRec*)fr.p, st_pts.p, st_env.p);
+  }
+  // ------------------------------------------------------------------ energy
+  // energies (and derivatives) of the envs in act at DOFs q; positions/contacts at q are
+  // computed here. Result per env in out.
+  template <int MODE>
+  void evaluate(const double* q, const uint8_t* act, double* out) {
+    launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p, q, ptx.p);
+    constraint_set(act);
+    stencil_table();
+    double h = desc.dt, h2 = h * h;
+    launch(k_inertia_energy, NN, 256, NN, layout(), act, q, (const double*)xtilde.p, nodeE.p);
+    launch(k_elastic<MODE>, NT, 128, NT, (const int4*)tets.p, (const double*)tet_prm.p, (const int*)tet_env.p, act, q,
+           h2, tetE.p, tet_g.p, tet_H.p, e_bad.p);
+    launch(k_bodies<MODE>, NB, 64, NB, (const int*)body_node.p, (const int*)body_env.p, (const uint8_t*)body_kin.p,
+           (const double*)M4.p, (const double*)bvol.p, act, q, (const double*)xtilde.p, h2 * desc.kappa_affine, bodyE.p,
+           body_g.p, body_H.p);
+    launch(k_barrier<MODE>, n_ct, 64, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, h2, desc.dhat, desc.kappa,
+           sE.p, sg.p, sH.p);
+    launch(k_friction<MODE>, n_fr, 128, n_fr, (const FrictionRec*)fr.p, act, (const double*)ptx.p,
+           (const double*)ptx_t.p, h2, desc.eps_v * h, sE.p + n_ct, sg.p + 12 * (size_t)n_ct, sH.p + 78 * (size_t)n_ct);
+    EnergyLists L{nodeE.p, node_off.p, tetE.p, tet_off.p, bodyE.p, body_off.p, sE.p, st_env.p,
+                  n_ct_pt, n_ct - n_ct_pt, n_fr_pt, n_fr};
+    launch_grid(k_env_energy, E, 256, E, L, act, out);
+  }
+
+  // stencil -> node incidence (stable by stencil order within each node)
+  void stencil_incidence(const uint8_t* act) {
+    int ns = n_ct + n_fr;
+    st_cnt.ensure(ns + 1);
+    st_off.ensure(ns + 1);
+    launch(k_stencil_nent, ns, 256, ns, (const int*)st_pts.p, (const int*)st_env.p, act, (const int*)pt_node.p, st_cnt.p);
+    int ne = scan(st_cnt.p, ns, st_off.p);
+    st_keys.ensure(ne + 1);
+    st_vals.ensure(ne + 1);
+    launch(k_stencil_emit, ns, 256, ns, (const int*)st_pts.p, (const int*)st_env.p, act, (const int*)pt_node.p,
+           (const int*)body_node.p, (const int*)st_off.p, st_keys.p, st_vals.p);
+    int bits = 1;
+    while ((1 << bits) < NN) ++bits;
+    radix_sort(st_keys, st_vals, st_keys2, st_vals2, st_hist, ne, bits);
+    CK(cudaMemsetAsync(ns_cnt.p, 0, (NN + 1) * sizeof(int), stream));
+    launch(k_count_keys, ne, 256, ne, (const unsigned long long*)st_keys.p, ns_cnt.p);
+    scan(ns_cnt.p, NN, ns_ptr.p, false);
+    ns_src.ensure(ne + 1);
+    if (ne > 0) CK(cudaMemcpyAsync(ns_src.p, st_vals.p, ne * sizeof(unsigned), cudaMemcpyDeviceToDevice, stream));
+  }
+
+  SpmvArgs spmv_args() {
+    return SpmvArgs{bsr_ptr.p, bsr_col.p, bsr_val.p, body_H.p, ns_ptr.p, ns_src.p, st_pts.p, st_t.p};
+  }
+  // y = H d over the envs in run (stencil product, then BSR/body rows); partial d.y per tile
+  void matvec(const uint8_t* run, const double* d, double* y, double* part) {
+    int ns = n_ct + n_fr;
+    launch(k_stencil_mv, ns, 128, ns, layout(), (const int*)st_env.p, (const int*)st_pts.p, run, (const double*)sH.p, d,
+           st_t.p);
+    launch_grid(k_spmv, NTILE, TILE, tiles(), layout(), spmv_args(), run, d, y, part);
+  }
+
+  // ------------------------------------------------------------------ PCG
+  void pcg(const uint8_t* act) {
+    PcgState S{pcg_rz.p, pcg_bb.p, pcg_it.p, pcg_run.p, pcg_active.p, e_stats.p + 0};
+    // per-env cumulative iterations live in e_stats[5e + 1]: pass a strided view via a kernel
+    CK(cudaMemsetAsync(pcg_active.p, 0, sizeof(int), stream));
+    launch_grid(k_pcg_init, NTILE, TILE, tiles(), layout(), act, (const double*)Ps.p, (const double*)Pb.p,
+                (const double*)pcg_r.p, pcg_z.p, pcg_d.p, pcg_x.p, part_b.p, part_c.p);
+    pcg_iters.ensure(E);
+    pcg_iters.zero(stream, E);
+    S.total_iters = pcg_iters.p;
+    launch(k_pcg_init_env, E, 128, E, tiles(), act, (const double*)part_b.p, (const double*)part_c.p, S);
+    int active = read_int(pcg_active.p);
+    int parity = 0;
+    int done_iters = 0;
+    double tol2 = desc.pcg_rel_tol * desc.pcg_rel_tol;
+    const int chunk = 8;
+    while (active > 0 && done_iters < desc.max_pcg_iters) {
+      for (int c = 0; c < chunk; ++c) {
+        matvec(pcg_run.p, pcg_d.p, pcg_y.p, part_a.p);
+        launch_grid(k_pcg_update, NTILE, TILE, tiles(), layout(), S, parity, E, (const double*)part_a.p,
+                    (const double*)Ps.p, (const double*)Pb.p, (const double*)pcg_d.p, (const double*)pcg_y.p, pcg_x.p,
+                    pcg_r.p, pcg_z.p, part_b.p, part_c.p);
+        launch_grid(k_pcg_direction, NTILE, TILE, tiles(), layout(), S, parity, E, tol2, desc.max_pcg_iters,
+                    (const double*)part_b.p, (const double*)part_c.p, (const double*)part_a.p, (const double*)pcg_z.p,
+                    pcg_d.p);
+        parity ^= 1;
+      }
+      done_iters += chunk;
+      active = read_int(pcg_active.p);
+    }
+    launch(k_add_stats, E, 128, E, (const long long*)pcg_iters.p, e_stats.p);
+    CK(cudaStreamSynchronize(stream));
+  }
+
+  // ------------------------------------------------------------------ one Newton iteration
+  void assemble(const uint8_t* act) {
+    stencil_incidence(act);
+    launch(k_assemble_grad, NN, 256, NN, layout(), act, (const double*)x.p, (const double*)xtilde.p, (const int*)nt_ptr.p,
+           (const int*)nt_src.p, (const double*)tet_g.p, (const double*)body_g.p, (const int*)ns_ptr.p,
+           (const int*)ns_src.p, (const int*)st_pts.p, (const double*)sg.p, grad.p, nodeE.p);
+    launch(k_assemble_bsr, NNZB, 128, NNZB, (const int*)blk_row.p, (const int*)bsr_col.p, layout(), act,
+           (const int*)blk_ptr.p, (const int*)blk_src.p, (const double*)tet_H.p, bsr_val.p);
+    launch(k_precond_soft, NN, 256, NN, layout(), act, (const int*)bsr_diag.p, (const double*)bsr_val.p,
+           (const int*)ns_ptr.p, (const int*)ns_src.p, (const double*)sH.p, Ps.p);
+    launch_grid(k_precond_body, NB, 144, NB, layout(), (const int*)body_env.p, act, (const double*)body_H.p,
+                (const int*)ns_ptr.p, (const int*)ns_src.p, (const int*)st_pts.p, (const double*)sH.p, Pb.p);
+  }
+
+  // step set-up for the envs in act: x^t, x~, targets, positions at x^t, trees, friction lag
+  void step_setup(const uint8_t* act) {
+    launch(k_step_setup_nodes, NN, 256, NN, layout(), ctl(), act, sched_view(), desc.dt, desc.gravity[0],
+           desc.gravity[1], desc.gravity[2], (const double*)x.p, (const double*)v.p, xt.p, xtilde.p, xtarget.p);
+    launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p,
+           (const double*)x.p, ptx.p);
+    build_trees();
+    n_fr = n_fr_pt = 0;
+    constraint_set(act);
+    CK(cudaMemcpyAsync(ptx_t.p, ptx.p, 3 * (size_t)NP * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    fr.ensure(n_ct + 1);
+    launch(k_friction_setup, n_ct, 128, n_ct, (const ContactRec*)ct.p, (const double*)ptx.p, (const double*)env_mu.p,
+           desc.dhat, desc.kappa, fr.p);
+    n_fr = n_ct;
+    n_fr_pt = n_ct_pt;
+  }
+
+  void newton_step() {
+    EnvCtl C = ctl();
+    launch(k_env_begin_step, E, 128, E, C);
+    if (count_flags(e_stepping.p) == 0) return;
+    step_setup(e_stepping.p);
+    for (int it = 0; it < desc.max_newton; ++it) {
+      if (count_flags(e_iter.p) == 0) break;
+      launch(k_env_iter_begin, E, 128, E, C);
+      evaluate<MODE_HESS>(x.p, e_iter.p, e_E0.p);
+      assemble(e_iter.p);
+      // kinematic step and the reduced right-hand side -g - H pbar
+      launch(k_pbar, NN, 256, NN, layout(), C, (const double*)x.p, (const double*)xtarget.p, pbar.p);
+      matvec(e_iter.p, pbar.p, pcg_y.p, part_a.p);
+      launch(k_rhs, NN, 256, NN, layout(), (const uint8_t*)e_iter.p, (const double*)grad.p, (const double*)pcg_y.p,
+             pcg_r.p);
+      pcg(e_iter.p);
+      launch(k_direction, NN, 256, NN, layout(), C, (const double*)pcg_x.p, (const double*)pbar.p, (const double*)bbox.p,
+             p.p);
+      launch(k_env_converge, E, 128, E, C, desc.dt, desc.newton_tol);
+      if (count_flags(e_iter.p) == 0) break;
+      // CCD step filter: swept candidates at [x, x + p], ACCD, per-env minimum
+      launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p,
+             (const double*)x.p, ptx.p);
+      launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p,
+             (const double*)p.p, ptp.p);
+      launch(k_add_vec, 3L * NP, 256, 3L * NP, (const double*)ptx.p, (const double*)ptp.p, pte.p);
+      boxes_and_refit(pte.p, 0.0);
+      CandOut oc{nullptr, nullptr, nullptr, overflow.p};
+      launch(k_trav_pt<TRAV_CCD>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, (const uint8_t*)e_iter.p,
+             (const double*)ptx.p, (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), oc,
+             (const double*)ptp.p, C);
+      launch(k_trav_ee<TRAV_CCD>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, (const uint8_t*)e_iter.p,
+             (const double*)tedge.pbox.p, tree(tedge), ptinfo(), oc, (const double*)ptx.p, (const double*)ptp.p, C);
+      check_overflow();
+      // backtracking line search on the envs still iterating
+      launch(k_env_ls_begin, E, 128, E, C);
+      for (int ls = 0; ls <= desc.max_ls_halvings + 1; ++ls) {
+        launch(k_trial, NN, 256, NN, layout(), C, (const double*)x.p, (const double*)p.p, xtrial.p);
+        evaluate<MODE_ENERGY>(xtrial.p, e_ls.p, e_Et.p);
+        launch(k_env_ls_decide, E, 128, E, C, desc.max_ls_halvings);
+        if (count_flags(e_ls.p) == 0) break;
+      }
+      launch(k_accept, NN, 256, NN, layout(), C, (const double*)xtrial.p, (const double*)xtarget.p, x.p);
+      launch(k_env_newton_end, E, 128, E, C, desc.max_newton);
+    }
+    launch(k_end_step_nodes, NN, 256, NN, layout(), C, desc.dt, (const double*)x.p, (const double*)xt.p, v.p);
+    launch(k_env_end_step, E, 128, E, C);
+    CK(cudaStreamSynchronize(stream));
+  }
+
+  // ------------------------------------------------------------------ validation / queries
+  void invariants(const uint8_t* act, const double* q) {
+    CK(cudaMemsetAsync(e_inter.p, 0, E * 8, stream));
+    CK(cudaMemsetAsync(e_inv.p, 0, E * 8, stream));
+    launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p, q, ptx.p);
+    if (!ttri.built || !tedge.built) build_trees();
+    boxes_and_refit(nullptr, 0.0);
+    launch(k_intersections, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act, (const double*)tedge.pbox.p,
+           tree(ttri), (const int*)tri_pt.p, ptinfo(), (const double*)ptx.p, e_inter.p, overflow.p);
+    launch(k_inverted, NT, 256, NT, (const int4*)tets.p, (const int*)tet_env.p, act, q, e_inv.p);
+    check_overflow();
+  }
+  void initial_checks() {
+    // newly laid-out envs that were never checked: an intersecting start fails the env
+    std::vector<uint8_t> sel(E, 0);
+    bool any = false;
+    for (int li = 0; li < E; ++li)
+      if (!envs[ids[li]].checked) {
+        sel[li] = 1;
+        any = true;
+      }
+    if (!any) return;
+    CK(cudaMemcpyAsync(e_sel.p, sel.data(), E, cudaMemcpyHostToDevice, stream));
+    invariants(e_sel.p, x.p);
+    std::vector<unsigned long long> inter(E);
+    CK(cudaMemcpyAsync(inter.data(), e_inter.p, E * 8, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    std::vector<int> st(E), rs(E);
+    CK(cudaMemcpy(st.data(), e_status.p, E * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rs.data(), e_reason.p, E * 4, cudaMemcpyDeviceToHost));
+    for (int li = 0; li < E; ++li) {
+      if (!sel[li]) continue;
+      envs[ids[li]].checked = true;
+      if (inter[li] > 0) {
+        st[li] = ST_FAILED;
+        rs[li] = FAIL_INIT_INTERSECT;
+      }
+    }
+    CK(cudaMemcpy(e_status.p, st.data(), E * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(e_reason.p, rs.data(), E * 4, cudaMemcpyHostToDevice));
+    ttri.built = tedge.built = false;
+  }
+  int layout_index(int id) {
+    for (int li = 0; li < E; ++li)
+      if (ids[li] == id) return li;
+    fail_with(IPC_ERR_ARG, "unknown env id " + std::to_string(id));
+  }
+  void select(int li) { launch(k_set_single, E, 128, E, e_sel.p, li); }
+};
+
+
+// ==================================================================== C ABI
+#define API_BEGIN try {
+#define API_END                              \
+  }                                          \
+  catch (const IpcError& err) {              \
+    g_err = err.msg;                         \
+    return err.st;                           \
+  }                                          \
+  catch (const std::bad_alloc&) {            \
+    g_err = "host allocation failed";        \
+    return IPC_ERR_OOM;                      \
+  }                                          \
+  catch (const std::exception& ex) {         \
+    g_err = ex.what();                       \
+    return IPC_ERR_INTERNAL;                 \
+  }                                          \
+  return IPC_OK;
+
+extern "C" {
+
+const char* ipc_last_error(void) { return g_err.c_str(); }
+const char* ipc_version(void) { return "b300-ipc 0.1 (sm_103a, FP64)"; }
+
+ipc_status ipc_scene_create(const ipc_scene_desc* desc, ipc_scene** out) {
+  API_BEGIN
+  if (!desc || !out) fail_with(IPC_ERR_ARG, "null argument");
+  if (!(desc->dt > 0) || !(desc->dhat > 0) || !(desc->kappa > 0)) fail_with(IPC_ERR_ARG, "dt, dhat and kappa must be > 0");
+  if (desc->precision != IPC_FP64 && desc->precision != IPC_MIXED) fail_with(IPC_ERR_ARG, "unknown precision");
+  std::unique_ptr<ipc_scene> s(new ipc_scene());
+  s->desc = *desc;
+  if (s->desc.max_newton <= 0) s->desc.max_newton = 100;
+  if (s->desc.max_ls_halvings <= 0) s->desc.max_ls_halvings = 40;
+  if (s->desc.max_pcg_iters <= 0) s->desc.max_pcg_iters = 1000;
+  s->device = desc->device;
+  CK(cudaSetDevice(s->device));
+  if (desc->cuda_stream) {
+    s->stream = (cudaStream_t)desc->cuda_stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  CK(cudaMallocHost(&s->hpin, 64));
+  *out = s.release();
+  API_END
+}
+
+ipc_status ipc_scene_destroy(ipc_scene* s) {
+  API_BEGIN
+  if (!s) fail_with(IPC_ERR_ARG, "null scene");
+  cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  delete s;
+  API_END
+}
+
+ipc_status ipc_env_estimate_bytes(const ipc_env_desc* env, int32_t precision, uint64_t* bytes) {
+  API_BEGIN
+  if (!bytes) fail_with(IPC_ERR_ARG, "null output");
+  HostEnv h;
+  build_env(h, env);
+  *bytes = estimate_bytes(h, precision);
+  API_END
+}
+
+ipc_status ipc_env_add(ipc_scene* s, const ipc_env_desc* env, int32_t* env_id) {
+  API_BEGIN
+  if (!s || !env) fail_with(IPC_ERR_ARG, "null argument");
+  HostEnv h;
+  build_env(h, env);
+  h.est_bytes = estimate_bytes(h, s->desc.precision);
+  if (s->desc.hbm_budget_bytes && s->used_bytes + h.est_bytes > s->desc.hbm_budget_bytes)
+    fail_with(IPC_ERR_BUDGET, "env does not fit the HBM budget");
+  if (!s->dirty && !s->ids.empty()) {
+    CK(cudaSetDevice(s->device));
+    s->pull_state();
+  }
+  h.id = s->next_id++;
+  s->used_bytes += h.est_bytes;
+  int id = h.id;
+  s->envs.emplace(id, std::move(h));
+  s->dirty = true;
+  if (env_id) *env_id = id;
+  API_END
+}
+
+ipc_status ipc_env_remove(ipc_scene* s, int32_t env_id) {
+  API_BEGIN
+  if (!s) fail_with(IPC_ERR_ARG, "null scene");
+  auto it = s->envs.find(env_id);
+  if (it == s->envs.end()) fail_with(IPC_ERR_ARG, "unknown env id");
+  if (!s->dirty && !s->ids.empty()) {
+    CK(cudaSetDevice(s->device));
+    s->pull_state();
+  }
+  s->used_bytes -= it->second.est_bytes;
+  s->envs.erase(it);
+  s->dirty = true;
+  API_END
+}
+
+ipc_status ipc_step(ipc_scene* s, int32_t n_steps) {
+  API_BEGIN
+  if (!s || n_steps < 0) fail_with(IPC_ERR_ARG, "bad argument");
+  CK(cudaSetDevice(s->device));
+  s->commit();
+  for (int i = 0; i < n_steps; ++i) s->newton_step();
+  API_END
+}
+
+ipc_status ipc_env_set_state(ipc_scene* s, int32_t env_id, const double* x, const double* v, int32_t step) {
+  API_BEGIN
+  if (!s || !x || !v) fail_with(IPC_ERR_ARG, "null argument");
+  CK(cudaSetDevice(s->device));
+  s->commit();
+  int li = s->layout_index(env_id);
+  HostEnv& h = s->envs[env_id];
+  if (step < 0 || step > h.n_steps) fail_with(IPC_ERR_ARG, "step out of range");
+  size_t o = 3 * (size_t)s->h_node_off[li];
+  CK(cudaMemcpyAsync(s->x.p + o, x, h.ndof * 8, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->v.p + o, v, h.ndof * 8, cudaMemcpyHostToDevice, s->stream));
+  int st = step >= h.n_steps ? ST_DONE : ST_ACTIVE, rs = FAIL_NONE;
+  CK(cudaMemcpyAsync(s->e_step.p + li, &step, 4, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->e_status.p + li, &st, 4, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->e_reason.p + li, &rs, 4, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  API_END
+}
+
+ipc_status ipc_eval(ipc_scene* s, int32_t env_id, const double* q, double* energy, double* grad) {
+  API_BEGIN
+  if (!s || !q || !energy) fail_with(IPC_ERR_ARG, "null argument");
+  CK(cudaSetDevice(s->device));
+  s->commit();
+  int li = s->layout_index(env_id);
+  HostEnv& h = s->envs[env_id];
+  s->select(li);
+  s->step_setup(s->e_sel.p);
+  size_t o = 3 * (size_t)s->h_node_off[li];
+  CK(cudaMemcpyAsync(s->xtrial.p, s->x.p, 3 * (size_t)s->NN * 8, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->xtrial.p + o, q, h.ndof * 8, cudaMemcpyHostToDevice, s->stream));
+  s->evaluate<MODE_GRAD>(s->xtrial.p, s->e_sel.p, s->e_E0.p);
+  // gradient: gather with the stencil incidence of this evaluation, at q
+  s->stencil_incidence(s->e_sel.p);
+  s->launch(k_assemble_grad, s->NN, 256, s->NN, s->layout(), (const uint8_t*)s->e_sel.p, (const double*)s->xtrial.p,
+            (const double*)s->xtilde.p, (const int*)s->nt_ptr.p, (const int*)s->nt_src.p, (const double*)s->tet_g.p,
+            (const double*)s->body_g.p, (const int*)s->ns_ptr.p, (const int*)s->ns_src.p, (const int*)s->st_pts.p,
+            (const double*)s->sg.p, s->grad.p, s->nodeE.p);
+  CK(cudaMemcpyAsync(energy, s->e_E0.p + li, 8, cudaMemcpyDeviceToHost, s->stream));
+  if (grad) CK(cudaMemcpyAsync(grad, s->grad.p + o, h.ndof * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->ttri.built = s->tedge.built = false;
+  API_END
+}
+
+static ipc_status copy_out(const void* src, size_t bytes, void* out, size_t out_bytes, size_t* written) {
+  if (written) *written = bytes;
+  if (out_bytes < bytes || (!out && bytes)) {
+    g_err = "output buffer too small";
+    return IPC_ERR_ARG;
+  }
+  if (bytes) std::memcpy(out, src, bytes);
+  return IPC_OK;
+}
+
+ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size_t out_bytes, size_t* written) {
+  API_BEGIN
+  if (!s) fail_with(IPC_ERR_ARG, "null scene");
+  CK(cudaSetDevice(s->device));
+  s->commit();
+  int li = s->layout_index(env_id);
+  HostEnv& h = s->envs[env_id];
+  size_t o = 3 * (size_t)s->h_node_off[li];
+  switch (kind) {
+    case IPC_Q_DOFS:
+    case IPC_Q_VELOCITIES: {
+      std::vector<double> buf(h.ndof);
+      CK(cudaMemcpyAsync(buf.data(), (kind == IPC_Q_DOFS ? s->x.p : s->v.p) + o, h.ndof * 8, cudaMemcpyDeviceToHost,
+                         s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      return copy_out(buf.data(), buf.size() * 8, out, out_bytes, written);
+    }
+    case IPC_Q_STATUS: {
+      int v[4];
+      CK(cudaMemcpyAsync(&v[0], s->e_status.p + li, 4, cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaMemcpyAsync(&v[1], s->e_reason.p + li, 4, cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaMemcpyAsync(&v[3], s->e_step.p + li, 4, cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      v[2] = v[3];
+      return copy_out(v, sizeof(v), out, out_bytes, written);
+    }
+    case IPC_Q_STATS: {
+      long long v[5];
+      CK(cudaMemcpyAsync(v, s->e_stats.p + 5 * li, 40, cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      return copy_out(v, sizeof(v), out, out_bytes, written);
+    }
+    case IPC_Q_SIZES: {
+      long long v[8] = {h.ndof, (long long)h.pt_node.size(), (long long)h.sv.size(), (long long)h.edges.size() / 2,
+                        (long long)h.tris.size() / 3, h.ntets, h.nbodies, h.n_steps};
+      return copy_out(v, sizeof(v), out, out_bytes, written);
+    }
+    case IPC_Q_POINTS: {
+      s->launch(k_points, s->NP, 256, s->NP, (const int*)s->pt_node.p, (const double*)s->pt_xb.p,
+                (const int*)s->body_node.p, (const double*)s->x.p, s->ptx.p);
+      int np = (int)h.pt_node.size();
+      std::vector<double> buf(3 * (size_t)np);
+      CK(cudaMemcpyAsync(buf.data(), s->ptx.p + 3 * (size_t)s->h_pt_off[li], buf.size() * 8, cudaMemcpyDeviceToHost,
+                         s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      return copy_out(buf.data(), buf.size() * 8, out, out_bytes, written);
+    }
+    case IPC_Q_INTERSECTIONS: {
+      s->select(li);
+      s->invariants(s->e_sel.p, s->x.p);
+      long long v[2];
+      CK(cudaMemcpyAsync(&v[0], s->e_inter.p + li, 8, cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaMemcpyAsync(&v[1], s->e_inv.p + li, 8, cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      s->ttri.built = s->tedge.built = false;
+      return copy_out(v, sizeof(v), out, out_bytes, written);
+    }
+    case IPC_Q_CANDIDATES:
+    case IPC_Q_CONTACTS: {
+      s->select(li);
+      s->launch(k_points, s->NP, 256, s->NP, (const int*)s->pt_node.p, (const double*)s->pt_xb.p,
+                (const int*)s->body_node.p, (const double*)s->x.p, s->ptx.p);
+      s->build_trees();
+      s->constraint_set(s->e_sel.p);
+      int nc = s->n_pt + s->n_ee;
+      std::vector<int> cj(nc), offp(s->NSV + 1), offe(s->NED + 1);
+      std::vector<ContactRec> ct(s->n_ct);
+      if (nc) CK(cudaMemcpyAsync(cj.data(), s->cand_j.p, nc * 4, cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaMemcpyAsync(offp.data(), s->off_pt.p, (s->NSV + 1) * 4, cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaMemcpyAsync(offe.data(), s->off_ee.p, (s->NED + 1) * 4, cudaMemcpyDeviceToHost, s->stream));
+      if (s->n_ct) CK(cudaMemcpyAsync(ct.data(), s->ct.p, s->n_ct * sizeof(ContactRec), cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      s->ttri.built = s->tedge.built = false;
+      int sv0 = s->h_sv_off[li], ed0 = s->h_ed_off[li], tr0 = s->h_tri_off[li];
+      std::vector<int> rows;
+      if (kind == IPC_Q_CANDIDATES) {
+        for (int q = s->h_sv_off[li]; q < s->h_sv_off[li + 1]; ++q)
+          for (int k = offp[q]; k < offp[q + 1]; ++k) rows.insert(rows.end(), {0, q - sv0, cj[k] - tr0});
+        for (int q = s->h_ed_off[li]; q < s->h_ed_off[li + 1]; ++q)
+          for (int k = offe[q]; k < offe[q + 1]; ++k) rows.insert(rows.end(), {1, q - ed0, cj[s->n_pt + k] - ed0});
+      } else {
+        for (auto& c : ct) {
+          int i = c.cand;
+          if (c.kind == 0) {
+            int q = (int)(std::upper_bound(offp.begin(), offp.end(), i) - offp.begin()) - 1;
+            while (q + 1 <= s->NSV && offp[q + 1] <= i) ++q;
+            rows.insert(rows.end(), {0, q - sv0, cj[i] - tr0, c.type});
+          } else {
+            int k = i - s->n_pt;
+            int q = (int)(std::upper_bound(offe.begin(), offe.end(), k) - offe.begin()) - 1;
+            rows.insert(rows.end(), {1, q - ed0, cj[i] - ed0, c.type});
+          }
+        }
+      }
+      return copy_out(rows.data(), rows.size() * 4, out, out_bytes, written);
+    }
+    default:
+      fail_with(IPC_ERR_ARG, "unknown query kind");
+  }
+  API_END
+}
+
+ipc_status ipc_set_next_targets(ipc_scene* s, const double* targets, size_t bytes) {
+  API_BEGIN
+  if (!s || !targets) fail_with(IPC_ERR_ARG, "null argument");
+  CK(cudaSetDevice(s->device));
+  s->commit();
+  std::vector<int> st(s->E), sp(s->E);
+  CK(cudaMemcpyAsync(st.data(), s->e_status.p, s->E * 4, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(sp.data(), s->e_step.p, s->E * 4, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  size_t need = 0;
+  for (int li = 0; li < s->E; ++li)
+    if (st[li] == ST_ACTIVE) need += 12 * 8 * (s->envs[s->ids[li]].soft.size() + s->envs[s->ids[li]].aff.size());
+  if (bytes != need) fail_with(IPC_ERR_ARG, "targets: expected " + std::to_string(need) + " bytes");
+  size_t src = 0;
+  long so = 0;
+  for (int li = 0; li < s->E; ++li) {
+    HostEnv& h = s->envs[s->ids[li]];
+    int nhb = (int)(h.soft.size() + h.aff.size());
+    if (st[li] == ST_ACTIVE) {
+      size_t dst = so + (size_t)sp[li] * nhb * 12;
+      CK(cudaMemcpyAsync(s->sched.p + dst, targets + src, nhb * 12 * 8, cudaMemcpyHostToDevice, s->stream));
+      src += nhb * 12;
+    }
+    so += (long)h.targets.size();
+  }
+  API_END
+}
+
+ipc_status ipc_get_all_dofs(ipc_scene* s, double* out, size_t out_bytes, size_t* written) {
+  API_BEGIN
+  if (!s) fail_with(IPC_ERR_ARG, "null scene");
+  CK(cudaSetDevice(s->device));
+  s->commit();
+  size_t bytes = 3 * (size_t)s->NN * 8;
+  if (written) *written = bytes;
+  if (out_bytes < bytes || !out) fail_with(IPC_ERR_ARG, "output buffer too small");
+  CK(cudaMemcpyAsync(out, s->x.p, bytes, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  API_END
+}
+
+ipc_status ipc_launch_count(ipc_scene* s, int64_t* count) {
+  API_BEGIN
+  if (!s || !count) fail_with(IPC_ERR_ARG, "null argument");
+  *count = s->launches;
+  API_END
+}
+
+}  // extern "C"

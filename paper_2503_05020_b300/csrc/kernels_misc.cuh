@@ -1,0 +1,650 @@
+// Per-node, per-env and per-candidate control kernels of the batched Newton loop: step
+// set-up, kinematic targets, Newton direction bookkeeping, convergence, line search, candidate
+// generation, narrow phase, CCD step filter, friction lagging and stencil incidence.
+#pragma once
+#include "common.cuh"
+#include "geometry.cuh"
+#include "lbvh.cuh"
+#include "energy.cuh"
+#include "solver.cuh"
+
+enum { ST_ACTIVE = 0, ST_DONE = 1, ST_FAILED = 2 };
+enum { FAIL_NONE = 0, FAIL_NEWTON = 1, FAIL_LINESEARCH = 2, FAIL_NAN = 3, FAIL_INIT_INTERSECT = 4, FAIL_INTERNAL = 5 };
+enum { STAT_NEWTON = 0, STAT_PCG = 1, STAT_LS = 2, STAT_STEPS = 3, STAT_ACCD = 4 };
+
+struct EnvCtl {
+  int* status;
+  int* reason;
+  int* step;
+  int* nsteps;
+  uint8_t* stepping;   // stepping in the current time step
+  uint8_t* iter;       // Newton still iterating
+  uint8_t* ls;         // line search pending
+  uint8_t* accept;     // accepted a trial this iteration
+  int* constrained;    // kinematic DOFs not at target
+  int* bad;            // some tet inverted at the trial
+  int* nanp;           // non-finite Newton direction
+  int* halv;
+  int* newton_it;
+  double* E0;
+  double* Et;
+  double* alpha;
+  unsigned long long* alpha_bits;
+  unsigned long long* pnorm_bits;
+  long long* stats;    // 5 per env
+  int* flag_count;
+};
+
+struct Sched {
+  const double* targets;
+  const uint8_t* gravity;
+  const long* sched_off;  // doubles
+  const int* grav_off;
+  const int* nh;          // handles per env
+  const int* node_handle; // env-local handle of each node (soft: its body; body nodes: n_soft + b)
+  const double* X0;
+};
+
+// x^t = x; predicted x~ = (x^t + h v) + h^2 g (gravity only on soft nodes and body translations);
+// kinematic targets of this step.
+__global__ void k_step_setup_nodes(int n_nodes, Layout L, EnvCtl C, const uint8_t* __restrict__ act, Sched S, double h,
+                                   double gx, double gy, double gz, const double* __restrict__ x,
+                                   const double* __restrict__ v, double* __restrict__ xt, double* __restrict__ xtilde,
+                                   double* __restrict__ xtarget) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  int e = L.node_env[i];
+  if (!act[e]) return;
+  int step = C.step[e];
+  if (step >= C.nsteps[e]) step = C.nsteps[e] - 1;
+  double hh = S.gravity[S.grav_off[e] + step] ? h * h : 0.0;
+  int b = L.node_body[i];
+  bool grav_node = b < 0 || (i - L.body_node[b]) == 0;
+  double g[3] = {gx, gy, gz};
+  for (int k = 0; k < 3; ++k) {
+    double xv = x[3L * i + k];
+    xt[3L * i + k] = xv;
+    double r = xv + h * v[3L * i + k];
+    if (grav_node) r = r + hh * g[k];
+    xtilde[3L * i + k] = r;
+  }
+  const double* T = S.targets + S.sched_off[e] + ((long)step * S.nh[e] + S.node_handle[i]) * 12;
+  if (b < 0) {
+    if (L.node_kin[i]) {
+      const double* X0 = S.X0 + 3L * i;
+      for (int k = 0; k < 3; ++k) {
+        double r = add_mul_rn(T[k], X0[0], T[3 + k]);
+        r = add_mul_rn(r, X0[1], T[6 + k]);
+        r = add_mul_rn(r, X0[2], T[9 + k]);
+        xtarget[3L * i + k] = r;
+      }
+    }
+  } else if (L.body_kin[b]) {
+    int blk = i - L.body_node[b];
+    for (int k = 0; k < 3; ++k) xtarget[3L * i + k] = T[3 * blk + k];
+  }
+}
+
+// kinematic part of the Newton step: pbar = target - x on kinematic nodes, 0 elsewhere
+__global__ void k_pbar(int n_nodes, Layout L, EnvCtl C, const double* __restrict__ x, const double* __restrict__ xtarget,
+                       double* __restrict__ pbar) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  int e = L.node_env[i];
+  if (!C.iter[e]) return;
+  int b = L.node_body[i];
+  bool kin = b < 0 ? L.node_kin[i] : L.body_kin[b];
+  d3 p = mk3(0, 0, 0);
+  if (kin) {
+    p = ld3(xtarget, i) - ld3(x, i);
+    if (p.x != 0.0 || p.y != 0.0 || p.z != 0.0) atomicOr(&C.constrained[e], 1);
+  }
+  st3(pbar, i, p);
+}
+
+// r = -g - y on free DOFs, 0 on kinematic ones
+__global__ void k_rhs(int n_nodes, Layout L, const uint8_t* __restrict__ act, const double* __restrict__ g,
+                      const double* __restrict__ y, double* __restrict__ r) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  if (!act[L.node_env[i]]) return;
+  int b = L.node_body[i];
+  bool kin = b < 0 ? L.node_kin[i] : L.body_kin[b];
+  for (int k = 0; k < 3; ++k) r[3L * i + k] = kin ? 0.0 : -g[3L * i + k] - y[3L * i + k];
+}
+
+// p = delta (free) or pbar (kinematic); infinity norm in world space of the free part
+__global__ void k_direction(int n_nodes, Layout L, EnvCtl C, const double* __restrict__ delta,
+                            const double* __restrict__ pbar, const double* __restrict__ bbox, double* __restrict__ p) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  int e = L.node_env[i];
+  if (!C.iter[e]) return;
+  int b = L.node_body[i];
+  bool kin = b < 0 ? L.node_kin[i] : L.body_kin[b];
+  d3 v = kin ? ld3(pbar, i) : ld3(delta, i);
+  st3(p, i, v);
+  if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(&C.nanp[e], 1);
+  if (kin) return;
+  double m = 0.0;
+  if (b < 0) {
+    m = fmax(fabs(v.x), fmax(fabs(v.y), fabs(v.z)));
+  } else if (i == L.body_node[b]) {
+    // max over the 8 rest bounding-box corners of |J(corner) p_q|_inf
+    long base = i;
+    d3 pq[4];
+    for (int k = 0; k < 4; ++k) pq[k] = kin ? mk3(0, 0, 0) : ld3(delta, base + k);
+    const double* B = bbox + 6L * b;
+    for (int c = 0; c < 8; ++c) {
+      double xb0 = (c & 1) ? B[3] : B[0], xb1 = (c & 2) ? B[4] : B[1], xb2 = (c & 4) ? B[5] : B[2];
+      for (int k = 0; k < 3; ++k) {
+        double r = add_mul_rn(comp(pq[0], k), xb0, comp(pq[1], k));
+        r = add_mul_rn(r, xb1, comp(pq[2], k));
+        r = add_mul_rn(r, xb2, comp(pq[3], k));
+        m = fmax(m, fabs(r));
+      }
+    }
+  } else {
+    return;
+  }
+  if (isfinite(m)) atomic_max_pos(&C.pnorm_bits[e], m);
+}
+
+__global__ void k_trial(int n_nodes, Layout L, EnvCtl C, const double* __restrict__ x, const double* __restrict__ p,
+                        double* __restrict__ xtr) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  int e = L.node_env[i];
+  double a = C.ls[e] ? C.alpha[e] : 0.0;
+  for (int k = 0; k < 3; ++k) {
+    double xv = x[3L * i + k];
+    xtr[3L * i + k] = C.ls[e] ? xv + a * p[3L * i + k] : xv;
+  }
+}
+
+__global__ void k_accept(int n_nodes, Layout L, EnvCtl C, const double* __restrict__ xtr,
+                         const double* __restrict__ xtarget, double* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  int e = L.node_env[i];
+  if (!C.accept[e]) return;
+  int b = L.node_body[i];
+  bool kin = b < 0 ? L.node_kin[i] : L.body_kin[b];
+  bool snap = kin && C.constrained[e] && C.alpha[e] == 1.0;
+  for (int k = 0; k < 3; ++k) x[3L * i + k] = snap ? xtarget[3L * i + k] : xtr[3L * i + k];
+}
+
+__global__ void k_end_step_nodes(int n_nodes, Layout L, EnvCtl C, double h, const double* __restrict__ x,
+                                 const double* __restrict__ xt, double* __restrict__ v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  int e = L.node_env[i];
+  if (!C.stepping[e] || C.status[e] != ST_ACTIVE) return;
+  for (int k = 0; k < 3; ++k) v[3L * i + k] = (x[3L * i + k] - xt[3L * i + k]) / h;
+}
+
+// ---------------------------------------------------------------- per-env control
+__global__ void k_env_begin_step(int n_env, EnvCtl C) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_env) return;
+  bool go = C.status[e] == ST_ACTIVE && C.step[e] < C.nsteps[e];
+  C.stepping[e] = go;
+  C.iter[e] = go;
+  C.newton_it[e] = 0;
+}
+__global__ void k_env_iter_begin(int n_env, EnvCtl C) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_env) return;
+  C.constrained[e] = 0;
+  C.nanp[e] = 0;
+  C.bad[e] = 0;
+  C.pnorm_bits[e] = 0ull;
+  C.accept[e] = 0;
+}
+// after the Newton solve: failure on non-finite values, convergence test, CCD start value
+__global__ void k_env_converge(int n_env, EnvCtl C, double h, double tol) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_env) return;
+  if (!C.iter[e]) return;
+  C.stats[5 * e + STAT_NEWTON] += 1;
+  if (C.nanp[e] || !isfinite(C.E0[e]) || C.bad[e]) {
+    C.iter[e] = 0;
+    C.status[e] = ST_FAILED;
+    C.reason[e] = FAIL_NAN;
+    return;
+  }
+  double pn = bits_to_double(C.pnorm_bits[e]);
+  if (!C.constrained[e] && pn / h < tol) {
+    C.iter[e] = 0;  // converged: frozen for the rest of this step
+    return;
+  }
+  C.alpha_bits[e] = (unsigned long long)__double_as_longlong(1.0);
+}
+__global__ void k_env_ls_begin(int n_env, EnvCtl C) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_env) return;
+  C.ls[e] = C.iter[e];
+  C.halv[e] = 0;
+  if (C.iter[e]) C.alpha[e] = bits_to_double(C.alpha_bits[e]);
+  C.bad[e] = 0;
+}
+__global__ void k_env_ls_decide(int n_env, EnvCtl C, int max_ls) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_env) return;
+  if (!C.ls[e]) return;
+  bool ok = !C.bad[e] && (C.constrained[e] || C.Et[e] <= C.E0[e]);
+  C.bad[e] = 0;
+  if (ok) {
+    C.ls[e] = 0;
+    C.accept[e] = 1;
+    return;
+  }
+  int hv = C.halv[e] + 1;
+  C.halv[e] = hv;
+  if (hv > max_ls) {
+    C.ls[e] = 0;
+    C.iter[e] = 0;
+    C.status[e] = ST_FAILED;
+    C.reason[e] = FAIL_LINESEARCH;
+    return;
+  }
+  C.stats[5 * e + STAT_LS] += 1;
+  C.alpha[e] = C.alpha[e] / 2.0;
+}
+__global__ void k_env_newton_end(int n_env, EnvCtl C, int max_newton) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_env) return;
+  if (!C.iter[e]) return;
+  int it = C.newton_it[e] + 1;
+  C.newton_it[e] = it;
+  if (it >= max_newton) {
+    C.iter[e] = 0;
+    C.status[e] = ST_FAILED;
+    C.reason[e] = FAIL_NEWTON;
+  }
+}
+__global__ void k_env_end_step(int n_env, EnvCtl C) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_env) return;
+  if (!C.stepping[e] || C.status[e] != ST_ACTIVE) return;
+  int s = C.step[e] + 1;
+  C.step[e] = s;
+  C.stats[5 * e + STAT_STEPS] += 1;
+  if (s >= C.nsteps[e]) C.status[e] = ST_DONE;
+}
+__global__ void k_count_flags(int n, const uint8_t* __restrict__ f, int* __restrict__ out) {
+  __shared__ int sh[256];
+  int acc = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += f[i] ? 1 : 0;
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+__global__ void k_fill_u8(int n, uint8_t* a, uint8_t v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+__global__ void k_set_single(int n, uint8_t* a, int which) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (i == which) ? 1 : 0;
+}
+__global__ void k_add_vec(long n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) c[i] = __dadd_rn(a[i], b[i]);
+}
+
+// ---------------------------------------------------------------- primitive boxes
+// box = [min - r, max + r] per axis (r = dhat/2), or swept [min(x, x_end), max(x, x_end)].
+template <int NV>
+__global__ void k_prim_boxes(int n, const int* __restrict__ prim_pt, const double* __restrict__ ptx,
+                             const double* __restrict__ pte, double r, double* __restrict__ box) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = 0; k < 3; ++k) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int v = 0; v < NV; ++v) {
+      int pt = prim_pt[NV * i + v];
+      double a = ptx[3L * pt + k];
+      lo = fmin(lo, a);
+      hi = fmax(hi, a);
+      if (pte) {
+        double b = pte[3L * pt + k];
+        lo = fmin(lo, b);
+        hi = fmax(hi, b);
+      }
+    }
+    box[6L * i + k] = __dsub_rn(lo, r);
+    box[6L * i + 3 + k] = __dadd_rn(hi, r);
+  }
+}
+
+// ---------------------------------------------------------------- candidates
+struct PtInfo {
+  const int* body;     // affine body index (>= 0) or -1 - soft body id
+  const uint8_t* kin;
+};
+DEV bool excluded(const PtInfo& P, int a, int b, int c, int d) {
+  if (P.kin[a] && P.kin[b] && P.kin[c] && P.kin[d]) return true;
+  int ba = P.body[a];
+  return ba >= 0 && P.body[b] == ba && P.body[c] == ba && P.body[d] == ba;
+}
+
+enum { TRAV_COUNT = 0, TRAV_FILL = 1, TRAV_CCD = 2 };
+
+struct CandOut {
+  int* cnt;        // per query (count mode)
+  const int* off;  // per query (fill mode)
+  int* cj;         // candidate partner (fill mode)
+  int* overflow;
+};
+
+// point-triangle candidates: surface vertex q against the triangle tree of its env
+template <int MODE>
+__global__ void k_trav_pt(int n_sv, const int* __restrict__ sv_pt, const int* __restrict__ sv_env,
+                          const uint8_t* __restrict__ act, const double* __restrict__ ptx, const double* __restrict__ pte,
+                          double r, Tree T, const int* __restrict__ tri_pt, PtInfo P, CandOut O,
+                          const double* __restrict__ ptp, EnvCtl C) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_sv) return;
+  int e = sv_env[q];
+  if (!act[e]) {
+    if (MODE == TRAV_COUNT) O.cnt[q] = 0;
+    return;
+  }
+  int v = sv_pt[q];
+  double qb[6];
+  for (int k = 0; k < 3; ++k) {
+    double a = ptx[3L * v + k];
+    double lo = a, hi = a;
+    if (pte) {
+      lo = fmin(lo, pte[3L * v + k]);
+      hi = fmax(hi, pte[3L * v + k]);
+    }
+    qb[k] = __dsub_rn(lo, r);
+    qb[3 + k] = __dadd_rn(hi, r);
+  }
+  int count = 0;
+  int base = MODE == TRAV_FILL ? O.off[q] : 0;
+  double tmin = 1.0;
+  long iters = 0;
+  bool ok = bvh_visit(T, e, qb, [&](int j) {
+    int a = tri_pt[3 * j], b = tri_pt[3 * j + 1], c = tri_pt[3 * j + 2];
+    if (a == v || b == v || c == v) return;
+    if (excluded(P, v, a, b, c)) return;
+    if (MODE == TRAV_FILL) O.cj[base + count] = j;
+    if (MODE == TRAV_CCD) {
+      d3 X[4] = {ld3(ptx, v), ld3(ptx, a), ld3(ptx, b), ld3(ptx, c)};
+      d3 Pd[4] = {ld3(ptp, v), ld3(ptp, a), ld3(ptp, b), ld3(ptp, c)};
+      long it;
+      double t = accd(0, X, Pd, 0.1, 1.0, 1000000L, &it);
+      iters += it;
+      tmin = fmin(tmin, t);
+    }
+    ++count;
+  });
+  if (!ok) atomicOr(O.overflow, 1);
+  if (MODE == TRAV_COUNT) O.cnt[q] = count;
+  if (MODE == TRAV_FILL) {
+    // sort this query's partners ascending (insertion sort; short lists)
+    int* s = O.cj + base;
+    for (int i = 1; i < count; ++i) {
+      int key = s[i], k = i - 1;
+      while (k >= 0 && s[k] > key) {
+        s[k + 1] = s[k];
+        --k;
+      }
+      s[k + 1] = key;
+    }
+  }
+  if (MODE == TRAV_CCD && count > 0) {
+    atomic_min_pos(&C.alpha_bits[e], tmin);
+    atomicAdd((unsigned long long*)&C.stats[5 * e + STAT_ACCD], (unsigned long long)iters);
+  }
+}
+
+// edge-edge candidates: edge q against the edge tree of its env, partners j > q
+template <int MODE>
+__global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __restrict__ ed_env,
+                          const uint8_t* __restrict__ act, const double* __restrict__ edge_box, Tree T, PtInfo P,
+                          CandOut O, const double* __restrict__ ptx, const double* __restrict__ ptp, EnvCtl C) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_ed) return;
+  int e = ed_env[q];
+  if (!act[e]) {
+    if (MODE == TRAV_COUNT) O.cnt[q] = 0;
+    return;
+  }
+  int a0 = ed_pt[2 * q], a1 = ed_pt[2 * q + 1];
+  const double* qb = edge_box + 6L * q;
+  int count = 0;
+  int base = MODE == TRAV_FILL ? O.off[q] : 0;
+  double tmin = 1.0;
+  long iters = 0;
+  bool ok = bvh_visit(T, e, qb, [&](int j) {
+    if (j <= q) return;
+    int b0 = ed_pt[2 * j], b1 = ed_pt[2 * j + 1];
+    if (a0 == b0 || a0 == b1 || a1 == b0 || a1 == b1) return;
+    if (excluded(P, a0, a1, b0, b1)) return;
+    if (MODE == TRAV_FILL) O.cj[base + count] = j;
+    if (MODE == TRAV_CCD) {
+      d3 X[4] = {ld3(ptx, a0), ld3(ptx, a1), ld3(ptx, b0), ld3(ptx, b1)};
+      d3 Pd[4] = {ld3(ptp, a0), ld3(ptp, a1), ld3(ptp, b0), ld3(ptp, b1)};
+      long it;
+      double t = accd(1, X, Pd, 0.1, 1.0, 1000000L, &it);
+      iters += it;
+      tmin = fmin(tmin, t);
+    }
+    ++count;
+  });
+  if (!ok) atomicOr(O.overflow, 1);
+  if (MODE == TRAV_COUNT) O.cnt[q] = count;
+  if (MODE == TRAV_FILL) {
+    int* s = O.cj + base;
+    for (int i = 1; i < count; ++i) {
+      int key = s[i], k = i - 1;
+      while (k >= 0 && s[k] > key) {
+        s[k + 1] = s[k];
+        --k;
+      }
+      s[k + 1] = key;
+    }
+  }
+  if (MODE == TRAV_CCD && count > 0) {
+    atomic_min_pos(&C.alpha_bits[e], tmin);
+    atomicAdd((unsigned long long*)&C.stats[5 * e + STAT_ACCD], (unsigned long long)iters);
+  }
+}
+
+// candidate i (global over PT then EE) -> its query index (upper bound search in offsets)
+DEV int cand_query(const int* __restrict__ off, int nq, int i) {
+  int lo = 0, hi = nq;  // find q with off[q] <= i < off[q+1]
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// narrow phase: keep the candidates with d^2 < dhat^2 (flag), typed for the stencils
+__global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ off_pt, int n_sv, const int* __restrict__ off_ee,
+                         int n_ed, const int* __restrict__ cj, const int* __restrict__ sv_pt,
+                         const int* __restrict__ sv_env, const int* __restrict__ tri_pt, const int* __restrict__ ed_pt,
+                         const int* __restrict__ ed_env, const double* __restrict__ ptx, double dhat2,
+                         int* __restrict__ flag, ContactRec* __restrict__ tmp, const double* __restrict__ ed_rest2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pt + n_ee) return;
+  ContactRec c;
+  if (i < n_pt) {
+    int q = cand_query(off_pt, n_sv, i);
+    int j = cj[i];
+    c.kind = 0;
+    c.pts[0] = sv_pt[q];
+    c.pts[1] = tri_pt[3 * j];
+    c.pts[2] = tri_pt[3 * j + 1];
+    c.pts[3] = tri_pt[3 * j + 2];
+    c.env = sv_env[q];
+    c.eps_x = 0.0;
+  } else {
+    int k = i - n_pt;
+    int q = cand_query(off_ee, n_ed, k);
+    int j = cj[i];
+    c.kind = 1;
+    c.pts[0] = ed_pt[2 * q];
+    c.pts[1] = ed_pt[2 * q + 1];
+    c.pts[2] = ed_pt[2 * j];
+    c.pts[3] = ed_pt[2 * j + 1];
+    c.env = ed_env[q];
+    c.eps_x = 1e-3 * ed_rest2[q] * ed_rest2[j];
+  }
+  c.cand = i;
+  d3 X[4];
+  for (int k = 0; k < 4; ++k) X[k] = ld3(ptx, c.pts[k]);
+  int type;
+  double d2 = pair_d2(c.kind, X, &type);
+  c.type = type;
+  tmp[i] = c;
+  flag[i] = d2 < dhat2 ? 1 : 0;
+}
+__global__ void k_compact_contacts(int n, const int* __restrict__ flag, const int* __restrict__ off,
+                                   const ContactRec* __restrict__ tmp, ContactRec* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (flag[i]) out[off[i]] = tmp[i];
+}
+
+// lagged friction at x^t: lambda = kappa e |b'(d)|, closest-point coefficients and normal
+__global__ void k_friction_setup(int n_ct, const ContactRec* __restrict__ ct, const double* __restrict__ ptx,
+                                 const double* __restrict__ env_mu, double dhat, double kappa,
+                                 FrictionRec* __restrict__ fr) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_ct) return;
+  ContactRec c = ct[k];
+  d3 X[4];
+  for (int i = 0; i < 4; ++i) X[i] = ld3(ptx, c.pts[i]);
+  double d = sqrt(typed_d2(c.kind, c.type, X));
+  double b, b1, b2;
+  barrier3(d, dhat, &b, &b1, &b2);
+  double m = 1.0;
+  if (c.kind == 1) {
+    d3 n = cross(X[1] - X[0], X[3] - X[2]);
+    double cc = dot(n, n);
+    if (cc < c.eps_x) {
+      double r = cc / c.eps_x;
+      m = -r * r + 2.0 * r;
+    }
+  }
+  FrictionRec f;
+  for (int i = 0; i < 4; ++i) f.pts[i] = c.pts[i];
+  f.env = c.env;
+  f.pad = 0;
+  d3 n;
+  pair_closest(c.kind, X, f.c, &n);
+  f.n[0] = n.x;
+  f.n[1] = n.y;
+  f.n[2] = n.z;
+  f.mu_lambda = env_mu[c.env] * kappa * m * fabs(b1);
+  fr[k] = f;
+}
+
+// stencil table [contacts | friction]: points and env of every 4-point stencil
+__global__ void k_stencil_table(int n_ct, int n_fr, const ContactRec* __restrict__ ct, const FrictionRec* __restrict__ fr,
+                                int* __restrict__ st_pts, int* __restrict__ st_env) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_ct + n_fr) return;
+  const int* p;
+  int e;
+  if (s < n_ct) {
+    p = ct[s].pts;
+    e = ct[s].env;
+  } else {
+    p = fr[s - n_ct].pts;
+    e = fr[s - n_ct].env;
+  }
+  for (int k = 0; k < 4; ++k) st_pts[4 * s + k] = p[k];
+  st_env[s] = e;
+}
+
+// stencil -> node incidence entries: number per stencil, then (node key, stencil*4 + slot)
+__global__ void k_stencil_nent(int n_st, const int* __restrict__ st_pts, const int* __restrict__ st_env,
+                               const uint8_t* __restrict__ act, const int* __restrict__ pt_node, int* __restrict__ cnt) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_st) return;
+  int c = 0;
+  if (act[st_env[s]])
+    for (int a = 0; a < 4; ++a) c += pt_node[st_pts[4 * s + a]] >= 0 ? 1 : 4;
+  cnt[s] = c;
+}
+__global__ void k_stencil_emit(int n_st, const int* __restrict__ st_pts, const int* __restrict__ st_env,
+                               const uint8_t* __restrict__ act, const int* __restrict__ pt_node,
+                               const int* __restrict__ body_node, const int* __restrict__ off,
+                               unsigned long long* __restrict__ keys, unsigned* __restrict__ vals) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_st) return;
+  if (!act[st_env[s]]) return;
+  int o = off[s];
+  for (int a = 0; a < 4; ++a) {
+    int nd = pt_node[st_pts[4 * s + a]];
+    if (nd >= 0) {
+      keys[o] = (unsigned long long)nd;
+      vals[o++] = (unsigned)(4 * s + a);
+    } else {
+      int base = body_node[-1 - nd];
+      for (int k = 0; k < 4; ++k) {
+        keys[o] = (unsigned long long)(base + k);
+        vals[o++] = (unsigned)(4 * s + a);
+      }
+    }
+  }
+}
+__global__ void k_count_keys(int n, const unsigned long long* __restrict__ keys, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(&cnt[keys[i]], 1);
+}
+
+// ---------------------------------------------------------------- invariants
+DEV double orient3(d3 a, d3 b, d3 c, d3 d) { return dot(cross(b - a, c - a), d - a); }
+// segment s0s1 against triangle abc by signed volumes (proper or touching crossings)
+DEV bool seg_tri_cross(d3 s0, d3 s1, d3 a, d3 b, d3 c) {
+  double o0 = orient3(a, b, c, s0), o1 = orient3(a, b, c, s1);
+  if ((o0 > 0 && o1 > 0) || (o0 < 0 && o1 < 0)) return false;
+  if (o0 == 0 && o1 == 0) return false;  // coplanar: not counted as a crossing
+  double u = orient3(s0, s1, a, b), v = orient3(s0, s1, b, c), w = orient3(s0, s1, c, a);
+  return (u >= 0 && v >= 0 && w >= 0) || (u <= 0 && v <= 0 && w <= 0);
+}
+__global__ void k_intersections(int n_ed, const int* __restrict__ ed_pt, const int* __restrict__ ed_env,
+                                const uint8_t* __restrict__ act, const double* __restrict__ edge_box, Tree T,
+                                const int* __restrict__ tri_pt, PtInfo P, const double* __restrict__ ptx,
+                                unsigned long long* __restrict__ count, int* __restrict__ overflow) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_ed) return;
+  int e = ed_env[q];
+  if (!act[e]) return;
+  int a0 = ed_pt[2 * q], a1 = ed_pt[2 * q + 1];
+  unsigned long long n = 0;
+  bool ok = bvh_visit(T, e, edge_box + 6L * q, [&](int j) {
+    int a = tri_pt[3 * j], b = tri_pt[3 * j + 1], c = tri_pt[3 * j + 2];
+    if (a0 == a || a0 == b || a0 == c || a1 == a || a1 == b || a1 == c) return;
+    int ba = P.body[a0];
+    if (ba >= 0 && P.body[a1] == ba && P.body[a] == ba) return;
+    if (seg_tri_cross(ld3(ptx, a0), ld3(ptx, a1), ld3(ptx, a), ld3(ptx, b), ld3(ptx, c))) ++n;
+  });
+  if (!ok) atomicOr(overflow, 1);
+  if (n) atomicAdd(&count[e], n);
+}
+__global__ void k_inverted(int n_tets, const int4* __restrict__ tets, const int* __restrict__ tenv,
+                           const uint8_t* __restrict__ act, const double* __restrict__ q,
+                           unsigned long long* __restrict__ count) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tets) return;
+  int e = tenv[t];
+  if (!act[e]) return;
+  int4 T = tets[t];
+  d3 x0 = ld3(q, T.x);
+  double J = dot(cross(ld3(q, T.y) - x0, ld3(q, T.z) - x0), ld3(q, T.w) - x0);
+  if (!(J > 0.0)) atomicAdd(&count[e], 1ull);
+}

@@ -1,0 +1,221 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a B300).
+
+Bars: candidate lists bit-exact; energy and gradient at the same state within 1e-10 relative
+(FP64); trajectories within 1e-6 m; isolation of environments bit-exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_05020_b300 import ipc
+from paper_2503_05020_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-10
+TRAJ_TOL = 1e-6
+
+
+def oracle_state(params, env, steps):
+    o = O.OracleEnv(params, env)
+    if steps:
+        o.step(steps)
+    x, v = o.state()
+    return o, x, v
+
+
+def pads_pressed(env, shift):
+    """Initial DOFs of a pad scene with both soft pads moved `shift` towards the object."""
+    o = O.OracleEnv(S.scene_params(0.005), env)
+    x, v = o.state()
+    n0 = len(env["soft"][0]["verts"])
+    n1 = len(env["soft"][1]["verts"])
+    xs = x.copy()
+    xs[: 3 * n0].reshape(-1, 3)[:, 0] -= shift
+    xs[3 * n0: 3 * (n0 + n1)].reshape(-1, 3)[:, 0] += shift
+    return xs, v
+
+
+def test_candidates_and_contacts_bit_exact_cube():
+    p = S.scene_params(0.01)
+    env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+    o, x, v = oracle_state(p, env, 25)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    sc.set_state(eid, x, v, 25)
+    cg = sc.candidates(eid)
+    co = o.candidates(x)
+    assert len(co) > 100
+    assert cg.shape == co.shape and np.array_equal(cg, co)
+    kg = sc.contacts(eid)
+    ko, d2 = o.contacts(x)
+    assert len(ko) > 10
+    assert np.array_equal(kg[:, :3], ko[:, :3])
+
+
+def test_candidates_bit_exact_pads_and_hull():
+    p = S.scene_params(0.005)
+    env = S.pad_grasp_env(0)
+    x, v = pads_pressed(env, 1.2e-3)
+    o = O.OracleEnv(p, env)
+    o.set_state(x, v, 0)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    sc.set_state(eid, x, v, 0)
+    cg = sc.candidates(eid)
+    co = o.candidates(x)
+    assert len(co) > 1000
+    assert np.array_equal(cg, co)
+    kg = sc.contacts(eid)
+    ko, _ = o.contacts(x)
+    assert len(ko) > 0
+    assert np.array_equal(kg[:, :3], ko[:, :3])
+
+
+def _energy_parity(p, env, x, v, step, q):
+    o = O.OracleEnv(p, env)
+    o.set_state(x, v, step)
+    Eo, go = o.eval(q)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    sc.set_state(eid, x, v, step)
+    Eg, gg = sc.eval(eid, q)
+    assert abs(Eg - Eo) <= E_TOL * abs(Eo), (Eg, Eo)
+    assert np.abs(gg - go).max() <= E_TOL * np.abs(go).max(), np.abs(gg - go).max() / np.abs(go).max()
+    return Eo, go
+
+
+def test_energy_gradient_parity_cube_with_contact_and_friction():
+    p = S.scene_params(0.01)
+    env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+    o, x, v = oracle_state(p, env, 25)
+    rng = np.random.default_rng(5)
+    q = x + rng.normal(size=x.size) * 2e-6
+    q[3 * 125:] = x[3 * 125:]  # plates stay where they are
+    _energy_parity(p, env, x, v, 25, q)
+
+
+def test_energy_gradient_parity_pads_and_rigid_hull():
+    p = S.scene_params(0.005)
+    env = S.pad_grasp_env(1)
+    x, v = pads_pressed(env, 1.3e-3)
+    rng = np.random.default_rng(6)
+    q = x + rng.normal(size=x.size) * 1e-7
+    _energy_parity(p, env, x, v, 120, q)  # a lifting step: gravity on
+
+
+def test_energy_gradient_parity_rigid_on_incline():
+    p = S.scene_params(0.01)
+    env = S.resting_env("rigid", n_steps=30, mu=0.4, incline_deg=15)
+    o, x, v = oracle_state(p, env, 10)
+    q = x.copy()
+    q[:12] += np.random.default_rng(7).normal(size=12) * 1e-6
+    _energy_parity(p, env, x, v, 10, q)
+
+
+@pytest.mark.parametrize("body", ["tet", "rigid", "block"])
+def test_resting_trajectory_parity(body):
+    p = S.parity_params(S.scene_params(0.01))
+    env = S.resting_env(body, n_steps=40)
+    o = O.OracleEnv(p, env)
+    o.step(40)
+    xo, _ = o.state()
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    sc.step(40)
+    assert sc.status(eid)["status"] == "DONE"
+    assert np.abs(sc.dofs(eid) - xo).max() <= TRAJ_TOL
+
+
+def test_free_fall_closed_form_gpu():
+    h = 0.01
+    p = S.scene_params(h)
+    env = S.single_tet_env(n_steps=10)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    x0 = sc.dofs(eid)
+    sc.step(10)
+    x = sc.dofs(eid)
+    vz, z = 0.0, 0.0
+    for _ in range(10):
+        vz -= h * 9.8
+        z += h * vz
+    assert np.allclose((x - x0).reshape(-1, 3)[:, 2], z, rtol=1e-9)
+
+
+@pytest.mark.slow
+def test_cube_grasp_trajectory_parity_100_steps():
+    """The cube-squeeze grasp, 100 steps of close (gravity off) and lift (gravity on): GPU and
+    oracle trajectories agree within 1e-6 m at every 20th step, with no intersection."""
+    p = S.parity_params(S.scene_params(0.01))
+    env = S.cube_squeeze_env(0)
+    o = O.OracleEnv(p, env)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    for k in range(5):
+        o.step(20)
+        sc.step(20)
+        xo, _ = o.state()
+        xg = sc.dofs(eid)
+        err = np.abs(xg - xo).max()
+        assert err <= TRAJ_TOL, (k, err)
+    assert sc.status(eid)["status"] == "DONE"
+    inv = sc.invariants(eid)
+    assert inv == {"intersections": 0, "inverted": 0}
+    dz = xg[: 3 * 125].reshape(-1, 3)[:, 2].mean() - S.cube_squeeze_env(0)["soft"][0]["verts"][:, 2].mean()
+    assert dz > 0.009  # lifted with the plates (1 cm)
+
+
+def test_pad_grasp_steps_parity():
+    """Soft pads squeezing the rigid hull, a few steps with gravity on."""
+    p = S.parity_params(S.scene_params(0.005))
+    env = S.pad_grasp_env(2, n_steps=8, close_steps=4, squeeze=4e-3)
+    x, v = pads_pressed(env, 1.0e-3)
+    o = O.OracleEnv(p, env)
+    o.set_state(x, v, 0)
+    o.step(8)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    sc.set_state(eid, x, v, 0)
+    sc.step(8)
+    assert sc.status(eid)["status"] == o.status()["status"] == "DONE"
+    xo, _ = o.state()
+    assert np.abs(sc.dofs(eid) - xo).max() <= TRAJ_TOL
+
+
+def test_batched_env_is_bit_identical_to_alone_and_isolated_from_failures():
+    """Sec. III-A: envs evolve independently. An env stepped in a batch with an uneven partner
+    and a failing partner gives exactly the bits it gives alone; the failure stays local."""
+    p = S.scene_params(0.01)
+    cube = S.cube_squeeze_env(0, n_steps=12, close_steps=6)
+    alone = ipc.Scene(p)
+    a = alone.add_env(cube)
+    alone.step(12)
+    xa = alone.dofs(a)
+    batch = ipc.Scene(p)
+    b0 = batch.add_env(S.resting_env("rigid", n_steps=12))
+    b1 = batch.add_env(cube)
+    bad_env = S.resting_env("block", n_steps=12)
+    b2 = batch.add_env(bad_env)
+    xb2 = batch.dofs(b2)
+    vb2 = np.zeros_like(xb2)
+    vb2[0] = np.nan  # a non-finite state injected from the host
+    batch.set_state(b2, xb2, vb2, 0)
+    batch.step(12)
+    assert np.array_equal(batch.dofs(b1), xa)
+    assert batch.status(b1)["status"] == "DONE"
+    assert batch.status(b0)["status"] == "DONE"
+    st = batch.status(b2)
+    assert st["status"] == "FAILED" and st["reason"] == "non_finite"
+
+
+def test_newton_cap_fails_only_that_env():
+    p = S.scene_params(0.01)
+    p["max_newton"] = 1
+    sc = ipc.Scene(p)
+    a = sc.add_env(S.cube_squeeze_env(0, n_steps=30, close_steps=20))
+    b = sc.add_env(S.spinning_body_env(n_steps=3, omega=(0, 0, 0)))
+    sc.step(30)
+    sa, sb = sc.status(a), sc.status(b)
+    assert sa["status"] == "FAILED" and sa["reason"] == "newton_cap"
+    assert sb["status"] == "DONE"
