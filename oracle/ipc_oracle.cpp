@@ -1063,7 +1063,8 @@ static double evaluate(Env& e, const std::vector<double>& q, const std::vector<C
 static void target_dofs(const Env& e, std::vector<double>& tgt) {
   // kinematic DOF targets for the current step (non-kinematic entries are untouched copies of x)
   tgt = e.x;
-  const double* T = e.targets.data() + (size_t)e.step * e.n_handles * 12;
+  const int s = std::min(e.step, e.n_steps - 1);  // a finished env keeps its last schedule entry
+  const double* T = e.targets.data() + (size_t)s * e.n_handles * 12;
   for (int i = 0; i < e.n_soft_verts; ++i) {
     if (!e.vkin[i]) continue;
     const double* qb = T + 12 * e.vhandle[i];
@@ -1083,7 +1084,7 @@ static void step_setup(Env& e) {
   const double h = e.P.dt;
   e.xt = e.x;
   e.xtilde.assign(e.ndof, 0.0);
-  double hh = e.gravity[e.step] ? h * h : 0.0;
+  double hh = e.gravity[std::min(e.step, e.n_steps - 1)] ? h * h : 0.0;
   for (int i = 0; i < e.n_soft_verts; ++i)
     for (int k = 0; k < 3; ++k) e.xtilde[3 * i + k] = (e.x[3 * i + k] + h * e.v[3 * i + k]) + hh * e.P.gravity[k];
   for (const Body& B : e.bodies)
