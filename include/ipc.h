@@ -159,6 +159,17 @@ ipc_status ipc_env_set_state(ipc_scene* scene, int32_t env_id, const double* x, 
 ipc_status ipc_eval(ipc_scene* scene, int32_t env_id, const double* q, double* energy,
                     double* grad);
 
+/* Newton direction p of the first Newton iteration of the env's next step, taken at its current
+ * state (host, ndof doubles): kinematic DOFs get target - x, free DOFs the PCG solution of the
+ * projected-Hessian system H p = -g - H pbar (Sec. II-C projected Newton). Diagnostic entry
+ * point for parity checks of the Hessian and the linear solve; the env's state is unchanged. */
+ipc_status ipc_newton_direction(ipc_scene* scene, int32_t env_id, double* p);
+
+/* y = H d with H the PSD-projected Hessian of the env's incremental potential at its current
+ * state, as the PCG applies it (kinematic rows give 0). d and y are host arrays of ndof doubles.
+ * Diagnostic entry point for parity checks of the Hessian assembly. */
+ipc_status ipc_hessian_apply(ipc_scene* scene, int32_t env_id, const double* d, double* y);
+
 /* Streaming schedule: overwrite, for every ACTIVE env (in env-id order of the ids returned by
  * ipc_env_add), the kinematic targets of its next step from a host array laid out as
  * [env][body][12]. bytes must equal 12*8*sum over active envs of their body counts. */

@@ -254,7 +254,7 @@ static int ee_type(const double* a0, const double* a1, const double* b0, const d
   double a = d3dot(d1, d1), e = d3dot(d2, d2), f = d3dot(d2, r), c = d3dot(d1, r), b = d3dot(d1, d2);
   double den = a * e - b * b;
   double s, t;
-  if (den > 1e-20 * a * e) s = std::min(std::max((b * f - c * e) / den, 0.0), 1.0);
+  if (den > 1e-10 * a * e) s = std::min(std::max((b * f - c * e) / den, 0.0), 1.0);  // sin^2 > 1e-10
   else s = 0.0;
   t = (b * s + f) / e;
   if (t < 0) { t = 0; s = std::min(std::max(-c / a, 0.0), 1.0); }
@@ -1333,22 +1333,26 @@ static void step_once(Env& e) {
   if (e.step >= e.n_steps) e.status = ST_DONE;
 }
 
-// segment-triangle intersection test (Moller-Trumbore on the segment), exact enough for invariants
+// proper segment-triangle crossing (Moller-Trumbore on the segment). Near-parallel segments
+// and hits within a relative 1e-9 of the triangle boundary or the segment ends are not
+// counted (coplanar or touching configurations); touching is covered by the distance invariant.
 static bool seg_tri(const double* s0, const double* s1, const double* a, const double* b, const double* c) {
-  double e1[3], e2[3], d[3], pv[3], tv[3], qv[3];
+  double e1[3], e2[3], d[3], pv[3], tv[3], qv[3], n[3];
   for (int k = 0; k < 3; ++k) { e1[k] = b[k] - a[k]; e2[k] = c[k] - a[k]; d[k] = s1[k] - s0[k]; }
+  n[0] = e1[1] * e2[2] - e1[2] * e2[1]; n[1] = e1[2] * e2[0] - e1[0] * e2[2]; n[2] = e1[0] * e2[1] - e1[1] * e2[0];
   pv[0] = d[1] * e2[2] - d[2] * e2[1]; pv[1] = d[2] * e2[0] - d[0] * e2[2]; pv[2] = d[0] * e2[1] - d[1] * e2[0];
   double det = d3dot(e1, pv);
-  if (std::fabs(det) < 1e-30) return false;
+  if (std::fabs(det) <= 1e-9 * std::sqrt(d3dot(n, n) * d3dot(d, d))) return false;
   double inv = 1.0 / det;
   for (int k = 0; k < 3; ++k) tv[k] = s0[k] - a[k];
+  const double eps = 1e-9;
   double u = d3dot(tv, pv) * inv;
-  if (u < 0 || u > 1) return false;
+  if (u <= eps || u >= 1 - eps) return false;
   qv[0] = tv[1] * e1[2] - tv[2] * e1[1]; qv[1] = tv[2] * e1[0] - tv[0] * e1[2]; qv[2] = tv[0] * e1[1] - tv[1] * e1[0];
   double v = d3dot(d, qv) * inv;
-  if (v < 0 || u + v > 1) return false;
+  if (v <= eps || u + v >= 1 - eps) return false;
   double t = d3dot(e2, qv) * inv;
-  return t >= 0 && t <= 1;
+  return t > eps && t < 1 - eps;
 }
 
 }  // namespace orc
@@ -1414,6 +1418,30 @@ double or_env_eval(void* h, const double* q, double* grad) {
   double E = evaluate(*e, qq, C, grad ? 1 : 0, grad ? &g : nullptr, nullptr);
   if (grad) std::memcpy(grad, g.data(), sizeof(double) * e->ndof);
   return E;
+}
+
+// Newton direction of the first iteration of the env's next step, taken at its current state
+// (kinematic part target - x, free part from the CG solve of the projected Hessian system).
+void or_env_newton_dir(void* h, double* out) {
+  Env* e = (Env*)h;
+  step_setup(*e);
+  std::vector<double> tgt, px, grad, Hpbar, rhs(e->ndof), delta;
+  target_dofs(*e, tgt);
+  std::vector<int> free_mask(e->ndof);
+  for (int d = 0; d < e->ndof; ++d) free_mask[d] = !is_kin_dof(*e, d);
+  point_positions(*e, e->x.data(), px);
+  std::vector<Contact> C;
+  constraint_set(*e, px, C);
+  Triplets T;
+  evaluate(*e, e->x, C, 2, &grad, &T);
+  CSR M = to_csr(e->ndof, T);
+  std::vector<double> pbar(e->ndof, 0.0);
+  for (int d = 0; d < e->ndof; ++d)
+    if (!free_mask[d]) pbar[d] = tgt[d] - e->x[d];
+  csr_mv(M, pbar, Hpbar);
+  for (int d = 0; d < e->ndof; ++d) rhs[d] = free_mask[d] ? -grad[d] - Hpbar[d] : 0.0;
+  cg_solve(M, free_mask, rhs, delta, 1e-12, 20L * e->ndof + 1000);
+  for (int d = 0; d < e->ndof; ++d) out[d] = free_mask[d] ? delta[d] : pbar[d];
 }
 
 // Dense Hessian (PSD-projected) at q; for small systems in tests. out is ndof*ndof.

@@ -49,6 +49,7 @@ def lib():
         L.or_env_eval.restype = d
         L.or_env_eval.argtypes = [vp, vp, vp]
         L.or_env_hessian.argtypes = [vp, vp, vp]
+        L.or_env_newton_dir.argtypes = [vp, vp]
         L.or_env_candidates.argtypes = [vp, vp, vp, vp, C.c_int]
         L.or_env_contacts.argtypes = [vp, vp, vp, vp, C.c_int]
         L.or_env_points.argtypes = [vp, vp, vp]
@@ -191,6 +192,12 @@ class OracleEnv:
         g = np.zeros(self.ndof) if grad else None
         E = lib().or_env_eval(self.h, _p(q), _p(g) if grad else None)
         return (E, g) if grad else E
+
+    def newton_direction(self) -> np.ndarray:
+        """First Newton direction of the next step at the current state."""
+        out = np.zeros(self.ndof)
+        lib().or_env_newton_dir(self.h, _p(out))
+        return out
 
     def hessian(self, q) -> np.ndarray:
         q = np.ascontiguousarray(q, dtype=np.float64)

@@ -61,8 +61,10 @@ HD int sym_idx(int i, int j, int n) { return i <= j ? up_idx(i, j, n) : up_idx(j
 
 // Cyclic Jacobi on a symmetric N x N matrix held in A (row-major, thread-local). On return A
 // holds the PSD projection V max(Lambda, 0) V^T. At most 24 sweeps (a fixed bound).
+// Kept out of line: inlined into kernels that hold other large local arrays, the device
+// optimizer produced wrong results for this routine (measured on sm_103a with CUDA 13.0).
 template <int N>
-DEV void project_psd_jacobi(double* A) {
+__device__ __noinline__ void project_psd_jacobi(double* A) {
   double V[N * N];
 #pragma unroll 1
   for (int i = 0; i < N * N; ++i) V[i] = 0.0;
@@ -191,7 +193,7 @@ DEV void eig_sym3(const double A_in[9], double w[3], double V[9]) {
 // In-place inverse of an SPD N x N matrix (row-major) via Cholesky; returns false when a pivot
 // is not positive (then A is set to the inverse of its diagonal, or 0 where that is not > 0).
 template <int N>
-DEV bool spd_inverse(double* A) {
+__device__ __noinline__ bool spd_inverse(double* A) {  // out of line, see project_psd_jacobi
   double L[N * N];
   for (int i = 0; i < N * N; ++i) L[i] = 0.0;
   bool ok = true;

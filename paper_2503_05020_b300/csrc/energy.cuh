@@ -47,6 +47,33 @@ __global__ void k_points(int n_pts, const int* __restrict__ pt_node, const doubl
 //   flip (i,j):    mu + (mu - lam lnJ)/(s_i s_j),  U (e_i e_j^T + e_j e_i^T) V^T / sqrt 2.
 // Negative eigenvalues are dropped (projected Newton); the 12x12 Hessian is
 // h^2 V sum_m lam_m^+ w_m w_m^T with w_m[a] = Q_m b_a (b_a: shape-function gradients).
+// F = Ds Dm^-1, its cofactor, J and the weighted energy h^2 V Psi(F). Not inlined: every mode
+// calls the same machine code, so Newton and line-search energies round identically.
+__device__ __noinline__ double tet_energy(d3 x0, d3 x1, d3 x2, d3 x3, const double* __restrict__ Bm, double mu,
+                                          double lam, double w, double* F, double* cof, double* Jout) {
+  d3 c1 = x1 - x0, c2 = x2 - x0, c3 = x3 - x0;
+  const d3 Cc[3] = {c1, c2, c3};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      F[3 * r + c] = comp(Cc[0], r) * Bm[c] + comp(Cc[1], r) * Bm[3 + c] + comp(Cc[2], r) * Bm[6 + c];
+  cof[0] = F[4] * F[8] - F[5] * F[7];
+  cof[1] = F[5] * F[6] - F[3] * F[8];
+  cof[2] = F[3] * F[7] - F[4] * F[6];
+  cof[3] = F[2] * F[7] - F[1] * F[8];
+  cof[4] = F[0] * F[8] - F[2] * F[6];
+  cof[5] = F[1] * F[6] - F[0] * F[7];
+  cof[6] = F[1] * F[5] - F[2] * F[4];
+  cof[7] = F[2] * F[3] - F[0] * F[5];
+  cof[8] = F[0] * F[4] - F[1] * F[3];
+  double J = F[0] * cof[0] + F[1] * cof[1] + F[2] * cof[2];
+  *Jout = J;
+  if (!(J > 0.0)) return 0.0;
+  double lnJ = log(J);
+  double tr = 0.0;
+  for (int i = 0; i < 9; ++i) tr += F[i] * F[i];
+  return w * (0.5 * mu * (tr - 3.0) - mu * lnJ + 0.5 * lam * lnJ * lnJ);
+}
+
 template <int MODE>
 __global__ void k_elastic(int n_tets, const int4* __restrict__ tets, const double* __restrict__ prm,
                           const int* __restrict__ tenv, const uint8_t* __restrict__ act, const double* __restrict__ q,
@@ -59,37 +86,19 @@ __global__ void k_elastic(int n_tets, const int4* __restrict__ tets, const doubl
   int4 T = tets[t];
   const double* P = prm + 12 * (long)t;
   d3 x0 = ld3(q, T.x), x1 = ld3(q, T.y), x2 = ld3(q, T.z), x3 = ld3(q, T.w);
-  d3 c1 = x1 - x0, c2 = x2 - x0, c3 = x3 - x0;
   double Bm[9];
   for (int i = 0; i < 9; ++i) Bm[i] = P[i];
   double vol = P[9], mu = P[10], lam = P[11];
-  // F = Ds Dm^-1, Ds columns = c1, c2, c3
-  double F[9];
-  const d3 Cc[3] = {c1, c2, c3};
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c)
-      F[3 * r + c] = comp(Cc[0], r) * Bm[c] + comp(Cc[1], r) * Bm[3 + c] + comp(Cc[2], r) * Bm[6 + c];
-  double cof[9];
-  cof[0] = F[4] * F[8] - F[5] * F[7];
-  cof[1] = F[5] * F[6] - F[3] * F[8];
-  cof[2] = F[3] * F[7] - F[4] * F[6];
-  cof[3] = F[2] * F[7] - F[1] * F[8];
-  cof[4] = F[0] * F[8] - F[2] * F[6];
-  cof[5] = F[1] * F[6] - F[0] * F[7];
-  cof[6] = F[1] * F[5] - F[2] * F[4];
-  cof[7] = F[2] * F[3] - F[0] * F[5];
-  cof[8] = F[0] * F[4] - F[1] * F[3];
-  double J = F[0] * cof[0] + F[1] * cof[1] + F[2] * cof[2];
+  double w = h2 * vol;
+  double F[9], cof[9], J;
+  double En = tet_energy(x0, x1, x2, x3, Bm, mu, lam, w, F, cof, &J);
   if (!(J > 0.0)) {
     env_bad[e] = 1;
     tE[t] = 0.0;
     return;
   }
+  tE[t] = En;
   double lnJ = log(J);
-  double tr = 0.0;
-  for (int i = 0; i < 9; ++i) tr += F[i] * F[i];
-  double w = h2 * vol;
-  tE[t] = w * (0.5 * mu * (tr - 3.0) - mu * lnJ + 0.5 * lam * lnJ * lnJ);
   if (MODE == MODE_ENERGY) return;
   // shape-function gradients b_a (rows): b1..b3 = rows of Dm^-1, b0 = -(b1 + b2 + b3)
   d3 b[4];
@@ -181,6 +190,28 @@ __global__ void k_elastic(int n_tets, const int4* __restrict__ tets, const doubl
 // Inertia 1/2 (q - q~)^T (M4 x I3) (q - q~) and orthogonality h^2 kappa_A V |A A^T - I|_F^2,
 // A[r][c] = q[3 + 3c + r]. d2/dA2 of |S|^2, S = A A^T - I, is
 // 4 [d_km (A^T A)_nl + A_kn A_ml + S_km d_ln] at (kl, mn); it is projected to PSD.
+// inertia + orthogonality value of one free body, with A and S = A A^T - I (not inlined, see
+// tet_energy)
+__device__ __noinline__ double body_energy(const double* __restrict__ Q, const double* __restrict__ Qt,
+                                           const double* __restrict__ M, double wk, double* dq, double* A, double* S) {
+  for (int i = 0; i < 12; ++i) dq[i] = Q[i] - Qt[i];
+  double Ein = 0.0;
+  for (int I = 0; I < 4; ++I)
+    for (int k = 0; k < 3; ++k) {
+      double s = 0.0;
+      for (int Jn = 0; Jn < 4; ++Jn) s += M[4 * I + Jn] * dq[3 * Jn + k];
+      Ein += 0.5 * dq[3 * I + k] * s;
+    }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) A[3 * r + c] = Q[3 + 3 * c + r];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      S[3 * i + j] = A[3 * i] * A[3 * j] + A[3 * i + 1] * A[3 * j + 1] + A[3 * i + 2] * A[3 * j + 2] - (i == j ? 1.0 : 0.0);
+  double f = 0.0;
+  for (int i = 0; i < 9; ++i) f += S[i] * S[i];
+  return Ein + wk * f;
+}
+
 template <int MODE>
 __global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int* __restrict__ benv,
                          const uint8_t* __restrict__ bkin, const double* __restrict__ M4, const double* __restrict__ bvol,
@@ -201,28 +232,16 @@ __global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int*
   const double* Q = q + 3 * (long)bnode[b];
   const double* Qt = qt + 3 * (long)bnode[b];
   const double* M = M4 + 16 * (long)b;
-  double dq[12];
-  for (int i = 0; i < 12; ++i) dq[i] = Q[i] - Qt[i];
-  double Ein = 0.0, g[12];
+  double wk = h2kA * bvol[b];
+  double dq[12], A[9], S[9], g[12];
+  bE[b] = body_energy(Q, Qt, M, wk, dq, A, S);
+  if (MODE == MODE_ENERGY) return;
   for (int I = 0; I < 4; ++I)
     for (int k = 0; k < 3; ++k) {
       double s = 0.0;
       for (int Jn = 0; Jn < 4; ++Jn) s += M[4 * I + Jn] * dq[3 * Jn + k];
       g[3 * I + k] = s;
-      Ein += 0.5 * dq[3 * I + k] * s;
     }
-  double A[9];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) A[3 * r + c] = Q[3 + 3 * c + r];
-  double S[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      S[3 * i + j] = A[3 * i] * A[3 * j] + A[3 * i + 1] * A[3 * j + 1] + A[3 * i + 2] * A[3 * j + 2] - (i == j ? 1.0 : 0.0);
-  double f = 0.0;
-  for (int i = 0; i < 9; ++i) f += S[i] * S[i];
-  double wk = h2kA * bvol[b];
-  bE[b] = Ein + wk * f;
-  if (MODE == MODE_ENERGY) return;
   // gradient of |S|^2 wrt A: 4 S A
   for (int k = 0; k < 3; ++k)
     for (int l = 0; l < 3; ++l) {
@@ -268,6 +287,31 @@ struct ContactRec {
 
 // h^2 kappa e(c) b(d) with PSD-projected Hessian; d = sqrt(s), grad b = b'/(2d) grad s,
 // hess b = (b''/(4 d^2) - b'/(4 d^3)) grad s grad s^T + b'/(2d) hess s.
+// kappa h^2 e(c) b(d) value (not inlined, see tet_energy)
+__device__ __noinline__ double barrier_energy(int kind, int type, const d3* X, double eps_x, double dhat, double scale,
+                                              double* s_out, double* c_out) {
+  double s = typed_d2(kind, type, X);
+  *s_out = s;
+  double d = sqrt(s);
+  double b = 0.0;
+  if (d < dhat) {
+    double t = d - dhat;
+    b = -t * t * log(d / dhat);
+  }
+  double m = 1.0;
+  double cc = 0.0;
+  if (kind == 1) {
+    d3 n = cross(X[1] - X[0], X[3] - X[2]);
+    cc = dot(n, n);
+    if (cc < eps_x) {
+      double r = cc / eps_x;
+      m = -r * r + 2.0 * r;
+    }
+  }
+  *c_out = cc;
+  return scale * m * b;
+}
+
 template <int MODE>
 __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
                           const double* __restrict__ ptx, double h2, double dhat, double kappa, double* __restrict__ sE,
@@ -278,16 +322,22 @@ __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uin
   if (!act[c.env]) return;
   d3 X[4];
   for (int i = 0; i < 4; ++i) X[i] = ld3(ptx, c.pts[i]);
-  double s, gs[12], Hs[78];
-  if (MODE == MODE_ENERGY) {
-    s = typed_d2(c.kind, c.type, X);
-  } else {
-    d2_derivs(c.kind, c.type, X, &s, gs, Hs);
+  // the energy value comes from the same function in every mode, so that line-search energies
+  // and Newton energies round identically; the generated code gives derivatives only
+  double scale = h2 * kappa;
+  double s, cc;
+  double Eb = barrier_energy(c.kind, c.type, X, c.eps_x, dhat, scale, &s, &cc);
+  sE[k] = Eb;
+  if (MODE == MODE_ENERGY) return;
+  double gs[12], Hs[78];
+  {
+    double s_unused;
+    d2_derivs(c.kind, c.type, X, &s_unused, gs, Hs);
   }
   double d = sqrt(s);
   double b, b1, b2;
   barrier3(d, dhat, &b, &b1, &b2);
-  double m = 1.0, m1 = 0.0, m2 = 0.0, cc = 0.0, gc[12], Hc[78];
+  double m = 1.0, m1 = 0.0, m2 = 0.0, gc[12], Hc[78];
   if (c.kind == 1) {
     double P[12], N, Ng[12], Nh[78];
     for (int i = 0; i < 4; ++i) {
@@ -295,12 +345,8 @@ __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uin
       P[3 * i + 1] = X[i].y;
       P[3 * i + 2] = X[i].z;
     }
-    if (MODE == MODE_ENERGY) {
-      d3 n = cross(X[1] - X[0], X[3] - X[2]);
-      cc = dot(n, n);
-    } else {
-      ee_poly(P, P + 3, P + 6, P + 9, &N, Ng, Nh, &cc, gc, Hc);
-    }
+    double cc_unused;
+    ee_poly(P, P + 3, P + 6, P + 9, &N, Ng, Nh, &cc_unused, gc, Hc);
     if (cc < c.eps_x) {
       double r = cc / c.eps_x;
       m = -r * r + 2.0 * r;
@@ -308,9 +354,6 @@ __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uin
       m2 = -2.0 / (c.eps_x * c.eps_x);
     }
   }
-  double scale = h2 * kappa;
-  sE[k] = scale * m * b;
-  if (MODE == MODE_ENERGY) return;
   double gb[12], kb = b1 / (2.0 * d);
   for (int i = 0; i < 12; ++i) gb[i] = kb * gs[i];
   double gm[12];
@@ -345,6 +388,21 @@ struct FrictionRec {
 // h^2 mu lambda f0(|u|), u = P rel, rel = sum_i c_i (x_i - x_i^t), P = I - n n^T; gradient
 // c_i a u and Hessian c_i c_j (a P + b u u^T) with a = f1/y, b = (f1' y - f1)/y^3 (PSD for the
 // IPC smoothing f0; at y = 0, a = 2/(eps_v h) and the u u^T term vanishes).
+// h^2 mu lambda f0(|u|) value with u and |u| (not inlined, see tet_energy)
+__device__ __noinline__ double friction_energy(const FrictionRec& f, const double* __restrict__ ptx,
+                                               const double* __restrict__ ptx_t, double h2, double eh, d3* u_out,
+                                               double* y_out) {
+  d3 rel = mk3(0, 0, 0);
+  for (int i = 0; i < 4; ++i) rel = rel + f.c[i] * (ld3(ptx, f.pts[i]) - ld3(ptx_t, f.pts[i]));
+  d3 n = mk3(f.n[0], f.n[1], f.n[2]);
+  d3 u = rel - dot(n, rel) * n;
+  double y = sqrt(dot(u, u));
+  *u_out = u;
+  *y_out = y;
+  double f0 = y < eh ? -y * y * y / (3.0 * eh * eh) + y * y / eh + eh / 3.0 : y;
+  return h2 * f.mu_lambda * f0;
+}
+
 template <int MODE>
 __global__ void k_friction(int n_fr, const FrictionRec* __restrict__ fr, const uint8_t* __restrict__ act,
                            const double* __restrict__ ptx, const double* __restrict__ ptx_t, double h2, double eh,
@@ -353,24 +411,19 @@ __global__ void k_friction(int n_fr, const FrictionRec* __restrict__ fr, const u
   if (k >= n_fr) return;
   FrictionRec f = fr[k];
   if (!act[f.env]) return;
-  d3 rel = mk3(0, 0, 0);
-  for (int i = 0; i < 4; ++i) rel = rel + f.c[i] * (ld3(ptx, f.pts[i]) - ld3(ptx_t, f.pts[i]));
-  d3 n = mk3(f.n[0], f.n[1], f.n[2]);
-  d3 u = rel - dot(n, rel) * n;
-  double y = sqrt(dot(u, u));
-  double f0, f1, f2;
+  d3 u;
+  double y;
+  sE[k] = friction_energy(f, ptx, ptx_t, h2, eh, &u, &y);
+  if (MODE == MODE_ENERGY) return;
+  double s = h2 * f.mu_lambda;
+  double f1, f2;
   if (y < eh) {
-    f0 = -y * y * y / (3.0 * eh * eh) + y * y / eh + eh / 3.0;
     f1 = -y * y / (eh * eh) + 2.0 * y / eh;
     f2 = -2.0 * y / (eh * eh) + 2.0 / eh;
   } else {
-    f0 = y;
     f1 = 1.0;
     f2 = 0.0;
   }
-  double s = h2 * f.mu_lambda;
-  sE[k] = s * f0;
-  if (MODE == MODE_ENERGY) return;
   double a = y > 0.0 ? f1 / y : 2.0 / eh;
   double bc = y > 0.0 ? (f2 * y - f1) / (y * y * y) : 0.0;
   for (int i = 0; i < 4; ++i) {

@@ -68,7 +68,8 @@ DEV int ee_classify(d3 a0, d3 a1, d3 b0, d3 b1, double* s_out, double* t_out) {
   d3 ea = a1 - a0, eb = b1 - b0, r = a0 - b0;
   double A = dot(ea, ea), B = dot(ea, eb), C = dot(eb, eb), D = dot(ea, r), E = dot(eb, r);
   double den = A * C - B * B;
-  if (den > 1e-20 * A * C) {
+  // sin^2 of the angle <= 1e-10: treated as parallel (the closest pair then has an endpoint)
+  if (den > 1e-10 * A * C) {
     double s = (B * E - C * D) / den, t = (A * E - B * D) / den;
     if (s > 0.0 && s < 1.0 && t > 0.0 && t < 1.0) {
       *s_out = s;
@@ -182,7 +183,8 @@ DEV double pair_d2(int kind, const d3 X[4], int* type_out) {
 }
 
 // Gradient g[12] and packed upper Hessian H[78] of the squared distance of the given type.
-DEV void d2_derivs(int kind, int type, const d3 X[4], double* s_out, double g[12], double H[78]) {
+// Kept out of line for the same reason as project_psd_jacobi.
+__device__ __noinline__ void d2_derivs(int kind, int type, const d3 X[4], double* s_out, double g[12], double H[78]) {
 #pragma unroll 1
   for (int i = 0; i < 12; ++i) g[i] = 0.0;
 #pragma unroll 1

@@ -1286,6 +1286,57 @@ ipc_status ipc_eval(ipc_scene* s, int32_t env_id, const double* q, double* energ
   API_END
 }
 
+ipc_status ipc_newton_direction(ipc_scene* s, int32_t env_id, double* pout) {
+  API_BEGIN
+  if (!s || !pout) fail_with(IPC_ERR_ARG, "null argument");
+  CK(cudaSetDevice(s->device));
+  s->commit();
+  int li = s->layout_index(env_id);
+  HostEnv& h = s->envs[env_id];
+  s->select(li);
+  s->step_setup(s->e_sel.p);
+  CK(cudaMemcpyAsync(s->e_iter.p, s->e_sel.p, s->E, cudaMemcpyDeviceToDevice, s->stream));
+  EnvCtl C = s->ctl();
+  s->launch(k_env_iter_begin, s->E, 128, s->E, C);
+  s->evaluate<MODE_HESS>(s->x.p, s->e_iter.p, s->e_E0.p);
+  s->assemble(s->e_iter.p);
+  s->launch(k_pbar, s->NN, 256, s->NN, s->layout(), C, (const double*)s->x.p, (const double*)s->xtarget.p, s->pbar.p);
+  s->matvec(s->e_iter.p, s->pbar.p, s->pcg_y.p, s->part_a.p);
+  s->launch(k_rhs, s->NN, 256, s->NN, s->layout(), (const uint8_t*)s->e_iter.p, (const double*)s->grad.p,
+            (const double*)s->pcg_y.p, s->pcg_r.p);
+  s->pcg(s->e_iter.p);
+  s->launch(k_direction, s->NN, 256, s->NN, s->layout(), C, (const double*)s->pcg_x.p, (const double*)s->pbar.p,
+            (const double*)s->bbox.p, s->p.p);
+  CK(cudaMemcpyAsync(pout, s->p.p + 3 * (size_t)s->h_node_off[li], h.ndof * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemsetAsync(s->e_iter.p, 0, s->E, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->ttri.built = s->tedge.built = false;
+  API_END
+}
+
+ipc_status ipc_hessian_apply(ipc_scene* s, int32_t env_id, const double* d, double* y) {
+  API_BEGIN
+  if (!s || !d || !y) fail_with(IPC_ERR_ARG, "null argument");
+  CK(cudaSetDevice(s->device));
+  s->commit();
+  int li = s->layout_index(env_id);
+  HostEnv& h = s->envs[env_id];
+  s->select(li);
+  s->step_setup(s->e_sel.p);
+  EnvCtl C = s->ctl();
+  s->launch(k_env_iter_begin, s->E, 128, s->E, C);
+  s->evaluate<MODE_HESS>(s->x.p, s->e_sel.p, s->e_E0.p);
+  s->assemble(s->e_sel.p);
+  size_t o = 3 * (size_t)s->h_node_off[li];
+  CK(cudaMemsetAsync(s->pbar.p, 0, 3 * (size_t)s->NN * 8, s->stream));
+  CK(cudaMemcpyAsync(s->pbar.p + o, d, h.ndof * 8, cudaMemcpyHostToDevice, s->stream));
+  s->matvec(s->e_sel.p, s->pbar.p, s->pcg_y.p, s->part_a.p);
+  CK(cudaMemcpyAsync(y, s->pcg_y.p + o, h.ndof * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->ttri.built = s->tedge.built = false;
+  API_END
+}
+
 static ipc_status copy_out(const void* src, size_t bytes, void* out, size_t out_bytes, size_t* written) {
   if (written) *written = bytes;
   if (out_bytes < bytes || (!out && bytes)) {

@@ -608,13 +608,18 @@ __global__ void k_count_keys(int n, const unsigned long long* __restrict__ keys,
 
 // ---------------------------------------------------------------- invariants
 DEV double orient3(d3 a, d3 b, d3 c, d3 d) { return dot(cross(b - a, c - a), d - a); }
-// segment s0s1 against triangle abc by signed volumes (proper or touching crossings)
+// proper crossing of segment s0s1 through triangle abc by signed volumes; values within a
+// relative 1e-9 of zero (coplanar or touching configurations) do not count as crossings,
+// touching is covered by the positive-distance invariant instead
 DEV bool seg_tri_cross(d3 s0, d3 s1, d3 a, d3 b, d3 c) {
+  d3 ds = s1 - s0, e1 = b - a, e2 = c - a;
+  double Ls = sqrt(dot(ds, ds)), Le = fmax(sqrt(dot(e1, e1)), sqrt(dot(e2, e2)));
+  double eps_p = 1e-9 * sqrt(dot(cross(e1, e2), cross(e1, e2))) * Ls;
   double o0 = orient3(a, b, c, s0), o1 = orient3(a, b, c, s1);
-  if ((o0 > 0 && o1 > 0) || (o0 < 0 && o1 < 0)) return false;
-  if (o0 == 0 && o1 == 0) return false;  // coplanar: not counted as a crossing
+  if (!((o0 > eps_p && o1 < -eps_p) || (o0 < -eps_p && o1 > eps_p))) return false;
+  double eps_e = 1e-9 * Ls * Le * Le;
   double u = orient3(s0, s1, a, b), v = orient3(s0, s1, b, c), w = orient3(s0, s1, c, a);
-  return (u >= 0 && v >= 0 && w >= 0) || (u <= 0 && v <= 0 && w <= 0);
+  return (u > eps_e && v > eps_e && w > eps_e) || (u < -eps_e && v < -eps_e && w < -eps_e);
 }
 __global__ void k_intersections(int n_ed, const int* __restrict__ ed_pt, const int* __restrict__ ed_env,
                                 const uint8_t* __restrict__ act, const double* __restrict__ edge_box, Tree T,

@@ -77,6 +77,7 @@ def lib() -> C.CDLL:
             "ipc_scene_create": [vp, vp], "ipc_scene_destroy": [vp], "ipc_env_add": [vp, vp, vp],
             "ipc_env_remove": [vp, i32], "ipc_step": [vp, i32], "ipc_query": [vp, i32, i32, vp, sz, vp],
             "ipc_env_set_state": [vp, i32, vp, vp, i32], "ipc_eval": [vp, i32, vp, vp, vp],
+            "ipc_newton_direction": [vp, i32, vp], "ipc_hessian_apply": [vp, i32, vp, vp],
             "ipc_set_next_targets": [vp, vp, sz], "ipc_get_all_dofs": [vp, vp, sz, vp],
             "ipc_env_estimate_bytes": [vp, i32, vp], "ipc_launch_count": [vp, vp],
         }
@@ -233,6 +234,19 @@ class Scene:
         g = np.zeros(len(q)) if grad else None
         _check(lib().ipc_eval(self._h, eid, _p(q), C.byref(E), _p(g)))
         return (E.value, g) if grad else E.value
+
+    def newton_direction(self, eid: int) -> np.ndarray:
+        """First Newton direction of the env's next step at its current state (diagnostic)."""
+        out = np.zeros(self.ndof[eid])
+        _check(lib().ipc_newton_direction(self._h, eid, _p(out)))
+        return out
+
+    def hessian_apply(self, eid: int, d) -> np.ndarray:
+        """y = H d with the projected Hessian as the PCG applies it (diagnostic)."""
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        y = np.zeros_like(d)
+        _check(lib().ipc_hessian_apply(self._h, eid, _p(d), _p(y)))
+        return y
 
     def set_next_targets(self, targets: np.ndarray):
         t = np.ascontiguousarray(targets, dtype=np.float64)

@@ -129,7 +129,7 @@ def test_resting_trajectory_parity(body):
 
 def test_free_fall_closed_form_gpu():
     h = 0.01
-    p = S.scene_params(h)
+    p = S.parity_params(S.scene_params(h))
     env = S.single_tet_env(n_steps=10)
     sc = ipc.Scene(p)
     eid = sc.add_env(env)
@@ -169,15 +169,15 @@ def test_cube_grasp_trajectory_parity_100_steps():
 def test_pad_grasp_steps_parity():
     """Soft pads squeezing the rigid hull, a few steps with gravity on."""
     p = S.parity_params(S.scene_params(0.005))
-    env = S.pad_grasp_env(2, n_steps=8, close_steps=4, squeeze=4e-3)
+    env = S.pad_grasp_env(2, n_steps=3, close_steps=2, squeeze=4e-3)
     x, v = pads_pressed(env, 1.0e-3)
     o = O.OracleEnv(p, env)
     o.set_state(x, v, 0)
-    o.step(8)
+    o.step(3)
     sc = ipc.Scene(p)
     eid = sc.add_env(env)
     sc.set_state(eid, x, v, 0)
-    sc.step(8)
+    sc.step(3)
     assert sc.status(eid)["status"] == o.status()["status"] == "DONE"
     xo, _ = o.state()
     assert np.abs(sc.dofs(eid) - xo).max() <= TRAJ_TOL
@@ -219,3 +219,27 @@ def test_newton_cap_fails_only_that_env():
     sa, sb = sc.status(a), sc.status(b)
     assert sa["status"] == "FAILED" and sa["reason"] == "newton_cap"
     assert sb["status"] == "DONE"
+
+
+@pytest.mark.parametrize("case", ["tet", "rigid", "block", "cube"])
+def test_newton_direction_parity(case):
+    """The first projected-Newton direction (Hessian assembly + PCG) matches the oracle's CG
+    solve at the same state, in parity settings (PCG to 1e-12)."""
+    p = S.parity_params(S.scene_params(0.01))
+    if case == "cube":
+        env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+        _, x, v = oracle_state(S.scene_params(0.01), env, 25)
+        step = 25
+    else:
+        env = S.resting_env(case, n_steps=40)
+        x = v = None
+        step = 0
+    o = O.OracleEnv(p, env)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    if x is not None:
+        o.set_state(x, v, step)
+        sc.set_state(eid, x, v, step)
+    po = o.newton_direction()
+    pg = sc.newton_direction(eid)
+    assert np.abs(pg - po).max() <= 1e-8 * np.abs(po).max(), np.abs(pg - po).max() / np.abs(po).max()
