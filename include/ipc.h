@@ -184,6 +184,26 @@ ipc_status ipc_env_estimate_bytes(const ipc_env_desc* env, int32_t precision, ui
 /* Number of kernel launches issued by this scene since creation (instrumentation). */
 ipc_status ipc_launch_count(ipc_scene* scene, int64_t* count);
 
+/* Kernel-family profiling on the scene's stream (CUDA events around each launch of the family;
+ * a few microseconds of overhead per launch). Families: */
+typedef enum {
+  IPC_PROF_SPMV = 0,        /* PCG / Newton matrix-vector product (BSR rows + stencil gathers) */
+  IPC_PROF_ELASTIC = 1,     /* Neo-Hookean energy, gradient and projected Hessian per tet */
+  IPC_PROF_CONTACT = 2,     /* barrier + friction stencils with projected Hessians */
+  IPC_PROF_CCD = 3,         /* swept-box traversal with additive CCD */
+  IPC_PROF_PCG_VECTOR = 4,  /* PCG vector updates, preconditioner and dot products */
+  IPC_PROF_BROAD = 5,       /* constraint-set traversal, narrow phase */
+  IPC_PROF_ASSEMBLY = 6,    /* gradient / BSR gather, preconditioner blocks, stencil incidence */
+  IPC_PROF_LS_ENERGY = 7,   /* energy-only evaluation of line-search trials */
+  IPC_PROF_COUNT = 8
+} ipc_prof_family;
+/* Turn profiling on (1) or off (0); turning it on clears the counters. */
+ipc_status ipc_profile_enable(ipc_scene* scene, int32_t on);
+/* Launches, summed event time (ms) and algorithmic work of one family since profiling was
+ * turned on. work: SPMV = algorithmic bytes (BSR blocks 76 B, node vectors 56 B, stencil
+ * entries 28 B, body blocks 1344 B), ELASTIC = tets processed, others 0. Synchronises. */
+ipc_status ipc_profile_read(ipc_scene* scene, int32_t family, int64_t* launches, double* ms, double* work);
+
 const char* ipc_last_error(void);
 const char* ipc_version(void);
 

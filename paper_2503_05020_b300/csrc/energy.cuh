@@ -78,10 +78,14 @@ template <int MODE>
 __global__ void k_elastic(int n_tets, const int4* __restrict__ tets, const double* __restrict__ prm,
                           const int* __restrict__ tenv, const uint8_t* __restrict__ act, const double* __restrict__ q,
                           double h2, double* __restrict__ tE, double* __restrict__ tg, double* __restrict__ tH,
-                          int* __restrict__ env_bad) {
+                          int* __restrict__ env_bad, unsigned long long* __restrict__ units) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tets) return;
   int e = tenv[t];
+  if (units) {  // count the tets this launch processes (one atomic per warp)
+    unsigned m = __ballot_sync(__activemask(), act[e] != 0);
+    if ((threadIdx.x & 31) == __ffs(__activemask()) - 1) atomicAdd(units, (unsigned long long)__popc(m));
+  }
   if (!act[e]) return;
   int4 T = tets[t];
   const double* P = prm + 12 * (long)t;

@@ -396,10 +396,49 @@ struct ipc_scene {
   DBuf<double> sE, sg, sH, st_t;
   DBuf<long long> pcg_iters;
   DBuf<int> st_hist, root_off_tri, root_off_ed;
+  // profiling: event pairs per family, device work counters
+  bool prof_on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[IPC_PROF_COUNT];
+  std::vector<cudaEvent_t> ev_pool;
+  long long prof_launches[IPC_PROF_COUNT] = {0};
+  DBuf<unsigned long long> prof_units;
+  cudaEvent_t take_event() {
+    if (ev_pool.empty()) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      return e;
+    }
+    cudaEvent_t e = ev_pool.back();
+    ev_pool.pop_back();
+    return e;
+  }
+  int prof_cur = -1;
+  cudaEvent_t prof_start{};
+  void pbeg(int fam) {
+    if (!prof_on) return;
+    prof_cur = fam;
+    prof_start = take_event();
+    CK(cudaEventRecord(prof_start, stream));
+  }
+  void pend(int fam) {
+    if (!prof_on || prof_cur != fam) return;
+    cudaEvent_t e = take_event();
+    CK(cudaEventRecord(e, stream));
+    prof_ev[fam].push_back({prof_start, e});
+    prof_launches[fam]++;
+    prof_cur = -1;
+  }
+  unsigned long long* punits(int fam) { return prof_on ? prof_units.p + fam : nullptr; }
   // pinned host scratch
   int* hpin = nullptr;
 
   ~ipc_scene() {
+    for (auto& v : prof_ev)
+      for (auto& pr : v) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+      }
+    for (auto e : ev_pool) cudaEventDestroy(e);
     if (hpin) cudaFreeHost(hpin);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
@@ -872,11 +911,13 @@ struct ipc_scene {
     double r = 0.5 * desc.dhat;
     boxes_and_refit(nullptr, r);
     CandOut o{cnt_pt.p, nullptr, nullptr, overflow.p};
+    pbeg(IPC_PROF_BROAD);
     launch(k_trav_pt<TRAV_COUNT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
            (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), o, (const double*)nullptr, ctl());
     CandOut oe{cnt_ee.p, nullptr, nullptr, overflow.p};
     launch(k_trav_ee<TRAV_COUNT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
            (const double*)tedge.pbox.p, tree(tedge), ptinfo(), oe, (const double*)nullptr, (const double*)nullptr, ctl());
+    pend(IPC_PROF_BROAD);
     n_pt = scan(cnt_pt.p, NSV, off_pt.p);
     n_ee = scan(cnt_ee.p, NED, off_ee.p);
     check_overflow();
@@ -920,15 +961,21 @@ struct ipc_scene {
     stencil_table();
     double h = desc.dt, h2 = h * h;
     launch(k_inertia_energy, NN, 256, NN, layout(), act, q, (const double*)xtilde.p, nodeE.p);
+    int efam = MODE == MODE_ENERGY ? IPC_PROF_LS_ENERGY : IPC_PROF_ELASTIC;
+    pbeg(efam);
     launch(k_elastic<MODE>, NT, 128, NT, (const int4*)tets.p, (const double*)tet_prm.p, (const int*)tet_env.p, act, q,
-           h2, tetE.p, tet_g.p, tet_H.p, e_bad.p);
+           h2, tetE.p, tet_g.p, tet_H.p, e_bad.p, MODE == MODE_ENERGY ? (unsigned long long*)nullptr : punits(IPC_PROF_ELASTIC));
+    pend(efam);
     launch(k_bodies<MODE>, NB, 64, NB, (const int*)body_node.p, (const int*)body_env.p, (const uint8_t*)body_kin.p,
            (const double*)M4.p, (const double*)bvol.p, act, q, (const double*)xtilde.p, h2 * desc.kappa_affine, bodyE.p,
            body_g.p, body_H.p);
+    int cfam = MODE == MODE_ENERGY ? IPC_PROF_LS_ENERGY : IPC_PROF_CONTACT;
+    pbeg(cfam);
     launch(k_barrier<MODE>, n_ct, 64, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, h2, desc.dhat, desc.kappa,
            sE.p, sg.p, sH.p);
     launch(k_friction<MODE>, n_fr, 128, n_fr, (const FrictionRec*)fr.p, act, (const double*)ptx.p,
            (const double*)ptx_t.p, h2, desc.eps_v * h, sE.p + n_ct, sg.p + 12 * (size_t)n_ct, sH.p + 78 * (size_t)n_ct);
+    pend(cfam);
     EnergyLists L{nodeE.p, node_off.p, tetE.p, tet_off.p, bodyE.p, body_off.p, sE.p, st_env.p,
                   n_ct_pt, n_ct - n_ct_pt, n_fr_pt, n_fr};
     launch_grid(k_env_energy, E, 256, E, L, act, out);
@@ -963,7 +1010,9 @@ struct ipc_scene {
     int ns = n_ct + n_fr;
     launch(k_stencil_mv, ns, 128, ns, layout(), (const int*)st_env.p, (const int*)st_pts.p, run, (const double*)sH.p, d,
            st_t.p);
-    launch_grid(k_spmv, NTILE, TILE, tiles(), layout(), spmv_args(), run, d, y, part);
+    pbeg(IPC_PROF_SPMV);
+    launch_grid(k_spmv, NTILE, TILE, tiles(), layout(), spmv_args(), run, d, y, part, punits(IPC_PROF_SPMV));
+    pend(IPC_PROF_SPMV);
   }
 
   // ------------------------------------------------------------------ PCG
@@ -985,12 +1034,14 @@ struct ipc_scene {
     while (active > 0 && done_iters < desc.max_pcg_iters) {
       for (int c = 0; c < chunk; ++c) {
         matvec(pcg_run.p, pcg_d.p, pcg_y.p, part_a.p);
+        pbeg(IPC_PROF_PCG_VECTOR);
         launch_grid(k_pcg_update, NTILE, TILE, tiles(), layout(), S, parity, E, (const double*)part_a.p,
                     (const double*)Ps.p, (const double*)Pb.p, (const double*)pcg_d.p, (const double*)pcg_y.p, pcg_x.p,
                     pcg_r.p, pcg_z.p, part_b.p, part_c.p);
         launch_grid(k_pcg_direction, NTILE, TILE, tiles(), layout(), S, parity, E, tol2, desc.max_pcg_iters,
                     (const double*)part_b.p, (const double*)part_c.p, (const double*)part_a.p, (const double*)pcg_z.p,
                     pcg_d.p);
+        pend(IPC_PROF_PCG_VECTOR);
         parity ^= 1;
       }
       done_iters += chunk;
@@ -1002,6 +1053,7 @@ struct ipc_scene {
 
   // ------------------------------------------------------------------ one Newton iteration
   void assemble(const uint8_t* act) {
+    pbeg(IPC_PROF_ASSEMBLY);
     stencil_incidence(act);
     launch(k_assemble_grad, NN, 256, NN, layout(), act, (const double*)x.p, (const double*)xtilde.p, (const int*)nt_ptr.p,
            (const int*)nt_src.p, (const double*)tet_g.p, (const double*)body_g.p, (const int*)ns_ptr.p,
@@ -1012,6 +1064,7 @@ struct ipc_scene {
            (const int*)ns_ptr.p, (const int*)ns_src.p, (const double*)sH.p, Ps.p);
     launch_grid(k_precond_body, NB, 144, NB, layout(), (const int*)body_env.p, act, (const double*)body_H.p,
                 (const int*)ns_ptr.p, (const int*)ns_src.p, (const int*)st_pts.p, (const double*)sH.p, Pb.p);
+    pend(IPC_PROF_ASSEMBLY);
   }
 
   // step set-up for the envs in act: x^t, x~, targets, positions at x^t, trees, friction lag
@@ -1059,11 +1112,13 @@ struct ipc_scene {
       launch(k_add_vec, 3L * NP, 256, 3L * NP, (const double*)ptx.p, (const double*)ptp.p, pte.p);
       boxes_and_refit(pte.p, 0.0);
       CandOut oc{nullptr, nullptr, nullptr, overflow.p};
+      pbeg(IPC_PROF_CCD);
       launch(k_trav_pt<TRAV_CCD>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, (const uint8_t*)e_iter.p,
              (const double*)ptx.p, (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), oc,
              (const double*)ptp.p, C);
       launch(k_trav_ee<TRAV_CCD>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, (const uint8_t*)e_iter.p,
              (const double*)tedge.pbox.p, tree(tedge), ptinfo(), oc, (const double*)ptx.p, (const double*)ptp.p, C);
+      pend(IPC_PROF_CCD);
       check_overflow();
       // backtracking line search on the envs still iterating
       launch(k_env_ls_begin, E, 128, E, C);
@@ -1487,6 +1542,45 @@ ipc_status ipc_get_all_dofs(ipc_scene* s, double* out, size_t out_bytes, size_t*
   if (out_bytes < bytes || !out) fail_with(IPC_ERR_ARG, "output buffer too small");
   CK(cudaMemcpyAsync(out, s->x.p, bytes, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
+  API_END
+}
+
+ipc_status ipc_profile_enable(ipc_scene* s, int32_t on) {
+  API_BEGIN
+  if (!s) fail_with(IPC_ERR_ARG, "null scene");
+  CK(cudaSetDevice(s->device));
+  CK(cudaStreamSynchronize(s->stream));
+  for (int f = 0; f < IPC_PROF_COUNT; ++f) {
+    for (auto& pr : s->prof_ev[f]) {
+      s->ev_pool.push_back(pr.first);
+      s->ev_pool.push_back(pr.second);
+    }
+    s->prof_ev[f].clear();
+    s->prof_launches[f] = 0;
+  }
+  s->prof_units.ensure(IPC_PROF_COUNT);
+  s->prof_units.zero(s->stream, IPC_PROF_COUNT);
+  CK(cudaStreamSynchronize(s->stream));
+  s->prof_on = on != 0;
+  API_END
+}
+
+ipc_status ipc_profile_read(ipc_scene* s, int32_t fam, int64_t* launches, double* ms, double* work) {
+  API_BEGIN
+  if (!s || fam < 0 || fam >= IPC_PROF_COUNT) fail_with(IPC_ERR_ARG, "bad argument");
+  CK(cudaSetDevice(s->device));
+  CK(cudaStreamSynchronize(s->stream));
+  double t = 0.0;
+  for (auto& pr : s->prof_ev[fam]) {
+    float m = 0.f;
+    CK(cudaEventElapsedTime(&m, pr.first, pr.second));
+    t += m;
+  }
+  unsigned long long u[IPC_PROF_COUNT] = {0};
+  if (s->prof_units.p) CK(cudaMemcpy(u, s->prof_units.p, sizeof(u), cudaMemcpyDeviceToHost));
+  if (launches) *launches = s->prof_launches[fam];
+  if (ms) *ms = t;
+  if (work) *work = (double)u[fam];
   API_END
 }
 

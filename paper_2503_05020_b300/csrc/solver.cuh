@@ -282,17 +282,35 @@ DEV double spmv_tile_item(const Layout& L, const SpmvArgs& A, int kind, int item
   return r;
 }
 
+// algorithmic bytes of one row item: BSR blocks (72 B values + 4 B index), the d read and y
+// write (24 B each), row pointers (8 B), stencil entries (4 B index + 24 B stencil product);
+// a body row item is its dense 12x12 block (1152 B) plus 96 B read and 96 B written.
+DEV double spmv_item_bytes(const Layout& L, const SpmvArgs& A, int kind, int item) {
+  if (kind == 0) {
+    if (L.node_kin[item]) return 24.0;
+    return 76.0 * (A.bsr_ptr[item + 1] - A.bsr_ptr[item]) + 56.0 + 8.0 +
+           28.0 * (A.ns_ptr[item + 1] - A.ns_ptr[item]);
+  }
+  long base = L.body_node[item];
+  return 1344.0 + 28.0 * (A.ns_ptr[base + 4] - A.ns_ptr[base]);
+}
+
 __global__ void k_spmv(Tiles T, Layout L, SpmvArgs A, const uint8_t* __restrict__ run, const double* __restrict__ d,
-                       double* __restrict__ y, double* __restrict__ part) {
+                       double* __restrict__ y, double* __restrict__ part, unsigned long long* __restrict__ bytes) {
   __shared__ double sh[TILE];
   int tile = blockIdx.x;
   int e = T.env[tile];
   if (!run[e]) return;
   int item = T.begin[tile] + threadIdx.x;
   double v = 0.0;
-  if (item < T.end[tile]) v = spmv_tile_item(L, A, T.kind[tile], item, d, y);
+  bool ok = item < T.end[tile];
+  if (ok) v = spmv_tile_item(L, A, T.kind[tile], item, d, y);
   v = block_sum(v, sh);
   if (threadIdx.x == 0) part[tile] = v;
+  if (bytes) {
+    double b = block_sum(ok ? spmv_item_bytes(L, A, T.kind[tile], item) : 0.0, sh);
+    if (threadIdx.x == 0) atomicAdd(bytes, (unsigned long long)b);
+  }
 }
 
 // sum of an env's per-tile partials in tile order (thread 0), broadcast to the block

@@ -80,6 +80,7 @@ def lib() -> C.CDLL:
             "ipc_newton_direction": [vp, i32, vp], "ipc_hessian_apply": [vp, i32, vp, vp],
             "ipc_set_next_targets": [vp, vp, sz], "ipc_get_all_dofs": [vp, vp, sz, vp],
             "ipc_env_estimate_bytes": [vp, i32, vp], "ipc_launch_count": [vp, vp],
+            "ipc_profile_enable": [vp, i32], "ipc_profile_read": [vp, i32, vp, vp, vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -261,6 +262,19 @@ class Scene:
         w = C.c_size_t()
         lib().ipc_get_all_dofs(self._h, None, 0, C.byref(w))
         return w.value // 8
+
+    PROF_FAMILIES = ["spmv", "elastic", "contact", "ccd", "pcg_vector", "broad", "assembly", "ls_energy"]
+
+    def profile(self, on: bool = True):
+        _check(lib().ipc_profile_enable(self._h, int(on)))
+
+    def profile_read(self) -> dict:
+        out = {}
+        for i, name in enumerate(self.PROF_FAMILIES):
+            n, ms, w = C.c_int64(), C.c_double(), C.c_double()
+            _check(lib().ipc_profile_read(self._h, i, C.byref(n), C.byref(ms), C.byref(w)))
+            out[name] = dict(launches=n.value, ms=ms.value, work=w.value)
+        return out
 
     def launch_count(self) -> int:
         c = C.c_int64()

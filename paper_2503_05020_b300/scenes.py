@@ -371,6 +371,27 @@ def pad_grasp_env(env_id: int = 0, base_seed: int = BASE_SEED, n_steps: int = 30
     return dict(soft=[pad_r, pad_l], affine=[obj], mu=mu, gravity=gravity, targets=targets)
 
 
+def initial_dofs(env: dict) -> np.ndarray:
+    """DOF vector of an env at its initial state: soft vertices (x, y, z) in body order, then the
+    12 affine coordinates q0 of every affine body."""
+    parts = [s["verts"].reshape(-1) for s in env["soft"]] + [np.asarray(a["q0"]) for a in env["affine"]]
+    return np.concatenate(parts).astype(np.float64)
+
+
+def pad_grasp_state_at(env: dict, step: int) -> tuple[np.ndarray, np.ndarray]:
+    """Synthetic start of a pad-grasp env at schedule step `step`: every pad vertex translated by
+    the displacement its kinematic base has reached at the end of step-1 (so the base sits on its
+    target), the object at rest. Returns (DOFs, zero velocities)."""
+    x = initial_dofs(env)
+    off = 0
+    for b, s in enumerate(env["soft"]):
+        n = len(s["verts"])
+        q = env["targets"][step - 1, b] if step > 0 else IDENTITY_Q
+        x[3 * off: 3 * (off + n)].reshape(-1, 3)[:] += np.asarray(q[:3])
+        off += n
+    return x, np.zeros_like(x)
+
+
 def soft_object_grasp_env(env_id: int, base_seed: int = BASE_SEED, n_steps: int = 100,
                           close_steps: int = 50, dt: float = 0.005, dhat: float = 1e-3,
                           tets_lo: int = 2000, tets_hi: int = 60000, bimanual: bool | None = None,

@@ -169,7 +169,7 @@ def test_cube_grasp_trajectory_parity_100_steps():
 def test_pad_grasp_steps_parity():
     """Soft pads squeezing the rigid hull, a few steps with gravity on."""
     p = S.parity_params(S.scene_params(0.005))
-    env = S.pad_grasp_env(2, n_steps=3, close_steps=2, squeeze=4e-3)
+    env = S.pad_grasp_env(2, n_steps=3, close_steps=10, squeeze=2e-3)
     x, v = pads_pressed(env, 1.0e-3)
     o = O.OracleEnv(p, env)
     o.set_state(x, v, 0)
