@@ -341,6 +341,7 @@ struct ipc_scene {
 
   // ---------------- layout sizes
   int E = 0, NN = 0, NB = 0, NT = 0, NP = 0, NSV = 0, NED = 0, NTR = 0, NTILE = 0, NNZB = 0;
+  long sell_nval = 0;
   std::vector<int> ids;  // layout index -> env id
   std::vector<int> h_node_off, h_tet_off, h_pt_off, h_sv_off, h_ed_off, h_tri_off, h_body_off, h_tile_off;
   // ---------------- device arrays (static per layout)
@@ -359,7 +360,9 @@ struct ipc_scene {
   DBuf<uint8_t> pt_kin;
   DBuf<int> sv_pt, sv_env, ed_pt, ed_env, tri_pt, tri_env;
   DBuf<double> ed_rest2;
-  DBuf<int> bsr_ptr, bsr_col, blk_row, bsr_diag, blk_ptr, blk_src, nt_ptr, nt_src;
+  DBuf<int> bsr_ptr, bsr_col, blk_row, blk_ptr, blk_src, nt_ptr, nt_src;
+  DBuf<int> tile_slice, slice_w, sell_col;
+  DBuf<long> slice_vbase, slice_cbase, blk_pos, diag_pos;
   // ---------------- state
   DBuf<double> x, v, xt, xtilde, xtarget, xtrial, p, pbar, grad;
   DBuf<double> ptx, ptx_t, ptp, pte;
@@ -671,11 +674,11 @@ struct ipc_scene {
         tb.push_back(n0 + s);
         tn.push_back(n0 + std::min(nsv, s + TILE));
       }
-      for (int s = body_off_h[li]; s < body_off_h[li + 1]; s += TILE) {
+      for (int s = body_off_h[li]; s < body_off_h[li + 1]; ++s) {  // one block per rigid body
         te.push_back(li);
         tk.push_back(1);
         tb.push_back(s);
-        tn.push_back(std::min(body_off_h[li + 1], s + TILE));
+        tn.push_back(s + 1);
       }
       toff.push_back((int)te.size());
     }
@@ -735,8 +738,46 @@ struct ipc_scene {
       int n4[4] = {tets_h[t].x, tets_h[t].y, tets_h[t].z, tets_h[t].w};
       for (int a = 0; a < 4; ++a) ntsrc[fillp[n4[a]]++] = 4 * t + a;
     }
+    // sliced ELL of the soft rows: 32-row slices inside each soft tile, padded to the slice's
+    // longest row; block kk, element e of lane l at vbase + (kk*9 + e)*32 + l
+    std::vector<int> tslice(te.size(), -1), sw;
+    std::vector<long> svb, scb, bpos(NNZB, -1), dpos(NN, -1);
+    std::vector<int> scol;
+    long vtot = 0, ctot = 0;
+    for (size_t ti = 0; ti < te.size(); ++ti) {
+      if (tk[ti] != 0) continue;
+      tslice[ti] = (int)sw.size();
+      for (int r0 = tb[ti]; r0 < tn[ti]; r0 += 32) {
+        int r1 = std::min(tn[ti], r0 + 32);
+        int w = 0;
+        for (int r = r0; r < r1; ++r) w = std::max(w, bptr[r + 1] - bptr[r]);
+        sw.push_back(w);
+        svb.push_back(vtot);
+        scb.push_back(ctot);
+        scol.resize(ctot + 32L * w, -1);
+        for (int r = r0; r < r1; ++r) {
+          int lane = r - r0;
+          for (int k = bptr[r]; k < bptr[r + 1]; ++k) {
+            int kk = k - bptr[r];
+            scol[ctot + 32L * kk + lane] = bcol[k];
+            bpos[k] = vtot + 288L * kk + lane;
+            if (bcol[k] == r) dpos[r] = bpos[k];
+          }
+        }
+        vtot += 288L * w;
+        ctot += 32L * w;
+      }
+    }
     // ---------- upload
     cudaStream_t s = stream;
+    tile_slice.upload(tslice, s);
+    slice_w.upload(sw, s);
+    slice_vbase.upload(svb, s);
+    slice_cbase.upload(scb, s);
+    sell_col.upload(scol, s);
+    blk_pos.upload(bpos, s);
+    diag_pos.upload(dpos, s);
+    sell_nval = vtot;
     node_off.upload(node_off_h, s);
     tet_off.upload(tet_off_h, s);
     body_off.upload(body_off_h, s);
@@ -784,7 +825,6 @@ struct ipc_scene {
     bsr_ptr.upload(bptr, s);
     bsr_col.upload(bcol, s);
     blk_row.upload(brow, s);
-    bsr_diag.upload(bdiag, s);
     blk_ptr.upload(blkptr, s);
     blk_src.upload(blksrc, s);
     nt_ptr.upload(ntcnt, s);
@@ -816,7 +856,7 @@ struct ipc_scene {
     bodyE.alloc(NB);
     body_g.alloc(12 * (size_t)NB);
     body_H.alloc(144 * (size_t)NB);
-    bsr_val.alloc(9 * (size_t)NNZB);
+    bsr_val.alloc(std::max(sell_nval, 1L));
     Ps.alloc(9 * (size_t)NN);
     Pb.alloc(144 * (size_t)NB);
     for (DBuf<double>* b : {&part_a, &part_b, &part_c}) b->alloc(NTILE);
@@ -1003,7 +1043,8 @@ struct ipc_scene {
   }
 
   SpmvArgs spmv_args() {
-    return SpmvArgs{bsr_ptr.p, bsr_col.p, bsr_val.p, body_H.p, ns_ptr.p, ns_src.p, st_pts.p, st_t.p};
+    Sell S{tile_slice.p, slice_w.p, slice_vbase.p, slice_cbase.p, sell_col.p, bsr_val.p};
+    return SpmvArgs{S, bsr_ptr.p, body_H.p, ns_ptr.p, ns_src.p, st_pts.p, st_t.p};
   }
   // y = H d over the envs in run (stencil product, then BSR/body rows); partial d.y per tile
   void matvec(const uint8_t* run, const double* d, double* y, double* part) {
@@ -1059,8 +1100,8 @@ struct ipc_scene {
            (const int*)nt_src.p, (const double*)tet_g.p, (const double*)body_g.p, (const int*)ns_ptr.p,
            (const int*)ns_src.p, (const int*)st_pts.p, (const double*)sg.p, grad.p, nodeE.p);
     launch(k_assemble_bsr, NNZB, 128, NNZB, (const int*)blk_row.p, (const int*)bsr_col.p, layout(), act,
-           (const int*)blk_ptr.p, (const int*)blk_src.p, (const double*)tet_H.p, bsr_val.p);
-    launch(k_precond_soft, NN, 256, NN, layout(), act, (const int*)bsr_diag.p, (const double*)bsr_val.p,
+           (const int*)blk_ptr.p, (const int*)blk_src.p, (const double*)tet_H.p, (const long*)blk_pos.p, bsr_val.p);
+    launch(k_precond_soft, NN, 256, NN, layout(), act, (const long*)diag_pos.p, (const double*)bsr_val.p,
            (const int*)ns_ptr.p, (const int*)ns_src.p, (const double*)sH.p, Ps.p);
     launch_grid(k_precond_body, NB, 144, NB, layout(), (const int*)body_env.p, act, (const double*)body_H.p,
                 (const int*)ns_ptr.p, (const int*)ns_src.p, (const int*)st_pts.p, (const double*)sH.p, Pb.p);

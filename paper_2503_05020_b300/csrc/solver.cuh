@@ -96,10 +96,15 @@ __global__ void k_inertia_energy(int n_nodes, Layout L, const uint8_t* __restric
   nodeE[i] = e;
 }
 
-// BSR block k = sum of the tet Hessian blocks that land on it (+ lumped mass on the diagonal)
+// Soft-node rows are stored as sliced ELL: 32 consecutive rows form a slice padded to its longest
+// row; block kk of lane l, element e (row-major 3x3) sits at vbase + (kk*9 + e)*32 + l, so every
+// warp-wide load of one element is one contiguous 256-byte access. Padding columns are -1.
+// BSR block k (CSR order) = sum of the tet Hessian blocks that land on it (+ lumped mass on the
+// diagonal), written to its sliced-ELL position pos[k].
 __global__ void k_assemble_bsr(int nnzb, const int* __restrict__ blk_row, const int* __restrict__ bsr_col, Layout L,
                                const uint8_t* __restrict__ act, const int* __restrict__ bptr,
-                               const int* __restrict__ bsrc, const double* __restrict__ tH, double* __restrict__ val) {
+                               const int* __restrict__ bsrc, const double* __restrict__ tH, const long* __restrict__ pos,
+                               double* __restrict__ val) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nnzb) return;
   int row = blk_row[k];
@@ -117,7 +122,7 @@ __global__ void k_assemble_bsr(int nnzb, const int* __restrict__ blk_row, const 
       for (int r = 0; r < 3; ++r)
         for (int cc = 0; cc < 3; ++cc) v[3 * r + cc] += H[3 * cc + r];
   }
-  for (int i = 0; i < 9; ++i) val[9L * k + i] = v[i];
+  for (int i = 0; i < 9; ++i) val[pos[k] + 32L * i] = v[i];
 }
 
 // 3x3 block of a packed 12x12 stencil Hessian between slots a and b
@@ -126,7 +131,7 @@ DEV void stencil_block(const double* __restrict__ H78, int a, int b, double* out
     for (int c = 0; c < 3; ++c) out[3 * r + c] = H78[sym_idx(3 * a + r, 3 * b + c, 12)];
 }
 
-__global__ void k_precond_soft(int n_nodes, Layout L, const uint8_t* __restrict__ act, const int* __restrict__ diag,
+__global__ void k_precond_soft(int n_nodes, Layout L, const uint8_t* __restrict__ act, const long* __restrict__ diag_pos,
                                const double* __restrict__ bsr_val, const int* __restrict__ ns_ptr,
                                const int* __restrict__ ns_src, const double* __restrict__ sH, double* __restrict__ Pinv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,7 +142,7 @@ __global__ void k_precond_soft(int n_nodes, Layout L, const uint8_t* __restrict_
     for (int k = 0; k < 9; ++k) Pinv[9L * i + k] = 0.0;
     return;
   }
-  for (int k = 0; k < 9; ++k) D[k] = bsr_val[9L * diag[i] + k];
+  for (int k = 0; k < 9; ++k) D[k] = bsr_val[diag_pos[i] + 32L * k];
   for (int k = ns_ptr[i]; k < ns_ptr[i + 1]; ++k) {
     int e = ns_src[k], s = e >> 2, slot = e & 3;
     double B[9];
@@ -221,10 +226,18 @@ __global__ void k_stencil_mv(int n_st, Layout L, const int* __restrict__ st_env,
   }
 }
 
+struct Sell {
+  const int* tile_slice;  // first slice of each soft tile
+  const int* width;       // blocks per row of each slice
+  const long* vbase;      // value offset (doubles) of each slice
+  const long* cbase;      // column offset of each slice
+  const int* col;         // block column (node), -1 for padding
+  const double* val;
+};
+
 struct SpmvArgs {
-  const int* bsr_ptr;
-  const int* bsr_col;
-  const double* bsr_val;
+  Sell S;
+  const int* bsr_ptr;     // CSR row pointers (for the algorithmic byte count only)
   const double* bH;
   const int* ns_ptr;
   const int* ns_src;
@@ -242,73 +255,119 @@ DEV d3 stencil_gather(const Layout& L, const SpmvArgs& A, int i) {
   return acc;
 }
 
-// y = A d on one tile; returns this thread's d . y (kinematic rows give y = 0)
-DEV double spmv_tile_item(const Layout& L, const SpmvArgs& A, int kind, int item, const double* __restrict__ d,
-                          double* __restrict__ y) {
-  if (kind == 0) {
-    int i = item;
-    d3 acc = mk3(0, 0, 0);
-    if (!L.node_kin[i]) {
-      for (int k = A.bsr_ptr[i]; k < A.bsr_ptr[i + 1]; ++k) {
-        const double* B = A.bsr_val + 9L * k;
-        d3 dv = ld3(d, A.bsr_col[k]);
-        acc = acc + mk3(B[0] * dv.x + B[1] * dv.y + B[2] * dv.z, B[3] * dv.x + B[4] * dv.y + B[5] * dv.z,
-                        B[6] * dv.x + B[7] * dv.y + B[8] * dv.z);
-      }
-      acc = acc + stencil_gather(L, A, i);
+// deterministic warp sum (fixed butterfly)
+DEV double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// y rows of one soft node from the sliced-ELL blocks and its stencil entries; returns d.y
+DEV double spmv_soft_row(const Layout& L, const SpmvArgs& A, int slice, int lane, int row, const double* __restrict__ d,
+                         double* __restrict__ y) {
+  d3 acc = mk3(0, 0, 0);
+  if (!L.node_kin[row]) {
+    int w = A.S.width[slice];
+    const int* col = A.S.col + A.S.cbase[slice] + lane;
+    const double* V = A.S.val + A.S.vbase[slice] + lane;
+    for (int kk = 0; kk < w; ++kk) {
+      int c = col[32 * kk];
+      if (c < 0) continue;
+      d3 dv = ld3(d, c);
+      const double* B = V + 288L * kk;
+      acc = acc + mk3(B[0] * dv.x + B[32] * dv.y + B[64] * dv.z, B[96] * dv.x + B[128] * dv.y + B[160] * dv.z,
+                      B[192] * dv.x + B[224] * dv.y + B[256] * dv.z);
     }
-    st3(y, i, acc);
-    return dot(acc, ld3(d, i));
+    acc = acc + stencil_gather(L, A, row);
   }
-  int b = item;
+  st3(y, row, acc);
+  return dot(acc, ld3(d, row));
+}
+
+// One rigid body per block: y = H_b d_b + sum over every stencil slot on the body of
+// (1, xb) (x) t_s[slot]. All threads stride over the body's stencil entries; 12 partial sums
+// are reduced by warp butterflies and then across warps in fixed order. Returns d.y (thread 0).
+DEV double spmv_body(const Layout& L, const SpmvArgs& A, int b, const double* __restrict__ d, double* __restrict__ y) {
+  __shared__ double red[12][TILE / 32];
+  __shared__ double dv[12];
+  __shared__ double dy[12];
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
   long base = L.body_node[b];
-  double r = 0.0;
-  if (L.body_kin[b]) {
-    for (int k = 0; k < 12; ++k) y[3 * base + k] = 0.0;
-    return 0.0;
-  }
-  const double* H = A.bH + 144L * b;
-  double dv[12];
-  for (int k = 0; k < 12; ++k) dv[k] = d[3 * base + k];
-  for (int I = 0; I < 4; ++I) {
-    d3 sg = stencil_gather(L, A, base + I);
-    for (int k = 0; k < 3; ++k) {
-      double acc = comp(sg, k);
-      for (int j = 0; j < 12; ++j) acc += H[12 * (3 * I + k) + j] * dv[j];
-      y[3 * (base + I) + k] = acc;
-      r += acc * dv[3 * I + k];
+  bool kin = L.body_kin[b];
+  if (t < 12) dv[t] = d[3 * base + t];
+  __syncthreads();
+  double acc[12];
+  for (int q = 0; q < 12; ++q) acc[q] = 0.0;
+  if (!kin) {
+    for (int k = A.ns_ptr[base] + t; k < A.ns_ptr[base + 1]; k += blockDim.x) {
+      int e = A.ns_src[k], s = e >> 2, slot = e & 3;
+      int pt = A.st_pts[4 * s + slot];
+      d3 tv = ld3(A.st_t, 4L * s + slot);
+      const double w[4] = {1.0, L.pt_xb[3 * pt], L.pt_xb[3 * pt + 1], L.pt_xb[3 * pt + 2]};
+      for (int I = 0; I < 4; ++I) {
+        acc[3 * I] += w[I] * tv.x;
+        acc[3 * I + 1] += w[I] * tv.y;
+        acc[3 * I + 2] += w[I] * tv.z;
+      }
     }
   }
+  for (int q = 0; q < 12; ++q) {
+    double v = warp_sum(acc[q]);
+    if (lane == 0) red[q][wp] = v;
+  }
+  __syncthreads();
+  if (t < 12) {
+    double v = 0.0;
+    if (!kin) {
+      const double* H = A.bH + 144L * b + 12 * t;
+      for (int j = 0; j < 12; ++j) v += H[j] * dv[j];
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[t][w];
+    }
+    y[3 * base + t] = v;
+    dy[t] = v * dv[t];
+  }
+  __syncthreads();
+  double r = 0.0;
+  if (t == 0)
+    for (int q = 0; q < 12; ++q) r += dy[q];
+  __syncthreads();
   return r;
 }
 
-// algorithmic bytes of one row item: BSR blocks (72 B values + 4 B index), the d read and y
-// write (24 B each), row pointers (8 B), stencil entries (4 B index + 24 B stencil product);
-// a body row item is its dense 12x12 block (1152 B) plus 96 B read and 96 B written.
-DEV double spmv_item_bytes(const Layout& L, const SpmvArgs& A, int kind, int item) {
+// algorithmic bytes of one row item: sliced-ELL blocks (72 B values + 4 B column), the d read
+// and y write (24 B each), row pointers (8 B), stencil entries (4 B index + 24 B stencil
+// product); a body is its dense 12x12 block (1152 B) plus 96 B read and 96 B written.
+DEV double spmv_item_bytes(const Layout& L, const SpmvArgs& A, int kind, int item, int slice) {
   if (kind == 0) {
     if (L.node_kin[item]) return 24.0;
-    return 76.0 * (A.bsr_ptr[item + 1] - A.bsr_ptr[item]) + 56.0 + 8.0 +
-           28.0 * (A.ns_ptr[item + 1] - A.ns_ptr[item]);
+    return 76.0 * (A.bsr_ptr[item + 1] - A.bsr_ptr[item]) + 56.0 + 8.0 + 28.0 * (A.ns_ptr[item + 1] - A.ns_ptr[item]);
   }
   long base = L.body_node[item];
-  return 1344.0 + 28.0 * (A.ns_ptr[base + 4] - A.ns_ptr[base]);
+  return 1344.0 + 28.0 * (A.ns_ptr[base + 1] - A.ns_ptr[base]);
 }
 
-__global__ void k_spmv(Tiles T, Layout L, SpmvArgs A, const uint8_t* __restrict__ run, const double* __restrict__ d,
-                       double* __restrict__ y, double* __restrict__ part, unsigned long long* __restrict__ bytes) {
+__global__ void __launch_bounds__(TILE) k_spmv(Tiles T, Layout L, SpmvArgs A, const uint8_t* __restrict__ run,
+                                               const double* __restrict__ d, double* __restrict__ y,
+                                               double* __restrict__ part, unsigned long long* __restrict__ bytes) {
   __shared__ double sh[TILE];
   int tile = blockIdx.x;
   int e = T.env[tile];
   if (!run[e]) return;
-  int item = T.begin[tile] + threadIdx.x;
-  double v = 0.0;
-  bool ok = item < T.end[tile];
-  if (ok) v = spmv_tile_item(L, A, T.kind[tile], item, d, y);
+  int kind = T.kind[tile];
+  double v = 0.0, nb = 0.0;
+  if (kind == 0) {
+    int row = T.begin[tile] + threadIdx.x;
+    int slice = A.S.tile_slice[tile] + (threadIdx.x >> 5);
+    bool ok = row < T.end[tile];
+    if (ok) v = spmv_soft_row(L, A, slice, threadIdx.x & 31, row, d, y);
+    if (bytes && ok) nb = spmv_item_bytes(L, A, 0, row, slice);
+  } else {
+    v = spmv_body(L, A, T.begin[tile], d, y);
+    if (bytes && threadIdx.x == 0) nb = spmv_item_bytes(L, A, 1, T.begin[tile], 0);
+  }
   v = block_sum(v, sh);
   if (threadIdx.x == 0) part[tile] = v;
   if (bytes) {
-    double b = block_sum(ok ? spmv_item_bytes(L, A, T.kind[tile], item) : 0.0, sh);
+    double b = block_sum(nb, sh);
     if (threadIdx.x == 0) atomicAdd(bytes, (unsigned long long)b);
   }
 }
@@ -326,56 +385,64 @@ DEV double env_total(const Tiles& T, int e, const double* __restrict__ part, dou
   return r;
 }
 
-// z = M^-1 r for one item, returns (r.z, r.r) contributions
-DEV void precond_item(const Layout& L, int kind, int item, const double* __restrict__ Ps, const double* __restrict__ Pb,
-                      const double* __restrict__ r, double* __restrict__ z, double* rz, double* rr) {
-  if (kind == 0) {
-    int i = item;
-    d3 rv = ld3(r, i);
-    const double* P = Ps + 9L * i;
-    d3 zv = mk3(P[0] * rv.x + P[1] * rv.y + P[2] * rv.z, P[3] * rv.x + P[4] * rv.y + P[5] * rv.z,
-                P[6] * rv.x + P[7] * rv.y + P[8] * rv.z);
-    st3(z, i, zv);
-    *rz = dot(rv, zv);
-    *rr = dot(rv, rv);
-    return;
-  }
-  int b = item;
-  long base = 3L * L.body_node[b];
-  const double* P = Pb + 144L * b;
-  double rv[12];
-  for (int k = 0; k < 12; ++k) rv[k] = r[base + k];
-  double a = 0.0, c = 0.0;
-  for (int i = 0; i < 12; ++i) {
+// z = M^-1 r for one soft node, returns (r.z, r.r)
+DEV void precond_soft(int i, const double* __restrict__ Ps, const double* __restrict__ r, double* __restrict__ z,
+                      double* rz, double* rr) {
+  d3 rv = ld3(r, i);
+  const double* P = Ps + 9L * i;
+  d3 zv = mk3(P[0] * rv.x + P[1] * rv.y + P[2] * rv.z, P[3] * rv.x + P[4] * rv.y + P[5] * rv.z,
+              P[6] * rv.x + P[7] * rv.y + P[8] * rv.z);
+  st3(z, i, zv);
+  *rz = dot(rv, zv);
+  *rr = dot(rv, rv);
+}
+
+// body preconditioner on one block: threads 0..11 hold one DOF each; rs must be in shared memory
+DEV void precond_body(const double* __restrict__ Pb, int b, const double* rs, long base3, double* __restrict__ z,
+                      double* rz, double* rr) {
+  int t = threadIdx.x;
+  *rz = 0.0;
+  *rr = 0.0;
+  if (t < 12) {
+    const double* P = Pb + 144L * b + 12 * t;
     double s = 0.0;
-    for (int j = 0; j < 12; ++j) s += P[12 * i + j] * rv[j];
-    z[base + i] = s;
-    a += rv[i] * s;
-    c += rv[i] * rv[i];
+    for (int j = 0; j < 12; ++j) s += P[j] * rs[j];
+    z[base3 + t] = s;
+    *rz = rs[t] * s;
+    *rr = rs[t] * rs[t];
   }
-  *rz = a;
-  *rr = c;
 }
 
 // PCG initialisation: z = M^-1 r, d = z, x = 0; partials of r.z and r.r
-__global__ void k_pcg_init(Tiles T, Layout L, const uint8_t* __restrict__ act, const double* __restrict__ Ps,
-                           const double* __restrict__ Pb, const double* __restrict__ r, double* __restrict__ z,
-                           double* __restrict__ d, double* __restrict__ xs, double* __restrict__ prz,
-                           double* __restrict__ prr) {
+__global__ void __launch_bounds__(TILE) k_pcg_init(Tiles T, Layout L, const uint8_t* __restrict__ act,
+                                                   const double* __restrict__ Ps, const double* __restrict__ Pb,
+                                                   const double* __restrict__ r, double* __restrict__ z,
+                                                   double* __restrict__ d, double* __restrict__ xs,
+                                                   double* __restrict__ prz, double* __restrict__ prr) {
   __shared__ double sh[TILE];
+  __shared__ double rs[12];
   int tile = blockIdx.x;
   int e = T.env[tile];
   if (!act[e]) return;
-  int item = T.begin[tile] + threadIdx.x;
   double a = 0.0, c = 0.0;
-  if (item < T.end[tile]) {
-    int kind = T.kind[tile];
-    precond_item(L, kind, item, Ps, Pb, r, z, &a, &c);
-    int n0 = kind == 0 ? item : L.body_node[item];
-    int nn = kind == 0 ? 1 : 4;
-    for (int k = 3 * n0; k < 3 * (n0 + nn); ++k) {
-      d[k] = z[k];
-      xs[k] = 0.0;
+  if (T.kind[tile] == 0) {
+    int i = T.begin[tile] + threadIdx.x;
+    if (i < T.end[tile]) {
+      precond_soft(i, Ps, r, z, &a, &c);
+      for (int k = 3 * i; k < 3 * i + 3; ++k) {
+        d[k] = z[k];
+        xs[k] = 0.0;
+      }
+    }
+  } else {
+    int b = T.begin[tile];
+    long base3 = 3L * L.body_node[b];
+    if (threadIdx.x < 12) rs[threadIdx.x] = r[base3 + threadIdx.x];
+    __syncthreads();
+    precond_body(Pb, b, rs, base3, z, &a, &c);
+    if (threadIdx.x < 12) {
+      d[base3 + threadIdx.x] = z[base3 + threadIdx.x];
+      xs[base3 + threadIdx.x] = 0.0;
     }
   }
   a = block_sum(a, sh);
@@ -417,28 +484,42 @@ __global__ void k_pcg_init_env(int n_env, Tiles T, const uint8_t* __restrict__ a
 }
 
 // alpha = rz / d.y; x += alpha d; r -= alpha y; z = M^-1 r; partials of r.z and r.r
-__global__ void k_pcg_update(Tiles T, Layout L, PcgState S, int parity, int n_env, const double* __restrict__ pdy,
-                             const double* __restrict__ Ps, const double* __restrict__ Pb, const double* __restrict__ d,
-                             const double* __restrict__ y, double* __restrict__ xs, double* __restrict__ r,
-                             double* __restrict__ z, double* __restrict__ prz, double* __restrict__ prr) {
+__global__ void __launch_bounds__(TILE) k_pcg_update(Tiles T, Layout L, PcgState S, int parity, int n_env,
+                                                     const double* __restrict__ pdy, const double* __restrict__ Ps,
+                                                     const double* __restrict__ Pb, const double* __restrict__ d,
+                                                     const double* __restrict__ y, double* __restrict__ xs,
+                                                     double* __restrict__ r, double* __restrict__ z,
+                                                     double* __restrict__ prz, double* __restrict__ prr) {
   __shared__ double sh[TILE];
   __shared__ double s1;
+  __shared__ double rs[12];
   int tile = blockIdx.x;
   int e = T.env[tile];
   if (!S.run[e]) return;
   double dy = env_total(T, e, pdy, &s1);
   double alpha = dy > 0.0 ? S.rz[parity * n_env + e] / dy : 0.0;
-  int item = T.begin[tile] + threadIdx.x;
   double a = 0.0, c = 0.0;
-  if (item < T.end[tile]) {
-    int kind = T.kind[tile];
-    int n0 = kind == 0 ? item : L.body_node[item];
-    int nn = kind == 0 ? 1 : 4;
-    for (int k = 3 * n0; k < 3 * (n0 + nn); ++k) {
-      xs[k] += alpha * d[k];
-      r[k] -= alpha * y[k];
+  if (T.kind[tile] == 0) {
+    int i = T.begin[tile] + threadIdx.x;
+    if (i < T.end[tile]) {
+      for (int k = 3 * i; k < 3 * i + 3; ++k) {
+        xs[k] += alpha * d[k];
+        r[k] -= alpha * y[k];
+      }
+      precond_soft(i, Ps, r, z, &a, &c);
     }
-    precond_item(L, kind, item, Ps, Pb, r, z, &a, &c);
+  } else {
+    int b = T.begin[tile];
+    long base3 = 3L * L.body_node[b];
+    if (threadIdx.x < 12) {
+      long k = base3 + threadIdx.x;
+      xs[k] += alpha * d[k];
+      double rv = r[k] - alpha * y[k];
+      r[k] = rv;
+      rs[threadIdx.x] = rv;
+    }
+    __syncthreads();
+    precond_body(Pb, b, rs, base3, z, &a, &c);
   }
   a = block_sum(a, sh);
   c = block_sum(c, sh);
@@ -449,9 +530,10 @@ __global__ void k_pcg_update(Tiles T, Layout L, PcgState S, int parity, int n_en
 }
 
 // beta = rz_new / rz; d = z + beta d; the env's first tile records rz_new and the stop test
-__global__ void k_pcg_direction(Tiles T, Layout L, PcgState S, int parity, int n_env, double tol2, int max_it,
-                                const double* __restrict__ prz, const double* __restrict__ prr,
-                                const double* __restrict__ pdy, const double* __restrict__ z, double* __restrict__ d) {
+__global__ void __launch_bounds__(TILE) k_pcg_direction(Tiles T, Layout L, PcgState S, int parity, int n_env,
+                                                        double tol2, int max_it, const double* __restrict__ prz,
+                                                        const double* __restrict__ prr, const double* __restrict__ pdy,
+                                                        const double* __restrict__ z, double* __restrict__ d) {
   __shared__ double s1, s2, s3;
   int tile = blockIdx.x;
   int e = T.env[tile];
@@ -471,12 +553,13 @@ __global__ void k_pcg_direction(Tiles T, Layout L, PcgState S, int parity, int n
   double rz_new = s1, rr = s2, dy = s3;
   double rz_old = S.rz[parity * n_env + e];
   double beta = rz_old > 0.0 ? rz_new / rz_old : 0.0;
-  int item = T.begin[tile] + threadIdx.x;
-  if (item < T.end[tile]) {
-    int kind = T.kind[tile];
-    int n0 = kind == 0 ? item : L.body_node[item];
-    int nn = kind == 0 ? 1 : 4;
-    for (int k = 3 * n0; k < 3 * (n0 + nn); ++k) d[k] = z[k] + beta * d[k];
+  if (T.kind[tile] == 0) {
+    int i = T.begin[tile] + threadIdx.x;
+    if (i < T.end[tile])
+      for (int k = 3 * i; k < 3 * i + 3; ++k) d[k] = z[k] + beta * d[k];
+  } else if (threadIdx.x < 12) {
+    long k = 3L * L.body_node[T.begin[tile]] + threadIdx.x;
+    d[k] = z[k] + beta * d[k];
   }
   if (tile == T.env_off[e] && threadIdx.x == 0) {
     S.rz[(1 - parity) * n_env + e] = rz_new;
