@@ -150,7 +150,8 @@ def run_ours(args):
 
     params = S.scene_params(DT)
     envs = make_envs(rank, args.envs)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # a non-default stream: the library's kernels and the timing events share it
+    torch.cuda.set_stream(stream)
     prec = ipc.MIXED if args.precision == "mixed" else ipc.FP64
     sc = ipc.Scene(params, precision=prec, device=local, stream=stream.cuda_stream)
     ids = [sc.add_env(e) for e in envs]
@@ -266,6 +267,10 @@ def run_ours(args):
         "gpu_launches": int(launches), "clocks": clk,
         "env_steps_done": int(steps_done), "envs_failed": int(failed),
         "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items()},
+        "counters_last_iteration": sc.scene_counters(ids[0]),
+        "newton_iters_per_env_step": round(sum(sc.status(e)["newton_iters"] for e in ids) / max(steps_done, 1), 2),
+        "pcg_iters_per_newton": round(sum(sc.status(e)["pcg_iters"] for e in ids)
+                                      / max(sum(sc.status(e)["newton_iters"] for e in ids), 1), 1),
     }
     print(json.dumps(line), flush=True)
     if world > 1:

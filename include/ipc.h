@@ -125,7 +125,11 @@ typedef enum {
                             (soft vertices, then affine rest vertices mapped by q) */
   IPC_Q_SIZES = 7,       /* int64[8]: ndof, points, surface vertices, edges, triangles, tets,
                             bodies, steps */
-  IPC_Q_INTERSECTIONS = 8 /* int64[2]: segment-triangle intersections, inverted tets */
+  IPC_Q_INTERSECTIONS = 8, /* int64[2]: segment-triangle intersections, inverted tets */
+  IPC_Q_SCENE_COUNTERS = 9 /* int64[8] for the whole scene (env_id ignored), from the last Newton
+                              iteration: contacts, point-triangle contacts, friction stencils,
+                              stencil-node incidence entries, longest node incidence list,
+                              candidates, BSR blocks, sliced-ELL padded blocks */
 } ipc_query_kind;
 
 /* Create / destroy a scene on desc->device. */

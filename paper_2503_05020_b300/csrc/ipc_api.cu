@@ -392,11 +392,11 @@ struct ipc_scene {
   DBuf<int> cnt_pt, off_pt, cnt_ee, off_ee, cand_j, nflag, noff, scan_tmp, overflow;
   DBuf<ContactRec> ct_tmp, ct;
   DBuf<FrictionRec> fr;
-  int n_pt = 0, n_ee = 0, n_ct = 0, n_ct_pt = 0, n_fr = 0, n_fr_pt = 0;
+  int n_pt = 0, n_ee = 0, n_ct = 0, n_ct_pt = 0, n_fr = 0, n_fr_pt = 0, n_inc = 0;
   DBuf<int> st_pts, st_env, st_cnt, st_off, ns_ptr, ns_src, ns_cnt;
   DBuf<unsigned long long> st_keys, st_keys2;
   DBuf<unsigned> st_vals, st_vals2;
-  DBuf<double> sE, sg, sH, st_t;
+  DBuf<double> sE, sg, sH, st_t, ns_w, ns_xb;
   DBuf<long long> pcg_iters;
   DBuf<int> st_hist, root_off_tri, root_off_ed;
   // profiling: event pairs per family, device work counters
@@ -417,19 +417,44 @@ struct ipc_scene {
   }
   int prof_cur = -1;
   cudaEvent_t prof_start{};
+  // events recorded inside a captured graph (external record nodes), resolved after each replay
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> graph_ev;
+  double prof_graph_ms[IPC_PROF_COUNT] = {0};
   void pbeg(int fam) {
     if (!prof_on) return;
     prof_cur = fam;
     prof_start = take_event();
-    CK(cudaEventRecord(prof_start, stream));
+    if (capturing) CK(cudaEventRecordWithFlags(prof_start, stream, cudaEventRecordExternal));
+    else CK(cudaEventRecord(prof_start, stream));
   }
   void pend(int fam) {
     if (!prof_on || prof_cur != fam) return;
     cudaEvent_t e = take_event();
-    CK(cudaEventRecord(e, stream));
-    prof_ev[fam].push_back({prof_start, e});
-    prof_launches[fam]++;
+    if (capturing) {
+      CK(cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal));
+      graph_ev.push_back({fam, {prof_start, e}});
+    } else {
+      CK(cudaEventRecord(e, stream));
+      prof_ev[fam].push_back({prof_start, e});
+      prof_launches[fam]++;
+    }
     prof_cur = -1;
+  }
+  // after a graph replay has completed: add its kernel times
+  void graph_prof_collect() {
+    for (auto& g : graph_ev) {
+      float m = 0.f;
+      CK(cudaEventElapsedTime(&m, g.second.first, g.second.second));
+      prof_graph_ms[g.first] += m;
+      prof_launches[g.first]++;
+    }
+  }
+  void graph_prof_release() {
+    for (auto& g : graph_ev) {
+      ev_pool.push_back(g.second.first);
+      ev_pool.push_back(g.second.second);
+    }
+    graph_ev.clear();
   }
   unsigned long long* punits(int fam) { return prof_on ? prof_units.p + fam : nullptr; }
   // pinned host scratch
@@ -447,19 +472,23 @@ struct ipc_scene {
   }
 
   // ------------------------------------------------------------------ launch helpers
+  bool capturing = false;
+  long long captured_kernels = 0;
   template <class K, class... Args>
   void launch(K kern, long n_threads, int block, Args... args) {
     if (n_threads <= 0) return;
     long grid = (n_threads + block - 1) / block;
     kern<<<(unsigned)grid, block, 0, stream>>>(args...);
-    ++launches;
+    if (capturing) ++captured_kernels;
+    else ++launches;
     CK(cudaGetLastError());
   }
   template <class K, class... Args>
   void launch_grid(K kern, long grid, int block, Args... args) {
     if (grid <= 0) return;
     kern<<<(unsigned)grid, block, 0, stream>>>(args...);
-    ++launches;
+    if (capturing) ++captured_kernels;
+    else ++launches;
     CK(cudaGetLastError());
   }
   int read_int(const int* dptr) {
@@ -1028,6 +1057,7 @@ struct ipc_scene {
     st_off.ensure(ns + 1);
     launch(k_stencil_nent, ns, 256, ns, (const int*)st_pts.p, (const int*)st_env.p, act, (const int*)pt_node.p, st_cnt.p);
     int ne = scan(st_cnt.p, ns, st_off.p);
+    n_inc = ne;
     st_keys.ensure(ne + 1);
     st_vals.ensure(ne + 1);
     launch(k_stencil_emit, ns, 256, ns, (const int*)st_pts.p, (const int*)st_env.p, act, (const int*)pt_node.p,
@@ -1040,11 +1070,15 @@ struct ipc_scene {
     scan(ns_cnt.p, NN, ns_ptr.p, false);
     ns_src.ensure(ne + 1);
     if (ne > 0) CK(cudaMemcpyAsync(ns_src.p, st_vals.p, ne * sizeof(unsigned), cudaMemcpyDeviceToDevice, stream));
+    ns_w.ensure(ne + 1);
+    ns_xb.ensure(3 * (size_t)ne + 3);
+    launch(k_entry_weights, NN, 256, NN, layout(), act, (const int*)ns_ptr.p, (const int*)ns_src.p, (const int*)st_pts.p,
+           ns_w.p, ns_xb.p);
   }
 
   SpmvArgs spmv_args() {
     Sell S{tile_slice.p, slice_w.p, slice_vbase.p, slice_cbase.p, sell_col.p, bsr_val.p};
-    return SpmvArgs{S, bsr_ptr.p, body_H.p, ns_ptr.p, ns_src.p, st_pts.p, st_t.p};
+    return SpmvArgs{S, bsr_ptr.p, body_H.p, ns_ptr.p, ns_src.p, ns_w.p, ns_xb.p, st_pts.p, st_t.p};
   }
   // y = H d over the envs in run (stencil product, then BSR/body rows); partial d.y per tile
   void matvec(const uint8_t* run, const double* d, double* y, double* part) {
@@ -1066,28 +1100,47 @@ struct ipc_scene {
     pcg_iters.ensure(E);
     pcg_iters.zero(stream, E);
     S.total_iters = pcg_iters.p;
-    launch(k_pcg_init_env, E, 128, E, tiles(), act, (const double*)part_b.p, (const double*)part_c.p, S);
+    launch_grid(k_pcg_init_env, E, 32, E, tiles(), act, (const double*)part_b.p, (const double*)part_c.p, S);
     int active = read_int(pcg_active.p);
     int parity = 0;
     int done_iters = 0;
     double tol2 = desc.pcg_rel_tol * desc.pcg_rel_tol;
-    const int chunk = 8;
+    const int chunk = 8;  // even, so every replay starts at parity 0
+    cudaGraphExec_t exec = nullptr;
+    long long graph_kernels = 0;
     while (active > 0 && done_iters < desc.max_pcg_iters) {
-      for (int c = 0; c < chunk; ++c) {
-        matvec(pcg_run.p, pcg_d.p, pcg_y.p, part_a.p);
-        pbeg(IPC_PROF_PCG_VECTOR);
-        launch_grid(k_pcg_update, NTILE, TILE, tiles(), layout(), S, parity, E, (const double*)part_a.p,
-                    (const double*)Ps.p, (const double*)Pb.p, (const double*)pcg_d.p, (const double*)pcg_y.p, pcg_x.p,
-                    pcg_r.p, pcg_z.p, part_b.p, part_c.p);
-        launch_grid(k_pcg_direction, NTILE, TILE, tiles(), layout(), S, parity, E, tol2, desc.max_pcg_iters,
-                    (const double*)part_b.p, (const double*)part_c.p, (const double*)part_a.p, (const double*)pcg_z.p,
-                    pcg_d.p);
-        pend(IPC_PROF_PCG_VECTOR);
-        parity ^= 1;
+      if (!exec) {
+        capturing = true;
+        captured_kernels = 0;
+        CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        for (int c = 0; c < chunk; ++c) {
+          matvec(pcg_run.p, pcg_d.p, pcg_y.p, part_a.p);
+          pbeg(IPC_PROF_PCG_VECTOR);
+          launch_grid(k_pcg_update, NTILE, TILE, tiles(), layout(), S, parity, E, (const double*)part_a.p,
+                      (const double*)Ps.p, (const double*)Pb.p, (const double*)pcg_d.p, (const double*)pcg_y.p,
+                      pcg_x.p, pcg_r.p, pcg_z.p, part_b.p, part_c.p);
+          launch_grid(k_pcg_direction, NTILE, TILE, tiles(), layout(), S, parity, E, tol2, desc.max_pcg_iters,
+                      (const double*)part_b.p, (const double*)part_c.p, (const double*)part_a.p,
+                      (const double*)pcg_z.p, pcg_d.p);
+          pend(IPC_PROF_PCG_VECTOR);
+          parity ^= 1;
+        }
+        cudaGraph_t g;
+        cudaError_t ce = cudaStreamEndCapture(stream, &g);
+        capturing = false;
+        graph_kernels = captured_kernels;
+        CK(ce);
+        CK(cudaGraphInstantiate(&exec, g, 0));
+        CK(cudaGraphDestroy(g));
       }
+      CK(cudaGraphLaunch(exec, stream));
+      launches += graph_kernels;
       done_iters += chunk;
       active = read_int(pcg_active.p);
+      if (prof_on) graph_prof_collect();
     }
+    if (exec) CK(cudaGraphExecDestroy(exec));
+    graph_prof_release();
     launch(k_add_stats, E, 128, E, (const long long*)pcg_iters.p, e_stats.p);
     CK(cudaStreamSynchronize(stream));
   }
@@ -1475,6 +1528,15 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       CK(cudaStreamSynchronize(s->stream));
       return copy_out(v, sizeof(v), out, out_bytes, written);
     }
+    case IPC_Q_SCENE_COUNTERS: {
+      std::vector<int> ptr(s->NN + 1);
+      CK(cudaMemcpy(ptr.data(), s->ns_ptr.p, (s->NN + 1) * 4, cudaMemcpyDeviceToHost));
+      long long mx = 0;
+      for (int i = 0; i < s->NN; ++i) mx = std::max(mx, (long long)(ptr[i + 1] - ptr[i]));
+      long long v[8] = {s->n_ct, s->n_ct_pt, s->n_fr, s->n_inc, mx, (long long)s->n_pt + s->n_ee, s->NNZB,
+                        s->sell_nval / 288};
+      return copy_out(v, sizeof(v), out, out_bytes, written);
+    }
     case IPC_Q_SIZES: {
       long long v[8] = {h.ndof, (long long)h.pt_node.size(), (long long)h.sv.size(), (long long)h.edges.size() / 2,
                         (long long)h.tris.size() / 3, h.ntets, h.nbodies, h.n_steps};
@@ -1598,6 +1660,7 @@ ipc_status ipc_profile_enable(ipc_scene* s, int32_t on) {
     }
     s->prof_ev[f].clear();
     s->prof_launches[f] = 0;
+    s->prof_graph_ms[f] = 0.0;
   }
   s->prof_units.ensure(IPC_PROF_COUNT);
   s->prof_units.zero(s->stream, IPC_PROF_COUNT);
@@ -1611,7 +1674,7 @@ ipc_status ipc_profile_read(ipc_scene* s, int32_t fam, int64_t* launches, double
   if (!s || fam < 0 || fam >= IPC_PROF_COUNT) fail_with(IPC_ERR_ARG, "bad argument");
   CK(cudaSetDevice(s->device));
   CK(cudaStreamSynchronize(s->stream));
-  double t = 0.0;
+  double t = s->prof_graph_ms[fam];
   for (auto& pr : s->prof_ev[fam]) {
     float m = 0.f;
     CK(cudaEventElapsedTime(&m, pr.first, pr.second));

@@ -240,19 +240,38 @@ struct SpmvArgs {
   const int* bsr_ptr;     // CSR row pointers (for the algorithmic byte count only)
   const double* bH;
   const int* ns_ptr;
-  const int* ns_src;
+  const int* ns_src;   // stencil*4 + slot of each incidence entry (row-sorted)
+  const double* ns_w;  // weight of the entry's node in the slot's point position
+  const double* ns_xb; // body p-node entries: rest coordinates (xb) of the entry's point
   const int* st_pts;
   const double* st_t;
 };
 
-DEV d3 stencil_gather(const Layout& L, const SpmvArgs& A, int i) {
+// sum over a node's incidence entries of w * t_s[slot]: one dependent load per entry
+DEV d3 stencil_gather(const SpmvArgs& A, int i) {
   d3 acc = mk3(0, 0, 0);
-  for (int k = A.ns_ptr[i]; k < A.ns_ptr[i + 1]; ++k) {
-    int e = A.ns_src[k], s = e >> 2, slot = e & 3;
-    double w = point_weight(L, A.st_pts[4 * s + slot], i);
-    acc = acc + w * ld3(A.st_t, 4L * s + slot);
-  }
+  int k = A.ns_ptr[i], end = A.ns_ptr[i + 1];
+#pragma unroll 4
+  for (; k < end; ++k) acc = acc + A.ns_w[k] * ld3(A.st_t, A.ns_src[k]);
   return acc;
+}
+
+// weight of every incidence entry, once per Newton iteration; entries of a body's p node also
+// get the rest coordinates of their point, so one pass over that list serves all 4 body nodes
+__global__ void k_entry_weights(int n_nodes, Layout L, const uint8_t* __restrict__ act, const int* __restrict__ ns_ptr,
+                                const int* __restrict__ ns_src, const int* __restrict__ st_pts, double* __restrict__ ns_w,
+                                double* __restrict__ ns_xb) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  if (!act[L.node_env[i]]) return;
+  int b = L.node_body[i];
+  bool pnode = b >= 0 && L.body_node[b] == i;
+  for (int k = ns_ptr[i]; k < ns_ptr[i + 1]; ++k) {
+    int pt = st_pts[ns_src[k]];
+    ns_w[k] = point_weight(L, pt, i);
+    if (pnode)
+      for (int c = 0; c < 3; ++c) ns_xb[3L * k + c] = L.pt_xb[3 * pt + c];
+  }
 }
 
 // deterministic warp sum (fixed butterfly)
@@ -269,6 +288,7 @@ DEV double spmv_soft_row(const Layout& L, const SpmvArgs& A, int slice, int lane
     int w = A.S.width[slice];
     const int* col = A.S.col + A.S.cbase[slice] + lane;
     const double* V = A.S.val + A.S.vbase[slice] + lane;
+#pragma unroll 4
     for (int kk = 0; kk < w; ++kk) {
       int c = col[32 * kk];
       if (c < 0) continue;
@@ -277,15 +297,16 @@ DEV double spmv_soft_row(const Layout& L, const SpmvArgs& A, int slice, int lane
       acc = acc + mk3(B[0] * dv.x + B[32] * dv.y + B[64] * dv.z, B[96] * dv.x + B[128] * dv.y + B[160] * dv.z,
                       B[192] * dv.x + B[224] * dv.y + B[256] * dv.z);
     }
-    acc = acc + stencil_gather(L, A, row);
+    acc = acc + stencil_gather(A, row);
   }
   st3(y, row, acc);
   return dot(acc, ld3(d, row));
 }
 
 // One rigid body per block: y = H_b d_b + sum over every stencil slot on the body of
-// (1, xb) (x) t_s[slot]. All threads stride over the body's stencil entries; 12 partial sums
-// are reduced by warp butterflies and then across warps in fixed order. Returns d.y (thread 0).
+// (1, xb) (x) t_s[slot], gathered once from the body's p-node list (every slot on the body
+// appears there once). 12 partial sums are reduced by warp butterflies, then across warps in
+// fixed order. Returns d.y on thread 0.
 DEV double spmv_body(const Layout& L, const SpmvArgs& A, int b, const double* __restrict__ d, double* __restrict__ y) {
   __shared__ double red[12][TILE / 32];
   __shared__ double dv[12];
@@ -298,16 +319,24 @@ DEV double spmv_body(const Layout& L, const SpmvArgs& A, int b, const double* __
   double acc[12];
   for (int q = 0; q < 12; ++q) acc[q] = 0.0;
   if (!kin) {
-    for (int k = A.ns_ptr[base] + t; k < A.ns_ptr[base + 1]; k += blockDim.x) {
-      int e = A.ns_src[k], s = e >> 2, slot = e & 3;
-      int pt = A.st_pts[4 * s + slot];
-      d3 tv = ld3(A.st_t, 4L * s + slot);
-      const double w[4] = {1.0, L.pt_xb[3 * pt], L.pt_xb[3 * pt + 1], L.pt_xb[3 * pt + 2]};
-      for (int I = 0; I < 4; ++I) {
-        acc[3 * I] += w[I] * tv.x;
-        acc[3 * I + 1] += w[I] * tv.y;
-        acc[3 * I + 2] += w[I] * tv.z;
-      }
+    int kb = A.ns_ptr[base], ke = A.ns_ptr[base + 1];
+#pragma unroll 2
+    for (int k = kb + t; k < ke; k += blockDim.x) {
+      d3 tv = ld3(A.st_t, A.ns_src[k]);
+      const double* xb = A.ns_xb + 3L * k;
+      double w1 = xb[0], w2 = xb[1], w3 = xb[2];
+      acc[0] += tv.x;
+      acc[1] += tv.y;
+      acc[2] += tv.z;
+      acc[3] += w1 * tv.x;
+      acc[4] += w1 * tv.y;
+      acc[5] += w1 * tv.z;
+      acc[6] += w2 * tv.x;
+      acc[7] += w2 * tv.y;
+      acc[8] += w2 * tv.z;
+      acc[9] += w3 * tv.x;
+      acc[10] += w3 * tv.y;
+      acc[11] += w3 * tv.z;
     }
   }
   for (int q = 0; q < 12; ++q) {
@@ -334,15 +363,16 @@ DEV double spmv_body(const Layout& L, const SpmvArgs& A, int b, const double* __
 }
 
 // algorithmic bytes of one row item: sliced-ELL blocks (72 B values + 4 B column), the d read
-// and y write (24 B each), row pointers (8 B), stencil entries (4 B index + 24 B stencil
-// product); a body is its dense 12x12 block (1152 B) plus 96 B read and 96 B written.
+// and y write (24 B each), row pointers (8 B), stencil entries (4 B index + 8 B weight + 24 B
+// stencil product); a body is its dense 12x12 block (1152 B) plus 96 B read and 96 B written,
+// and per p-node entry 4 B index + 24 B rest coordinates + 24 B stencil product.
 DEV double spmv_item_bytes(const Layout& L, const SpmvArgs& A, int kind, int item, int slice) {
   if (kind == 0) {
     if (L.node_kin[item]) return 24.0;
-    return 76.0 * (A.bsr_ptr[item + 1] - A.bsr_ptr[item]) + 56.0 + 8.0 + 28.0 * (A.ns_ptr[item + 1] - A.ns_ptr[item]);
+    return 76.0 * (A.bsr_ptr[item + 1] - A.bsr_ptr[item]) + 56.0 + 8.0 + 36.0 * (A.ns_ptr[item + 1] - A.ns_ptr[item]);
   }
   long base = L.body_node[item];
-  return 1344.0 + 28.0 * (A.ns_ptr[base + 1] - A.ns_ptr[base]);
+  return 1344.0 + 52.0 * (A.ns_ptr[base + 1] - A.ns_ptr[base]);
 }
 
 __global__ void __launch_bounds__(TILE) k_spmv(Tiles T, Layout L, SpmvArgs A, const uint8_t* __restrict__ run,
@@ -372,12 +402,18 @@ __global__ void __launch_bounds__(TILE) k_spmv(Tiles T, Layout L, SpmvArgs A, co
   }
 }
 
-// sum of an env's per-tile partials in tile order (thread 0), broadcast to the block
+// sum of an env's per-tile partials by warp 0 (lane-strided, fixed butterfly: deterministic and
+// the same in every tile of the env), broadcast to the block
+DEV double partial_sum_warp(const Tiles& T, int e, const double* __restrict__ part) {
+  int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int k = T.env_off[e] + lane; k < T.env_off[e + 1]; k += 32) s += part[k];
+  return warp_sum(s);
+}
 DEV double env_total(const Tiles& T, int e, const double* __restrict__ part, double* sh1) {
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = T.env_off[e]; k < T.env_off[e + 1]; ++k) s += part[k];
-    *sh1 = s;
+  if (threadIdx.x < 32) {
+    double s = partial_sum_warp(T, e, part);
+    if (threadIdx.x == 0) *sh1 = s;
   }
   __syncthreads();
   double r = *sh1;
@@ -462,19 +498,17 @@ struct PcgState {
   long long* total_iters;  // per env cumulative
 };
 
+// one warp per env (launch with 32 threads per block, one block per env)
 __global__ void k_pcg_init_env(int n_env, Tiles T, const uint8_t* __restrict__ act, const double* __restrict__ prz,
                                const double* __restrict__ prr, PcgState S) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = blockIdx.x;
   if (e >= n_env) return;
   if (!act[e]) {
-    S.run[e] = 0;
+    if (threadIdx.x == 0) S.run[e] = 0;
     return;
   }
-  double a = 0.0, c = 0.0;
-  for (int k = T.env_off[e]; k < T.env_off[e + 1]; ++k) {
-    a += prz[k];
-    c += prr[k];
-  }
+  double a = partial_sum_warp(T, e, prz), c = partial_sum_warp(T, e, prr);
+  if (threadIdx.x != 0) return;
   S.rz[e] = a;
   S.bb[e] = c;
   S.it[e] = 0;
@@ -538,16 +572,13 @@ __global__ void __launch_bounds__(TILE) k_pcg_direction(Tiles T, Layout L, PcgSt
   int tile = blockIdx.x;
   int e = T.env[tile];
   if (!S.run[e]) return;
-  if (threadIdx.x == 0) {
-    double a = 0.0, c = 0.0, g = 0.0;
-    for (int k = T.env_off[e]; k < T.env_off[e + 1]; ++k) {
-      a += prz[k];
-      c += prr[k];
-      g += pdy[k];
+  if (threadIdx.x < 32) {
+    double a = partial_sum_warp(T, e, prz), c = partial_sum_warp(T, e, prr), g = partial_sum_warp(T, e, pdy);
+    if (threadIdx.x == 0) {
+      s1 = a;
+      s2 = c;
+      s3 = g;
     }
-    s1 = a;
-    s2 = c;
-    s3 = g;
   }
   __syncthreads();
   double rz_new = s1, rr = s2, dy = s3;

@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_BUDGET", 4: "ERR_CU
 ENV_STATUS = {0: "ACTIVE", 1: "DONE", 2: "FAILED"}
 FAIL_REASON = {0: "none", 1: "newton_cap", 2: "line_search", 3: "non_finite", 4: "initial_intersection", 5: "internal"}
 FP64, MIXED = 0, 1
-Q_DOFS, Q_VELOCITIES, Q_STATUS, Q_STATS, Q_CANDIDATES, Q_CONTACTS, Q_POINTS, Q_SIZES, Q_INTERSECTIONS = range(9)
+Q_DOFS, Q_VELOCITIES, Q_STATUS, Q_STATS, Q_CANDIDATES, Q_CONTACTS, Q_POINTS, Q_SIZES, Q_INTERSECTIONS, \
+    Q_SCENE_COUNTERS = range(10)
 
 
 class IpcError(RuntimeError):
@@ -219,6 +220,12 @@ class Scene:
     def sizes(self, eid: int) -> dict:
         v = self._query(eid, Q_SIZES, np.int64)
         return dict(zip(["ndof", "points", "surface_verts", "edges", "tris", "tets", "bodies", "steps"], map(int, v)))
+
+    def scene_counters(self, eid: int) -> dict:
+        v = self._query(eid, Q_SCENE_COUNTERS, np.int64)
+        keys = ["contacts", "pt_contacts", "friction", "incidence_entries", "longest_list", "candidates",
+                "bsr_blocks", "sell_blocks"]
+        return dict(zip(keys, map(int, v)))
 
     def invariants(self, eid: int) -> dict:
         v = self._query(eid, Q_INTERSECTIONS, np.int64)
