@@ -185,6 +185,31 @@ ipc_status ipc_get_all_dofs(ipc_scene* scene, double* out, size_t out_bytes, siz
 /* Estimated device bytes an env would hold (used for admission control). */
 ipc_status ipc_env_estimate_bytes(const ipc_env_desc* env, int32_t precision, uint64_t* bytes);
 
+/* Allocation-free Neo-Hookean energy (the paper has no counterpart; this is a deployment
+ * convenience). For callers that cannot call cudaMalloc: code that runs while a CUDA graph is
+ * being captured, real-time control loops where an allocation's latency or failure is not
+ * acceptable, or hosts whose memory manager owns every device allocation. It computes, for each
+ * group g of tets [group_offsets[g], group_offsets[g+1]), h2 * sum V Psi(F) over the group with
+ * the same per-tet energy code and the same fixed-order reduction as the scene path, and sets
+ * inverted[g] = 1 when a tet of the group has J <= 0 (its energy then counts as 0).
+ * All pointers are DEVICE pointers on the current device, owned by the caller:
+ *   tets: n_tets*4 int32 node indices into x; tet_params: n_tets*12 doubles per tet (row-major
+ *   Dm^-1, rest volume, mu, lambda); x: node positions (3 doubles each); group_offsets:
+ *   n_groups+1 int32 (ascending); energy: n_groups doubles (written); inverted: n_groups int32
+ *   (written). stream: cudaStream_t or NULL for the legacy default stream.
+ * Scratch lives in a file-scope device array of IPC_NOALLOC_MAX_TETS doubles (2 MiB), held by
+ * every device that loads the library until the process exits. Calls with n_tets above that
+ * maximum, or more than IPC_NOALLOC_MAX_GROUPS groups, return IPC_ERR_ARG. The first call on a
+ * device looks the array up (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture. All calls share the array: calls that overlap on the GPU
+ * (different streams, or different host threads) race on it. The call enqueues its work and
+ * returns without synchronising; it performs no allocation of any kind. */
+#define IPC_NOALLOC_MAX_TETS 262144
+#define IPC_NOALLOC_MAX_GROUPS 65536
+ipc_status ipc_elastic_energy_noalloc(int32_t n_tets, const int32_t* tets, const double* tet_params, const double* x,
+                                      int32_t n_groups, const int32_t* group_offsets, double h2, double* energy,
+                                      int32_t* inverted, void* stream);
+
 /* Number of kernel launches issued by this scene since creation (instrumentation). */
 ipc_status ipc_launch_count(ipc_scene* scene, int64_t* count);
 

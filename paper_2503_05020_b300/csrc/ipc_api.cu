@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <numeric>
 #include <stdexcept>
@@ -1685,6 +1686,87 @@ ipc_status ipc_profile_read(ipc_scene* s, int32_t fam, int64_t* launches, double
   if (launches) *launches = s->prof_launches[fam];
   if (ms) *ms = t;
   if (work) *work = (double)u[fam];
+  API_END
+}
+
+// ---- allocation-free Neo-Hookean energy: scratch in a file-scope device array
+static __device__ __align__(256) double g_noalloc_tet_energy[IPC_NOALLOC_MAX_TETS];
+static double* g_noalloc_ptr[256] = {nullptr};
+static std::mutex g_noalloc_mutex;
+
+// per-tet energy into the scratch array (same tet_energy as the scene path); the group of a tet
+// is found by binary search in the offsets; an inverted tet flags its group
+__global__ void k_noalloc_tet_energy(int n_tets, const int4* __restrict__ tets, const double* __restrict__ prm,
+                                     const double* __restrict__ x, int n_groups, const int* __restrict__ goff, double h2,
+                                     double* __restrict__ tE, int* __restrict__ inverted) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tets) return;
+  int lo = 0, hi = n_groups - 1;  // last group g with goff[g] <= t
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (goff[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  int4 T = tets[t];
+  const double* P = prm + 12L * t;
+  double F[9], cof[9], J;
+  double En = tet_energy(ld3(x, T.x), ld3(x, T.y), ld3(x, T.z), ld3(x, T.w), P, P[10], P[11], h2 * P[9], F, cof, &J);
+  if (!(J > 0.0)) {
+    inverted[lo] = 1;
+    En = 0.0;
+  }
+  tE[t] = En;
+}
+__global__ void k_noalloc_clear(int n, int* __restrict__ a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = 0;
+}
+// one block per group, the same strided fixed-order block reduction as the scene path
+__global__ void k_noalloc_group_sum(int n_groups, const int* __restrict__ goff, const double* __restrict__ tE,
+                                    double* __restrict__ out) {
+  __shared__ double sh[256];
+  int g = blockIdx.x;
+  if (g >= n_groups) return;
+  double s = 0.0;
+  for (int i = goff[g] + threadIdx.x; i < goff[g + 1]; i += blockDim.x) s += tE[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[g] = s;
+}
+
+ipc_status ipc_elastic_energy_noalloc(int32_t n_tets, const int32_t* tets, const double* tet_params, const double* x,
+                                      int32_t n_groups, const int32_t* group_offsets, double h2, double* energy,
+                                      int32_t* inverted, void* stream) {
+  API_BEGIN
+  if (n_tets < 0 || n_groups <= 0 || !group_offsets || !energy || !inverted || (n_tets > 0 && (!tets || !tet_params || !x)))
+    fail_with(IPC_ERR_ARG, "ipc_elastic_energy_noalloc: null pointer or bad count");
+  if (n_tets > IPC_NOALLOC_MAX_TETS)
+    fail_with(IPC_ERR_ARG, "ipc_elastic_energy_noalloc: " + std::to_string(n_tets) + " tets exceed the maximum of " +
+                               std::to_string(IPC_NOALLOC_MAX_TETS));
+  if (n_groups > IPC_NOALLOC_MAX_GROUPS)
+    fail_with(IPC_ERR_ARG, "ipc_elastic_energy_noalloc: more than " + std::to_string(IPC_NOALLOC_MAX_GROUPS) + " groups");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) fail_with(IPC_ERR_ARG, "ipc_elastic_energy_noalloc: device ordinal out of range");
+  double* scratch;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {  // once per device, with that device current
+      void* p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_noalloc_tet_energy));
+      g_noalloc_ptr[dev] = (double*)p;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  k_noalloc_clear<<<(n_groups + 255) / 256, 256, 0, st>>>(n_groups, inverted);
+  CK(cudaGetLastError());
+  if (n_tets > 0) {
+    k_noalloc_tet_energy<<<(n_tets + 127) / 128, 128, 0, st>>>(n_tets, (const int4*)tets, tet_params, x, n_groups,
+                                                               group_offsets, h2, scratch, inverted);
+    CK(cudaGetLastError());
+  }
+  k_noalloc_group_sum<<<n_groups, 256, 0, st>>>(n_groups, group_offsets, scratch, energy);
+  CK(cudaGetLastError());
   API_END
 }
 

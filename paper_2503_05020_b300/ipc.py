@@ -82,6 +82,7 @@ def lib() -> C.CDLL:
             "ipc_set_next_targets": [vp, vp, sz], "ipc_get_all_dofs": [vp, vp, sz, vp],
             "ipc_env_estimate_bytes": [vp, i32, vp], "ipc_launch_count": [vp, vp],
             "ipc_profile_enable": [vp, i32], "ipc_profile_read": [vp, i32, vp, vp, vp],
+            "ipc_elastic_energy_noalloc": [i32, vp, vp, vp, i32, vp, C.c_double, vp, vp, vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
