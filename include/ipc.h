@@ -68,7 +68,9 @@ typedef struct {
   int32_t precision;     /* ipc_precision */
   uint64_t hbm_budget_bytes; /* 0 = no admission limit */
   int32_t device;        /* CUDA device ordinal */
-  int32_t pad;
+  int32_t pcg_cluster;   /* PCG launch shape: 0 = automatic, 1/2/4/8 = one persistent cluster of
+                            that many CTAs per environment, -1 = one launch per PCG phase over
+                            tiles of all environments */
   void* cuda_stream;     /* cudaStream_t to borrow, or NULL for a library-owned stream */
 } ipc_scene_desc;
 
@@ -126,10 +128,12 @@ typedef enum {
   IPC_Q_SIZES = 7,       /* int64[8]: ndof, points, surface vertices, edges, triangles, tets,
                             bodies, steps */
   IPC_Q_INTERSECTIONS = 8, /* int64[2]: segment-triangle intersections, inverted tets */
-  IPC_Q_SCENE_COUNTERS = 9 /* int64[8] for the whole scene (env_id ignored), from the last Newton
+  IPC_Q_SCENE_COUNTERS = 9 /* int64[10] for the whole scene (env_id ignored), from the last Newton
                               iteration: contacts, point-triangle contacts, friction stencils,
                               stencil-node incidence entries, longest node incidence list,
-                              candidates, BSR blocks, sliced-ELL padded blocks */
+                              candidates, BSR blocks, sliced-ELL padded blocks; then the PCG
+                              cluster size in use (0 = tiled multi-launch PCG) and the most
+                              32-row slices of one environment */
 } ipc_query_kind;
 
 /* Create / destroy a scene on desc->device. */
@@ -224,7 +228,8 @@ typedef enum {
   IPC_PROF_BROAD = 5,       /* constraint-set traversal, narrow phase */
   IPC_PROF_ASSEMBLY = 6,    /* gradient / BSR gather, preconditioner blocks, stencil incidence */
   IPC_PROF_LS_ENERGY = 7,   /* energy-only evaluation of line-search trials */
-  IPC_PROF_COUNT = 8
+  IPC_PROF_PCG_SOLVE = 8,   /* persistent per-environment PCG (whole solve in one launch) */
+  IPC_PROF_COUNT = 9
 } ipc_prof_family;
 /* Turn profiling on (1) or off (0); turning it on clears the counters. */
 ipc_status ipc_profile_enable(ipc_scene* scene, int32_t on);

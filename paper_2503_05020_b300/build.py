@@ -9,7 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libipc_b300.so")
 SOURCES = ["ipc_api.cu"]
-HEADERS = ["common.cuh", "geometry.cuh", "lbvh.cuh", "energy.cuh", "solver.cuh", "kernels_misc.cuh", "dist_poly.cuh"]
+HEADERS = ["common.cuh", "geometry.cuh", "lbvh.cuh", "energy.cuh", "solver.cuh", "kernels_misc.cuh", "dist_poly.cuh",
+           "pcg_cluster.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -21,6 +21,7 @@
 #include "energy.cuh"
 #include "solver.cuh"
 #include "kernels_misc.cuh"
+#include "pcg_cluster.cuh"
 
 namespace {
 
@@ -342,6 +343,8 @@ struct ipc_scene {
 
   // ---------------- layout sizes
   int E = 0, NN = 0, NB = 0, NT = 0, NP = 0, NSV = 0, NED = 0, NTR = 0, NTILE = 0, NNZB = 0;
+  int max_env_slices = 0, n_slices = 0;
+  int pcg_C = 0;  // CTAs per environment cluster of the persistent PCG (0: tiled multi-launch PCG)
   long sell_nval = 0;
   std::vector<int> ids;  // layout index -> env id
   std::vector<int> h_node_off, h_tet_off, h_pt_off, h_sv_off, h_ed_off, h_tri_off, h_body_off, h_tile_off;
@@ -362,7 +365,7 @@ struct ipc_scene {
   DBuf<int> sv_pt, sv_env, ed_pt, ed_env, tri_pt, tri_env;
   DBuf<double> ed_rest2;
   DBuf<int> bsr_ptr, bsr_col, blk_row, blk_ptr, blk_src, nt_ptr, nt_src;
-  DBuf<int> tile_slice, slice_w, sell_col;
+  DBuf<int> tile_slice, slice_w, sell_col, pslice_off, pslice_row, pslice_sel;
   DBuf<long> slice_vbase, slice_cbase, blk_pos, diag_pos;
   // ---------------- state
   DBuf<double> x, v, xt, xtilde, xtarget, xtrial, p, pbar, grad;
@@ -378,6 +381,7 @@ struct ipc_scene {
   DBuf<double> bsr_val, Ps, Pb;
   DBuf<double> pcg_r, pcg_z, pcg_d, pcg_y, pcg_x, part_a, part_b, part_c, pcg_rz, pcg_bb;
   DBuf<int> pcg_it, pcg_active;
+  DBuf<double> pcg_part;  // per-slot partial sums of the persistent PCG
   DBuf<uint8_t> pcg_run;
   // trees
   struct TreeBufs {
@@ -770,7 +774,7 @@ struct ipc_scene {
     }
     // sliced ELL of the soft rows: 32-row slices inside each soft tile, padded to the slice's
     // longest row; block kk, element e of lane l at vbase + (kk*9 + e)*32 + l
-    std::vector<int> tslice(te.size(), -1), sw;
+    std::vector<int> tslice(te.size(), -1), sw, row_sel(NN, -1);
     std::vector<long> svb, scb, bpos(NNZB, -1), dpos(NN, -1);
     std::vector<int> scol;
     long vtot = 0, ctot = 0;
@@ -787,6 +791,10 @@ struct ipc_scene {
         scol.resize(ctot + 32L * w, -1);
         for (int r = r0; r < r1; ++r) {
           int lane = r - r0;
+          row_sel[r] = 32 * ((int)sw.size() - 1) + lane;
+          // padding blocks of a row point at the row itself with zero values, so the product
+          // loop needs no branch (the values stay zero: assembly writes only real blocks)
+          for (int kk = bptr[r + 1] - bptr[r]; kk < w; ++kk) scol[ctot + 32L * kk + lane] = r;
           for (int k = bptr[r]; k < bptr[r + 1]; ++k) {
             int kk = k - bptr[r];
             scol[ctot + 32L * kk + lane] = bcol[k];
@@ -801,6 +809,33 @@ struct ipc_scene {
     // ---------- upload
     cudaStream_t s = stream;
     tile_slice.upload(tslice, s);
+    // free soft rows of each env in node order, in chunks of 32 (the persistent PCG's slices):
+    // kinematic rows have r = 0 and a zero preconditioner block, so their d, z stay 0 and the
+    // solve never needs them
+    {
+      std::vector<int> prow, psel, poff(E + 1, 0);
+      std::vector<std::vector<int>> free_rows(E);
+      for (size_t ti = 0; ti < te.size(); ++ti)
+        if (tk[ti] == 0)
+          for (int r = tb[ti]; r < tn[ti]; ++r)
+            if (!node_kin_h[r]) free_rows[te[ti]].push_back(r);
+      for (int li = 0; li < E; ++li) {
+        int nf = (int)free_rows[li].size(), nch = (nf + 31) / 32;
+        for (int q = 0; q < 32 * nch; ++q) {
+          int r = q < nf ? free_rows[li][q] : -1;
+          prow.push_back(r);
+          psel.push_back(r >= 0 ? row_sel[r] : -1);
+        }
+        poff[li + 1] = poff[li] + nch;
+      }
+      n_slices = poff[E];
+      max_env_slices = 0;
+      for (int li = 0; li < E; ++li) max_env_slices = std::max(max_env_slices, poff[li + 1] - poff[li]);
+      pslice_off.upload(poff, s);
+      pslice_row.upload(prow, s);
+      pslice_sel.upload(psel, s);
+      pcg_part.alloc(6 * ((size_t)n_slices + NB) + 6);
+    }
     slice_w.upload(sw, s);
     slice_vbase.upload(svb, s);
     slice_cbase.upload(scb, s);
@@ -850,6 +885,7 @@ struct ipc_scene {
     tile_begin.upload(tb, s);
     tile_end.upload(tn, s);
     tile_off.upload(toff, s);
+    pcg_C = choose_pcg_cluster();
     root_off_tri.upload(tri_off_h, s);
     root_off_ed.upload(ed_off_h, s);
     bsr_ptr.upload(bptr, s);
@@ -865,6 +901,8 @@ struct ipc_scene {
     for (DBuf<double>* b : {&xt, &xtilde, &xtarget, &xtrial, &p, &pbar, &grad, &pcg_r, &pcg_z, &pcg_d, &pcg_y, &pcg_x})
       b->alloc(n3);
     xtarget.zero(s);
+    // the persistent PCG never writes kinematic soft rows: their d (read by neighbours) stays 0
+    for (DBuf<double>* b : {&pcg_r, &pcg_z, &pcg_d, &pcg_y, &pcg_x}) b->zero(s);
     for (DBuf<double>* b : {&ptx, &ptx_t, &ptp, &pte}) b->alloc(3 * (size_t)NP);
     e_status.upload(status_h, s);
     e_reason.upload(reason_h, s);
@@ -887,6 +925,7 @@ struct ipc_scene {
     body_g.alloc(12 * (size_t)NB);
     body_H.alloc(144 * (size_t)NB);
     bsr_val.alloc(std::max(sell_nval, 1L));
+    bsr_val.zero(s);  // padding blocks must read as zero
     Ps.alloc(9 * (size_t)NN);
     Pb.alloc(144 * (size_t)NB);
     for (DBuf<double>* b : {&part_a, &part_b, &part_c}) b->alloc(NTILE);
@@ -1084,7 +1123,7 @@ struct ipc_scene {
   // y = H d over the envs in run (stencil product, then BSR/body rows); partial d.y per tile
   void matvec(const uint8_t* run, const double* d, double* y, double* part) {
     int ns = n_ct + n_fr;
-    launch(k_stencil_mv, ns, 128, ns, layout(), (const int*)st_env.p, (const int*)st_pts.p, run, (const double*)sH.p, d,
+    launch(k_stencil_mv, 16L * ns, 128, ns, layout(), (const int*)st_env.p, (const int*)st_pts.p, run, (const double*)sH.p, d,
            st_t.p);
     pbeg(IPC_PROF_SPMV);
     launch_grid(k_spmv, NTILE, TILE, tiles(), layout(), spmv_args(), run, d, y, part, punits(IPC_PROF_SPMV));
@@ -1092,7 +1131,80 @@ struct ipc_scene {
   }
 
   // ------------------------------------------------------------------ PCG
+  // Clusters that can be resident at once for a cluster size C (occupancy of k_pcg_cluster<C>).
+  template <int C>
+  int resident_clusters() {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(C * std::max(E, 1)));
+    cfg.blockDim = dim3(PCG_THREADS);
+    cfg.stream = stream;
+    int n = 0;
+    CK(cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<C>, &cfg));
+    return n;
+  }
+  // Persistent-PCG cluster size: the caller's choice, else the largest C <= 8 whose clusters
+  // are all resident at once and whose warps the largest env can still keep busy (one 32-row
+  // slice per warp or more).
+  int choose_pcg_cluster() {
+    int want = desc.pcg_cluster;
+    if (want < 0 || E == 0) return 0;
+    if (want > 0) return want;
+    int useful = 1;
+    while (useful < 8 && useful * PCG_WARPS < max_env_slices) useful *= 2;
+    for (int C = useful; C > 1; C /= 2) {
+      int n = C == 8 ? resident_clusters<8>() : C == 4 ? resident_clusters<4>() : resident_clusters<2>();
+      if (n >= E) return C;
+    }
+    return 1;
+  }
+  template <int C>
+  void launch_pcg_cluster(const PcgClusterArgs& a) {
+    launch_grid(k_pcg_cluster<C>, (long)C * E, PCG_THREADS, a);
+  }
+  // one launch per solve: every env in act runs its PCG to its own stop inside its cluster
+  void pcg_persistent(const uint8_t* act) {
+    PcgClusterArgs a;
+    a.L = layout();
+    a.A = spmv_args();
+    a.pslice_off = pslice_off.p;
+    a.pslice_row = pslice_row.p;
+    a.pslice_sel = pslice_sel.p;
+    a.body_off = body_off.p;
+    a.st_env = st_env.p;
+    a.sH = sH.p;
+    int b[5] = {0, n_ct_pt, n_ct, n_ct + n_fr_pt, n_ct + n_fr};
+    for (int i = 0; i < 5; ++i) a.st_bounds[i] = b[i];
+    a.Ps = Ps.p;
+    a.Pb = Pb.p;
+    a.act = act;
+    a.x = pcg_x.p;
+    a.r = pcg_r.p;
+    a.z = pcg_z.p;
+    a.d = pcg_d.p;
+    a.y = pcg_y.p;
+    a.st_t = st_t.p;
+    a.tol2 = desc.pcg_rel_tol * desc.pcg_rel_tol;
+    a.max_it = desc.max_pcg_iters;
+    a.part = pcg_part.p;
+    a.s_total = n_slices;
+    a.n_bodies = NB;
+    a.stats = e_stats.p;
+    a.bytes = punits(IPC_PROF_PCG_SOLVE);
+    pbeg(IPC_PROF_PCG_SOLVE);
+    switch (pcg_C) {
+      case 1: launch_pcg_cluster<1>(a); break;
+      case 2: launch_pcg_cluster<2>(a); break;
+      case 4: launch_pcg_cluster<4>(a); break;
+      case 8: launch_pcg_cluster<8>(a); break;
+      default: fail_with(IPC_ERR_ARG, "pcg_cluster must be -1, 0, 1, 2, 4 or 8");
+    }
+    pend(IPC_PROF_PCG_SOLVE);
+  }
   void pcg(const uint8_t* act) {
+    if (pcg_C > 0) {
+      pcg_persistent(act);
+      return;
+    }
     PcgState S{pcg_rz.p, pcg_bb.p, pcg_it.p, pcg_run.p, pcg_active.p, e_stats.p + 0};
     // per-env cumulative iterations live in e_stats[5e + 1]: pass a strided view via a kernel
     CK(cudaMemsetAsync(pcg_active.p, 0, sizeof(int), stream));
@@ -1310,6 +1422,11 @@ ipc_status ipc_scene_create(const ipc_scene_desc* desc, ipc_scene** out) {
   if (!desc || !out) fail_with(IPC_ERR_ARG, "null argument");
   if (!(desc->dt > 0) || !(desc->dhat > 0) || !(desc->kappa > 0)) fail_with(IPC_ERR_ARG, "dt, dhat and kappa must be > 0");
   if (desc->precision != IPC_FP64 && desc->precision != IPC_MIXED) fail_with(IPC_ERR_ARG, "unknown precision");
+  {
+    int c = desc->pcg_cluster;
+    if (c != -1 && c != 0 && c != 1 && c != 2 && c != 4 && c != 8)
+      fail_with(IPC_ERR_ARG, "pcg_cluster must be -1, 0, 1, 2, 4 or 8");
+  }
   std::unique_ptr<ipc_scene> s(new ipc_scene());
   s->desc = *desc;
   if (s->desc.max_newton <= 0) s->desc.max_newton = 100;
@@ -1534,8 +1651,8 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       CK(cudaMemcpy(ptr.data(), s->ns_ptr.p, (s->NN + 1) * 4, cudaMemcpyDeviceToHost));
       long long mx = 0;
       for (int i = 0; i < s->NN; ++i) mx = std::max(mx, (long long)(ptr[i + 1] - ptr[i]));
-      long long v[8] = {s->n_ct, s->n_ct_pt, s->n_fr, s->n_inc, mx, (long long)s->n_pt + s->n_ee, s->NNZB,
-                        s->sell_nval / 288};
+      long long v[10] = {s->n_ct, s->n_ct_pt, s->n_fr, s->n_inc, mx, (long long)s->n_pt + s->n_ee, s->NNZB,
+                         s->sell_nval / 288, s->pcg_C, s->max_env_slices};
       return copy_out(v, sizeof(v), out, out_bytes, written);
     }
     case IPC_Q_SIZES: {

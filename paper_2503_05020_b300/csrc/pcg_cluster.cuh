@@ -1,0 +1,346 @@
+// Persistent per-environment PCG: one thread-block cluster per environment runs the whole
+// block-Jacobi conjugate-gradient solve of that environment (Sec. III-A: one linear solve per
+// environment, each with its own scalars and its own stop). The cluster's CTAs synchronise with
+// hardware cluster barriers; there is no host round trip and no launch per iteration.
+//
+// Work split inside a cluster: stencil products go to half-warps round-robin over the cluster; the
+// env's free soft rows, in chunks of 32 (one row per lane), are dealt to warps round-robin, the
+// same way in every phase, so a row's x, r, y, z entries are only touched by its owner thread; a
+// rigid body belongs to CTA (body index mod C), its 12 DOFs to that CTA's threads 0..11.
+// Kinematic soft rows are never visited: their right-hand side and preconditioner block are
+// zero, so their d and z stay zero (d is zeroed when the buffers are laid out).
+//
+// Determinism: every dot product is summed per slot (a slice: warp butterfly over its 32 rows; a
+// body: fixed CTA tree), and the env's slots are added in a fixed order that depends on the env
+// alone. So the results are the same bits for every cluster size and every batch the env is in.
+// Vectors that other CTAs write inside the kernel (d, t, the slot partials) are read with
+// L2-coherent loads after the cluster barrier that publishes them.
+#pragma once
+#include <cooperative_groups.h>
+
+#include "kernels_misc.cuh"
+#include "solver.cuh"
+
+namespace cg = cooperative_groups;
+
+constexpr int PCG_THREADS = 256;
+constexpr int PCG_WARPS = PCG_THREADS / 32;
+
+struct PcgClusterArgs {
+  Layout L;
+  SpmvArgs A;
+  const int* pslice_off;  // per env: first slice of its free soft rows (n_env + 1 entries)
+  const int* pslice_row;  // 32 per slice: the row (node), -1 for padding
+  const int* pslice_sel;  // 32 per slice: sliced-ELL slice * 32 + lane of that row
+  const int* body_off;    // per env: first body (n_env + 1 entries)
+  const int* st_env;
+  const double* sH;
+  int st_bounds[5];       // stencil sublists [pt | ee | friction pt | friction ee], each env-sorted
+  const double* Ps;
+  const double* Pb;
+  const uint8_t* act;
+  double* x;              // solution (delta), out
+  double* r;              // in: right-hand side; out: residual
+  double* z;
+  double* d;
+  double* y;
+  double* st_t;           // stencil products (the same buffer SpmvArgs reads)
+  double tol2;
+  int max_it;
+  double* part;               // slot partials: 2 x 3 doubles x (s_total + n_bodies)
+  int s_total;                // slices of the whole batch
+  int n_bodies;               // rigid bodies of the whole batch
+  long long* stats;           // 5 per env; [STAT_PCG] += iterations of this solve
+  unsigned long long* bytes;  // algorithmic bytes of all iterations (may be null)
+};
+
+// Sum of an env's slot partials (its slices, then its bodies) in a fixed order that depends on
+// the env alone: lane l of warp 0 adds slots l, l + 32, ... and the lanes are combined by a fixed
+// butterfly. Every CTA of the cluster computes the same bits; the result is broadcast through
+// shared memory. Call after a cluster barrier that publishes the partials.
+template <int K>
+DEV void env_sum(const double* part, int S0, int S1, int s_total, int b0, int b1, double* tot, double (&v)[K]) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x, ns = S1 - S0, n = ns + (b1 - b0);
+    double s[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) s[q] = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      long slot = j < ns ? S0 + j : (long)s_total + b0 + (j - ns);
+#pragma unroll
+      for (int q = 0; q < K; ++q) s[q] += __ldcg(part + 3 * slot + q);
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      s[q] = warp_sum(s[q]);
+      if (lane == 0) tot[q] = s[q];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = tot[q];
+}
+
+// y row of one free soft node (sliced-ELL blocks at sel = slice * 32 + lane, plus its stencil
+// entries); returns d_row . y_row
+DEV double soft_row_cg(const SpmvArgs& A, int sel, int row, const double* d, double* y) {
+  const int slice = sel >> 5, lane = sel & 31;
+  d3 acc = mk3(0, 0, 0);
+  int w = A.S.width[slice];
+  const int* col = A.S.col + A.S.cbase[slice] + lane;
+  const double* V = A.S.val + A.S.vbase[slice] + lane;
+#pragma unroll 4
+  for (int kk = 0; kk < w; ++kk) {
+    int c = col[32 * kk];  // padding blocks: the row itself, zero values
+    d3 dv = ldcg3(d, c);
+    const double* B = V + 288L * kk;
+    acc = acc + mk3(B[0] * dv.x + B[32] * dv.y + B[64] * dv.z, B[96] * dv.x + B[128] * dv.y + B[160] * dv.z,
+                    B[192] * dv.x + B[224] * dv.y + B[256] * dv.z);
+  }
+  int k = A.ns_ptr[row], end = A.ns_ptr[row + 1];
+#pragma unroll 4
+  for (; k < end; ++k) acc = acc + A.ns_w[k] * ldcg3(A.st_t, A.ns_src[k]);
+  st3(y, row, acc);
+  return dot(acc, ldcg3(d, row));
+}
+
+// Algorithmic bytes of one PCG iteration, per item. A soft row: its sliced-ELL blocks and
+// stencil entries as in the stand-alone product (76 B per block, 36 B per entry, 8 B row
+// pointers, 24 B d and 24 B y), plus the vector phase: x, r read and written (96 B), d, y read
+// (48 B), the 3x3 preconditioner block (72 B), z written (24 B), then d = z + beta d (72 B).
+// A rigid body: dense block 1152 B, its d and y (192 B), 52 B per p-node entry, the 12x12
+// preconditioner (1152 B) and 12 DOFs x 80 B of vector traffic. A stencil: packed Hessian
+// (624 B), 4 point indices (16 B), 4 gathered d triples (96 B) and t written (96 B).
+DEV double soft_iter_bytes(const SpmvArgs& A, int row) {
+  return 76.0 * (A.bsr_ptr[row + 1] - A.bsr_ptr[row]) + 56.0 + 8.0 + 36.0 * (A.ns_ptr[row + 1] - A.ns_ptr[row]) +
+         312.0;
+}
+DEV double body_iter_bytes(const Layout& L, const SpmvArgs& A, int b) {
+  long base = L.body_node[b];
+  return 1344.0 + 52.0 * (A.ns_ptr[base + 1] - A.ns_ptr[base]) + 1152.0 + 960.0;
+}
+constexpr double STENCIL_ITER_BYTES = 624.0 + 16.0 + 96.0 + 96.0;
+
+template <int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int e = blockIdx.x / C;
+  if (!P.act[e]) return;  // uniform over the cluster: every CTA leaves
+  __shared__ double wred[PCG_WARPS][12];
+  __shared__ double tot[4];
+  __shared__ double sbody[12];
+  __shared__ int srange[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gwarp = rank * PCG_WARPS + warp, nwarps = C * PCG_WARPS;
+  const int gth = rank * PCG_THREADS + tid, nth = C * PCG_THREADS;
+  const Layout& L = P.L;
+  const int S0 = P.pslice_off[e], S1 = P.pslice_off[e + 1];
+  const int b0 = P.body_off[e], b1 = P.body_off[e + 1];
+  const int ST = P.s_total;
+  double* part_dy = P.part;                              // 3 doubles per slot, [0] used
+  double* part_rz = P.part + 3L * (P.s_total + P.n_bodies);  // (r.z, r.r, bytes) per slot
+  if (tid < 4) {  // this env's range in each stencil sublist
+    int lo = P.st_bounds[tid], hi = P.st_bounds[tid + 1];
+    srange[2 * tid] = lower_env(P.st_env, lo, hi, e);
+    srange[2 * tid + 1] = lower_env(P.st_env, lo, hi, e + 1);
+  }
+  __syncthreads();
+
+  // ---- z = M^-1 r, d = z, x = 0; per-slot (r.z, r.r) and the bytes of one iteration
+  for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {  // warp-uniform
+    double a = 0.0, c = 0.0, nb = 0.0;
+    const int i = P.pslice_row[32 * sl + lane];
+    if (i >= 0) {
+      precond_soft(i, P.Ps, P.r, P.z, &a, &c);
+      for (int k = 3 * i; k < 3 * i + 3; ++k) {
+        P.d[k] = P.z[k];
+        P.x[k] = 0.0;
+      }
+      if (P.bytes) nb = soft_iter_bytes(P.A, i);
+    }
+    a = warp_sum(a);
+    c = warp_sum(c);
+    nb = warp_sum(nb);
+    if (lane == 0) {
+      part_rz[3L * sl] = a;
+      part_rz[3L * sl + 1] = c;
+      part_rz[3L * sl + 2] = nb;
+    }
+  }
+  for (int b = b0; b < b1; ++b) {
+    if (rank != (b - b0) % C) continue;  // CTA-uniform
+    long base3 = 3L * L.body_node[b];
+    if (tid < 12) sbody[tid] = P.r[base3 + tid];
+    __syncthreads();
+    double a, c;
+    precond_body(P.Pb, b, sbody, base3, P.z, &a, &c);
+    if (tid < 12) {
+      P.d[base3 + tid] = P.z[base3 + tid];
+      P.x[base3 + tid] = 0.0;
+    }
+    if (warp == 0) {
+      a = warp_sum(a);
+      c = warp_sum(c);
+      if (lane == 0) {
+        long slot = (long)ST + b;
+        part_rz[3 * slot] = a;
+        part_rz[3 * slot + 1] = c;
+        double nb = P.bytes ? body_iter_bytes(L, P.A, b) : 0.0;
+        if (b == b0)  // the env's stencils are counted once, on its first body slot
+          nb += STENCIL_ITER_BYTES * (srange[1] - srange[0] + srange[3] - srange[2] + srange[5] - srange[4] +
+                                      srange[7] - srange[6]);
+        part_rz[3 * slot + 2] = P.bytes ? nb : 0.0;
+      }
+    }
+    __syncthreads();
+  }
+  cl.sync();
+  double v3[3];
+  env_sum<3>(part_rz, S0, S1, ST, b0, b1, tot, v3);
+  double rz = v3[0];
+  const double bb = v3[1];
+  double iter_bytes = v3[2];
+  if (P.bytes && b1 == b0)  // an env without bodies: its stencils
+    iter_bytes += STENCIL_ITER_BYTES * (srange[1] - srange[0] + srange[3] - srange[2] + srange[5] - srange[4] +
+                                        srange[7] - srange[6]);
+  int it = 0;
+  bool go = bb > 0.0 && isfinite(bb);
+  while (go) {
+    // ---- t_s = H_s (P_s d) for the env's stencils (the barrier publishes every CTA's d)
+    cl.sync();
+    for (int q = 0; q < 4; ++q)  // one half-warp per stencil (warp-uniform loop)
+      for (int s0 = srange[2 * q] + 2 * gwarp; s0 < srange[2 * q + 1]; s0 += 2 * nwarps) {
+        int s = s0 + (lane >> 4);
+        stencil_product_hw<true>(L, P.A.st_pts, P.sH, P.d, P.st_t, s, s < srange[2 * q + 1]);
+      }
+    cl.sync();
+    // ---- y = A d: soft rows, one partial d.y per slice
+    for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {
+      double dy = 0.0;
+      const int i = P.pslice_row[32 * sl + lane];
+      if (i >= 0) dy = soft_row_cg(P.A, P.pslice_sel[32 * sl + lane], i, P.d, P.y);
+      dy = warp_sum(dy);
+      if (lane == 0) part_dy[3L * sl] = dy;
+    }
+    // ---- rigid bodies on their owner CTA: stencil entries gathered by its threads in a fixed
+    // partition, the dense 12x12 block, one partial d.y per body
+    for (int b = b0; b < b1; ++b) {
+      if (rank != (b - b0) % C) continue;  // CTA-uniform
+      long base = L.body_node[b];
+      bool kin = L.body_kin[b];
+      double acc[12];
+      for (int q = 0; q < 12; ++q) acc[q] = 0.0;
+      if (!kin) {
+        int kb = P.A.ns_ptr[base], ke = P.A.ns_ptr[base + 1];
+        for (int k = kb + tid; k < ke; k += PCG_THREADS) {
+          d3 tv = ldcg3(P.A.st_t, P.A.ns_src[k]);
+          const double* xb = P.A.ns_xb + 3L * k;
+          double w1 = xb[0], w2 = xb[1], w3 = xb[2];
+          acc[0] += tv.x;
+          acc[1] += tv.y;
+          acc[2] += tv.z;
+          acc[3] += w1 * tv.x;
+          acc[4] += w1 * tv.y;
+          acc[5] += w1 * tv.z;
+          acc[6] += w2 * tv.x;
+          acc[7] += w2 * tv.y;
+          acc[8] += w2 * tv.z;
+          acc[9] += w3 * tv.x;
+          acc[10] += w3 * tv.y;
+          acc[11] += w3 * tv.z;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        double sq = warp_sum(acc[q]);
+        if (lane == 0) wred[warp][q] = sq;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double dyb = 0.0;
+        if (lane < 12) {
+          double v = 0.0;
+          if (!kin) {
+            for (int w = 0; w < PCG_WARPS; ++w) v += wred[w][lane];
+            const double* H = P.A.bH + 144L * b + 12 * lane;
+            for (int j = 0; j < 12; ++j) v += H[j] * __ldcg(P.d + 3 * base + j);
+          }
+          P.y[3 * base + lane] = v;
+          dyb = v * __ldcg(P.d + 3 * base + lane);
+        }
+        dyb = warp_sum(dyb);
+        if (lane == 0) part_dy[3 * ((long)ST + b)] = dyb;
+      }
+      __syncthreads();
+    }
+    cl.sync();
+    double dy[1];
+    env_sum<1>(part_dy, S0, S1, ST, b0, b1, tot, dy);
+    const double alpha = dy[0] > 0.0 ? rz / dy[0] : 0.0;
+    // ---- x += alpha d; r -= alpha y; z = M^-1 r (owner threads only)
+    for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {
+      double a = 0.0, c = 0.0;
+      const int i = P.pslice_row[32 * sl + lane];
+      if (i >= 0) {
+        for (int k = 3 * i; k < 3 * i + 3; ++k) {
+          P.x[k] += alpha * P.d[k];
+          P.r[k] -= alpha * P.y[k];
+        }
+        precond_soft(i, P.Ps, P.r, P.z, &a, &c);
+      }
+      a = warp_sum(a);
+      c = warp_sum(c);
+      if (lane == 0) {
+        part_rz[3L * sl] = a;
+        part_rz[3L * sl + 1] = c;
+      }
+    }
+    for (int b = b0; b < b1; ++b) {
+      if (rank != (b - b0) % C) continue;  // CTA-uniform
+      long base3 = 3L * L.body_node[b];
+      if (tid < 12) {
+        long k = base3 + tid;
+        P.x[k] += alpha * P.d[k];
+        double rv = P.r[k] - alpha * P.y[k];
+        P.r[k] = rv;
+        sbody[tid] = rv;
+      }
+      __syncthreads();
+      double a, c;
+      precond_body(P.Pb, b, sbody, base3, P.z, &a, &c);
+      if (warp == 0) {
+        a = warp_sum(a);
+        c = warp_sum(c);
+        if (lane == 0) {
+          part_rz[3 * ((long)ST + b)] = a;
+          part_rz[3 * ((long)ST + b) + 1] = c;
+        }
+      }
+      __syncthreads();
+    }
+    cl.sync();
+    double u2[2];
+    env_sum<2>(part_rz, S0, S1, ST, b0, b1, tot, u2);
+    const double rz_new = u2[0], rr = u2[1];
+    ++it;
+    if (rr <= P.tol2 * bb || it >= P.max_it || !(dy[0] > 0.0) || !isfinite(rr)) break;
+    const double beta = rz > 0.0 ? rz_new / rz : 0.0;
+    rz = rz_new;
+    // ---- d = z + beta d (owner threads)
+    for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {
+      const int i = P.pslice_row[32 * sl + lane];
+      if (i >= 0)
+        for (int k = 3 * i; k < 3 * i + 3; ++k) P.d[k] = P.z[k] + beta * P.d[k];
+    }
+    for (int b = b0; b < b1; ++b)
+      if (rank == (b - b0) % C && tid < 12) {
+        long k = 3L * L.body_node[b] + tid;
+        P.d[k] = P.z[k] + beta * P.d[k];
+      }
+  }
+  if (rank == 0 && tid == 0) {
+    P.stats[5 * e + STAT_PCG] += it;
+    if (P.bytes) atomicAdd(P.bytes, (unsigned long long)(iter_bytes * it));
+  }
+}

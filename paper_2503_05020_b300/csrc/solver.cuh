@@ -204,26 +204,49 @@ __global__ void k_precond_body(int n_bodies, Layout L, const int* __restrict__ b
 }
 
 // ---------------------------------------------------------------- matrix-free stencil product
-// t_s = H_s (P_s d) for every stencil of an env whose solve is still running
+// L2-coherent loads, for vectors that other CTAs write while a kernel runs
+DEV d3 ldcg3(const double* p, long i) { return d3{__ldcg(p + 3 * i), __ldcg(p + 3 * i + 1), __ldcg(p + 3 * i + 2)}; }
+DEV d3 point_gather_cg(const Layout& L, int pt, const double* v) {
+  int nd = L.pt_node[pt];
+  if (nd >= 0) return ldcg3(v, nd);
+  long base = L.body_node[-1 - nd];
+  const double* xb = L.pt_xb + 3 * pt;
+  return ldcg3(v, base) + xb[0] * ldcg3(v, base + 1) + xb[1] * ldcg3(v, base + 2) + xb[2] * ldcg3(v, base + 3);
+}
+
+// t_s = H_s (P_s d) for stencil s by the 16 lanes of a half-warp (H_s: packed upper triangle,
+// 78 doubles). Every lane of the warp calls it (shuffles); ok = false idles a half. Lanes 0..3
+// gather the stencil's points, the 12 entries of P_s d reach every lane by shuffles, and lane
+// i < 12 forms row i from 12 independent loads, summed in column order.
+template <bool CG>
+DEV void stencil_product_hw(const Layout& L, const int* __restrict__ st_pts, const double* __restrict__ sH,
+                            const double* d, double* st_t, int s, bool ok) {
+  const int lane = threadIdx.x & 31, half = lane & 16, l = lane & 15;
+  d3 v = mk3(0, 0, 0);
+  if (ok && l < 4) v = CG ? point_gather_cg(L, st_pts[4 * s + l], d) : point_gather(L, st_pts[4 * s + l], d);
+  double u[12];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    u[3 * a] = __shfl_sync(0xffffffffu, v.x, half + a);
+    u[3 * a + 1] = __shfl_sync(0xffffffffu, v.y, half + a);
+    u[3 * a + 2] = __shfl_sync(0xffffffffu, v.z, half + a);
+  }
+  if (ok && l < 12) {
+    const double* H = sH + 78L * s;
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc += H[sym_idx(l, j, 12)] * u[j];
+    st_t[12L * s + l] = acc;
+  }
+}
+
+// every stencil of an env whose solve is still running; one half-warp per stencil
 __global__ void k_stencil_mv(int n_st, Layout L, const int* __restrict__ st_env, const int* __restrict__ st_pts,
                              const uint8_t* __restrict__ run, const double* __restrict__ sH, const double* __restrict__ d,
                              double* __restrict__ st_t) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n_st) return;
-  if (!run[st_env[s]]) return;
-  double u[12];
-  for (int a = 0; a < 4; ++a) {
-    d3 v = point_gather(L, st_pts[4 * s + a], d);
-    u[3 * a] = v.x;
-    u[3 * a + 1] = v.y;
-    u[3 * a + 2] = v.z;
-  }
-  const double* H = sH + 78L * s;
-  for (int i = 0; i < 12; ++i) {
-    double acc = 0.0;
-    for (int j = 0; j < 12; ++j) acc += H[sym_idx(i, j, 12)] * u[j];
-    st_t[12L * s + i] = acc;
-  }
+  int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  bool ok = s < n_st && run[st_env[s]];
+  stencil_product_hw<false>(L, st_pts, sH, d, st_t, s, ok);
 }
 
 struct Sell {
@@ -290,8 +313,7 @@ DEV double spmv_soft_row(const Layout& L, const SpmvArgs& A, int slice, int lane
     const double* V = A.S.val + A.S.vbase[slice] + lane;
 #pragma unroll 4
     for (int kk = 0; kk < w; ++kk) {
-      int c = col[32 * kk];
-      if (c < 0) continue;
+      int c = col[32 * kk];  // padding blocks: the row itself, zero values
       d3 dv = ld3(d, c);
       const double* B = V + 288L * kk;
       acc = acc + mk3(B[0] * dv.x + B[32] * dv.y + B[64] * dv.z, B[96] * dv.x + B[128] * dv.y + B[160] * dv.z,

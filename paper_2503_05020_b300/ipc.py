@@ -35,7 +35,7 @@ class SceneDesc(C.Structure):
                 ("newton_tol", C.c_double), ("pcg_rel_tol", C.c_double), ("kappa_affine", C.c_double),
                 ("gravity", C.c_double * 3), ("max_newton", C.c_int32), ("max_ls_halvings", C.c_int32),
                 ("max_pcg_iters", C.c_int32), ("precision", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
-                ("device", C.c_int32), ("pad", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("device", C.c_int32), ("pcg_cluster", C.c_int32), ("cuda_stream", C.c_void_p)]
 
 
 class SoftDesc(C.Structure):
@@ -147,7 +147,7 @@ class Scene:
     """A batch of grasp environments stepped together on one GPU."""
 
     def __init__(self, params: dict, precision: int = FP64, device: int = 0, stream: int | None = None,
-                 hbm_budget_bytes: int = 0):
+                 hbm_budget_bytes: int = 0, pcg_cluster: int = 0):
         d = SceneDesc()
         d.dt, d.dhat, d.kappa, d.eps_v = params["dt"], params["dhat"], params["kappa"], params["eps_v"]
         d.newton_tol, d.pcg_rel_tol, d.kappa_affine = params["newton_tol"], params["pcg_rel_tol"], params["kappa_affine"]
@@ -155,6 +155,7 @@ class Scene:
             d.gravity[k] = params["gravity"][k]
         d.max_newton, d.max_ls_halvings, d.max_pcg_iters = params["max_newton"], params["max_ls"], params["max_pcg"]
         d.precision, d.hbm_budget_bytes, d.device = precision, hbm_budget_bytes, device
+        d.pcg_cluster = pcg_cluster  # 0 automatic, 1/2/4/8 CTAs per env cluster, -1 tiled multi-launch
         d.cuda_stream = stream
         self._h = C.c_void_p()
         _check(lib().ipc_scene_create(C.byref(d), C.byref(self._h)))
@@ -225,7 +226,7 @@ class Scene:
     def scene_counters(self, eid: int) -> dict:
         v = self._query(eid, Q_SCENE_COUNTERS, np.int64)
         keys = ["contacts", "pt_contacts", "friction", "incidence_entries", "longest_list", "candidates",
-                "bsr_blocks", "sell_blocks"]
+                "bsr_blocks", "sell_blocks", "pcg_cluster", "max_env_slices"]
         return dict(zip(keys, map(int, v)))
 
     def invariants(self, eid: int) -> dict:
@@ -271,7 +272,7 @@ class Scene:
         lib().ipc_get_all_dofs(self._h, None, 0, C.byref(w))
         return w.value // 8
 
-    PROF_FAMILIES = ["spmv", "elastic", "contact", "ccd", "pcg_vector", "broad", "assembly", "ls_energy"]
+    PROF_FAMILIES = ["spmv", "elastic", "contact", "ccd", "pcg_vector", "broad", "assembly", "ls_energy", "pcg_solve"]
 
     def profile(self, on: bool = True):
         _check(lib().ipc_profile_enable(self._h, int(on)))

@@ -221,10 +221,12 @@ def test_newton_cap_fails_only_that_env():
     assert sb["status"] == "DONE"
 
 
+@pytest.mark.parametrize("pcg_cluster", [0, -1], ids=["persistent", "tiled"])
 @pytest.mark.parametrize("case", ["tet", "rigid", "block", "cube"])
-def test_newton_direction_parity(case):
+def test_newton_direction_parity(case, pcg_cluster):
     """The first projected-Newton direction (Hessian assembly + PCG) matches the oracle's CG
-    solve at the same state, in parity settings (PCG to 1e-12)."""
+    solve at the same state, in parity settings (PCG to 1e-12), with the persistent
+    per-environment solve and with the multi-launch tiled one."""
     p = S.parity_params(S.scene_params(0.01))
     if case == "cube":
         env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
@@ -235,7 +237,7 @@ def test_newton_direction_parity(case):
         x = v = None
         step = 0
     o = O.OracleEnv(p, env)
-    sc = ipc.Scene(p)
+    sc = ipc.Scene(p, pcg_cluster=pcg_cluster)
     eid = sc.add_env(env)
     if x is not None:
         o.set_state(x, v, step)
@@ -243,3 +245,51 @@ def test_newton_direction_parity(case):
     po = o.newton_direction()
     pg = sc.newton_direction(eid)
     assert np.abs(pg - po).max() <= 1e-8 * np.abs(po).max(), np.abs(pg - po).max() / np.abs(po).max()
+
+
+def pressed_cube_state():
+    env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+    _, x, v = oracle_state(S.scene_params(0.01), env, 25)
+    return env, x, v, 25
+
+
+def test_persistent_pcg_bits_do_not_depend_on_cluster_size_or_batch():
+    """The persistent solve sums every dot product per slice / per body and adds an env's slots
+    in an order fixed by the env alone: cluster sizes 1, 2, 4, 8 and the automatic choice, alone
+    or next to a larger env, give the same bits; the tiled multi-launch solve agrees to rounding."""
+    p = S.parity_params(S.scene_params(0.01))
+    env, x, v, step = pressed_cube_state()
+    dirs = {}
+    for c in (1, 2, 4, 8, 0, -1):
+        sc = ipc.Scene(p, pcg_cluster=c)
+        eid = sc.add_env(env)
+        sc.set_state(eid, x, v, step)
+        dirs[c] = sc.newton_direction(eid)
+        if c > 0:
+            assert sc.scene_counters(eid)["pcg_cluster"] == c
+        elif c < 0:
+            assert sc.scene_counters(eid)["pcg_cluster"] == 0
+    big = ipc.Scene(p)
+    big.add_env(S.pad_grasp_env(0, n_steps=40, close_steps=10))
+    eid = big.add_env(env)
+    big.set_state(eid, x, v, step)
+    dirs["batch"] = big.newton_direction(eid)
+    for k in (2, 4, 8, 0, "batch"):
+        assert np.array_equal(dirs[k], dirs[1]), k
+    scale = np.abs(dirs[1]).max()
+    assert np.abs(dirs[-1] - dirs[1]).max() <= 1e-9 * scale
+
+
+def test_persistent_pcg_trajectory_matches_tiled():
+    """Whole steps of the pad grasp with the persistent and the tiled PCG (default settings,
+    PCG to 1e-4): both stay on the same trajectory to well inside 1e-6 m."""
+    p = S.scene_params(0.005)
+    env = S.pad_grasp_env(1, n_steps=30, close_steps=10)
+    out = []
+    for c in (0, -1):
+        sc = ipc.Scene(p, pcg_cluster=c)
+        eid = sc.add_env(env)
+        sc.step(4)
+        assert sc.status(eid)["status"] in ("ACTIVE", "DONE")
+        out.append(sc.dofs(eid))
+    assert np.abs(out[0] - out[1]).max() <= 1e-6
