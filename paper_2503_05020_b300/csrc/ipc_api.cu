@@ -344,7 +344,8 @@ struct ipc_scene {
   // ---------------- layout sizes
   int E = 0, NN = 0, NB = 0, NT = 0, NP = 0, NSV = 0, NED = 0, NTR = 0, NTILE = 0, NNZB = 0;
   int max_env_slices = 0, n_slices = 0;
-  int pcg_C = 0;  // CTAs per environment cluster of the persistent PCG (0: tiled multi-launch PCG)
+  int pcg_C = 0;  // CTAs per env cluster of the last solve's first persistent-PCG launch (0: tiled PCG)
+  int pcg_resident[5] = {0, 0, 0, 0, 0};  // clusters of 1, 2, 4, 8, 16 CTAs resident at once
   long sell_nval = 0;
   std::vector<int> ids;  // layout index -> env id
   std::vector<int> h_node_off, h_tet_off, h_pt_off, h_sv_off, h_ed_off, h_tri_off, h_body_off, h_tile_off;
@@ -382,6 +383,9 @@ struct ipc_scene {
   DBuf<double> pcg_r, pcg_z, pcg_d, pcg_y, pcg_x, part_a, part_b, part_c, pcg_rz, pcg_bb;
   DBuf<int> pcg_it, pcg_active;
   DBuf<double> pcg_part;  // per-slot partial sums of the persistent PCG
+  DBuf<double> pcg_rzs, pcg_bbs, pcg_iterb;  // per-env state of the persistent PCG between launches
+  DBuf<int> pcg_its, env_iota, env_list;
+  DBuf<uint8_t> pcg_runs;
   DBuf<uint8_t> pcg_run;
   // trees
   struct TreeBufs {
@@ -885,7 +889,23 @@ struct ipc_scene {
     tile_begin.upload(tb, s);
     tile_end.upload(tn, s);
     tile_off.upload(toff, s);
-    pcg_C = choose_pcg_cluster();
+    pcg_C = 0;
+    if (desc.pcg_cluster >= 0) {
+      std::vector<int> iota(E);
+      std::iota(iota.begin(), iota.end(), 0);
+      env_iota.upload(iota, s);
+      env_list.alloc(E + 1);
+      pcg_rzs.alloc(E);
+      pcg_bbs.alloc(E);
+      pcg_iterb.alloc(E);
+      pcg_its.alloc(E);
+      pcg_runs.alloc(E);
+      pcg_resident[0] = resident_clusters<1>();
+      pcg_resident[1] = resident_clusters<2>();
+      pcg_resident[2] = resident_clusters<4>();
+      pcg_resident[3] = resident_clusters<8>();
+      pcg_resident[4] = resident_clusters<16>();
+    }
     root_off_tri.upload(tri_off_h, s);
     root_off_ed.upload(ed_off_h, s);
     bsr_ptr.upload(bptr, s);
@@ -1133,35 +1153,68 @@ struct ipc_scene {
   // ------------------------------------------------------------------ PCG
   // Clusters that can be resident at once for a cluster size C (occupancy of k_pcg_cluster<C>).
   template <int C>
+  static cudaLaunchAttribute cluster_attr() {
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = C;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    return at;
+  }
+  template <int C>
   int resident_clusters() {
+    if (C > 8) CK(cudaFuncSetAttribute(k_pcg_cluster<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchAttribute at = cluster_attr<C>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(C * std::max(E, 1)));
     cfg.blockDim = dim3(PCG_THREADS);
     cfg.stream = stream;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
     int n = 0;
-    CK(cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<C>, &cfg));
+    if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<C>, &cfg) != cudaSuccess) {
+      cudaGetLastError();  // a size the device cannot schedule: never chosen
+      n = 0;
+    }
     return n;
   }
-  // Persistent-PCG cluster size: the caller's choice, else the largest C <= 8 whose clusters
-  // are all resident at once and whose warps the largest env can still keep busy (one 32-row
-  // slice per warp or more).
-  int choose_pcg_cluster() {
-    int want = desc.pcg_cluster;
-    if (want < 0 || E == 0) return 0;
-    if (want > 0) return want;
-    int useful = 1;
-    while (useful < 8 && useful * PCG_WARPS < max_env_slices) useful *= 2;
-    for (int C = useful; C > 1; C /= 2) {
-      int n = C == 8 ? resident_clusters<8>() : C == 4 ? resident_clusters<4>() : resident_clusters<2>();
-      if (n >= E) return C;
+  // Cluster size for n running solves: the caller's choice, else the largest C <= 16 whose n
+  // clusters are all resident at once and that still leaves each CTA two 32-row slices of the
+  // largest env. Fewer running solves get more SMs each; the bits do not depend on C.
+  int pick_cluster(int n) {
+    if (desc.pcg_cluster > 0) return desc.pcg_cluster;
+    for (int k = 4; k > 0; --k) {
+      int C = 1 << k;
+      if (2 * C <= std::max(max_env_slices, 2) && n <= pcg_resident[k]) return C;
     }
     return 1;
   }
   template <int C>
-  void launch_pcg_cluster(const PcgClusterArgs& a) {
-    launch_grid(k_pcg_cluster<C>, (long)C * E, PCG_THREADS, a);
+  void launch_pcg_cluster(const PcgClusterArgs& a, int n) {
+    cudaLaunchAttribute at = cluster_attr<C>();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(C * n));
+    cfg.blockDim = dim3(PCG_THREADS);
+    cfg.stream = stream;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<C>, a));
+    ++launches;
   }
-  // one launch per solve: every env in act runs its PCG to its own stop inside its cluster
+  void launch_pcg_any(int C, const PcgClusterArgs& a, int n) {
+    switch (C) {
+      case 1: launch_pcg_cluster<1>(a, n); break;
+      case 2: launch_pcg_cluster<2>(a, n); break;
+      case 4: launch_pcg_cluster<4>(a, n); break;
+      case 8: launch_pcg_cluster<8>(a, n); break;
+      case 16: launch_pcg_cluster<16>(a, n); break;
+      default: fail_with(IPC_ERR_ARG, "pcg_cluster must be -1, 0, 1, 2, 4, 8 or 16");
+    }
+  }
+  // The solves of the envs in act, PCG_CHUNK iterations per launch at most: after each launch the
+  // envs still running are listed on the device and relaunched, with a cluster size chosen for
+  // their number. The first launch starts every solve.
+  static constexpr int PCG_CHUNK = 32;
   void pcg_persistent(const uint8_t* act) {
     PcgClusterArgs a;
     a.L = layout();
@@ -1188,20 +1241,33 @@ struct ipc_scene {
     a.part = pcg_part.p;
     a.s_total = n_slices;
     a.n_bodies = NB;
+    a.env_list = env_iota.p;
+    a.first = 1;
+    a.chunk = PCG_CHUNK;
+    a.rz_state = pcg_rzs.p;
+    a.bb_state = pcg_bbs.p;
+    a.iterb_state = pcg_iterb.p;
+    a.it_state = pcg_its.p;
+    a.run = pcg_runs.p;
     a.stats = e_stats.p;
     a.bytes = punits(IPC_PROF_PCG_SOLVE);
-    pbeg(IPC_PROF_PCG_SOLVE);
-    switch (pcg_C) {
-      case 1: launch_pcg_cluster<1>(a); break;
-      case 2: launch_pcg_cluster<2>(a); break;
-      case 4: launch_pcg_cluster<4>(a); break;
-      case 8: launch_pcg_cluster<8>(a); break;
-      default: fail_with(IPC_ERR_ARG, "pcg_cluster must be -1, 0, 1, 2, 4 or 8");
+    int n = E;
+    pcg_C = pick_cluster(n);
+    int C = pcg_C;
+    for (;;) {
+      pbeg(IPC_PROF_PCG_SOLVE);
+      launch_pcg_any(C, a, n);
+      pend(IPC_PROF_PCG_SOLVE);
+      launch_grid(k_list_running, 1, 32, E, (const uint8_t*)pcg_runs.p, env_list.p, pcg_active.p);
+      n = read_int(pcg_active.p);
+      if (n == 0) break;
+      a.first = 0;
+      a.env_list = env_list.p;
+      C = pick_cluster(n);
     }
-    pend(IPC_PROF_PCG_SOLVE);
   }
   void pcg(const uint8_t* act) {
-    if (pcg_C > 0) {
+    if (desc.pcg_cluster >= 0) {
       pcg_persistent(act);
       return;
     }
@@ -1424,8 +1490,8 @@ ipc_status ipc_scene_create(const ipc_scene_desc* desc, ipc_scene** out) {
   if (desc->precision != IPC_FP64 && desc->precision != IPC_MIXED) fail_with(IPC_ERR_ARG, "unknown precision");
   {
     int c = desc->pcg_cluster;
-    if (c != -1 && c != 0 && c != 1 && c != 2 && c != 4 && c != 8)
-      fail_with(IPC_ERR_ARG, "pcg_cluster must be -1, 0, 1, 2, 4 or 8");
+    if (c != -1 && c != 0 && c != 1 && c != 2 && c != 4 && c != 8 && c != 16)
+      fail_with(IPC_ERR_ARG, "pcg_cluster must be -1, 0, 1, 2, 4, 8 or 16");
   }
   std::unique_ptr<ipc_scene> s(new ipc_scene());
   s->desc = *desc;

@@ -50,6 +50,14 @@ struct PcgClusterArgs {
   double* part;               // slot partials: 2 x 3 doubles x (s_total + n_bodies)
   int s_total;                // slices of the whole batch
   int n_bodies;               // rigid bodies of the whole batch
+  const int* env_list;        // env of each cluster
+  int first;                  // 1: start the solves (z = M^-1 r, d = z, x = 0); 0: resume them
+  int chunk;                  // iterations at most in this launch
+  double* rz_state;           // per env: r.z after the last iteration
+  double* bb_state;           // per env: |b|^2 (right-hand side)
+  double* iterb_state;        // per env: algorithmic bytes of one iteration
+  int* it_state;              // per env: iterations so far
+  uint8_t* run;               // per env: 1 while the solve continues
   long long* stats;           // 5 per env; [STAT_PCG] += iterations of this solve
   unsigned long long* bytes;  // algorithmic bytes of all iterations (may be null)
 };
@@ -122,23 +130,26 @@ DEV double body_iter_bytes(const Layout& L, const SpmvArgs& A, int b) {
 constexpr double STENCIL_ITER_BYTES = 624.0 + 16.0 + 96.0 + 96.0;
 
 template <int C>
-__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const int e = blockIdx.x / C;
-  if (!P.act[e]) return;  // uniform over the cluster: every CTA leaves
+  const int e = P.env_list[blockIdx.x / C];
+  if (P.first && !P.act[e]) {  // uniform over the cluster: every CTA leaves
+    if (rank == 0 && threadIdx.x == 0) P.run[e] = 0;
+    return;
+  }
   __shared__ double wred[PCG_WARPS][12];
   __shared__ double tot[4];
   __shared__ double sbody[12];
   __shared__ int srange[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int gwarp = rank * PCG_WARPS + warp, nwarps = C * PCG_WARPS;
-  const int gth = rank * PCG_THREADS + tid, nth = C * PCG_THREADS;
+  // warps are interleaved over the cluster's CTAs, so consecutive slices land on different SMs
+  const int gwarp = warp * C + rank, nwarps = C * PCG_WARPS;
   const Layout& L = P.L;
   const int S0 = P.pslice_off[e], S1 = P.pslice_off[e + 1];
   const int b0 = P.body_off[e], b1 = P.body_off[e + 1];
   const int ST = P.s_total;
-  double* part_dy = P.part;                              // 3 doubles per slot, [0] used
+  double* part_dy = P.part;                                  // 3 doubles per slot, [0] used
   double* part_rz = P.part + 3L * (P.s_total + P.n_bodies);  // (r.z, r.r, bytes) per slot
   if (tid < 4) {  // this env's range in each stencil sublist
     int lo = P.st_bounds[tid], hi = P.st_bounds[tid + 1];
@@ -146,67 +157,74 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(PCG_THREADS) k_pcg_c
     srange[2 * tid + 1] = lower_env(P.st_env, lo, hi, e + 1);
   }
   __syncthreads();
+  const int n_stencils = srange[1] - srange[0] + srange[3] - srange[2] + srange[5] - srange[4] + srange[7] - srange[6];
 
-  // ---- z = M^-1 r, d = z, x = 0; per-slot (r.z, r.r) and the bytes of one iteration
-  for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {  // warp-uniform
-    double a = 0.0, c = 0.0, nb = 0.0;
-    const int i = P.pslice_row[32 * sl + lane];
-    if (i >= 0) {
-      precond_soft(i, P.Ps, P.r, P.z, &a, &c);
-      for (int k = 3 * i; k < 3 * i + 3; ++k) {
-        P.d[k] = P.z[k];
-        P.x[k] = 0.0;
+  double rz, bb, iter_bytes;
+  int it;
+  bool go;
+  if (P.first) {
+    // ---- z = M^-1 r, d = z, x = 0; per-slot (r.z, r.r) and the bytes of one iteration
+    for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {  // warp-uniform
+      double a = 0.0, c = 0.0, nb = 0.0;
+      const int i = P.pslice_row[32 * sl + lane];
+      if (i >= 0) {
+        precond_soft(i, P.Ps, P.r, P.z, &a, &c);
+        for (int k = 3 * i; k < 3 * i + 3; ++k) {
+          P.d[k] = P.z[k];
+          P.x[k] = 0.0;
+        }
+        if (P.bytes) nb = soft_iter_bytes(P.A, i);
       }
-      if (P.bytes) nb = soft_iter_bytes(P.A, i);
-    }
-    a = warp_sum(a);
-    c = warp_sum(c);
-    nb = warp_sum(nb);
-    if (lane == 0) {
-      part_rz[3L * sl] = a;
-      part_rz[3L * sl + 1] = c;
-      part_rz[3L * sl + 2] = nb;
-    }
-  }
-  for (int b = b0; b < b1; ++b) {
-    if (rank != (b - b0) % C) continue;  // CTA-uniform
-    long base3 = 3L * L.body_node[b];
-    if (tid < 12) sbody[tid] = P.r[base3 + tid];
-    __syncthreads();
-    double a, c;
-    precond_body(P.Pb, b, sbody, base3, P.z, &a, &c);
-    if (tid < 12) {
-      P.d[base3 + tid] = P.z[base3 + tid];
-      P.x[base3 + tid] = 0.0;
-    }
-    if (warp == 0) {
       a = warp_sum(a);
       c = warp_sum(c);
+      nb = warp_sum(nb);
       if (lane == 0) {
-        long slot = (long)ST + b;
-        part_rz[3 * slot] = a;
-        part_rz[3 * slot + 1] = c;
-        double nb = P.bytes ? body_iter_bytes(L, P.A, b) : 0.0;
-        if (b == b0)  // the env's stencils are counted once, on its first body slot
-          nb += STENCIL_ITER_BYTES * (srange[1] - srange[0] + srange[3] - srange[2] + srange[5] - srange[4] +
-                                      srange[7] - srange[6]);
-        part_rz[3 * slot + 2] = P.bytes ? nb : 0.0;
+        part_rz[3L * sl] = a;
+        part_rz[3L * sl + 1] = c;
+        part_rz[3L * sl + 2] = nb;
       }
     }
-    __syncthreads();
+    for (int b = b0; b < b1; ++b) {
+      if (rank != (b - b0) % C) continue;  // CTA-uniform
+      long base3 = 3L * L.body_node[b];
+      if (tid < 12) sbody[tid] = P.r[base3 + tid];
+      __syncthreads();
+      double a, c;
+      precond_body(P.Pb, b, sbody, base3, P.z, &a, &c);
+      if (tid < 12) {
+        P.d[base3 + tid] = P.z[base3 + tid];
+        P.x[base3 + tid] = 0.0;
+      }
+      if (warp == 0) {
+        a = warp_sum(a);
+        c = warp_sum(c);
+        if (lane == 0) {
+          long slot = (long)ST + b;
+          part_rz[3 * slot] = a;
+          part_rz[3 * slot + 1] = c;
+          part_rz[3 * slot + 2] = P.bytes ? body_iter_bytes(L, P.A, b) : 0.0;
+        }
+      }
+      __syncthreads();
+    }
+    cl.sync();
+    double v3[3];
+    env_sum<3>(part_rz, S0, S1, ST, b0, b1, tot, v3);
+    rz = v3[0];
+    bb = v3[1];
+    iter_bytes = v3[2] + (P.bytes ? STENCIL_ITER_BYTES * n_stencils : 0.0);
+    it = 0;
+    go = bb > 0.0 && isfinite(bb);
+  } else {
+    rz = P.rz_state[e];
+    bb = P.bb_state[e];
+    iter_bytes = P.iterb_state[e];
+    it = P.it_state[e];
+    go = true;
   }
-  cl.sync();
-  double v3[3];
-  env_sum<3>(part_rz, S0, S1, ST, b0, b1, tot, v3);
-  double rz = v3[0];
-  const double bb = v3[1];
-  double iter_bytes = v3[2];
-  if (P.bytes && b1 == b0)  // an env without bodies: its stencils
-    iter_bytes += STENCIL_ITER_BYTES * (srange[1] - srange[0] + srange[3] - srange[2] + srange[5] - srange[4] +
-                                        srange[7] - srange[6]);
-  int it = 0;
-  bool go = bb > 0.0 && isfinite(bb);
-  while (go) {
+  const int it0 = it;
+  bool more = go;  // the solve continues after this launch
+  for (int k = 0; go && k < P.chunk; ++k) {
     // ---- t_s = H_s (P_s d) for the env's stencils (the barrier publishes every CTA's d)
     cl.sync();
     for (int q = 0; q < 4; ++q)  // one half-warp per stencil (warp-uniform loop)
@@ -233,9 +251,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(PCG_THREADS) k_pcg_c
       for (int q = 0; q < 12; ++q) acc[q] = 0.0;
       if (!kin) {
         int kb = P.A.ns_ptr[base], ke = P.A.ns_ptr[base + 1];
-        for (int k = kb + tid; k < ke; k += PCG_THREADS) {
-          d3 tv = ldcg3(P.A.st_t, P.A.ns_src[k]);
-          const double* xb = P.A.ns_xb + 3L * k;
+        for (int k2 = kb + tid; k2 < ke; k2 += PCG_THREADS) {
+          d3 tv = ldcg3(P.A.st_t, P.A.ns_src[k2]);
+          const double* xb = P.A.ns_xb + 3L * k2;
           double w1 = xb[0], w2 = xb[1], w3 = xb[2];
           acc[0] += tv.x;
           acc[1] += tv.y;
@@ -283,9 +301,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(PCG_THREADS) k_pcg_c
       double a = 0.0, c = 0.0;
       const int i = P.pslice_row[32 * sl + lane];
       if (i >= 0) {
-        for (int k = 3 * i; k < 3 * i + 3; ++k) {
-          P.x[k] += alpha * P.d[k];
-          P.r[k] -= alpha * P.y[k];
+        for (int k2 = 3 * i; k2 < 3 * i + 3; ++k2) {
+          P.x[k2] += alpha * P.d[k2];
+          P.r[k2] -= alpha * P.y[k2];
         }
         precond_soft(i, P.Ps, P.r, P.z, &a, &c);
       }
@@ -300,10 +318,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(PCG_THREADS) k_pcg_c
       if (rank != (b - b0) % C) continue;  // CTA-uniform
       long base3 = 3L * L.body_node[b];
       if (tid < 12) {
-        long k = base3 + tid;
-        P.x[k] += alpha * P.d[k];
-        double rv = P.r[k] - alpha * P.y[k];
-        P.r[k] = rv;
+        long k2 = base3 + tid;
+        P.x[k2] += alpha * P.d[k2];
+        double rv = P.r[k2] - alpha * P.y[k2];
+        P.r[k2] = rv;
         sbody[tid] = rv;
       }
       __syncthreads();
@@ -324,23 +342,47 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(PCG_THREADS) k_pcg_c
     env_sum<2>(part_rz, S0, S1, ST, b0, b1, tot, u2);
     const double rz_new = u2[0], rr = u2[1];
     ++it;
-    if (rr <= P.tol2 * bb || it >= P.max_it || !(dy[0] > 0.0) || !isfinite(rr)) break;
+    if (rr <= P.tol2 * bb || it >= P.max_it || !(dy[0] > 0.0) || !isfinite(rr)) {
+      more = false;
+      break;
+    }
     const double beta = rz > 0.0 ? rz_new / rz : 0.0;
     rz = rz_new;
     // ---- d = z + beta d (owner threads)
     for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {
       const int i = P.pslice_row[32 * sl + lane];
       if (i >= 0)
-        for (int k = 3 * i; k < 3 * i + 3; ++k) P.d[k] = P.z[k] + beta * P.d[k];
+        for (int k2 = 3 * i; k2 < 3 * i + 3; ++k2) P.d[k2] = P.z[k2] + beta * P.d[k2];
     }
     for (int b = b0; b < b1; ++b)
       if (rank == (b - b0) % C && tid < 12) {
-        long k = 3L * L.body_node[b] + tid;
-        P.d[k] = P.z[k] + beta * P.d[k];
+        long k2 = 3L * L.body_node[b] + tid;
+        P.d[k2] = P.z[k2] + beta * P.d[k2];
       }
   }
+  // every CTA read the slot partials before it got here; CTA 0 records the env's state
   if (rank == 0 && tid == 0) {
-    P.stats[5 * e + STAT_PCG] += it;
-    if (P.bytes) atomicAdd(P.bytes, (unsigned long long)(iter_bytes * it));
+    P.rz_state[e] = rz;
+    P.bb_state[e] = bb;
+    P.iterb_state[e] = iter_bytes;
+    P.it_state[e] = it;
+    P.run[e] = more ? 1 : 0;
+    P.stats[5 * e + STAT_PCG] += it - it0;
+    if (P.bytes) atomicAdd(P.bytes, (unsigned long long)(iter_bytes * (it - it0)));
   }
+}
+
+// ids of the envs whose solve continues, in env order, and their count (one warp)
+__global__ void k_list_running(int n_env, const uint8_t* __restrict__ run, int* __restrict__ list,
+                               int* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  for (int e0 = 0; e0 < n_env; e0 += 32) {
+    int e = e0 + lane;
+    bool f = e < n_env && run[e];
+    unsigned m = __ballot_sync(0xffffffffu, f);
+    if (f) list[base + __popc(m & ((1u << lane) - 1u))] = e;
+    base += __popc(m);
+  }
+  if (lane == 0) *count = base;
 }

@@ -255,12 +255,12 @@ def pressed_cube_state():
 
 def test_persistent_pcg_bits_do_not_depend_on_cluster_size_or_batch():
     """The persistent solve sums every dot product per slice / per body and adds an env's slots
-    in an order fixed by the env alone: cluster sizes 1, 2, 4, 8 and the automatic choice, alone
+    in an order fixed by the env alone: cluster sizes 1, 2, 4, 8, 16 and the automatic choice, alone
     or next to a larger env, give the same bits; the tiled multi-launch solve agrees to rounding."""
     p = S.parity_params(S.scene_params(0.01))
     env, x, v, step = pressed_cube_state()
     dirs = {}
-    for c in (1, 2, 4, 8, 0, -1):
+    for c in (1, 2, 4, 8, 16, 0, -1):
         sc = ipc.Scene(p, pcg_cluster=c)
         eid = sc.add_env(env)
         sc.set_state(eid, x, v, step)
@@ -274,7 +274,7 @@ def test_persistent_pcg_bits_do_not_depend_on_cluster_size_or_batch():
     eid = big.add_env(env)
     big.set_state(eid, x, v, step)
     dirs["batch"] = big.newton_direction(eid)
-    for k in (2, 4, 8, 0, "batch"):
+    for k in (2, 4, 8, 16, 0, "batch"):
         assert np.array_equal(dirs[k], dirs[1]), k
     scale = np.abs(dirs[1]).max()
     assert np.abs(dirs[-1] - dirs[1]).max() <= 1e-9 * scale
