@@ -59,120 +59,129 @@ HD double ordered_to_double(unsigned long long b) {
 HD int up_idx(int i, int j, int n) { return i * n - i * (i - 1) / 2 + (j - i); }
 HD int sym_idx(int i, int j, int n) { return i <= j ? up_idx(i, j, n) : up_idx(j, i, n); }
 
-// Cyclic Jacobi on a symmetric N x N matrix held in A (row-major, thread-local). On return A
-// holds the PSD projection V max(Lambda, 0) V^T. At most 24 sweeps (a fixed bound).
+// Squared relative size of the off-diagonal part at which the Jacobi sweeps below stop.
+template <class T>
+struct JacobiTol;
+template <>
+struct JacobiTol<double> {
+  static constexpr double psd = 1e-28, eig3 = 1e-30;
+};
+template <>
+struct JacobiTol<float> {
+  static constexpr float psd = 1e-13f, eig3 = 1e-13f;
+};
+
+// Cyclic Jacobi on a symmetric N x N matrix held in A (row-major, thread-local), in the
+// precision T. On return A holds the PSD projection V max(Lambda, 0) V^T. At most 24 sweeps
+// (a fixed bound).
 // Kept out of line: inlined into kernels that hold other large local arrays, the device
 // optimizer produced wrong results for this routine (measured on sm_103a with CUDA 13.0).
-template <int N>
-__device__ __noinline__ void project_psd_jacobi(double* A) {
-  double V[N * N];
+template <int N, class T = double>
+__device__ __noinline__ void project_psd_jacobi(T* A) {
+  T V[N * N];
 #pragma unroll 1
-  for (int i = 0; i < N * N; ++i) V[i] = 0.0;
+  for (int i = 0; i < N * N; ++i) V[i] = T(0);
 #pragma unroll 1
-  for (int i = 0; i < N; ++i) V[i * N + i] = 1.0;
-  double fro = 0.0;
+  for (int i = 0; i < N; ++i) V[i * N + i] = T(1);
+  T fro = T(0);
 #pragma unroll 1
   for (int i = 0; i < N * N; ++i) fro += A[i] * A[i];
-  if (fro == 0.0) return;
-  const double tol = 1e-28 * fro;
+  if (fro == T(0)) return;
+  const T tol = JacobiTol<T>::psd * fro;
 #pragma unroll 1
   for (int sweep = 0; sweep < 24; ++sweep) {
-    double off = 0.0;
+    T off = T(0);
 #pragma unroll 1
     for (int i = 0; i < N; ++i)
 #pragma unroll 1
-      for (int j = i + 1; j < N; ++j) off += 2.0 * A[i * N + j] * A[i * N + j];
+      for (int j = i + 1; j < N; ++j) off += T(2) * A[i * N + j] * A[i * N + j];
     if (off <= tol) break;
 #pragma unroll 1
     for (int p = 0; p < N - 1; ++p) {
 #pragma unroll 1
       for (int q = p + 1; q < N; ++q) {
-        double apq = A[p * N + q];
-        if (apq == 0.0) continue;
-        double app = A[p * N + p], aqq = A[q * N + q];
-        double theta = (aqq - app) / (2.0 * apq);
-        double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        double c = rsqrt(t * t + 1.0), s = t * c;
+        T apq = A[p * N + q];
+        if (apq == T(0)) continue;
+        T app = A[p * N + p], aqq = A[q * N + q];
+        T theta = (aqq - app) / (T(2) * apq);
+        T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+        T c = rsqrt(t * t + T(1)), s = t * c;
 #pragma unroll 1
         for (int k = 0; k < N; ++k) {
-          double akp = A[k * N + p], akq = A[k * N + q];
+          T akp = A[k * N + p], akq = A[k * N + q];
           A[k * N + p] = c * akp - s * akq;
           A[k * N + q] = s * akp + c * akq;
         }
 #pragma unroll 1
         for (int k = 0; k < N; ++k) {
-          double apk = A[p * N + k], aqk = A[q * N + k];
+          T apk = A[p * N + k], aqk = A[q * N + k];
           A[p * N + k] = c * apk - s * aqk;
           A[q * N + k] = s * apk + c * aqk;
         }
 #pragma unroll 1
         for (int k = 0; k < N; ++k) {
-          double vkp = V[k * N + p], vkq = V[k * N + q];
+          T vkp = V[k * N + p], vkq = V[k * N + q];
           V[k * N + p] = c * vkp - s * vkq;
           V[k * N + q] = s * vkp + c * vkq;
         }
       }
     }
   }
-  double lam[N];
-  bool any_neg = false;
+  T lam[N];
 #pragma unroll 1
-  for (int i = 0; i < N; ++i) {
-    lam[i] = A[i * N + i];
-    if (lam[i] < 0.0) any_neg = true;
-  }
+  for (int i = 0; i < N; ++i) lam[i] = A[i * N + i];
   // rebuild only the clamped part: A_proj = sum_k max(lam_k, 0) v_k v_k^T
 #pragma unroll 1
   for (int i = 0; i < N; ++i)
 #pragma unroll 1
     for (int j = i; j < N; ++j) {
-      double s = 0.0;
+      T s = T(0);
 #pragma unroll 1
       for (int k = 0; k < N; ++k)
-        if (lam[k] > 0.0) s += V[i * N + k] * lam[k] * V[j * N + k];
+        if (lam[k] > T(0)) s += V[i * N + k] * lam[k] * V[j * N + k];
       A[i * N + j] = s;
       A[j * N + i] = s;
     }
-  (void)any_neg;
 }
 
-// Symmetric 3x3 eigen-decomposition by cyclic Jacobi: A (row-major) -> eigenvalues w and
-// eigenvector columns of V (det V = +1).
-DEV void eig_sym3(const double A_in[9], double w[3], double V[9]) {
-  double A[9];
+// Symmetric 3x3 eigen-decomposition by cyclic Jacobi in the precision T: A (row-major) ->
+// eigenvalues w and eigenvector columns of V (det V = +1).
+template <class T>
+DEV void eig_sym3(const T A_in[9], T w[3], T V[9]) {
+  T A[9];
   for (int i = 0; i < 9; ++i) A[i] = A_in[i];
-  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.0 : 0.0;
-  double fro = 0.0;
+  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? T(1) : T(0);
+  T fro = T(0);
   for (int i = 0; i < 9; ++i) fro += A[i] * A[i];
 #pragma unroll 1
   for (int sweep = 0; sweep < 16; ++sweep) {
-    double off = 2.0 * (A[1] * A[1] + A[2] * A[2] + A[5] * A[5]);
-    if (off <= 1e-30 * fro || off == 0.0) break;
+    T off = T(2) * (A[1] * A[1] + A[2] * A[2] + A[5] * A[5]);
+    if (off <= JacobiTol<T>::eig3 * fro || off == T(0)) break;
 #pragma unroll
     for (int pq = 0; pq < 3; ++pq) {
       const int p = pq == 2 ? 1 : 0;
       const int q = pq == 0 ? 1 : 2;
-      double apq = A[p * 3 + q];
-      if (apq == 0.0) continue;
-      double app = A[p * 3 + p], aqq = A[q * 3 + q];
-      double theta = (aqq - app) / (2.0 * apq);
-      double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-      double c = rsqrt(t * t + 1.0), s = t * c;
+      T apq = A[p * 3 + q];
+      if (apq == T(0)) continue;
+      T app = A[p * 3 + p], aqq = A[q * 3 + q];
+      T theta = (aqq - app) / (T(2) * apq);
+      T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+      T c = rsqrt(t * t + T(1)), s = t * c;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        double akp = A[k * 3 + p], akq = A[k * 3 + q];
+        T akp = A[k * 3 + p], akq = A[k * 3 + q];
         A[k * 3 + p] = c * akp - s * akq;
         A[k * 3 + q] = s * akp + c * akq;
       }
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        double apk = A[p * 3 + k], aqk = A[q * 3 + k];
+        T apk = A[p * 3 + k], aqk = A[q * 3 + k];
         A[p * 3 + k] = c * apk - s * aqk;
         A[q * 3 + k] = s * apk + c * aqk;
       }
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        double vkp = V[k * 3 + p], vkq = V[k * 3 + q];
+        T vkp = V[k * 3 + p], vkq = V[k * 3 + q];
         V[k * 3 + p] = c * vkp - s * vkq;
         V[k * 3 + q] = s * vkp + c * vkq;
       }
@@ -181,33 +190,32 @@ DEV void eig_sym3(const double A_in[9], double w[3], double V[9]) {
   w[0] = A[0];
   w[1] = A[4];
   w[2] = A[8];
-  double det = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
-               V[2] * (V[3] * V[7] - V[4] * V[6]);
-  if (det < 0.0) {
+  T det = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) + V[2] * (V[3] * V[7] - V[4] * V[6]);
+  if (det < T(0)) {
     V[2] = -V[2];
     V[5] = -V[5];
     V[8] = -V[8];
   }
 }
 
-// In-place inverse of an SPD N x N matrix (row-major) via Cholesky; returns false when a pivot
+// In-place inverse of an SPD N x N matrix (row-major) via Cholesky in the precision T; returns false when a pivot
 // is not positive (then A is set to the inverse of its diagonal, or 0 where that is not > 0).
-template <int N>
-__device__ __noinline__ bool spd_inverse(double* A) {  // out of line, see project_psd_jacobi
-  double L[N * N];
-  for (int i = 0; i < N * N; ++i) L[i] = 0.0;
+template <int N, class T = double>
+__device__ __noinline__ bool spd_inverse(T* A) {  // out of line, see project_psd_jacobi
+  T L[N * N];
+  for (int i = 0; i < N * N; ++i) L[i] = T(0);
   bool ok = true;
   for (int j = 0; j < N && ok; ++j) {
-    double s = A[j * N + j];
+    T s = A[j * N + j];
     for (int k = 0; k < j; ++k) s -= L[j * N + k] * L[j * N + k];
-    if (!(s > 0.0)) {
+    if (!(s > T(0))) {
       ok = false;
       break;
     }
-    double d = sqrt(s);
+    T d = sqrt(s);
     L[j * N + j] = d;
     for (int i = j + 1; i < N; ++i) {
-      double t = A[i * N + j];
+      T t = A[i * N + j];
       for (int k = 0; k < j; ++k) t -= L[i * N + k] * L[j * N + k];
       L[i * N + j] = t / d;
     }
@@ -215,25 +223,25 @@ __device__ __noinline__ bool spd_inverse(double* A) {  // out of line, see proje
   if (!ok) {
     for (int i = 0; i < N; ++i)
       for (int j = 0; j < N; ++j) {
-        double d = A[i * N + i];
-        A[i * N + j] = (i == j && d > 0.0) ? 1.0 / d : 0.0;
+        T d = A[i * N + i];
+        A[i * N + j] = (i == j && d > T(0)) ? T(1) / d : T(0);
       }
     return false;
   }
   // inverse of L (lower), then A^-1 = L^-T L^-1
-  double Li[N * N];
-  for (int i = 0; i < N * N; ++i) Li[i] = 0.0;
+  T Li[N * N];
+  for (int i = 0; i < N * N; ++i) Li[i] = T(0);
   for (int i = 0; i < N; ++i) {
-    Li[i * N + i] = 1.0 / L[i * N + i];
+    Li[i * N + i] = T(1) / L[i * N + i];
     for (int j = 0; j < i; ++j) {
-      double s = 0.0;
+      T s = T(0);
       for (int k = j; k < i; ++k) s -= L[i * N + k] * Li[k * N + j];
       Li[i * N + j] = s / L[i * N + i];
     }
   }
   for (int i = 0; i < N; ++i)
     for (int j = i; j < N; ++j) {
-      double s = 0.0;
+      T s = T(0);
       for (int k = j; k < N; ++k) s += Li[k * N + i] * Li[k * N + j];
       A[i * N + j] = s;
       A[j * N + i] = s;
@@ -242,18 +250,19 @@ __device__ __noinline__ bool spd_inverse(double* A) {  // out of line, see proje
 }
 
 // 3x3 symmetric positive-definite inverse by the adjugate (row-major); zero if not invertible.
-DEV void inv_sym3(const double* M, double* R) {
-  double a = M[0], b = M[1], c = M[2], d = M[4], e = M[5], f = M[8];
-  double A = d * f - e * e, B = c * e - b * f, C = b * e - c * d;
-  double det = a * A + b * B + c * C;
-  if (!(det > 0.0) || !isfinite(det)) {
-    for (int i = 0; i < 9; ++i) R[i] = 0.0;
-    if (a > 0) R[0] = 1.0 / a;
-    if (d > 0) R[4] = 1.0 / d;
-    if (f > 0) R[8] = 1.0 / f;
+template <class T>
+DEV void inv_sym3(const T* M, T* R) {
+  T a = M[0], b = M[1], c = M[2], d = M[4], e = M[5], f = M[8];
+  T A = d * f - e * e, B = c * e - b * f, C = b * e - c * d;
+  T det = a * A + b * B + c * C;
+  if (!(det > T(0)) || !isfinite(det)) {
+    for (int i = 0; i < 9; ++i) R[i] = T(0);
+    if (a > 0) R[0] = T(1) / a;
+    if (d > 0) R[4] = T(1) / d;
+    if (f > 0) R[8] = T(1) / f;
     return;
   }
-  double id = 1.0 / det;
+  T id = T(1) / det;
   R[0] = A * id;
   R[1] = B * id;
   R[2] = C * id;

@@ -74,10 +74,107 @@ __device__ __noinline__ double tet_energy(d3 x0, d3 x1, d3 x2, d3 x3, const doub
   return w * (0.5 * mu * (tr - 3.0) - mu * lnJ + 0.5 * lam * lnJ * lnJ);
 }
 
-template <int MODE>
+// Smallest squared singular value used when dividing by s_i (a degenerate tet).
+template <class T>
+struct TinyS2;
+template <>
+struct TinyS2<double> {
+  static constexpr double v = 1e-300;
+};
+template <>
+struct TinyS2<float> {
+  static constexpr float v = 1e-30f;
+};
+
+// PSD-projected Hessian of the weighted Neo-Hookean energy w Psi(F), in the precision HT, as
+// the 10 upper 3x3 blocks (a <= b, row-major) of the 12x12 tet Hessian (90 values). F, the
+// Lame parameters, ln J, Dm^-1 (Bm) and w come in FP64 and are rounded to HT first.
+template <class HT>
+DEV void tet_hessian(const double* F64, double mu64, double lam64, double lnJ64, const double* Bm, double w64,
+                     HT* __restrict__ out) {
+  const HT mu = HT(mu64), lam = HT(lam64), lnJ = HT(lnJ64);
+  HT F[9];
+  for (int i = 0; i < 9; ++i) F[i] = HT(F64[i]);
+  // shape-function gradients b_a: b1..b3 = rows of Dm^-1, b0 = -(b1 + b2 + b3)
+  HT b[4][3];
+  for (int c = 0; c < 3; ++c) {
+    b[1][c] = HT(Bm[c]);
+    b[2][c] = HT(Bm[3 + c]);
+    b[3][c] = HT(Bm[6 + c]);
+    b[0][c] = HT(-(Bm[c] + Bm[3 + c] + Bm[6 + c]));
+  }
+  // SVD through the eigen-decomposition of F^T F
+  HT C[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) C[3 * r + c] = F[r] * F[c] + F[3 + r] * F[3 + c] + F[6 + r] * F[6 + c];
+  HT s2[3], V[9];
+  eig_sym3<HT>(C, s2, V);
+  HT s[3];
+  for (int i = 0; i < 3; ++i) s[i] = sqrt(fmax(s2[i], TinyS2<HT>::v));
+  HT U[9];  // U = F V diag(1/s)
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      U[3 * r + c] = (F[3 * r] * V[c] + F[3 * r + 1] * V[3 + c] + F[3 * r + 2] * V[6 + c]) / s[c];
+  // c_a = V^T b_a
+  HT cb[4][3];
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 3; ++k) cb[a][k] = V[k] * b[a][0] + V[3 + k] * b[a][1] + V[6 + k] * b[a][2];
+  HT Hb[90];
+  for (int i = 0; i < 90; ++i) Hb[i] = HT(0);
+  // accumulate lam * w w^T over the 10 upper 3x3 blocks; w_a = U m_a where m_a = M c_a
+  auto add_mode = [&](HT lm, const HT (*m)[3]) {
+    if (!(lm > HT(0))) return;
+    HT wv[4][3];
+    for (int a = 0; a < 4; ++a)
+      for (int r = 0; r < 3; ++r) wv[a][r] = U[3 * r] * m[a][0] + U[3 * r + 1] * m[a][1] + U[3 * r + 2] * m[a][2];
+    int blk = 0;
+    for (int a = 0; a < 4; ++a)
+      for (int bb = a; bb < 4; ++bb, ++blk)
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c) Hb[9 * blk + 3 * r + c] += lm * wv[a][r] * wv[bb][c];
+  };
+  // scaling modes
+  HT A[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      A[3 * i + j] = (i == j) ? mu + (mu - lam * lnJ + lam) / (s[i] * s[i]) : lam / (s[i] * s[j]);
+  HT la[3], av[9];
+  eig_sym3<HT>(A, la, av);
+  for (int k = 0; k < 3; ++k) {
+    HT m[4][3];
+    for (int a = 0; a < 4; ++a) {
+      m[a][0] = av[k] * cb[a][0];
+      m[a][1] = av[3 + k] * cb[a][1];
+      m[a][2] = av[6 + k] * cb[a][2];
+    }
+    add_mode(la[k], m);
+  }
+  // twist and flip modes of each pair: (e_i e_j^T -/+ e_j e_i^T) c = e_i c_j -/+ e_j c_i
+  const HT r2 = HT(0.70710678118654752440);
+  for (int pr = 0; pr < 3; ++pr) {
+    int i = pr == 2 ? 0 : pr, j = pr == 2 ? 2 : pr + 1;
+    HT ss = s[i] * s[j];
+    HT lt = mu + (lam * lnJ - mu) / ss, lf = mu + (mu - lam * lnJ) / ss;
+    HT mt[4][3], mf[4][3];
+    for (int a = 0; a < 4; ++a) {
+      HT ci = cb[a][i], cj = cb[a][j];
+      for (int k = 0; k < 3; ++k) mt[a][k] = mf[a][k] = HT(0);
+      mt[a][i] = r2 * cj;
+      mt[a][j] = -r2 * ci;
+      mf[a][i] = r2 * cj;
+      mf[a][j] = r2 * ci;
+    }
+    add_mode(lt, mt);
+    add_mode(lf, mf);
+  }
+  const HT w = HT(w64);
+  for (int i = 0; i < 90; ++i) out[i] = w * Hb[i];
+}
+
+template <int MODE, class HT = double>
 __global__ void k_elastic(int n_tets, const int4* __restrict__ tets, const double* __restrict__ prm,
                           const int* __restrict__ tenv, const uint8_t* __restrict__ act, const double* __restrict__ q,
-                          double h2, double* __restrict__ tE, double* __restrict__ tg, double* __restrict__ tH,
+                          double h2, double* __restrict__ tE, double* __restrict__ tg, HT* __restrict__ tH,
                           int* __restrict__ env_bad, unsigned long long* __restrict__ units) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tets) return;
@@ -104,13 +201,13 @@ __global__ void k_elastic(int n_tets, const int4* __restrict__ tets, const doubl
   tE[t] = En;
   double lnJ = log(J);
   if (MODE == MODE_ENERGY) return;
-  // shape-function gradients b_a (rows): b1..b3 = rows of Dm^-1, b0 = -(b1 + b2 + b3)
+  // gradient (FP64): w P(F) b_a, first Piola-Kirchhoff stress P = mu F + (lam lnJ - mu) cof(F) / J,
+  // b_a the shape-function gradients (b1..b3 = rows of Dm^-1, b0 = -(b1 + b2 + b3))
   d3 b[4];
   b[1] = mk3(Bm[0], Bm[1], Bm[2]);
   b[2] = mk3(Bm[3], Bm[4], Bm[5]);
   b[3] = mk3(Bm[6], Bm[7], Bm[8]);
   b[0] = mk3(-(Bm[0] + Bm[3] + Bm[6]), -(Bm[1] + Bm[4] + Bm[7]), -(Bm[2] + Bm[5] + Bm[8]));
-  // first Piola-Kirchhoff stress P = mu F + (lam lnJ - mu) cof(F) / J
   double kk = (lam * lnJ - mu) / J;
   double Pk[9];
   for (int i = 0; i < 9; ++i) Pk[i] = mu * F[i] + kk * cof[i];
@@ -122,72 +219,7 @@ __global__ void k_elastic(int n_tets, const int4* __restrict__ tets, const doubl
     tg[12 * (long)t + 3 * a + 2] = w * ga.z;
   }
   if (MODE == MODE_GRAD) return;
-  // SVD through the eigen-decomposition of F^T F
-  double C[9];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) C[3 * r + c] = F[r] * F[c] + F[3 + r] * F[3 + c] + F[6 + r] * F[6 + c];
-  double s2[3], V[9];
-  eig_sym3(C, s2, V);
-  double s[3];
-  for (int i = 0; i < 3; ++i) s[i] = sqrt(fmax(s2[i], 1e-300));
-  double U[9];  // U = F V diag(1/s)
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c)
-      U[3 * r + c] = (F[3 * r] * V[c] + F[3 * r + 1] * V[3 + c] + F[3 * r + 2] * V[6 + c]) / s[c];
-  // c_a = V^T b_a
-  d3 cb[4];
-  for (int a = 0; a < 4; ++a)
-    cb[a] = mk3(V[0] * b[a].x + V[3] * b[a].y + V[6] * b[a].z, V[1] * b[a].x + V[4] * b[a].y + V[7] * b[a].z,
-                V[2] * b[a].x + V[5] * b[a].y + V[8] * b[a].z);
-  double Hb[90];
-  for (int i = 0; i < 90; ++i) Hb[i] = 0.0;
-  // accumulate lam * w w^T over the 10 upper 3x3 blocks; w_a = U m_a where m_a = M c_a
-  auto add_mode = [&](double lm, const d3* m) {
-    if (!(lm > 0.0)) return;
-    d3 wv[4];
-    for (int a = 0; a < 4; ++a)
-      wv[a] = mk3(U[0] * m[a].x + U[1] * m[a].y + U[2] * m[a].z, U[3] * m[a].x + U[4] * m[a].y + U[5] * m[a].z,
-                  U[6] * m[a].x + U[7] * m[a].y + U[8] * m[a].z);
-    int blk = 0;
-    for (int a = 0; a < 4; ++a)
-      for (int bb = a; bb < 4; ++bb, ++blk)
-        for (int r = 0; r < 3; ++r)
-          for (int c = 0; c < 3; ++c) Hb[9 * blk + 3 * r + c] += lm * comp(wv[a], r) * comp(wv[bb], c);
-  };
-  // scaling modes
-  double A[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      A[3 * i + j] = (i == j) ? mu + (mu - lam * lnJ + lam) / (s[i] * s[i]) : lam / (s[i] * s[j]);
-  double la[3], av[9];
-  eig_sym3(A, la, av);
-  for (int k = 0; k < 3; ++k) {
-    d3 m[4];
-    for (int a = 0; a < 4; ++a) m[a] = mk3(av[k] * cb[a].x, av[3 + k] * cb[a].y, av[6 + k] * cb[a].z);
-    add_mode(la[k], m);
-  }
-  // twist and flip modes of each pair
-  const double r2 = 0.70710678118654752440;
-  for (int pr = 0; pr < 3; ++pr) {
-    int i = pr == 2 ? 0 : pr, j = pr == 2 ? 2 : pr + 1;
-    double ss = s[i] * s[j];
-    double lt = mu + (lam * lnJ - mu) / ss, lf = mu + (mu - lam * lnJ) / ss;
-    d3 mt[4], mf[4];
-    for (int a = 0; a < 4; ++a) {
-      double ci = comp(cb[a], i), cj = comp(cb[a], j);
-      double vt[3] = {0, 0, 0}, vf[3] = {0, 0, 0};
-      // (e_i e_j^T -/+ e_j e_i^T) c = e_i c_j -/+ e_j c_i
-      vt[i] = r2 * cj;
-      vt[j] = -r2 * ci;
-      vf[i] = r2 * cj;
-      vf[j] = r2 * ci;
-      mt[a] = mk3(vt[0], vt[1], vt[2]);
-      mf[a] = mk3(vf[0], vf[1], vf[2]);
-    }
-    add_mode(lt, mt);
-    add_mode(lf, mf);
-  }
-  for (int i = 0; i < 90; ++i) tH[90 * (long)t + i] = w * Hb[i];
+  tet_hessian<HT>(F, mu, lam, lnJ, Bm, w, tH + 90 * (long)t);
 }
 
 // ----------------------------------------------------------------- affine bodies
@@ -216,11 +248,11 @@ __device__ __noinline__ double body_energy(const double* __restrict__ Q, const d
   return Ein + wk * f;
 }
 
-template <int MODE>
+template <int MODE, class HT = double>
 __global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int* __restrict__ benv,
                          const uint8_t* __restrict__ bkin, const double* __restrict__ M4, const double* __restrict__ bvol,
                          const uint8_t* __restrict__ act, const double* __restrict__ q, const double* __restrict__ qt,
-                         double h2kA, double* __restrict__ bE, double* __restrict__ bg, double* __restrict__ bH) {
+                         double h2kA, double* __restrict__ bE, double* __restrict__ bg, HT* __restrict__ bH) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_bodies) return;
   int e = benv[b];
@@ -230,7 +262,7 @@ __global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int*
     if (MODE >= MODE_GRAD)
       for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = 0.0;
     if (MODE == MODE_HESS)
-      for (int i = 0; i < 144; ++i) bH[144 * (long)b + i] = (i % 13 == 0) ? 1.0 : 0.0;
+      for (int i = 0; i < 144; ++i) bH[144 * (long)b + i] = (i % 13 == 0) ? HT(1) : HT(0);
     return;
   }
   const double* Q = q + 3 * (long)bnode[b];
@@ -254,31 +286,38 @@ __global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int*
     }
   for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = g[i];
   if (MODE == MODE_GRAD) return;
-  double Ho[81];
-  double AtA[9];
+  // Hessian in the precision HT: orthogonality term projected to PSD, plus the mass blocks
+  HT Ah[9], Sh[9];
+  for (int i = 0; i < 9; ++i) {
+    Ah[i] = HT(A[i]);
+    Sh[i] = HT(S[i]);
+  }
+  HT Ho[81];
+  HT AtA[9];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) AtA[3 * i + j] = A[i] * A[j] + A[3 + i] * A[3 + j] + A[6 + i] * A[6 + j];
+    for (int j = 0; j < 3; ++j) AtA[3 * i + j] = Ah[i] * Ah[j] + Ah[3 + i] * Ah[3 + j] + Ah[6 + i] * Ah[6 + j];
   for (int k = 0; k < 3; ++k)
     for (int l = 0; l < 3; ++l)
       for (int m = 0; m < 3; ++m)
         for (int n = 0; n < 3; ++n) {
-          double v = A[3 * k + n] * A[3 * m + l];
+          HT v = Ah[3 * k + n] * Ah[3 * m + l];
           if (k == m) v += AtA[3 * n + l];
-          if (l == n) v += S[3 * k + m];
-          Ho[(3 * k + l) * 9 + 3 * m + n] = 4.0 * v;
+          if (l == n) v += Sh[3 * k + m];
+          Ho[(3 * k + l) * 9 + 3 * m + n] = HT(4) * v;
         }
-  project_psd_jacobi<9>(Ho);
-  double* Hout = bH + 144 * (long)b;
+  project_psd_jacobi<9, HT>(Ho);
+  HT* Hout = bH + 144 * (long)b;
   for (int I = 0; I < 4; ++I)
     for (int Jn = 0; Jn < 4; ++Jn)
       for (int k = 0; k < 3; ++k)
-        for (int l = 0; l < 3; ++l) Hout[(3 * I + k) * 12 + 3 * Jn + l] = (k == l) ? M[4 * I + Jn] : 0.0;
+        for (int l = 0; l < 3; ++l) Hout[(3 * I + k) * 12 + 3 * Jn + l] = (k == l) ? HT(M[4 * I + Jn]) : HT(0);
+  const HT wkh = HT(wk);
   for (int k = 0; k < 3; ++k)
     for (int l = 0; l < 3; ++l)
       for (int m = 0; m < 3; ++m)
         for (int n = 0; n < 3; ++n) {
           int qi = 3 + 3 * l + k, qj = 3 + 3 * n + m;
-          Hout[qi * 12 + qj] += wk * Ho[(3 * k + l) * 9 + 3 * m + n];
+          Hout[qi * 12 + qj] += wkh * Ho[(3 * k + l) * 9 + 3 * m + n];
         }
 }
 
@@ -316,10 +355,10 @@ __device__ __noinline__ double barrier_energy(int kind, int type, const d3* X, d
   return scale * m * b;
 }
 
-template <int MODE>
+template <int MODE, class HT = double>
 __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
                           const double* __restrict__ ptx, double h2, double dhat, double kappa, double* __restrict__ sE,
-                          double* __restrict__ sg, double* __restrict__ sH) {
+                          double* __restrict__ sg, HT* __restrict__ sH) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_ct) return;
   ContactRec c = ct[k];
@@ -364,7 +403,8 @@ __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uin
   for (int i = 0; i < 12; ++i) gm[i] = c.kind == 1 ? m1 * gc[i] : 0.0;
   for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = scale * (m * gb[i] + b * gm[i]);
   if (MODE == MODE_GRAD) return;
-  double H[144];
+  // the Hessian is formed in FP64 and projected to PSD in the precision HT
+  HT H[144];
   double ka = b2 / (4.0 * d * d) - b1 / (4.0 * d * d * d);
   for (int i = 0; i < 12; ++i)
     for (int j = i; j < 12; ++j) {
@@ -372,10 +412,10 @@ __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uin
       double hb = ka * gs[i] * gs[j] + kb * Hs[u];
       double v = m * hb;
       if (c.kind == 1) v += b * (m2 * gc[i] * gc[j] + m1 * Hc[u]) + gm[i] * gb[j] + gb[i] * gm[j];
-      H[12 * i + j] = scale * v;
-      H[12 * j + i] = scale * v;
+      H[12 * i + j] = HT(scale * v);
+      H[12 * j + i] = HT(scale * v);
     }
-  project_psd_jacobi<12>(H);
+  project_psd_jacobi<12, HT>(H);
   for (int i = 0; i < 12; ++i)
     for (int j = i; j < 12; ++j) sH[78 * (long)k + up_idx(i, j, 12)] = H[12 * i + j];
 }
@@ -407,10 +447,10 @@ __device__ __noinline__ double friction_energy(const FrictionRec& f, const doubl
   return h2 * f.mu_lambda * f0;
 }
 
-template <int MODE>
+template <int MODE, class HT = double>
 __global__ void k_friction(int n_fr, const FrictionRec* __restrict__ fr, const uint8_t* __restrict__ act,
                            const double* __restrict__ ptx, const double* __restrict__ ptx_t, double h2, double eh,
-                           double* __restrict__ sE, double* __restrict__ sg, double* __restrict__ sH) {
+                           double* __restrict__ sE, double* __restrict__ sg, HT* __restrict__ sH) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_fr) return;
   FrictionRec f = fr[k];
@@ -441,7 +481,7 @@ __global__ void k_friction(int n_fr, const FrictionRec* __restrict__ fr, const u
     for (int c = 0; c < 3; ++c) M[3 * r + c] = a * ((r == c ? 1.0 : 0.0) - f.n[r] * f.n[c]) + bc * comp(u, r) * comp(u, c);
   for (int i = 0; i < 12; ++i)
     for (int j = i; j < 12; ++j)
-      sH[78 * (long)k + up_idx(i, j, 12)] = s * f.c[i / 3] * f.c[j / 3] * M[3 * (i % 3) + (j % 3)];
+      sH[78 * (long)k + up_idx(i, j, 12)] = HT(s * f.c[i / 3] * f.c[j / 3] * M[3 * (i % 3) + (j % 3)]);
 }
 
 // ----------------------------------------------------------------- per-env energy sums

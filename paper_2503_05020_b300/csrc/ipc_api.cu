@@ -12,6 +12,7 @@
 #include <numeric>
 #include <stdexcept>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ipc.h"
@@ -380,6 +381,16 @@ struct ipc_scene {
   // energies / stencils
   DBuf<double> nodeE, tetE, tet_g, tet_H, bodyE, body_g, body_H;
   DBuf<double> bsr_val, Ps, Pb;
+  // mixed precision: FP32 Hessians, sliced-ELL values, preconditioner blocks, stencil Hessians,
+  // entry weights and every vector of the PCG (the FP64 twins above hold them otherwise)
+  DBuf<float> f_tet_H, f_body_H, f_bsr_val, f_Ps, f_Pb, f_sH, f_ns_w, f_ns_xb, f_st_t;
+  DBuf<float> f_r, f_z, f_d, f_y, f_x, f_part;
+  bool mixed() const { return desc.precision == IPC_MIXED; }
+  template <class T>
+  static T* hp(DBuf<double>& d, DBuf<float>& f) {
+    if constexpr (std::is_same<T, double>::value) return d.p;
+    else return f.p;
+  }
   DBuf<double> pcg_r, pcg_z, pcg_d, pcg_y, pcg_x, part_a, part_b, part_c, pcg_rz, pcg_bb;
   DBuf<int> pcg_it, pcg_active;
   DBuf<double> pcg_part;  // per-slot partial sums of the persistent PCG
@@ -838,7 +849,7 @@ struct ipc_scene {
       pslice_off.upload(poff, s);
       pslice_row.upload(prow, s);
       pslice_sel.upload(psel, s);
-      pcg_part.alloc(6 * ((size_t)n_slices + NB) + 6);
+      pcg_part.alloc(mixed() ? 1 : 6 * ((size_t)n_slices + NB) + 6);
     }
     slice_w.upload(sw, s);
     slice_vbase.upload(svb, s);
@@ -890,7 +901,7 @@ struct ipc_scene {
     tile_end.upload(tn, s);
     tile_off.upload(toff, s);
     pcg_C = 0;
-    if (desc.pcg_cluster >= 0) {
+    if (desc.pcg_cluster >= 0 || mixed()) {
       std::vector<int> iota(E);
       std::iota(iota.begin(), iota.end(), 0);
       env_iota.upload(iota, s);
@@ -900,11 +911,19 @@ struct ipc_scene {
       pcg_iterb.alloc(E);
       pcg_its.alloc(E);
       pcg_runs.alloc(E);
-      pcg_resident[0] = resident_clusters<1>();
-      pcg_resident[1] = resident_clusters<2>();
-      pcg_resident[2] = resident_clusters<4>();
-      pcg_resident[3] = resident_clusters<8>();
-      pcg_resident[4] = resident_clusters<16>();
+      if (mixed()) {
+        pcg_resident[0] = resident_clusters<1, float>();
+        pcg_resident[1] = resident_clusters<2, float>();
+        pcg_resident[2] = resident_clusters<4, float>();
+        pcg_resident[3] = resident_clusters<8, float>();
+        pcg_resident[4] = resident_clusters<16, float>();
+      } else {
+        pcg_resident[0] = resident_clusters<1, double>();
+        pcg_resident[1] = resident_clusters<2, double>();
+        pcg_resident[2] = resident_clusters<4, double>();
+        pcg_resident[3] = resident_clusters<8, double>();
+        pcg_resident[4] = resident_clusters<16, double>();
+      }
     }
     root_off_tri.upload(tri_off_h, s);
     root_off_ed.upload(ed_off_h, s);
@@ -940,14 +959,28 @@ struct ipc_scene {
     nodeE.alloc(NN);
     tetE.alloc(NT);
     tet_g.alloc(12 * (size_t)NT);
-    tet_H.alloc(90 * (size_t)NT);
     bodyE.alloc(NB);
     body_g.alloc(12 * (size_t)NB);
-    body_H.alloc(144 * (size_t)NB);
-    bsr_val.alloc(std::max(sell_nval, 1L));
-    bsr_val.zero(s);  // padding blocks must read as zero
-    Ps.alloc(9 * (size_t)NN);
-    Pb.alloc(144 * (size_t)NB);
+    if (mixed()) {
+      f_tet_H.alloc(90 * (size_t)NT);
+      f_body_H.alloc(144 * (size_t)NB);
+      f_bsr_val.alloc(std::max(sell_nval, 1L));
+      f_bsr_val.zero(s);  // padding blocks must read as zero
+      f_Ps.alloc(9 * (size_t)NN);
+      f_Pb.alloc(144 * (size_t)NB);
+      for (DBuf<float>* b : {&f_r, &f_z, &f_d, &f_y, &f_x}) {
+        b->alloc(n3);
+        b->zero(s);  // kinematic soft rows are never written by the persistent PCG: d stays 0
+      }
+      f_part.alloc(6 * ((size_t)n_slices + NB) + 6);
+    } else {
+      tet_H.alloc(90 * (size_t)NT);
+      body_H.alloc(144 * (size_t)NB);
+      bsr_val.alloc(std::max(sell_nval, 1L));
+      bsr_val.zero(s);  // padding blocks must read as zero
+      Ps.alloc(9 * (size_t)NN);
+      Pb.alloc(144 * (size_t)NB);
+    }
     for (DBuf<double>* b : {&part_a, &part_b, &part_c}) b->alloc(NTILE);
     pcg_rz.alloc(2 * (size_t)E);
     pcg_bb.alloc(E);
@@ -1076,8 +1109,13 @@ struct ipc_scene {
     st_env.ensure(ns + 1);
     sE.ensure(ns + 1);
     sg.ensure(12 * (size_t)ns + 12);
-    sH.ensure(78 * (size_t)ns + 78);
     st_t.ensure(12 * (size_t)ns + 12);
+    if (mixed()) {
+      f_sH.ensure(78 * (size_t)ns + 78);
+      f_st_t.ensure(12 * (size_t)ns + 12);
+    } else {
+      sH.ensure(78 * (size_t)ns + 78);
+    }
     launch(k_stencil_table, ns, 256, n_ct, n_fr, (const ContactRec*)ct.p, (const FrictionRec*)fr.p, st_pts.p, st_env.p);
   }
   // ------------------------------------------------------------------ energy
@@ -1085,25 +1123,36 @@ struct ipc_scene {
   // computed here. Result per env in out.
   template <int MODE>
   void evaluate(const double* q, const uint8_t* act, double* out) {
+    if (MODE == MODE_HESS && mixed()) evaluate_t<MODE, float>(q, act, out);
+    else evaluate_t<MODE, double>(q, act, out);
+  }
+  // HT: precision of the Hessians (energies and gradients are FP64 in every mode)
+  template <int MODE, class HT>
+  void evaluate_t(const double* q, const uint8_t* act, double* out) {
     launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p, q, ptx.p);
     constraint_set(act);
     stencil_table();
+    // Hessian outputs (taken after stencil_table, which may grow the stencil buffers)
+    HT* tH = MODE == MODE_HESS ? hp<HT>(tet_H, f_tet_H) : nullptr;
+    HT* bH = MODE == MODE_HESS ? hp<HT>(body_H, f_body_H) : nullptr;
+    HT* sHp = MODE == MODE_HESS ? hp<HT>(sH, f_sH) : nullptr;
     double h = desc.dt, h2 = h * h;
     launch(k_inertia_energy, NN, 256, NN, layout(), act, q, (const double*)xtilde.p, nodeE.p);
     int efam = MODE == MODE_ENERGY ? IPC_PROF_LS_ENERGY : IPC_PROF_ELASTIC;
     pbeg(efam);
-    launch(k_elastic<MODE>, NT, 128, NT, (const int4*)tets.p, (const double*)tet_prm.p, (const int*)tet_env.p, act, q,
-           h2, tetE.p, tet_g.p, tet_H.p, e_bad.p, MODE == MODE_ENERGY ? (unsigned long long*)nullptr : punits(IPC_PROF_ELASTIC));
+    launch(k_elastic<MODE, HT>, NT, 128, NT, (const int4*)tets.p, (const double*)tet_prm.p, (const int*)tet_env.p, act,
+           q, h2, tetE.p, tet_g.p, tH, e_bad.p, MODE == MODE_ENERGY ? (unsigned long long*)nullptr : punits(IPC_PROF_ELASTIC));
     pend(efam);
-    launch(k_bodies<MODE>, NB, 64, NB, (const int*)body_node.p, (const int*)body_env.p, (const uint8_t*)body_kin.p,
+    launch(k_bodies<MODE, HT>, NB, 64, NB, (const int*)body_node.p, (const int*)body_env.p, (const uint8_t*)body_kin.p,
            (const double*)M4.p, (const double*)bvol.p, act, q, (const double*)xtilde.p, h2 * desc.kappa_affine, bodyE.p,
-           body_g.p, body_H.p);
+           body_g.p, bH);
     int cfam = MODE == MODE_ENERGY ? IPC_PROF_LS_ENERGY : IPC_PROF_CONTACT;
     pbeg(cfam);
-    launch(k_barrier<MODE>, n_ct, 64, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, h2, desc.dhat, desc.kappa,
-           sE.p, sg.p, sH.p);
-    launch(k_friction<MODE>, n_fr, 128, n_fr, (const FrictionRec*)fr.p, act, (const double*)ptx.p,
-           (const double*)ptx_t.p, h2, desc.eps_v * h, sE.p + n_ct, sg.p + 12 * (size_t)n_ct, sH.p + 78 * (size_t)n_ct);
+    launch(k_barrier<MODE, HT>, n_ct, 64, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, h2, desc.dhat,
+           desc.kappa, sE.p, sg.p, sHp);
+    launch(k_friction<MODE, HT>, n_fr, 128, n_fr, (const FrictionRec*)fr.p, act, (const double*)ptx.p,
+           (const double*)ptx_t.p, h2, desc.eps_v * h, sE.p + n_ct, sg.p + 12 * (size_t)n_ct,
+           sHp ? sHp + 78 * (size_t)n_ct : sHp);
     pend(cfam);
     EnergyLists L{nodeE.p, node_off.p, tetE.p, tet_off.p, bodyE.p, body_off.p, sE.p, st_env.p,
                   n_ct_pt, n_ct - n_ct_pt, n_fr_pt, n_fr};
@@ -1130,23 +1179,41 @@ struct ipc_scene {
     scan(ns_cnt.p, NN, ns_ptr.p, false);
     ns_src.ensure(ne + 1);
     if (ne > 0) CK(cudaMemcpyAsync(ns_src.p, st_vals.p, ne * sizeof(unsigned), cudaMemcpyDeviceToDevice, stream));
-    ns_w.ensure(ne + 1);
-    ns_xb.ensure(3 * (size_t)ne + 3);
-    launch(k_entry_weights, NN, 256, NN, layout(), act, (const int*)ns_ptr.p, (const int*)ns_src.p, (const int*)st_pts.p,
-           ns_w.p, ns_xb.p);
+    if (mixed()) {
+      f_ns_w.ensure(ne + 1);
+      f_ns_xb.ensure(3 * (size_t)ne + 3);
+      launch(k_entry_weights<float>, NN, 256, NN, layout(), act, (const int*)ns_ptr.p, (const int*)ns_src.p,
+             (const int*)st_pts.p, f_ns_w.p, f_ns_xb.p);
+    } else {
+      ns_w.ensure(ne + 1);
+      ns_xb.ensure(3 * (size_t)ne + 3);
+      launch(k_entry_weights<double>, NN, 256, NN, layout(), act, (const int*)ns_ptr.p, (const int*)ns_src.p,
+             (const int*)st_pts.p, ns_w.p, ns_xb.p);
+    }
   }
 
-  SpmvArgs spmv_args() {
-    Sell S{tile_slice.p, slice_w.p, slice_vbase.p, slice_cbase.p, sell_col.p, bsr_val.p};
-    return SpmvArgs{S, bsr_ptr.p, body_H.p, ns_ptr.p, ns_src.p, ns_w.p, ns_xb.p, st_pts.p, st_t.p};
+  // matrix in HT, vectors and stencil products (st) in VT
+  template <class HT, class VT>
+  SpmvArgsT<HT, VT> spmv_args(const VT* st) {
+    SellT<HT> S{tile_slice.p, slice_w.p, slice_vbase.p, slice_cbase.p, sell_col.p, hp<HT>(bsr_val, f_bsr_val)};
+    return SpmvArgsT<HT, VT>{S,  bsr_ptr.p, hp<HT>(body_H, f_body_H), ns_ptr.p, ns_src.p, hp<HT>(ns_w, f_ns_w),
+                             hp<HT>(ns_xb, f_ns_xb), st_pts.p, st};
   }
-  // y = H d over the envs in run (stencil product, then BSR/body rows); partial d.y per tile
+  SpmvArgs spmv_args() { return spmv_args<double, double>(st_t.p); }
+  // y = H d over the envs in run (stencil product, then BSR/body rows); partial d.y per tile.
+  // FP64 vectors; the matrix is in the scene's Hessian precision.
   void matvec(const uint8_t* run, const double* d, double* y, double* part) {
+    if (mixed()) matvec_t<float>(run, d, y, part);
+    else matvec_t<double>(run, d, y, part);
+  }
+  template <class HT>
+  void matvec_t(const uint8_t* run, const double* d, double* y, double* part) {
     int ns = n_ct + n_fr;
-    launch(k_stencil_mv, 16L * ns, 128, ns, layout(), (const int*)st_env.p, (const int*)st_pts.p, run, (const double*)sH.p, d,
-           st_t.p);
+    launch(k_stencil_mv<HT, double>, 16L * ns, 128, ns, layout(), (const int*)st_env.p, (const int*)st_pts.p, run,
+           (const HT*)hp<HT>(sH, f_sH), d, st_t.p);
     pbeg(IPC_PROF_SPMV);
-    launch_grid(k_spmv, NTILE, TILE, tiles(), layout(), spmv_args(), run, d, y, part, punits(IPC_PROF_SPMV));
+    launch_grid(k_spmv<HT, double>, NTILE, TILE, tiles(), layout(), spmv_args<HT, double>(st_t.p), run, d, y, part,
+                punits(IPC_PROF_SPMV));
     pend(IPC_PROF_SPMV);
   }
 
@@ -1161,9 +1228,9 @@ struct ipc_scene {
     at.val.clusterDim.z = 1;
     return at;
   }
-  template <int C>
+  template <int C, class T>
   int resident_clusters() {
-    if (C > 8) CK(cudaFuncSetAttribute(k_pcg_cluster<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    if (C > 8) CK(cudaFuncSetAttribute(k_pcg_cluster<C, T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchAttribute at = cluster_attr<C>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(C * std::max(E, 1)));
@@ -1172,7 +1239,7 @@ struct ipc_scene {
     cfg.attrs = &at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<C>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<C, T>, &cfg) != cudaSuccess) {
       cudaGetLastError();  // a size the device cannot schedule: never chosen
       n = 0;
     }
@@ -1189,8 +1256,8 @@ struct ipc_scene {
     }
     return 1;
   }
-  template <int C>
-  void launch_pcg_cluster(const PcgClusterArgs& a, int n) {
+  template <int C, class T>
+  void launch_pcg_cluster(const PcgClusterArgs<T>& a, int n) {
     cudaLaunchAttribute at = cluster_attr<C>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(C * n));
@@ -1198,10 +1265,11 @@ struct ipc_scene {
     cfg.stream = stream;
     cfg.attrs = &at;
     cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<C>, a));
+    CK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<C, T>, a));
     ++launches;
   }
-  void launch_pcg_any(int C, const PcgClusterArgs& a, int n) {
+  template <class T>
+  void launch_pcg_any(int C, const PcgClusterArgs<T>& a, int n) {
     switch (C) {
       case 1: launch_pcg_cluster<1>(a, n); break;
       case 2: launch_pcg_cluster<2>(a, n); break;
@@ -1215,30 +1283,33 @@ struct ipc_scene {
   // envs still running are listed on the device and relaunched, with a cluster size chosen for
   // their number. The first launch starts every solve.
   static constexpr int PCG_CHUNK = 32;
+  // T: precision of the solve (FP64, or FP32 in mixed precision)
+  template <class T>
   void pcg_persistent(const uint8_t* act) {
-    PcgClusterArgs a;
+    PcgClusterArgs<T> a;
     a.L = layout();
-    a.A = spmv_args();
+    T* st = hp<T>(st_t, f_st_t);
+    a.A = spmv_args<T, T>(st);
     a.pslice_off = pslice_off.p;
     a.pslice_row = pslice_row.p;
     a.pslice_sel = pslice_sel.p;
     a.body_off = body_off.p;
     a.st_env = st_env.p;
-    a.sH = sH.p;
+    a.sH = hp<T>(sH, f_sH);
     int b[5] = {0, n_ct_pt, n_ct, n_ct + n_fr_pt, n_ct + n_fr};
     for (int i = 0; i < 5; ++i) a.st_bounds[i] = b[i];
-    a.Ps = Ps.p;
-    a.Pb = Pb.p;
+    a.Ps = hp<T>(Ps, f_Ps);
+    a.Pb = hp<T>(Pb, f_Pb);
     a.act = act;
-    a.x = pcg_x.p;
-    a.r = pcg_r.p;
-    a.z = pcg_z.p;
-    a.d = pcg_d.p;
-    a.y = pcg_y.p;
-    a.st_t = st_t.p;
+    a.x = hp<T>(pcg_x, f_x);
+    a.r = hp<T>(pcg_r, f_r);
+    a.z = hp<T>(pcg_z, f_z);
+    a.d = hp<T>(pcg_d, f_d);
+    a.y = hp<T>(pcg_y, f_y);
+    a.st_t = st;
     a.tol2 = desc.pcg_rel_tol * desc.pcg_rel_tol;
     a.max_it = desc.max_pcg_iters;
-    a.part = pcg_part.p;
+    a.part = hp<T>(pcg_part, f_part);
     a.s_total = n_slices;
     a.n_bodies = NB;
     a.env_list = env_iota.p;
@@ -1267,8 +1338,12 @@ struct ipc_scene {
     }
   }
   void pcg(const uint8_t* act) {
+    if (mixed()) {
+      pcg_persistent<float>(act);
+      return;
+    }
     if (desc.pcg_cluster >= 0) {
-      pcg_persistent(act);
+      pcg_persistent<double>(act);
       return;
     }
     PcgState S{pcg_rz.p, pcg_bb.p, pcg_it.p, pcg_run.p, pcg_active.p, e_stats.p + 0};
@@ -1331,13 +1406,38 @@ struct ipc_scene {
     launch(k_assemble_grad, NN, 256, NN, layout(), act, (const double*)x.p, (const double*)xtilde.p, (const int*)nt_ptr.p,
            (const int*)nt_src.p, (const double*)tet_g.p, (const double*)body_g.p, (const int*)ns_ptr.p,
            (const int*)ns_src.p, (const int*)st_pts.p, (const double*)sg.p, grad.p, nodeE.p);
-    launch(k_assemble_bsr, NNZB, 128, NNZB, (const int*)blk_row.p, (const int*)bsr_col.p, layout(), act,
-           (const int*)blk_ptr.p, (const int*)blk_src.p, (const double*)tet_H.p, (const long*)blk_pos.p, bsr_val.p);
-    launch(k_precond_soft, NN, 256, NN, layout(), act, (const long*)diag_pos.p, (const double*)bsr_val.p,
-           (const int*)ns_ptr.p, (const int*)ns_src.p, (const double*)sH.p, Ps.p);
-    launch_grid(k_precond_body, NB, 144, NB, layout(), (const int*)body_env.p, act, (const double*)body_H.p,
-                (const int*)ns_ptr.p, (const int*)ns_src.p, (const int*)st_pts.p, (const double*)sH.p, Pb.p);
+    if (mixed()) assemble_h<float>(act);
+    else assemble_h<double>(act);
     pend(IPC_PROF_ASSEMBLY);
+  }
+  // sliced-ELL values and block-Jacobi blocks in the Hessian precision HT
+  template <class HT>
+  void assemble_h(const uint8_t* act) {
+    HT* val = hp<HT>(bsr_val, f_bsr_val);
+    const HT* sHp = hp<HT>(sH, f_sH);
+    launch(k_assemble_bsr<HT>, NNZB, 128, NNZB, (const int*)blk_row.p, (const int*)bsr_col.p, layout(), act,
+           (const int*)blk_ptr.p, (const int*)blk_src.p, (const HT*)hp<HT>(tet_H, f_tet_H), (const long*)blk_pos.p,
+           val);
+    launch(k_precond_soft<HT>, NN, 256, NN, layout(), act, (const long*)diag_pos.p, (const HT*)val,
+           (const int*)ns_ptr.p, (const int*)ns_src.p, sHp, hp<HT>(Ps, f_Ps));
+    launch_grid(k_precond_body<HT>, NB, 144, NB, layout(), (const int*)body_env.p, act,
+                (const HT*)hp<HT>(body_H, f_body_H), (const int*)ns_ptr.p, (const int*)ns_src.p, (const int*)st_pts.p,
+                sHp, hp<HT>(Pb, f_Pb));
+  }
+  // r = -g - H pbar in the solve's precision, for the envs in act
+  void rhs(const uint8_t* act) {
+    if (mixed())
+      launch(k_rhs<float>, NN, 256, NN, layout(), act, (const double*)grad.p, (const double*)pcg_y.p, f_r.p);
+    else
+      launch(k_rhs<double>, NN, 256, NN, layout(), act, (const double*)grad.p, (const double*)pcg_y.p, pcg_r.p);
+  }
+  void direction(EnvCtl C) {
+    if (mixed())
+      launch(k_direction<float>, NN, 256, NN, layout(), C, (const float*)f_x.p, (const double*)pbar.p,
+             (const double*)bbox.p, p.p);
+    else
+      launch(k_direction<double>, NN, 256, NN, layout(), C, (const double*)pcg_x.p, (const double*)pbar.p,
+             (const double*)bbox.p, p.p);
   }
 
   // step set-up for the envs in act: x^t, x~, targets, positions at x^t, trees, friction lag
@@ -1370,11 +1470,9 @@ struct ipc_scene {
       // kinematic step and the reduced right-hand side -g - H pbar
       launch(k_pbar, NN, 256, NN, layout(), C, (const double*)x.p, (const double*)xtarget.p, pbar.p);
       matvec(e_iter.p, pbar.p, pcg_y.p, part_a.p);
-      launch(k_rhs, NN, 256, NN, layout(), (const uint8_t*)e_iter.p, (const double*)grad.p, (const double*)pcg_y.p,
-             pcg_r.p);
+      rhs(e_iter.p);
       pcg(e_iter.p);
-      launch(k_direction, NN, 256, NN, layout(), C, (const double*)pcg_x.p, (const double*)pbar.p, (const double*)bbox.p,
-             p.p);
+      direction(C);
       launch(k_env_converge, E, 128, E, C, desc.dt, desc.newton_tol);
       if (count_flags(e_iter.p) == 0) break;
       // CCD step filter: swept candidates at [x, x + p], ACCD, per-env minimum
@@ -1635,11 +1733,9 @@ ipc_status ipc_newton_direction(ipc_scene* s, int32_t env_id, double* pout) {
   s->assemble(s->e_iter.p);
   s->launch(k_pbar, s->NN, 256, s->NN, s->layout(), C, (const double*)s->x.p, (const double*)s->xtarget.p, s->pbar.p);
   s->matvec(s->e_iter.p, s->pbar.p, s->pcg_y.p, s->part_a.p);
-  s->launch(k_rhs, s->NN, 256, s->NN, s->layout(), (const uint8_t*)s->e_iter.p, (const double*)s->grad.p,
-            (const double*)s->pcg_y.p, s->pcg_r.p);
+  s->rhs(s->e_iter.p);
   s->pcg(s->e_iter.p);
-  s->launch(k_direction, s->NN, 256, s->NN, s->layout(), C, (const double*)s->pcg_x.p, (const double*)s->pbar.p,
-            (const double*)s->bbox.p, s->p.p);
+  s->direction(C);
   CK(cudaMemcpyAsync(pout, s->p.p + 3 * (size_t)s->h_node_off[li], h.ndof * 8, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemsetAsync(s->e_iter.p, 0, s->E, s->stream));
   CK(cudaStreamSynchronize(s->stream));

@@ -102,19 +102,21 @@ __global__ void k_pbar(int n_nodes, Layout L, EnvCtl C, const double* __restrict
   st3(pbar, i, p);
 }
 
-// r = -g - y on free DOFs, 0 on kinematic ones
+// r = -g - y on free DOFs, 0 on kinematic ones (formed in FP64, stored in the solve's type VT)
+template <class VT>
 __global__ void k_rhs(int n_nodes, Layout L, const uint8_t* __restrict__ act, const double* __restrict__ g,
-                      const double* __restrict__ y, double* __restrict__ r) {
+                      const double* __restrict__ y, VT* __restrict__ r) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
   if (!act[L.node_env[i]]) return;
   int b = L.node_body[i];
   bool kin = b < 0 ? L.node_kin[i] : L.body_kin[b];
-  for (int k = 0; k < 3; ++k) r[3L * i + k] = kin ? 0.0 : -g[3L * i + k] - y[3L * i + k];
+  for (int k = 0; k < 3; ++k) r[3L * i + k] = kin ? VT(0) : VT(-g[3L * i + k] - y[3L * i + k]);
 }
 
 // p = delta (free) or pbar (kinematic); infinity norm in world space of the free part
-__global__ void k_direction(int n_nodes, Layout L, EnvCtl C, const double* __restrict__ delta,
+template <class VT>
+__global__ void k_direction(int n_nodes, Layout L, EnvCtl C, const VT* __restrict__ delta,
                             const double* __restrict__ pbar, const double* __restrict__ bbox, double* __restrict__ p) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
@@ -122,7 +124,7 @@ __global__ void k_direction(int n_nodes, Layout L, EnvCtl C, const double* __res
   if (!C.iter[e]) return;
   int b = L.node_body[i];
   bool kin = b < 0 ? L.node_kin[i] : L.body_kin[b];
-  d3 v = kin ? ld3(pbar, i) : ld3(delta, i);
+  d3 v = kin ? ld3(pbar, i) : mk3(double(delta[3L * i]), double(delta[3L * i + 1]), double(delta[3L * i + 2]));
   st3(p, i, v);
   if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(&C.nanp[e], 1);
   if (kin) return;
@@ -133,7 +135,8 @@ __global__ void k_direction(int n_nodes, Layout L, EnvCtl C, const double* __res
     // max over the 8 rest bounding-box corners of |J(corner) p_q|_inf
     long base = i;
     d3 pq[4];
-    for (int k = 0; k < 4; ++k) pq[k] = kin ? mk3(0, 0, 0) : ld3(delta, base + k);
+    for (int k = 0; k < 4; ++k)
+      pq[k] = mk3(double(delta[3 * (base + k)]), double(delta[3 * (base + k) + 1]), double(delta[3 * (base + k) + 2]));
     const double* B = bbox + 6L * b;
     for (int c = 0; c < 8; ++c) {
       double xb0 = (c & 1) ? B[3] : B[0], xb1 = (c & 2) ? B[4] : B[1], xb2 = (c & 4) ? B[5] : B[2];

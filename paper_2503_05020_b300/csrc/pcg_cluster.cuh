@@ -26,28 +26,30 @@ namespace cg = cooperative_groups;
 constexpr int PCG_THREADS = 256;
 constexpr int PCG_WARPS = PCG_THREADS / 32;
 
+// T: precision of the matrix, the vectors and every sum (FP64, or FP32 in mixed precision).
+template <class T>
 struct PcgClusterArgs {
   Layout L;
-  SpmvArgs A;
+  SpmvArgsT<T, T> A;
   const int* pslice_off;  // per env: first slice of its free soft rows (n_env + 1 entries)
   const int* pslice_row;  // 32 per slice: the row (node), -1 for padding
   const int* pslice_sel;  // 32 per slice: sliced-ELL slice * 32 + lane of that row
   const int* body_off;    // per env: first body (n_env + 1 entries)
   const int* st_env;
-  const double* sH;
+  const T* sH;
   int st_bounds[5];       // stencil sublists [pt | ee | friction pt | friction ee], each env-sorted
-  const double* Ps;
-  const double* Pb;
+  const T* Ps;
+  const T* Pb;
   const uint8_t* act;
-  double* x;              // solution (delta), out
-  double* r;              // in: right-hand side; out: residual
-  double* z;
-  double* d;
-  double* y;
-  double* st_t;           // stencil products (the same buffer SpmvArgs reads)
-  double tol2;
+  T* x;                   // solution (delta), out
+  T* r;                   // in: right-hand side; out: residual
+  T* z;
+  T* d;
+  T* y;
+  T* st_t;                // stencil products (the same buffer SpmvArgs reads)
+  double tol2;             // (relative tolerance)^2
   int max_it;
-  double* part;               // slot partials: 2 x 3 doubles x (s_total + n_bodies)
+  T* part;                    // slot partials: 2 x 3 values x (s_total + n_bodies)
   int s_total;                // slices of the whole batch
   int n_bodies;               // rigid bodies of the whole batch
   const int* env_list;        // env of each cluster
@@ -66,13 +68,13 @@ struct PcgClusterArgs {
 // the env alone: lane l of warp 0 adds slots l, l + 32, ... and the lanes are combined by a fixed
 // butterfly. Every CTA of the cluster computes the same bits; the result is broadcast through
 // shared memory. Call after a cluster barrier that publishes the partials.
-template <int K>
-DEV void env_sum(const double* part, int S0, int S1, int s_total, int b0, int b1, double* tot, double (&v)[K]) {
+template <int K, class T>
+DEV void env_sum(const T* part, int S0, int S1, int s_total, int b0, int b1, T* tot, T (&v)[K]) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x, ns = S1 - S0, n = ns + (b1 - b0);
-    double s[K];
+    T s[K];
 #pragma unroll
-    for (int q = 0; q < K; ++q) s[q] = 0.0;
+    for (int q = 0; q < K; ++q) s[q] = T(0);
     for (int j = lane; j < n; j += 32) {
       long slot = j < ns ? S0 + j : (long)s_total + b0 + (j - ns);
 #pragma unroll
@@ -89,48 +91,33 @@ DEV void env_sum(const double* part, int S0, int S1, int s_total, int b0, int b1
   for (int q = 0; q < K; ++q) v[q] = tot[q];
 }
 
-// y row of one free soft node (sliced-ELL blocks at sel = slice * 32 + lane, plus its stencil
-// entries); returns d_row . y_row
-DEV double soft_row_cg(const SpmvArgs& A, int sel, int row, const double* d, double* y) {
-  const int slice = sel >> 5, lane = sel & 31;
-  d3 acc = mk3(0, 0, 0);
-  int w = A.S.width[slice];
-  const int* col = A.S.col + A.S.cbase[slice] + lane;
-  const double* V = A.S.val + A.S.vbase[slice] + lane;
-#pragma unroll 4
-  for (int kk = 0; kk < w; ++kk) {
-    int c = col[32 * kk];  // padding blocks: the row itself, zero values
-    d3 dv = ldcg3(d, c);
-    const double* B = V + 288L * kk;
-    acc = acc + mk3(B[0] * dv.x + B[32] * dv.y + B[64] * dv.z, B[96] * dv.x + B[128] * dv.y + B[160] * dv.z,
-                    B[192] * dv.x + B[224] * dv.y + B[256] * dv.z);
-  }
-  int k = A.ns_ptr[row], end = A.ns_ptr[row + 1];
-#pragma unroll 4
-  for (; k < end; ++k) acc = acc + A.ns_w[k] * ldcg3(A.st_t, A.ns_src[k]);
-  st3(y, row, acc);
-  return dot(acc, ldcg3(d, row));
+// Algorithmic bytes of one PCG iteration, per item, with values of b = sizeof(T) bytes. A soft
+// row: its sliced-ELL blocks (9b + 4 B column each), d read and y written (6b), 16 B of row
+// pointers, its stencil entries (4 B index + b weight + 3b stencil product each), then the
+// vector phase: x, r read and written (12b), d, y read (6b), the 3x3 preconditioner block (9b),
+// z written (3b) and d = z + beta d (9b). A rigid body: dense block (144b), its d and y (24b),
+// per p-node entry 4 B + 3b rest coordinates + 3b stencil product, the 12x12 preconditioner
+// (144b) and 12 DOFs x 10b of vector traffic. A stencil: packed Hessian (78b), 4 point indices
+// (16 B), 4 gathered d triples (12b) and t written (12b).
+template <class T>
+DEV double soft_iter_bytes(const SpmvArgsT<T, T>& A, int row) {
+  const double b = sizeof(T);
+  return (9 * b + 4) * (A.bsr_ptr[row + 1] - A.bsr_ptr[row]) + 6 * b + 16.0 +
+         (4 + 4 * b) * (A.ns_ptr[row + 1] - A.ns_ptr[row]) + 39 * b;
+}
+template <class T>
+DEV double body_iter_bytes(const Layout& L, const SpmvArgsT<T, T>& A, int bd) {
+  const double b = sizeof(T);
+  long base = L.body_node[bd];
+  return 168 * b + (4 + 6 * b) * (A.ns_ptr[base + 1] - A.ns_ptr[base]) + 144 * b + 120 * b;
+}
+template <class T>
+DEV double stencil_iter_bytes() {
+  return 78.0 * sizeof(T) + 16.0 + 24.0 * sizeof(T);
 }
 
-// Algorithmic bytes of one PCG iteration, per item. A soft row: its sliced-ELL blocks and
-// stencil entries as in the stand-alone product (76 B per block, 36 B per entry, 8 B row
-// pointers, 24 B d and 24 B y), plus the vector phase: x, r read and written (96 B), d, y read
-// (48 B), the 3x3 preconditioner block (72 B), z written (24 B), then d = z + beta d (72 B).
-// A rigid body: dense block 1152 B, its d and y (192 B), 52 B per p-node entry, the 12x12
-// preconditioner (1152 B) and 12 DOFs x 80 B of vector traffic. A stencil: packed Hessian
-// (624 B), 4 point indices (16 B), 4 gathered d triples (96 B) and t written (96 B).
-DEV double soft_iter_bytes(const SpmvArgs& A, int row) {
-  return 76.0 * (A.bsr_ptr[row + 1] - A.bsr_ptr[row]) + 56.0 + 8.0 + 36.0 * (A.ns_ptr[row + 1] - A.ns_ptr[row]) +
-         312.0;
-}
-DEV double body_iter_bytes(const Layout& L, const SpmvArgs& A, int b) {
-  long base = L.body_node[b];
-  return 1344.0 + 52.0 * (A.ns_ptr[base + 1] - A.ns_ptr[base]) + 1152.0 + 960.0;
-}
-constexpr double STENCIL_ITER_BYTES = 624.0 + 16.0 + 96.0 + 96.0;
-
-template <int C>
-__global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
+template <int C, class T>
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int e = P.env_list[blockIdx.x / C];
@@ -138,9 +125,9 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
     if (rank == 0 && threadIdx.x == 0) P.run[e] = 0;
     return;
   }
-  __shared__ double wred[PCG_WARPS][12];
-  __shared__ double tot[4];
-  __shared__ double sbody[12];
+  __shared__ T wred[PCG_WARPS][12];
+  __shared__ T tot[4];
+  __shared__ T sbody[12];
   __shared__ int srange[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // warps are interleaved over the cluster's CTAs, so consecutive slices land on different SMs
@@ -149,8 +136,8 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
   const int S0 = P.pslice_off[e], S1 = P.pslice_off[e + 1];
   const int b0 = P.body_off[e], b1 = P.body_off[e + 1];
   const int ST = P.s_total;
-  double* part_dy = P.part;                                  // 3 doubles per slot, [0] used
-  double* part_rz = P.part + 3L * (P.s_total + P.n_bodies);  // (r.z, r.r, bytes) per slot
+  T* part_dy = P.part;                                  // 3 values per slot, [0] used
+  T* part_rz = P.part + 3L * (P.s_total + P.n_bodies);  // (r.z, r.r, bytes) per slot
   if (tid < 4) {  // this env's range in each stencil sublist
     int lo = P.st_bounds[tid], hi = P.st_bounds[tid + 1];
     srange[2 * tid] = lower_env(P.st_env, lo, hi, e);
@@ -159,21 +146,22 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
   __syncthreads();
   const int n_stencils = srange[1] - srange[0] + srange[3] - srange[2] + srange[5] - srange[4] + srange[7] - srange[6];
 
-  double rz, bb, iter_bytes;
+  T rz, bb;
+  double iter_bytes;
   int it;
   bool go;
   if (P.first) {
     // ---- z = M^-1 r, d = z, x = 0; per-slot (r.z, r.r) and the bytes of one iteration
     for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {  // warp-uniform
-      double a = 0.0, c = 0.0, nb = 0.0;
+      T a = T(0), c = T(0), nb = T(0);
       const int i = P.pslice_row[32 * sl + lane];
       if (i >= 0) {
         precond_soft(i, P.Ps, P.r, P.z, &a, &c);
         for (int k = 3 * i; k < 3 * i + 3; ++k) {
           P.d[k] = P.z[k];
-          P.x[k] = 0.0;
+          P.x[k] = T(0);
         }
-        if (P.bytes) nb = soft_iter_bytes(P.A, i);
+        if (P.bytes) nb = T(soft_iter_bytes(P.A, i));
       }
       a = warp_sum(a);
       c = warp_sum(c);
@@ -189,11 +177,11 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
       long base3 = 3L * L.body_node[b];
       if (tid < 12) sbody[tid] = P.r[base3 + tid];
       __syncthreads();
-      double a, c;
+      T a, c;
       precond_body(P.Pb, b, sbody, base3, P.z, &a, &c);
       if (tid < 12) {
         P.d[base3 + tid] = P.z[base3 + tid];
-        P.x[base3 + tid] = 0.0;
+        P.x[base3 + tid] = T(0);
       }
       if (warp == 0) {
         a = warp_sum(a);
@@ -202,26 +190,27 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
           long slot = (long)ST + b;
           part_rz[3 * slot] = a;
           part_rz[3 * slot + 1] = c;
-          part_rz[3 * slot + 2] = P.bytes ? body_iter_bytes(L, P.A, b) : 0.0;
+          part_rz[3 * slot + 2] = P.bytes ? T(body_iter_bytes(L, P.A, b)) : T(0);
         }
       }
       __syncthreads();
     }
     cl.sync();
-    double v3[3];
+    T v3[3];
     env_sum<3>(part_rz, S0, S1, ST, b0, b1, tot, v3);
     rz = v3[0];
     bb = v3[1];
-    iter_bytes = v3[2] + (P.bytes ? STENCIL_ITER_BYTES * n_stencils : 0.0);
+    iter_bytes = double(v3[2]) + (P.bytes ? stencil_iter_bytes<T>() * n_stencils : 0.0);
     it = 0;
-    go = bb > 0.0 && isfinite(bb);
+    go = bb > T(0) && isfinite(bb);
   } else {
-    rz = P.rz_state[e];
-    bb = P.bb_state[e];
+    rz = T(P.rz_state[e]);
+    bb = T(P.bb_state[e]);
     iter_bytes = P.iterb_state[e];
     it = P.it_state[e];
     go = true;
   }
+  const T tol2 = T(P.tol2);
   const int it0 = it;
   bool more = go;  // the solve continues after this launch
   for (int k = 0; go && k < P.chunk; ++k) {
@@ -230,14 +219,17 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
     for (int q = 0; q < 4; ++q)  // one half-warp per stencil (warp-uniform loop)
       for (int s0 = srange[2 * q] + 2 * gwarp; s0 < srange[2 * q + 1]; s0 += 2 * nwarps) {
         int s = s0 + (lane >> 4);
-        stencil_product_hw<true>(L, P.A.st_pts, P.sH, P.d, P.st_t, s, s < srange[2 * q + 1]);
+        stencil_product_hw<true>(L, P.A.st_pts, P.sH, (const T*)P.d, P.st_t, s, s < srange[2 * q + 1]);
       }
     cl.sync();
     // ---- y = A d: soft rows, one partial d.y per slice
     for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {
-      double dy = 0.0;
+      T dy = T(0);
       const int i = P.pslice_row[32 * sl + lane];
-      if (i >= 0) dy = soft_row_cg(P.A, P.pslice_sel[32 * sl + lane], i, P.d, P.y);
+      if (i >= 0) {
+        const int sel = P.pslice_sel[32 * sl + lane];
+        dy = soft_row<true>(P.A, sel >> 5, sel & 31, i, (const T*)P.d, P.y);
+      }
       dy = warp_sum(dy);
       if (lane == 0) part_dy[3L * sl] = dy;
     }
@@ -247,41 +239,43 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
       if (rank != (b - b0) % C) continue;  // CTA-uniform
       long base = L.body_node[b];
       bool kin = L.body_kin[b];
-      double acc[12];
-      for (int q = 0; q < 12; ++q) acc[q] = 0.0;
+      T acc[12];
+      for (int q = 0; q < 12; ++q) acc[q] = T(0);
       if (!kin) {
         int kb = P.A.ns_ptr[base], ke = P.A.ns_ptr[base + 1];
         for (int k2 = kb + tid; k2 < ke; k2 += PCG_THREADS) {
-          d3 tv = ldcg3(P.A.st_t, P.A.ns_src[k2]);
-          const double* xb = P.A.ns_xb + 3L * k2;
-          double w1 = xb[0], w2 = xb[1], w3 = xb[2];
-          acc[0] += tv.x;
-          acc[1] += tv.y;
-          acc[2] += tv.z;
-          acc[3] += w1 * tv.x;
-          acc[4] += w1 * tv.y;
-          acc[5] += w1 * tv.z;
-          acc[6] += w2 * tv.x;
-          acc[7] += w2 * tv.y;
-          acc[8] += w2 * tv.z;
-          acc[9] += w3 * tv.x;
-          acc[10] += w3 * tv.y;
-          acc[11] += w3 * tv.z;
+          const long src = P.A.ns_src[k2];
+          const T tx = __ldcg(P.A.st_t + 3 * src), ty = __ldcg(P.A.st_t + 3 * src + 1),
+                  tz = __ldcg(P.A.st_t + 3 * src + 2);
+          const T* xb = P.A.ns_xb + 3L * k2;
+          const T w1 = xb[0], w2 = xb[1], w3 = xb[2];
+          acc[0] += tx;
+          acc[1] += ty;
+          acc[2] += tz;
+          acc[3] += w1 * tx;
+          acc[4] += w1 * ty;
+          acc[5] += w1 * tz;
+          acc[6] += w2 * tx;
+          acc[7] += w2 * ty;
+          acc[8] += w2 * tz;
+          acc[9] += w3 * tx;
+          acc[10] += w3 * ty;
+          acc[11] += w3 * tz;
         }
       }
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
-        double sq = warp_sum(acc[q]);
+        T sq = warp_sum(acc[q]);
         if (lane == 0) wred[warp][q] = sq;
       }
       __syncthreads();
       if (warp == 0) {
-        double dyb = 0.0;
+        T dyb = T(0);
         if (lane < 12) {
-          double v = 0.0;
+          T v = T(0);
           if (!kin) {
             for (int w = 0; w < PCG_WARPS; ++w) v += wred[w][lane];
-            const double* H = P.A.bH + 144L * b + 12 * lane;
+            const T* H = P.A.bH + 144L * b + 12 * lane;
             for (int j = 0; j < 12; ++j) v += H[j] * __ldcg(P.d + 3 * base + j);
           }
           P.y[3 * base + lane] = v;
@@ -293,12 +287,12 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
       __syncthreads();
     }
     cl.sync();
-    double dy[1];
+    T dy[1];
     env_sum<1>(part_dy, S0, S1, ST, b0, b1, tot, dy);
-    const double alpha = dy[0] > 0.0 ? rz / dy[0] : 0.0;
+    const T alpha = dy[0] > T(0) ? rz / dy[0] : T(0);
     // ---- x += alpha d; r -= alpha y; z = M^-1 r (owner threads only)
     for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {
-      double a = 0.0, c = 0.0;
+      T a = T(0), c = T(0);
       const int i = P.pslice_row[32 * sl + lane];
       if (i >= 0) {
         for (int k2 = 3 * i; k2 < 3 * i + 3; ++k2) {
@@ -320,12 +314,12 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
       if (tid < 12) {
         long k2 = base3 + tid;
         P.x[k2] += alpha * P.d[k2];
-        double rv = P.r[k2] - alpha * P.y[k2];
+        T rv = P.r[k2] - alpha * P.y[k2];
         P.r[k2] = rv;
         sbody[tid] = rv;
       }
       __syncthreads();
-      double a, c;
+      T a, c;
       precond_body(P.Pb, b, sbody, base3, P.z, &a, &c);
       if (warp == 0) {
         a = warp_sum(a);
@@ -338,15 +332,15 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
       __syncthreads();
     }
     cl.sync();
-    double u2[2];
+    T u2[2];
     env_sum<2>(part_rz, S0, S1, ST, b0, b1, tot, u2);
-    const double rz_new = u2[0], rr = u2[1];
+    const T rz_new = u2[0], rr = u2[1];
     ++it;
-    if (rr <= P.tol2 * bb || it >= P.max_it || !(dy[0] > 0.0) || !isfinite(rr)) {
+    if (rr <= tol2 * bb || it >= P.max_it || !(dy[0] > T(0)) || !isfinite(rr)) {
       more = false;
       break;
     }
-    const double beta = rz > 0.0 ? rz_new / rz : 0.0;
+    const T beta = rz > T(0) ? rz_new / rz : T(0);
     rz = rz_new;
     // ---- d = z + beta d (owner threads)
     for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {
@@ -362,8 +356,8 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs P) {
   }
   // every CTA read the slot partials before it got here; CTA 0 records the env's state
   if (rank == 0 && tid == 0) {
-    P.rz_state[e] = rz;
-    P.bb_state[e] = bb;
+    P.rz_state[e] = double(rz);
+    P.bb_state[e] = double(bb);
     P.iterb_state[e] = iter_bytes;
     P.it_state[e] = it;
     P.run[e] = more ? 1 : 0;

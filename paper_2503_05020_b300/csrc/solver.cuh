@@ -101,21 +101,23 @@ __global__ void k_inertia_energy(int n_nodes, Layout L, const uint8_t* __restric
 // warp-wide load of one element is one contiguous 256-byte access. Padding columns are -1.
 // BSR block k (CSR order) = sum of the tet Hessian blocks that land on it (+ lumped mass on the
 // diagonal), written to its sliced-ELL position pos[k].
+// Values and sums are in the Hessian precision HT.
+template <class HT>
 __global__ void k_assemble_bsr(int nnzb, const int* __restrict__ blk_row, const int* __restrict__ bsr_col, Layout L,
                                const uint8_t* __restrict__ act, const int* __restrict__ bptr,
-                               const int* __restrict__ bsrc, const double* __restrict__ tH, const long* __restrict__ pos,
-                               double* __restrict__ val) {
+                               const int* __restrict__ bsrc, const HT* __restrict__ tH, const long* __restrict__ pos,
+                               HT* __restrict__ val) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nnzb) return;
   int row = blk_row[k];
   if (!act[L.node_env[row]]) return;
-  double v[9];
-  double m = (bsr_col[k] == row) ? L.node_mass[row] : 0.0;
-  for (int i = 0; i < 9; ++i) v[i] = (i % 4 == 0) ? m : 0.0;
+  HT v[9];
+  HT m = (bsr_col[k] == row) ? HT(L.node_mass[row]) : HT(0);
+  for (int i = 0; i < 9; ++i) v[i] = (i % 4 == 0) ? m : HT(0);
   for (int c = bptr[k]; c < bptr[k + 1]; ++c) {
     int src = bsrc[c];
     int t = src >> 4, a = (src >> 2) & 3, b = src & 3;
-    const double* H = tH + 90L * t + 9 * up_idx(min(a, b), max(a, b), 4);
+    const HT* H = tH + 90L * t + 9 * up_idx(min(a, b), max(a, b), 4);
     if (a <= b)
       for (int i = 0; i < 9; ++i) v[i] += H[i];
     else
@@ -126,45 +128,48 @@ __global__ void k_assemble_bsr(int nnzb, const int* __restrict__ blk_row, const 
 }
 
 // 3x3 block of a packed 12x12 stencil Hessian between slots a and b
-DEV void stencil_block(const double* __restrict__ H78, int a, int b, double* out) {
+template <class HT>
+DEV void stencil_block(const HT* __restrict__ H78, int a, int b, HT* out) {
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) out[3 * r + c] = H78[sym_idx(3 * a + r, 3 * b + c, 12)];
 }
 
+template <class HT>
 __global__ void k_precond_soft(int n_nodes, Layout L, const uint8_t* __restrict__ act, const long* __restrict__ diag_pos,
-                               const double* __restrict__ bsr_val, const int* __restrict__ ns_ptr,
-                               const int* __restrict__ ns_src, const double* __restrict__ sH, double* __restrict__ Pinv) {
+                               const HT* __restrict__ bsr_val, const int* __restrict__ ns_ptr,
+                               const int* __restrict__ ns_src, const HT* __restrict__ sH, HT* __restrict__ Pinv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
   if (L.node_body[i] >= 0 || !act[L.node_env[i]]) return;
-  double D[9];
+  HT D[9];
   if (L.node_kin[i]) {
-    for (int k = 0; k < 9; ++k) Pinv[9L * i + k] = 0.0;
+    for (int k = 0; k < 9; ++k) Pinv[9L * i + k] = HT(0);
     return;
   }
   for (int k = 0; k < 9; ++k) D[k] = bsr_val[diag_pos[i] + 32L * k];
   for (int k = ns_ptr[i]; k < ns_ptr[i + 1]; ++k) {
     int e = ns_src[k], s = e >> 2, slot = e & 3;
-    double B[9];
+    HT B[9];
     stencil_block(sH + 78L * s, slot, slot, B);
     for (int q = 0; q < 9; ++q) D[q] += B[q];
   }
-  inv_sym3(D, Pinv + 9L * i);
+  inv_sym3<HT>(D, Pinv + 9L * i);
 }
 
 // one block of 144 threads per body: thread (row, col) of the 12x12 body block adds
 // sum over the body's stencil slot pairs (a, c) of w_a[I] w_c[J] H_s[3a+k][3c+l].
+template <class HT>
 __global__ void k_precond_body(int n_bodies, Layout L, const int* __restrict__ benv, const uint8_t* __restrict__ act,
-                               const double* __restrict__ bH, const int* __restrict__ ns_ptr,
+                               const HT* __restrict__ bH, const int* __restrict__ ns_ptr,
                                const int* __restrict__ ns_src, const int* __restrict__ st_pts,
-                               const double* __restrict__ sH, double* __restrict__ Pinv) {
-  __shared__ double P[144];
+                               const HT* __restrict__ sH, HT* __restrict__ Pinv) {
+  __shared__ HT P[144];
   int b = blockIdx.x;
   if (!act[benv[b]]) return;
   int t = threadIdx.x;
   int row = t / 12, col = t % 12;
   int I = row / 3, k = row % 3, J = col / 3, l = col % 3;
-  double v = bH[144L * b + t];
+  HT v = bH[144L * b + t];
   if (!L.body_kin[b]) {
     int pn = L.body_node[b];
     int beg = ns_ptr[pn], end = ns_ptr[pn + 1];
@@ -176,11 +181,11 @@ __global__ void k_precond_body(int n_bodies, Layout L, const int* __restrict__ b
       for (int x = g; x < ge; ++x) {
         int a = ns_src[x] & 3;
         int pa = st_pts[4 * s + a];
-        double wa = I == 0 ? 1.0 : L.pt_xb[3 * pa + I - 1];
+        HT wa = I == 0 ? HT(1) : HT(L.pt_xb[3 * pa + I - 1]);
         for (int y = g; y < ge; ++y) {
           int c = ns_src[y] & 3;
           int pc = st_pts[4 * s + c];
-          double wc = J == 0 ? 1.0 : L.pt_xb[3 * pc + J - 1];
+          HT wc = J == 0 ? HT(1) : HT(L.pt_xb[3 * pc + J - 1]);
           v += wa * wc * sH[78L * s + sym_idx(3 * a + k, 3 * c + l, 12)];
         }
       }
@@ -190,12 +195,12 @@ __global__ void k_precond_body(int n_bodies, Layout L, const int* __restrict__ b
   P[t] = v;
   __syncthreads();
   if (t == 0) {
-    double A[144];
+    HT A[144];
     for (int i = 0; i < 144; ++i) A[i] = P[i];
     if (L.body_kin[b]) {
-      for (int i = 0; i < 144; ++i) A[i] = 0.0;
+      for (int i = 0; i < 144; ++i) A[i] = HT(0);
     } else {
-      spd_inverse<12>(A);
+      spd_inverse<12, HT>(A);
     }
     for (int i = 0; i < 144; ++i) P[i] = A[i];
   }
@@ -204,86 +209,97 @@ __global__ void k_precond_body(int n_bodies, Layout L, const int* __restrict__ b
 }
 
 // ---------------------------------------------------------------- matrix-free stencil product
-// L2-coherent loads, for vectors that other CTAs write while a kernel runs
+// Vector loads: plain, or L2-coherent (for vectors that other CTAs write while a kernel runs).
+template <bool CG, class VT>
+DEV VT ldv(const VT* p, long i) {
+  if (CG) return __ldcg(p + i);
+  return p[i];
+}
 DEV d3 ldcg3(const double* p, long i) { return d3{__ldcg(p + 3 * i), __ldcg(p + 3 * i + 1), __ldcg(p + 3 * i + 2)}; }
-DEV d3 point_gather_cg(const Layout& L, int pt, const double* v) {
+
+// position-weighted gather of a 3-vector field at point pt: the node's value for a soft point,
+// v_p + xb0 v_a1 + xb1 v_a2 + xb2 v_a3 for a point of an affine body
+template <bool CG, class VT>
+DEV void point_gather_t(const Layout& L, int pt, const VT* v, VT out[3]) {
   int nd = L.pt_node[pt];
-  if (nd >= 0) return ldcg3(v, nd);
+  if (nd >= 0) {
+    for (int c = 0; c < 3; ++c) out[c] = ldv<CG>(v, 3L * nd + c);
+    return;
+  }
   long base = L.body_node[-1 - nd];
   const double* xb = L.pt_xb + 3 * pt;
-  return ldcg3(v, base) + xb[0] * ldcg3(v, base + 1) + xb[1] * ldcg3(v, base + 2) + xb[2] * ldcg3(v, base + 3);
+  const VT x0 = VT(xb[0]), x1 = VT(xb[1]), x2 = VT(xb[2]);
+  for (int c = 0; c < 3; ++c)
+    out[c] = ldv<CG>(v, 3 * base + c) + x0 * ldv<CG>(v, 3 * base + 3 + c) + x1 * ldv<CG>(v, 3 * base + 6 + c) +
+             x2 * ldv<CG>(v, 3 * base + 9 + c);
 }
 
 // t_s = H_s (P_s d) for stencil s by the 16 lanes of a half-warp (H_s: packed upper triangle,
-// 78 doubles). Every lane of the warp calls it (shuffles); ok = false idles a half. Lanes 0..3
-// gather the stencil's points, the 12 entries of P_s d reach every lane by shuffles, and lane
-// i < 12 forms row i from 12 independent loads, summed in column order.
-template <bool CG>
-DEV void stencil_product_hw(const Layout& L, const int* __restrict__ st_pts, const double* __restrict__ sH,
-                            const double* d, double* st_t, int s, bool ok) {
+// 78 values in the Hessian precision HT; products and sums in the vector type VT). Every lane
+// of the warp calls it (shuffles); ok = false idles a half. Lanes 0..3 gather the stencil's
+// points, the 12 entries of P_s d reach every lane by shuffles, and lane i < 12 forms row i from
+// 12 independent loads, summed in column order.
+template <bool CG, class HT, class VT>
+DEV void stencil_product_hw(const Layout& L, const int* __restrict__ st_pts, const HT* __restrict__ sH, const VT* d,
+                            VT* st_t, int s, bool ok) {
   const int lane = threadIdx.x & 31, half = lane & 16, l = lane & 15;
-  d3 v = mk3(0, 0, 0);
-  if (ok && l < 4) v = CG ? point_gather_cg(L, st_pts[4 * s + l], d) : point_gather(L, st_pts[4 * s + l], d);
-  double u[12];
+  VT v[3] = {VT(0), VT(0), VT(0)};
+  if (ok && l < 4) point_gather_t<CG>(L, st_pts[4 * s + l], d, v);
+  VT u[12];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    u[3 * a] = __shfl_sync(0xffffffffu, v.x, half + a);
-    u[3 * a + 1] = __shfl_sync(0xffffffffu, v.y, half + a);
-    u[3 * a + 2] = __shfl_sync(0xffffffffu, v.z, half + a);
-  }
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[3 * a + c] = __shfl_sync(0xffffffffu, v[c], half + a);
   if (ok && l < 12) {
-    const double* H = sH + 78L * s;
-    double acc = 0.0;
+    const HT* H = sH + 78L * s;
+    VT acc = VT(0);
 #pragma unroll
-    for (int j = 0; j < 12; ++j) acc += H[sym_idx(l, j, 12)] * u[j];
+    for (int j = 0; j < 12; ++j) acc += VT(H[sym_idx(l, j, 12)]) * u[j];
     st_t[12L * s + l] = acc;
   }
 }
 
 // every stencil of an env whose solve is still running; one half-warp per stencil
+template <class HT, class VT>
 __global__ void k_stencil_mv(int n_st, Layout L, const int* __restrict__ st_env, const int* __restrict__ st_pts,
-                             const uint8_t* __restrict__ run, const double* __restrict__ sH, const double* __restrict__ d,
-                             double* __restrict__ st_t) {
+                             const uint8_t* __restrict__ run, const HT* __restrict__ sH, const VT* __restrict__ d,
+                             VT* __restrict__ st_t) {
   int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
   bool ok = s < n_st && run[st_env[s]];
   stencil_product_hw<false>(L, st_pts, sH, d, st_t, s, ok);
 }
 
-struct Sell {
+template <class HT>
+struct SellT {
   const int* tile_slice;  // first slice of each soft tile
   const int* width;       // blocks per row of each slice
-  const long* vbase;      // value offset (doubles) of each slice
+  const long* vbase;      // value offset of each slice
   const long* cbase;      // column offset of each slice
-  const int* col;         // block column (node), -1 for padding
-  const double* val;
+  const int* col;         // block column (node); padding blocks point at the row itself
+  const HT* val;
 };
 
-struct SpmvArgs {
-  Sell S;
-  const int* bsr_ptr;     // CSR row pointers (for the algorithmic byte count only)
-  const double* bH;
+// Matrix in the Hessian precision HT, vectors (and stencil products) in VT.
+template <class HT, class VT>
+struct SpmvArgsT {
+  SellT<HT> S;
+  const int* bsr_ptr;  // CSR row pointers (for the algorithmic byte count only)
+  const HT* bH;
   const int* ns_ptr;
-  const int* ns_src;   // stencil*4 + slot of each incidence entry (row-sorted)
-  const double* ns_w;  // weight of the entry's node in the slot's point position
-  const double* ns_xb; // body p-node entries: rest coordinates (xb) of the entry's point
+  const int* ns_src;  // stencil*4 + slot of each incidence entry (row-sorted)
+  const HT* ns_w;     // weight of the entry's node in the slot's point position
+  const HT* ns_xb;    // body p-node entries: rest coordinates (xb) of the entry's point
   const int* st_pts;
-  const double* st_t;
+  const VT* st_t;
 };
-
-// sum over a node's incidence entries of w * t_s[slot]: one dependent load per entry
-DEV d3 stencil_gather(const SpmvArgs& A, int i) {
-  d3 acc = mk3(0, 0, 0);
-  int k = A.ns_ptr[i], end = A.ns_ptr[i + 1];
-#pragma unroll 4
-  for (; k < end; ++k) acc = acc + A.ns_w[k] * ld3(A.st_t, A.ns_src[k]);
-  return acc;
-}
+using SpmvArgs = SpmvArgsT<double, double>;
 
 // weight of every incidence entry, once per Newton iteration; entries of a body's p node also
 // get the rest coordinates of their point, so one pass over that list serves all 4 body nodes
+template <class HT>
 __global__ void k_entry_weights(int n_nodes, Layout L, const uint8_t* __restrict__ act, const int* __restrict__ ns_ptr,
-                                const int* __restrict__ ns_src, const int* __restrict__ st_pts, double* __restrict__ ns_w,
-                                double* __restrict__ ns_xb) {
+                                const int* __restrict__ ns_src, const int* __restrict__ st_pts, HT* __restrict__ ns_w,
+                                HT* __restrict__ ns_xb) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
   if (!act[L.node_env[i]]) return;
@@ -291,115 +307,140 @@ __global__ void k_entry_weights(int n_nodes, Layout L, const uint8_t* __restrict
   bool pnode = b >= 0 && L.body_node[b] == i;
   for (int k = ns_ptr[i]; k < ns_ptr[i + 1]; ++k) {
     int pt = st_pts[ns_src[k]];
-    ns_w[k] = point_weight(L, pt, i);
+    ns_w[k] = HT(point_weight(L, pt, i));
     if (pnode)
-      for (int c = 0; c < 3; ++c) ns_xb[3L * k + c] = L.pt_xb[3 * pt + c];
+      for (int c = 0; c < 3; ++c) ns_xb[3L * k + c] = HT(L.pt_xb[3 * pt + c]);
   }
 }
 
 // deterministic warp sum (fixed butterfly)
-DEV double warp_sum(double v) {
+template <class T>
+DEV T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// y rows of one soft node from the sliced-ELL blocks and its stencil entries; returns d.y
-DEV double spmv_soft_row(const Layout& L, const SpmvArgs& A, int slice, int lane, int row, const double* __restrict__ d,
-                         double* __restrict__ y) {
-  d3 acc = mk3(0, 0, 0);
-  if (!L.node_kin[row]) {
-    int w = A.S.width[slice];
-    const int* col = A.S.col + A.S.cbase[slice] + lane;
-    const double* V = A.S.val + A.S.vbase[slice] + lane;
+// y row of one soft node from its sliced-ELL blocks (slice, lane) and its stencil entries;
+// returns d_row . y_row. Products in VT.
+template <bool CG, class HT, class VT>
+DEV VT soft_row(const SpmvArgsT<HT, VT>& A, int slice, int lane, int row, const VT* d, VT* y) {
+  VT acc[3] = {VT(0), VT(0), VT(0)};
+  int w = A.S.width[slice];
+  const int* col = A.S.col + A.S.cbase[slice] + lane;
+  const HT* V = A.S.val + A.S.vbase[slice] + lane;
 #pragma unroll 4
-    for (int kk = 0; kk < w; ++kk) {
-      int c = col[32 * kk];  // padding blocks: the row itself, zero values
-      d3 dv = ld3(d, c);
-      const double* B = V + 288L * kk;
-      acc = acc + mk3(B[0] * dv.x + B[32] * dv.y + B[64] * dv.z, B[96] * dv.x + B[128] * dv.y + B[160] * dv.z,
-                      B[192] * dv.x + B[224] * dv.y + B[256] * dv.z);
-    }
-    acc = acc + stencil_gather(A, row);
+  for (int kk = 0; kk < w; ++kk) {
+    long c = col[32 * kk];  // padding blocks: the row itself, zero values
+    VT d0 = ldv<CG>(d, 3 * c), d1 = ldv<CG>(d, 3 * c + 1), d2 = ldv<CG>(d, 3 * c + 2);
+    const HT* B = V + 288L * kk;
+    acc[0] = acc[0] + (VT(B[0]) * d0 + VT(B[32]) * d1 + VT(B[64]) * d2);
+    acc[1] = acc[1] + (VT(B[96]) * d0 + VT(B[128]) * d1 + VT(B[160]) * d2);
+    acc[2] = acc[2] + (VT(B[192]) * d0 + VT(B[224]) * d1 + VT(B[256]) * d2);
   }
-  st3(y, row, acc);
-  return dot(acc, ld3(d, row));
+  int k = A.ns_ptr[row], end = A.ns_ptr[row + 1];
+#pragma unroll 4
+  for (; k < end; ++k) {
+    const VT wk = VT(A.ns_w[k]);
+    const long src = A.ns_src[k];
+    for (int c = 0; c < 3; ++c) acc[c] = acc[c] + wk * ldv<CG>(A.st_t, 3 * src + c);
+  }
+  for (int c = 0; c < 3; ++c) y[3L * row + c] = acc[c];
+  return acc[0] * ldv<CG>(d, 3L * row) + acc[1] * ldv<CG>(d, 3L * row + 1) + acc[2] * ldv<CG>(d, 3L * row + 2);
+}
+
+// the same row for a tile thread: kinematic rows get y = 0
+template <class HT, class VT>
+DEV VT spmv_soft_row(const Layout& L, const SpmvArgsT<HT, VT>& A, int slice, int lane, int row, const VT* __restrict__ d,
+                     VT* __restrict__ y) {
+  if (L.node_kin[row]) {
+    for (int c = 0; c < 3; ++c) y[3L * row + c] = VT(0);
+    return VT(0);
+  }
+  return soft_row<false>(A, slice, lane, row, d, y);
 }
 
 // One rigid body per block: y = H_b d_b + sum over every stencil slot on the body of
 // (1, xb) (x) t_s[slot], gathered once from the body's p-node list (every slot on the body
 // appears there once). 12 partial sums are reduced by warp butterflies, then across warps in
 // fixed order. Returns d.y on thread 0.
-DEV double spmv_body(const Layout& L, const SpmvArgs& A, int b, const double* __restrict__ d, double* __restrict__ y) {
-  __shared__ double red[12][TILE / 32];
-  __shared__ double dv[12];
-  __shared__ double dy[12];
+template <class HT, class VT>
+DEV VT spmv_body(const Layout& L, const SpmvArgsT<HT, VT>& A, int b, const VT* __restrict__ d, VT* __restrict__ y) {
+  __shared__ VT red[12][TILE / 32];
+  __shared__ VT dv[12];
+  __shared__ VT dy[12];
   const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
   long base = L.body_node[b];
   bool kin = L.body_kin[b];
   if (t < 12) dv[t] = d[3 * base + t];
   __syncthreads();
-  double acc[12];
-  for (int q = 0; q < 12; ++q) acc[q] = 0.0;
+  VT acc[12];
+  for (int q = 0; q < 12; ++q) acc[q] = VT(0);
   if (!kin) {
     int kb = A.ns_ptr[base], ke = A.ns_ptr[base + 1];
 #pragma unroll 2
     for (int k = kb + t; k < ke; k += blockDim.x) {
-      d3 tv = ld3(A.st_t, A.ns_src[k]);
-      const double* xb = A.ns_xb + 3L * k;
-      double w1 = xb[0], w2 = xb[1], w3 = xb[2];
-      acc[0] += tv.x;
-      acc[1] += tv.y;
-      acc[2] += tv.z;
-      acc[3] += w1 * tv.x;
-      acc[4] += w1 * tv.y;
-      acc[5] += w1 * tv.z;
-      acc[6] += w2 * tv.x;
-      acc[7] += w2 * tv.y;
-      acc[8] += w2 * tv.z;
-      acc[9] += w3 * tv.x;
-      acc[10] += w3 * tv.y;
-      acc[11] += w3 * tv.z;
+      const long src = A.ns_src[k];
+      const VT tx = A.st_t[3 * src], ty = A.st_t[3 * src + 1], tz = A.st_t[3 * src + 2];
+      const HT* xb = A.ns_xb + 3L * k;
+      const VT w1 = VT(xb[0]), w2 = VT(xb[1]), w3 = VT(xb[2]);
+      acc[0] += tx;
+      acc[1] += ty;
+      acc[2] += tz;
+      acc[3] += w1 * tx;
+      acc[4] += w1 * ty;
+      acc[5] += w1 * tz;
+      acc[6] += w2 * tx;
+      acc[7] += w2 * ty;
+      acc[8] += w2 * tz;
+      acc[9] += w3 * tx;
+      acc[10] += w3 * ty;
+      acc[11] += w3 * tz;
     }
   }
   for (int q = 0; q < 12; ++q) {
-    double v = warp_sum(acc[q]);
+    VT v = warp_sum(acc[q]);
     if (lane == 0) red[q][wp] = v;
   }
   __syncthreads();
   if (t < 12) {
-    double v = 0.0;
+    VT v = VT(0);
     if (!kin) {
-      const double* H = A.bH + 144L * b + 12 * t;
-      for (int j = 0; j < 12; ++j) v += H[j] * dv[j];
+      const HT* H = A.bH + 144L * b + 12 * t;
+      for (int j = 0; j < 12; ++j) v += VT(H[j]) * dv[j];
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[t][w];
     }
     y[3 * base + t] = v;
     dy[t] = v * dv[t];
   }
   __syncthreads();
-  double r = 0.0;
+  VT r = VT(0);
   if (t == 0)
     for (int q = 0; q < 12; ++q) r += dy[q];
   __syncthreads();
   return r;
 }
 
-// algorithmic bytes of one row item: sliced-ELL blocks (72 B values + 4 B column), the d read
-// and y write (24 B each), row pointers (8 B), stencil entries (4 B index + 8 B weight + 24 B
-// stencil product); a body is its dense 12x12 block (1152 B) plus 96 B read and 96 B written,
-// and per p-node entry 4 B index + 24 B rest coordinates + 24 B stencil product.
-DEV double spmv_item_bytes(const Layout& L, const SpmvArgs& A, int kind, int item, int slice) {
+// algorithmic bytes of one row item with H values of hb bytes: sliced-ELL blocks (9 hb values
+// + 4 B column), the d read and y write (3 vb each), row pointers (8 B), stencil entries (4 B
+// index + hb weight + 3 vb stencil product); a body is its dense 12x12 block (144 hb) plus its
+// d read and y written (12 vb each), and per p-node entry 4 B index + 3 hb rest coordinates +
+// 3 vb stencil product.
+template <class HT, class VT>
+DEV double spmv_item_bytes(const Layout& L, const SpmvArgsT<HT, VT>& A, int kind, int item) {
+  const double hb = sizeof(HT), vb = sizeof(VT);
   if (kind == 0) {
-    if (L.node_kin[item]) return 24.0;
-    return 76.0 * (A.bsr_ptr[item + 1] - A.bsr_ptr[item]) + 56.0 + 8.0 + 36.0 * (A.ns_ptr[item + 1] - A.ns_ptr[item]);
+    if (L.node_kin[item]) return 3 * vb;
+    return (9 * hb + 4) * (A.bsr_ptr[item + 1] - A.bsr_ptr[item]) + 6 * vb + 8.0 +
+           (4 + hb + 3 * vb) * (A.ns_ptr[item + 1] - A.ns_ptr[item]);
   }
   long base = L.body_node[item];
-  return 1344.0 + 52.0 * (A.ns_ptr[base + 1] - A.ns_ptr[base]);
+  return 144 * hb + 24 * vb + (4 + 3 * hb + 3 * vb) * (A.ns_ptr[base + 1] - A.ns_ptr[base]);
 }
 
-__global__ void __launch_bounds__(TILE) k_spmv(Tiles T, Layout L, SpmvArgs A, const uint8_t* __restrict__ run,
-                                               const double* __restrict__ d, double* __restrict__ y,
-                                               double* __restrict__ part, unsigned long long* __restrict__ bytes) {
+template <class HT, class VT>
+__global__ void __launch_bounds__(TILE) k_spmv(Tiles T, Layout L, SpmvArgsT<HT, VT> A, const uint8_t* __restrict__ run,
+                                               const VT* __restrict__ d, VT* __restrict__ y, double* __restrict__ part,
+                                               unsigned long long* __restrict__ bytes) {
   __shared__ double sh[TILE];
   int tile = blockIdx.x;
   int e = T.env[tile];
@@ -410,11 +451,11 @@ __global__ void __launch_bounds__(TILE) k_spmv(Tiles T, Layout L, SpmvArgs A, co
     int row = T.begin[tile] + threadIdx.x;
     int slice = A.S.tile_slice[tile] + (threadIdx.x >> 5);
     bool ok = row < T.end[tile];
-    if (ok) v = spmv_soft_row(L, A, slice, threadIdx.x & 31, row, d, y);
-    if (bytes && ok) nb = spmv_item_bytes(L, A, 0, row, slice);
+    if (ok) v = double(spmv_soft_row(L, A, slice, threadIdx.x & 31, row, d, y));
+    if (bytes && ok) nb = spmv_item_bytes(L, A, 0, row);
   } else {
-    v = spmv_body(L, A, T.begin[tile], d, y);
-    if (bytes && threadIdx.x == 0) nb = spmv_item_bytes(L, A, 1, T.begin[tile], 0);
+    v = double(spmv_body(L, A, T.begin[tile], d, y));
+    if (bytes && threadIdx.x == 0) nb = spmv_item_bytes(L, A, 1, T.begin[tile]);
   }
   v = block_sum(v, sh);
   if (threadIdx.x == 0) part[tile] = v;
@@ -444,26 +485,28 @@ DEV double env_total(const Tiles& T, int e, const double* __restrict__ part, dou
 }
 
 // z = M^-1 r for one soft node, returns (r.z, r.r)
-DEV void precond_soft(int i, const double* __restrict__ Ps, const double* __restrict__ r, double* __restrict__ z,
-                      double* rz, double* rr) {
-  d3 rv = ld3(r, i);
-  const double* P = Ps + 9L * i;
-  d3 zv = mk3(P[0] * rv.x + P[1] * rv.y + P[2] * rv.z, P[3] * rv.x + P[4] * rv.y + P[5] * rv.z,
-              P[6] * rv.x + P[7] * rv.y + P[8] * rv.z);
-  st3(z, i, zv);
-  *rz = dot(rv, zv);
-  *rr = dot(rv, rv);
+template <class T>
+DEV void precond_soft(int i, const T* __restrict__ Ps, const T* __restrict__ r, T* __restrict__ z, T* rz, T* rr) {
+  const T r0 = r[3L * i], r1 = r[3L * i + 1], r2 = r[3L * i + 2];
+  const T* P = Ps + 9L * i;
+  const T z0 = P[0] * r0 + P[1] * r1 + P[2] * r2, z1 = P[3] * r0 + P[4] * r1 + P[5] * r2,
+          z2 = P[6] * r0 + P[7] * r1 + P[8] * r2;
+  z[3L * i] = z0;
+  z[3L * i + 1] = z1;
+  z[3L * i + 2] = z2;
+  *rz = r0 * z0 + r1 * z1 + r2 * z2;
+  *rr = r0 * r0 + r1 * r1 + r2 * r2;
 }
 
 // body preconditioner on one block: threads 0..11 hold one DOF each; rs must be in shared memory
-DEV void precond_body(const double* __restrict__ Pb, int b, const double* rs, long base3, double* __restrict__ z,
-                      double* rz, double* rr) {
+template <class T>
+DEV void precond_body(const T* __restrict__ Pb, int b, const T* rs, long base3, T* __restrict__ z, T* rz, T* rr) {
   int t = threadIdx.x;
-  *rz = 0.0;
-  *rr = 0.0;
+  *rz = T(0);
+  *rr = T(0);
   if (t < 12) {
-    const double* P = Pb + 144L * b + 12 * t;
-    double s = 0.0;
+    const T* P = Pb + 144L * b + 12 * t;
+    T s = T(0);
     for (int j = 0; j < 12; ++j) s += P[j] * rs[j];
     z[base3 + t] = s;
     *rz = rs[t] * s;
