@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--pcg-cluster", type=int, default=0,
                     help="PCG launch shape: 0 automatic, 1/2/4/8 CTAs per env cluster, -1 tiled multi-launch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed-leg", action="store_true",
+                    help="skip the mixed-precision run of the same steps that the FP64 line reports beside it")
     ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle time for --impl reference")
     return ap.parse_args()
 
@@ -163,6 +165,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         sc.step(1)
     snap = [(sc.dofs(e), sc.velocities(e), sc.status(e)["step"]) for e in ids]
+    p_start = [sc.points(e) for e in ids]
 
     def barrier():
         if world > 1:
@@ -192,6 +195,7 @@ def run_ours(args):
     sc.profile(False)
     steps_done = sum(sc.status(e)["steps"] for e in ids)
     failed = sum(sc.status(e)["status"] == "FAILED" for e in ids)
+    x_end = [sc.points(e) for e in ids]
     t_max = ms
     if world > 1:
         import torch.distributed as dist
@@ -229,6 +233,10 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_value = world * args.envs * args.steps / e2e_s
+
+    mixed = None
+    if world == 1 and args.precision == "fp64" and not args.no_mixed_leg:
+        mixed = mixed_leg(args, params, envs, snap, p_start, x_end, stream, local, t_max / args.steps)
 
     if rank != 0:
         if world > 1:
@@ -271,7 +279,7 @@ def run_ours(args):
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h_tg.nbytes),
                 "d2h_bytes_per_step": int(h_out.nbytes)},
-        "gpu_launches": int(launches), "clocks": clk,
+        "gpu_launches": int(launches), "clocks": clk, "mixed_precision": mixed,
         "env_steps_done": int(steps_done), "envs_failed": int(failed),
         "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items()},
         "counters_last_iteration": sc.scene_counters(ids[0]),
@@ -284,6 +292,54 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def mixed_leg(args, params, envs, snap, p_start, x_end, stream, device, ms_fp64):
+    """The same K timed steps from the same state with FP32 Hessians and PCG (FP64 energies,
+    gradients, barrier, CCD and line search): throughput, speedup over the FP64 run, and the
+    largest difference of a point's world position from the FP64 run (all points, and the
+    grasped objects' points) relative to the largest FP64 point displacement of the run."""
+    import torch
+
+    from paper_2503_05020_b300 import ipc
+
+    sc = ipc.Scene(params, precision=ipc.MIXED, device=device, stream=stream.cuda_stream,
+                   pcg_cluster=args.pcg_cluster)
+    ids = [sc.add_env(e) for e in envs]
+    for eid, env in zip(ids, envs):
+        x, v = S.pad_grasp_state_at(env, START_STEP)
+        sc.set_state(eid, x, v, START_STEP)
+    for _ in range(args.warmup):
+        sc.step(1)
+    for eid, (x, v, st) in zip(ids, snap):
+        sc.set_state(eid, x, v, st)
+    sc.profile(True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sc.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = sc.profile_read()
+    sc.profile(False)
+    # world positions of every point (soft vertices, then the object's vertices)
+    diff = max(float(np.abs(sc.points(e) - x).max()) for e, x in zip(ids, x_end))
+    disp = max(float(np.abs(x - x0).max()) for x, x0 in zip(x_end, p_start))
+    obj_diff = 0.0
+    for e, x, env in zip(ids, x_end, envs):
+        o = sum(len(s["verts"]) for s in env["soft"])
+        obj_diff = max(obj_diff, float(np.abs(sc.points(e)[o:] - x[o:]).max()))
+    failed = sum(sc.status(e)["status"] == "FAILED" for e in ids)
+    value = args.envs * args.steps / (ms / 1000.0)
+    return {"value": round(value, 2), "unit": UNIT, "ms_per_step": round(ms / args.steps, 3),
+            "speedup_vs_fp64": round((ms_fp64 * args.steps) / ms, 3), "max_displacement_diff_m": diff,
+            "rel_displacement_diff": diff / disp if disp > 0 else None,
+            "rel_object_displacement_diff": obj_diff / disp if disp > 0 else None, "envs_failed": int(failed),
+            "dtype": "f32 Hessians + PCG, f64 energies/gradients/barrier/CCD/line search",
+            "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items()}}
 
 
 def run_reference(args):
