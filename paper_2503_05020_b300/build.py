@@ -27,7 +27,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not needs_build():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-shared", "-Xcompiler", "-fPIC",
+    cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-diag-suppress", "128", "-shared", "-Xcompiler", "-fPIC",
            "-o", LIB + ".tmp", *[os.path.join(CSRC, f) for f in SOURCES]]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

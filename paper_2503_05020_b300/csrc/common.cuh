@@ -144,6 +144,103 @@ __device__ __noinline__ void project_psd_jacobi(T* A) {
     }
 }
 
+// Half-warp-parallel cyclic Jacobi with round-robin ordering (Brent & Luk 1985): each round
+// applies N/2 disjoint plane rotations at once, computed from the same matrix, and N - 1 rounds
+// make a sweep over all N (N - 1) / 2 pairs. A and V are N x N row-major arrays in shared memory
+// owned by the calling half-warp (lanes hw_lane = 0..15, mask = its 16 lanes); rot holds 3N
+// values of scratch. On return A holds the PSD projection V max(Lambda, 0) V^T (sweeps stop when
+// the off-diagonal part is below JacobiTol<T>::psd of the Frobenius norm, 24 at most). N is even
+// and at most 16; pad odd sizes with a zero row and column.
+template <int N, class T>
+DEV void project_psd_hw(T* A, T* V, T* rot, int hw_lane, unsigned mask) {
+  static_assert(N % 2 == 0 && N <= 16, "N must be even and at most 16");
+  constexpr int NE = (N * N + 15) / 16;  // elements per lane
+  T* alpha = rot;          // coefficient of column i in the new column i
+  T* beta = rot + N;       // coefficient of its partner column
+  int* partner = (int*)(rot + 2 * N);
+  for (int e = hw_lane; e < N * N; e += 16) V[e] = (e / N == e % N) ? T(1) : T(0);
+  T fro = T(0);
+  for (int e = hw_lane; e < N * N; e += 16) fro += A[e] * A[e];
+  for (int o = 8; o > 0; o >>= 1) fro += __shfl_xor_sync(mask, fro, o);
+  __syncwarp(mask);
+  if (fro == T(0)) return;
+  const T tol = JacobiTol<T>::psd * fro;
+  for (int sweep = 0; sweep < 24; ++sweep) {
+    T off = T(0);
+    for (int e = hw_lane; e < N * N; e += 16)
+      if (e / N < e % N) off += T(2) * A[e] * A[e];
+    for (int o = 8; o > 0; o >>= 1) off += __shfl_xor_sync(mask, off, o);
+    if (off <= tol) break;
+    for (int r = 0; r < N - 1; ++r) {
+      if (hw_lane < N / 2) {  // pair k = hw_lane of round r
+        const int k = hw_lane;
+        int a = k == 0 ? 0 : 1 + (r + k) % (N - 1);
+        int b = k == 0 ? 1 + r % (N - 1) : 1 + (r - k + N - 1) % (N - 1);
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        const T apq = A[p * N + q];
+        T c = T(1), sn = T(0);
+        if (apq != T(0)) {
+          const T app = A[p * N + p], aqq = A[q * N + q];
+          const T theta = (aqq - app) / (T(2) * apq);
+          const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+          c = rsqrt(t * t + T(1));
+          sn = t * c;
+        }
+        // new column p = c col_p - s col_q, new column q = s col_p + c col_q
+        alpha[p] = c;
+        beta[p] = -sn;
+        partner[p] = q;
+        alpha[q] = c;
+        beta[q] = sn;
+        partner[q] = p;
+      }
+      __syncwarp(mask);
+      T na[NE], nv[NE];
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        const int e = hw_lane + 16 * u;
+        if (e < N * N) {
+          const int i = e / N, j = e % N, i2 = partner[i], j2 = partner[j];
+          const T ai = alpha[i], bi = beta[i], aj = alpha[j], bj = beta[j];
+          na[u] = ai * (aj * A[i * N + j] + bj * A[i * N + j2]) + bi * (aj * A[i2 * N + j] + bj * A[i2 * N + j2]);
+          nv[u] = aj * V[i * N + j] + bj * V[i * N + j2];
+        }
+      }
+      __syncwarp(mask);
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        const int e = hw_lane + 16 * u;
+        if (e < N * N) {
+          A[e] = na[u];
+          V[e] = nv[u];
+        }
+      }
+      __syncwarp(mask);
+    }
+  }
+  // A_proj = sum_k max(lam_k, 0) v_k v_k^T, lam_k = A[k][k]
+  T out[NE];
+#pragma unroll
+  for (int u = 0; u < NE; ++u) {
+    const int e = hw_lane + 16 * u;
+    out[u] = T(0);
+    if (e < N * N) {
+      const int i = e / N, j = e % N;
+      for (int k = 0; k < N; ++k) {
+        const T lk = A[k * N + k];
+        if (lk > T(0)) out[u] += V[i * N + k] * lk * V[j * N + k];
+      }
+    }
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int u = 0; u < NE; ++u) {
+    const int e = hw_lane + 16 * u;
+    if (e < N * N) A[e] = out[u];
+  }
+  __syncwarp(mask);
+}
+
 // Symmetric 3x3 eigen-decomposition by cyclic Jacobi in the precision T: A (row-major) ->
 // eigenvalues w and eigenvector columns of V (det V = +1).
 template <class T>

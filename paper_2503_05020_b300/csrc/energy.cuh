@@ -248,30 +248,14 @@ __device__ __noinline__ double body_energy(const double* __restrict__ Q, const d
   return Ein + wk * f;
 }
 
-template <int MODE, class HT = double>
-__global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int* __restrict__ benv,
-                         const uint8_t* __restrict__ bkin, const double* __restrict__ M4, const double* __restrict__ bvol,
-                         const uint8_t* __restrict__ act, const double* __restrict__ q, const double* __restrict__ qt,
-                         double h2kA, double* __restrict__ bE, double* __restrict__ bg, HT* __restrict__ bH) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= n_bodies) return;
-  int e = benv[b];
-  if (!act[e]) return;
-  if (bkin[b]) {
-    bE[b] = 0.0;
-    if (MODE >= MODE_GRAD)
-      for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = 0.0;
-    if (MODE == MODE_HESS)
-      for (int i = 0; i < 144; ++i) bH[144 * (long)b + i] = (i % 13 == 0) ? HT(1) : HT(0);
-    return;
-  }
-  const double* Q = q + 3 * (long)bnode[b];
-  const double* Qt = qt + 3 * (long)bnode[b];
-  const double* M = M4 + 16 * (long)b;
-  double wk = h2kA * bvol[b];
-  double dq[12], A[9], S[9], g[12];
-  bE[b] = body_energy(Q, Qt, M, wk, dq, A, S);
-  if (MODE == MODE_ENERGY) return;
+// Energy, gradient (MODE >= MODE_GRAD) and, for MODE_HESS, the unprojected 9x9 orthogonality
+// Hessian d2|S|^2/dA2 in the precision HT (row-major, leading dimension ldo) of one free body.
+template <int MODE, class HT>
+DEV double body_eval(const double* __restrict__ Q, const double* __restrict__ Qt, const double* __restrict__ M,
+                     double wk, double* g, HT* Ho, int ldo) {
+  double dq[12], A[9], S[9];
+  double E = body_energy(Q, Qt, M, wk, dq, A, S);
+  if (MODE == MODE_ENERGY) return E;
   for (int I = 0; I < 4; ++I)
     for (int k = 0; k < 3; ++k) {
       double s = 0.0;
@@ -284,15 +268,12 @@ __global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int*
       double sa = S[3 * k] * A[l] + S[3 * k + 1] * A[3 + l] + S[3 * k + 2] * A[6 + l];
       g[3 + 3 * l + k] += wk * 4.0 * sa;
     }
-  for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = g[i];
-  if (MODE == MODE_GRAD) return;
-  // Hessian in the precision HT: orthogonality term projected to PSD, plus the mass blocks
+  if (MODE == MODE_GRAD) return E;
   HT Ah[9], Sh[9];
   for (int i = 0; i < 9; ++i) {
     Ah[i] = HT(A[i]);
     Sh[i] = HT(S[i]);
   }
-  HT Ho[81];
   HT AtA[9];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) AtA[3 * i + j] = Ah[i] * Ah[j] + Ah[3 + i] * Ah[3 + j] + Ah[6 + i] * Ah[6 + j];
@@ -303,22 +284,85 @@ __global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int*
           HT v = Ah[3 * k + n] * Ah[3 * m + l];
           if (k == m) v += AtA[3 * n + l];
           if (l == n) v += Sh[3 * k + m];
-          Ho[(3 * k + l) * 9 + 3 * m + n] = HT(4) * v;
+          Ho[(3 * k + l) * ldo + 3 * m + n] = HT(4) * v;
         }
-  project_psd_jacobi<9, HT>(Ho);
+  return E;
+}
+
+// energy and gradient modes: one thread per body
+template <int MODE>
+__global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int* __restrict__ benv,
+                         const uint8_t* __restrict__ bkin, const double* __restrict__ M4, const double* __restrict__ bvol,
+                         const uint8_t* __restrict__ act, const double* __restrict__ q, const double* __restrict__ qt,
+                         double h2kA, double* __restrict__ bE, double* __restrict__ bg) {
+  static_assert(MODE != MODE_HESS, "the Hessian mode is k_bodies_hess");
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_bodies) return;
+  int e = benv[b];
+  if (!act[e]) return;
+  if (bkin[b]) {
+    bE[b] = 0.0;
+    if (MODE >= MODE_GRAD)
+      for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = 0.0;
+    return;
+  }
+  double g[12];
+  bE[b] = body_eval<MODE, double>(q + 3 * (long)bnode[b], qt + 3 * (long)bnode[b], M4 + 16 * (long)b,
+                                  h2kA * bvol[b], g, (double*)nullptr, 0);
+  if (MODE == MODE_GRAD)
+    for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = g[i];
+}
+
+// Hessian mode: one half-warp per body. Lane 0 forms the energy, gradient and the 9x9
+// orthogonality Hessian (padded to 10x10 with zeros) in shared memory, the half-warp projects it
+// to PSD in the precision HT, and the 12x12 block (mass blocks + h^2 kappa_A V times the
+// projection) is written out.
+constexpr int BODY_HESS_THREADS = 64;
+template <class HT>
+__global__ void __launch_bounds__(BODY_HESS_THREADS)
+    k_bodies_hess(int n_bodies, const int* __restrict__ bnode, const int* __restrict__ benv,
+                  const uint8_t* __restrict__ bkin, const double* __restrict__ M4, const double* __restrict__ bvol,
+                  const uint8_t* __restrict__ act, const double* __restrict__ q, const double* __restrict__ qt,
+                  double h2kA, double* __restrict__ bE, double* __restrict__ bg, HT* __restrict__ bH) {
+  constexpr int HALVES = BODY_HESS_THREADS / 16;
+  __shared__ HT shA[HALVES][100], shV[HALVES][100], shR[HALVES][30];
+  const int half = threadIdx.x >> 4, hl = threadIdx.x & 15;
+  const unsigned mask = 0xffffu << (threadIdx.x & 16);
+  const int b = (blockIdx.x * BODY_HESS_THREADS + threadIdx.x) >> 4;
+  if (b >= n_bodies) return;  // uniform over the half-warp
+  if (!act[benv[b]]) return;
   HT* Hout = bH + 144 * (long)b;
-  for (int I = 0; I < 4; ++I)
-    for (int Jn = 0; Jn < 4; ++Jn)
-      for (int k = 0; k < 3; ++k)
-        for (int l = 0; l < 3; ++l) Hout[(3 * I + k) * 12 + 3 * Jn + l] = (k == l) ? HT(M[4 * I + Jn]) : HT(0);
+  if (bkin[b]) {
+    if (hl == 0) {
+      bE[b] = 0.0;
+      for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = 0.0;
+    }
+    for (int i = hl; i < 144; i += 16) Hout[i] = (i % 13 == 0) ? HT(1) : HT(0);
+    return;
+  }
+  const double* M = M4 + 16 * (long)b;
+  const double wk = h2kA * bvol[b];
+  HT* A = shA[half];
+  for (int i = hl; i < 100; i += 16) A[i] = HT(0);
+  __syncwarp(mask);
+  if (hl == 0) {
+    double g[12];
+    bE[b] = body_eval<MODE_HESS, HT>(q + 3 * (long)bnode[b], qt + 3 * (long)bnode[b], M, wk, g, A, 10);
+    for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = g[i];
+  }
+  __syncwarp(mask);
+  project_psd_hw<10, HT>(A, shV[half], shR[half], hl, mask);
   const HT wkh = HT(wk);
-  for (int k = 0; k < 3; ++k)
-    for (int l = 0; l < 3; ++l)
-      for (int m = 0; m < 3; ++m)
-        for (int n = 0; n < 3; ++n) {
-          int qi = 3 + 3 * l + k, qj = 3 + 3 * n + m;
-          Hout[qi * 12 + qj] += wkh * Ho[(3 * k + l) * 9 + 3 * m + n];
-        }
+  for (int e = hl; e < 144; e += 16) {
+    const int qi = e / 12, qj = e % 12;
+    const int I = qi / 3, k = qi % 3, Jn = qj / 3, m = qj % 3;
+    HT v = (k == m) ? HT(M[4 * I + Jn]) : HT(0);
+    if (qi >= 3 && qj >= 3) {  // q index 3 + 3 l + k  <->  orthogonality index 3 k + l
+      const int l = (qi - 3) / 3, n = (qj - 3) / 3;
+      v += wkh * A[(3 * k + l) * 10 + 3 * m + n];
+    }
+    Hout[e] = v;
+  }
 }
 
 // ----------------------------------------------------------------- contacts (barrier)
@@ -355,14 +399,11 @@ __device__ __noinline__ double barrier_energy(int kind, int type, const d3* X, d
   return scale * m * b;
 }
 
-template <int MODE, class HT = double>
-__global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
-                          const double* __restrict__ ptx, double h2, double dhat, double kappa, double* __restrict__ sE,
-                          double* __restrict__ sg, HT* __restrict__ sH) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_ct) return;
-  ContactRec c = ct[k];
-  if (!act[c.env]) return;
+// Energy (returned), gradient g (MODE >= MODE_GRAD) and the unprojected 12x12 Hessian H
+// (MODE == MODE_HESS, row-major) of one contact, in FP64.
+template <int MODE>
+DEV double barrier_eval(const ContactRec& c, const double* __restrict__ ptx, double h2, double dhat, double kappa,
+                        double* g, double* H) {
   d3 X[4];
   for (int i = 0; i < 4; ++i) X[i] = ld3(ptx, c.pts[i]);
   // the energy value comes from the same function in every mode, so that line-search energies
@@ -370,8 +411,7 @@ __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uin
   double scale = h2 * kappa;
   double s, cc;
   double Eb = barrier_energy(c.kind, c.type, X, c.eps_x, dhat, scale, &s, &cc);
-  sE[k] = Eb;
-  if (MODE == MODE_ENERGY) return;
+  if (MODE == MODE_ENERGY) return Eb;
   double gs[12], Hs[78];
   {
     double s_unused;
@@ -401,10 +441,8 @@ __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uin
   for (int i = 0; i < 12; ++i) gb[i] = kb * gs[i];
   double gm[12];
   for (int i = 0; i < 12; ++i) gm[i] = c.kind == 1 ? m1 * gc[i] : 0.0;
-  for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = scale * (m * gb[i] + b * gm[i]);
-  if (MODE == MODE_GRAD) return;
-  // the Hessian is formed in FP64 and projected to PSD in the precision HT
-  HT H[144];
+  for (int i = 0; i < 12; ++i) g[i] = scale * (m * gb[i] + b * gm[i]);
+  if (MODE == MODE_GRAD) return Eb;
   double ka = b2 / (4.0 * d * d) - b1 / (4.0 * d * d * d);
   for (int i = 0; i < 12; ++i)
     for (int j = i; j < 12; ++j) {
@@ -412,12 +450,57 @@ __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uin
       double hb = ka * gs[i] * gs[j] + kb * Hs[u];
       double v = m * hb;
       if (c.kind == 1) v += b * (m2 * gc[i] * gc[j] + m1 * Hc[u]) + gm[i] * gb[j] + gb[i] * gm[j];
-      H[12 * i + j] = HT(scale * v);
-      H[12 * j + i] = HT(scale * v);
+      H[12 * i + j] = scale * v;
+      H[12 * j + i] = scale * v;
     }
-  project_psd_jacobi<12, HT>(H);
-  for (int i = 0; i < 12; ++i)
-    for (int j = i; j < 12; ++j) sH[78 * (long)k + up_idx(i, j, 12)] = H[12 * i + j];
+  return Eb;
+}
+
+// energy and gradient modes: one thread per contact
+template <int MODE>
+__global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
+                          const double* __restrict__ ptx, double h2, double dhat, double kappa, double* __restrict__ sE,
+                          double* __restrict__ sg) {
+  static_assert(MODE != MODE_HESS, "the Hessian mode is k_barrier_hess");
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_ct) return;
+  ContactRec c = ct[k];
+  if (!act[c.env]) return;
+  double g[12];
+  sE[k] = barrier_eval<MODE>(c, ptx, h2, dhat, kappa, g, nullptr);
+  if (MODE == MODE_GRAD)
+    for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = g[i];
+}
+
+// Hessian mode: one half-warp per contact. Lane 0 forms the energy, gradient and 12x12 Hessian
+// (FP64) in shared memory, the half-warp projects the Hessian to PSD in FP64, and its packed
+// upper triangle is stored in the precision HT.
+constexpr int BARRIER_HESS_THREADS = 128;
+template <class HT>
+__global__ void __launch_bounds__(BARRIER_HESS_THREADS)
+    k_barrier_hess(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
+                   const double* __restrict__ ptx, double h2, double dhat, double kappa, double* __restrict__ sE,
+                   double* __restrict__ sg, HT* __restrict__ sH) {
+  constexpr int HALVES = BARRIER_HESS_THREADS / 16;
+  __shared__ double shA[HALVES][144], shV[HALVES][144], shR[HALVES][36];
+  const int half = threadIdx.x >> 4, hl = threadIdx.x & 15;
+  const unsigned mask = 0xffffu << (threadIdx.x & 16);
+  const int k = (blockIdx.x * BARRIER_HESS_THREADS + threadIdx.x) >> 4;
+  if (k >= n_ct) return;  // uniform over the half-warp
+  const ContactRec c = ct[k];
+  if (!act[c.env]) return;
+  double* A = shA[half];
+  if (hl == 0) {
+    double g[12];
+    sE[k] = barrier_eval<MODE_HESS>(c, ptx, h2, dhat, kappa, g, A);
+    for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = g[i];
+  }
+  __syncwarp(mask);
+  project_psd_hw<12, double>(A, shV[half], shR[half], hl, mask);
+  for (int e = hl; e < 144; e += 16) {
+    const int i = e / 12, j = e % 12;
+    if (j >= i) sH[78 * (long)k + up_idx(i, j, 12)] = HT(A[e]);
+  }
 }
 
 // ----------------------------------------------------------------- lagged friction

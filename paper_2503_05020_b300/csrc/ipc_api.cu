@@ -1143,13 +1143,22 @@ struct ipc_scene {
     launch(k_elastic<MODE, HT>, NT, 128, NT, (const int4*)tets.p, (const double*)tet_prm.p, (const int*)tet_env.p, act,
            q, h2, tetE.p, tet_g.p, tH, e_bad.p, MODE == MODE_ENERGY ? (unsigned long long*)nullptr : punits(IPC_PROF_ELASTIC));
     pend(efam);
-    launch(k_bodies<MODE, HT>, NB, 64, NB, (const int*)body_node.p, (const int*)body_env.p, (const uint8_t*)body_kin.p,
-           (const double*)M4.p, (const double*)bvol.p, act, q, (const double*)xtilde.p, h2 * desc.kappa_affine, bodyE.p,
-           body_g.p, bH);
+    if constexpr (MODE == MODE_HESS)
+      launch(k_bodies_hess<HT>, 16L * NB, BODY_HESS_THREADS, NB, (const int*)body_node.p, (const int*)body_env.p,
+             (const uint8_t*)body_kin.p, (const double*)M4.p, (const double*)bvol.p, act, q, (const double*)xtilde.p,
+             h2 * desc.kappa_affine, bodyE.p, body_g.p, bH);
+    else
+      launch(k_bodies<MODE>, NB, 64, NB, (const int*)body_node.p, (const int*)body_env.p, (const uint8_t*)body_kin.p,
+             (const double*)M4.p, (const double*)bvol.p, act, q, (const double*)xtilde.p, h2 * desc.kappa_affine,
+             bodyE.p, body_g.p);
     int cfam = MODE == MODE_ENERGY ? IPC_PROF_LS_ENERGY : IPC_PROF_CONTACT;
     pbeg(cfam);
-    launch(k_barrier<MODE, HT>, n_ct, 64, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, h2, desc.dhat,
-           desc.kappa, sE.p, sg.p, sHp);
+    if constexpr (MODE == MODE_HESS)
+      launch(k_barrier_hess<HT>, 16L * n_ct, BARRIER_HESS_THREADS, n_ct, (const ContactRec*)ct.p, act,
+             (const double*)ptx.p, h2, desc.dhat, desc.kappa, sE.p, sg.p, sHp);
+    else
+      launch(k_barrier<MODE>, n_ct, 64, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, h2, desc.dhat,
+             desc.kappa, sE.p, sg.p);
     launch(k_friction<MODE, HT>, n_fr, 128, n_fr, (const FrictionRec*)fr.p, act, (const double*)ptx.p,
            (const double*)ptx_t.p, h2, desc.eps_v * h, sE.p + n_ct, sg.p + 12 * (size_t)n_ct,
            sHp ? sHp + 78 * (size_t)n_ct : sHp);
