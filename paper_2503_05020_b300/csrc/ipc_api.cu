@@ -400,7 +400,8 @@ struct ipc_scene {
   DBuf<uint8_t> pcg_run;
   // trees
   struct TreeBufs {
-    DBuf<double> pbox, nbox;
+    DBuf<double> pbox;
+    DBuf<float4> nbox;  // outward-rounded FP32 node boxes, 2 float4 per node
     DBuf<unsigned long long> keys, keys2;
     DBuf<unsigned> vals, vals2;
     DBuf<int> child, parent, range, root, flags, hist;
@@ -410,6 +411,7 @@ struct ipc_scene {
   } ttri, tedge;
   // candidates / contacts
   DBuf<int> cnt_pt, off_pt, cnt_ee, off_ee, cand_j, nflag, noff, scan_tmp, overflow;
+  DBuf<int> ccd_cnt_pt, ccd_off_pt, ccd_cnt_ee, ccd_off_ee, ccd_j;  // swept-box candidates
   DBuf<ContactRec> ct_tmp, ct;
   DBuf<FrictionRec> fr;
   int n_pt = 0, n_ee = 0, n_ct = 0, n_ct_pt = 0, n_fr = 0, n_fr_pt = 0, n_inc = 0;
@@ -566,7 +568,7 @@ struct ipc_scene {
     return Sched{sched.p, grav.p, sched_off.p, grav_off.p, nh.p, node_handle.p, X0.p};
   }
   PtInfo ptinfo() const { return PtInfo{pt_body.p, pt_kin.p}; }
-  Tree tree(TreeBufs& T) const { return Tree{T.n, T.vals.p, T.child.p, T.nbox.p, T.root.p}; }
+  Tree tree(TreeBufs& T) const { return Tree{T.n, T.vals.p, T.child.p, T.nbox.p, T.pbox.p, T.root.p}; }
 
   // ------------------------------------------------------------------ layout
   void pull_state() {
@@ -1008,7 +1010,7 @@ struct ipc_scene {
   void tree_build(TreeBufs& T, const int* prim_pt, int nv, const int* prim_env, const int* prim_off) {
     int n = T.n;
     T.pbox.ensure(6 * (size_t)std::max(n, 1));
-    T.nbox.ensure(6 * (size_t)std::max(2 * n - 1, 1));
+    T.nbox.ensure(2 * (size_t)std::max(2 * n - 1, 1));
     T.keys.ensure(std::max(n, 1));
     T.vals.ensure(std::max(n, 1));
     T.child.ensure(2 * (size_t)std::max(n, 1));
@@ -1466,6 +1468,36 @@ struct ipc_scene {
     n_fr_pt = n_ct_pt;
   }
 
+  // CCD step filter on the envs still iterating: swept-box candidates at [x, x + p] (boxes
+  // already refit), then additive CCD per candidate pair; each env's alpha_max is the minimum
+  void ccd_filter(EnvCtl C) {
+    const uint8_t* act = e_iter.p;
+    ccd_cnt_pt.ensure(NSV + 1);
+    ccd_off_pt.ensure(NSV + 1);
+    ccd_cnt_ee.ensure(NED + 1);
+    ccd_off_ee.ensure(NED + 1);
+    CandOut cp{ccd_cnt_pt.p, nullptr, nullptr, overflow.p};
+    launch(k_trav_pt<TRAV_COUNT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
+           (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), cp, (const double*)nullptr, C);
+    CandOut ce{ccd_cnt_ee.p, nullptr, nullptr, overflow.p};
+    launch(k_trav_ee<TRAV_COUNT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+           (const double*)tedge.pbox.p, tree(tedge), ptinfo(), ce, (const double*)nullptr, (const double*)nullptr, C);
+    int np = scan(ccd_cnt_pt.p, NSV, ccd_off_pt.p);
+    int ne = scan(ccd_cnt_ee.p, NED, ccd_off_ee.p);
+    check_overflow();
+    if (np + ne == 0) return;
+    ccd_j.ensure(np + ne + 1);
+    CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p};
+    launch(k_trav_pt<TRAV_FILLU>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
+           (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp, (const double*)nullptr, C);
+    CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p};
+    launch(k_trav_ee<TRAV_FILLU>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+           (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr, C);
+    launch(k_accd_pairs, np + ne, 128, np, ne, (const int*)ccd_off_pt.p, NSV, (const int*)ccd_off_ee.p, NED,
+           (const int*)ccd_j.p, (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p,
+           (const int*)ed_env.p, (const double*)ptx.p, (const double*)ptp.p, C);
+  }
+
   void newton_step() {
     EnvCtl C = ctl();
     launch(k_env_begin_step, E, 128, E, C);
@@ -1491,15 +1523,9 @@ struct ipc_scene {
              (const double*)p.p, ptp.p);
       launch(k_add_vec, 3L * NP, 256, 3L * NP, (const double*)ptx.p, (const double*)ptp.p, pte.p);
       boxes_and_refit(pte.p, 0.0);
-      CandOut oc{nullptr, nullptr, nullptr, overflow.p};
       pbeg(IPC_PROF_CCD);
-      launch(k_trav_pt<TRAV_CCD>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, (const uint8_t*)e_iter.p,
-             (const double*)ptx.p, (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), oc,
-             (const double*)ptp.p, C);
-      launch(k_trav_ee<TRAV_CCD>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, (const uint8_t*)e_iter.p,
-             (const double*)tedge.pbox.p, tree(tedge), ptinfo(), oc, (const double*)ptx.p, (const double*)ptp.p, C);
+      ccd_filter(C);
       pend(IPC_PROF_CCD);
-      check_overflow();
       // backtracking line search on the envs still iterating
       launch(k_env_ls_begin, E, 128, E, C);
       for (int ls = 0; ls <= desc.max_ls_halvings + 1; ++ls) {

@@ -336,7 +336,8 @@ DEV bool excluded(const PtInfo& P, int a, int b, int c, int d) {
   return ba >= 0 && P.body[b] == ba && P.body[c] == ba && P.body[d] == ba;
 }
 
-enum { TRAV_COUNT = 0, TRAV_FILL = 1, TRAV_CCD = 2 };
+// count, fill (partners sorted per query), swept-box ACCD inline, fill unsorted
+enum { TRAV_COUNT = 0, TRAV_FILL = 1, TRAV_CCD = 2, TRAV_FILLU = 3 };
 
 struct CandOut {
   int* cnt;        // per query (count mode)
@@ -371,14 +372,14 @@ __global__ void k_trav_pt(int n_sv, const int* __restrict__ sv_pt, const int* __
     qb[3 + k] = __dadd_rn(hi, r);
   }
   int count = 0;
-  int base = MODE == TRAV_FILL ? O.off[q] : 0;
+  int base = (MODE == TRAV_FILL || MODE == TRAV_FILLU) ? O.off[q] : 0;
   double tmin = 1.0;
   long iters = 0;
   bool ok = bvh_visit(T, e, qb, [&](int j) {
     int a = tri_pt[3 * j], b = tri_pt[3 * j + 1], c = tri_pt[3 * j + 2];
     if (a == v || b == v || c == v) return;
     if (excluded(P, v, a, b, c)) return;
-    if (MODE == TRAV_FILL) O.cj[base + count] = j;
+    if (MODE == TRAV_FILL || MODE == TRAV_FILLU) O.cj[base + count] = j;
     if (MODE == TRAV_CCD) {
       d3 X[4] = {ld3(ptx, v), ld3(ptx, a), ld3(ptx, b), ld3(ptx, c)};
       d3 Pd[4] = {ld3(ptp, v), ld3(ptp, a), ld3(ptp, b), ld3(ptp, c)};
@@ -424,15 +425,14 @@ __global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __
   int a0 = ed_pt[2 * q], a1 = ed_pt[2 * q + 1];
   const double* qb = edge_box + 6L * q;
   int count = 0;
-  int base = MODE == TRAV_FILL ? O.off[q] : 0;
+  int base = (MODE == TRAV_FILL || MODE == TRAV_FILLU) ? O.off[q] : 0;
   double tmin = 1.0;
   long iters = 0;
-  bool ok = bvh_visit(T, e, qb, [&](int j) {
-    if (j <= q) return;
+  bool ok = bvh_visit(T, e, qb, [&](int j) { return j > q; }, [&](int j) {
     int b0 = ed_pt[2 * j], b1 = ed_pt[2 * j + 1];
     if (a0 == b0 || a0 == b1 || a1 == b0 || a1 == b1) return;
     if (excluded(P, a0, a1, b0, b1)) return;
-    if (MODE == TRAV_FILL) O.cj[base + count] = j;
+    if (MODE == TRAV_FILL || MODE == TRAV_FILLU) O.cj[base + count] = j;
     if (MODE == TRAV_CCD) {
       d3 X[4] = {ld3(ptx, a0), ld3(ptx, a1), ld3(ptx, b0), ld3(ptx, b1)};
       d3 Pd[4] = {ld3(ptp, a0), ld3(ptp, a1), ld3(ptp, b0), ld3(ptp, b1)};
@@ -512,6 +512,47 @@ __global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ off_pt, int
   c.type = type;
   tmp[i] = c;
   flag[i] = d2 < dhat2 ? 1 : 0;
+}
+
+// Additive CCD of every swept candidate pair (point-triangle pairs first, then edge-edge), one
+// thread per pair: the time of impact along [x, x + p] lowers the env's step bound alpha_max
+// (an atomic minimum on non-negative doubles: exact and independent of order).
+__global__ void k_accd_pairs(int n_pt, int n_ee, const int* __restrict__ off_pt, int n_sv,
+                             const int* __restrict__ off_ee, int n_ed, const int* __restrict__ cj,
+                             const int* __restrict__ sv_pt, const int* __restrict__ sv_env,
+                             const int* __restrict__ tri_pt, const int* __restrict__ ed_pt,
+                             const int* __restrict__ ed_env, const double* __restrict__ ptx,
+                             const double* __restrict__ ptp, EnvCtl C) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pt + n_ee) return;
+  int kind, e, pts[4];
+  if (i < n_pt) {
+    int q = cand_query(off_pt, n_sv, i), j = cj[i];
+    kind = 0;
+    e = sv_env[q];
+    pts[0] = sv_pt[q];
+    pts[1] = tri_pt[3 * j];
+    pts[2] = tri_pt[3 * j + 1];
+    pts[3] = tri_pt[3 * j + 2];
+  } else {
+    int k = i - n_pt;
+    int q = cand_query(off_ee, n_ed, k), j = cj[i];
+    kind = 1;
+    e = ed_env[q];
+    pts[0] = ed_pt[2 * q];
+    pts[1] = ed_pt[2 * q + 1];
+    pts[2] = ed_pt[2 * j];
+    pts[3] = ed_pt[2 * j + 1];
+  }
+  d3 X[4], Pd[4];
+  for (int a = 0; a < 4; ++a) {
+    X[a] = ld3(ptx, pts[a]);
+    Pd[a] = ld3(ptp, pts[a]);
+  }
+  long it;
+  double t = accd(kind, X, Pd, 0.1, 1.0, 1000000L, &it);
+  atomic_min_pos(&C.alpha_bits[e], t);
+  atomicAdd((unsigned long long*)&C.stats[5 * e + STAT_ACCD], (unsigned long long)it);
 }
 __global__ void k_compact_contacts(int n, const int* __restrict__ flag, const int* __restrict__ off,
                                    const ContactRec* __restrict__ tmp, ContactRec* __restrict__ out) {

@@ -218,34 +218,44 @@ __global__ void k_env_roots(int n, const int* __restrict__ range, const int* __r
   }
 }
 
-// Refit: leaves copy their primitive boxes; the second thread to reach an internal node
-// writes the union of its children and continues upward. flags must be zero on entry.
+// Node boxes are FP32, rounded outward from the FP64 primitive boxes (min down, max up), as two
+// float4 (lo, hi; w unused): a node box contains the exact box of everything below it, so a
+// culling test on them never drops a pair whose FP64 boxes overlap. Leaves are decided by the
+// exact FP64 test on the primitive boxes, so the candidate set is that of FP64 boxes.
+DEV void round_box_out(const double* b, float4* out) {
+  out[0] = make_float4(__double2float_rd(b[0]), __double2float_rd(b[1]), __double2float_rd(b[2]), 0.f);
+  out[1] = make_float4(__double2float_ru(b[3]), __double2float_ru(b[4]), __double2float_ru(b[5]), 0.f);
+}
+
+// Refit: leaves take their primitive boxes (rounded outward); the second thread to reach an
+// internal node writes the union of its children and continues upward. flags must be zero on
+// entry.
 __global__ void k_refit(int n, const unsigned* __restrict__ sorted, const double* __restrict__ pbox,
-                        const int* __restrict__ child, const int* __restrict__ parent, double* nbox,
+                        const int* __restrict__ child, const int* __restrict__ parent, float4* nbox,
                         int* __restrict__ flags) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   int leaf = n - 1 + j;
-  const double* b = pbox + 6 * (long)sorted[j];
-  for (int k = 0; k < 6; ++k) nbox[6 * (long)leaf + k] = b[k];
+  round_box_out(pbox + 6 * (long)sorted[j], nbox + 2 * (long)leaf);
   int node = parent[leaf];
   while (node >= 0) {
     __threadfence();
     if (atomicAdd(&flags[node], 1) == 0) return;
     __threadfence();
     int a = child[2 * node], c = child[2 * node + 1];
-    for (int k = 0; k < 3; ++k) {
-      double lo = fmin(__ldcg(nbox + 6 * (long)a + k), __ldcg(nbox + 6 * (long)c + k));
-      double hi = fmax(__ldcg(nbox + 6 * (long)a + 3 + k), __ldcg(nbox + 6 * (long)c + 3 + k));
-      nbox[6 * (long)node + k] = lo;
-      nbox[6 * (long)node + 3 + k] = hi;
-    }
+    float4 alo = __ldcg(nbox + 2 * (long)a), ahi = __ldcg(nbox + 2 * (long)a + 1);
+    float4 clo = __ldcg(nbox + 2 * (long)c), chi = __ldcg(nbox + 2 * (long)c + 1);
+    nbox[2 * (long)node] = make_float4(fminf(alo.x, clo.x), fminf(alo.y, clo.y), fminf(alo.z, clo.z), 0.f);
+    nbox[2 * (long)node + 1] = make_float4(fmaxf(ahi.x, chi.x), fmaxf(ahi.y, chi.y), fmaxf(ahi.z, chi.z), 0.f);
     node = parent[node];
   }
 }
 
 DEV bool box_overlap(const double* a, const double* b) {
   return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
+}
+DEV bool box_overlap_f(const float4& alo, const float4& ahi, const float4& blo, const float4& bhi) {
+  return alo.x <= bhi.x && blo.x <= ahi.x && alo.y <= bhi.y && blo.y <= ahi.y && alo.z <= bhi.z && blo.z <= ahi.z;
 }
 
 constexpr int BVH_STACK = 64;
@@ -255,29 +265,55 @@ struct Tree {
   int n;                  // primitives
   const unsigned* sorted; // leaf j -> primitive
   const int* child;
-  const double* nbox;     // 2n-1 boxes (internal then leaves)
+  const float4* nbox;     // 2n-1 outward-rounded boxes (internal then leaves), 2 float4 each
+  const double* pbox;     // exact primitive boxes (by primitive index)
   const int* root;        // per env
 };
 
 // Visit every primitive of env e whose box overlaps qbox; f(prim) is called in traversal order.
 // Returns false if the stack overflowed (then the visit is incomplete).
-template <class F>
-DEV bool bvh_visit(const Tree& T, int e, const double* qbox, F&& f) {
+// Visit every primitive j of env e with pre(j) true and an FP64 box overlapping qbox; f(j) is
+// called once for each, in no particular order. Children are tested on their outward-rounded
+// FP32 boxes before they are pushed; a leaf's exact FP64 test runs only after pre(j) and its FP32
+// test pass. Returns false if the stack overflowed (then the visit is incomplete).
+template <class P, class F>
+DEV bool bvh_visit(const Tree& T, int e, const double* qbox, P&& pre, F&& f) {
   int r = T.root[e];
   if (r < 0) return true;
+  float4 q[2];
+  round_box_out(qbox, q);
+  const int n1 = T.n - 1;
+  auto leaf = [&](int node) {
+    const int prim = (int)T.sorted[node - n1];
+    if (pre(prim) && box_overlap(qbox, T.pbox + 6 * (long)prim)) f(prim);
+  };
+  if (!box_overlap_f(q[0], q[1], T.nbox[2 * (long)r], T.nbox[2 * (long)r + 1])) return true;
+  if (r >= n1) {
+    leaf(r);
+    return true;
+  }
   int stack[BVH_STACK];
   int sp = 0;
   stack[sp++] = r;
   while (sp > 0) {
-    int node = stack[--sp];
-    if (!box_overlap(qbox, T.nbox + 6 * (long)node)) continue;
-    if (node >= T.n - 1) {
-      f((int)T.sorted[node - (T.n - 1)]);
-    } else {
-      if (sp + 2 > BVH_STACK) return false;
-      stack[sp++] = T.child[2 * node + 1];
-      stack[sp++] = T.child[2 * node];
+    const int node = stack[--sp];
+    const int c0 = T.child[2 * node], c1 = T.child[2 * node + 1];
+    const bool o0 = box_overlap_f(q[0], q[1], T.nbox[2 * (long)c0], T.nbox[2 * (long)c0 + 1]);
+    const bool o1 = box_overlap_f(q[0], q[1], T.nbox[2 * (long)c1], T.nbox[2 * (long)c1 + 1]);
+    if (o1) {
+      if (c1 >= n1) leaf(c1);
+      else if (sp < BVH_STACK) stack[sp++] = c1;
+      else return false;
+    }
+    if (o0) {
+      if (c0 >= n1) leaf(c0);
+      else if (sp < BVH_STACK) stack[sp++] = c0;
+      else return false;
     }
   }
   return true;
+}
+template <class F>
+DEV bool bvh_visit(const Tree& T, int e, const double* qbox, F&& f) {
+  return bvh_visit(T, e, qbox, [](int) { return true; }, f);
 }
