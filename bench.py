@@ -122,6 +122,41 @@ def peaks():
     return 6400.0, "fallback"
 
 
+# FP64 peak of one B300 from its unit counts and clock: 148 SMs x 4 FP64 flop/clk (2 DFMA) x
+# 2.032 GHz (1.25 TFLOP/s nominal at the boost clock; 1.11 measured by an FMA loop at 2032 MHz).
+FP64_PEAK_TFLOPS = 148 * 4 * 2.032e9 / 1e12
+
+
+def roofline(prof, precision):
+    kern = {"pcg_solve": "k_pcg_cluster (persistent per-environment PCG, whole solve per launch)",
+            "spmv": "k_spmv (PCG matrix-vector product)"}
+    solve = "pcg_solve" if prof["pcg_solve"]["launches"] > 0 else "spmv"
+    sp = prof[solve]
+    if not (sp["ms"] > 0 and sp["launches"] > 0):
+        return None
+    hbm, hbm_kind = peaks()
+    sec = sp["ms"] / 1000.0
+    gbs = sp["work"] / sec / 1e9
+    flops = prof["pcg_flops"]["work"] if solve == "pcg_solve" else 0.0
+    tflops = flops / sec / 1e12
+    fp64 = precision == "fp64"
+    # ridge point: intensity (flop/B) above peak_flops / peak_bandwidth is arithmetic-bound
+    intensity = flops / sp["work"] if sp["work"] > 0 else 0.0
+    alu_bound = fp64 and flops > 0 and intensity > FP64_PEAK_TFLOPS * 1e12 / (hbm * 1e9)
+    base = {"kernel": kern[solve], "traffic": None, "bytes_per_launch": sp["work"] / sp["launches"],
+            "flops_per_launch": flops / sp["launches"], "intensity_flop_per_byte": round(intensity, 4),
+            "avg_launch_us": 1000.0 * sp["ms"] / sp["launches"], "launches": sp["launches"],
+            "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4), "hbm_peak_source": f"{hbm_kind} hbm_gbs"}
+    if alu_bound:
+        base.update({"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                     "unit": "TFLOP/s (FP64)", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                     "note": "FP64 FMA pipe: peak from 148 SMs x 4 flop/clk x 2.032 GHz"})
+    else:
+        base.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                     "note": "fraction of measured HBM copy bandwidth"})
+    return base
+
+
 def cpu_oracle_sample(envs, states, params, n_threads):
     """Time the oracle on n_threads envs x 1 step from the given states (bounded CPU sample)."""
     from oracle import oracle as O
@@ -245,23 +280,11 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant profiled kernel family
-    peak, peak_kind = peaks()
+    # ---- roofline of the dominant kernel: the persistent per-env PCG when it runs, else the
+    # tiled SpMV. Its bound is the roof its arithmetic intensity reaches first: FP64 arithmetic
+    # (B300 runs FP64 at 1/58 of FP32) or HBM bandwidth.
     fam = max(prof, key=lambda k: prof[k]["ms"])
-    # the linear solve is the dominant HBM-bound kernel: the persistent per-env PCG when it runs,
-    # else the tiled SpMV
-    kern = {"pcg_solve": "k_pcg_cluster (persistent per-environment PCG, whole solve per launch)",
-            "spmv": "k_spmv (PCG matrix-vector product)"}
-    solve = "pcg_solve" if prof["pcg_solve"]["launches"] > 0 else "spmv"
-    sp = prof[solve]
-    roof = None
-    if sp["ms"] > 0 and sp["launches"] > 0:
-        achieved = sp["work"] / (sp["ms"] / 1000.0) / 1e9
-        roof = {"kernel": kern[solve], "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": peak, "peak_source": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "bytes_per_launch": sp["work"] / sp["launches"],
-                "avg_launch_us": 1000.0 * sp["ms"] / sp["launches"], "launches": sp["launches"],
-                "dominant_family": fam, "note": "fraction of measured HBM copy bandwidth"}
+    roof = roofline(prof, args.precision)
     tets = int(np.mean([sum(len(s["tets"]) for s in e["soft"]) for e in envs]))
 
     cpu = None
@@ -281,7 +304,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(h_out.nbytes)},
         "gpu_launches": int(launches), "clocks": clk, "mixed_precision": mixed,
         "env_steps_done": int(steps_done), "envs_failed": int(failed),
-        "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items()},
+        "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k != "pcg_flops"},
         "counters_last_iteration": sc.scene_counters(ids[0]),
         "newton_iters_per_env_step": round(sum(sc.status(e)["newton_iters"] for e in ids) / max(steps_done, 1), 2),
         "pcg_iters_per_newton": round(sum(sc.status(e)["pcg_iters"] for e in ids)
@@ -339,7 +362,8 @@ def mixed_leg(args, params, envs, snap, p_start, x_end, stream, device, ms_fp64)
             "rel_displacement_diff": diff / disp if disp > 0 else None,
             "rel_object_displacement_diff": obj_diff / disp if disp > 0 else None, "envs_failed": int(failed),
             "dtype": "f32 Hessians + PCG, f64 energies/gradients/barrier/CCD/line search",
-            "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items()}}
+            "roofline": roofline(prof, "mixed"),
+            "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k != "pcg_flops"}}
 
 
 def run_reference(args):

@@ -228,8 +228,10 @@ typedef enum {
   IPC_PROF_BROAD = 5,       /* constraint-set traversal, narrow phase */
   IPC_PROF_ASSEMBLY = 6,    /* gradient / BSR gather, preconditioner blocks, stencil incidence */
   IPC_PROF_LS_ENERGY = 7,   /* energy-only evaluation of line-search trials */
-  IPC_PROF_PCG_SOLVE = 8,   /* persistent per-environment PCG (whole solve in one launch) */
-  IPC_PROF_COUNT = 9
+  IPC_PROF_PCG_SOLVE = 8,   /* persistent per-environment PCG (work: algorithmic bytes) */
+  IPC_PROF_PCG_FLOPS = 9,   /* work only: floating-point operations of the persistent PCG (an FMA
+                               counts 2); its launches and time are those of IPC_PROF_PCG_SOLVE */
+  IPC_PROF_COUNT = 10
 } ipc_prof_family;
 /* Turn profiling on (1) or off (0); turning it on clears the counters. */
 ipc_status ipc_profile_enable(ipc_scene* scene, int32_t on);

@@ -394,7 +394,7 @@ struct ipc_scene {
   DBuf<double> pcg_r, pcg_z, pcg_d, pcg_y, pcg_x, part_a, part_b, part_c, pcg_rz, pcg_bb;
   DBuf<int> pcg_it, pcg_active;
   DBuf<double> pcg_part;  // per-slot partial sums of the persistent PCG
-  DBuf<double> pcg_rzs, pcg_bbs, pcg_iterb;  // per-env state of the persistent PCG between launches
+  DBuf<double> pcg_rzs, pcg_bbs, pcg_iterb, pcg_iterf;  // per-env state of the persistent PCG
   DBuf<int> pcg_its, env_iota, env_list;
   DBuf<uint8_t> pcg_runs;
   DBuf<uint8_t> pcg_run;
@@ -851,7 +851,7 @@ struct ipc_scene {
       pslice_off.upload(poff, s);
       pslice_row.upload(prow, s);
       pslice_sel.upload(psel, s);
-      pcg_part.alloc(mixed() ? 1 : 6 * ((size_t)n_slices + NB) + 6);
+      pcg_part.alloc(mixed() ? 1 : 8 * ((size_t)n_slices + NB) + 8);
     }
     slice_w.upload(sw, s);
     slice_vbase.upload(svb, s);
@@ -911,6 +911,7 @@ struct ipc_scene {
       pcg_rzs.alloc(E);
       pcg_bbs.alloc(E);
       pcg_iterb.alloc(E);
+      pcg_iterf.alloc(E);
       pcg_its.alloc(E);
       pcg_runs.alloc(E);
       if (mixed()) {
@@ -974,7 +975,7 @@ struct ipc_scene {
         b->alloc(n3);
         b->zero(s);  // kinematic soft rows are never written by the persistent PCG: d stays 0
       }
-      f_part.alloc(6 * ((size_t)n_slices + NB) + 6);
+      f_part.alloc(8 * ((size_t)n_slices + NB) + 8);
     } else {
       tet_H.alloc(90 * (size_t)NT);
       body_H.alloc(144 * (size_t)NB);
@@ -1329,10 +1330,12 @@ struct ipc_scene {
     a.rz_state = pcg_rzs.p;
     a.bb_state = pcg_bbs.p;
     a.iterb_state = pcg_iterb.p;
+    a.iterf_state = pcg_iterf.p;
     a.it_state = pcg_its.p;
     a.run = pcg_runs.p;
     a.stats = e_stats.p;
     a.bytes = punits(IPC_PROF_PCG_SOLVE);
+    a.flops = punits(IPC_PROF_PCG_FLOPS);
     int n = E;
     pcg_C = pick_cluster(n);
     int C = pcg_C;
@@ -1989,15 +1992,16 @@ ipc_status ipc_profile_read(ipc_scene* s, int32_t fam, int64_t* launches, double
   if (!s || fam < 0 || fam >= IPC_PROF_COUNT) fail_with(IPC_ERR_ARG, "bad argument");
   CK(cudaSetDevice(s->device));
   CK(cudaStreamSynchronize(s->stream));
-  double t = s->prof_graph_ms[fam];
-  for (auto& pr : s->prof_ev[fam]) {
+  const int tf = fam == IPC_PROF_PCG_FLOPS ? IPC_PROF_PCG_SOLVE : fam;  // a work-only family
+  double t = s->prof_graph_ms[tf];
+  for (auto& pr : s->prof_ev[tf]) {
     float m = 0.f;
     CK(cudaEventElapsedTime(&m, pr.first, pr.second));
     t += m;
   }
   unsigned long long u[IPC_PROF_COUNT] = {0};
   if (s->prof_units.p) CK(cudaMemcpy(u, s->prof_units.p, sizeof(u), cudaMemcpyDeviceToHost));
-  if (launches) *launches = s->prof_launches[fam];
+  if (launches) *launches = s->prof_launches[tf];
   if (ms) *ms = t;
   if (work) *work = (double)u[fam];
   API_END

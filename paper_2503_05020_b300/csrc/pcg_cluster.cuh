@@ -49,7 +49,7 @@ struct PcgClusterArgs {
   T* st_t;                // stencil products (the same buffer SpmvArgs reads)
   double tol2;             // (relative tolerance)^2
   int max_it;
-  T* part;                    // slot partials: 2 x 3 values x (s_total + n_bodies)
+  T* part;                    // slot partials: 2 x 4 values x (s_total + n_bodies)
   int s_total;                // slices of the whole batch
   int n_bodies;               // rigid bodies of the whole batch
   const int* env_list;        // env of each cluster
@@ -58,10 +58,12 @@ struct PcgClusterArgs {
   double* rz_state;           // per env: r.z after the last iteration
   double* bb_state;           // per env: |b|^2 (right-hand side)
   double* iterb_state;        // per env: algorithmic bytes of one iteration
+  double* iterf_state;        // per env: floating-point operations of one iteration
   int* it_state;              // per env: iterations so far
   uint8_t* run;               // per env: 1 while the solve continues
   long long* stats;           // 5 per env; [STAT_PCG] += iterations of this solve
   unsigned long long* bytes;  // algorithmic bytes of all iterations (may be null)
+  unsigned long long* flops;  // floating-point operations of all iterations (null when bytes is)
 };
 
 // Sum of an env's slot partials (its slices, then its bodies) in a fixed order that depends on
@@ -78,7 +80,7 @@ DEV void env_sum(const T* part, int S0, int S1, int s_total, int b0, int b1, T* 
     for (int j = lane; j < n; j += 32) {
       long slot = j < ns ? S0 + j : (long)s_total + b0 + (j - ns);
 #pragma unroll
-      for (int q = 0; q < K; ++q) s[q] += __ldcg(part + 3 * slot + q);
+      for (int q = 0; q < K; ++q) s[q] += __ldcg(part + 4 * slot + q);
     }
 #pragma unroll
     for (int q = 0; q < K; ++q) {
@@ -115,6 +117,21 @@ template <class T>
 DEV double stencil_iter_bytes() {
   return 78.0 * sizeof(T) + 16.0 + 24.0 * sizeof(T);
 }
+// Floating-point operations of one iteration (an FMA counts 2). A soft row: 18 per sliced-ELL
+// block, 6 per stencil entry, 6 for d.y; then x, r updates (12), z = M^-1 r (18), r.z and r.r
+// (12), d = z + beta d (6). A rigid body: 21 per p-node entry, the dense block (288) and d.y
+// (24), x, r updates (48), the 12x12 preconditioner (288), r.z and r.r (48), d update (24). A
+// stencil: the 12x12 product (288).
+template <class T>
+DEV double soft_iter_flops(const SpmvArgsT<T, T>& A, int row) {
+  return 18.0 * (A.bsr_ptr[row + 1] - A.bsr_ptr[row]) + 6.0 * (A.ns_ptr[row + 1] - A.ns_ptr[row]) + 6.0 + 48.0;
+}
+template <class T>
+DEV double body_iter_flops(const Layout& L, const SpmvArgsT<T, T>& A, int bd) {
+  long base = L.body_node[bd];
+  return 21.0 * (A.ns_ptr[base + 1] - A.ns_ptr[base]) + 288.0 + 24.0 + 48.0 + 288.0 + 48.0 + 24.0;
+}
+constexpr double STENCIL_ITER_FLOPS = 288.0;
 
 template <int C, class T>
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P) {
@@ -136,8 +153,8 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P
   const int S0 = P.pslice_off[e], S1 = P.pslice_off[e + 1];
   const int b0 = P.body_off[e], b1 = P.body_off[e + 1];
   const int ST = P.s_total;
-  T* part_dy = P.part;                                  // 3 values per slot, [0] used
-  T* part_rz = P.part + 3L * (P.s_total + P.n_bodies);  // (r.z, r.r, bytes) per slot
+  T* part_dy = P.part;                                  // 4 values per slot, [0] used
+  T* part_rz = P.part + 4L * (P.s_total + P.n_bodies);  // (r.z, r.r, bytes, flops) per slot
   if (tid < 4) {  // this env's range in each stencil sublist
     int lo = P.st_bounds[tid], hi = P.st_bounds[tid + 1];
     srange[2 * tid] = lower_env(P.st_env, lo, hi, e);
@@ -147,13 +164,13 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P
   const int n_stencils = srange[1] - srange[0] + srange[3] - srange[2] + srange[5] - srange[4] + srange[7] - srange[6];
 
   T rz, bb;
-  double iter_bytes;
+  double iter_bytes, iter_flops;
   int it;
   bool go;
   if (P.first) {
     // ---- z = M^-1 r, d = z, x = 0; per-slot (r.z, r.r) and the bytes of one iteration
     for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {  // warp-uniform
-      T a = T(0), c = T(0), nb = T(0);
+      T a = T(0), c = T(0), nb = T(0), nf = T(0);
       const int i = P.pslice_row[32 * sl + lane];
       if (i >= 0) {
         precond_soft(i, P.Ps, P.r, P.z, &a, &c);
@@ -161,15 +178,20 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P
           P.d[k] = P.z[k];
           P.x[k] = T(0);
         }
-        if (P.bytes) nb = T(soft_iter_bytes(P.A, i));
+        if (P.bytes) {
+          nb = T(soft_iter_bytes(P.A, i));
+          nf = T(soft_iter_flops(P.A, i));
+        }
       }
       a = warp_sum(a);
       c = warp_sum(c);
       nb = warp_sum(nb);
+      nf = warp_sum(nf);
       if (lane == 0) {
-        part_rz[3L * sl] = a;
-        part_rz[3L * sl + 1] = c;
-        part_rz[3L * sl + 2] = nb;
+        part_rz[4L * sl] = a;
+        part_rz[4L * sl + 1] = c;
+        part_rz[4L * sl + 2] = nb;
+        part_rz[4L * sl + 3] = nf;
       }
     }
     for (int b = b0; b < b1; ++b) {
@@ -188,25 +210,28 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P
         c = warp_sum(c);
         if (lane == 0) {
           long slot = (long)ST + b;
-          part_rz[3 * slot] = a;
-          part_rz[3 * slot + 1] = c;
-          part_rz[3 * slot + 2] = P.bytes ? T(body_iter_bytes(L, P.A, b)) : T(0);
+          part_rz[4 * slot] = a;
+          part_rz[4 * slot + 1] = c;
+          part_rz[4 * slot + 2] = P.bytes ? T(body_iter_bytes(L, P.A, b)) : T(0);
+          part_rz[4 * slot + 3] = P.bytes ? T(body_iter_flops(L, P.A, b)) : T(0);
         }
       }
       __syncthreads();
     }
     cl.sync();
-    T v3[3];
-    env_sum<3>(part_rz, S0, S1, ST, b0, b1, tot, v3);
-    rz = v3[0];
-    bb = v3[1];
-    iter_bytes = double(v3[2]) + (P.bytes ? stencil_iter_bytes<T>() * n_stencils : 0.0);
+    T v4[4];
+    env_sum<4>(part_rz, S0, S1, ST, b0, b1, tot, v4);
+    rz = v4[0];
+    bb = v4[1];
+    iter_bytes = double(v4[2]) + (P.bytes ? stencil_iter_bytes<T>() * n_stencils : 0.0);
+    iter_flops = double(v4[3]) + (P.bytes ? STENCIL_ITER_FLOPS * n_stencils : 0.0);
     it = 0;
     go = bb > T(0) && isfinite(bb);
   } else {
     rz = T(P.rz_state[e]);
     bb = T(P.bb_state[e]);
     iter_bytes = P.iterb_state[e];
+    iter_flops = P.iterf_state[e];
     it = P.it_state[e];
     go = true;
   }
@@ -231,7 +256,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P
         dy = soft_row<true>(P.A, sel >> 5, sel & 31, i, (const T*)P.d, P.y);
       }
       dy = warp_sum(dy);
-      if (lane == 0) part_dy[3L * sl] = dy;
+      if (lane == 0) part_dy[4L * sl] = dy;
     }
     // ---- rigid bodies on their owner CTA: stencil entries gathered by its threads in a fixed
     // partition, the dense 12x12 block, one partial d.y per body
@@ -282,7 +307,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P
           dyb = v * __ldcg(P.d + 3 * base + lane);
         }
         dyb = warp_sum(dyb);
-        if (lane == 0) part_dy[3 * ((long)ST + b)] = dyb;
+        if (lane == 0) part_dy[4 * ((long)ST + b)] = dyb;
       }
       __syncthreads();
     }
@@ -304,8 +329,8 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P
       a = warp_sum(a);
       c = warp_sum(c);
       if (lane == 0) {
-        part_rz[3L * sl] = a;
-        part_rz[3L * sl + 1] = c;
+        part_rz[4L * sl] = a;
+        part_rz[4L * sl + 1] = c;
       }
     }
     for (int b = b0; b < b1; ++b) {
@@ -325,8 +350,8 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P
         a = warp_sum(a);
         c = warp_sum(c);
         if (lane == 0) {
-          part_rz[3 * ((long)ST + b)] = a;
-          part_rz[3 * ((long)ST + b) + 1] = c;
+          part_rz[4 * ((long)ST + b)] = a;
+          part_rz[4 * ((long)ST + b) + 1] = c;
         }
       }
       __syncthreads();
@@ -359,10 +384,14 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P
     P.rz_state[e] = double(rz);
     P.bb_state[e] = double(bb);
     P.iterb_state[e] = iter_bytes;
+    P.iterf_state[e] = iter_flops;
     P.it_state[e] = it;
     P.run[e] = more ? 1 : 0;
     P.stats[5 * e + STAT_PCG] += it - it0;
-    if (P.bytes) atomicAdd(P.bytes, (unsigned long long)(iter_bytes * (it - it0)));
+    if (P.bytes) {
+      atomicAdd(P.bytes, (unsigned long long)(iter_bytes * (it - it0)));
+      atomicAdd(P.flops, (unsigned long long)(iter_flops * (it - it0)));
+    }
   }
 }
 

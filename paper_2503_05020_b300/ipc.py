@@ -272,7 +272,8 @@ class Scene:
         lib().ipc_get_all_dofs(self._h, None, 0, C.byref(w))
         return w.value // 8
 
-    PROF_FAMILIES = ["spmv", "elastic", "contact", "ccd", "pcg_vector", "broad", "assembly", "ls_energy", "pcg_solve"]
+    PROF_FAMILIES = ["spmv", "elastic", "contact", "ccd", "pcg_vector", "broad", "assembly", "ls_energy", "pcg_solve",
+                     "pcg_flops"]
 
     def profile(self, on: bool = True):
         _check(lib().ipc_profile_enable(self._h, int(on)))
