@@ -383,7 +383,7 @@ struct ipc_scene {
   DBuf<double> bsr_val, Ps, Pb;
   // mixed precision: FP32 Hessians, sliced-ELL values, preconditioner blocks, stencil Hessians,
   // entry weights and every vector of the PCG (the FP64 twins above hold them otherwise)
-  DBuf<float> f_tet_H, f_body_H, f_bsr_val, f_Ps, f_Pb, f_sH, f_ns_w, f_ns_xb, f_st_t;
+  DBuf<float> f_tet_H, f_body_H, f_bsr_val, f_Ps, f_Pb, f_sH, f_ns_w, f_ns_xb, f_st_t, f_st_xb;
   DBuf<float> f_r, f_z, f_d, f_y, f_x, f_part;
   bool mixed() const { return desc.precision == IPC_MIXED; }
   template <class T>
@@ -418,7 +418,8 @@ struct ipc_scene {
   DBuf<int> st_pts, st_env, st_cnt, st_off, ns_ptr, ns_src, ns_cnt;
   DBuf<unsigned long long> st_keys, st_keys2;
   DBuf<unsigned> st_vals, st_vals2;
-  DBuf<double> sE, sg, sH, st_t, ns_w, ns_xb;
+  DBuf<double> sE, sg, sH, st_t, ns_w, ns_xb, st_xb;
+  DBuf<int> st_node;  // per stencil point: its node, or -1 - the p node of its affine body
   DBuf<long long> pcg_iters;
   DBuf<int> st_hist, root_off_tri, root_off_ed;
   // profiling: event pairs per family, device work counters
@@ -1113,11 +1114,14 @@ struct ipc_scene {
     sE.ensure(ns + 1);
     sg.ensure(12 * (size_t)ns + 12);
     st_t.ensure(12 * (size_t)ns + 12);
+    st_node.ensure(4 * (size_t)ns + 4);
     if (mixed()) {
       f_sH.ensure(78 * (size_t)ns + 78);
       f_st_t.ensure(12 * (size_t)ns + 12);
+      f_st_xb.ensure(12 * (size_t)ns + 12);
     } else {
       sH.ensure(78 * (size_t)ns + 78);
+      st_xb.ensure(12 * (size_t)ns + 12);
     }
     launch(k_stencil_table, ns, 256, n_ct, n_fr, (const ContactRec*)ct.p, (const FrictionRec*)fr.p, st_pts.p, st_env.p);
   }
@@ -1196,11 +1200,15 @@ struct ipc_scene {
       f_ns_xb.ensure(3 * (size_t)ne + 3);
       launch(k_entry_weights<float>, NN, 256, NN, layout(), act, (const int*)ns_ptr.p, (const int*)ns_src.p,
              (const int*)st_pts.p, f_ns_w.p, f_ns_xb.p);
+      launch(k_stencil_nodes<float>, 4L * ns, 256, ns, layout(), (const int*)st_pts.p, (const int*)st_env.p, act,
+             st_node.p, f_st_xb.p);
     } else {
       ns_w.ensure(ne + 1);
       ns_xb.ensure(3 * (size_t)ne + 3);
       launch(k_entry_weights<double>, NN, 256, NN, layout(), act, (const int*)ns_ptr.p, (const int*)ns_src.p,
              (const int*)st_pts.p, ns_w.p, ns_xb.p);
+      launch(k_stencil_nodes<double>, 4L * ns, 256, ns, layout(), (const int*)st_pts.p, (const int*)st_env.p, act,
+             st_node.p, st_xb.p);
     }
   }
 
@@ -1208,8 +1216,9 @@ struct ipc_scene {
   template <class HT, class VT>
   SpmvArgsT<HT, VT> spmv_args(const VT* st) {
     SellT<HT> S{tile_slice.p, slice_w.p, slice_vbase.p, slice_cbase.p, sell_col.p, hp<HT>(bsr_val, f_bsr_val)};
-    return SpmvArgsT<HT, VT>{S,  bsr_ptr.p, hp<HT>(body_H, f_body_H), ns_ptr.p, ns_src.p, hp<HT>(ns_w, f_ns_w),
-                             hp<HT>(ns_xb, f_ns_xb), st_pts.p, st};
+    return SpmvArgsT<HT, VT>{S,      bsr_ptr.p,  hp<HT>(body_H, f_body_H), ns_ptr.p,
+                             ns_src.p, hp<HT>(ns_w, f_ns_w), hp<HT>(ns_xb, f_ns_xb), st_pts.p,
+                             st,     hp<HT>(sH, f_sH), st_node.p, hp<HT>(st_xb, f_st_xb)};
   }
   SpmvArgs spmv_args() { return spmv_args<double, double>(st_t.p); }
   // y = H d over the envs in run (stencil product, then BSR/body rows); partial d.y per tile.

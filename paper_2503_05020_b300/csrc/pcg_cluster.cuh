@@ -25,6 +25,9 @@ namespace cg = cooperative_groups;
 
 constexpr int PCG_THREADS = 256;
 constexpr int PCG_WARPS = PCG_THREADS / 32;
+#ifndef PCG_MIN_CTAS
+#define PCG_MIN_CTAS 2  // CTAs per SM the register budget must allow
+#endif
 
 // T: precision of the matrix, the vectors and every sum (FP64, or FP32 in mixed precision).
 template <class T>
@@ -95,12 +98,12 @@ DEV void env_sum(const T* part, int S0, int S1, int s_total, int b0, int b1, T* 
 
 // Algorithmic bytes of one PCG iteration, per item, with values of b = sizeof(T) bytes. A soft
 // row: its sliced-ELL blocks (9b + 4 B column each), d read and y written (6b), 16 B of row
-// pointers, its stencil entries (4 B index + b weight + 3b stencil product each), then the
-// vector phase: x, r read and written (12b), d, y read (6b), the 3x3 preconditioner block (9b),
-// z written (3b) and d = z + beta d (9b). A rigid body: dense block (144b), its d and y (24b),
-// per p-node entry 4 B + 3b rest coordinates + 3b stencil product, the 12x12 preconditioner
-// (144b) and 12 DOFs x 10b of vector traffic. A stencil: packed Hessian (78b), 4 point indices
-// (16 B), 4 gathered d triples (12b) and t written (12b).
+// pointers, its stencil entries (4 B index + b weight each), then the vector phase: x, r read
+// and written (12b), d, y read (6b), the 3x3 preconditioner block (9b), z written (3b) and
+// d = z + beta d (9b). A rigid body: dense block (144b), its d and y (24b), per p-node entry
+// 4 B + 3b rest coordinates, the 12x12 preconditioner (144b) and 12 DOFs x 10b of vector
+// traffic. A stencil: packed Hessian (78b), 4 point nodes (16 B), their rest coordinates (12b),
+// 4 gathered d triples (12b) and t written (12b); each entry then reads its slot of t (3b).
 template <class T>
 DEV double soft_iter_bytes(const SpmvArgsT<T, T>& A, int row) {
   const double b = sizeof(T);
@@ -115,7 +118,7 @@ DEV double body_iter_bytes(const Layout& L, const SpmvArgsT<T, T>& A, int bd) {
 }
 template <class T>
 DEV double stencil_iter_bytes() {
-  return 78.0 * sizeof(T) + 16.0 + 24.0 * sizeof(T);
+  return 78.0 * sizeof(T) + 16.0 + 36.0 * sizeof(T);
 }
 // Floating-point operations of one iteration (an FMA counts 2). A soft row: 18 per sliced-ELL
 // block, 6 per stencil entry, 6 for d.y; then x, r updates (12), z = M^-1 r (18), r.z and r.r
@@ -134,7 +137,7 @@ DEV double body_iter_flops(const Layout& L, const SpmvArgsT<T, T>& A, int bd) {
 constexpr double STENCIL_ITER_FLOPS = 288.0;
 
 template <int C, class T>
-__global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P) {
+__global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgClusterArgs<T> P) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int e = P.env_list[blockIdx.x / C];
@@ -239,12 +242,13 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_cluster(PcgClusterArgs<T> P
   const int it0 = it;
   bool more = go;  // the solve continues after this launch
   for (int k = 0; go && k < P.chunk; ++k) {
-    // ---- t_s = H_s (P_s d) for the env's stencils (the barrier publishes every CTA's d)
+    // ---- t_s = H_s (P_s d) for the env's stencils, one half-warp per stencil (the barrier
+    // publishes every CTA's d)
     cl.sync();
-    for (int q = 0; q < 4; ++q)  // one half-warp per stencil (warp-uniform loop)
+    for (int q = 0; q < 4; ++q)  // warp-uniform loop
       for (int s0 = srange[2 * q] + 2 * gwarp; s0 < srange[2 * q + 1]; s0 += 2 * nwarps) {
         int s = s0 + (lane >> 4);
-        stencil_product_hw<true>(L, P.A.st_pts, P.sH, (const T*)P.d, P.st_t, s, s < srange[2 * q + 1]);
+        stencil_product_nodes<true>(P.A, (const T*)P.d, P.st_t, s, s < srange[2 * q + 1]);
       }
     cl.sync();
     // ---- y = A d: soft rows, one partial d.y per slice

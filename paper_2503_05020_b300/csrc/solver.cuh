@@ -290,9 +290,64 @@ struct SpmvArgsT {
   const HT* ns_w;     // weight of the entry's node in the slot's point position
   const HT* ns_xb;    // body p-node entries: rest coordinates (xb) of the entry's point
   const int* st_pts;
-  const VT* st_t;
+  const VT* st_t;      // stencil products
+  const HT* sH;        // stencil Hessians (packed)
+  const int* sn;       // per stencil point: its node, or -1 - the p node of its affine body
+  const HT* sxb;       // per stencil point: rest coordinates of an affine point (else 0)
 };
 using SpmvArgs = SpmvArgsT<double, double>;
+
+// Point nodes of every stencil, once per Newton iteration, so that the PCG's stencil products
+// need one dependent load (the node) before the vector loads. One thread per stencil point.
+template <class HT>
+__global__ void k_stencil_nodes(int n_st, Layout L, const int* __restrict__ st_pts, const int* __restrict__ st_env,
+                                const uint8_t* __restrict__ act, int* __restrict__ sn, HT* __restrict__ sxb) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= 4 * n_st) return;
+  if (!act[st_env[k >> 2]]) return;
+  int pt = st_pts[k], nd = L.pt_node[pt];
+  if (nd >= 0) {
+    sn[k] = nd;
+    for (int c = 0; c < 3; ++c) sxb[3L * k + c] = HT(0);
+  } else {
+    sn[k] = -1 - L.body_node[-1 - nd];
+    for (int c = 0; c < 3; ++c) sxb[3L * k + c] = HT(L.pt_xb[3 * pt + c]);
+  }
+}
+
+// t_s = H_s (P_s d) for stencil s by the 16 lanes of a half-warp, like stencil_product_hw but
+// with the point nodes precomputed (k_stencil_nodes): lanes 0..3 load their point's node and
+// then its vector entries. Every lane of the warp calls it; ok = false idles a half.
+template <bool CG, class T>
+DEV void stencil_product_nodes(const SpmvArgsT<T, T>& A, const T* d, T* st_t, int s, bool ok) {
+  const int lane = threadIdx.x & 31, half = lane & 16, l = lane & 15;
+  T v[3] = {T(0), T(0), T(0)};
+  if (ok && l < 4) {
+    const int nd = A.sn[4 * s + l];
+    if (nd >= 0) {
+      for (int c = 0; c < 3; ++c) v[c] = ldv<CG>(d, 3L * nd + c);
+    } else {
+      const long base = -1 - nd;
+      const T* xb = A.sxb + 3L * (4 * s + l);
+      const T x0 = xb[0], x1 = xb[1], x2 = xb[2];
+      for (int c = 0; c < 3; ++c)
+        v[c] = ldv<CG>(d, 3 * base + c) + x0 * ldv<CG>(d, 3 * base + 3 + c) + x1 * ldv<CG>(d, 3 * base + 6 + c) +
+               x2 * ldv<CG>(d, 3 * base + 9 + c);
+    }
+  }
+  T u[12];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[3 * a + c] = __shfl_sync(0xffffffffu, v[c], half + a);
+  if (ok && l < 12) {
+    const T* H = A.sH + 78L * s;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc += H[sym_idx(l, j, 12)] * u[j];
+    st_t[12L * s + l] = acc;
+  }
+}
 
 // weight of every incidence entry, once per Newton iteration; entries of a body's p node also
 // get the rest coordinates of their point, so one pass over that list serves all 4 body nodes
@@ -321,7 +376,7 @@ DEV T warp_sum(T v) {
 }
 
 // y row of one soft node from its sliced-ELL blocks (slice, lane) and its stencil entries;
-// returns d_row . y_row. Products in VT.
+// returns d_row . y_row. Products in VT; the entries' stencil products are read from st_t.
 template <bool CG, class HT, class VT>
 DEV VT soft_row(const SpmvArgsT<HT, VT>& A, int slice, int lane, int row, const VT* d, VT* y) {
   VT acc[3] = {VT(0), VT(0), VT(0)};
