@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--pcg-cluster", type=int, default=0,
                     help="PCG launch shape: 0 automatic, 1/2/4/8 CTAs per env cluster, -1 tiled multi-launch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: none)")
+    ap.add_argument("--serve-rate", type=float, default=1.5, help="Poisson arrival rate of the serving leg (1/s)")
     ap.add_argument("--no-mixed-leg", action="store_true",
                     help="skip the mixed-precision run of the same steps that the FP64 line reports beside it")
     ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle time for --impl reference")
@@ -302,7 +304,7 @@ def run_ours(args):
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h_tg.nbytes),
                 "d2h_bytes_per_step": int(h_out.nbytes)},
-        "gpu_launches": int(launches), "clocks": clk, "mixed_precision": mixed,
+        "gpu_launches": int(launches), "clocks": clk, "mixed_precision": mixed, "serving": None,
         "env_steps_done": int(steps_done), "envs_failed": int(failed),
         "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k != "pcg_flops"},
         "counters_last_iteration": sc.scene_counters(ids[0]),
@@ -310,6 +312,8 @@ def run_ours(args):
         "pcg_iters_per_newton": round(sum(sc.status(e)["pcg_iters"] for e in ids)
                                       / max(sum(sc.status(e)["newton_iters"] for e in ids), 1), 1),
     }
+    if world == 1 and args.serve_requests > 0:
+        line["serving"] = serving_leg(args, params, local)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -364,6 +368,32 @@ def mixed_leg(args, params, envs, snap, p_start, x_end, stream, device, ms_fp64)
             "dtype": "f32 Hessians + PCG, f64 energies/gradients/barrier/CCD/line search",
             "roofline": roofline(prof, "mixed"),
             "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k != "pcg_flops"}}
+
+
+def serving_leg(args, params, device):
+    """Grasp-evaluation serving: a seeded Poisson stream of requests (one pad grasp each: close,
+    lift 0.1 m, shake +/-15 deg at 2 Hz; 200 steps; seeded objects of uneven size) served by
+    continuous batching on one device-resident scene, in FP64 and in mixed precision."""
+    from paper_2503_05020_b300 import ipc
+    from paper_2503_05020_b300.serve import GraspServer, Request, poisson_arrivals
+
+    n = args.serve_requests
+    envs = [S.grasp_request_env(5000 + i) for i in range(n)]
+    arrivals = poisson_arrivals(args.serve_rate, n, 20250306)
+    out = {"requests": n, "rate_req_s": args.serve_rate, "steps_per_request": len(envs[0]["targets"]),
+           "request": "pad grasp: close 80 steps, lift 0.1 m in 60, shake +/-15 deg at 2 Hz for 60; dt 5 ms"}
+    for name, prec in (("fp64", ipc.FP64), ("mixed", ipc.MIXED)):
+        reqs = [Request(i, e, t) for i, (e, t) in enumerate(zip(envs, arrivals))]
+        srv = GraspServer(params, precision=prec, device=device, max_envs=64, admit_period=8)
+        rep = srv.run(reqs)
+        held = [bool(r.result.get("held")) for r in reqs]
+        out[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rep.items()}
+        out[name]["held"] = int(sum(held))
+        out.setdefault("held_labels", {})[name] = held
+        del srv
+    lab = out.pop("held_labels")
+    out["grasp_labels_agree"] = lab["fp64"] == lab["mixed"]
+    return out
 
 
 def run_reference(args):

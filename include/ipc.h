@@ -128,12 +128,15 @@ typedef enum {
   IPC_Q_SIZES = 7,       /* int64[8]: ndof, points, surface vertices, edges, triangles, tets,
                             bodies, steps */
   IPC_Q_INTERSECTIONS = 8, /* int64[2]: segment-triangle intersections, inverted tets */
-  IPC_Q_SCENE_COUNTERS = 9 /* int64[10] for the whole scene (env_id ignored), from the last Newton
+  IPC_Q_SCENE_COUNTERS = 9, /* int64[10] for the whole scene (env_id ignored), from the last Newton
                               iteration: contacts, point-triangle contacts, friction stencils,
                               stencil-node incidence entries, longest node incidence list,
                               candidates, BSR blocks, sliced-ELL padded blocks; then the PCG
                               cluster size in use (0 = tiled multi-launch PCG) and the most
                               32-row slices of one environment */
+  IPC_Q_ALL_STATUS = 10    /* int32[4 * n_env] for the whole scene (env_id ignored): env id,
+                              status, failure reason, next step of every environment, in one
+                              read-back (a serving loop polls this once per step) */
 } ipc_query_kind;
 
 /* Create / destroy a scene on desc->device. */

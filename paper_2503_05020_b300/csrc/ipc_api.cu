@@ -53,9 +53,10 @@ struct DBuf {
     p = nullptr;
     n = 0;
   }
-  void alloc(size_t m) {  // exact (re)allocation, contents undefined
-    release();
+  void alloc(size_t m) {  // at least m elements, contents undefined; reuses a capacity of m..2m+1024
     if (m == 0) m = 1;
+    if (p && m <= n && n <= 2 * m + 1024) return;
+    release();
     cudaError_t e = cudaMalloc(&p, m * sizeof(T));
     if (e != cudaSuccess) {
       p = nullptr;
@@ -121,7 +122,64 @@ struct HostEnv {
   long long stats[5] = {0, 0, 0, 0, 0};
   bool checked = false;  // initial intersection check done
   uint64_t est_bytes = 0;
+  // Hessian pattern in env-local numbering, built once (an env's pattern never changes), so that
+  // a relayout of the batch only concatenates: 3x3-block rows of every local node (body nodes
+  // have none), the tet-block contributions of each block in tet order, and the tet corners of
+  // each node.
+  bool have_pattern = false;
+  std::vector<int> bptr, bcol;      // CSR over local nodes (nsv_verts + 4 nbodies rows)
+  std::vector<int> blkptr, blksrc;  // per block: contributions 16 t + 4 a + b (local t)
+  std::vector<int> ntptr, ntsrc;    // per node: tet corners 4 t + a (local t)
 };
+
+// The env's Hessian pattern (see HostEnv): blocks of each row are the sorted distinct tet
+// neighbours; an isolated soft vertex keeps a diagonal (mass) block.
+void build_pattern(HostEnv& h) {
+  if (h.have_pattern) return;
+  const int nn = h.nsv_verts + 4 * h.nbodies, nt = h.ntets;
+  std::vector<std::vector<int>> adj(nn);
+  for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) adj[h.tet_nodes[4 * t + a]].push_back(h.tet_nodes[4 * t + b]);
+  h.bptr.assign(1, 0);
+  h.bcol.clear();
+  for (int i = 0; i < nn; ++i) {
+    auto& a = adj[i];
+    std::sort(a.begin(), a.end());
+    a.erase(std::unique(a.begin(), a.end()), a.end());
+    for (int j : a) h.bcol.push_back(j);
+    if (i < h.nsv_verts && a.empty()) h.bcol.push_back(i);
+    h.bptr.push_back((int)h.bcol.size());
+  }
+  const int nnzb = (int)h.bcol.size();
+  auto find_blk = [&](int r, int c) {
+    auto b = h.bcol.begin() + h.bptr[r], e = h.bcol.begin() + h.bptr[r + 1];
+    return (int)(std::lower_bound(b, e, c) - h.bcol.begin());
+  };
+  // counting sort of the contributions by block, tet order kept within a block
+  std::vector<int> blk(16 * (size_t)nt);
+  h.blkptr.assign(nnzb + 1, 0);
+  h.ntptr.assign(nn + 1, 0);
+  for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < 4; ++a) {
+      h.ntptr[h.tet_nodes[4 * t + a] + 1]++;
+      for (int b = 0; b < 4; ++b) {
+        int k = find_blk(h.tet_nodes[4 * t + a], h.tet_nodes[4 * t + b]);
+        blk[16 * t + 4 * a + b] = k;
+        h.blkptr[k + 1]++;
+      }
+    }
+  for (int k = 0; k < nnzb; ++k) h.blkptr[k + 1] += h.blkptr[k];
+  for (int i = 0; i < nn; ++i) h.ntptr[i + 1] += h.ntptr[i];
+  h.blksrc.assign(16 * (size_t)nt, 0);
+  std::vector<int> fill(h.blkptr.begin(), h.blkptr.end() - 1);
+  for (int src = 0; src < 16 * nt; ++src) h.blksrc[fill[blk[src]]++] = src;
+  h.ntsrc.assign(4 * (size_t)nt, 0);
+  std::vector<int> fillp(h.ntptr.begin(), h.ntptr.end() - 1);
+  for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < 4; ++a) h.ntsrc[fillp[h.tet_nodes[4 * t + a]]++] = 4 * t + a;
+  h.have_pattern = true;
+}
 
 uint64_t estimate_bytes(const HostEnv& h, int precision) {
   uint64_t nn = h.nsv_verts + 4 * h.nbodies;
@@ -736,60 +794,26 @@ struct ipc_scene {
     }
     NTILE = (int)te.size();
     h_tile_off = toff;
-    // BSR pattern of the soft nodes from the tets, gather lists for blocks and gradients
-    std::vector<std::vector<int>> adj(NN);
-    for (int t = 0; t < NT; ++t) {
-      int n4[4] = {tets_h[t].x, tets_h[t].y, tets_h[t].z, tets_h[t].w};
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) adj[n4[a]].push_back(n4[b]);
-    }
-    std::vector<int> bptr{0}, bcol, brow, bdiag(NN, -1);
-    for (int i = 0; i < NN; ++i) {
-      auto& a = adj[i];
-      std::sort(a.begin(), a.end());
-      a.erase(std::unique(a.begin(), a.end()), a.end());
-      for (int j : a) {
-        if (j == i) bdiag[i] = (int)bcol.size();
-        bcol.push_back(j);
-        brow.push_back(i);
+    // BSR pattern, block contributions and tet corners: each env's cached pattern, shifted
+    std::vector<int> bptr{0}, bcol, brow, blkptr{0}, blksrc, ntcnt{0}, ntsrc;
+    for (int li = 0; li < E; ++li) {
+      HostEnv& h = envs[ids[li]];
+      build_pattern(h);
+      const int n0 = node_off_h[li], t0 = tet_off_h[li], nn = node_off_h[li + 1] - n0;
+      const int b0 = (int)bcol.size(), c0 = blkptr.back(), q0 = ntcnt.back();
+      for (int i = 0; i < nn; ++i) {
+        for (int k = h.bptr[i]; k < h.bptr[i + 1]; ++k) {
+          bcol.push_back(n0 + h.bcol[k]);
+          brow.push_back(n0 + i);
+        }
+        bptr.push_back(b0 + h.bptr[i + 1]);
+        ntcnt.push_back(q0 + h.ntptr[i + 1]);
       }
-      if (node_body_h[i] < 0 && a.empty()) {  // isolated soft vertex: diagonal mass block only
-        bdiag[i] = (int)bcol.size();
-        bcol.push_back(i);
-        brow.push_back(i);
-      }
-      bptr.push_back((int)bcol.size());
+      for (size_t k = 1; k < h.blkptr.size(); ++k) blkptr.push_back(c0 + h.blkptr[k]);
+      for (int src : h.blksrc) blksrc.push_back(16 * t0 + src);
+      for (int src : h.ntsrc) ntsrc.push_back(4 * t0 + src);
     }
     NNZB = (int)bcol.size();
-    std::vector<int> bcnt(NNZB + 1, 0), ntcnt(NN + 1, 0);
-    auto find_blk = [&](int r, int c) {
-      auto b = bcol.begin() + bptr[r], e = bcol.begin() + bptr[r + 1];
-      return (int)(std::lower_bound(b, e, c) - bcol.begin());
-    };
-    std::vector<std::pair<int, int>> contrib;  // (block, src) in tet order
-    contrib.reserve((size_t)16 * NT);
-    for (int t = 0; t < NT; ++t) {
-      int n4[4] = {tets_h[t].x, tets_h[t].y, tets_h[t].z, tets_h[t].w};
-      for (int a = 0; a < 4; ++a) {
-        ntcnt[n4[a] + 1]++;
-        for (int b = 0; b < 4; ++b) contrib.push_back({find_blk(n4[a], n4[b]), 16 * t + 4 * a + b});
-      }
-    }
-    std::stable_sort(contrib.begin(), contrib.end(),
-                     [](const std::pair<int, int>& u, const std::pair<int, int>& w) { return u.first < w.first; });
-    std::vector<int> blkptr(NNZB + 1, 0), blksrc;
-    blksrc.reserve(contrib.size());
-    for (auto& c : contrib) {
-      blkptr[c.first + 1]++;
-      blksrc.push_back(c.second);
-    }
-    for (int k = 0; k < NNZB; ++k) blkptr[k + 1] += blkptr[k];
-    for (int i = 0; i < NN; ++i) ntcnt[i + 1] += ntcnt[i];
-    std::vector<int> ntsrc(4 * (size_t)NT), fillp(ntcnt.begin(), ntcnt.end() - 1);
-    for (int t = 0; t < NT; ++t) {
-      int n4[4] = {tets_h[t].x, tets_h[t].y, tets_h[t].z, tets_h[t].w};
-      for (int a = 0; a < 4; ++a) ntsrc[fillp[n4[a]]++] = 4 * t + a;
-    }
     // sliced ELL of the soft rows: 32-row slices inside each soft tile, padded to the slice's
     // longest row; block kk, element e of lane l at vbase + (kk*9 + e)*32 + l
     std::vector<int> tslice(te.size(), -1), sw, row_sel(NN, -1);
@@ -1828,6 +1852,21 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
   if (!s) fail_with(IPC_ERR_ARG, "null scene");
   CK(cudaSetDevice(s->device));
   s->commit();
+  if (kind == IPC_Q_ALL_STATUS) {
+    const int E = s->E;
+    std::vector<int> st(E), rs(E), sp(E), v(4 * (size_t)E);
+    CK(cudaMemcpyAsync(st.data(), s->e_status.p, E * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(rs.data(), s->e_reason.p, E * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(sp.data(), s->e_step.p, E * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int li = 0; li < E; ++li) {
+      v[4 * li] = s->ids[li];
+      v[4 * li + 1] = st[li];
+      v[4 * li + 2] = rs[li];
+      v[4 * li + 3] = sp[li];
+    }
+    return copy_out(v.data(), v.size() * 4, out, out_bytes, written);
+  }
   int li = s->layout_index(env_id);
   HostEnv& h = s->envs[env_id];
   size_t o = 3 * (size_t)s->h_node_off[li];

@@ -17,11 +17,12 @@ HEADER = os.path.join(HERE, "..", "include", "ipc.h")
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_BUDGET", 4: "ERR_CUDA", 5: "ERR_INIT_INTERSECT",
                 6: "ERR_INIT_INVERTED", 7: "ERR_NO_ENV", 8: "ERR_INTERNAL"}
+STATUS_CODES = {v: k for k, v in STATUS_NAMES.items()}
 ENV_STATUS = {0: "ACTIVE", 1: "DONE", 2: "FAILED"}
 FAIL_REASON = {0: "none", 1: "newton_cap", 2: "line_search", 3: "non_finite", 4: "initial_intersection", 5: "internal"}
 FP64, MIXED = 0, 1
 Q_DOFS, Q_VELOCITIES, Q_STATUS, Q_STATS, Q_CANDIDATES, Q_CONTACTS, Q_POINTS, Q_SIZES, Q_INTERSECTIONS, \
-    Q_SCENE_COUNTERS = range(10)
+    Q_SCENE_COUNTERS, Q_ALL_STATUS = range(11)
 
 
 class IpcError(RuntimeError):
@@ -228,6 +229,11 @@ class Scene:
         keys = ["contacts", "pt_contacts", "friction", "incidence_entries", "longest_list", "candidates",
                 "bsr_blocks", "sell_blocks", "pcg_cluster", "max_env_slices"]
         return dict(zip(keys, map(int, v)))
+
+    def all_status(self) -> dict:
+        """{env id: (status, reason, next step)} for every environment, in one read-back."""
+        v = self._query(-1, Q_ALL_STATUS, np.int32, 4)
+        return {int(r[0]): (ENV_STATUS[int(r[1])], FAIL_REASON.get(int(r[2]), int(r[2])), int(r[3])) for r in v}
 
     def invariants(self, eid: int) -> dict:
         v = self._query(eid, Q_INTERSECTIONS, np.int64)

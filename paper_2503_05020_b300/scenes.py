@@ -288,7 +288,8 @@ def cube_squeeze_env(env_id: int = 0, base_seed: int = BASE_SEED, n_steps: int =
         gravity[s] = 1 if s >= close_steps else 0
     soft = dict(verts=verts, tets=tets, tris=tris, E=E, nu=nu, rho=rho,
                 kin=np.zeros(len(verts), dtype=np.uint8))
-    return dict(soft=[soft], affine=[pl, pr], mu=mu, gravity=gravity, targets=targets)
+    lift = lift_speed * dt * max(n_steps - close_steps, 0)
+    return dict(soft=[soft], affine=[pl, pr], mu=mu, gravity=gravity, targets=targets, object=("soft", 0), lift=lift)
 
 
 def finger_pad(rng: SplitMix64, side: int, inner_x: float, E: float, nu: float,
@@ -368,7 +369,42 @@ def pad_grasp_env(env_id: int = 0, base_seed: int = BASE_SEED, n_steps: int = 30
         targets[s, 1] = _translation_q((dx, 0, dz))
         targets[s, 2] = IDENTITY_Q
         gravity[s] = 1 if s >= close_steps else 0
-    return dict(soft=[pad_r, pad_l], affine=[obj], mu=mu, gravity=gravity, targets=targets)
+    return dict(soft=[pad_r, pad_l], affine=[obj], mu=mu, gravity=gravity, targets=targets,
+                object=("affine", 0), lift=lift)
+
+
+def _rot_x(deg: float) -> np.ndarray:
+    a = math.radians(deg)
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[1.0, 0.0, 0.0], [0.0, c, -s], [0.0, s, c]])
+
+
+def grasp_request_env(req_id: int, base_seed: int = BASE_SEED + 7919, close_steps: int = 80, lift_steps: int = 60,
+                      shake_steps: int = 60, shake_deg: float = 15.0, shake_hz: float = 2.0, dt: float = 0.005,
+                      lift: float = 0.1, pad_cells=(6, 8, 18), object_points: int = 200) -> dict:
+    """A grasp-evaluation request: the pad grasp of one seeded object (uneven hull sizes), closed
+    in `close_steps`, lifted by `lift` in `lift_steps`, then shaken about the grasp (x) axis through
+    the lifted object centre by shake_deg * sin(2 pi shake_hz t) for `shake_steps`."""
+    n_cl = close_steps + lift_steps
+    env = pad_grasp_env(req_id, base_seed=base_seed, n_steps=n_cl, close_steps=close_steps, dt=dt, lift=lift,
+                        pad_cells=pad_cells, object_points=object_points)
+    last = env["targets"][-1]
+    c = np.array([0.0, 0.0, lift])
+    frames = []
+    for k in range(1, shake_steps + 1):
+        R = _rot_x(shake_deg * math.sin(2.0 * math.pi * shake_hz * k * dt))
+        fr = last.copy()
+        for b in range(2):  # the two pads: x = R (X0 + t - c) + c
+            t = last[b, :3]
+            q = np.zeros(12)
+            q[:3] = R @ (t - c) + c
+            q[3:6], q[6:9], q[9:12] = R[:, 0], R[:, 1], R[:, 2]
+            fr[b] = q
+        frames.append(fr)
+    if frames:
+        env["targets"] = np.concatenate([env["targets"], np.array(frames)], axis=0)
+        env["gravity"] = np.concatenate([env["gravity"], np.ones(shake_steps, dtype=np.uint8)])
+    return env
 
 
 def initial_dofs(env: dict) -> np.ndarray:

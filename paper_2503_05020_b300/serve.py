@@ -1,0 +1,187 @@
+"""Serving form: grasp-evaluation requests stepped by continuous batching on one GPU.
+
+A request is one environment with its whole schedule (Sec. III-D's evaluation protocol: close,
+lift, optionally shake) and an arrival time. The server keeps one device-resident scene. At step
+boundaries it admits requests that have arrived, in arrival order, while the scene's HBM budget
+(checked by the library on ipc_env_add from each environment's estimated bytes) and the slot cap
+allow; admitted environments join the running batch and advance one time step per batch step
+alongside the others (Sec. III-A: every environment keeps its own state, step size, stopping
+test and failure). A finished environment (DONE or FAILED) is read back at once; it leaves the
+scene at the next admission round, so one relayout of the batch serves both its departure and
+new arrivals. Relayouts are spaced at least `admit_period` batch steps apart while environments
+are running.
+
+Latency of a request = time its result was read back - its arrival time; the report gives p50
+and p99 over requests, throughput in requests/s and environment-steps/s, and per-request queue
+wait. The loop itself is thin host code over the C ABI: every step of the simulation runs in the
+library's kernels.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import ipc
+
+
+@dataclass
+class Request:
+    rid: int
+    env: dict
+    arrival: float  # seconds after the start of the run
+    # filled in by the server
+    admitted: float | None = None
+    finished: float | None = None
+    status: str | None = None
+    reason: str | None = None
+    steps: int = 0
+    result: dict = field(default_factory=dict)
+
+    @property
+    def latency(self) -> float | None:
+        return None if self.finished is None else self.finished - self.arrival
+
+
+def poisson_arrivals(rate: float, n: int, seed: int) -> list[float]:
+    """n arrival times of a Poisson process of the given rate (1/s), from a SplitMix64 stream."""
+    from .scenes import SplitMix64
+
+    rng = SplitMix64(seed)
+    t, out = 0.0, []
+    for _ in range(n):
+        u = rng.uniform(0.0, 1.0)
+        t += -math.log(max(1.0 - u, 1e-300)) / rate
+        out.append(t)
+    return out
+
+
+def percentile(values, q: float) -> float | None:
+    v = sorted(values)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))  # nearest rank
+    return v[k]
+
+
+def object_points(env: dict) -> slice | None:
+    """Rows of the grasped object (env["object"] = ("soft" | "affine", index)) in the point list:
+    soft bodies' vertices first, then each affine body's vertices."""
+    if "object" not in env:
+        return None
+    kind, idx = env["object"]
+    if kind == "soft":
+        o = sum(len(s["verts"]) for s in env["soft"][:idx])
+        return slice(o, o + len(env["soft"][idx]["verts"]))
+    o = sum(len(s["verts"]) for s in env["soft"]) + sum(len(a["verts"]) for a in env["affine"][:idx])
+    return slice(o, o + len(env["affine"][idx]["verts"]))
+
+
+def initial_points(env: dict) -> np.ndarray:
+    """World positions of every point at the env's initial state: soft vertices, then each
+    affine body's rest vertices mapped by its q0 (x = p + A X, A's columns q0[3:6], [6:9], [9:12])."""
+    parts = [np.asarray(s["verts"], dtype=np.float64) for s in env["soft"]]
+    for a in env["affine"]:
+        q = np.asarray(a["q0"], dtype=np.float64)
+        A = np.stack([q[3:6], q[6:9], q[9:12]], axis=1)
+        parts.append(q[:3] + np.asarray(a["verts"], dtype=np.float64) @ A.T)
+    return np.concatenate(parts, axis=0)
+
+
+def object_result(env: dict, points: np.ndarray, points0: np.ndarray) -> dict:
+    """Grasp outcome: mean displacement of the grasped object's points and whether it rose by
+    more than half the schedule's lift."""
+    sl = object_points(env)
+    if sl is None or points0 is None:
+        return {}
+    disp = (points[sl] - points0[sl]).mean(axis=0)
+    lift = float(env.get("lift", 0.0))
+    return {"object_disp": disp.tolist(), "held": bool(lift > 0 and disp[2] > 0.5 * lift)}
+
+
+class GraspServer:
+    def __init__(self, params: dict, precision: int = ipc.FP64, hbm_budget_bytes: int = 0, max_envs: int = 64,
+                 admit_period: int = 8, device: int = 0, scene=None, clock=None, sleep=None):
+        self.scene = scene if scene is not None else ipc.Scene(params, precision=precision, device=device,
+                                                             hbm_budget_bytes=hbm_budget_bytes)
+        self.max_envs = max_envs
+        self.admit_period = max(1, admit_period)
+        self.clock = clock or time.perf_counter
+        self.sleep = sleep or time.sleep
+        self.batch_steps = 0
+        self.env_steps = 0
+        self.relayouts = 0
+        self.max_active = 0
+
+    def run(self, requests: list[Request]) -> dict:
+        sc = self.scene
+        pending = deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        active: dict[int, Request] = {}  # env id -> request, still stepping
+        done_in_scene: list[int] = []  # finished env ids not yet removed
+        start_pts: dict[int, np.ndarray] = {}
+        t0 = self.clock()
+        since_relayout = self.admit_period
+        while pending or active:
+            now = self.clock() - t0
+            arrived = bool(pending) and pending[0].arrival <= now
+            if (not active) or (since_relayout >= self.admit_period and (arrived or done_in_scene)):
+                changed = False
+                for eid in done_in_scene:
+                    sc.remove_env(eid)
+                    changed = True
+                done_in_scene.clear()
+                while pending and pending[0].arrival <= now and len(active) < self.max_envs:
+                    req = pending[0]
+                    try:
+                        eid = sc.add_env(req.env)
+                    except ipc.IpcError as e:
+                        if e.status == ipc.STATUS_CODES["ERR_BUDGET"] and active:
+                            break  # waits for memory to free up
+                        pending.popleft()
+                        req.status, req.reason, req.finished = "REJECTED", str(e), now
+                        continue
+                    pending.popleft()
+                    req.admitted = now
+                    active[eid] = req
+                    # host-side (no relayout per admission); only what the grasp outcome needs
+                    start_pts[eid] = initial_points(req.env) if "object" in req.env else None
+                    changed = True
+                if changed:
+                    self.relayouts += 1
+                    since_relayout = 0
+            if not active:
+                if pending:
+                    self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
+                continue
+            self.max_active = max(self.max_active, len(active))
+            sc.step(1)
+            self.batch_steps += 1
+            since_relayout += 1
+            self.env_steps += len(active)
+            status = sc.all_status()
+            t_now = self.clock() - t0
+            for eid in list(active):
+                st, reason, step = status[eid]
+                if st in ("DONE", "FAILED"):
+                    req = active.pop(eid)
+                    req.finished, req.status, req.reason, req.steps = t_now, st, reason, step
+                    pts = sc.points(eid)
+                    req.result = {"dofs": sc.dofs(eid), "points": pts, **object_result(req.env, pts, start_pts.pop(eid))}
+                    done_in_scene.append(eid)
+        for eid in done_in_scene:
+            sc.remove_env(eid)
+        wall = self.clock() - t0
+        lat = [r.latency for r in requests if r.status in ("DONE", "FAILED")]
+        wait = [r.admitted - r.arrival for r in requests if r.admitted is not None]
+        return {"requests": len(requests), "completed": sum(r.status == "DONE" for r in requests),
+                "failed": sum(r.status == "FAILED" for r in requests),
+                "rejected": sum(r.status == "REJECTED" for r in requests), "wall_s": wall,
+                "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
+                "mean_latency_s": float(np.mean(lat)) if lat else None,
+                "p50_wait_s": percentile(wait, 50), "p99_wait_s": percentile(wait, 99),
+                "throughput_req_s": len(lat) / wall if wall > 0 else None,
+                "env_steps_s": self.env_steps / wall if wall > 0 else None, "batch_steps": self.batch_steps,
+                "relayouts": self.relayouts, "max_active": self.max_active}

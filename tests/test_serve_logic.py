@@ -1,0 +1,119 @@
+"""Host logic of the serving loop (no GPU): a fake scene with the library's admission contract
+(ipc_env_add fails with ERR_BUDGET when the scene's HBM budget is exhausted) and a simulated
+clock. Checks arrival-order admission, continuous batching (a request joins while others run),
+budget waits, rejection of a request that can never fit, relayout spacing, and latency
+accounting."""
+import math
+
+import numpy as np
+
+from paper_2503_05020_b300 import ipc
+from paper_2503_05020_b300.serve import GraspServer, Request, percentile, poisson_arrivals
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 0.0)
+
+
+class FakeScene:
+    """Each env finishes after env["steps"] batch steps; a batch step costs 0.1 s of fake time."""
+
+    def __init__(self, clock, budget=math.inf):
+        self.clock, self.budget, self.used = clock, budget, 0.0
+        self.envs, self.next_id, self.log = {}, 0, []
+
+    def add_env(self, env):
+        if env["bytes"] > self.budget:
+            raise ipc.IpcError(ipc.STATUS_CODES["ERR_BUDGET"], "larger than the budget")
+        if self.used + env["bytes"] > self.budget:
+            raise ipc.IpcError(ipc.STATUS_CODES["ERR_BUDGET"], "budget")
+        eid = self.next_id
+        self.next_id += 1
+        self.used += env["bytes"]
+        self.envs[eid] = {"env": env, "step": 0}
+        self.log.append(("add", env["name"], self.clock()))
+        return eid
+
+    def remove_env(self, eid):
+        self.used -= self.envs[eid]["env"]["bytes"]
+        self.log.append(("remove", self.envs[eid]["env"]["name"], self.clock()))
+        del self.envs[eid]
+
+    def step(self, n=1):
+        for e in self.envs.values():
+            if e["step"] < e["env"]["steps"]:
+                e["step"] += 1
+        self.clock.t += 0.1
+
+    def all_status(self):
+        return {k: ("DONE" if e["step"] >= e["env"]["steps"] else "ACTIVE", "none", e["step"])
+                for k, e in self.envs.items()}
+
+    def points(self, eid):
+        return np.full((1, 3), float(self.envs[eid]["step"]))
+
+    def dofs(self, eid):
+        return np.full(3, float(self.envs[eid]["step"]))
+
+
+def env(name, steps, nbytes=1.0):
+    return {"name": name, "steps": steps, "bytes": nbytes, "soft": [], "affine": []}
+
+
+def serve(reqs, budget=math.inf, max_envs=64, admit_period=1):
+    clk = FakeClock()
+    sc = FakeScene(clk, budget)
+    srv = GraspServer({}, scene=sc, clock=clk, sleep=clk.sleep, max_envs=max_envs, admit_period=admit_period)
+    return srv, sc, srv.run(reqs)
+
+
+def test_continuous_batching_joins_running_batch_and_accounts_latency():
+    reqs = [Request(0, env("a", 10), 0.0), Request(1, env("b", 5), 0.35), Request(2, env("c", 3), 5.0)]
+    srv, sc, rep = serve(reqs)
+    assert rep["completed"] == 3 and rep["rejected"] == 0
+    a, b, c = reqs
+    assert b.admitted < a.finished  # b joined while a was running
+    assert abs(a.latency - 1.0) < 1e-9  # 10 steps of 0.1 s from t = 0
+    assert b.steps == 5 and abs(b.finished - (b.admitted + 0.5)) < 0.11
+    assert c.admitted >= 5.0  # the idle server waits for the late arrival
+    assert rep["max_active"] == 2
+    assert rep["p50_latency_s"] == percentile([r.latency for r in reqs], 50)
+
+
+def test_budget_admits_in_arrival_order_and_waits_for_memory():
+    reqs = [Request(i, env(f"r{i}", 4, nbytes=1.0), 0.0) for i in range(4)]
+    big = Request(9, env("big", 4, nbytes=5.0), 0.0)
+    srv, sc, rep = serve(reqs + [big], budget=2.0)
+    assert rep["completed"] == 4 and rep["rejected"] == 1 and big.status == "REJECTED"
+    assert rep["max_active"] == 2
+    adds = [name for kind, name, _ in sc.log if kind == "add"]
+    assert adds == ["r0", "r1", "r2", "r3"]
+    assert reqs[2].admitted >= reqs[0].finished  # waited for a slot of memory
+
+
+def test_relayouts_are_spaced_by_the_admission_period():
+    reqs = [Request(i, env(f"r{i}", 20), 0.1 * i) for i in range(10)]
+    srv, sc, rep = serve(reqs, admit_period=8)
+    assert rep["completed"] == 10
+    adds = sorted(t for kind, _, t in sc.log if kind == "add")
+    rounds = sorted(set(round(t, 6) for t in adds))
+    assert all(b - a >= 0.8 - 1e-9 for a, b in zip(rounds, rounds[1:]))  # >= 8 steps of 0.1 s apart
+    assert rep["relayouts"] >= len(rounds)  # every admission round relayouts the batch once
+
+
+def test_percentile_nearest_rank_and_poisson_arrivals():
+    v = list(range(1, 101))
+    assert percentile(v, 50) == 50 and percentile(v, 99) == 99 and percentile(v, 100) == 100
+    assert percentile([], 50) is None
+    t = poisson_arrivals(20.0, 4000, 7)
+    assert all(b > a for a, b in zip(t, t[1:]))
+    gaps = np.diff([0.0] + t)
+    assert abs(gaps.mean() - 1 / 20.0) < 0.1 / 20.0
+    assert abs(gaps.std() - 1 / 20.0) < 0.15 / 20.0  # exponential gaps: std = mean
