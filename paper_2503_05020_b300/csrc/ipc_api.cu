@@ -470,6 +470,7 @@ struct ipc_scene {
   // candidates / contacts
   DBuf<int> cnt_pt, off_pt, cnt_ee, off_ee, cand_j, nflag, noff, scan_tmp, overflow;
   DBuf<int> ccd_cnt_pt, ccd_off_pt, ccd_cnt_ee, ccd_off_ee, ccd_j;  // swept-box candidates
+  DBuf<int> slots_pt, slots_ee;  // partner slots of collect traversals (CAND_CAP per query)
   DBuf<ContactRec> ct_tmp, ct;
   DBuf<FrictionRec> fr;
   int n_pt = 0, n_ee = 0, n_ct = 0, n_ct_pt = 0, n_fr = 0, n_fr_pt = 0, n_inc = 0;
@@ -1019,7 +1020,7 @@ struct ipc_scene {
     off_pt.alloc(NSV + 1);
     cnt_ee.alloc(NED + 1);
     off_ee.alloc(NED + 1);
-    overflow.alloc(1);
+    overflow.alloc(2);
     overflow.zero(s);
     ns_ptr.alloc(NN + 1);
     ns_cnt.alloc(NN + 1);
@@ -1088,37 +1089,57 @@ struct ipc_scene {
     tree_refit(ttri);
     tree_refit(tedge);
   }
-  void check_overflow() {
-    if (read_int(overflow.p)) {
-      overflow.zero(stream);
-      fail_with(IPC_ERR_INTERNAL, "BVH traversal stack overflow");
-    }
+  void check_overflow() { collect_spilled(); }
+  // reads and clears the traversal flags; fails on a stack overflow, returns whether a collect
+  // traversal had a query with more partners than its slots
+  bool collect_spilled() {
+    CK(cudaMemcpyAsync(hpin, overflow.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    const int stack = hpin[0], spill = hpin[1];
+    if (stack || spill) overflow.zero(stream);
+    if (stack) fail_with(IPC_ERR_INTERNAL, "BVH traversal stack overflow");
+    return spill != 0;
   }
+  static constexpr int CAND_CAP = 64;  // partner slots per query of a collect traversal
 
   // ------------------------------------------------------------------ constraint set
   // contacts (d < dhat) of the envs in act at positions ptx (already computed)
   void constraint_set(const uint8_t* act) {
     double r = 0.5 * desc.dhat;
     boxes_and_refit(nullptr, r);
-    CandOut o{cnt_pt.p, nullptr, nullptr, overflow.p};
+    // one traversal per query kind keeps up to CAND_CAP partners per query (edge-edge queries
+    // on fine surfaces find a few dozen non-adjacent neighbours); a fill traversal
+    // runs only if some query found more
+    slots_pt.ensure((size_t)NSV * CAND_CAP + 1);
+    slots_ee.ensure((size_t)NED * CAND_CAP + 1);
+    CandOut o{cnt_pt.p, nullptr, slots_pt.p, overflow.p, CAND_CAP};
     pbeg(IPC_PROF_BROAD);
-    launch(k_trav_pt<TRAV_COUNT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
-           (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), o, (const double*)nullptr, ctl());
-    CandOut oe{cnt_ee.p, nullptr, nullptr, overflow.p};
-    launch(k_trav_ee<TRAV_COUNT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+    launch(k_trav_pt<TRAV_COLLECT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
+           (const double*)ptx.p, (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), o,
+           (const double*)nullptr, ctl());
+    CandOut oe{cnt_ee.p, nullptr, slots_ee.p, overflow.p, CAND_CAP};
+    launch(k_trav_ee<TRAV_COLLECT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
            (const double*)tedge.pbox.p, tree(tedge), ptinfo(), oe, (const double*)nullptr, (const double*)nullptr, ctl());
     pend(IPC_PROF_BROAD);
     n_pt = scan(cnt_pt.p, NSV, off_pt.p);
     n_ee = scan(cnt_ee.p, NED, off_ee.p);
-    check_overflow();
+    const bool spilled = collect_spilled();
     int nc = n_pt + n_ee;
     cand_j.ensure(nc + 1);
-    CandOut f{nullptr, off_pt.p, cand_j.p, overflow.p};
-    launch(k_trav_pt<TRAV_FILL>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
-           (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), f, (const double*)nullptr, ctl());
-    CandOut fe{nullptr, off_ee.p, cand_j.p + n_pt, overflow.p};
-    launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
-           (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr, ctl());
+    if (spilled) {
+      CandOut f{nullptr, off_pt.p, cand_j.p, overflow.p};
+      launch(k_trav_pt<TRAV_FILL>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
+             (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), f, (const double*)nullptr, ctl());
+      CandOut fe{nullptr, off_ee.p, cand_j.p + n_pt, overflow.p};
+      launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+             (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr,
+             ctl());
+    } else {
+      launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)cnt_pt.p, (const int*)slots_pt.p,
+             (const int*)off_pt.p, cand_j.p, 1);
+      launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)cnt_ee.p, (const int*)slots_ee.p,
+             (const int*)off_ee.p, cand_j.p + n_pt, 1);
+    }
     nflag.ensure(nc + 1);
     noff.ensure(nc + 1);
     ct_tmp.ensure(nc + 1);
@@ -1512,23 +1533,35 @@ struct ipc_scene {
     ccd_off_pt.ensure(NSV + 1);
     ccd_cnt_ee.ensure(NED + 1);
     ccd_off_ee.ensure(NED + 1);
-    CandOut cp{ccd_cnt_pt.p, nullptr, nullptr, overflow.p};
-    launch(k_trav_pt<TRAV_COUNT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
-           (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), cp, (const double*)nullptr, C);
-    CandOut ce{ccd_cnt_ee.p, nullptr, nullptr, overflow.p};
-    launch(k_trav_ee<TRAV_COUNT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+    slots_pt.ensure((size_t)NSV * CAND_CAP + 1);
+    slots_ee.ensure((size_t)NED * CAND_CAP + 1);
+    CandOut cp{ccd_cnt_pt.p, nullptr, slots_pt.p, overflow.p, CAND_CAP};
+    launch(k_trav_pt<TRAV_COLLECT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
+           (const double*)ptx.p, (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), cp,
+           (const double*)nullptr, C);
+    CandOut ce{ccd_cnt_ee.p, nullptr, slots_ee.p, overflow.p, CAND_CAP};
+    launch(k_trav_ee<TRAV_COLLECT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
            (const double*)tedge.pbox.p, tree(tedge), ptinfo(), ce, (const double*)nullptr, (const double*)nullptr, C);
     int np = scan(ccd_cnt_pt.p, NSV, ccd_off_pt.p);
     int ne = scan(ccd_cnt_ee.p, NED, ccd_off_ee.p);
-    check_overflow();
+    const bool spilled = collect_spilled();
     if (np + ne == 0) return;
     ccd_j.ensure(np + ne + 1);
-    CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p};
-    launch(k_trav_pt<TRAV_FILLU>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
-           (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp, (const double*)nullptr, C);
-    CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p};
-    launch(k_trav_ee<TRAV_FILLU>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
-           (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr, C);
+    if (spilled) {
+      CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p};
+      launch(k_trav_pt<TRAV_FILLU>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
+             (const double*)ptx.p, (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
+             (const double*)nullptr, C);
+      CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p};
+      launch(k_trav_ee<TRAV_FILLU>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+             (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr,
+             C);
+    } else {
+      launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)ccd_cnt_pt.p, (const int*)slots_pt.p,
+             (const int*)ccd_off_pt.p, ccd_j.p, 0);
+      launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)ccd_cnt_ee.p, (const int*)slots_ee.p,
+             (const int*)ccd_off_ee.p, ccd_j.p + np, 0);
+    }
     launch(k_accd_pairs, np + ne, 128, np, ne, (const int*)ccd_off_pt.p, NSV, (const int*)ccd_off_ee.p, NED,
            (const int*)ccd_j.p, (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p,
            (const int*)ed_env.p, (const double*)ptx.p, (const double*)ptp.p, C);

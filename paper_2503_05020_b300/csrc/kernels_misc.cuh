@@ -336,14 +336,17 @@ DEV bool excluded(const PtInfo& P, int a, int b, int c, int d) {
   return ba >= 0 && P.body[b] == ba && P.body[c] == ba && P.body[d] == ba;
 }
 
-// count, fill (partners sorted per query), swept-box ACCD inline, fill unsorted
-enum { TRAV_COUNT = 0, TRAV_FILL = 1, TRAV_CCD = 2, TRAV_FILLU = 3 };
+// count, fill (partners sorted per query), swept-box ACCD inline, fill unsorted, and collect:
+// count while keeping the first `cap` partners of each query in its own slots (one traversal
+// instead of count + fill when no query finds more than cap)
+enum { TRAV_COUNT = 0, TRAV_FILL = 1, TRAV_CCD = 2, TRAV_FILLU = 3, TRAV_COLLECT = 4 };
 
 struct CandOut {
-  int* cnt;        // per query (count mode)
+  int* cnt;        // per query (count and collect modes)
   const int* off;  // per query (fill mode)
-  int* cj;         // candidate partner (fill mode)
-  int* overflow;
+  int* cj;         // candidate partner (fill mode), or cap slots per query (collect mode)
+  int* overflow;   // [0]: traversal stack overflow, [1]: a query found more than cap (collect)
+  int cap = 0;
 };
 
 // point-triangle candidates: surface vertex q against the triangle tree of its env
@@ -356,7 +359,7 @@ __global__ void k_trav_pt(int n_sv, const int* __restrict__ sv_pt, const int* __
   if (q >= n_sv) return;
   int e = sv_env[q];
   if (!act[e]) {
-    if (MODE == TRAV_COUNT) O.cnt[q] = 0;
+    if (MODE == TRAV_COUNT || MODE == TRAV_COLLECT) O.cnt[q] = 0;
     return;
   }
   int v = sv_pt[q];
@@ -380,6 +383,7 @@ __global__ void k_trav_pt(int n_sv, const int* __restrict__ sv_pt, const int* __
     if (a == v || b == v || c == v) return;
     if (excluded(P, v, a, b, c)) return;
     if (MODE == TRAV_FILL || MODE == TRAV_FILLU) O.cj[base + count] = j;
+    if (MODE == TRAV_COLLECT && count < O.cap) O.cj[(long)q * O.cap + count] = j;
     if (MODE == TRAV_CCD) {
       d3 X[4] = {ld3(ptx, v), ld3(ptx, a), ld3(ptx, b), ld3(ptx, c)};
       d3 Pd[4] = {ld3(ptp, v), ld3(ptp, a), ld3(ptp, b), ld3(ptp, c)};
@@ -391,7 +395,8 @@ __global__ void k_trav_pt(int n_sv, const int* __restrict__ sv_pt, const int* __
     ++count;
   });
   if (!ok) atomicOr(O.overflow, 1);
-  if (MODE == TRAV_COUNT) O.cnt[q] = count;
+  if (MODE == TRAV_COUNT || MODE == TRAV_COLLECT) O.cnt[q] = count;
+  if (MODE == TRAV_COLLECT && count > O.cap) atomicOr(O.overflow + 1, 1);
   if (MODE == TRAV_FILL) {
     // sort this query's partners ascending (insertion sort; short lists)
     int* s = O.cj + base;
@@ -419,7 +424,7 @@ __global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __
   if (q >= n_ed) return;
   int e = ed_env[q];
   if (!act[e]) {
-    if (MODE == TRAV_COUNT) O.cnt[q] = 0;
+    if (MODE == TRAV_COUNT || MODE == TRAV_COLLECT) O.cnt[q] = 0;
     return;
   }
   int a0 = ed_pt[2 * q], a1 = ed_pt[2 * q + 1];
@@ -433,6 +438,7 @@ __global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __
     if (a0 == b0 || a0 == b1 || a1 == b0 || a1 == b1) return;
     if (excluded(P, a0, a1, b0, b1)) return;
     if (MODE == TRAV_FILL || MODE == TRAV_FILLU) O.cj[base + count] = j;
+    if (MODE == TRAV_COLLECT && count < O.cap) O.cj[(long)q * O.cap + count] = j;
     if (MODE == TRAV_CCD) {
       d3 X[4] = {ld3(ptx, a0), ld3(ptx, a1), ld3(ptx, b0), ld3(ptx, b1)};
       d3 Pd[4] = {ld3(ptp, a0), ld3(ptp, a1), ld3(ptp, b0), ld3(ptp, b1)};
@@ -444,7 +450,8 @@ __global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __
     ++count;
   });
   if (!ok) atomicOr(O.overflow, 1);
-  if (MODE == TRAV_COUNT) O.cnt[q] = count;
+  if (MODE == TRAV_COUNT || MODE == TRAV_COLLECT) O.cnt[q] = count;
+  if (MODE == TRAV_COLLECT && count > O.cap) atomicOr(O.overflow + 1, 1);
   if (MODE == TRAV_FILL) {
     int* s = O.cj + base;
     for (int i = 1; i < count; ++i) {
@@ -512,6 +519,28 @@ __global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ off_pt, int
   c.type = type;
   tmp[i] = c;
   flag[i] = d2 < dhat2 ? 1 : 0;
+}
+
+// Candidates of a collect traversal to their final places: query q's partners (at most cap,
+// in its slots) go to out[off[q] ...], sorted ascending when `sorted` (the fill mode's order).
+__global__ void k_gather_cands(int nq, int cap, const int* __restrict__ cnt, const int* __restrict__ slots,
+                               const int* __restrict__ off, int* __restrict__ out, int sorted) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int n = cnt[q];
+  if (n == 0) return;
+  int* o = out + off[q];
+  const int* sl = slots + (long)q * cap;
+  for (int i = 0; i < n; ++i) o[i] = sl[i];
+  if (!sorted) return;
+  for (int i = 1; i < n; ++i) {
+    int key = o[i], k = i - 1;
+    while (k >= 0 && o[k] > key) {
+      o[k + 1] = o[k];
+      --k;
+    }
+    o[k + 1] = key;
+  }
 }
 
 // Additive CCD of every swept candidate pair (point-triangle pairs first, then edge-edge), one
