@@ -453,6 +453,8 @@ struct ipc_scene {
   DBuf<int> pcg_it, pcg_active;
   DBuf<double> pcg_part;  // per-slot partial sums of the persistent PCG
   DBuf<double> pcg_rzs, pcg_bbs, pcg_iterb, pcg_iterf;  // per-env state of the persistent PCG
+  DBuf<unsigned long long> pcg_tune_iters;                 // env-iterations of a timed launch
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
   DBuf<int> pcg_its, env_iota, env_list;
   DBuf<uint8_t> pcg_runs;
   DBuf<uint8_t> pcg_run;
@@ -549,6 +551,8 @@ struct ipc_scene {
         cudaEventDestroy(pr.second);
       }
     for (auto e : ev_pool) cudaEventDestroy(e);
+    for (auto e : tune_ev)
+      if (e) cudaEventDestroy(e);
     if (hpin) cudaFreeHost(hpin);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
@@ -929,6 +933,7 @@ struct ipc_scene {
     tile_end.upload(tn, s);
     tile_off.upload(toff, s);
     pcg_C = 0;
+    tune_reset();  // a new batch composition is tuned afresh
     if (desc.pcg_cluster >= 0 || mixed()) {
       std::vector<int> iota(E);
       std::iota(iota.begin(), iota.end(), 0);
@@ -1322,6 +1327,50 @@ struct ipc_scene {
     }
     return 1;
   }
+  // Launch-shape autotuner of the persistent PCG. The running-env count of a launch falls in one
+  // of three buckets (more than fit resident with 8-CTA clusters; more than fit with 16; fewer).
+  // A bucket's candidates are the largest all-resident cluster size h (pick_cluster) and 2h,
+  // which oversubscribes the GPU but gives each env more SMs; they are tried alternately on the
+  // bucket's first launches, timed with CUDA events per env-iteration, and the faster is kept.
+  // The cluster size changes no bit of any result, so tuning never changes a trajectory.
+  struct TuneBucket {
+    int cand[2] = {0, 0};
+    double ms[2] = {0.0, 0.0};
+    unsigned long long its[2] = {0, 0};
+    int tries[2] = {0, 0};
+    int best = -1;
+  };
+  static constexpr int TUNE_TRIES = 2;
+  TuneBucket tune[3];
+  void tune_reset() {
+    for (auto& b : tune) b = TuneBucket();
+  }
+  int bucket_of(int n) const { return n > pcg_resident[3] ? 0 : (n > pcg_resident[4] ? 1 : 2); }
+  // cluster size for the next launch over n running envs, and the candidate slot being timed (-1)
+  int tuned_cluster(int n, int* slot) {
+    *slot = -1;
+    int h = pick_cluster(n);
+    if (desc.pcg_cluster > 0) return h;
+    TuneBucket& b = tune[bucket_of(n)];
+    if (b.cand[0] == 0) {
+      b.cand[0] = h;
+      int h2 = 2 * h, k2 = h2 == 2 ? 1 : h2 == 4 ? 2 : h2 == 8 ? 3 : h2 == 16 ? 4 : -1;
+      b.cand[1] = (k2 > 0 && pcg_resident[k2] > 0 && 2 * h2 <= std::max(max_env_slices, 2)) ? h2 : 0;
+      if (b.cand[1] == 0) b.best = 0;
+    }
+    if (b.best >= 0) return b.cand[b.best];
+    *slot = b.tries[0] <= b.tries[1] ? 0 : 1;
+    return b.cand[*slot];
+  }
+  void tune_record(int n, int slot, float ms, unsigned long long its) {
+    TuneBucket& b = tune[bucket_of(n)];
+    if (slot < 0 || b.best >= 0 || its == 0) return;
+    b.ms[slot] += ms;
+    b.its[slot] += its;
+    b.tries[slot]++;
+    if (b.tries[0] >= TUNE_TRIES && b.tries[1] >= TUNE_TRIES)
+      b.best = (b.ms[1] / (double)b.its[1] < b.ms[0] / (double)b.its[0]) ? 1 : 0;
+  }
   template <int C, class T>
   void launch_pcg_cluster(const PcgClusterArgs<T>& a, int n) {
     cudaLaunchAttribute at = cluster_attr<C>();
@@ -1390,19 +1439,38 @@ struct ipc_scene {
     a.stats = e_stats.p;
     a.bytes = punits(IPC_PROF_PCG_SOLVE);
     a.flops = punits(IPC_PROF_PCG_FLOPS);
-    int n = E;
-    pcg_C = pick_cluster(n);
-    int C = pcg_C;
+    int n = E, slot = -1;
+    int C = tuned_cluster(n, &slot);
+    pcg_C = C;
+    if (!tune_ev[0]) {
+      CK(cudaEventCreate(&tune_ev[0]));
+      CK(cudaEventCreate(&tune_ev[1]));
+    }
+    pcg_tune_iters.ensure(1);
     for (;;) {
+      const int n_launch = n;
+      a.iters = slot >= 0 ? pcg_tune_iters.p : nullptr;
+      if (slot >= 0) {
+        CK(cudaMemsetAsync(pcg_tune_iters.p, 0, sizeof(unsigned long long), stream));
+        CK(cudaEventRecord(tune_ev[0], stream));
+      }
       pbeg(IPC_PROF_PCG_SOLVE);
       launch_pcg_any(C, a, n);
       pend(IPC_PROF_PCG_SOLVE);
+      if (slot >= 0) CK(cudaEventRecord(tune_ev[1], stream));
       launch_grid(k_list_running, 1, 32, E, (const uint8_t*)pcg_runs.p, env_list.p, pcg_active.p);
-      n = read_int(pcg_active.p);
+      n = read_int(pcg_active.p);  // synchronises the stream
+      if (slot >= 0) {
+        float ms = 0.f;
+        unsigned long long its = 0;
+        CK(cudaEventElapsedTime(&ms, tune_ev[0], tune_ev[1]));
+        CK(cudaMemcpy(&its, pcg_tune_iters.p, sizeof(its), cudaMemcpyDeviceToHost));
+        tune_record(n_launch, slot, ms, its);
+      }
       if (n == 0) break;
       a.first = 0;
       a.env_list = env_list.p;
-      C = pick_cluster(n);
+      C = tuned_cluster(n, &slot);
     }
   }
   void pcg(const uint8_t* act) {

@@ -67,6 +67,7 @@ struct PcgClusterArgs {
   long long* stats;           // 5 per env; [STAT_PCG] += iterations of this solve
   unsigned long long* bytes;  // algorithmic bytes of all iterations (may be null)
   unsigned long long* flops;  // floating-point operations of all iterations (null when bytes is)
+  unsigned long long* iters;  // env-iterations done by this launch (may be null)
 };
 
 // Sum of an env's slot partials (its slices, then its bodies) in a fixed order that depends on
@@ -392,6 +393,7 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
     P.it_state[e] = it;
     P.run[e] = more ? 1 : 0;
     P.stats[5 * e + STAT_PCG] += it - it0;
+    if (P.iters) atomicAdd(P.iters, (unsigned long long)(it - it0));
     if (P.bytes) {
       atomicAdd(P.bytes, (unsigned long long)(iter_bytes * (it - it0)));
       atomicAdd(P.flops, (unsigned long long)(iter_flops * (it - it0)));
