@@ -88,7 +88,8 @@ typedef struct {
 } ipc_soft_body_desc;
 
 /* Affine body: closed outward rest surface (n_verts*3 doubles, n_tris*3 int32), density,
- * initial coordinates q0 and rates qdot0 (12 each). A kinematic body follows the schedule. */
+ * initial coordinates q0 and rates qdot0 (12 each). A kinematic body follows the schedule; a free
+ * body with pd_stiffness > 0 is pulled toward it. */
 typedef struct {
   int32_t n_verts, n_tris, kinematic, pad;
   const double* verts;
@@ -96,6 +97,9 @@ typedef struct {
   double density;
   double q0[12];
   double qdot0[12];
+  double pd_stiffness; /* k_pd (1/s^2) of a free body driven toward its scheduled coordinates by
+                          1/2 h^2 k_pd (q - q^)^T (M4 x I3) (q - q^) = 1/2 h^2 k_pd int rho |x - x^|^2
+                          (rigid links of a hand following joint targets); 0 = none */
 } ipc_affine_body_desc;
 
 /* One environment. gravity_on: n_steps bytes (gravity acts during step s when 1).

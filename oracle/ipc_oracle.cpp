@@ -478,6 +478,7 @@ struct AffineDesc {
   double rho;
   double q0[12];
   double qdot0[12];
+  double pd_stiffness;  // k_pd (1/s^2); 0: no PD target potential
 };
 struct EnvDesc {
   int32_t n_soft, n_affine, n_steps, pad;
@@ -503,6 +504,7 @@ struct Body {
   int dof;   // first DOF of q
   int kin;
   int handle;  // index into the per-step target table
+  double kpd;  // PD target stiffness k_pd (1/s^2), free bodies only
   double M4[16];
   double vol;
   double lo[3], hi[3];
@@ -685,6 +687,7 @@ static Env* build_env(const Params& P, const EnvDesc& D) {
     B.dof = 3 * nsv + 12 * b;
     B.kin = A.kinematic;
     B.handle = D.n_soft + b;
+    B.kpd = A.kinematic ? 0.0 : A.pd_stiffness;
     mass_properties(A.n_verts, A.verts, A.n_tris, A.tris, A.rho, B.M4, &B.vol);
     for (int k = 0; k < 3; ++k) { B.lo[k] = 1e300; B.hi[k] = -1e300; }
     for (int i = 0; i < A.n_verts; ++i)
@@ -895,7 +898,7 @@ static bool is_kin_dof(const Env& e, int d) {
 static double evaluate(Env& e, const std::vector<double>& q, const std::vector<Contact>& C, int want,
                        std::vector<double>* grad, Triplets* H) {
   const double h = e.P.dt, h2 = h * h;
-  double Einert = 0, Eelas = 0, Ebar = 0, Efric = 0, Eorth = 0;
+  double Einert = 0, Eelas = 0, Ebar = 0, Efric = 0, Eorth = 0, Epd = 0;
   if (grad) grad->assign(e.ndof, 0.0);
   // inertia of free soft vertices
   for (int i = 0; i < e.n_soft_verts; ++i) {
@@ -968,6 +971,21 @@ static double evaluate(Env& e, const std::vector<double>& q, const std::vector<C
           if (want >= 1) (*grad)[B.dof + 3 * I + k] += m * (qb[3 * Jn + k] - qt[3 * Jn + k]);
           if (want >= 2) H->add(B.dof + 3 * I + k, B.dof + 3 * Jn + k, m);
         }
+    // PD target potential 1/2 h^2 k_pd (q - q^)^T (M4 x I3) (q - q^) = 1/2 h^2 k_pd int rho |x - x^|^2,
+    // q^ the body's scheduled coordinates for this step
+    if (B.kpd > 0.0) {
+      const int st = std::min(e.step, e.n_steps - 1);
+      const double* qh = e.targets.data() + ((size_t)st * e.n_handles + B.handle) * 12;
+      const double w = h2 * B.kpd;
+      for (int I = 0; I < 4; ++I)
+        for (int Jn = 0; Jn < 4; ++Jn)
+          for (int k = 0; k < 3; ++k) {
+            double m = B.M4[4 * I + Jn];
+            Epd += 0.5 * w * (qb[3 * I + k] - qh[3 * I + k]) * m * (qb[3 * Jn + k] - qh[3 * Jn + k]);
+            if (want >= 1) (*grad)[B.dof + 3 * I + k] += w * m * (qb[3 * Jn + k] - qh[3 * Jn + k]);
+            if (want >= 2) H->add(B.dof + 3 * I + k, B.dof + 3 * Jn + k, w * m);
+          }
+    }
     // A[r][c] = a_c[r] = q[3 + 3c + r]
     Dual<9> A[9];
     for (int r = 0; r < 3; ++r)
@@ -1056,7 +1074,7 @@ static double evaluate(Env& e, const std::vector<double>& q, const std::vector<C
           for (int l = 0; l < 3; ++l) H12[(3 * i + k) * 12 + 3 * j + l] = f.c[i] * f.c[j] * M[3 * k + l];
     scatter(f.pts, g12, H12, s);
   }
-  return Einert + Eelas + Eorth + Ebar + Efric;
+  return Einert + Eelas + Eorth + Epd + Ebar + Efric;
 }
 
 // ---------------------------------------------------------------- step pieces

@@ -226,10 +226,12 @@ __global__ void k_elastic(int n_tets, const int4* __restrict__ tets, const doubl
 // Inertia 1/2 (q - q~)^T (M4 x I3) (q - q~) and orthogonality h^2 kappa_A V |A A^T - I|_F^2,
 // A[r][c] = q[3 + 3c + r]. d2/dA2 of |S|^2, S = A A^T - I, is
 // 4 [d_km (A^T A)_nl + A_kn A_ml + S_km d_ln] at (kl, mn); it is projected to PSD.
-// inertia + orthogonality value of one free body, with A and S = A A^T - I (not inlined, see
-// tet_energy)
+// inertia + orthogonality (+ PD target) value of one free body, with A and S = A A^T - I (not
+// inlined, see tet_energy). The PD target term is 1/2 wpd (q - q^)^T (M4 x I3) (q - q^) with
+// wpd = h^2 k_pd, q^ = Qh.
 __device__ __noinline__ double body_energy(const double* __restrict__ Q, const double* __restrict__ Qt,
-                                           const double* __restrict__ M, double wk, double* dq, double* A, double* S) {
+                                           const double* __restrict__ M, double wk, double* dq, double* A, double* S,
+                                           const double* __restrict__ Qh, double wpd) {
   for (int i = 0; i < 12; ++i) dq[i] = Q[i] - Qt[i];
   double Ein = 0.0;
   for (int I = 0; I < 4; ++I)
@@ -238,6 +240,13 @@ __device__ __noinline__ double body_energy(const double* __restrict__ Q, const d
       for (int Jn = 0; Jn < 4; ++Jn) s += M[4 * I + Jn] * dq[3 * Jn + k];
       Ein += 0.5 * dq[3 * I + k] * s;
     }
+  if (wpd > 0.0)
+    for (int I = 0; I < 4; ++I)
+      for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int Jn = 0; Jn < 4; ++Jn) s += M[4 * I + Jn] * (Q[3 * Jn + k] - Qh[3 * Jn + k]);
+        Ein += 0.5 * wpd * (Q[3 * I + k] - Qh[3 * I + k]) * s;
+      }
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) A[3 * r + c] = Q[3 + 3 * c + r];
   for (int i = 0; i < 3; ++i)
@@ -252,14 +261,16 @@ __device__ __noinline__ double body_energy(const double* __restrict__ Q, const d
 // Hessian d2|S|^2/dA2 in the precision HT (row-major, leading dimension ldo) of one free body.
 template <int MODE, class HT>
 DEV double body_eval(const double* __restrict__ Q, const double* __restrict__ Qt, const double* __restrict__ M,
-                     double wk, double* g, HT* Ho, int ldo) {
+                     double wk, const double* __restrict__ Qh, double wpd, double* g, HT* Ho, int ldo) {
   double dq[12], A[9], S[9];
-  double E = body_energy(Q, Qt, M, wk, dq, A, S);
+  double E = body_energy(Q, Qt, M, wk, dq, A, S, Qh, wpd);
   if (MODE == MODE_ENERGY) return E;
   for (int I = 0; I < 4; ++I)
     for (int k = 0; k < 3; ++k) {
       double s = 0.0;
       for (int Jn = 0; Jn < 4; ++Jn) s += M[4 * I + Jn] * dq[3 * Jn + k];
+      if (wpd > 0.0)
+        for (int Jn = 0; Jn < 4; ++Jn) s += wpd * M[4 * I + Jn] * (Q[3 * Jn + k] - Qh[3 * Jn + k]);
       g[3 * I + k] = s;
     }
   // gradient of |S|^2 wrt A: 4 S A
@@ -294,7 +305,8 @@ template <int MODE>
 __global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int* __restrict__ benv,
                          const uint8_t* __restrict__ bkin, const double* __restrict__ M4, const double* __restrict__ bvol,
                          const uint8_t* __restrict__ act, const double* __restrict__ q, const double* __restrict__ qt,
-                         double h2kA, double* __restrict__ bE, double* __restrict__ bg) {
+                         const double* __restrict__ qh, const double* __restrict__ kpd, double h2, double h2kA,
+                         double* __restrict__ bE, double* __restrict__ bg) {
   static_assert(MODE != MODE_HESS, "the Hessian mode is k_bodies_hess");
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_bodies) return;
@@ -308,22 +320,23 @@ __global__ void k_bodies(int n_bodies, const int* __restrict__ bnode, const int*
   }
   double g[12];
   bE[b] = body_eval<MODE, double>(q + 3 * (long)bnode[b], qt + 3 * (long)bnode[b], M4 + 16 * (long)b,
-                                  h2kA * bvol[b], g, (double*)nullptr, 0);
+                                  h2kA * bvol[b], qh + 3 * (long)bnode[b], h2 * kpd[b], g, (double*)nullptr, 0);
   if (MODE == MODE_GRAD)
     for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = g[i];
 }
 
 // Hessian mode: one half-warp per body. Lane 0 forms the energy, gradient and the 9x9
 // orthogonality Hessian (padded to 10x10 with zeros) in shared memory, the half-warp projects it
-// to PSD in the precision HT, and the 12x12 block (mass blocks + h^2 kappa_A V times the
-// projection) is written out.
+// to PSD in the precision HT, and the 12x12 block ((1 + h^2 k_pd) times the mass blocks, plus
+// h^2 kappa_A V times the projection) is written out.
 constexpr int BODY_HESS_THREADS = 64;
 template <class HT>
 __global__ void __launch_bounds__(BODY_HESS_THREADS)
     k_bodies_hess(int n_bodies, const int* __restrict__ bnode, const int* __restrict__ benv,
                   const uint8_t* __restrict__ bkin, const double* __restrict__ M4, const double* __restrict__ bvol,
                   const uint8_t* __restrict__ act, const double* __restrict__ q, const double* __restrict__ qt,
-                  double h2kA, double* __restrict__ bE, double* __restrict__ bg, HT* __restrict__ bH) {
+                  const double* __restrict__ qh, const double* __restrict__ kpd, double h2, double h2kA,
+                  double* __restrict__ bE, double* __restrict__ bg, HT* __restrict__ bH) {
   constexpr int HALVES = BODY_HESS_THREADS / 16;
   __shared__ HT shA[HALVES][100], shV[HALVES][100], shR[HALVES][30];
   const int half = threadIdx.x >> 4, hl = threadIdx.x & 15;
@@ -341,13 +354,14 @@ __global__ void __launch_bounds__(BODY_HESS_THREADS)
     return;
   }
   const double* M = M4 + 16 * (long)b;
-  const double wk = h2kA * bvol[b];
+  const double wk = h2kA * bvol[b], wpd = h2 * kpd[b];
   HT* A = shA[half];
   for (int i = hl; i < 100; i += 16) A[i] = HT(0);
   __syncwarp(mask);
   if (hl == 0) {
     double g[12];
-    bE[b] = body_eval<MODE_HESS, HT>(q + 3 * (long)bnode[b], qt + 3 * (long)bnode[b], M, wk, g, A, 10);
+    bE[b] = body_eval<MODE_HESS, HT>(q + 3 * (long)bnode[b], qt + 3 * (long)bnode[b], M, wk, qh + 3 * (long)bnode[b],
+                                     wpd, g, A, 10);
     for (int i = 0; i < 12; ++i) bg[12 * (long)b + i] = g[i];
   }
   __syncwarp(mask);
@@ -356,7 +370,7 @@ __global__ void __launch_bounds__(BODY_HESS_THREADS)
   for (int e = hl; e < 144; e += 16) {
     const int qi = e / 12, qj = e % 12;
     const int I = qi / 3, k = qi % 3, Jn = qj / 3, m = qj % 3;
-    HT v = (k == m) ? HT(M[4 * I + Jn]) : HT(0);
+    HT v = (k == m) ? HT(M[4 * I + Jn] + wpd * M[4 * I + Jn]) : HT(0);  // inertia + PD target
     if (qi >= 3 && qj >= 3) {  // q index 3 + 3 l + k  <->  orthogonality index 3 k + l
       const int l = (qi - 3) / 3, n = (qj - 3) / 3;
       v += wkh * A[(3 * k + l) * 10 + 3 * m + n];

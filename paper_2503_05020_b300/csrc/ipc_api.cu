@@ -93,6 +93,7 @@ struct HostEnv {
     double rho;
     double q0[12], qdot0[12];
     int kin;
+    double kpd;  // PD target stiffness (free bodies)
   };
   std::vector<Soft> soft;
   std::vector<Aff> aff;
@@ -231,6 +232,7 @@ void build_env(HostEnv& h, const ipc_env_desc* D) {
     std::memcpy(a.q0, A.q0, sizeof(a.q0));
     std::memcpy(a.qdot0, A.qdot0, sizeof(a.qdot0));
     a.kin = A.kinematic;
+    a.kpd = A.kinematic ? 0.0 : A.pd_stiffness;
     h.aff.push_back(std::move(a));
   }
   h.nsv_verts = nsv;
@@ -415,7 +417,7 @@ struct ipc_scene {
   DBuf<uint8_t> grav;
   DBuf<int> node_env, node_body, node_handle, body_node, body_env;
   DBuf<uint8_t> node_kin, body_kin;
-  DBuf<double> node_mass, X0, M4, bvol, bbox;
+  DBuf<double> node_mass, X0, M4, bvol, bbox, body_pd;
   DBuf<int4> tets;
   DBuf<double> tet_prm;
   DBuf<int> tet_env;
@@ -677,7 +679,7 @@ struct ipc_scene {
     std::vector<uint8_t> grav_h;
     std::vector<int> node_env_h, node_body_h, node_handle_h, body_node_h, body_env_h;
     std::vector<uint8_t> node_kin_h, body_kin_h, pt_kin_h;
-    std::vector<double> node_mass_h, X0_h, M4_h, bvol_h, bbox_h, tet_prm_h, pt_xb_h, ed_rest2_h, x_h, v_h;
+    std::vector<double> node_mass_h, X0_h, M4_h, bvol_h, bpd_h, bbox_h, tet_prm_h, pt_xb_h, ed_rest2_h, x_h, v_h;
     std::vector<int4> tets_h;
     std::vector<int> tet_env_h, pt_node_h, pt_body_h, pt_env_h, sv_pt_h, sv_env_h, ed_pt_h, ed_env_h, tri_pt_h, tri_env_h;
     std::vector<int> status_h, reason_h, step_h;
@@ -702,6 +704,7 @@ struct ipc_scene {
         body_kin_h.push_back(h.aff[b].kin ? 1 : 0);
         for (int k = 0; k < 16; ++k) M4_h.push_back(h.M4[16 * b + k]);
         bvol_h.push_back(h.bvol[b]);
+        bpd_h.push_back(h.aff[b].kpd);
         for (int k = 0; k < 6; ++k) bbox_h.push_back(h.bbox[6 * b + k]);
         for (int k = 0; k < 4; ++k) {
           node_env_h.push_back(li);
@@ -911,6 +914,7 @@ struct ipc_scene {
     body_kin.upload(body_kin_h, s);
     M4.upload(M4_h, s);
     bvol.upload(bvol_h, s);
+    body_pd.upload(bpd_h, s);
     bbox.upload(bbox_h, s);
     tets.upload(tets_h, s);
     tet_prm.upload(tet_prm_h, s);
@@ -1203,11 +1207,11 @@ struct ipc_scene {
     if constexpr (MODE == MODE_HESS)
       launch(k_bodies_hess<HT>, 16L * NB, BODY_HESS_THREADS, NB, (const int*)body_node.p, (const int*)body_env.p,
              (const uint8_t*)body_kin.p, (const double*)M4.p, (const double*)bvol.p, act, q, (const double*)xtilde.p,
-             h2 * desc.kappa_affine, bodyE.p, body_g.p, bH);
+             (const double*)xtarget.p, (const double*)body_pd.p, h2, h2 * desc.kappa_affine, bodyE.p, body_g.p, bH);
     else
       launch(k_bodies<MODE>, NB, 64, NB, (const int*)body_node.p, (const int*)body_env.p, (const uint8_t*)body_kin.p,
-             (const double*)M4.p, (const double*)bvol.p, act, q, (const double*)xtilde.p, h2 * desc.kappa_affine,
-             bodyE.p, body_g.p);
+             (const double*)M4.p, (const double*)bvol.p, act, q, (const double*)xtilde.p, (const double*)xtarget.p,
+             (const double*)body_pd.p, h2, h2 * desc.kappa_affine, bodyE.p, body_g.p);
     int cfam = MODE == MODE_ENERGY ? IPC_PROF_LS_ENERGY : IPC_PROF_CONTACT;
     pbeg(cfam);
     if constexpr (MODE == MODE_HESS)

@@ -79,7 +79,7 @@ __global__ void k_step_setup_nodes(int n_nodes, Layout L, EnvCtl C, const uint8_
         xtarget[3L * i + k] = r;
       }
     }
-  } else if (L.body_kin[b]) {
+  } else {  // every body: kinematic bodies follow it, PD-driven bodies are pulled toward it
     int blk = i - L.body_node[b];
     for (int k = 0; k < 3; ++k) xtarget[3L * i + k] = T[3 * blk + k];
   }

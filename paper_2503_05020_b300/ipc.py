@@ -48,7 +48,7 @@ class SoftDesc(C.Structure):
 class AffineDesc(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("n_tris", C.c_int32), ("kinematic", C.c_int32), ("pad", C.c_int32),
                 ("verts", C.c_void_p), ("tris", C.c_void_p), ("density", C.c_double),
-                ("q0", C.c_double * 12), ("qdot0", C.c_double * 12)]
+                ("q0", C.c_double * 12), ("qdot0", C.c_double * 12), ("pd_stiffness", C.c_double)]
 
 
 class EnvDesc(C.Structure):
@@ -127,6 +127,7 @@ class _EnvMarshal:
             for k in range(12):
                 aff[i].q0[k] = a["q0"][k]
                 aff[i].qdot0[k] = a["qdot0"][k]
+            aff[i].pd_stiffness = float(a.get("pd", 0.0))
         g = np.ascontiguousarray(env["gravity"], dtype=np.uint8)
         tg = np.ascontiguousarray(env["targets"], dtype=np.float64)
         self.keep += [g, tg, soft, aff]

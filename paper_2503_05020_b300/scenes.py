@@ -569,6 +569,21 @@ def spinning_body_env(n_steps: int = 20, omega=(0.0, 0.0, 20.0)) -> dict:
                 targets=np.tile(IDENTITY_Q, (n_steps, 1, 1)))
 
 
+def pd_body_env(k_pd: float = 400.0, n_steps: int = 100, gravity: bool = True, target_shift=(0.0, 0.0, 0.0),
+                shift_steps: int = 0) -> dict:
+    """A free rigid box held by a PD target potential (stiffness k_pd, 1/s^2) toward its initial
+    pose, or toward a pose translated by `target_shift` over the first `shift_steps` steps."""
+    bv, btris = box_surface((0.02, 0.015, 0.01))
+    body = dict(verts=bv, tris=btris, rho=800.0, q0=IDENTITY_Q.copy(), qdot0=np.zeros(12), kinematic=False, pd=k_pd)
+    targets = np.tile(IDENTITY_Q, (n_steps, 1, 1))
+    sh = np.asarray(target_shift, dtype=np.float64)
+    for s in range(n_steps):
+        f = min(1.0, (s + 1) / shift_steps) if shift_steps > 0 else (1.0 if sh.any() else 0.0)
+        targets[s, 0, :3] = f * sh
+    return dict(soft=[], affine=[body], mu=0.0, gravity=np.full(n_steps, 1 if gravity else 0, dtype=np.uint8),
+                targets=targets)
+
+
 def env_sizes(env: dict) -> dict:
     """Counts used to size buffers and to report workloads."""
     nv = sum(len(s["verts"]) for s in env["soft"])

@@ -293,3 +293,22 @@ def test_persistent_pcg_trajectory_matches_tiled():
         assert sc.status(eid)["status"] in ("ACTIVE", "DONE")
         out.append(sc.dofs(eid))
     assert np.abs(out[0] - out[1]).max() <= 1e-6
+
+
+def test_pd_target_body_energy_gradient_and_trajectory_parity():
+    """Free rigid box pulled toward a moving scheduled pose by the PD target potential: energy
+    and gradient at a perturbed state (1e-10) and a 60-step trajectory (1e-6 m) match the oracle."""
+    p = S.scene_params(0.01)
+    env = S.pd_body_env(k_pd=900.0, n_steps=60, target_shift=(0.01, -0.02, 0.005), shift_steps=30)
+    o, x, v = oracle_state(p, env, 7)
+    q = x + np.random.default_rng(3).normal(size=x.size) * 1e-4
+    _energy_parity(p, env, x, v, 7, q)
+    pp = S.parity_params(p)
+    o = O.OracleEnv(pp, env)
+    o.step(60)
+    xo, _ = o.state()
+    sc = ipc.Scene(pp)
+    eid = sc.add_env(env)
+    sc.step(60)
+    assert sc.status(eid)["status"] == "DONE"
+    assert np.abs(sc.dofs(eid) - xo).max() <= TRAJ_TOL

@@ -206,3 +206,29 @@ def test_cube_grasp_lift_outcome_and_invariants(mu, lifts):
         assert abs(dz - plate_dz) < 0.1 * plate_dz
     else:
         assert dz < 0.2 * plate_dz
+
+
+def test_pd_target_body_sags_by_g_over_kpd():
+    """A free box held toward its initial pose by the PD target potential
+    1/2 h^2 k_pd (q - q^)^T (M4 x I3) (q - q^) settles under gravity where k_pd * offset = g:
+    an offset of g / k_pd straight down, with A staying at I (implicit Euler damps the
+    oscillation; omega h = 0.2 decays it by ~1e-4 over 500 steps)."""
+    k = 400.0
+    p = S.scene_params(0.01)
+    env = S.pd_body_env(k_pd=k, n_steps=500)
+    e = O.OracleEnv(p, env)
+    e.step(500)
+    x, v = e.state()
+    assert abs(x[2] - (-G / k)) <= 2e-3 * G / k
+    assert np.abs(x[:2]).max() < 1e-9
+    assert np.abs(x[3:12] - S.IDENTITY_Q[3:12]).max() < 1e-6
+
+
+def test_env_gradient_fd_pd_target_term():
+    p = S.scene_params(0.01)
+    env = S.pd_body_env(k_pd=900.0, n_steps=30, target_shift=(0.01, -0.02, 0.005), shift_steps=10)
+    e = O.OracleEnv(p, env)
+    e.step(5)
+    x, _ = e.state()
+    q = x + np.random.default_rng(2).normal(size=x.size) * 1e-4
+    _fd_check(e, q, list(range(12)))
