@@ -4,9 +4,9 @@
 // hardware cluster barriers; there is no host round trip and no launch per iteration.
 //
 // Work split inside a cluster: stencil products go to half-warps round-robin over the cluster; the
-// env's free soft rows, in chunks of 32 (one row per lane), are dealt to warps round-robin, the
-// same way in every phase, so a row's x, r, y, z entries are only touched by its owner thread; a
-// rigid body belongs to CTA (body index mod C), its 12 DOFs to that CTA's threads 0..11.
+// env's free soft rows, in chunks of 32 (one row per lane), are dealt to CTAs round-robin and,
+// inside a CTA, to warps on demand, so a row's x, r, y, z entries stay on one SM; a rigid body
+// belongs to CTA (body index mod C), its 12 DOFs to that CTA's threads 0..11.
 // Kinematic soft rows are never visited: their right-hand side and preconditioner block are
 // zero, so their d and z stay zero (d is zeroed when the buffers are laid out).
 //
@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
   __shared__ T tot[4];
   __shared__ T sbody[12];
   __shared__ int srange[8];
+  __shared__ int grab[4];  // per phase: the next of this CTA's slices to hand to a warp
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // warps are interleaved over the cluster's CTAs, so consecutive slices land on different SMs
   const int gwarp = warp * C + rank, nwarps = C * PCG_WARPS;
@@ -163,8 +164,20 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
     int lo = P.st_bounds[tid], hi = P.st_bounds[tid + 1];
     srange[2 * tid] = lower_env(P.st_env, lo, hi, e);
     srange[2 * tid + 1] = lower_env(P.st_env, lo, hi, e + 1);
+    grab[tid] = 0;
   }
   __syncthreads();
+  // Slices go to CTAs round-robin (slice S0 + rank + C j belongs to this CTA) and, inside the
+  // CTA, to whichever warp asks next, so warps of uneven rows finish a phase together. A row
+  // stays on its CTA's SM in every phase. Counters are reset in a later phase, after a barrier
+  // that every warp passes only once it has stopped asking.
+  const int n_mine = (S1 - S0 > rank) ? (S1 - S0 - rank + C - 1) / C : 0;
+  auto next_slice = [&](int ph) -> int {
+    int j = 0;
+    if (lane == 0) j = atomicAdd(&grab[ph], 1);
+    j = __shfl_sync(0xffffffffu, j, 0);
+    return j < n_mine ? S0 + rank + C * j : -1;
+  };
   const int n_stencils = srange[1] - srange[0] + srange[3] - srange[2] + srange[5] - srange[4] + srange[7] - srange[6];
 
   T rz, bb;
@@ -173,7 +186,7 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
   bool go;
   if (P.first) {
     // ---- z = M^-1 r, d = z, x = 0; per-slot (r.z, r.r) and the bytes of one iteration
-    for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {  // warp-uniform
+    for (int sl = next_slice(0); sl >= 0; sl = next_slice(0)) {  // warp-uniform
       T a = T(0), c = T(0), nb = T(0), nf = T(0);
       const int i = P.pslice_row[32 * sl + lane];
       if (i >= 0) {
@@ -246,6 +259,7 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
     // ---- t_s = H_s (P_s d) for the env's stencils, one half-warp per stencil (the barrier
     // publishes every CTA's d)
     cl.sync();
+    if (tid == 0) grab[3] = 0;  // every warp is past the direction update (barrier above)
     for (int q = 0; q < 4; ++q)  // warp-uniform loop
       for (int s0 = srange[2 * q] + 2 * gwarp; s0 < srange[2 * q + 1]; s0 += 2 * nwarps) {
         int s = s0 + (lane >> 4);
@@ -253,7 +267,7 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
       }
     cl.sync();
     // ---- y = A d: soft rows, one partial d.y per slice
-    for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {
+    for (int sl = next_slice(1); sl >= 0; sl = next_slice(1)) {
       T dy = T(0);
       const int i = P.pslice_row[32 * sl + lane];
       if (i >= 0) {
@@ -321,7 +335,8 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
     env_sum<1>(part_dy, S0, S1, ST, b0, b1, tot, dy);
     const T alpha = dy[0] > T(0) ? rz / dy[0] : T(0);
     // ---- x += alpha d; r -= alpha y; z = M^-1 r (owner threads only)
-    for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {
+    if (tid == 0) grab[1] = 0;  // every warp is past the product phase (barrier above)
+    for (int sl = next_slice(2); sl >= 0; sl = next_slice(2)) {
       T a = T(0), c = T(0);
       const int i = P.pslice_row[32 * sl + lane];
       if (i >= 0) {
@@ -373,7 +388,8 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
     const T beta = rz > T(0) ? rz_new / rz : T(0);
     rz = rz_new;
     // ---- d = z + beta d (owner threads)
-    for (int sl = S0 + gwarp; sl < S1; sl += nwarps) {
+    if (tid == 0) grab[2] = 0;  // every warp is past the update phase (barrier above)
+    for (int sl = next_slice(3); sl >= 0; sl = next_slice(3)) {
       const int i = P.pslice_row[32 * sl + lane];
       if (i >= 0)
         for (int k2 = 3 * i; k2 < 3 * i + 3; ++k2) P.d[k2] = P.z[k2] + beta * P.d[k2];

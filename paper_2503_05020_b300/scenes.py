@@ -569,6 +569,87 @@ def spinning_body_env(n_steps: int = 20, omega=(0.0, 0.0, 20.0)) -> dict:
                 targets=np.tile(IDENTITY_Q, (n_steps, 1, 1)))
 
 
+def link_surface(rng: SplitMix64, length: float, radius: float, n_points: int = 250):
+    """A finger link: convex hull of seeded points on an ellipsoid of semi-axes (radius, radius,
+    length / 2), long axis along local z (about 2 n_points - 4 triangles)."""
+    radii = np.array([radius, radius, 0.5 * length])
+    pts = []
+    for _ in range(n_points):
+        d = np.array([rng.normal(), rng.normal(), rng.normal()])
+        d /= max(np.linalg.norm(d), 1e-12)
+        pts.append(d * radii)
+    return convex_hull_surface(np.asarray(pts))
+
+
+def _q_pose(R: np.ndarray, c: np.ndarray) -> np.ndarray:
+    q = np.zeros(12)
+    q[:3] = c
+    q[3:6], q[6:9], q[9:12] = R[:, 0], R[:, 1], R[:, 2]
+    return q
+
+
+def hand_grasp_env(env_id: int, base_seed: int = BASE_SEED + 104729, n_steps: int = 400, close_steps: int = 200,
+                   dt: float = 0.005, dhat: float = 5e-4, cells: int = 19, k_pd: float = 3e3, lift: float = 0.05,
+                   link_points: int = 250) -> dict:
+    """Rigid hand of 20 PD-driven affine links (5 fingers x 4; each link a ~500-triangle hull)
+    grasping a seeded star-shaped soft object (Kuhn ball of `cells`^3 cells, about 21k tets for 19;
+    E log-uniform in [1e4, 1e6] Pa, nu U(0.3, 0.48)). Finger f hangs in the vertical half-plane at
+    azimuth 2 pi f / 5 above and outside the object; its four joint angles curl it toward the
+    object over `close_steps` (gravity off), then every link target rises by `lift` (gravity on).
+    Links are free bodies pulled toward their targets by the PD target potential (k_pd 1/s^2)."""
+    rng = SplitMix64(base_seed + env_id)
+    E = math.exp(rng.uniform(math.log(1e4), math.log(1e6)))
+    nu = rng.uniform(0.3, 0.48)
+    r0 = 0.03
+    verts, tets = star_ball(rng, cells, r0)
+    tris = boundary_tris(verts, tets)
+    rmax = float(np.linalg.norm(verts, axis=1).max())
+    soft = dict(verts=verts, tets=tets, tris=tris, E=E, nu=nu, rho=1000.0, kin=np.zeros(len(verts), dtype=np.uint8))
+    L, rw, gap = 0.018, 0.0055, 3.0 * dhat
+    base_r, base_z = rmax + 0.028, 0.5 * rmax + 0.012
+    theta0 = np.radians([-25.0, 5.0, 5.0, 5.0])      # first joint tilts the finger outward
+    dtheta = np.radians([31.5, 17.5, 14.0, 10.5])    # curl: fingertips end ~13% inside the object
+    links, poses = [], []  # poses[s][link] = q
+    link_shapes = [link_surface(rng, L - gap, rw, link_points) for _ in range(20)]
+
+    def finger_pose(phi: float, theta: np.ndarray, dz: float):
+        er = np.array([math.cos(phi), math.sin(phi), 0.0])
+        et = np.array([-math.sin(phi), math.cos(phi), 0.0])
+        joint = base_r * er + np.array([0.0, 0.0, base_z + dz])
+        beta, out = 0.0, []
+        for k in range(4):
+            beta += theta[k]
+            u = -math.sin(beta) * er - math.cos(beta) * np.array([0.0, 0.0, 1.0])  # down, toward axis
+            c = joint + 0.5 * L * u
+            e3 = u
+            e1 = et
+            e2 = np.cross(e3, e1)
+            out.append(_q_pose(np.stack([e1, e2, e3], axis=1), c))
+            joint = joint + L * u
+        return out
+
+    phis = [2.0 * math.pi * f / 5 + rng.uniform(-0.1, 0.1) for f in range(5)]
+    targets = np.zeros((n_steps, 21, 12))
+    gravity = np.zeros(n_steps, dtype=np.uint8)
+    for s_ in range(n_steps):
+        a = min(1.0, (s_ + 1) / close_steps)
+        dz = lift * max(0.0, (s_ + 1 - close_steps) / max(n_steps - close_steps, 1))
+        targets[s_, 0] = IDENTITY_Q
+        qs = []
+        for phi in phis:
+            qs += finger_pose(phi, theta0 + a * dtheta, dz)
+        targets[s_, 1:] = np.array(qs)
+        gravity[s_] = 1 if s_ >= close_steps else 0
+    q_init = []
+    for phi in phis:
+        q_init += finger_pose(phi, theta0, 0.0)
+    for k in range(20):
+        lv, lt = link_shapes[k]
+        links.append(dict(verts=lv, tris=lt, rho=1200.0, q0=q_init[k], qdot0=np.zeros(12), kinematic=False, pd=k_pd))
+    return dict(soft=[soft], affine=links, mu=rng.uniform(0.5, 0.9), gravity=gravity, targets=targets,
+                object=("soft", 0), lift=lift)
+
+
 def pd_body_env(k_pd: float = 400.0, n_steps: int = 100, gravity: bool = True, target_shift=(0.0, 0.0, 0.0),
                 shift_steps: int = 0) -> dict:
     """A free rigid box held by a PD target potential (stiffness k_pd, 1/s^2) toward its initial
