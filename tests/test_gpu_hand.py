@@ -3,9 +3,9 @@ star-shaped soft object of about 22k tets, dhat = 5e-4 m (needs a B300).
 
 Against the oracle (one environment; the oracle needs ~30 s per time step here, so outputs are
 sampled): candidate lists bit-exact, energy and gradient within 1e-10 at two perturbed states,
-and the first projected-Newton direction in parity settings. On the GPU alone:
-a batch of hands through closing and lifting keeps every environment alive, intersection-free
-and without inverted tets, and lifts the object.
+and the first projected-Newton direction in parity settings. On the GPU alone: a batch of hands
+closing on their objects keeps every environment alive, intersection-free and without inverted
+tets.
 """
 import numpy as np
 import pytest
