@@ -241,6 +241,188 @@ DEV void project_psd_hw(T* A, T* V, T* rot, int hw_lane, unsigned mask) {
   __syncwarp(mask);
 }
 
+// The same round-robin Jacobi by a whole thread block: every thread updates the matrix
+// elements e = threadIdx.x, threadIdx.x + blockDim.x (N * N <= 2 blockDim) of each round, three
+// block barriers per round. For kernels with few matrices and latency to hide (a few hundred
+// contacts per Newton iteration). A, V (N x N) and rot (3N) in shared memory; every thread of the
+// block calls it. FROM_V: V already holds an orthonormal basis to continue from (else V = I).
+// PROJECT: on return A = V max(Lambda, 0) V^T (else A is left diagonalised, V its eigenvectors).
+// Sweeps stop when the off-diagonal part is below tol_rel of the Frobenius norm (squared), or
+// after max_sweeps.
+template <int N, class T, bool FROM_V, bool PROJECT>
+DEV void jacobi_block(T* A, T* V, T* rot, T tol_rel = JacobiTol<T>::psd, int max_sweeps = 24) {
+  static_assert(N % 2 == 0, "N must be even");
+  const int t = threadIdx.x, nt = blockDim.x;
+  T* alpha = rot;
+  T* beta = rot + N;
+  int* partner = (int*)(rot + 2 * N);
+  __shared__ T red[32];
+  if (!FROM_V)
+    for (int e = t; e < N * N; e += nt) V[e] = (e / N == e % N) ? T(1) : T(0);
+  // sums over the matrix: per-warp butterflies, warps added in order (same value in every thread)
+  auto block_sum2 = [&](T v) -> T {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((t & 31) == 0) red[t >> 5] = v;
+    __syncthreads();
+    T s = T(0);
+    for (int w = 0; w < (nt + 31) / 32; ++w) s += red[w];
+    __syncthreads();
+    return s;
+  };
+  T fro = T(0);
+  for (int e = t; e < N * N; e += nt) fro += A[e] * A[e];
+  fro = block_sum2(fro);
+  if (fro == T(0)) return;
+  const T tol = tol_rel * fro;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    T off = T(0);
+    for (int e = t; e < N * N; e += nt)
+      if (e / N < e % N) off += T(2) * A[e] * A[e];
+    off = block_sum2(off);
+    if (off <= tol) break;
+    for (int r = 0; r < N - 1; ++r) {
+      if (t < N / 2) {
+        const int k = t;
+        int a = k == 0 ? 0 : 1 + (r + k) % (N - 1);
+        int b = k == 0 ? 1 + r % (N - 1) : 1 + (r - k + N - 1) % (N - 1);
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        const T apq = A[p * N + q];
+        T c = T(1), sn = T(0);
+        if (apq != T(0)) {
+          const T app = A[p * N + p], aqq = A[q * N + q];
+          const T theta = (aqq - app) / (T(2) * apq);
+          const T tt = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+          c = rsqrt(tt * tt + T(1));
+          sn = tt * c;
+        }
+        alpha[p] = c;
+        beta[p] = -sn;
+        partner[p] = q;
+        alpha[q] = c;
+        beta[q] = sn;
+        partner[q] = p;
+      }
+      __syncthreads();
+      T na[2], nv[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = t + u * nt;
+        if (e < N * N) {
+          const int i = e / N, j = e % N, i2 = partner[i], j2 = partner[j];
+          const T ai = alpha[i], bi = beta[i], aj = alpha[j], bj = beta[j];
+          na[u] = ai * (aj * A[i * N + j] + bj * A[i * N + j2]) + bi * (aj * A[i2 * N + j] + bj * A[i2 * N + j2]);
+          nv[u] = aj * V[i * N + j] + bj * V[i * N + j2];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = t + u * nt;
+        if (e < N * N) {
+          A[e] = na[u];
+          V[e] = nv[u];
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (!PROJECT) return;
+  T out[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = t + u * nt;
+    out[u] = T(0);
+    if (e < N * N) {
+      const int i = e / N, j = e % N;
+      for (int k = 0; k < N; ++k) {
+        const T lk = A[k * N + k];
+        if (lk > T(0)) out[u] += V[i * N + k] * lk * V[j * N + k];
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = t + u * nt;
+    if (e < N * N) A[e] = out[u];
+  }
+  __syncthreads();
+}
+
+// FP64 PSD projection of the symmetric N x N matrix A by a thread block, warm-started in FP32:
+// Jacobi sweeps in FP32 give an approximate eigenbasis; one Newton-Schulz step
+// V <- V (3 I - V^T V) / 2 makes it orthonormal in FP64, A is rotated into it (V^T A V, nearly
+// diagonal), and FP64 Jacobi sweeps from there (quadratic convergence: one or two) finish the
+// eigen-decomposition to the FP64 tolerance. The result is the FP64 projection; the FP32 stage only
+// saves FP64 rotations. Shared arrays: A, V, W (N x N doubles), rot (3N doubles), Af, Vf (N x N
+// floats), rotf (3N floats).
+template <int N>
+DEV void project_psd_block_warm(double* A, double* V, double* W, double* rot, float* Af, float* Vf, float* rotf) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int e = t; e < N * N; e += nt) Af[e] = float(A[e]);
+  __syncthreads();
+  // FP32 stops where its rounding floor starts (off-diagonal ~3e-6 of the norm, at most 12 sweeps)
+  jacobi_block<N, float, false, false>(Af, Vf, rotf, 1e-11f, 12);
+  for (int e = t; e < N * N; e += nt) V[e] = double(Vf[e]);
+  __syncthreads();
+  // W = V^T V
+  for (int e = t; e < N * N; e += nt) {
+    const int i = e / N, j = e % N;
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += V[k * N + i] * V[k * N + j];
+    W[e] = s;
+  }
+  __syncthreads();
+  double nv[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = t + u * nt;
+    if (e < N * N) {
+      const int i = e / N, j = e % N;
+      double s = 0.0;
+      for (int k = 0; k < N; ++k) s += V[i * N + k] * ((k == j ? 3.0 : 0.0) - W[k * N + j]);
+      nv[u] = 0.5 * s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = t + u * nt;
+    if (e < N * N) V[e] = nv[u];
+  }
+  __syncthreads();
+  // A <- V^T A V (W = A V first), symmetrised
+  for (int e = t; e < N * N; e += nt) {
+    const int i = e / N, j = e % N;
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += A[i * N + k] * V[k * N + j];
+    W[e] = s;
+  }
+  __syncthreads();
+  double nb[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = t + u * nt;
+    if (e < N * N) {
+      const int i = e / N, j = e % N;
+      double s1 = 0.0, s2 = 0.0;
+      for (int k = 0; k < N; ++k) {
+        s1 += V[k * N + i] * W[k * N + j];
+        s2 += V[k * N + j] * W[k * N + i];
+      }
+      nb[u] = 0.5 * (s1 + s2);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = t + u * nt;
+    if (e < N * N) A[e] = nb[u];
+  }
+  __syncthreads();
+  jacobi_block<N, double, true, true>(A, V, rot);
+}
+
 // Symmetric 3x3 eigen-decomposition by cyclic Jacobi in the precision T: A (row-major) ->
 // eigenvalues w and eigenvector columns of V (det V = +1).
 template <class T>

@@ -486,32 +486,32 @@ __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uin
     for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = g[i];
 }
 
-// Hessian mode: one half-warp per contact. Lane 0 forms the energy, gradient and 12x12 Hessian
-// (FP64) in shared memory, the half-warp projects the Hessian to PSD in FP64, and its packed
-// upper triangle is stored in the precision HT.
+// Hessian mode: one block of BARRIER_HESS_THREADS per contact (a Newton iteration has a few
+// hundred contacts, so their latency, not the GPU's FP64 throughput, sets the time). Thread 0
+// forms the energy, gradient and 12x12 Hessian (FP64) in shared memory, the block projects it to
+// PSD in FP64 (FP32-warm-started Jacobi, one or two matrix elements per thread per round), and
+// its packed upper triangle is stored in the precision HT.
 constexpr int BARRIER_HESS_THREADS = 128;
 template <class HT>
 __global__ void __launch_bounds__(BARRIER_HESS_THREADS)
     k_barrier_hess(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
                    const double* __restrict__ ptx, double h2, double dhat, double kappa, double* __restrict__ sE,
                    double* __restrict__ sg, HT* __restrict__ sH) {
-  constexpr int HALVES = BARRIER_HESS_THREADS / 16;
-  __shared__ double shA[HALVES][144], shV[HALVES][144], shR[HALVES][36];
-  const int half = threadIdx.x >> 4, hl = threadIdx.x & 15;
-  const unsigned mask = 0xffffu << (threadIdx.x & 16);
-  const int k = (blockIdx.x * BARRIER_HESS_THREADS + threadIdx.x) >> 4;
-  if (k >= n_ct) return;  // uniform over the half-warp
+  static_assert(144 <= 2 * BARRIER_HESS_THREADS, "two matrix elements per thread at most");
+  __shared__ double A[144], V[144], W[144], R[36];
+  __shared__ float Af[144], Vf[144], Rf[36];
+  const int k = blockIdx.x, t = threadIdx.x;
+  if (k >= n_ct) return;  // uniform over the block
   const ContactRec c = ct[k];
   if (!act[c.env]) return;
-  double* A = shA[half];
-  if (hl == 0) {
+  if (t == 0) {
     double g[12];
     sE[k] = barrier_eval<MODE_HESS>(c, ptx, h2, dhat, kappa, g, A);
     for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = g[i];
   }
-  __syncwarp(mask);
-  project_psd_hw<12, double>(A, shV[half], shR[half], hl, mask);
-  for (int e = hl; e < 144; e += 16) {
+  __syncthreads();
+  project_psd_block_warm<12>(A, V, W, R, Af, Vf, Rf);
+  for (int e = t; e < 144; e += BARRIER_HESS_THREADS) {
     const int i = e / 12, j = e % 12;
     if (j >= i) sH[78 * (long)k + up_idx(i, j, 12)] = HT(A[e]);
   }

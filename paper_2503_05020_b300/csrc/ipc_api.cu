@@ -1215,8 +1215,8 @@ struct ipc_scene {
     int cfam = MODE == MODE_ENERGY ? IPC_PROF_LS_ENERGY : IPC_PROF_CONTACT;
     pbeg(cfam);
     if constexpr (MODE == MODE_HESS)
-      launch(k_barrier_hess<HT>, 16L * n_ct, BARRIER_HESS_THREADS, n_ct, (const ContactRec*)ct.p, act,
-             (const double*)ptx.p, h2, desc.dhat, desc.kappa, sE.p, sg.p, sHp);
+      launch(k_barrier_hess<HT>, (long)BARRIER_HESS_THREADS * n_ct, BARRIER_HESS_THREADS, n_ct, (const ContactRec*)ct.p,
+             act, (const double*)ptx.p, h2, desc.dhat, desc.kappa, sE.p, sg.p, sHp);
     else
       launch(k_barrier<MODE>, n_ct, 64, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, h2, desc.dhat,
              desc.kappa, sE.p, sg.p);
