@@ -71,6 +71,12 @@ typedef struct {
   int32_t pcg_cluster;   /* PCG launch shape: 0 = automatic, 1/2/4/8 = one persistent cluster of
                             that many CTAs per environment, -1 = one launch per PCG phase over
                             tiles of all environments */
+  int32_t fresh_broad_phase; /* 0: inside a time step, the line-search trials and the later Newton
+                            iterations take their contact sets from the step filter's swept
+                            candidates (boxes swept over [x, x + p] and grown by dhat/2, which
+                            hold every pair that can come within dhat on the segment); 1: a BVH
+                            traversal at every evaluation. Both give the same contacts in the
+                            same order. */
   void* cuda_stream;     /* cudaStream_t to borrow, or NULL for a library-owned stream */
 } ipc_scene_desc;
 

@@ -1149,17 +1149,42 @@ struct ipc_scene {
       launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)cnt_ee.p, (const int*)slots_ee.p,
              (const int*)off_ee.p, cand_j.p + n_pt, 1);
     }
+    contacts_from_list(nullptr, n_pt, n_ee, off_pt.p, off_ee.p, cand_j.p);
+  }
+  // Narrow phase over a candidate list (point-triangle per surface vertex, then edge-edge per
+  // edge, partners ascending): contacts d < dhat at positions ptx, in list order. act (or null)
+  // keeps only the envs of this evaluation when the list holds more.
+  void contacts_from_list(const uint8_t* act, int np, int ne, const int* offp, const int* offe, const int* cj) {
+    const int nc = np + ne;
     nflag.ensure(nc + 1);
     noff.ensure(nc + 1);
     ct_tmp.ensure(nc + 1);
     double dh2 = desc.dhat * desc.dhat;
-    launch(k_narrow, nc, 128, n_pt, n_ee, (const int*)off_pt.p, NSV, (const int*)off_ee.p, NED, (const int*)cand_j.p,
-           (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p, (const int*)ed_env.p,
-           (const double*)ptx.p, dh2, nflag.p, ct_tmp.p, (const double*)ed_rest2.p);
+    launch(k_narrow, nc, 128, np, ne, offp, NSV, offe, NED, cj, (const int*)sv_pt.p, (const int*)sv_env.p,
+           (const int*)tri_pt.p, (const int*)ed_pt.p, (const int*)ed_env.p, (const double*)ptx.p, dh2, nflag.p,
+           ct_tmp.p, (const double*)ed_rest2.p, act);
     n_ct = scan(nflag.p, nc, noff.p);
-    n_ct_pt = n_pt > 0 ? read_int(noff.p + n_pt) : 0;
+    n_ct_pt = np > 0 ? read_int(noff.p + np) : 0;
     ct.ensure(n_ct + 1);
     launch(k_compact_contacts, nc, 256, nc, (const int*)nflag.p, (const int*)noff.p, (const ContactRec*)ct_tmp.p, ct.p);
+  }
+  // Where the contact set of the next evaluation inside a time step comes from. STATIC: the
+  // step start's list at x^t, while the DOFs are still x^t. SWEPT: the step filter's list of
+  // boxes swept over [x, x + p] and grown by dhat/2 (plus a margin far above the rounding of
+  // x + alpha p): a pair that comes within dhat anywhere on that segment has overlapping grown
+  // boxes, so the list holds every contact of every line-search trial and of the accepted
+  // point. Either way the narrow phase keeps exactly the pairs with d < dhat, in the order a
+  // fresh traversal gives (per query, partners ascending): the contacts, and every result, are
+  // the same as with a traversal at each evaluation.
+  enum { CAND_FRESH = 0, CAND_STATIC = 1, CAND_SWEPT = 2 };
+  int cand_src = CAND_FRESH;
+  int ccd_np = 0, ccd_ne = 0;
+  bool reuse_lists() const { return desc.fresh_broad_phase == 0; }
+  double swept_growth() const { return reuse_lists() ? 0.5 * desc.dhat * (1.0 + 1e-6) : 0.0; }
+  void contacts_at(const uint8_t* act) {
+    if (cand_src == CAND_SWEPT) contacts_from_list(act, ccd_np, ccd_ne, ccd_off_pt.p, ccd_off_ee.p, ccd_j.p);
+    else if (cand_src == CAND_STATIC) contacts_from_list(act, n_pt, n_ee, off_pt.p, off_ee.p, cand_j.p);
+    else constraint_set(act);
   }
   void stencil_table() {
     int ns = n_ct + n_fr;
@@ -1191,7 +1216,7 @@ struct ipc_scene {
   template <int MODE, class HT>
   void evaluate_t(const double* q, const uint8_t* act, double* out) {
     launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p, q, ptx.p);
-    constraint_set(act);
+    contacts_at(act);
     stencil_table();
     // Hessian outputs (taken after stencil_table, which may grow the stencil buffers)
     HT* tH = MODE == MODE_HESS ? hp<HT>(tet_H, f_tet_H) : nullptr;
@@ -1588,6 +1613,7 @@ struct ipc_scene {
            (const double*)x.p, ptx.p);
     build_trees();
     n_fr = n_fr_pt = 0;
+    cand_src = CAND_FRESH;
     constraint_set(act);
     CK(cudaMemcpyAsync(ptx_t.p, ptx.p, 3 * (size_t)NP * sizeof(double), cudaMemcpyDeviceToDevice, stream));
     fr.ensure(n_ct + 1);
@@ -1607,9 +1633,12 @@ struct ipc_scene {
     ccd_off_ee.ensure(NED + 1);
     slots_pt.ensure((size_t)NSV * CAND_CAP + 1);
     slots_ee.ensure((size_t)NED * CAND_CAP + 1);
+    const double r = swept_growth();
+    const bool keep = reuse_lists();  // the list also serves the narrow phases: sorted per query
+    ccd_np = ccd_ne = 0;
     CandOut cp{ccd_cnt_pt.p, nullptr, slots_pt.p, overflow.p, CAND_CAP};
     launch(k_trav_pt<TRAV_COLLECT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
-           (const double*)ptx.p, (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), cp,
+           (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), cp,
            (const double*)nullptr, C);
     CandOut ce{ccd_cnt_ee.p, nullptr, slots_ee.p, overflow.p, CAND_CAP};
     launch(k_trav_ee<TRAV_COLLECT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
@@ -1617,12 +1646,23 @@ struct ipc_scene {
     int np = scan(ccd_cnt_pt.p, NSV, ccd_off_pt.p);
     int ne = scan(ccd_cnt_ee.p, NED, ccd_off_ee.p);
     const bool spilled = collect_spilled();
+    ccd_np = np;
+    ccd_ne = ne;
     if (np + ne == 0) return;
     ccd_j.ensure(np + ne + 1);
-    if (spilled) {
+    if (spilled && keep) {
+      CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p};
+      launch(k_trav_pt<TRAV_FILL>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
+             (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
+             (const double*)nullptr, C);
+      CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p};
+      launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+             (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr,
+             C);
+    } else if (spilled) {
       CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p};
       launch(k_trav_pt<TRAV_FILLU>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
-             (const double*)ptx.p, (const double*)pte.p, 0.0, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
+             (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
              (const double*)nullptr, C);
       CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p};
       launch(k_trav_ee<TRAV_FILLU>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
@@ -1630,13 +1670,14 @@ struct ipc_scene {
              C);
     } else {
       launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)ccd_cnt_pt.p, (const int*)slots_pt.p,
-             (const int*)ccd_off_pt.p, ccd_j.p, 0);
+             (const int*)ccd_off_pt.p, ccd_j.p, keep ? 1 : 0);
       launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)ccd_cnt_ee.p, (const int*)slots_ee.p,
-             (const int*)ccd_off_ee.p, ccd_j.p + np, 0);
+             (const int*)ccd_off_ee.p, ccd_j.p + np, keep ? 1 : 0);
     }
     launch(k_accd_pairs, np + ne, 128, np, ne, (const int*)ccd_off_pt.p, NSV, (const int*)ccd_off_ee.p, NED,
            (const int*)ccd_j.p, (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p,
-           (const int*)ed_env.p, (const double*)ptx.p, (const double*)ptp.p, C);
+           (const int*)ed_env.p, (const double*)ptx.p, (const double*)ptp.p, keep ? (const double*)pte.p : nullptr,
+           C);
   }
 
   void newton_step() {
@@ -1644,6 +1685,7 @@ struct ipc_scene {
     launch(k_env_begin_step, E, 128, E, C);
     if (count_flags(e_stepping.p) == 0) return;
     step_setup(e_stepping.p);
+    if (reuse_lists()) cand_src = CAND_STATIC;  // the first Newton iteration evaluates at x^t
     for (int it = 0; it < desc.max_newton; ++it) {
       if (count_flags(e_iter.p) == 0) break;
       launch(k_env_iter_begin, E, 128, E, C);
@@ -1663,10 +1705,11 @@ struct ipc_scene {
       launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p,
              (const double*)p.p, ptp.p);
       launch(k_add_vec, 3L * NP, 256, 3L * NP, (const double*)ptx.p, (const double*)ptp.p, pte.p);
-      boxes_and_refit(pte.p, 0.0);
+      boxes_and_refit(pte.p, swept_growth());
       pbeg(IPC_PROF_CCD);
       ccd_filter(C);
       pend(IPC_PROF_CCD);
+      if (reuse_lists()) cand_src = CAND_SWEPT;  // the trials and the next iteration's point
       // backtracking line search on the envs still iterating
       launch(k_env_ls_begin, E, 128, E, C);
       for (int ls = 0; ls <= desc.max_ls_halvings + 1; ++ls) {
@@ -1678,6 +1721,7 @@ struct ipc_scene {
       launch(k_accept, NN, 256, NN, layout(), C, (const double*)xtrial.p, (const double*)xtarget.p, x.p);
       launch(k_env_newton_end, E, 128, E, C, desc.max_newton);
     }
+    cand_src = CAND_FRESH;
     launch(k_end_step_nodes, NN, 256, NN, layout(), C, desc.dt, (const double*)x.p, (const double*)xt.p, v.p);
     launch(k_env_end_step, E, 128, E, C);
     CK(cudaStreamSynchronize(stream));

@@ -485,7 +485,8 @@ __global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ off_pt, int
                          int n_ed, const int* __restrict__ cj, const int* __restrict__ sv_pt,
                          const int* __restrict__ sv_env, const int* __restrict__ tri_pt, const int* __restrict__ ed_pt,
                          const int* __restrict__ ed_env, const double* __restrict__ ptx, double dhat2,
-                         int* __restrict__ flag, ContactRec* __restrict__ tmp, const double* __restrict__ ed_rest2) {
+                         int* __restrict__ flag, ContactRec* __restrict__ tmp, const double* __restrict__ ed_rest2,
+                         const uint8_t* __restrict__ act) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_pt + n_ee) return;
   ContactRec c;
@@ -512,6 +513,10 @@ __global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ off_pt, int
     c.eps_x = 1e-3 * ed_rest2[q] * ed_rest2[j];
   }
   c.cand = i;
+  if (act && !act[c.env]) {  // a list that holds envs outside this evaluation
+    flag[i] = 0;
+    return;
+  }
   d3 X[4];
   for (int k = 0; k < 4; ++k) X[k] = ld3(ptx, c.pts[k]);
   int type;
@@ -543,15 +548,33 @@ __global__ void k_gather_cands(int nq, int cap, const int* __restrict__ cnt, con
   }
 }
 
+// Swept box [min(x, x_end), max(x, x_end)] of n points: the box k_prim_boxes and the
+// point-triangle query build with no growth.
+DEV void swept_box(const double* __restrict__ ptx, const double* __restrict__ pte, const int* pts, int n,
+                   double* box) {
+  for (int k = 0; k < 3; ++k) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int v = 0; v < n; ++v) {
+      const double a = ptx[3L * pts[v] + k], b = pte[3L * pts[v] + k];
+      lo = fmin(lo, fmin(a, b));
+      hi = fmax(hi, fmax(a, b));
+    }
+    box[k] = lo;
+    box[3 + k] = hi;
+  }
+}
+
 // Additive CCD of every swept candidate pair (point-triangle pairs first, then edge-edge), one
 // thread per pair: the time of impact along [x, x + p] lowers the env's step bound alpha_max
-// (an atomic minimum on non-negative doubles: exact and independent of order).
+// (an atomic minimum on non-negative doubles: exact and independent of order). When the
+// candidates were gathered with grown boxes (pte given), a pair whose plain swept boxes do
+// not overlap is skipped, so the set of tested pairs is the plain swept-box set.
 __global__ void k_accd_pairs(int n_pt, int n_ee, const int* __restrict__ off_pt, int n_sv,
                              const int* __restrict__ off_ee, int n_ed, const int* __restrict__ cj,
                              const int* __restrict__ sv_pt, const int* __restrict__ sv_env,
                              const int* __restrict__ tri_pt, const int* __restrict__ ed_pt,
                              const int* __restrict__ ed_env, const double* __restrict__ ptx,
-                             const double* __restrict__ ptp, EnvCtl C) {
+                             const double* __restrict__ ptp, const double* __restrict__ pte, EnvCtl C) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_pt + n_ee) return;
   int kind, e, pts[4];
@@ -572,6 +595,13 @@ __global__ void k_accd_pairs(int n_pt, int n_ee, const int* __restrict__ off_pt,
     pts[1] = ed_pt[2 * q + 1];
     pts[2] = ed_pt[2 * j];
     pts[3] = ed_pt[2 * j + 1];
+  }
+  if (pte) {
+    const int na = kind == 0 ? 1 : 2;
+    double ba[6], bb[6];
+    swept_box(ptx, pte, pts, na, ba);
+    swept_box(ptx, pte, pts + na, 4 - na, bb);
+    if (!box_overlap(ba, bb)) return;
   }
   d3 X[4], Pd[4];
   for (int a = 0; a < 4; ++a) {

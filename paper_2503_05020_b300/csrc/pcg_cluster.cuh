@@ -10,6 +10,12 @@
 // Kinematic soft rows are never visited: their right-hand side and preconditioner block are
 // zero, so their d and z stay zero (d is zeroed when the buffers are laid out).
 //
+// One iteration has three phases, each ended by a cluster barrier: y = A d with the slot
+// partials of d.y; x, r, z updates with the partials of r.z and r.r; d = z + beta d together with
+// the stencil products of the next iteration, t_s = H_s P_s d = H_s P_s z + beta t_s (by
+// linearity, from z, which the previous barrier published, so no barrier sits between the
+// direction update and the products).
+//
 // Determinism: every dot product is summed per slot (a slice: warp butterfly over its 32 rows; a
 // body: fixed CTA tree), and the env's slots are added in a fixed order that depends on the env
 // alone. So the results are the same bits for every cluster size and every batch the env is in.
@@ -81,7 +87,8 @@ DEV void env_sum(const T* part, int S0, int S1, int s_total, int b0, int b1, T* 
     T s[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) s[q] = T(0);
-    for (int j = lane; j < n; j += 32) {
+#pragma unroll 4
+    for (int j = lane; j < n; j += 32) {  // unrolled: the loads of several slots in flight at once
       long slot = j < ns ? S0 + j : (long)s_total + b0 + (j - ns);
 #pragma unroll
       for (int q = 0; q < K; ++q) s[q] += __ldcg(part + 4 * slot + q);
@@ -104,7 +111,7 @@ DEV void env_sum(const T* part, int S0, int S1, int s_total, int b0, int b1, T* 
 // d = z + beta d (9b). A rigid body: dense block (144b), its d and y (24b), per p-node entry
 // 4 B + 3b rest coordinates, the 12x12 preconditioner (144b) and 12 DOFs x 10b of vector
 // traffic. A stencil: packed Hessian (78b), 4 point nodes (16 B), their rest coordinates (12b),
-// 4 gathered d triples (12b) and t written (12b); each entry then reads its slot of t (3b).
+// 4 gathered z triples (12b), t read and written (24b); each entry then reads its slot of t (3b).
 template <class T>
 DEV double soft_iter_bytes(const SpmvArgsT<T, T>& A, int row) {
   const double b = sizeof(T);
@@ -119,7 +126,7 @@ DEV double body_iter_bytes(const Layout& L, const SpmvArgsT<T, T>& A, int bd) {
 }
 template <class T>
 DEV double stencil_iter_bytes() {
-  return 78.0 * sizeof(T) + 16.0 + 36.0 * sizeof(T);
+  return 78.0 * sizeof(T) + 16.0 + 48.0 * sizeof(T);
 }
 // Floating-point operations of one iteration (an FMA counts 2). A soft row: 18 per sliced-ELL
 // block, 6 per stencil entry, 6 for d.y; then x, r updates (12), z = M^-1 r (18), r.z and r.r
@@ -244,6 +251,14 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
     iter_flops = double(v4[3]) + (P.bytes ? STENCIL_ITER_FLOPS * n_stencils : 0.0);
     it = 0;
     go = bb > T(0) && isfinite(bb);
+    // ---- t_s = H_s (P_s d) for the env's stencils, one half-warp per stencil (d = z was
+    // published by the barrier above)
+    if (go)
+      for (int q = 0; q < 4; ++q)  // warp-uniform loop
+        for (int s0 = srange[2 * q] + 2 * gwarp; s0 < srange[2 * q + 1]; s0 += 2 * nwarps) {
+          int s = s0 + (lane >> 4);
+          stencil_product_nodes<true>(P.A, (const T*)P.d, P.st_t, s, s < srange[2 * q + 1]);
+        }
   } else {
     rz = T(P.rz_state[e]);
     bb = T(P.bb_state[e]);
@@ -256,16 +271,9 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
   const int it0 = it;
   bool more = go;  // the solve continues after this launch
   for (int k = 0; go && k < P.chunk; ++k) {
-    // ---- t_s = H_s (P_s d) for the env's stencils, one half-warp per stencil (the barrier
-    // publishes every CTA's d)
+    // the barrier publishes every CTA's d and stencil products t = H_s (P_s d)
     cl.sync();
     if (tid == 0) grab[3] = 0;  // every warp is past the direction update (barrier above)
-    for (int q = 0; q < 4; ++q)  // warp-uniform loop
-      for (int s0 = srange[2 * q] + 2 * gwarp; s0 < srange[2 * q + 1]; s0 += 2 * nwarps) {
-        int s = s0 + (lane >> 4);
-        stencil_product_nodes<true>(P.A, (const T*)P.d, P.st_t, s, s < srange[2 * q + 1]);
-      }
-    cl.sync();
     // ---- y = A d: soft rows, one partial d.y per slice
     for (int sl = next_slice(1); sl >= 0; sl = next_slice(1)) {
       T dy = T(0);
@@ -398,6 +406,14 @@ __global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgCl
       if (rank == (b - b0) % C && tid < 12) {
         long k2 = 3L * L.body_node[b] + tid;
         P.d[k2] = P.z[k2] + beta * P.d[k2];
+      }
+    // ---- the stencil products follow d by linearity, H_s P_s d_new = H_s P_s z + beta t_s,
+    // so they need z (published by the barrier above) and not the d being written: the next
+    // product phase waits on one barrier instead of two
+    for (int q = 0; q < 4; ++q)  // warp-uniform loop
+      for (int s0 = srange[2 * q] + 2 * gwarp; s0 < srange[2 * q + 1]; s0 += 2 * nwarps) {
+        int s = s0 + (lane >> 4);
+        stencil_product_nodes<true>(P.A, (const T*)P.z, P.st_t, s, s < srange[2 * q + 1], beta);
       }
   }
   // every CTA read the slot partials before it got here; CTA 0 records the env's state

@@ -315,11 +315,12 @@ __global__ void k_stencil_nodes(int n_st, Layout L, const int* __restrict__ st_p
   }
 }
 
-// t_s = H_s (P_s d) for stencil s by the 16 lanes of a half-warp, like stencil_product_hw but
-// with the point nodes precomputed (k_stencil_nodes): lanes 0..3 load their point's node and
-// then its vector entries. Every lane of the warp calls it; ok = false idles a half.
+// t_s = H_s (P_s v) + beta t_s for stencil s by the 16 lanes of a half-warp, like
+// stencil_product_hw but with the point nodes precomputed (k_stencil_nodes): lanes 0..3 load
+// their point's node and then its vector entries. beta = 0 overwrites t_s without reading it.
+// Every lane of the warp calls it; ok = false idles a half.
 template <bool CG, class T>
-DEV void stencil_product_nodes(const SpmvArgsT<T, T>& A, const T* d, T* st_t, int s, bool ok) {
+DEV void stencil_product_nodes(const SpmvArgsT<T, T>& A, const T* d, T* st_t, int s, bool ok, T beta = T(0)) {
   const int lane = threadIdx.x & 31, half = lane & 16, l = lane & 15;
   T v[3] = {T(0), T(0), T(0)};
   if (ok && l < 4) {
@@ -345,6 +346,7 @@ DEV void stencil_product_nodes(const SpmvArgsT<T, T>& A, const T* d, T* st_t, in
     T acc = T(0);
 #pragma unroll
     for (int j = 0; j < 12; ++j) acc += H[sym_idx(l, j, 12)] * u[j];
+    if (beta != T(0)) acc = fma(beta, st_t[12L * s + l], acc);
     st_t[12L * s + l] = acc;
   }
 }
@@ -388,9 +390,12 @@ DEV VT soft_row(const SpmvArgsT<HT, VT>& A, int slice, int lane, int row, const 
     long c = col[32 * kk];  // padding blocks: the row itself, zero values
     VT d0 = ldv<CG>(d, 3 * c), d1 = ldv<CG>(d, 3 * c + 1), d2 = ldv<CG>(d, 3 * c + 2);
     const HT* B = V + 288L * kk;
-    acc[0] = acc[0] + (VT(B[0]) * d0 + VT(B[32]) * d1 + VT(B[64]) * d2);
-    acc[1] = acc[1] + (VT(B[96]) * d0 + VT(B[128]) * d1 + VT(B[160]) * d2);
-    acc[2] = acc[2] + (VT(B[192]) * d0 + VT(B[224]) * d1 + VT(B[256]) * d2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {  // one FMA per block entry
+      acc[a] = fma(VT(B[96 * a]), d0, acc[a]);
+      acc[a] = fma(VT(B[96 * a + 32]), d1, acc[a]);
+      acc[a] = fma(VT(B[96 * a + 64]), d2, acc[a]);
+    }
   }
   int k = A.ns_ptr[row], end = A.ns_ptr[row + 1];
 #pragma unroll 4

@@ -36,7 +36,8 @@ class SceneDesc(C.Structure):
                 ("newton_tol", C.c_double), ("pcg_rel_tol", C.c_double), ("kappa_affine", C.c_double),
                 ("gravity", C.c_double * 3), ("max_newton", C.c_int32), ("max_ls_halvings", C.c_int32),
                 ("max_pcg_iters", C.c_int32), ("precision", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
-                ("device", C.c_int32), ("pcg_cluster", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("device", C.c_int32), ("pcg_cluster", C.c_int32), ("fresh_broad_phase", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
 
 
 class SoftDesc(C.Structure):
@@ -149,7 +150,7 @@ class Scene:
     """A batch of grasp environments stepped together on one GPU."""
 
     def __init__(self, params: dict, precision: int = FP64, device: int = 0, stream: int | None = None,
-                 hbm_budget_bytes: int = 0, pcg_cluster: int = 0):
+                 hbm_budget_bytes: int = 0, pcg_cluster: int = 0, fresh_broad_phase: bool = False):
         d = SceneDesc()
         d.dt, d.dhat, d.kappa, d.eps_v = params["dt"], params["dhat"], params["kappa"], params["eps_v"]
         d.newton_tol, d.pcg_rel_tol, d.kappa_affine = params["newton_tol"], params["pcg_rel_tol"], params["kappa_affine"]
@@ -158,6 +159,7 @@ class Scene:
         d.max_newton, d.max_ls_halvings, d.max_pcg_iters = params["max_newton"], params["max_ls"], params["max_pcg"]
         d.precision, d.hbm_budget_bytes, d.device = precision, hbm_budget_bytes, device
         d.pcg_cluster = pcg_cluster  # 0 automatic, 1/2/4/8 CTAs per env cluster, -1 tiled multi-launch
+        d.fresh_broad_phase = int(bool(fresh_broad_phase))  # 1: a BVH traversal at every evaluation
         d.cuda_stream = stream
         self._h = C.c_void_p()
         _check(lib().ipc_scene_create(C.byref(d), C.byref(self._h)))

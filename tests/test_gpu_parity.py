@@ -312,3 +312,25 @@ def test_pd_target_body_energy_gradient_and_trajectory_parity():
     sc.step(60)
     assert sc.status(eid)["status"] == "DONE"
     assert np.abs(sc.dofs(eid) - xo).max() <= TRAJ_TOL
+
+
+def test_contacts_from_swept_candidates_give_the_same_bits_as_fresh_traversals():
+    """Inside a time step the line-search trials and the later Newton iterations take their
+    contacts from the step filter's swept candidates (boxes over [x, x + p] grown by dhat/2);
+    a BVH traversal at every evaluation must give the same bits: same DOFs, same Newton,
+    line-search, PCG and ACCD counts. Pad grasp from its contact phase and the squeezed cube."""
+    pad = S.pad_grasp_env(3)
+    x, v = S.pad_grasp_state_at(pad, 20)
+    cube, xc, vc, step = pressed_cube_state()
+    cases = [(S.scene_params(0.005), pad, x, v, 20, 6), (S.scene_params(0.01), cube, xc, vc, step, 6)]
+    for p, env, x0, v0, s0, n in cases:
+        out = []
+        for fresh in (False, True):
+            sc = ipc.Scene(p, fresh_broad_phase=fresh)
+            eid = sc.add_env(env)
+            sc.set_state(eid, x0, v0, s0)
+            sc.step(n)
+            out.append((sc.dofs(eid), sc.status(eid)))
+        assert out[0][1]["status"] == "ACTIVE" and out[0][1]["ls_halvings"] >= 0
+        assert out[0][1] == out[1][1]
+        assert np.array_equal(out[0][0], out[1][0])
