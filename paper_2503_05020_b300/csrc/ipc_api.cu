@@ -433,8 +433,8 @@ struct ipc_scene {
   DBuf<double> x, v, xt, xtilde, xtarget, xtrial, p, pbar, grad;
   DBuf<double> ptx, ptx_t, ptp, pte;
   // env control
-  DBuf<int> e_status, e_reason, e_step, e_constrained, e_bad, e_nanp, e_halv, e_newton_it, e_count;
-  DBuf<uint8_t> e_stepping, e_iter, e_ls, e_accept, e_sel, e_all;
+  DBuf<int> e_status, e_reason, e_step, e_constrained, e_bad, e_nanp, e_halv, e_newton_it, e_count, e_rem;
+  DBuf<uint8_t> e_stepping, e_iter, e_ls, e_accept, e_sel, e_all, e_start, e_cover;
   DBuf<double> e_E0, e_Et, e_alpha;
   DBuf<unsigned long long> e_alpha_bits, e_pnorm_bits, e_inter, e_inv;
   DBuf<long long> e_stats;
@@ -472,11 +472,14 @@ struct ipc_scene {
     bool built = false;
   } ttri, tedge;
   // candidates / contacts
-  DBuf<int> cnt_pt, off_pt, cnt_ee, off_ee, cand_j, nflag, noff, scan_tmp, overflow;
-  DBuf<int> ccd_cnt_pt, ccd_off_pt, ccd_cnt_ee, ccd_off_ee, ccd_j;  // swept-box candidates
+  DBuf<int> cnt_pt, off_pt, cnt_ee, off_ee, cand_j, cand_q, nflag, noff, scan_tmp, overflow;
+  DBuf<int> ccd_cnt_pt, ccd_off_pt, ccd_cnt_ee, ccd_off_ee, ccd_j, ccd_q;  // swept-box candidates
   DBuf<int> slots_pt, slots_ee;  // partner slots of collect traversals (CAND_CAP per query)
   DBuf<ContactRec> ct_tmp, ct;
-  DBuf<FrictionRec> fr;
+  DBuf<FrictionRec> fr, fr_new, fr_tmp;
+  DBuf<unsigned long long> fr_keys, fr_keys2;
+  DBuf<unsigned> fr_vals, fr_vals2;
+  DBuf<int> fr_hist;
   int n_pt = 0, n_ee = 0, n_ct = 0, n_ct_pt = 0, n_fr = 0, n_fr_pt = 0, n_inc = 0;
   DBuf<int> st_pts, st_env, st_cnt, st_off, ns_ptr, ns_src, ns_cnt;
   DBuf<unsigned long long> st_keys, st_keys2;
@@ -579,6 +582,11 @@ struct ipc_scene {
     else ++launches;
     CK(cudaGetLastError());
   }
+  void read_ints(const int* dptr, int* out, int n) {
+    CK(cudaMemcpyAsync(hpin, dptr, n * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    for (int i = 0; i < n; ++i) out[i] = hpin[i];
+  }
   int read_int(const int* dptr) {
     CK(cudaMemcpyAsync(hpin, dptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
@@ -628,7 +636,7 @@ struct ipc_scene {
   EnvCtl ctl() {
     return EnvCtl{e_status.p, e_reason.p, e_step.p, nsteps.p, e_stepping.p, e_iter.p, e_ls.p, e_accept.p,
                   e_constrained.p, e_bad.p, e_nanp.p, e_halv.p, e_newton_it.p, e_E0.p, e_Et.p, e_alpha.p,
-                  e_alpha_bits.p, e_pnorm_bits.p, e_stats.p, e_count.p};
+                  e_alpha_bits.p, e_pnorm_bits.p, e_stats.p, e_count.p, e_rem.p};
   }
   Sched sched_view() const {
     return Sched{sched.p, grav.p, sched_off.p, grav_off.p, nh.p, node_handle.p, X0.p};
@@ -978,6 +986,8 @@ struct ipc_scene {
     for (DBuf<double>* b : {&xt, &xtilde, &xtarget, &xtrial, &p, &pbar, &grad, &pcg_r, &pcg_z, &pcg_d, &pcg_y, &pcg_x})
       b->alloc(n3);
     xtarget.zero(s);
+    // trial points are written only for envs in a line search: start them at x
+    CK(cudaMemcpyAsync(xtrial.p, x.p, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     // the persistent PCG never writes kinematic soft rows: their d (read by neighbours) stays 0
     for (DBuf<double>* b : {&pcg_r, &pcg_z, &pcg_d, &pcg_y, &pcg_x}) b->zero(s);
     for (DBuf<double>* b : {&ptx, &ptx_t, &ptp, &pte}) b->alloc(3 * (size_t)NP);
@@ -985,9 +995,9 @@ struct ipc_scene {
     e_reason.upload(reason_h, s);
     e_step.upload(step_h, s);
     e_stats.upload(stats_h, s);
-    for (DBuf<int>* b : {&e_constrained, &e_bad, &e_nanp, &e_halv, &e_newton_it}) b->alloc(E);
+    for (DBuf<int>* b : {&e_constrained, &e_bad, &e_nanp, &e_halv, &e_newton_it, &e_rem}) b->alloc(E);
     e_count.alloc(4);
-    for (DBuf<uint8_t>* b : {&e_stepping, &e_iter, &e_ls, &e_accept, &e_sel, &e_all}) {
+    for (DBuf<uint8_t>* b : {&e_stepping, &e_iter, &e_ls, &e_accept, &e_sel, &e_all, &e_start, &e_cover}) {
       b->alloc(E);
       b->zero(s);
     }
@@ -1135,34 +1145,35 @@ struct ipc_scene {
     const bool spilled = collect_spilled();
     int nc = n_pt + n_ee;
     cand_j.ensure(nc + 1);
+    cand_q.ensure(nc + 1);
     if (spilled) {
-      CandOut f{nullptr, off_pt.p, cand_j.p, overflow.p};
+      CandOut f{nullptr, off_pt.p, cand_j.p, overflow.p, 0, cand_q.p};
       launch(k_trav_pt<TRAV_FILL>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
              (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), f, (const double*)nullptr, ctl());
-      CandOut fe{nullptr, off_ee.p, cand_j.p + n_pt, overflow.p};
+      CandOut fe{nullptr, off_ee.p, cand_j.p + n_pt, overflow.p, 0, cand_q.p + n_pt};
       launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
              (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr,
              ctl());
     } else {
       launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)cnt_pt.p, (const int*)slots_pt.p,
-             (const int*)off_pt.p, cand_j.p, 1);
+             (const int*)off_pt.p, cand_j.p, cand_q.p, 1);
       launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)cnt_ee.p, (const int*)slots_ee.p,
-             (const int*)off_ee.p, cand_j.p + n_pt, 1);
+             (const int*)off_ee.p, cand_j.p + n_pt, cand_q.p + n_pt, 1);
     }
-    contacts_from_list(nullptr, n_pt, n_ee, off_pt.p, off_ee.p, cand_j.p);
+    contacts_from_list(nullptr, n_pt, n_ee, cand_q.p, cand_j.p);
   }
   // Narrow phase over a candidate list (point-triangle per surface vertex, then edge-edge per
   // edge, partners ascending): contacts d < dhat at positions ptx, in list order. act (or null)
   // keeps only the envs of this evaluation when the list holds more.
-  void contacts_from_list(const uint8_t* act, int np, int ne, const int* offp, const int* offe, const int* cj) {
+  void contacts_from_list(const uint8_t* act, int np, int ne, const int* cq, const int* cj) {
     const int nc = np + ne;
     nflag.ensure(nc + 1);
     noff.ensure(nc + 1);
     ct_tmp.ensure(nc + 1);
     double dh2 = desc.dhat * desc.dhat;
-    launch(k_narrow, nc, 128, np, ne, offp, NSV, offe, NED, cj, (const int*)sv_pt.p, (const int*)sv_env.p,
-           (const int*)tri_pt.p, (const int*)ed_pt.p, (const int*)ed_env.p, (const double*)ptx.p, dh2, nflag.p,
-           ct_tmp.p, (const double*)ed_rest2.p, act);
+    launch(k_narrow, nc, 128, np, ne, cq, cj, (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p,
+           (const int*)ed_pt.p, (const int*)ed_env.p, (const double*)ptx.p, dh2, nflag.p, ct_tmp.p,
+           (const double*)ed_rest2.p, act);
     n_ct = scan(nflag.p, nc, noff.p);
     n_ct_pt = np > 0 ? read_int(noff.p + np) : 0;
     ct.ensure(n_ct + 1);
@@ -1182,8 +1193,8 @@ struct ipc_scene {
   bool reuse_lists() const { return desc.fresh_broad_phase == 0; }
   double swept_growth() const { return reuse_lists() ? 0.5 * desc.dhat * (1.0 + 1e-6) : 0.0; }
   void contacts_at(const uint8_t* act) {
-    if (cand_src == CAND_SWEPT) contacts_from_list(act, ccd_np, ccd_ne, ccd_off_pt.p, ccd_off_ee.p, ccd_j.p);
-    else if (cand_src == CAND_STATIC) contacts_from_list(act, n_pt, n_ee, off_pt.p, off_ee.p, cand_j.p);
+    if (cand_src == CAND_SWEPT) contacts_from_list(act, ccd_np, ccd_ne, ccd_q.p, ccd_j.p);
+    else if (cand_src == CAND_STATIC) contacts_from_list(act, n_pt, n_ee, cand_q.p, cand_j.p);
     else constraint_set(act);
   }
   void stencil_table() {
@@ -1277,15 +1288,15 @@ struct ipc_scene {
     if (mixed()) {
       f_ns_w.ensure(ne + 1);
       f_ns_xb.ensure(3 * (size_t)ne + 3);
-      launch(k_entry_weights<float>, NN, 256, NN, layout(), act, (const int*)ns_ptr.p, (const int*)ns_src.p,
-             (const int*)st_pts.p, f_ns_w.p, f_ns_xb.p);
+      launch(k_entry_weights<float>, ne, 256, ne, layout(), act, (const unsigned long long*)st_keys.p,
+             (const int*)ns_src.p, (const int*)st_pts.p, f_ns_w.p, f_ns_xb.p);
       launch(k_stencil_nodes<float>, 4L * ns, 256, ns, layout(), (const int*)st_pts.p, (const int*)st_env.p, act,
              st_node.p, f_st_xb.p);
     } else {
       ns_w.ensure(ne + 1);
       ns_xb.ensure(3 * (size_t)ne + 3);
-      launch(k_entry_weights<double>, NN, 256, NN, layout(), act, (const int*)ns_ptr.p, (const int*)ns_src.p,
-             (const int*)st_pts.p, ns_w.p, ns_xb.p);
+      launch(k_entry_weights<double>, ne, 256, ne, layout(), act, (const unsigned long long*)st_keys.p,
+             (const int*)ns_src.p, (const int*)st_pts.p, ns_w.p, ns_xb.p);
       launch(k_stencil_nodes<double>, 4L * ns, 256, ns, layout(), (const int*)st_pts.p, (const int*)st_env.p, act,
              st_node.p, st_xb.p);
     }
@@ -1586,8 +1597,8 @@ struct ipc_scene {
     launch(k_precond_soft<HT>, NN, 256, NN, layout(), act, (const long*)diag_pos.p, (const HT*)val,
            (const int*)ns_ptr.p, (const int*)ns_src.p, sHp, hp<HT>(Ps, f_Ps));
     launch_grid(k_precond_body<HT>, NB, 144, NB, layout(), (const int*)body_env.p, act,
-                (const HT*)hp<HT>(body_H, f_body_H), (const int*)ns_ptr.p, (const int*)ns_src.p, (const int*)st_pts.p,
-                sHp, hp<HT>(Pb, f_Pb));
+                (const HT*)hp<HT>(body_H, f_body_H), (const int*)ns_ptr.p, (const int*)ns_src.p,
+                (const HT*)hp<HT>(ns_xb, f_ns_xb), sHp, hp<HT>(Pb, f_Pb));
   }
   // r = -g - H pbar in the solve's precision, for the envs in act
   void rhs(const uint8_t* act) {
@@ -1625,8 +1636,7 @@ struct ipc_scene {
 
   // CCD step filter on the envs still iterating: swept-box candidates at [x, x + p] (boxes
   // already refit), then additive CCD per candidate pair; each env's alpha_max is the minimum
-  void ccd_filter(EnvCtl C) {
-    const uint8_t* act = e_iter.p;
+  void ccd_filter(EnvCtl C, const uint8_t* act) {
     ccd_cnt_pt.ensure(NSV + 1);
     ccd_off_pt.ensure(NSV + 1);
     ccd_cnt_ee.ensure(NED + 1);
@@ -1650,66 +1660,146 @@ struct ipc_scene {
     ccd_ne = ne;
     if (np + ne == 0) return;
     ccd_j.ensure(np + ne + 1);
+    ccd_q.ensure(np + ne + 1);
     if (spilled && keep) {
-      CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p};
+      CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p, 0, ccd_q.p};
       launch(k_trav_pt<TRAV_FILL>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
              (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
              (const double*)nullptr, C);
-      CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p};
+      CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p, 0, ccd_q.p + np};
       launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
              (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr,
              C);
     } else if (spilled) {
-      CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p};
+      CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p, 0, ccd_q.p};
       launch(k_trav_pt<TRAV_FILLU>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
              (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
              (const double*)nullptr, C);
-      CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p};
+      CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p, 0, ccd_q.p + np};
       launch(k_trav_ee<TRAV_FILLU>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
              (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr,
              C);
     } else {
       launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)ccd_cnt_pt.p, (const int*)slots_pt.p,
-             (const int*)ccd_off_pt.p, ccd_j.p, keep ? 1 : 0);
+             (const int*)ccd_off_pt.p, ccd_j.p, ccd_q.p, keep ? 1 : 0);
       launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)ccd_cnt_ee.p, (const int*)slots_ee.p,
-             (const int*)ccd_off_ee.p, ccd_j.p + np, keep ? 1 : 0);
+             (const int*)ccd_off_ee.p, ccd_j.p + np, ccd_q.p + np, keep ? 1 : 0);
     }
-    launch(k_accd_pairs, np + ne, 128, np, ne, (const int*)ccd_off_pt.p, NSV, (const int*)ccd_off_ee.p, NED,
-           (const int*)ccd_j.p, (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p,
+    launch(k_accd_pairs, np + ne, 128, np, ne, (const int*)ccd_q.p, (const int*)ccd_j.p, (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p,
            (const int*)ed_env.p, (const double*)ptx.p, (const double*)ptp.p, keep ? (const double*)pte.p : nullptr,
            C);
   }
 
-  void newton_step() {
+  // ------------------------------------------------------------------ time stepping
+  // Every env of the scene advances n time steps (fewer where its schedule ends or it fails),
+  // each at its own pace (Sec. III-A: every environment keeps its own Newton loop and stopping
+  // test). A round runs one Newton iteration of every env inside a step; an env whose Newton
+  // loop stopped ends its step in that round and starts its next step in the following round,
+  // so the batch stays full while slow envs iterate. Each env goes through exactly the
+  // operations of stepping it alone, in the same order: its results do not depend on the batch.
+  void run_steps(int n) {
+    if (n <= 0) return;
     EnvCtl C = ctl();
-    launch(k_env_begin_step, E, 128, E, C);
-    if (count_flags(e_stepping.p) == 0) return;
-    step_setup(e_stepping.p);
-    if (reuse_lists()) cand_src = CAND_STATIC;  // the first Newton iteration evaluates at x^t
-    for (int it = 0; it < desc.max_newton; ++it) {
-      if (count_flags(e_iter.p) == 0) break;
-      launch(k_env_iter_begin, E, 128, E, C);
-      evaluate<MODE_HESS>(x.p, e_iter.p, e_E0.p);
-      assemble(e_iter.p);
-      // kinematic step and the reduced right-hand side -g - H pbar
-      launch(k_pbar, NN, 256, NN, layout(), C, (const double*)x.p, (const double*)xtarget.p, pbar.p);
-      matvec(e_iter.p, pbar.p, pcg_y.p, part_a.p);
-      rhs(e_iter.p);
-      pcg(e_iter.p);
-      direction(C);
-      launch(k_env_converge, E, 128, E, C, desc.dt, desc.newton_tol);
-      if (count_flags(e_iter.p) == 0) break;
-      // CCD step filter: swept candidates at [x, x + p], ACCD, per-env minimum
+    launch(k_env_call_begin, E, 128, E, C, n);
+    cand_src = CAND_FRESH;
+    const long max_rounds = (long)n * (desc.max_newton + 1) + 1;
+    for (long round = 0;; ++round) {
+      launch_grid(k_env_round_begin, 1, 256, E, C, e_start.p);
+      int cnt[2];
+      read_ints(e_count.p, cnt, 2);  // [starting, iterating]
+      if (cnt[1] == 0) break;
+      if (round > max_rounds) fail_with(IPC_ERR_INTERNAL, "time stepping did not finish");
+      if (cnt[0] > 0) step_start(e_start.p);
+      newton_round(C);
+      // the envs whose Newton loop stopped this round end their step
+      launch(k_end_step_nodes, NN, 256, NN, layout(), C, desc.dt, (const double*)x.p, (const double*)xt.p, v.p);
+      launch(k_env_end_step, E, 128, E, C);
+    }
+    cand_src = CAND_FRESH;
+    CK(cudaStreamSynchronize(stream));
+  }
+  // Step set-up of the envs in start: x^t, x~, targets, positions and contacts at x^t, the
+  // friction lag. Their contacts come from the previous round's swept candidates, which cover
+  // x^t (an env done with a step stays at its last point); in a call's first round, from a
+  // traversal (then every iterating env is a starting one).
+  int since_build = 0;  // rounds since the trees' topology was last built
+  void step_start(const uint8_t* start) {
+    launch(k_step_setup_nodes, NN, 256, NN, layout(), ctl(), start, sched_view(), desc.dt, desc.gravity[0],
+           desc.gravity[1], desc.gravity[2], (const double*)x.p, (const double*)v.p, xt.p, xtilde.p, xtarget.p);
+    launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p,
+           (const double*)x.p, ptx.p);
+    if (cand_src == CAND_SWEPT) {
+      contacts_from_list(start, ccd_np, ccd_ne, ccd_q.p, ccd_j.p);
+    } else {
+      build_trees();
+      since_build = 0;
+      constraint_set(start);
+      if (reuse_lists()) cand_src = CAND_STATIC;  // this round's evaluations are at x^t
+    }
+    launch(k_copy_points_env, NP, 256, NP, layout(), start, (const double*)ptx.p, ptx_t.p);
+    friction_merge(start);
+  }
+  // lagged friction records of the starting envs from their contacts at x^t (ct), merged with
+  // the records of the envs that stay inside their step; every sublist stays env-sorted
+  void friction_merge(const uint8_t* start) {
+    const int n_new = n_ct, n_new_pt = n_ct_pt, n_old = n_fr, n_old_pt = n_fr_pt, tot = n_old + n_new;
+    fr_new.ensure(n_new + 1);
+    launch(k_friction_setup, n_new, 128, n_new, (const ContactRec*)ct.p, (const double*)ptx.p,
+           (const double*)env_mu.p, desc.dhat, desc.kappa, fr_new.p);
+    if (tot == 0) {
+      n_fr = n_fr_pt = 0;
+      return;
+    }
+    fr_keys.ensure(tot);
+    fr_vals.ensure(tot);
+    CK(cudaMemsetAsync(e_count.p + 2, 0, 2 * sizeof(int), stream));
+    launch(k_fr_keys, tot, 256, n_old, n_old_pt, (const FrictionRec*)fr.p, n_new, n_new_pt,
+           (const FrictionRec*)fr_new.p, (const uint8_t*)e_stepping.p, start, fr_keys.p, fr_vals.p, e_count.p + 2);
+    radix_sort(fr_keys, fr_vals, fr_keys2, fr_vals2, fr_hist, tot, 34);
+    int c[2];
+    read_ints(e_count.p + 2, c, 2);  // [kept point-triangle, kept]
+    fr_tmp.ensure(c[1] + 1);
+    launch(k_fr_gather, c[1], 256, c[1], (const unsigned*)fr_vals.p, n_old, (const FrictionRec*)fr.p,
+           (const FrictionRec*)fr_new.p, fr_tmp.p);
+    std::swap(fr.p, fr_tmp.p);
+    std::swap(fr.n, fr_tmp.n);
+    n_fr = c[1];
+    n_fr_pt = c[0];
+  }
+  // one Newton iteration of every iterating env
+  void newton_round(EnvCtl C) {
+    launch(k_env_iter_begin, E, 128, E, C);
+    evaluate<MODE_HESS>(x.p, e_iter.p, e_E0.p);
+    assemble(e_iter.p);
+    // kinematic step and the reduced right-hand side -g - H pbar
+    launch(k_pbar, NN, 256, NN, layout(), C, (const double*)x.p, (const double*)xtarget.p, pbar.p);
+    matvec(e_iter.p, pbar.p, pcg_y.p, part_a.p);
+    rhs(e_iter.p);
+    pcg(e_iter.p);
+    direction(C);
+    launch(k_env_converge, E, 128, E, C, desc.dt, desc.newton_tol);
+    launch_grid(k_env_cover, 1, 256, E, C, e_cover.p);
+    int cnt[2];
+    read_ints(e_count.p, cnt, 2);  // [iterating, covered]
+    if (cnt[1] > 0) {
+      // CCD step filter: swept candidates at [x, x + p] (also for the envs that start their next
+      // step next round: the segment starts at their point), ACCD and per-env minimum
       launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p,
              (const double*)x.p, ptx.p);
       launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p,
              (const double*)p.p, ptp.p);
       launch(k_add_vec, 3L * NP, 256, 3L * NP, (const double*)ptx.p, (const double*)ptp.p, pte.p);
+      if (since_build >= TREE_REBUILD_ROUNDS) {  // refits keep the trees valid; a rebuild keeps them tight
+        build_trees();
+        since_build = 0;
+      }
       boxes_and_refit(pte.p, swept_growth());
       pbeg(IPC_PROF_CCD);
-      ccd_filter(C);
+      ccd_filter(C, e_cover.p);
       pend(IPC_PROF_CCD);
-      if (reuse_lists()) cand_src = CAND_SWEPT;  // the trials and the next iteration's point
+      if (reuse_lists()) cand_src = CAND_SWEPT;  // the trials and the next round's points
+    }
+    if (cnt[0] > 0) {
       // backtracking line search on the envs still iterating
       launch(k_env_ls_begin, E, 128, E, C);
       for (int ls = 0; ls <= desc.max_ls_halvings + 1; ++ls) {
@@ -1719,13 +1809,11 @@ struct ipc_scene {
         if (count_flags(e_ls.p) == 0) break;
       }
       launch(k_accept, NN, 256, NN, layout(), C, (const double*)xtrial.p, (const double*)xtarget.p, x.p);
-      launch(k_env_newton_end, E, 128, E, C, desc.max_newton);
     }
-    cand_src = CAND_FRESH;
-    launch(k_end_step_nodes, NN, 256, NN, layout(), C, desc.dt, (const double*)x.p, (const double*)xt.p, v.p);
-    launch(k_env_end_step, E, 128, E, C);
-    CK(cudaStreamSynchronize(stream));
+    launch(k_env_newton_end, E, 128, E, C, desc.max_newton);
+    ++since_build;
   }
+  static constexpr int TREE_REBUILD_ROUNDS = 16;
 
   // ------------------------------------------------------------------ validation / queries
   void invariants(const uint8_t* act, const double* q) {
@@ -1888,7 +1976,7 @@ ipc_status ipc_step(ipc_scene* s, int32_t n_steps) {
   if (!s || n_steps < 0) fail_with(IPC_ERR_ARG, "bad argument");
   CK(cudaSetDevice(s->device));
   s->commit();
-  for (int i = 0; i < n_steps; ++i) s->newton_step();
+  s->run_steps(n_steps);
   API_END
 }
 

@@ -33,6 +33,7 @@ struct EnvCtl {
   unsigned long long* pnorm_bits;
   long long* stats;    // 5 per env
   int* flag_count;
+  int* rem;            // time steps left in the current ipc_step call
 };
 
 struct Sched {
@@ -153,16 +154,16 @@ __global__ void k_direction(int n_nodes, Layout L, EnvCtl C, const VT* __restric
   if (isfinite(m)) atomic_max_pos(&C.pnorm_bits[e], m);
 }
 
+// trial point x + alpha p of the envs still searching; an env that has accepted keeps its
+// accepted trial point while the others go on halving
 __global__ void k_trial(int n_nodes, Layout L, EnvCtl C, const double* __restrict__ x, const double* __restrict__ p,
                         double* __restrict__ xtr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
   int e = L.node_env[i];
-  double a = C.ls[e] ? C.alpha[e] : 0.0;
-  for (int k = 0; k < 3; ++k) {
-    double xv = x[3L * i + k];
-    xtr[3L * i + k] = C.ls[e] ? xv + a * p[3L * i + k] : xv;
-  }
+  if (!C.ls[e]) return;
+  const double a = C.alpha[e];
+  for (int k = 0; k < 3; ++k) xtr[3L * i + k] = x[3L * i + k] + a * p[3L * i + k];
 }
 
 __global__ void k_accept(int n_nodes, Layout L, EnvCtl C, const double* __restrict__ xtr,
@@ -182,18 +183,57 @@ __global__ void k_end_step_nodes(int n_nodes, Layout L, EnvCtl C, double h, cons
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
   int e = L.node_env[i];
-  if (!C.stepping[e] || C.status[e] != ST_ACTIVE) return;
+  if (!C.stepping[e] || C.iter[e] || C.status[e] != ST_ACTIVE) return;
   for (int k = 0; k < 3; ++k) v[3L * i + k] = (x[3L * i + k] - xt[3L * i + k]) / h;
 }
 
 // ---------------------------------------------------------------- per-env control
-__global__ void k_env_begin_step(int n_env, EnvCtl C) {
+// Continuous stepping: within one ipc_step call every env runs its time steps at its own pace.
+// A round is one Newton iteration of every env inside a step; an env whose Newton loop stopped
+// ends its step in that round and starts the next one in the following round.
+__global__ void k_env_call_begin(int n_env, EnvCtl C, int n_steps) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_env) return;
-  bool go = C.status[e] == ST_ACTIVE && C.step[e] < C.nsteps[e];
-  C.stepping[e] = go;
-  C.iter[e] = go;
-  C.newton_it[e] = 0;
+  C.rem[e] = n_steps;
+  C.stepping[e] = 0;
+  C.iter[e] = 0;
+}
+// envs that start a time step this round (not inside one, active, schedule and call budget
+// left); counts of [starting, iterating] envs go to C.flag_count[0..1]
+__global__ void k_env_round_begin(int n_env, EnvCtl C, uint8_t* __restrict__ start) {
+  __shared__ int cnt[2];
+  if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < n_env; e += blockDim.x) {
+    bool go = !C.stepping[e] && C.status[e] == ST_ACTIVE && C.step[e] < C.nsteps[e] && C.rem[e] > 0;
+    start[e] = go;
+    if (go) {
+      C.stepping[e] = 1;
+      C.iter[e] = 1;
+      C.newton_it[e] = 0;
+      atomicAdd(&cnt[0], 1);
+    }
+    if (C.iter[e]) atomicAdd(&cnt[1], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) C.flag_count[threadIdx.x] = cnt[threadIdx.x];
+}
+// after the convergence test: envs whose contacts the next round takes from this round's
+// swept candidates (still iterating, or done with this step and starting another in this call);
+// counts of [iterating, covered] envs go to C.flag_count[0..1]
+__global__ void k_env_cover(int n_env, EnvCtl C, uint8_t* __restrict__ cover) {
+  __shared__ int cnt[2];
+  if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < n_env; e += blockDim.x) {
+    bool next = C.stepping[e] && !C.iter[e] && C.status[e] == ST_ACTIVE && C.rem[e] > 1 && C.step[e] + 1 < C.nsteps[e];
+    bool c = C.iter[e] || next;
+    cover[e] = c;
+    if (C.iter[e]) atomicAdd(&cnt[0], 1);
+    if (c) atomicAdd(&cnt[1], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) C.flag_count[threadIdx.x] = cnt[threadIdx.x];
 }
 __global__ void k_env_iter_begin(int n_env, EnvCtl C) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -266,12 +306,16 @@ __global__ void k_env_newton_end(int n_env, EnvCtl C, int max_newton) {
     C.reason[e] = FAIL_NEWTON;
   }
 }
+// the envs inside a step whose Newton loop stopped leave the step; the active ones count it
 __global__ void k_env_end_step(int n_env, EnvCtl C) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_env) return;
-  if (!C.stepping[e] || C.status[e] != ST_ACTIVE) return;
+  if (!C.stepping[e] || C.iter[e]) return;
+  C.stepping[e] = 0;
+  if (C.status[e] != ST_ACTIVE) return;
   int s = C.step[e] + 1;
   C.step[e] = s;
+  C.rem[e] -= 1;
   C.stats[5 * e + STAT_STEPS] += 1;
   if (s >= C.nsteps[e]) C.status[e] = ST_DONE;
 }
@@ -347,6 +391,7 @@ struct CandOut {
   int* cj;         // candidate partner (fill mode), or cap slots per query (collect mode)
   int* overflow;   // [0]: traversal stack overflow, [1]: a query found more than cap (collect)
   int cap = 0;
+  int* cq = nullptr;  // fill modes: the query of each candidate (beside cj), or null
 };
 
 // point-triangle candidates: surface vertex q against the triangle tree of its env
@@ -382,7 +427,10 @@ __global__ void k_trav_pt(int n_sv, const int* __restrict__ sv_pt, const int* __
     int a = tri_pt[3 * j], b = tri_pt[3 * j + 1], c = tri_pt[3 * j + 2];
     if (a == v || b == v || c == v) return;
     if (excluded(P, v, a, b, c)) return;
-    if (MODE == TRAV_FILL || MODE == TRAV_FILLU) O.cj[base + count] = j;
+    if (MODE == TRAV_FILL || MODE == TRAV_FILLU) {
+      O.cj[base + count] = j;
+      if (O.cq) O.cq[base + count] = q;
+    }
     if (MODE == TRAV_COLLECT && count < O.cap) O.cj[(long)q * O.cap + count] = j;
     if (MODE == TRAV_CCD) {
       d3 X[4] = {ld3(ptx, v), ld3(ptx, a), ld3(ptx, b), ld3(ptx, c)};
@@ -437,7 +485,10 @@ __global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __
     int b0 = ed_pt[2 * j], b1 = ed_pt[2 * j + 1];
     if (a0 == b0 || a0 == b1 || a1 == b0 || a1 == b1) return;
     if (excluded(P, a0, a1, b0, b1)) return;
-    if (MODE == TRAV_FILL || MODE == TRAV_FILLU) O.cj[base + count] = j;
+    if (MODE == TRAV_FILL || MODE == TRAV_FILLU) {
+      O.cj[base + count] = j;
+      if (O.cq) O.cq[base + count] = q;
+    }
     if (MODE == TRAV_COLLECT && count < O.cap) O.cj[(long)q * O.cap + count] = j;
     if (MODE == TRAV_CCD) {
       d3 X[4] = {ld3(ptx, a0), ld3(ptx, a1), ld3(ptx, b0), ld3(ptx, b1)};
@@ -469,29 +520,18 @@ __global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __
   }
 }
 
-// candidate i (global over PT then EE) -> its query index (upper bound search in offsets)
-DEV int cand_query(const int* __restrict__ off, int nq, int i) {
-  int lo = 0, hi = nq;  // find q with off[q] <= i < off[q+1]
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= i) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-// narrow phase: keep the candidates with d^2 < dhat^2 (flag), typed for the stencils
-__global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ off_pt, int n_sv, const int* __restrict__ off_ee,
-                         int n_ed, const int* __restrict__ cj, const int* __restrict__ sv_pt,
-                         const int* __restrict__ sv_env, const int* __restrict__ tri_pt, const int* __restrict__ ed_pt,
-                         const int* __restrict__ ed_env, const double* __restrict__ ptx, double dhat2,
-                         int* __restrict__ flag, ContactRec* __restrict__ tmp, const double* __restrict__ ed_rest2,
-                         const uint8_t* __restrict__ act) {
+// narrow phase: keep the candidates with d^2 < dhat^2 (flag), typed for the stencils; the
+// record of a kept candidate goes to tmp[i]. cq[i] is the query of candidate i.
+__global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ cq, const int* __restrict__ cj,
+                         const int* __restrict__ sv_pt, const int* __restrict__ sv_env, const int* __restrict__ tri_pt,
+                         const int* __restrict__ ed_pt, const int* __restrict__ ed_env, const double* __restrict__ ptx,
+                         double dhat2, int* __restrict__ flag, ContactRec* __restrict__ tmp,
+                         const double* __restrict__ ed_rest2, const uint8_t* __restrict__ act) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_pt + n_ee) return;
   ContactRec c;
   if (i < n_pt) {
-    int q = cand_query(off_pt, n_sv, i);
+    int q = cq[i];
     int j = cj[i];
     c.kind = 0;
     c.pts[0] = sv_pt[q];
@@ -501,8 +541,7 @@ __global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ off_pt, int
     c.env = sv_env[q];
     c.eps_x = 0.0;
   } else {
-    int k = i - n_pt;
-    int q = cand_query(off_ee, n_ed, k);
+    int q = cq[i];
     int j = cj[i];
     c.kind = 1;
     c.pts[0] = ed_pt[2 * q];
@@ -519,24 +558,48 @@ __global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ off_pt, int
   }
   d3 X[4];
   for (int k = 0; k < 4; ++k) X[k] = ld3(ptx, c.pts[k]);
+  // a pair whose boxes are more than dhat apart along an axis is no contact: tested before
+  // the distance, with a margin far above the rounding of the box differences
+  const double gap = sqrt(dhat2) * (1.0 + 1e-9);
+  const int na = c.kind == 0 ? 1 : 2;
+  double ga[3] = {X[0].x, X[0].y, X[0].z}, gb[3] = {X[na].x, X[na].y, X[na].z};
+  double ha[3] = {ga[0], ga[1], ga[2]}, hb[3] = {gb[0], gb[1], gb[2]};
+  for (int k = 1; k < 4; ++k) {
+    const double u[3] = {X[k].x, X[k].y, X[k].z};
+    double* lo = k < na ? ga : gb;
+    double* hi = k < na ? ha : hb;
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fmin(lo[a], u[a]);
+      hi[a] = fmax(hi[a], u[a]);
+    }
+  }
+  for (int a = 0; a < 3; ++a)
+    if (gb[a] - ha[a] > gap || ga[a] - hb[a] > gap) {
+      flag[i] = 0;
+      return;
+    }
   int type;
   double d2 = pair_d2(c.kind, X, &type);
   c.type = type;
-  tmp[i] = c;
-  flag[i] = d2 < dhat2 ? 1 : 0;
+  const bool keep = d2 < dhat2;
+  if (keep) tmp[i] = c;
+  flag[i] = keep ? 1 : 0;
 }
 
 // Candidates of a collect traversal to their final places: query q's partners (at most cap,
 // in its slots) go to out[off[q] ...], sorted ascending when `sorted` (the fill mode's order).
 __global__ void k_gather_cands(int nq, int cap, const int* __restrict__ cnt, const int* __restrict__ slots,
-                               const int* __restrict__ off, int* __restrict__ out, int sorted) {
+                               const int* __restrict__ off, int* __restrict__ out, int* __restrict__ out_q, int sorted) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
   const int n = cnt[q];
   if (n == 0) return;
   int* o = out + off[q];
   const int* sl = slots + (long)q * cap;
-  for (int i = 0; i < n; ++i) o[i] = sl[i];
+  for (int i = 0; i < n; ++i) {
+    o[i] = sl[i];
+    out_q[off[q] + i] = q;
+  }
   if (!sorted) return;
   for (int i = 1; i < n; ++i) {
     int key = o[i], k = i - 1;
@@ -569,8 +632,7 @@ DEV void swept_box(const double* __restrict__ ptx, const double* __restrict__ pt
 // (an atomic minimum on non-negative doubles: exact and independent of order). When the
 // candidates were gathered with grown boxes (pte given), a pair whose plain swept boxes do
 // not overlap is skipped, so the set of tested pairs is the plain swept-box set.
-__global__ void k_accd_pairs(int n_pt, int n_ee, const int* __restrict__ off_pt, int n_sv,
-                             const int* __restrict__ off_ee, int n_ed, const int* __restrict__ cj,
+__global__ void k_accd_pairs(int n_pt, int n_ee, const int* __restrict__ cq, const int* __restrict__ cj,
                              const int* __restrict__ sv_pt, const int* __restrict__ sv_env,
                              const int* __restrict__ tri_pt, const int* __restrict__ ed_pt,
                              const int* __restrict__ ed_env, const double* __restrict__ ptx,
@@ -579,7 +641,7 @@ __global__ void k_accd_pairs(int n_pt, int n_ee, const int* __restrict__ off_pt,
   if (i >= n_pt + n_ee) return;
   int kind, e, pts[4];
   if (i < n_pt) {
-    int q = cand_query(off_pt, n_sv, i), j = cj[i];
+    int q = cq[i], j = cj[i];
     kind = 0;
     e = sv_env[q];
     pts[0] = sv_pt[q];
@@ -587,8 +649,7 @@ __global__ void k_accd_pairs(int n_pt, int n_ee, const int* __restrict__ off_pt,
     pts[2] = tri_pt[3 * j + 1];
     pts[3] = tri_pt[3 * j + 2];
   } else {
-    int k = i - n_pt;
-    int q = cand_query(off_ee, n_ed, k), j = cj[i];
+    int q = cq[i], j = cj[i];
     kind = 1;
     e = ed_env[q];
     pts[0] = ed_pt[2 * q];
@@ -596,6 +657,7 @@ __global__ void k_accd_pairs(int n_pt, int n_ee, const int* __restrict__ off_pt,
     pts[2] = ed_pt[2 * j];
     pts[3] = ed_pt[2 * j + 1];
   }
+  if (!C.iter[e]) return;  // an env covered for its next step only needs the candidates
   if (pte) {
     const int na = kind == 0 ? 1 : 2;
     double ba[6], bb[6];
@@ -707,6 +769,48 @@ __global__ void k_stencil_emit(int n_st, const int* __restrict__ st_pts, const i
 __global__ void k_count_keys(int n, const unsigned long long* __restrict__ keys, int* __restrict__ cnt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) atomicAdd(&cnt[keys[i]], 1);
+}
+
+// ---------------------------------------------------------------- per-env step start
+// positions of the points of the envs in act, src -> dst
+__global__ void k_copy_points_env(int n_pts, Layout L, const uint8_t* __restrict__ act, const double* __restrict__ src,
+                                  double* __restrict__ dst) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_pts) return;
+  int nd = L.pt_node[q];
+  int e = L.node_env[nd >= 0 ? nd : L.body_node[-1 - nd]];
+  if (!act[e]) return;
+  for (int k = 0; k < 3; ++k) dst[3L * q + k] = src[3L * q + k];
+}
+// Friction records after some envs started a step: the old records of the envs that stay
+// inside their step, and the new records of the starting envs, keyed (kind, env) for a stable
+// sort that keeps each env's records in their order; dropped records sort last.
+__global__ void k_fr_keys(int n_old, int n_old_pt, const FrictionRec* __restrict__ old_fr, int n_new, int n_new_pt,
+                          const FrictionRec* __restrict__ new_fr, const uint8_t* __restrict__ stepping,
+                          const uint8_t* __restrict__ start, unsigned long long* __restrict__ keys,
+                          unsigned* __restrict__ vals, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_old + n_new) return;
+  unsigned long long key;
+  if (i < n_old) {
+    int e = old_fr[i].env;
+    bool keep = stepping[e] && !start[e];
+    key = keep ? ((unsigned long long)(i >= n_old_pt) << 32) | (unsigned)e : (2ull << 32);
+  } else {
+    int j = i - n_old;
+    key = ((unsigned long long)(j >= n_new_pt) << 32) | (unsigned)new_fr[j].env;
+  }
+  keys[i] = key;
+  vals[i] = (unsigned)i;
+  if (key < (1ull << 32)) atomicAdd(&cnt[0], 1);  // kept point-triangle records
+  if (key < (2ull << 32)) atomicAdd(&cnt[1], 1);  // kept records
+}
+__global__ void k_fr_gather(int n, const unsigned* __restrict__ vals, int n_old, const FrictionRec* __restrict__ old_fr,
+                            const FrictionRec* __restrict__ new_fr, FrictionRec* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int v = (int)vals[k];
+  out[k] = v < n_old ? old_fr[v] : new_fr[v - n_old];
 }
 
 // ---------------------------------------------------------------- invariants

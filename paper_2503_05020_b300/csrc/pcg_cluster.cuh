@@ -31,9 +31,13 @@ namespace cg = cooperative_groups;
 
 constexpr int PCG_THREADS = 256;
 constexpr int PCG_WARPS = PCG_THREADS / 32;
-#ifndef PCG_MIN_CTAS
-#define PCG_MIN_CTAS 2  // CTAs per SM the register budget must allow
-#endif
+// CTAs per SM the register budget must allow: the FP64 solve keeps 128 registers a thread (it
+// is bound by the FP64 pipe, and fewer registers spill); the FP32 solve is bound by memory
+// latency and gains from 4 resident CTAs (64 registers, a few spilled bytes on cold paths).
+template <class T>
+constexpr int pcg_min_ctas() {
+  return sizeof(T) == 8 ? 2 : 4;
+}
 
 // T: precision of the matrix, the vectors and every sum (FP64, or FP32 in mixed precision).
 template <class T>
@@ -145,7 +149,7 @@ DEV double body_iter_flops(const Layout& L, const SpmvArgsT<T, T>& A, int bd) {
 constexpr double STENCIL_ITER_FLOPS = 288.0;
 
 template <int C, class T>
-__global__ void __launch_bounds__(PCG_THREADS, PCG_MIN_CTAS) k_pcg_cluster(PcgClusterArgs<T> P) {
+__global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(PcgClusterArgs<T> P) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int e = P.env_list[blockIdx.x / C];

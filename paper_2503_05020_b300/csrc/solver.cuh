@@ -161,51 +161,62 @@ __global__ void k_precond_soft(int n_nodes, Layout L, const uint8_t* __restrict_
 template <class HT>
 __global__ void k_precond_body(int n_bodies, Layout L, const int* __restrict__ benv, const uint8_t* __restrict__ act,
                                const HT* __restrict__ bH, const int* __restrict__ ns_ptr,
-                               const int* __restrict__ ns_src, const int* __restrict__ st_pts,
+                               const int* __restrict__ ns_src, const HT* __restrict__ ns_xb,
                                const HT* __restrict__ sH, HT* __restrict__ Pinv) {
-  __shared__ HT P[144];
+  __shared__ double P[144];  // the block and its inverse in FP64 whatever HT is: the 12x12
+  __shared__ double D[12];   // body block mixes mass, orthogonality and contact scales
   int b = blockIdx.x;
   if (!act[benv[b]]) return;
   int t = threadIdx.x;
   int row = t / 12, col = t % 12;
   int I = row / 3, k = row % 3, J = col / 3, l = col % 3;
-  HT v = bH[144L * b + t];
-  if (!L.body_kin[b]) {
+  double v = double(bH[144L * b + t]);
+  const bool kin = L.body_kin[b];
+  if (!kin) {
+    // every pair of slots (a, c) of one stencil on the body adds (1, xb_a)(1, xb_c)^T (x) H_ac;
+    // a stencil's entries are consecutive (at most 4), so the partners of entry x lie within
+    // x - 3 .. x + 3, and every load of an entry depends on its index alone
     int pn = L.body_node[b];
     int beg = ns_ptr[pn], end = ns_ptr[pn + 1];
-    int g = beg;
-    while (g < end) {
-      int s = ns_src[g] >> 2;
-      int ge = g;
-      while (ge < end && (ns_src[ge] >> 2) == s) ++ge;
-      for (int x = g; x < ge; ++x) {
-        int a = ns_src[x] & 3;
-        int pa = st_pts[4 * s + a];
-        HT wa = I == 0 ? HT(1) : HT(L.pt_xb[3 * pa + I - 1]);
-        for (int y = g; y < ge; ++y) {
-          int c = ns_src[y] & 3;
-          int pc = st_pts[4 * s + c];
-          HT wc = J == 0 ? HT(1) : HT(L.pt_xb[3 * pc + J - 1]);
-          v += wa * wc * sH[78L * s + sym_idx(3 * a + k, 3 * c + l, 12)];
-        }
+    for (int x = beg; x < end; ++x) {
+      const int ex = ns_src[x], s = ex >> 2, a = ex & 3;
+      const double wa = I == 0 ? 1.0 : double(ns_xb[3L * x + I - 1]);
+      for (int y = max(beg, x - 3); y <= min(end - 1, x + 3); ++y) {
+        const int ey = ns_src[y];
+        if ((ey >> 2) != s) continue;
+        const int c = ey & 3;
+        const double wc = J == 0 ? 1.0 : double(ns_xb[3L * y + J - 1]);
+        v += wa * wc * double(sH[78L * s + sym_idx(3 * a + k, 3 * c + l, 12)]);
       }
-      g = ge;
     }
   }
   P[t] = v;
+  if (row == col) D[row] = v;
   __syncthreads();
-  if (t == 0) {
-    HT A[144];
-    for (int i = 0; i < 144; ++i) A[i] = P[i];
-    if (L.body_kin[b]) {
-      for (int i = 0; i < 144; ++i) A[i] = HT(0);
-    } else {
-      spd_inverse<12, HT>(A);
+  // In-place Gauss-Jordan inverse, one entry per thread, no pivoting: for an SPD block the
+  // pivots are the squared Cholesky pivots, all positive. A pivot that is not positive (a block
+  // that is not SPD) falls back to the inverse of the diagonal, 0 where that is not > 0.
+  bool ok = !kin;
+  for (int q = 0; q < 12 && ok; ++q) {
+    const double pqq = P[13 * q], piq = P[12 * row + q], pqj = P[12 * q + col], pij = P[t];
+    __syncthreads();
+    if (!(pqq > 0.0)) {  // uniform over the block
+      ok = false;
+      break;
     }
-    for (int i = 0; i < 144; ++i) P[i] = A[i];
+    const double inv = 1.0 / pqq;
+    double nv;
+    if (row == q && col == q) nv = inv;
+    else if (row == q) nv = pqj * inv;
+    else if (col == q) nv = -piq * inv;
+    else nv = pij - piq * pqj * inv;
+    P[t] = nv;
+    __syncthreads();
   }
-  __syncthreads();
-  Pinv[144L * b + t] = P[t];
+  double out = P[t];
+  if (kin) out = 0.0;
+  else if (!ok) out = (row == col && D[row] > 0.0) ? 1.0 / D[row] : 0.0;
+  Pinv[144L * b + t] = HT(out);
 }
 
 // ---------------------------------------------------------------- matrix-free stencil product
@@ -351,23 +362,23 @@ DEV void stencil_product_nodes(const SpmvArgsT<T, T>& A, const T* d, T* st_t, in
   }
 }
 
-// weight of every incidence entry, once per Newton iteration; entries of a body's p node also
-// get the rest coordinates of their point, so one pass over that list serves all 4 body nodes
+// weight of every incidence entry, once per Newton iteration, one thread per entry (keys: the
+// entry's node, from the sorted incidence keys); entries of a body's p node also get the rest
+// coordinates of their point, so one pass over that list serves all 4 body nodes
 template <class HT>
-__global__ void k_entry_weights(int n_nodes, Layout L, const uint8_t* __restrict__ act, const int* __restrict__ ns_ptr,
-                                const int* __restrict__ ns_src, const int* __restrict__ st_pts, HT* __restrict__ ns_w,
-                                HT* __restrict__ ns_xb) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_nodes) return;
+__global__ void k_entry_weights(int n_entries, Layout L, const uint8_t* __restrict__ act,
+                                const unsigned long long* __restrict__ keys, const int* __restrict__ ns_src,
+                                const int* __restrict__ st_pts, HT* __restrict__ ns_w, HT* __restrict__ ns_xb) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_entries) return;
+  const int i = (int)keys[k];
   if (!act[L.node_env[i]]) return;
   int b = L.node_body[i];
   bool pnode = b >= 0 && L.body_node[b] == i;
-  for (int k = ns_ptr[i]; k < ns_ptr[i + 1]; ++k) {
-    int pt = st_pts[ns_src[k]];
-    ns_w[k] = HT(point_weight(L, pt, i));
-    if (pnode)
-      for (int c = 0; c < 3; ++c) ns_xb[3L * k + c] = HT(L.pt_xb[3 * pt + c]);
-  }
+  int pt = st_pts[ns_src[k]];
+  ns_w[k] = HT(point_weight(L, pt, i));
+  if (pnode)
+    for (int c = 0; c < 3; ++c) ns_xb[3L * k + c] = HT(L.pt_xb[3 * pt + c]);
 }
 
 // deterministic warp sum (fixed butterfly)

@@ -203,6 +203,8 @@ def test_batched_env_is_bit_identical_to_alone_and_isolated_from_failures():
     batch.set_state(b2, xb2, vb2, 0)
     batch.step(12)
     assert np.array_equal(batch.dofs(b1), xa)
+    work = ("newton_iters", "pcg_iters", "ls_halvings", "steps", "accd_iters")
+    assert {k: batch.status(b1)[k] for k in work} == {k: alone.status(a)[k] for k in work}
     assert batch.status(b1)["status"] == "DONE"
     assert batch.status(b0)["status"] == "DONE"
     st = batch.status(b2)
@@ -334,3 +336,47 @@ def test_contacts_from_swept_candidates_give_the_same_bits_as_fresh_traversals()
         assert out[0][1]["status"] == "ACTIVE" and out[0][1]["ls_halvings"] >= 0
         assert out[0][1] == out[1][1]
         assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_one_call_of_k_steps_gives_the_bits_of_k_calls_of_one_step():
+    """Inside one ipc_step call every env runs its steps at its own pace (an env done with a step
+    starts the next while others still iterate). Each env's results must be those of stepping
+    the batch one step per call: same DOFs and the same Newton, line-search, PCG and ACCD counts."""
+    envs = [S.pad_grasp_env(i) for i in range(4)] + [S.cube_squeeze_env(1, n_steps=40, close_steps=20, dt=0.005)]
+    p = S.scene_params(0.005)
+    out = []
+    for per_call in (6, 1):
+        sc = ipc.Scene(p)
+        ids = [sc.add_env(e) for e in envs]
+        for eid, env in zip(ids[:4], envs[:4]):
+            x, v = S.pad_grasp_state_at(env, 20)
+            sc.set_state(eid, x, v, 20)
+        for _ in range(6 // per_call):
+            sc.step(per_call)
+        out.append([(sc.dofs(e), sc.status(e)) for e in ids])
+    for (xa, sa), (xb, sb) in zip(*out):
+        assert sa["status"] == "ACTIVE" and sa == sb
+        assert np.array_equal(xa, xb)
+
+
+def test_batched_pad_grasps_do_the_work_of_each_alone():
+    """Two pad grasps in contact stepped together: each env's DOFs and its Newton, line-search,
+    PCG and ACCD counts equal those of stepping it alone (an env whose line search accepts keeps
+    its point while the other env goes on halving)."""
+    p = S.scene_params(0.005)
+    envs = [S.pad_grasp_env(i) for i in range(2)]
+
+    def run(which):
+        sc = ipc.Scene(p)
+        ids = [sc.add_env(envs[k]) for k in which]
+        for eid, k in zip(ids, which):
+            x, v = S.pad_grasp_state_at(envs[k], 20)
+            sc.set_state(eid, x, v, 20)
+        sc.step(3)
+        return [(sc.dofs(e), sc.status(e)) for e in ids]
+
+    both = run([0, 1])
+    for k in (0, 1):
+        (xa, sa), = run([k])
+        assert sa["status"] == "ACTIVE" and sa == both[k][1]
+        assert np.array_equal(xa, both[k][0])
