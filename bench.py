@@ -380,7 +380,7 @@ def serving_leg(args, params, device):
            "request": "pad grasp: close 80 steps, lift 0.1 m in 60, shake +/-15 deg at 2 Hz for 60; dt 5 ms"}
     for name, prec in (("fp64", ipc.FP64), ("mixed", ipc.MIXED)):
         reqs = [Request(i, e, t) for i, (e, t) in enumerate(zip(envs, arrivals))]
-        srv = GraspServer(params, precision=prec, device=device, max_envs=64, admit_period=8)
+        srv = GraspServer(params, precision=prec, device=device, max_envs=64, admit_period=8, steps_per_call=8)
         rep = srv.run(reqs)
         held = [bool(r.result.get("held")) for r in reqs]
         out[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rep.items()}

@@ -4,12 +4,13 @@ A request is one environment with its whole schedule (Sec. III-D's evaluation pr
 lift, optionally shake) and an arrival time. The server keeps one device-resident scene. At step
 boundaries it admits requests that have arrived, in arrival order, while the scene's HBM budget
 (checked by the library on ipc_env_add from each environment's estimated bytes) and the slot cap
-allow; admitted environments join the running batch and advance one time step per batch step
-alongside the others (Sec. III-A: every environment keeps its own state, step size, stopping
-test and failure). A finished environment (DONE or FAILED) is read back at once; it leaves the
-scene at the next admission round, so one relayout of the batch serves both its departure and
-new arrivals. Relayouts are spaced at least `admit_period` batch steps apart while environments
-are running.
+allow; admitted environments join the running batch (Sec. III-A: every environment keeps its own
+state, step size, stopping test and failure). Each call of ipc_step advances every running
+environment `steps_per_call` time steps, each at its own pace: inside the call an environment
+that has finished a step starts the next one while slower ones still iterate. A finished
+environment (DONE or FAILED) is read back at the end of that call; it leaves the scene at the
+next admission round, so one relayout of the batch serves both its departure and new arrivals.
+Relayouts are spaced at least `admit_period` batch steps apart while environments are running.
 
 Latency of a request = time its result was read back - its arrival time; the report gives p50
 and p99 over requests, throughput in requests/s and environment-steps/s, and per-request queue
@@ -104,11 +105,12 @@ def object_result(env: dict, points: np.ndarray, points0: np.ndarray) -> dict:
 
 class GraspServer:
     def __init__(self, params: dict, precision: int = ipc.FP64, hbm_budget_bytes: int = 0, max_envs: int = 64,
-                 admit_period: int = 8, device: int = 0, scene=None, clock=None, sleep=None):
+                 admit_period: int = 8, steps_per_call: int = 1, device: int = 0, scene=None, clock=None, sleep=None):
         self.scene = scene if scene is not None else ipc.Scene(params, precision=precision, device=device,
                                                              hbm_budget_bytes=hbm_budget_bytes)
         self.max_envs = max_envs
         self.admit_period = max(1, admit_period)
+        self.steps_per_call = max(1, steps_per_call)
         self.clock = clock or time.perf_counter
         self.sleep = sleep or time.sleep
         self.batch_steps = 0
@@ -122,6 +124,7 @@ class GraspServer:
         active: dict[int, Request] = {}  # env id -> request, still stepping
         done_in_scene: list[int] = []  # finished env ids not yet removed
         start_pts: dict[int, np.ndarray] = {}
+        last_step: dict[int, int] = {}  # env id -> its step count at the last read-back
         t0 = self.clock()
         since_relayout = self.admit_period
         while pending or active:
@@ -146,6 +149,7 @@ class GraspServer:
                     pending.popleft()
                     req.admitted = now
                     active[eid] = req
+                    last_step[eid] = 0
                     # host-side (no relayout per admission); only what the grasp outcome needs
                     start_pts[eid] = initial_points(req.env) if "object" in req.env else None
                     changed = True
@@ -157,14 +161,16 @@ class GraspServer:
                     self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
                 continue
             self.max_active = max(self.max_active, len(active))
-            sc.step(1)
-            self.batch_steps += 1
-            since_relayout += 1
-            self.env_steps += len(active)
+            n = self.steps_per_call
+            sc.step(n)
+            self.batch_steps += n
+            since_relayout += n
             status = sc.all_status()
             t_now = self.clock() - t0
             for eid in list(active):
                 st, reason, step = status[eid]
+                self.env_steps += step - last_step[eid]
+                last_step[eid] = step
                 if st in ("DONE", "FAILED"):
                     req = active.pop(eid)
                     req.finished, req.status, req.reason, req.steps = t_now, st, reason, step

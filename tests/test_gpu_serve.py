@@ -28,7 +28,7 @@ def test_served_results_are_identical_to_results_alone(precision):
     envs = [short_request(i) for i in range(4)]
     arrivals = [0.0, 0.01, 0.25, 0.6]
     reqs = [Request(i, e, t) for i, (e, t) in enumerate(zip(envs, arrivals))]
-    srv = GraspServer(p, precision=precision, max_envs=8, admit_period=2)
+    srv = GraspServer(p, precision=precision, max_envs=8, admit_period=2, steps_per_call=2)
     rep = srv.run(reqs)
     assert rep["completed"] == 4, rep
     assert any(r.admitted < q.finished and r.admitted > q.admitted for r in reqs for q in reqs), \

@@ -47,10 +47,11 @@ class FakeScene:
         del self.envs[eid]
 
     def step(self, n=1):
-        for e in self.envs.values():
-            if e["step"] < e["env"]["steps"]:
-                e["step"] += 1
-        self.clock.t += 0.1
+        for _ in range(n):
+            for e in self.envs.values():
+                if e["step"] < e["env"]["steps"]:
+                    e["step"] += 1
+            self.clock.t += 0.1
 
     def all_status(self):
         return {k: ("DONE" if e["step"] >= e["env"]["steps"] else "ACTIVE", "none", e["step"])
@@ -67,10 +68,11 @@ def env(name, steps, nbytes=1.0):
     return {"name": name, "steps": steps, "bytes": nbytes, "soft": [], "affine": []}
 
 
-def serve(reqs, budget=math.inf, max_envs=64, admit_period=1):
+def serve(reqs, budget=math.inf, max_envs=64, admit_period=1, steps_per_call=1):
     clk = FakeClock()
     sc = FakeScene(clk, budget)
-    srv = GraspServer({}, scene=sc, clock=clk, sleep=clk.sleep, max_envs=max_envs, admit_period=admit_period)
+    srv = GraspServer({}, scene=sc, clock=clk, sleep=clk.sleep, max_envs=max_envs, admit_period=admit_period,
+                      steps_per_call=steps_per_call)
     return srv, sc, srv.run(reqs)
 
 
@@ -117,3 +119,14 @@ def test_percentile_nearest_rank_and_poisson_arrivals():
     gaps = np.diff([0.0] + t)
     assert abs(gaps.mean() - 1 / 20.0) < 0.1 / 20.0
     assert abs(gaps.std() - 1 / 20.0) < 0.15 / 20.0  # exponential gaps: std = mean
+
+
+def test_multi_step_calls_count_each_env_step_once():
+    """With several time steps per call an env that finishes inside the call is read back at the
+    call's end; env-steps count each env's own steps (not the call length)."""
+    reqs = [Request(0, env("a", 10), 0.0), Request(1, env("b", 3), 0.0)]
+    srv, sc, rep = serve(reqs, admit_period=4, steps_per_call=4)
+    assert rep["completed"] == 2
+    assert srv.env_steps == 13
+    assert rep["batch_steps"] == 12  # three calls of four steps
+    assert reqs[1].finished == 0.4 and reqs[0].finished == 1.2
