@@ -162,7 +162,10 @@ ipc_status ipc_env_add(ipc_scene* scene, const ipc_env_desc* env, int32_t* env_i
 ipc_status ipc_env_remove(ipc_scene* scene, int32_t env_id);
 
 /* Advance every ACTIVE environment by up to n_steps time steps (Sec. III-A: each env has its
- * own step size, stopping test and failure state; a failure never fails the call). */
+ * own step size, stopping test and failure state; a failure never fails the call). Inside the
+ * call the envs step at their own pace: an env whose Newton loop has stopped starts its next
+ * step while slower envs still iterate. Each env's results are those of stepping it alone, one
+ * step per call. Returns when every env has done its steps (or stopped: DONE, FAILED). */
 ipc_status ipc_step(ipc_scene* scene, int32_t n_steps);
 
 /* Copy one result of one environment into out (host). */
