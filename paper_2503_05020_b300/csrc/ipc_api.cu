@@ -1625,6 +1625,7 @@ struct ipc_scene {
     build_trees();
     n_fr = n_fr_pt = 0;
     cand_src = CAND_FRESH;
+    list_ok = false;
     constraint_set(act);
     CK(cudaMemcpyAsync(ptx_t.p, ptx.p, 3 * (size_t)NP * sizeof(double), cudaMemcpyDeviceToDevice, stream));
     fr.ensure(n_ct + 1);
@@ -1636,16 +1637,50 @@ struct ipc_scene {
 
   // CCD step filter on the envs still iterating: swept-box candidates at [x, x + p] (boxes
   // already refit), then additive CCD per candidate pair; each env's alpha_max is the minimum
+  // The step filter's candidate list is kept across Newton rounds of a call while it covers the
+  // new segments: it is made with boxes grown by an extra slack, and remade only when some
+  // primitive's swept box (grown by the plain growth) leaves the box it was listed with.
+  DBuf<double> keep_tri, keep_ed, keep_sv;  // boxes the kept list was made with
+  bool list_ok = false;
+  double swept_slack() const { return reuse_lists() ? 0.25 * desc.dhat : 0.0; }
+  bool list_covers(const uint8_t* act) {
+    if (!list_ok) return false;
+    CK(cudaMemsetAsync(e_count.p + 2, 0, sizeof(int), stream));
+    const double r = swept_growth();
+    launch(k_swept_inside<3>, NTR, 256, NTR, (const int*)tri_pt.p, (const int*)tri_env.p, act, (const double*)ptx.p,
+           (const double*)pte.p, r, (const double*)keep_tri.p, e_count.p + 2);
+    launch(k_swept_inside<2>, NED, 256, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act, (const double*)ptx.p,
+           (const double*)pte.p, r, (const double*)keep_ed.p, e_count.p + 2);
+    launch(k_swept_inside<1>, NSV, 256, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
+           (const double*)pte.p, r, (const double*)keep_sv.p, e_count.p + 2);
+    return read_int(e_count.p + 2) == 0;
+  }
+  long lists_made = 0, lists_kept = 0;
+  // CCD step filter on the envs in act: swept-box candidates at [x, x + p] (ptx, pte current),
+  // then additive CCD per candidate pair of the iterating envs; each env's alpha_max is the
+  // minimum
   void ccd_filter(EnvCtl C, const uint8_t* act) {
+    const bool keep = reuse_lists();  // the list also serves the narrow phases: sorted per query
+    if (keep && list_covers(act)) {
+      ++lists_kept;
+      accd_all(C, keep);
+      return;
+    }
+    ++lists_made;
+    if (since_build >= TREE_REBUILD_ROUNDS) {  // refits keep the trees valid; a rebuild keeps them tight
+      build_trees();
+      since_build = 0;
+    }
+    const double r = swept_growth() + swept_slack();
+    boxes_and_refit(pte.p, r);
     ccd_cnt_pt.ensure(NSV + 1);
     ccd_off_pt.ensure(NSV + 1);
     ccd_cnt_ee.ensure(NED + 1);
     ccd_off_ee.ensure(NED + 1);
     slots_pt.ensure((size_t)NSV * CAND_CAP + 1);
     slots_ee.ensure((size_t)NED * CAND_CAP + 1);
-    const double r = swept_growth();
-    const bool keep = reuse_lists();  // the list also serves the narrow phases: sorted per query
     ccd_np = ccd_ne = 0;
+    list_ok = false;
     CandOut cp{ccd_cnt_pt.p, nullptr, slots_pt.p, overflow.p, CAND_CAP};
     launch(k_trav_pt<TRAV_COLLECT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
            (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), cp,
@@ -1658,36 +1693,53 @@ struct ipc_scene {
     const bool spilled = collect_spilled();
     ccd_np = np;
     ccd_ne = ne;
-    if (np + ne == 0) return;
     ccd_j.ensure(np + ne + 1);
     ccd_q.ensure(np + ne + 1);
-    if (spilled && keep) {
-      CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p, 0, ccd_q.p};
-      launch(k_trav_pt<TRAV_FILL>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
-             (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
-             (const double*)nullptr, C);
-      CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p, 0, ccd_q.p + np};
-      launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
-             (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr,
-             C);
-    } else if (spilled) {
-      CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p, 0, ccd_q.p};
-      launch(k_trav_pt<TRAV_FILLU>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
-             (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
-             (const double*)nullptr, C);
-      CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p, 0, ccd_q.p + np};
-      launch(k_trav_ee<TRAV_FILLU>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
-             (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr,
-             C);
-    } else {
-      launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)ccd_cnt_pt.p, (const int*)slots_pt.p,
-             (const int*)ccd_off_pt.p, ccd_j.p, ccd_q.p, keep ? 1 : 0);
-      launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)ccd_cnt_ee.p, (const int*)slots_ee.p,
-             (const int*)ccd_off_ee.p, ccd_j.p + np, ccd_q.p + np, keep ? 1 : 0);
+    if (np + ne > 0) {
+      if (spilled) {
+        CandOut fp{nullptr, ccd_off_pt.p, ccd_j.p, overflow.p, 0, ccd_q.p};
+        CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p, 0, ccd_q.p + np};
+        if (keep) {
+          launch(k_trav_pt<TRAV_FILL>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
+                 (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
+                 (const double*)nullptr, C);
+          launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+                 (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr,
+                 (const double*)nullptr, C);
+        } else {
+          launch(k_trav_pt<TRAV_FILLU>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
+                 (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
+                 (const double*)nullptr, C);
+          launch(k_trav_ee<TRAV_FILLU>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
+                 (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr,
+                 (const double*)nullptr, C);
+        }
+      } else {
+        launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)ccd_cnt_pt.p, (const int*)slots_pt.p,
+               (const int*)ccd_off_pt.p, ccd_j.p, ccd_q.p, keep ? 1 : 0);
+        launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)ccd_cnt_ee.p, (const int*)slots_ee.p,
+               (const int*)ccd_off_ee.p, ccd_j.p + np, ccd_q.p + np, keep ? 1 : 0);
+      }
     }
-    launch(k_accd_pairs, np + ne, 128, np, ne, (const int*)ccd_q.p, (const int*)ccd_j.p, (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p,
-           (const int*)ed_env.p, (const double*)ptx.p, (const double*)ptp.p, keep ? (const double*)pte.p : nullptr,
-           C);
+    if (keep) {  // the boxes this list was made with: triangles, edges (the trees' boxes), vertices
+      keep_tri.ensure(6 * (size_t)std::max(NTR, 1));
+      keep_ed.ensure(6 * (size_t)std::max(NED, 1));
+      keep_sv.ensure(6 * (size_t)std::max(NSV, 1));
+      if (NTR) CK(cudaMemcpyAsync(keep_tri.p, ttri.pbox.p, 6 * (size_t)NTR * 8, cudaMemcpyDeviceToDevice, stream));
+      if (NED) CK(cudaMemcpyAsync(keep_ed.p, tedge.pbox.p, 6 * (size_t)NED * 8, cudaMemcpyDeviceToDevice, stream));
+      launch(k_prim_boxes<1>, NSV, 256, NSV, (const int*)sv_pt.p, (const double*)ptx.p, (const double*)pte.p, r,
+             keep_sv.p);
+      list_ok = true;
+    }
+    accd_all(C, keep);
+  }
+  // ACCD of the listed pairs; with a grown list (keep) only the pairs whose plain swept boxes
+  // overlap are tested
+  void accd_all(EnvCtl C, bool keep) {
+    if (ccd_np + ccd_ne == 0) return;
+    launch(k_accd_pairs, ccd_np + ccd_ne, 128, ccd_np, ccd_ne, (const int*)ccd_q.p, (const int*)ccd_j.p,
+           (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p, (const int*)ed_env.p,
+           (const double*)ptx.p, (const double*)ptp.p, keep ? (const double*)pte.p : nullptr, C);
   }
 
   // ------------------------------------------------------------------ time stepping
@@ -1702,6 +1754,7 @@ struct ipc_scene {
     EnvCtl C = ctl();
     launch(k_env_call_begin, E, 128, E, C, n);
     cand_src = CAND_FRESH;
+    list_ok = false;
     const long max_rounds = (long)n * (desc.max_newton + 1) + 1;
     for (long round = 0;; ++round) {
       launch_grid(k_env_round_begin, 1, 256, E, C, e_start.p);
@@ -1789,11 +1842,6 @@ struct ipc_scene {
       launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p,
              (const double*)p.p, ptp.p);
       launch(k_add_vec, 3L * NP, 256, 3L * NP, (const double*)ptx.p, (const double*)ptp.p, pte.p);
-      if (since_build >= TREE_REBUILD_ROUNDS) {  // refits keep the trees valid; a rebuild keeps them tight
-        build_trees();
-        since_build = 0;
-      }
-      boxes_and_refit(pte.p, swept_growth());
       pbeg(IPC_PROF_CCD);
       ccd_filter(C, e_cover.p);
       pend(IPC_PROF_CCD);

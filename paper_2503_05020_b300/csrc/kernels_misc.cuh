@@ -369,6 +369,32 @@ __global__ void k_prim_boxes(int n, const int* __restrict__ prim_pt, const doubl
   }
 }
 
+// Whether the swept boxes [min(x, x_end) - r, max(x, x_end) + r] of the primitives of the envs in
+// act (computed as k_prim_boxes computes them) lie inside the boxes a stored candidate list was
+// made with; a primitive outside sets *out. Inside, every pair whose new boxes overlap had
+// overlapping stored boxes, so the stored list still holds it.
+template <int NV>
+__global__ void k_swept_inside(int n, const int* __restrict__ prim_pt, const int* __restrict__ prim_env,
+                               const uint8_t* __restrict__ act, const double* __restrict__ ptx,
+                               const double* __restrict__ pte, double r, const double* __restrict__ stored,
+                               int* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !act[prim_env[i]]) return;
+  for (int k = 0; k < 3; ++k) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int v = 0; v < NV; ++v) {
+      int pt = prim_pt[NV * i + v];
+      double a = ptx[3L * pt + k], b = pte[3L * pt + k];
+      lo = fmin(fmin(lo, a), b);
+      hi = fmax(fmax(hi, a), b);
+    }
+    if (__dsub_rn(lo, r) < stored[6L * i + k] || __dadd_rn(hi, r) > stored[6L * i + 3 + k]) {
+      atomicOr(out, 1);
+      return;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- candidates
 struct PtInfo {
   const int* body;     // affine body index (>= 0) or -1 - soft body id
