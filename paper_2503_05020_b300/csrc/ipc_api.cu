@@ -182,12 +182,17 @@ void build_pattern(HostEnv& h) {
   h.have_pattern = true;
 }
 
+// partner slots per query of a collect traversal: edge-edge queries on fine surfaces find a few
+// dozen non-adjacent neighbours within the step filter's grown boxes
+constexpr int CAND_SLOTS = 128;
+
 uint64_t estimate_bytes(const HostEnv& h, int precision) {
   uint64_t nn = h.nsv_verts + 4 * h.nbodies;
   uint64_t hb = precision == IPC_MIXED ? 4 : 8;
   uint64_t b = nn * (24 * 14 + 72) + (uint64_t)h.ntets * (96 + 16 + 96 + 90 * 8 + 64) + nn * 15 * (9 * hb + 8);
   uint64_t np = h.pt_node.size(), nprim = h.tris.size() / 3 + h.edges.size() / 2 + h.sv.size();
-  b += np * 96 + nprim * 4 * 64 + 4096 * (78 * 8 + 200);  // contact capacity estimate
+  // contact capacity estimate: collect slots, kept list boxes (6 doubles per primitive)
+  b += np * 96 + nprim * (4 * CAND_SLOTS + 48) + 4096 * (78 * 8 + 200);
   b += (uint64_t)h.targets.size() * 8;
   return b;
 }
@@ -475,7 +480,7 @@ struct ipc_scene {
   DBuf<int> cnt_pt, off_pt, cnt_ee, off_ee, cand_j, cand_q, nflag, noff, scan_tmp, overflow;
   DBuf<int> ccd_cnt_pt, ccd_off_pt, ccd_cnt_ee, ccd_off_ee, ccd_j, ccd_q;  // swept-box candidates
   DBuf<int> slots_pt, slots_ee;  // partner slots of collect traversals (CAND_CAP per query)
-  DBuf<ContactRec> ct_tmp, ct;
+  DBuf<ContactRec> ct_tmp, ct, cand_rec, ccd_rec;  // contacts; pair records of the two lists
   DBuf<FrictionRec> fr, fr_new, fr_tmp;
   DBuf<unsigned long long> fr_keys, fr_keys2;
   DBuf<unsigned> fr_vals, fr_vals2;
@@ -1119,7 +1124,22 @@ struct ipc_scene {
     if (stack) fail_with(IPC_ERR_INTERNAL, "BVH traversal stack overflow");
     return spill != 0;
   }
-  static constexpr int CAND_CAP = 64;  // partner slots per query of a collect traversal
+  static constexpr int CAND_CAP = CAND_SLOTS;
+  // the candidate totals of a pair of collect traversals (the last entries of their offset
+  // scans) and the traversal flags, in one read-back; fails on a stack overflow, returns
+  // whether a query had more partners than its slots
+  bool read_totals(const int* tot_pt, const int* tot_ee, int* np, int* ne) {
+    CK(cudaMemcpyAsync(hpin, tot_pt, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(hpin + 1, tot_ee, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(hpin + 2, overflow.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    *np = hpin[0];
+    *ne = hpin[1];
+    const int stack = hpin[2], spill = hpin[3];
+    if (stack || spill) overflow.zero(stream);
+    if (stack) fail_with(IPC_ERR_INTERNAL, "BVH traversal stack overflow");
+    return spill != 0;
+  }
 
   // ------------------------------------------------------------------ constraint set
   // contacts (d < dhat) of the envs in act at positions ptx (already computed)
@@ -1140,9 +1160,9 @@ struct ipc_scene {
     launch(k_trav_ee<TRAV_COLLECT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
            (const double*)tedge.pbox.p, tree(tedge), ptinfo(), oe, (const double*)nullptr, (const double*)nullptr, ctl());
     pend(IPC_PROF_BROAD);
-    n_pt = scan(cnt_pt.p, NSV, off_pt.p);
-    n_ee = scan(cnt_ee.p, NED, off_ee.p);
-    const bool spilled = collect_spilled();
+    scan(cnt_pt.p, NSV, off_pt.p, false);
+    scan(cnt_ee.p, NED, off_ee.p, false);
+    const bool spilled = read_totals(off_pt.p + NSV, off_ee.p + NED, &n_pt, &n_ee);
     int nc = n_pt + n_ee;
     cand_j.ensure(nc + 1);
     cand_q.ensure(nc + 1);
@@ -1160,22 +1180,29 @@ struct ipc_scene {
       launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)cnt_ee.p, (const int*)slots_ee.p,
              (const int*)off_ee.p, cand_j.p + n_pt, cand_q.p + n_pt, 1);
     }
-    contacts_from_list(nullptr, n_pt, n_ee, cand_q.p, cand_j.p);
+    cand_rec.ensure(nc + 1);
+    launch(k_cand_records, nc, 256, n_pt, n_ee, (const int*)cand_q.p, (const int*)cand_j.p, (const int*)sv_pt.p,
+           (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p, (const int*)ed_env.p,
+           (const double*)ed_rest2.p, cand_rec.p);
+    contacts_from_list(nullptr, n_pt, n_ee, cand_rec.p);
   }
   // Narrow phase over a candidate list (point-triangle per surface vertex, then edge-edge per
   // edge, partners ascending): contacts d < dhat at positions ptx, in list order. act (or null)
   // keeps only the envs of this evaluation when the list holds more.
-  void contacts_from_list(const uint8_t* act, int np, int ne, const int* cq, const int* cj) {
+  void contacts_from_list(const uint8_t* act, int np, int ne, const ContactRec* rec) {
     const int nc = np + ne;
     nflag.ensure(nc + 1);
     noff.ensure(nc + 1);
     ct_tmp.ensure(nc + 1);
     double dh2 = desc.dhat * desc.dhat;
-    launch(k_narrow, nc, 128, np, ne, cq, cj, (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p,
-           (const int*)ed_pt.p, (const int*)ed_env.p, (const double*)ptx.p, dh2, nflag.p, ct_tmp.p,
-           (const double*)ed_rest2.p, act);
-    n_ct = scan(nflag.p, nc, noff.p);
-    n_ct_pt = np > 0 ? read_int(noff.p + np) : 0;
+    launch(k_narrow, nc, 128, nc, rec, act, (const double*)ptx.p, dh2, nflag.p, ct_tmp.p);
+    scan(nflag.p, nc, noff.p, false);
+    // the contacts' count and the point-triangle part of it, in one read-back
+    CK(cudaMemcpyAsync(hpin, noff.p + np, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(hpin + 1, noff.p + nc, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    n_ct_pt = hpin[0];
+    n_ct = hpin[1];
     ct.ensure(n_ct + 1);
     launch(k_compact_contacts, nc, 256, nc, (const int*)nflag.p, (const int*)noff.p, (const ContactRec*)ct_tmp.p, ct.p);
   }
@@ -1193,8 +1220,8 @@ struct ipc_scene {
   bool reuse_lists() const { return desc.fresh_broad_phase == 0; }
   double swept_growth() const { return reuse_lists() ? 0.5 * desc.dhat * (1.0 + 1e-6) : 0.0; }
   void contacts_at(const uint8_t* act) {
-    if (cand_src == CAND_SWEPT) contacts_from_list(act, ccd_np, ccd_ne, ccd_q.p, ccd_j.p);
-    else if (cand_src == CAND_STATIC) contacts_from_list(act, n_pt, n_ee, cand_q.p, cand_j.p);
+    if (cand_src == CAND_SWEPT) contacts_from_list(act, ccd_np, ccd_ne, ccd_rec.p);
+    else if (cand_src == CAND_STATIC) contacts_from_list(act, n_pt, n_ee, cand_rec.p);
     else constraint_set(act);
   }
   void stencil_table() {
@@ -1688,9 +1715,10 @@ struct ipc_scene {
     CandOut ce{ccd_cnt_ee.p, nullptr, slots_ee.p, overflow.p, CAND_CAP};
     launch(k_trav_ee<TRAV_COLLECT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
            (const double*)tedge.pbox.p, tree(tedge), ptinfo(), ce, (const double*)nullptr, (const double*)nullptr, C);
-    int np = scan(ccd_cnt_pt.p, NSV, ccd_off_pt.p);
-    int ne = scan(ccd_cnt_ee.p, NED, ccd_off_ee.p);
-    const bool spilled = collect_spilled();
+    scan(ccd_cnt_pt.p, NSV, ccd_off_pt.p, false);
+    scan(ccd_cnt_ee.p, NED, ccd_off_ee.p, false);
+    int np = 0, ne = 0;
+    const bool spilled = read_totals(ccd_off_pt.p + NSV, ccd_off_ee.p + NED, &np, &ne);
     ccd_np = np;
     ccd_ne = ne;
     ccd_j.ensure(np + ne + 1);
@@ -1721,6 +1749,10 @@ struct ipc_scene {
                (const int*)ccd_off_ee.p, ccd_j.p + np, ccd_q.p + np, keep ? 1 : 0);
       }
     }
+    ccd_rec.ensure(np + ne + 1);
+    launch(k_cand_records, np + ne, 256, np, ne, (const int*)ccd_q.p, (const int*)ccd_j.p, (const int*)sv_pt.p,
+           (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p, (const int*)ed_env.p,
+           (const double*)ed_rest2.p, ccd_rec.p);
     if (keep) {  // the boxes this list was made with: triangles, edges (the trees' boxes), vertices
       keep_tri.ensure(6 * (size_t)std::max(NTR, 1));
       keep_ed.ensure(6 * (size_t)std::max(NED, 1));
@@ -1737,9 +1769,8 @@ struct ipc_scene {
   // overlap are tested
   void accd_all(EnvCtl C, bool keep) {
     if (ccd_np + ccd_ne == 0) return;
-    launch(k_accd_pairs, ccd_np + ccd_ne, 128, ccd_np, ccd_ne, (const int*)ccd_q.p, (const int*)ccd_j.p,
-           (const int*)sv_pt.p, (const int*)sv_env.p, (const int*)tri_pt.p, (const int*)ed_pt.p, (const int*)ed_env.p,
-           (const double*)ptx.p, (const double*)ptp.p, keep ? (const double*)pte.p : nullptr, C);
+    launch(k_accd_pairs, ccd_np + ccd_ne, 128, ccd_np + ccd_ne, (const ContactRec*)ccd_rec.p, (const double*)ptx.p,
+           (const double*)ptp.p, keep ? (const double*)pte.p : nullptr, C);
   }
 
   // ------------------------------------------------------------------ time stepping
@@ -1782,7 +1813,7 @@ struct ipc_scene {
     launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p,
            (const double*)x.p, ptx.p);
     if (cand_src == CAND_SWEPT) {
-      contacts_from_list(start, ccd_np, ccd_ne, ccd_q.p, ccd_j.p);
+      contacts_from_list(start, ccd_np, ccd_ne, ccd_rec.p);
     } else {
       build_trees();
       since_build = 0;

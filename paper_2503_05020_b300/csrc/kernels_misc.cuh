@@ -546,19 +546,19 @@ __global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __
   }
 }
 
-// narrow phase: keep the candidates with d^2 < dhat^2 (flag), typed for the stencils; the
-// record of a kept candidate goes to tmp[i]. cq[i] is the query of candidate i.
-__global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ cq, const int* __restrict__ cj,
-                         const int* __restrict__ sv_pt, const int* __restrict__ sv_env, const int* __restrict__ tri_pt,
-                         const int* __restrict__ ed_pt, const int* __restrict__ ed_env, const double* __restrict__ ptx,
-                         double dhat2, int* __restrict__ flag, ContactRec* __restrict__ tmp,
-                         const double* __restrict__ ed_rest2, const uint8_t* __restrict__ act) {
+// The pair record of every listed candidate (kind, points, env, EE mollifier threshold, list
+// index), made once per candidate list, so that each narrow phase and ACCD read one record per
+// pair. cq[i] is the query of candidate i, cj[i] its partner.
+__global__ void k_cand_records(int n_pt, int n_ee, const int* __restrict__ cq, const int* __restrict__ cj,
+                               const int* __restrict__ sv_pt, const int* __restrict__ sv_env,
+                               const int* __restrict__ tri_pt, const int* __restrict__ ed_pt,
+                               const int* __restrict__ ed_env, const double* __restrict__ ed_rest2,
+                               ContactRec* __restrict__ rec) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_pt + n_ee) return;
   ContactRec c;
+  const int q = cq[i], j = cj[i];
   if (i < n_pt) {
-    int q = cq[i];
-    int j = cj[i];
     c.kind = 0;
     c.pts[0] = sv_pt[q];
     c.pts[1] = tri_pt[3 * j];
@@ -567,8 +567,6 @@ __global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ cq, const i
     c.env = sv_env[q];
     c.eps_x = 0.0;
   } else {
-    int q = cq[i];
-    int j = cj[i];
     c.kind = 1;
     c.pts[0] = ed_pt[2 * q];
     c.pts[1] = ed_pt[2 * q + 1];
@@ -577,7 +575,19 @@ __global__ void k_narrow(int n_pt, int n_ee, const int* __restrict__ cq, const i
     c.env = ed_env[q];
     c.eps_x = 1e-3 * ed_rest2[q] * ed_rest2[j];
   }
+  c.type = 0;
   c.cand = i;
+  rec[i] = c;
+}
+
+// narrow phase: keep the listed pairs with d^2 < dhat^2 (flag), typed for the stencils; the
+// record of a kept pair goes to tmp[i]. act (or null) keeps only the envs of this evaluation.
+__global__ void k_narrow(int n, const ContactRec* __restrict__ rec, const uint8_t* __restrict__ act,
+                         const double* __restrict__ ptx, double dhat2, int* __restrict__ flag,
+                         ContactRec* __restrict__ tmp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ContactRec c = rec[i];
   if (act && !act[c.env]) {  // a list that holds envs outside this evaluation
     flag[i] = 0;
     return;
@@ -658,31 +668,13 @@ DEV void swept_box(const double* __restrict__ ptx, const double* __restrict__ pt
 // (an atomic minimum on non-negative doubles: exact and independent of order). When the
 // candidates were gathered with grown boxes (pte given), a pair whose plain swept boxes do
 // not overlap is skipped, so the set of tested pairs is the plain swept-box set.
-__global__ void k_accd_pairs(int n_pt, int n_ee, const int* __restrict__ cq, const int* __restrict__ cj,
-                             const int* __restrict__ sv_pt, const int* __restrict__ sv_env,
-                             const int* __restrict__ tri_pt, const int* __restrict__ ed_pt,
-                             const int* __restrict__ ed_env, const double* __restrict__ ptx,
+__global__ void k_accd_pairs(int n, const ContactRec* __restrict__ rec, const double* __restrict__ ptx,
                              const double* __restrict__ ptp, const double* __restrict__ pte, EnvCtl C) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_pt + n_ee) return;
-  int kind, e, pts[4];
-  if (i < n_pt) {
-    int q = cq[i], j = cj[i];
-    kind = 0;
-    e = sv_env[q];
-    pts[0] = sv_pt[q];
-    pts[1] = tri_pt[3 * j];
-    pts[2] = tri_pt[3 * j + 1];
-    pts[3] = tri_pt[3 * j + 2];
-  } else {
-    int q = cq[i], j = cj[i];
-    kind = 1;
-    e = ed_env[q];
-    pts[0] = ed_pt[2 * q];
-    pts[1] = ed_pt[2 * q + 1];
-    pts[2] = ed_pt[2 * j];
-    pts[3] = ed_pt[2 * j + 1];
-  }
+  if (i >= n) return;
+  const ContactRec& c = rec[i];
+  const int kind = c.kind, e = c.env;
+  int pts[4] = {c.pts[0], c.pts[1], c.pts[2], c.pts[3]};
   if (!C.iter[e]) return;  // an env covered for its next step only needs the candidates
   if (pte) {
     const int na = kind == 0 ? 1 : 2;
