@@ -399,6 +399,10 @@ __global__ void k_add_stats(int n_env, const long long* __restrict__ it, long lo
 struct ipc_scene {
   ipc_scene_desc desc;
   cudaStream_t stream = nullptr;
+  // side stream for the latency-bound contact and body Hessians, which overlap the element
+  // Hessians of the same evaluation (fork and join through the two events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   bool own_stream = false;
   int device = 0;
   std::map<int, HostEnv> envs;
@@ -564,6 +568,9 @@ struct ipc_scene {
     for (auto e : tune_ev)
       if (e) cudaEventDestroy(e);
     if (hpin) cudaFreeHost(hpin);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_ev) cudaEventDestroy(join_ev);
+    if (side) cudaStreamDestroy(side);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
 
@@ -1261,12 +1268,33 @@ struct ipc_scene {
     HT* bH = MODE == MODE_HESS ? hp<HT>(body_H, f_body_H) : nullptr;
     HT* sHp = MODE == MODE_HESS ? hp<HT>(sH, f_sH) : nullptr;
     double h = desc.dt, h2 = h * h;
+    // Hessian evaluations: the body and contact kernels (few blocks, long serial FP64 chains)
+    // run on the side stream beside the element kernels; they write disjoint outputs
+    const bool fork = MODE == MODE_HESS && !capturing;
+    if (fork) {
+      CK(cudaEventRecord(fork_ev, stream));
+      CK(cudaStreamWaitEvent(side, fork_ev, 0));
+      std::swap(stream, side);  // the launches below go to the side stream
+      launch_contacts<MODE, HT>(act, q, h2, bH, sHp);
+      CK(cudaEventRecord(join_ev, stream));
+      std::swap(stream, side);
+    }
     launch(k_inertia_energy, NN, 256, NN, layout(), act, q, (const double*)xtilde.p, nodeE.p);
     int efam = MODE == MODE_ENERGY ? IPC_PROF_LS_ENERGY : IPC_PROF_ELASTIC;
     pbeg(efam);
     launch(k_elastic<MODE, HT>, NT, 128, NT, (const int4*)tets.p, (const double*)tet_prm.p, (const int*)tet_env.p, act,
            q, h2, tetE.p, tet_g.p, tH, e_bad.p, MODE == MODE_ENERGY ? (unsigned long long*)nullptr : punits(IPC_PROF_ELASTIC));
     pend(efam);
+    if (fork) CK(cudaStreamWaitEvent(stream, join_ev, 0));
+    else launch_contacts<MODE, HT>(act, q, h2, bH, sHp);
+    EnergyLists L{nodeE.p, node_off.p, tetE.p, tet_off.p, bodyE.p, body_off.p, sE.p, st_env.p,
+                  n_ct_pt, n_ct - n_ct_pt, n_fr_pt, n_fr};
+    launch_grid(k_env_energy, E, 256, E, L, act, out);
+  }
+  // affine bodies, barrier and friction stencils of one evaluation
+  template <int MODE, class HT>
+  void launch_contacts(const uint8_t* act, const double* q, double h2, HT* bH, HT* sHp) {
+    const double h = desc.dt;
     if constexpr (MODE == MODE_HESS)
       launch(k_bodies_hess<HT>, 16L * NB, BODY_HESS_THREADS, NB, (const int*)body_node.p, (const int*)body_env.p,
              (const uint8_t*)body_kin.p, (const double*)M4.p, (const double*)bvol.p, act, q, (const double*)xtilde.p,
@@ -1287,9 +1315,6 @@ struct ipc_scene {
            (const double*)ptx_t.p, h2, desc.eps_v * h, sE.p + n_ct, sg.p + 12 * (size_t)n_ct,
            sHp ? sHp + 78 * (size_t)n_ct : sHp);
     pend(cfam);
-    EnergyLists L{nodeE.p, node_off.p, tetE.p, tet_off.p, bodyE.p, body_off.p, sE.p, st_env.p,
-                  n_ct_pt, n_ct - n_ct_pt, n_fr_pt, n_fr};
-    launch_grid(k_env_energy, E, 256, E, L, act, out);
   }
 
   // stencil -> node incidence (stable by stencil order within each node)
@@ -1461,10 +1486,15 @@ struct ipc_scene {
       default: fail_with(IPC_ERR_ARG, "pcg_cluster must be -1, 0, 1, 2, 4, 8 or 16");
     }
   }
-  // The solves of the envs in act, PCG_CHUNK iterations per launch at most: after each launch the
+  // The solves of the envs in act, pcg_chunk() iterations per launch at most: after each launch the
   // envs still running are listed on the device and relaunched, with a cluster size chosen for
   // their number. The first launch starts every solve.
-  static constexpr int PCG_CHUNK = 32;
+  // iterations per launch: the FP64 solve (arithmetic-bound) gains from compacting the running
+  // envs more often, the FP32 solve (latency-bound) from fewer host round trips (measured)
+  template <class T>
+  static constexpr int pcg_chunk() {
+    return sizeof(T) == 8 ? 16 : 64;
+  }
   // T: precision of the solve (FP64, or FP32 in mixed precision)
   template <class T>
   void pcg_persistent(const uint8_t* act) {
@@ -1496,7 +1526,7 @@ struct ipc_scene {
     a.n_bodies = NB;
     a.env_list = env_iota.p;
     a.first = 1;
-    a.chunk = PCG_CHUNK;
+    a.chunk = pcg_chunk<T>();
     a.rz_state = pcg_rzs.p;
     a.bb_state = pcg_bbs.p;
     a.iterb_state = pcg_iterb.p;
@@ -1992,6 +2022,9 @@ ipc_status ipc_scene_create(const ipc_scene_desc* desc, ipc_scene** out) {
     s->own_stream = true;
   }
   CK(cudaMallocHost(&s->hpin, 64));
+  CK(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming));
   *out = s.release();
   API_END
 }
