@@ -77,6 +77,12 @@ typedef struct {
                             hold every pair that can come within dhat on the segment); 1: a BVH
                             traversal at every evaluation. Both give the same contacts in the
                             same order. */
+  int32_t kappa_adapt;   /* 0: the barrier stiffness is kappa throughout (Sec. III-D). 1: adapted
+                            per env: at each step start the least-squares balance of the barrier
+                            gradient against the other terms' gradient over the free DOFs,
+                            -(g_E . G) / (G . G), clamped to [kappa, 1000 kappa]; inside a step
+                            doubled (up to 1000 kappa) at an iterate whose closest contact is
+                            nearer than 1e-2 dhat and nearer than at the previous iterate */
   void* cuda_stream;     /* cudaStream_t to borrow, or NULL for a library-owned stream */
 } ipc_scene_desc;
 
@@ -144,9 +150,10 @@ typedef enum {
                               candidates, BSR blocks, sliced-ELL padded blocks; then the PCG
                               cluster size in use (0 = tiled multi-launch PCG) and the most
                               32-row slices of one environment */
-  IPC_Q_ALL_STATUS = 10    /* int32[4 * n_env] for the whole scene (env_id ignored): env id,
+  IPC_Q_ALL_STATUS = 10,   /* int32[4 * n_env] for the whole scene (env_id ignored): env id,
                               status, failure reason, next step of every environment, in one
                               read-back (a serving loop polls this once per step) */
+  IPC_Q_KAPPA = 11         /* double[1]: the env's barrier stiffness in its current (or last) step */
 } ipc_query_kind;
 
 /* Create / destroy a scene on desc->device. */

@@ -460,7 +460,7 @@ static double accd(int kind, const double* x0, const double* p0, double s, doubl
 // ============================================================== environment
 struct Params {
   double dt, dhat, kappa, eps_v, newton_tol, pcg_rel_tol, kappa_affine, gravity[3];
-  int32_t max_newton, max_ls, max_pcg, pad;
+  int32_t max_newton, max_ls, max_pcg, kappa_adapt;  // kappa_adapt: 1 = adapted barrier stiffness
 };
 
 struct SoftDesc {
@@ -546,6 +546,8 @@ struct Env {
   double last_alpha = 1.0;
   std::vector<FrictionContact> fric;
   std::vector<double> ptx_t;  // point positions at step start
+  double kappa = 0.0;            // barrier stiffness of the current step (P.kappa unless adapted)
+  double prev_dmin2 = INFINITY;  // smallest squared contact distance at the previous iterate
   // per-iteration trace (optional)
   int trace = 0;
   std::vector<double> trace_E;
@@ -622,6 +624,7 @@ static void mass_properties(int nv, const double* v, int nt, const int32_t* t, d
 static Env* build_env(const Params& P, const EnvDesc& D) {
   Env* e = new Env();
   e->P = P;
+  e->kappa = P.kappa;
   e->mu = D.mu;
   e->n_soft_bodies = D.n_soft;
   e->n_handles = D.n_soft + D.n_affine;
@@ -1034,12 +1037,12 @@ static double evaluate(Env& e, const std::vector<double>& q, const std::vector<C
     double x12[12];
     gather12(px, c.pts, x12);
     if (want == 0) {
-      Ebar += h2 * contact_barrier_energy(c.kind, x12, e.P.dhat, e.P.kappa, c.eps_x, c.type);
+      Ebar += h2 * contact_barrier_energy(c.kind, x12, e.P.dhat, e.kappa, c.eps_x, c.type);
       continue;
     }
     Dual<12> X[12];
     for (int i = 0; i < 12; ++i) X[i] = Dual<12>::var(i, x12[i]);
-    Dual<12> E = contact_barrier_energy(c.kind, X, e.P.dhat, e.P.kappa, c.eps_x, c.type);
+    Dual<12> E = contact_barrier_energy(c.kind, X, e.P.dhat, e.kappa, c.eps_x, c.type);
     Ebar += h2 * E.v;
     double H12[144];
     for (int i = 0; i < 144; ++i) H12[i] = E.h[i];
@@ -1098,6 +1101,44 @@ static void target_dofs(const Env& e, std::vector<double>& tgt) {
       for (int k = 0; k < 12; ++k) tgt[B.dof + k] = T[12 * B.handle + k];
 }
 
+// smallest squared distance over a contact set at point positions px (INFINITY when empty)
+static double min_contact_d2(const std::vector<double>& px, const std::vector<Contact>& C) {
+  double m = INFINITY;
+  for (const Contact& c : C) {
+    double x12[12];
+    gather12(px, c.pts, x12);
+    m = std::min(m, pair_dist2(c.kind, x12));
+  }
+  return m;
+}
+
+// Barrier stiffness at the start of a step (reading of the adapted-stiffness rule): with g_E the
+// gradient of every other term of the incremental potential at x^t and G the gradient of the
+// barrier term per unit stiffness, the kappa that minimises |g_E + kappa G| over the free DOFs,
+// -(g_E . G) / (G . G), clamped to [kappa, 1000 kappa] of the scene; the scene's kappa when no
+// pair is within dhat. Also records the smallest contact distance at x^t.
+static void kappa_start(Env& e, const std::vector<Contact>& C) {
+  e.prev_dmin2 = min_contact_d2(e.ptx_t, C);
+  if (C.empty()) return;
+  std::vector<double> g0(e.ndof, 0.0), g1(e.ndof, 0.0);
+  e.kappa = 0.0;
+  evaluate(e, e.x, C, 1, &g0, nullptr);
+  e.kappa = 1.0;
+  evaluate(e, e.x, C, 1, &g1, nullptr);
+  double eg = 0.0, gg = 0.0;
+  for (int d = 0; d < e.ndof; ++d) {
+    if (is_kin_dof(e, d)) continue;
+    const double G = g1[d] - g0[d];
+    eg += g0[d] * G;
+    gg += G * G;
+  }
+  e.kappa = e.P.kappa;
+  if (gg > 0.0) {
+    const double k = -eg / gg;
+    if (std::isfinite(k)) e.kappa = std::min(std::max(k, e.P.kappa), 1000.0 * e.P.kappa);
+  }
+}
+
 static void step_setup(Env& e) {
   const double h = e.P.dt;
   e.xt = e.x;
@@ -1116,6 +1157,8 @@ static void step_setup(Env& e) {
   std::vector<Contact> C;
   constraint_set(e, e.ptx_t, C);
   e.fric.clear();
+  e.kappa = e.P.kappa;
+  if (e.P.kappa_adapt) kappa_start(e, C);
   for (const Contact& c : C) {
     double x12[12];
     gather12(e.ptx_t, c.pts, x12);
@@ -1131,7 +1174,7 @@ static void step_setup(Env& e) {
     FrictionContact f;
     for (int i = 0; i < 4; ++i) f.pts[i] = c.pts[i];
     pair_closest(c.kind, x12, f.c, f.n);
-    f.lambda = e.P.kappa * moll * std::fabs(b1);
+    f.lambda = e.kappa * moll * std::fabs(b1);
     e.fric.push_back(f);
   }
 }
@@ -1294,6 +1337,13 @@ static void step_once(Env& e) {
   for (int it = 0; it < e.P.max_newton; ++it) {
     point_positions(e, e.x.data(), px);
     constraint_set(e, px, C);
+    if (e.P.kappa_adapt && it > 0) {
+      // inside a step the stiffness doubles (up to 1000 times the scene's) while the smallest
+      // contact distance is below 1e-2 dhat and still shrinking from one iterate to the next
+      const double m = min_contact_d2(px, C), lim = 1e-2 * e.P.dhat;
+      if (m < lim * lim && m < e.prev_dmin2) e.kappa = std::min(2.0 * e.kappa, 1000.0 * e.P.kappa);
+      e.prev_dmin2 = m;
+    }
     Triplets T;
     double E0 = evaluate(e, e.x, C, 2, &grad, &T);
     if (!std::isfinite(E0)) { e.status = ST_FAILED; e.reason = FAIL_NAN; return; }
@@ -1382,6 +1432,7 @@ extern "C" {
 
 void* or_env_create(const Params* P, const EnvDesc* D) { return build_env(*P, *D); }
 void or_env_destroy(void* h) { delete (Env*)h; }
+double or_env_kappa(void* h) { return ((Env*)h)->kappa; }
 int or_env_ndof(void* h) { return ((Env*)h)->ndof; }
 int or_env_npoints(void* h) { return (int)((Env*)h)->pts.size(); }
 

@@ -55,6 +55,8 @@ def lib():
         L.or_env_points.argtypes = [vp, vp, vp]
         L.or_env_invariants.argtypes = [vp, vp, vp]
         L.or_env_trace.argtypes = [vp, C.c_int]
+        L.or_env_kappa.restype = d
+        L.or_env_kappa.argtypes = [vp]
         L.or_env_trace_get.argtypes = [vp, vp, C.c_int]
         L.or_env_body_mass.argtypes = [vp, C.c_int, vp, vp]
         L.or_env_soft_mass.argtypes = [vp, vp]
@@ -87,7 +89,7 @@ class _Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double), ("eps_v", C.c_double),
                 ("newton_tol", C.c_double), ("pcg_rel_tol", C.c_double), ("kappa_affine", C.c_double),
                 ("gravity", C.c_double * 3), ("max_newton", C.c_int32), ("max_ls", C.c_int32),
-                ("max_pcg", C.c_int32), ("pad", C.c_int32)]
+                ("max_pcg", C.c_int32), ("kappa_adapt", C.c_int32)]
 
 
 class _Soft(C.Structure):
@@ -115,6 +117,7 @@ def _params_struct(p: dict) -> _Params:
     for k in range(3):
         s.gravity[k] = p["gravity"][k]
     s.max_newton, s.max_ls, s.max_pcg = p["max_newton"], p["max_ls"], p["max_pcg"]
+    s.kappa_adapt = int(bool(p.get("kappa_adapt", False)))
     return s
 
 
@@ -178,6 +181,10 @@ class OracleEnv:
         x = np.ascontiguousarray(x, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.float64)
         lib().or_env_set_state(self.h, _p(x), _p(v), step)
+
+    def kappa(self) -> float:
+        """Barrier stiffness of the current (or last) step."""
+        return float(lib().or_env_kappa(self.h))
 
     def status(self) -> dict:
         st = np.zeros(4, dtype=np.int32)

@@ -473,15 +473,15 @@ DEV double barrier_eval(const ContactRec& c, const double* __restrict__ ptx, dou
 // energy and gradient modes: one thread per contact
 template <int MODE>
 __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
-                          const double* __restrict__ ptx, double h2, double dhat, double kappa, double* __restrict__ sE,
-                          double* __restrict__ sg) {
+                          const double* __restrict__ ptx, double h2, double dhat, const double* __restrict__ kappa,
+                          double* __restrict__ sE, double* __restrict__ sg) {
   static_assert(MODE != MODE_HESS, "the Hessian mode is k_barrier_hess");
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_ct) return;
   ContactRec c = ct[k];
   if (!act[c.env]) return;
   double g[12];
-  sE[k] = barrier_eval<MODE>(c, ptx, h2, dhat, kappa, g, nullptr);
+  sE[k] = barrier_eval<MODE>(c, ptx, h2, dhat, kappa[c.env], g, nullptr);
   if (MODE == MODE_GRAD)
     for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = g[i];
 }
@@ -495,8 +495,8 @@ constexpr int BARRIER_HESS_THREADS = 128;
 template <class HT>
 __global__ void __launch_bounds__(BARRIER_HESS_THREADS)
     k_barrier_hess(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
-                   const double* __restrict__ ptx, double h2, double dhat, double kappa, double* __restrict__ sE,
-                   double* __restrict__ sg, HT* __restrict__ sH) {
+                   const double* __restrict__ ptx, double h2, double dhat, const double* __restrict__ kappa,
+                   double* __restrict__ sE, double* __restrict__ sg, HT* __restrict__ sH) {
   static_assert(144 <= 2 * BARRIER_HESS_THREADS, "two matrix elements per thread at most");
   __shared__ double A[144], V[144], W[144], R[36];
   __shared__ float Af[144], Vf[144], Rf[36];
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(BARRIER_HESS_THREADS)
   if (!act[c.env]) return;
   if (t == 0) {
     double g[12];
-    sE[k] = barrier_eval<MODE_HESS>(c, ptx, h2, dhat, kappa, g, A);
+    sE[k] = barrier_eval<MODE_HESS>(c, ptx, h2, dhat, kappa[c.env], g, A);
     for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = g[i];
   }
   __syncthreads();

@@ -443,6 +443,9 @@ struct ipc_scene {
   DBuf<double> ptx, ptx_t, ptp, pte;
   // env control
   DBuf<int> e_status, e_reason, e_step, e_constrained, e_bad, e_nanp, e_halv, e_newton_it, e_count, e_rem;
+  // barrier stiffness per env, its closest-contact tracking and the step-start sums
+  DBuf<double> e_kappa, e_kprev, e_kdots, g0buf;
+  DBuf<unsigned long long> e_dmin2;
   DBuf<uint8_t> e_stepping, e_iter, e_ls, e_accept, e_sel, e_all, e_start, e_cover;
   DBuf<double> e_E0, e_Et, e_alpha;
   DBuf<unsigned long long> e_alpha_bits, e_pnorm_bits, e_inter, e_inv;
@@ -1015,6 +1018,11 @@ struct ipc_scene {
     }
     launch(k_fill_u8, E, 256, E, e_all.p, (uint8_t)1);
     for (DBuf<double>* b : {&e_E0, &e_Et, &e_alpha}) b->alloc(E);
+    e_kappa.alloc(E);
+    e_kprev.alloc(E);
+    e_kdots.alloc(2 * (size_t)E);
+    e_dmin2.alloc(E);
+    launch(k_env_fill, E, 128, E, (const uint8_t*)nullptr, e_kappa.p, desc.kappa);
     for (DBuf<unsigned long long>* b : {&e_alpha_bits, &e_pnorm_bits, &e_inter, &e_inv}) b->alloc(E);
     nodeE.alloc(NN);
     tetE.alloc(NT);
@@ -1262,6 +1270,7 @@ struct ipc_scene {
   void evaluate_t(const double* q, const uint8_t* act, double* out) {
     launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p, q, ptx.p);
     contacts_at(act);
+    if (MODE == MODE_HESS && desc.kappa_adapt) kappa_iterate(act);
     stencil_table();
     // Hessian outputs (taken after stencil_table, which may grow the stencil buffers)
     HT* tH = MODE == MODE_HESS ? hp<HT>(tet_H, f_tet_H) : nullptr;
@@ -1307,14 +1316,45 @@ struct ipc_scene {
     pbeg(cfam);
     if constexpr (MODE == MODE_HESS)
       launch(k_barrier_hess<HT>, (long)BARRIER_HESS_THREADS * n_ct, BARRIER_HESS_THREADS, n_ct, (const ContactRec*)ct.p,
-             act, (const double*)ptx.p, h2, desc.dhat, desc.kappa, sE.p, sg.p, sHp);
+             act, (const double*)ptx.p, h2, desc.dhat, (const double*)e_kappa.p, sE.p, sg.p, sHp);
     else
       launch(k_barrier<MODE>, n_ct, 64, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, h2, desc.dhat,
-             desc.kappa, sE.p, sg.p);
+             (const double*)e_kappa.p, sE.p, sg.p);
     launch(k_friction<MODE, HT>, n_fr, 128, n_fr, (const FrictionRec*)fr.p, act, (const double*)ptx.p,
            (const double*)ptx_t.p, h2, desc.eps_v * h, sE.p + n_ct, sg.p + 12 * (size_t)n_ct,
            sHp ? sHp + 78 * (size_t)n_ct : sHp);
     pend(cfam);
+  }
+
+  // ------------------------------------------------------------------ adapted stiffness
+  // closest contact of every env in act (contacts ct at ptx), then the doubling test
+  void kappa_iterate(const uint8_t* act) {
+    CK(cudaMemsetAsync(e_dmin2.p, 0x7f, E * sizeof(unsigned long long), stream));  // > every finite d^2
+    launch(k_env_min_d2, n_ct, 128, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, e_dmin2.p);
+    const double lim = 1e-2 * desc.dhat;
+    launch(k_env_kappa_iter, E, 128, E, ctl(), act, (const unsigned long long*)e_dmin2.p, e_kprev.p, e_kappa.p,
+           1000.0 * desc.kappa, lim * lim);
+  }
+  // gradient of the incremental potential at the DOFs x for the envs in act, into grad
+  void gradient_at_x(const uint8_t* act) {
+    evaluate<MODE_GRAD>(x.p, act, e_Et.p);
+    stencil_incidence(act);
+    launch(k_assemble_grad, NN, 256, NN, layout(), act, (const double*)x.p, (const double*)xtilde.p,
+           (const int*)nt_ptr.p, (const int*)nt_src.p, (const double*)tet_g.p, (const double*)body_g.p,
+           (const int*)ns_ptr.p, (const int*)ns_src.p, (const int*)st_pts.p, (const double*)sg.p, grad.p, nodeE.p);
+  }
+  // stiffness of the envs in act at their step start (x = x^t; their friction lag not yet made,
+  // or made at x^t, where it has no gradient)
+  void kappa_start(const uint8_t* act) {
+    g0buf.ensure(3 * (size_t)NN);
+    launch(k_env_fill, E, 128, E, act, e_kappa.p, 0.0);
+    gradient_at_x(act);
+    CK(cudaMemcpyAsync(g0buf.p, grad.p, 3 * (size_t)NN * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    launch(k_env_fill, E, 128, E, act, e_kappa.p, 1.0);
+    gradient_at_x(act);
+    launch_grid(k_env_kappa_dots, E, 256, E, layout(), act, (const int*)node_off.p, (const double*)g0buf.p,
+                (const double*)grad.p, e_kdots.p);
+    launch(k_env_kappa_start, E, 128, E, act, (const double*)e_kdots.p, desc.kappa, 1000.0 * desc.kappa, e_kappa.p);
   }
 
   // stencil -> node incidence (stable by stencil order within each node)
@@ -1685,9 +1725,13 @@ struct ipc_scene {
     list_ok = false;
     constraint_set(act);
     CK(cudaMemcpyAsync(ptx_t.p, ptx.p, 3 * (size_t)NP * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    if (desc.kappa_adapt) {
+      CK(cudaMemsetAsync(e_newton_it.p, 0, E * sizeof(int), stream));  // the evaluations here are iterate 0
+      kappa_start(act);  // its evaluations leave the contacts of act at x^t in ct
+    }
     fr.ensure(n_ct + 1);
     launch(k_friction_setup, n_ct, 128, n_ct, (const ContactRec*)ct.p, (const double*)ptx.p, (const double*)env_mu.p,
-           desc.dhat, desc.kappa, fr.p);
+           desc.dhat, (const double*)e_kappa.p, fr.p);
     n_fr = n_ct;
     n_fr_pt = n_ct_pt;
   }
@@ -1851,6 +1895,7 @@ struct ipc_scene {
       if (reuse_lists()) cand_src = CAND_STATIC;  // this round's evaluations are at x^t
     }
     launch(k_copy_points_env, NP, 256, NP, layout(), start, (const double*)ptx.p, ptx_t.p);
+    if (desc.kappa_adapt) kappa_start(start);
     friction_merge(start);
   }
   // lagged friction records of the starting envs from their contacts at x^t (ct), merged with
@@ -1859,7 +1904,7 @@ struct ipc_scene {
     const int n_new = n_ct, n_new_pt = n_ct_pt, n_old = n_fr, n_old_pt = n_fr_pt, tot = n_old + n_new;
     fr_new.ensure(n_new + 1);
     launch(k_friction_setup, n_new, 128, n_new, (const ContactRec*)ct.p, (const double*)ptx.p,
-           (const double*)env_mu.p, desc.dhat, desc.kappa, fr_new.p);
+           (const double*)env_mu.p, desc.dhat, (const double*)e_kappa.p, fr_new.p);
     if (tot == 0) {
       n_fr = n_fr_pt = 0;
       return;
@@ -2236,6 +2281,12 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       CK(cudaStreamSynchronize(s->stream));
       v[2] = v[3];
       return copy_out(v, sizeof(v), out, out_bytes, written);
+    }
+    case IPC_Q_KAPPA: {
+      double v = 0.0;
+      CK(cudaMemcpyAsync(&v, s->e_kappa.p + li, 8, cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      return copy_out(&v, sizeof(v), out, out_bytes, written);
     }
     case IPC_Q_STATS: {
       long long v[5];

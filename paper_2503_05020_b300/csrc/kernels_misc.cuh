@@ -702,7 +702,7 @@ __global__ void k_compact_contacts(int n, const int* __restrict__ flag, const in
 
 // lagged friction at x^t: lambda = kappa e |b'(d)|, closest-point coefficients and normal
 __global__ void k_friction_setup(int n_ct, const ContactRec* __restrict__ ct, const double* __restrict__ ptx,
-                                 const double* __restrict__ env_mu, double dhat, double kappa,
+                                 const double* __restrict__ env_mu, double dhat, const double* __restrict__ kappa_env,
                                  FrictionRec* __restrict__ fr) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_ct) return;
@@ -730,7 +730,7 @@ __global__ void k_friction_setup(int n_ct, const ContactRec* __restrict__ ct, co
   f.n[0] = n.x;
   f.n[1] = n.y;
   f.n[2] = n.z;
-  f.mu_lambda = env_mu[c.env] * kappa * m * fabs(b1);
+  f.mu_lambda = env_mu[c.env] * kappa_env[c.env] * m * fabs(b1);
   fr[k] = f;
 }
 
@@ -787,6 +787,74 @@ __global__ void k_stencil_emit(int n_st, const int* __restrict__ st_pts, const i
 __global__ void k_count_keys(int n, const unsigned long long* __restrict__ keys, int* __restrict__ cnt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) atomicAdd(&cnt[keys[i]], 1);
+}
+
+// ---------------------------------------------------------------- adapted barrier stiffness
+// Squared distance of the closest contact of every env (non-negative doubles: their bit patterns
+// order like the values, so an integer atomic minimum gives the exact minimum in any order).
+__global__ void k_env_min_d2(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
+                             const double* __restrict__ ptx, unsigned long long* __restrict__ dmin2) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_ct) return;
+  const ContactRec c = ct[k];
+  if (!act[c.env]) return;
+  d3 X[4];
+  for (int i = 0; i < 4; ++i) X[i] = ld3(ptx, c.pts[i]);
+  int type;
+  const double d2 = pair_d2(c.kind, X, &type);
+  atomicMin(&dmin2[c.env], (unsigned long long)__double_as_longlong(d2));
+}
+// Inside a step the stiffness of an env doubles (up to kmax) at an iterate whose closest contact
+// is nearer than lim (squared: lim2) and nearer than at the previous iterate.
+__global__ void k_env_kappa_iter(int n_env, EnvCtl C, const uint8_t* __restrict__ act,
+                                 const unsigned long long* __restrict__ dmin2, double* __restrict__ prev,
+                                 double* __restrict__ kappa, double kmax, double lim2) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_env || !act[e]) return;
+  const double m = __longlong_as_double((long long)dmin2[e]);
+  if (C.newton_it[e] > 0 && m < lim2 && m < prev[e]) kappa[e] = fmin(2.0 * kappa[e], kmax);
+  prev[e] = m;
+}
+// Start of a step: per env, over its free DOFs, g0 . G and G . G with g0 the gradient without the
+// barrier (stiffness 0) and G = g1 - g0 the barrier's gradient per unit stiffness; one block per
+// env, fixed-order block sums (the result does not depend on the batch).
+__global__ void k_env_kappa_dots(int n_env, Layout L, const uint8_t* __restrict__ act, const int* __restrict__ node_off,
+                                 const double* __restrict__ g0, const double* __restrict__ g1, double* __restrict__ dots) {
+  __shared__ double sh[256];
+  const int e = blockIdx.x;
+  if (e >= n_env || !act[e]) return;
+  double a = 0.0, b = 0.0;
+  for (long i = 3L * node_off[e] + threadIdx.x; i < 3L * node_off[e + 1]; i += blockDim.x) {
+    const int nd = (int)(i / 3), bd = L.node_body[nd];
+    const bool kin = bd < 0 ? L.node_kin[nd] : L.body_kin[bd];
+    if (kin) continue;
+    const double G = g1[i] - g0[i];
+    a += g0[i] * G;
+    b += G * G;
+  }
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    dots[2 * e] = a;
+    dots[2 * e + 1] = b;
+  }
+}
+// kappa = -(g0 . G) / (G . G) clamped to [kmin, kmax]; kmin where no contact pulls (G = 0)
+__global__ void k_env_kappa_start(int n_env, const uint8_t* __restrict__ act, const double* __restrict__ dots,
+                                  double kmin, double kmax, double* __restrict__ kappa) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_env || !act[e]) return;
+  double k = kmin;
+  const double gg = dots[2 * e + 1];
+  if (gg > 0.0) {
+    const double r = -dots[2 * e] / gg;
+    if (isfinite(r)) k = fmin(fmax(r, kmin), kmax);
+  }
+  kappa[e] = k;
+}
+__global__ void k_env_fill(int n_env, const uint8_t* __restrict__ act, double* __restrict__ a, double v) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n_env && (!act || act[e])) a[e] = v;
 }
 
 // ---------------------------------------------------------------- per-env step start

@@ -22,7 +22,7 @@ ENV_STATUS = {0: "ACTIVE", 1: "DONE", 2: "FAILED"}
 FAIL_REASON = {0: "none", 1: "newton_cap", 2: "line_search", 3: "non_finite", 4: "initial_intersection", 5: "internal"}
 FP64, MIXED = 0, 1
 Q_DOFS, Q_VELOCITIES, Q_STATUS, Q_STATS, Q_CANDIDATES, Q_CONTACTS, Q_POINTS, Q_SIZES, Q_INTERSECTIONS, \
-    Q_SCENE_COUNTERS, Q_ALL_STATUS = range(11)
+    Q_SCENE_COUNTERS, Q_ALL_STATUS, Q_KAPPA = range(12)
 
 
 class IpcError(RuntimeError):
@@ -37,7 +37,7 @@ class SceneDesc(C.Structure):
                 ("gravity", C.c_double * 3), ("max_newton", C.c_int32), ("max_ls_halvings", C.c_int32),
                 ("max_pcg_iters", C.c_int32), ("precision", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
                 ("device", C.c_int32), ("pcg_cluster", C.c_int32), ("fresh_broad_phase", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("kappa_adapt", C.c_int32), ("cuda_stream", C.c_void_p)]
 
 
 class SoftDesc(C.Structure):
@@ -160,6 +160,7 @@ class Scene:
         d.precision, d.hbm_budget_bytes, d.device = precision, hbm_budget_bytes, device
         d.pcg_cluster = pcg_cluster  # 0 automatic, 1/2/4/8 CTAs per env cluster, -1 tiled multi-launch
         d.fresh_broad_phase = int(bool(fresh_broad_phase))  # 1: a BVH traversal at every evaluation
+        d.kappa_adapt = int(bool(params.get("kappa_adapt", False)))  # 1: adapted barrier stiffness per env
         d.cuda_stream = stream
         self._h = C.c_void_p()
         _check(lib().ipc_scene_create(C.byref(d), C.byref(self._h)))
@@ -232,6 +233,10 @@ class Scene:
         keys = ["contacts", "pt_contacts", "friction", "incidence_entries", "longest_list", "candidates",
                 "bsr_blocks", "sell_blocks", "pcg_cluster", "max_env_slices"]
         return dict(zip(keys, map(int, v)))
+
+    def kappa(self, eid: int) -> float:
+        """The env's barrier stiffness in its current (or last) step."""
+        return float(self._query(eid, Q_KAPPA, np.float64)[0])
 
     def all_status(self) -> dict:
         """{env id: (status, reason, next step)} for every environment, in one read-back."""

@@ -380,3 +380,25 @@ def test_batched_pad_grasps_do_the_work_of_each_alone():
         (xa, sa), = run([k])
         assert sa["status"] == "ACTIVE" and sa == both[k][1]
         assert np.array_equal(xa, both[k][0])
+
+
+def test_adapted_stiffness_trajectory_and_kappa_parity():
+    """The squeezed cube with the adapted barrier stiffness: per step, the GPU's kappa equals the
+    oracle's (1e-9 relative: the step-start least squares sums in another order) and the
+    trajectories agree within 1e-6 m; the stiffness did adapt."""
+    p = dict(S.parity_params(S.scene_params(0.01)), kappa_adapt=True)
+    env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+    o = O.OracleEnv(p, env)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    ks = []
+    for k in range(40):
+        o.step(1)
+        sc.step(1)
+        ks.append(o.kappa())
+        assert abs(sc.kappa(eid) / o.kappa() - 1.0) <= 1e-9, (k, sc.kappa(eid), o.kappa())
+        if k % 10 == 9:
+            xo, _ = o.state()
+            assert np.abs(sc.dofs(eid) - xo).max() <= TRAJ_TOL, k
+    assert max(ks) > p["kappa"]
+    assert sc.invariants(eid) == {"intersections": 0, "inverted": 0}

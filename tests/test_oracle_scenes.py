@@ -232,3 +232,50 @@ def test_env_gradient_fd_pd_target_term():
     x, _ = e.state()
     q = x + np.random.default_rng(2).normal(size=x.size) * 1e-4
     _fd_check(e, q, list(range(12)))
+
+
+def test_adapted_stiffness_at_rest_balances_the_contact_vertices_weight():
+    """Adapted barrier stiffness at a step start: the kappa that minimises |g_E + kappa G| over
+    the free DOFs (g_E: gradient of every other term, G: the barrier's per unit kappa). A soft
+    block at rest with its 9 bottom vertices a gap d above a fixed ground triangle, gravity on,
+    has g_E = m_i h^2 g on each vertex and G = h^2 b'(d) on the bottom ones, so kappa equals
+    g times the bottom vertices' mean mass over |b'(d)| (b' written out from
+    b(d) = -(d - dhat)^2 ln(d / dhat)). The scene's kappa (the clamp's floor) is set low."""
+    h = 0.01
+    p = S.scene_params(h, kappa=1.0)
+    p["kappa_adapt"] = True
+    gap = 0.5 * p["dhat"]
+    env = S.resting_env("block", n_steps=2, gap=gap)
+    e = O.OracleEnv(p, env)
+    e.step(1)
+    verts = np.asarray(env["soft"][0]["verts"])
+    m = e.soft_mass(len(verts))
+    bottom = np.abs(verts[:, 2] - gap) < 1e-12
+    assert bottom.sum() == 9
+    d, dh = gap, p["dhat"]
+    b1 = -2.0 * (d - dh) * math.log(d / dh) - (d - dh) ** 2 / d
+    expect = G * m[bottom].mean() / abs(b1)
+    assert 1.0 < expect < 1000.0  # inside the clamp [kappa, 1000 kappa]
+    assert abs(e.kappa() / expect - 1.0) < 1e-9
+
+
+def test_adapted_stiffness_stays_in_its_bounds_and_keeps_the_invariants():
+    """Squeezed cube with the adapted stiffness: every step's kappa lies in [kappa, 1000 kappa]
+    of the scene, and the run stays free of intersections and inverted tets; without adaptation
+    the stiffness is the scene's throughout."""
+    p = S.scene_params(0.01)
+    env = S.cube_squeeze_env(0, n_steps=30, close_steps=15)
+    fixed = O.OracleEnv(p, env)
+    fixed.step(3)
+    assert fixed.kappa() == p["kappa"]
+    pa = dict(p, kappa_adapt=True)
+    e = O.OracleEnv(pa, env)
+    ks = []
+    for _ in range(30):
+        assert e.step(1) in ("ACTIVE", "DONE")
+        ks.append(e.kappa())
+        x, _ = e.state()
+        inv = e.invariants(x)
+        assert inv["intersections"] == 0 and inv["inverted"] == 0
+    assert min(ks) >= p["kappa"] and max(ks) <= 1000.0 * p["kappa"]
+    assert max(ks) > p["kappa"]  # contact made the stiffness adapt
