@@ -1,5 +1,5 @@
 // Device helpers shared by the sm_103a kernels: 3-vector math, order-preserving atomics on
-// non-negative doubles, small symmetric eigensolvers and Cholesky inverses.
+// non-negative doubles, small symmetric eigensolvers and inverses.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -475,57 +475,6 @@ DEV void eig_sym3(const T A_in[9], T w[3], T V[9]) {
     V[5] = -V[5];
     V[8] = -V[8];
   }
-}
-
-// In-place inverse of an SPD N x N matrix (row-major) via Cholesky in the precision T; returns false when a pivot
-// is not positive (then A is set to the inverse of its diagonal, or 0 where that is not > 0).
-template <int N, class T = double>
-__device__ __noinline__ bool spd_inverse(T* A) {  // out of line, see project_psd_jacobi
-  T L[N * N];
-  for (int i = 0; i < N * N; ++i) L[i] = T(0);
-  bool ok = true;
-  for (int j = 0; j < N && ok; ++j) {
-    T s = A[j * N + j];
-    for (int k = 0; k < j; ++k) s -= L[j * N + k] * L[j * N + k];
-    if (!(s > T(0))) {
-      ok = false;
-      break;
-    }
-    T d = sqrt(s);
-    L[j * N + j] = d;
-    for (int i = j + 1; i < N; ++i) {
-      T t = A[i * N + j];
-      for (int k = 0; k < j; ++k) t -= L[i * N + k] * L[j * N + k];
-      L[i * N + j] = t / d;
-    }
-  }
-  if (!ok) {
-    for (int i = 0; i < N; ++i)
-      for (int j = 0; j < N; ++j) {
-        T d = A[i * N + i];
-        A[i * N + j] = (i == j && d > T(0)) ? T(1) / d : T(0);
-      }
-    return false;
-  }
-  // inverse of L (lower), then A^-1 = L^-T L^-1
-  T Li[N * N];
-  for (int i = 0; i < N * N; ++i) Li[i] = T(0);
-  for (int i = 0; i < N; ++i) {
-    Li[i * N + i] = T(1) / L[i * N + i];
-    for (int j = 0; j < i; ++j) {
-      T s = T(0);
-      for (int k = j; k < i; ++k) s -= L[i * N + k] * Li[k * N + j];
-      Li[i * N + j] = s / L[i * N + i];
-    }
-  }
-  for (int i = 0; i < N; ++i)
-    for (int j = i; j < N; ++j) {
-      T s = T(0);
-      for (int k = j; k < N; ++k) s += Li[k * N + i] * Li[k * N + j];
-      A[i * N + j] = s;
-      A[j * N + i] = s;
-    }
-  return true;
 }
 
 // 3x3 symmetric positive-definite inverse by the adjugate (row-major); zero if not invertible.

@@ -1169,11 +1169,10 @@ struct ipc_scene {
     CandOut o{cnt_pt.p, nullptr, slots_pt.p, overflow.p, CAND_CAP};
     pbeg(IPC_PROF_BROAD);
     launch(k_trav_pt<TRAV_COLLECT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
-           (const double*)ptx.p, (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), o,
-           (const double*)nullptr, ctl());
+           (const double*)ptx.p, (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), o);
     CandOut oe{cnt_ee.p, nullptr, slots_ee.p, overflow.p, CAND_CAP};
     launch(k_trav_ee<TRAV_COLLECT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
-           (const double*)tedge.pbox.p, tree(tedge), ptinfo(), oe, (const double*)nullptr, (const double*)nullptr, ctl());
+           (const double*)tedge.pbox.p, tree(tedge), ptinfo(), oe);
     pend(IPC_PROF_BROAD);
     scan(cnt_pt.p, NSV, off_pt.p, false);
     scan(cnt_ee.p, NED, off_ee.p, false);
@@ -1184,11 +1183,10 @@ struct ipc_scene {
     if (spilled) {
       CandOut f{nullptr, off_pt.p, cand_j.p, overflow.p, 0, cand_q.p};
       launch(k_trav_pt<TRAV_FILL>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
-             (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), f, (const double*)nullptr, ctl());
+             (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), f);
       CandOut fe{nullptr, off_ee.p, cand_j.p + n_pt, overflow.p, 0, cand_q.p + n_pt};
       launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
-             (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr, (const double*)nullptr,
-             ctl());
+             (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe);
     } else {
       launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)cnt_pt.p, (const int*)slots_pt.p,
              (const int*)off_pt.p, cand_j.p, cand_q.p, 1);
@@ -1608,8 +1606,12 @@ struct ipc_scene {
       a.first = 0;
       a.env_list = env_list.p;
       C = tuned_cluster(n, &slot);
+      // once every running solve fits in the largest clusters, a relaunch gives none of them more
+      // CTAs: run them to the end in long chunks (fewer launches and host round trips)
+      if (bucket_of(n) == 2) a.chunk = PCG_TAIL_CHUNK;
     }
   }
+  static constexpr int PCG_TAIL_CHUNK = 128;
   void pcg(const uint8_t* act) {
     if (mixed()) {
       pcg_persistent<float>(act);
@@ -1784,11 +1786,10 @@ struct ipc_scene {
     list_ok = false;
     CandOut cp{ccd_cnt_pt.p, nullptr, slots_pt.p, overflow.p, CAND_CAP};
     launch(k_trav_pt<TRAV_COLLECT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
-           (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), cp,
-           (const double*)nullptr, C);
+           (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), cp);
     CandOut ce{ccd_cnt_ee.p, nullptr, slots_ee.p, overflow.p, CAND_CAP};
     launch(k_trav_ee<TRAV_COLLECT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
-           (const double*)tedge.pbox.p, tree(tedge), ptinfo(), ce, (const double*)nullptr, (const double*)nullptr, C);
+           (const double*)tedge.pbox.p, tree(tedge), ptinfo(), ce);
     scan(ccd_cnt_pt.p, NSV, ccd_off_pt.p, false);
     scan(ccd_cnt_ee.p, NED, ccd_off_ee.p, false);
     int np = 0, ne = 0;
@@ -1803,18 +1804,14 @@ struct ipc_scene {
         CandOut fe{nullptr, ccd_off_ee.p, ccd_j.p + np, overflow.p, 0, ccd_q.p + np};
         if (keep) {
           launch(k_trav_pt<TRAV_FILL>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
-                 (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
-                 (const double*)nullptr, C);
+                 (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp);
           launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
-                 (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr,
-                 (const double*)nullptr, C);
+                 (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe);
         } else {
           launch(k_trav_pt<TRAV_FILLU>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
-                 (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp,
-                 (const double*)nullptr, C);
+                 (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), fp);
           launch(k_trav_ee<TRAV_FILLU>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
-                 (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe, (const double*)nullptr,
-                 (const double*)nullptr, C);
+                 (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe);
         }
       } else {
         launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)ccd_cnt_pt.p, (const int*)slots_pt.p,

@@ -406,10 +406,10 @@ DEV bool excluded(const PtInfo& P, int a, int b, int c, int d) {
   return ba >= 0 && P.body[b] == ba && P.body[c] == ba && P.body[d] == ba;
 }
 
-// count, fill (partners sorted per query), swept-box ACCD inline, fill unsorted, and collect:
-// count while keeping the first `cap` partners of each query in its own slots (one traversal
-// instead of count + fill when no query finds more than cap)
-enum { TRAV_COUNT = 0, TRAV_FILL = 1, TRAV_CCD = 2, TRAV_FILLU = 3, TRAV_COLLECT = 4 };
+// fill (partners sorted per query, at offsets from a previous count), fill unsorted, and
+// collect: count while keeping the first `cap` partners of each query in its own slots (one
+// traversal instead of count + fill when no query finds more than cap)
+enum { TRAV_FILL = 1, TRAV_FILLU = 3, TRAV_COLLECT = 4 };
 
 struct CandOut {
   int* cnt;        // per query (count and collect modes)
@@ -424,13 +424,12 @@ struct CandOut {
 template <int MODE>
 __global__ void k_trav_pt(int n_sv, const int* __restrict__ sv_pt, const int* __restrict__ sv_env,
                           const uint8_t* __restrict__ act, const double* __restrict__ ptx, const double* __restrict__ pte,
-                          double r, Tree T, const int* __restrict__ tri_pt, PtInfo P, CandOut O,
-                          const double* __restrict__ ptp, EnvCtl C) {
+                          double r, Tree T, const int* __restrict__ tri_pt, PtInfo P, CandOut O) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n_sv) return;
   int e = sv_env[q];
   if (!act[e]) {
-    if (MODE == TRAV_COUNT || MODE == TRAV_COLLECT) O.cnt[q] = 0;
+    if (MODE == TRAV_COLLECT) O.cnt[q] = 0;
     return;
   }
   int v = sv_pt[q];
@@ -447,8 +446,6 @@ __global__ void k_trav_pt(int n_sv, const int* __restrict__ sv_pt, const int* __
   }
   int count = 0;
   int base = (MODE == TRAV_FILL || MODE == TRAV_FILLU) ? O.off[q] : 0;
-  double tmin = 1.0;
-  long iters = 0;
   bool ok = bvh_visit(T, e, qb, [&](int j) {
     int a = tri_pt[3 * j], b = tri_pt[3 * j + 1], c = tri_pt[3 * j + 2];
     if (a == v || b == v || c == v) return;
@@ -458,18 +455,10 @@ __global__ void k_trav_pt(int n_sv, const int* __restrict__ sv_pt, const int* __
       if (O.cq) O.cq[base + count] = q;
     }
     if (MODE == TRAV_COLLECT && count < O.cap) O.cj[(long)q * O.cap + count] = j;
-    if (MODE == TRAV_CCD) {
-      d3 X[4] = {ld3(ptx, v), ld3(ptx, a), ld3(ptx, b), ld3(ptx, c)};
-      d3 Pd[4] = {ld3(ptp, v), ld3(ptp, a), ld3(ptp, b), ld3(ptp, c)};
-      long it;
-      double t = accd(0, X, Pd, 0.1, 1.0, 1000000L, &it);
-      iters += it;
-      tmin = fmin(tmin, t);
-    }
     ++count;
   });
   if (!ok) atomicOr(O.overflow, 1);
-  if (MODE == TRAV_COUNT || MODE == TRAV_COLLECT) O.cnt[q] = count;
+  if (MODE == TRAV_COLLECT) O.cnt[q] = count;
   if (MODE == TRAV_COLLECT && count > O.cap) atomicOr(O.overflow + 1, 1);
   if (MODE == TRAV_FILL) {
     // sort this query's partners ascending (insertion sort; short lists)
@@ -483,30 +472,24 @@ __global__ void k_trav_pt(int n_sv, const int* __restrict__ sv_pt, const int* __
       s[k + 1] = key;
     }
   }
-  if (MODE == TRAV_CCD && count > 0) {
-    atomic_min_pos(&C.alpha_bits[e], tmin);
-    atomicAdd((unsigned long long*)&C.stats[5 * e + STAT_ACCD], (unsigned long long)iters);
-  }
 }
 
 // edge-edge candidates: edge q against the edge tree of its env, partners j > q
 template <int MODE>
 __global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __restrict__ ed_env,
                           const uint8_t* __restrict__ act, const double* __restrict__ edge_box, Tree T, PtInfo P,
-                          CandOut O, const double* __restrict__ ptx, const double* __restrict__ ptp, EnvCtl C) {
+                          CandOut O) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n_ed) return;
   int e = ed_env[q];
   if (!act[e]) {
-    if (MODE == TRAV_COUNT || MODE == TRAV_COLLECT) O.cnt[q] = 0;
+    if (MODE == TRAV_COLLECT) O.cnt[q] = 0;
     return;
   }
   int a0 = ed_pt[2 * q], a1 = ed_pt[2 * q + 1];
   const double* qb = edge_box + 6L * q;
   int count = 0;
   int base = (MODE == TRAV_FILL || MODE == TRAV_FILLU) ? O.off[q] : 0;
-  double tmin = 1.0;
-  long iters = 0;
   bool ok = bvh_visit(T, e, qb, [&](int j) { return j > q; }, [&](int j) {
     int b0 = ed_pt[2 * j], b1 = ed_pt[2 * j + 1];
     if (a0 == b0 || a0 == b1 || a1 == b0 || a1 == b1) return;
@@ -516,18 +499,10 @@ __global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __
       if (O.cq) O.cq[base + count] = q;
     }
     if (MODE == TRAV_COLLECT && count < O.cap) O.cj[(long)q * O.cap + count] = j;
-    if (MODE == TRAV_CCD) {
-      d3 X[4] = {ld3(ptx, a0), ld3(ptx, a1), ld3(ptx, b0), ld3(ptx, b1)};
-      d3 Pd[4] = {ld3(ptp, a0), ld3(ptp, a1), ld3(ptp, b0), ld3(ptp, b1)};
-      long it;
-      double t = accd(1, X, Pd, 0.1, 1.0, 1000000L, &it);
-      iters += it;
-      tmin = fmin(tmin, t);
-    }
     ++count;
   });
   if (!ok) atomicOr(O.overflow, 1);
-  if (MODE == TRAV_COUNT || MODE == TRAV_COLLECT) O.cnt[q] = count;
+  if (MODE == TRAV_COLLECT) O.cnt[q] = count;
   if (MODE == TRAV_COLLECT && count > O.cap) atomicOr(O.overflow + 1, 1);
   if (MODE == TRAV_FILL) {
     int* s = O.cj + base;
@@ -539,10 +514,6 @@ __global__ void k_trav_ee(int n_ed, const int* __restrict__ ed_pt, const int* __
       }
       s[k + 1] = key;
     }
-  }
-  if (MODE == TRAV_CCD && count > 0) {
-    atomic_min_pos(&C.alpha_bits[e], tmin);
-    atomicAdd((unsigned long long*)&C.stats[5 * e + STAT_ACCD], (unsigned long long)iters);
   }
 }
 
