@@ -419,7 +419,8 @@ def run_reference(args):
         t_timed += time.perf_counter() - t0
         done += 1
     value = len(oe) * done / t_timed
-    tets = int(np.mean([sum(len(s["tets"]) for s in e["soft"]) for e in envs]))
+    # the workload's config is the GPU arm's (all its envs); the timed sample is its first envs
+    tets = int(np.mean([sum(len(s["tets"]) for s in e["soft"]) for e in make_envs(0, args.envs)]))
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": 0, "steps": done,
             "warmup": min(args.warmup, 1), "ms_per_step": round(1000 * t_timed / max(done, 1), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
