@@ -66,8 +66,31 @@ def workload_config(n_env, tets, start):
             "parallelism": "replicas"}
 
 
+def shard_env_ids(rank, n_env):
+    """Env seeds of one rank: rank r steps envs r*n .. r*n + n - 1 (independent replicas with
+    disjoint envs; the batch shards across ranks with no data-path collective)."""
+    return [rank * n_env + i for i in range(n_env)]
+
+
 def make_envs(rank, n_env):
-    return [S.pad_grasp_env(rank * n_env + i) for i in range(n_env)]
+    return [S.pad_grasp_env(i) for i in shard_env_ids(rank, n_env)]
+
+
+def max_over_ranks(v, world, device):
+    """The largest value over the ranks: a run's time is its slowest rank's."""
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_env, steps, seconds):
+    """Whole-job env-steps/s: the envs and steps of every rank over the slowest rank's time."""
+    return world * n_env * steps / seconds
 
 
 class ClockSampler:
@@ -231,14 +254,8 @@ def run_ours(args):
     steps_done = sum(sc.status(e)["steps"] for e in ids)
     failed = sum(sc.status(e)["status"] == "FAILED" for e in ids)
     x_end = [sc.points(e) for e in ids]
-    t_max = ms
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.envs * args.steps / (t_max / 1000.0)
+    t_max = max_over_ranks(ms, world, "cuda")
+    value = job_throughput(world, args.envs, args.steps, t_max / 1000.0)
 
     # ---- end to end through the public API with host buffers: per step, the next kinematic
     # targets of every env go host -> device and the DOFs of every env come back.
@@ -260,14 +277,8 @@ def run_ours(args):
         sc.step(1)
         sc.all_dofs(h_out)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * args.envs * args.steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e_value = job_throughput(world, args.envs, args.steps, e2e_s)
 
     mixed = None
     if world == 1 and args.precision == "fp64" and not args.no_mixed_leg:

@@ -1758,18 +1758,15 @@ struct ipc_scene {
            (const double*)pte.p, r, (const double*)keep_sv.p, e_count.p + 2);
     return read_int(e_count.p + 2) == 0;
   }
-  long lists_made = 0, lists_kept = 0;
   // CCD step filter on the envs in act: swept-box candidates at [x, x + p] (ptx, pte current),
   // then additive CCD per candidate pair of the iterating envs; each env's alpha_max is the
   // minimum
   void ccd_filter(EnvCtl C, const uint8_t* act) {
     const bool keep = reuse_lists();  // the list also serves the narrow phases: sorted per query
     if (keep && list_covers(act)) {
-      ++lists_kept;
       accd_all(C, keep);
       return;
     }
-    ++lists_made;
     if (since_build >= TREE_REBUILD_ROUNDS) {  // refits keep the trees valid; a rebuild keeps them tight
       build_trees();
       since_build = 0;
