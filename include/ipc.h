@@ -153,7 +153,9 @@ typedef enum {
   IPC_Q_ALL_STATUS = 10,   /* int32[4 * n_env] for the whole scene (env_id ignored): env id,
                               status, failure reason, next step of every environment, in one
                               read-back (a serving loop polls this once per step) */
-  IPC_Q_KAPPA = 11         /* double[1]: the env's barrier stiffness in its current (or last) step */
+  IPC_Q_KAPPA = 11,        /* double[1]: the env's barrier stiffness in its current (or last) step */
+  IPC_Q_TET_STRESS = 12    /* double[n_tets]: von Mises stress (Pa) of the Neo-Hookean Cauchy
+                              stress of each of the env's tets at its current DOFs */
 } ipc_query_kind;
 
 /* Create / destroy a scene on desc->device. */

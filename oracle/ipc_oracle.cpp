@@ -1433,6 +1433,37 @@ extern "C" {
 void* or_env_create(const Params* P, const EnvDesc* D) { return build_env(*P, *D); }
 void or_env_destroy(void* h) { delete (Env*)h; }
 double or_env_kappa(void* h) { return ((Env*)h)->kappa; }
+// Von Mises stress of every tet at DOFs q: the Cauchy stress of the Neo-Hookean energy is
+// sigma = P F^T / J with P = mu (F - F^-T) + lam ln J F^-T, i.e. (mu (F F^T - I) + lam ln J I) / J,
+// and von Mises = sqrt(3/2 s:s) of its deviator s.
+void or_env_tet_stress(void* h, const double* q, double* out) {
+  const Env& e = *(const Env*)h;
+  for (size_t t = 0; t < e.tets.size(); ++t) {
+    const auto& T = e.tets[t];
+    const auto& Bi = e.Dminv[t];
+    double Ds[9], F[9];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) Ds[3 * r + c] = q[3 * T[c + 1] + r] - q[3 * T[0] + r];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) F[3 * r + c] = Ds[3 * r] * Bi[c] + Ds[3 * r + 1] * Bi[3 + c] + Ds[3 * r + 2] * Bi[6 + c];
+    const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) + F[2] * (F[3] * F[7] - F[4] * F[6]);
+    double sig[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double b = 0.0;
+        for (int k = 0; k < 3; ++k) b += F[3 * i + k] * F[3 * j + k];
+        sig[3 * i + j] = (e.tmu[t] * (b - (i == j ? 1.0 : 0.0)) + (i == j ? e.tlam[t] * std::log(J) : 0.0)) / J;
+      }
+    const double p = (sig[0] + sig[4] + sig[8]) / 3.0;
+    double ss = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const double d = sig[3 * i + j] - (i == j ? p : 0.0);
+        ss += d * d;
+      }
+    out[t] = std::sqrt(1.5 * ss);
+  }
+}
 int or_env_ndof(void* h) { return ((Env*)h)->ndof; }
 int or_env_npoints(void* h) { return (int)((Env*)h)->pts.size(); }
 

@@ -57,6 +57,7 @@ def lib():
         L.or_env_trace.argtypes = [vp, C.c_int]
         L.or_env_kappa.restype = d
         L.or_env_kappa.argtypes = [vp]
+        L.or_env_tet_stress.argtypes = [vp, vp, vp]
         L.or_env_trace_get.argtypes = [vp, vp, C.c_int]
         L.or_env_body_mass.argtypes = [vp, C.c_int, vp, vp]
         L.or_env_soft_mass.argtypes = [vp, vp]
@@ -181,6 +182,13 @@ class OracleEnv:
         x = np.ascontiguousarray(x, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.float64)
         lib().or_env_set_state(self.h, _p(x), _p(v), step)
+
+    def tet_stress(self, q, n_tets: int) -> np.ndarray:
+        """Von Mises stress of every tet (Pa) at DOFs q."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        out = np.zeros(n_tets)
+        lib().or_env_tet_stress(self.h, _p(q), _p(out))
+        return out
 
     def kappa(self) -> float:
         """Barrier stiffness of the current (or last) step."""

@@ -470,6 +470,36 @@ DEV double barrier_eval(const ContactRec& c, const double* __restrict__ ptx, dou
   return Eb;
 }
 
+// Von Mises stress of every tet of the envs in act at DOFs q, one thread per tet: the
+// Neo-Hookean Cauchy stress is (mu (F F^T - I) + lam ln J I) / J, so its deviator is
+// (mu / J) dev(F F^T) and von Mises = (mu / J) sqrt(3/2 dev(F F^T) : dev(F F^T)).
+__global__ void k_tet_von_mises(int n_tets, const int4* __restrict__ tets, const double* __restrict__ prm,
+                                const int* __restrict__ tenv, const uint8_t* __restrict__ act,
+                                const double* __restrict__ q, double* __restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tets || !act[tenv[t]]) return;
+  const int4 T = tets[t];
+  const double* P = prm + 12 * (long)t;
+  const d3 x0 = ld3(q, T.x), x1 = ld3(q, T.y), x2 = ld3(q, T.z), x3 = ld3(q, T.w);
+  const double Ds[9] = {x1.x - x0.x, x2.x - x0.x, x3.x - x0.x, x1.y - x0.y, x2.y - x0.y,
+                        x3.y - x0.y, x1.z - x0.z, x2.z - x0.z, x3.z - x0.z};
+  double F[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) F[3 * r + c] = Ds[3 * r] * P[c] + Ds[3 * r + 1] * P[3 + c] + Ds[3 * r + 2] * P[6 + c];
+  const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                   F[2] * (F[3] * F[7] - F[4] * F[6]);
+  double B[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) B[3 * i + j] = F[3 * i] * F[3 * j] + F[3 * i + 1] * F[3 * j + 1] + F[3 * i + 2] * F[3 * j + 2];
+  const double m = (B[0] + B[4] + B[8]) / 3.0;
+  double ss = 0.0;
+  for (int i = 0; i < 9; ++i) {
+    const double d = B[i] - ((i % 4 == 0) ? m : 0.0);
+    ss += d * d;
+  }
+  out[t] = P[10] / J * sqrt(1.5 * ss);
+}
+
 // energy and gradient modes: one thread per contact
 template <int MODE>
 __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,

@@ -445,6 +445,7 @@ struct ipc_scene {
   DBuf<int> e_status, e_reason, e_step, e_constrained, e_bad, e_nanp, e_halv, e_newton_it, e_count, e_rem;
   // barrier stiffness per env, its closest-contact tracking and the step-start sums
   DBuf<double> e_kappa, e_kprev, e_kdots, g0buf;
+  DBuf<double> tet_vm;  // per-tet von Mises stress (queries)
   DBuf<unsigned long long> e_dmin2;
   DBuf<uint8_t> e_stepping, e_iter, e_ls, e_accept, e_sel, e_all, e_start, e_cover;
   DBuf<double> e_E0, e_Et, e_alpha;
@@ -2275,6 +2276,17 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       CK(cudaStreamSynchronize(s->stream));
       v[2] = v[3];
       return copy_out(v, sizeof(v), out, out_bytes, written);
+    }
+    case IPC_Q_TET_STRESS: {
+      const int t0 = s->h_tet_off[li], nt = s->h_tet_off[li + 1] - t0;
+      s->select(li);
+      s->tet_vm.ensure((size_t)std::max(s->NT, 1));
+      s->launch(k_tet_von_mises, s->NT, 256, s->NT, (const int4*)s->tets.p, (const double*)s->tet_prm.p,
+                (const int*)s->tet_env.p, (const uint8_t*)s->e_sel.p, (const double*)s->x.p, s->tet_vm.p);
+      std::vector<double> v(std::max(nt, 1));
+      if (nt) CK(cudaMemcpyAsync(v.data(), s->tet_vm.p + t0, nt * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      return copy_out(v.data(), nt * sizeof(double), out, out_bytes, written);
     }
     case IPC_Q_KAPPA: {
       double v = 0.0;
