@@ -154,8 +154,10 @@ typedef enum {
                               status, failure reason, next step of every environment, in one
                               read-back (a serving loop polls this once per step) */
   IPC_Q_KAPPA = 11,        /* double[1]: the env's barrier stiffness in its current (or last) step */
-  IPC_Q_TET_STRESS = 12    /* double[n_tets]: von Mises stress (Pa) of the Neo-Hookean Cauchy
+  IPC_Q_TET_STRESS = 12,   /* double[n_tets]: von Mises stress (Pa) of the Neo-Hookean Cauchy
                               stress of each of the env's tets at its current DOFs */
+  IPC_Q_CONTACT_FORCES = 13 /* double[n]: normal force kappa e |b'(d)| (N) of each contact at the
+                              env's current DOFs, in the order of IPC_Q_CONTACTS */
 } ipc_query_kind;
 
 /* Create / destroy a scene on desc->device. */

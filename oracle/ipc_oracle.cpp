@@ -1603,6 +1603,36 @@ int or_env_contacts(void* h, const double* q, int32_t* out, double* d2out, int c
   }
   return n;
 }
+// Normal force of every contact at q, in or_env_contacts' order: kappa e |b'(d)| (N), with e the
+// edge-edge mollifier (1 for point-triangle pairs) and kappa the env's current stiffness.
+int or_env_contact_forces(void* h, const double* q, double* out, int cap) {
+  Env* e = (Env*)h;
+  std::vector<double> px;
+  point_positions(*e, q, px);
+  std::vector<std::array<int, 3>> cands;
+  candidates(*e, px, nullptr, 0.5 * e->P.dhat, cands);
+  std::sort(cands.begin(), cands.end());
+  int n = 0;
+  for (auto& c : cands) {
+    int pts[4];
+    cand_points(*e, c, pts);
+    double x12[12];
+    gather12(px, pts, x12);
+    double d2 = pair_dist2(c[0], x12);
+    if (!(d2 < e->P.dhat * e->P.dhat)) continue;
+    double b, b1, b2;
+    barrier_derivs(std::sqrt(d2), e->P.dhat, &b, &b1, &b2);
+    double moll = 1.0;
+    if (c[0] == 1) {
+      V3<double> P[4];
+      for (int i = 0; i < 4; ++i) P[i] = {x12[3 * i], x12[3 * i + 1], x12[3 * i + 2]};
+      moll = mollifier(P[0], P[1], P[2], P[3], 1e-3 * rest_len2(*e, pts[0], pts[1]) * rest_len2(*e, pts[2], pts[3]));
+    }
+    if (n < cap) out[n] = e->kappa * moll * std::fabs(b1);
+    ++n;
+  }
+  return n;
+}
 // world positions of all points at q (npoints x 3)
 void or_env_points(void* h, const double* q, double* out) {
   Env* e = (Env*)h;

@@ -58,6 +58,7 @@ def lib():
         L.or_env_kappa.restype = d
         L.or_env_kappa.argtypes = [vp]
         L.or_env_tet_stress.argtypes = [vp, vp, vp]
+        L.or_env_contact_forces.argtypes = [vp, vp, vp, C.c_int]
         L.or_env_trace_get.argtypes = [vp, vp, C.c_int]
         L.or_env_body_mass.argtypes = [vp, C.c_int, vp, vp]
         L.or_env_soft_mass.argtypes = [vp, vp]
@@ -189,6 +190,14 @@ class OracleEnv:
         out = np.zeros(n_tets)
         lib().or_env_tet_stress(self.h, _p(q), _p(out))
         return out
+
+    def contact_forces(self, q) -> np.ndarray:
+        """Normal force (N) of every contact at DOFs q, in the order of contacts(q)."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        n = lib().or_env_contact_forces(self.h, _p(q), None, 0)
+        out = np.zeros(max(n, 1))
+        lib().or_env_contact_forces(self.h, _p(q), _p(out), n)
+        return out[:n]
 
     def kappa(self) -> float:
         """Barrier stiffness of the current (or last) step."""

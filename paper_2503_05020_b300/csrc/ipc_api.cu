@@ -445,7 +445,7 @@ struct ipc_scene {
   DBuf<int> e_status, e_reason, e_step, e_constrained, e_bad, e_nanp, e_halv, e_newton_it, e_count, e_rem;
   // barrier stiffness per env, its closest-contact tracking and the step-start sums
   DBuf<double> e_kappa, e_kprev, e_kdots, g0buf;
-  DBuf<double> tet_vm;  // per-tet von Mises stress (queries)
+  DBuf<double> tet_vm;  // per-tet stress or per-contact force of a query
   DBuf<unsigned long long> e_dmin2;
   DBuf<uint8_t> e_stepping, e_iter, e_ls, e_accept, e_sel, e_all, e_start, e_cover;
   DBuf<double> e_E0, e_Et, e_alpha;
@@ -2276,6 +2276,22 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       CK(cudaStreamSynchronize(s->stream));
       v[2] = v[3];
       return copy_out(v, sizeof(v), out, out_bytes, written);
+    }
+    case IPC_Q_CONTACT_FORCES: {
+      s->select(li);
+      s->launch(k_points, s->NP, 256, s->NP, (const int*)s->pt_node.p, (const double*)s->pt_xb.p,
+                (const int*)s->body_node.p, (const double*)s->x.p, s->ptx.p);
+      s->build_trees();
+      s->constraint_set(s->e_sel.p);
+      const int n = s->n_ct;
+      s->tet_vm.ensure((size_t)std::max(n, 1));
+      s->launch(k_contact_force, n, 128, n, (const ContactRec*)s->ct.p, (const double*)s->ptx.p, s->desc.dhat,
+                (const double*)s->e_kappa.p, s->tet_vm.p);
+      std::vector<double> v(std::max(n, 1));
+      if (n) CK(cudaMemcpyAsync(v.data(), s->tet_vm.p, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      s->ttri.built = s->tedge.built = false;
+      return copy_out(v.data(), n * sizeof(double), out, out_bytes, written);
     }
     case IPC_Q_TET_STRESS: {
       const int t0 = s->h_tet_off[li], nt = s->h_tet_off[li + 1] - t0;

@@ -671,6 +671,29 @@ __global__ void k_compact_contacts(int n, const int* __restrict__ flag, const in
   if (flag[i]) out[off[i]] = tmp[i];
 }
 
+// normal force of every contact: kappa e |b'(d)| (the friction lag's lambda), per env kappa
+__global__ void k_contact_force(int n_ct, const ContactRec* __restrict__ ct, const double* __restrict__ ptx,
+                                double dhat, const double* __restrict__ kappa_env, double* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_ct) return;
+  ContactRec c = ct[k];
+  d3 X[4];
+  for (int i = 0; i < 4; ++i) X[i] = ld3(ptx, c.pts[i]);
+  double d = sqrt(typed_d2(c.kind, c.type, X));
+  double b, b1, b2;
+  barrier3(d, dhat, &b, &b1, &b2);
+  double m = 1.0;
+  if (c.kind == 1) {
+    d3 n = cross(X[1] - X[0], X[3] - X[2]);
+    double cc = dot(n, n);
+    if (cc < c.eps_x) {
+      double r = cc / c.eps_x;
+      m = -r * r + 2.0 * r;
+    }
+  }
+  out[k] = kappa_env[c.env] * m * fabs(b1);
+}
+
 // lagged friction at x^t: lambda = kappa e |b'(d)|, closest-point coefficients and normal
 __global__ void k_friction_setup(int n_ct, const ContactRec* __restrict__ ct, const double* __restrict__ ptx,
                                  const double* __restrict__ env_mu, double dhat, const double* __restrict__ kappa_env,

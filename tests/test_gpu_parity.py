@@ -418,3 +418,18 @@ def test_tet_stress_query_matches_the_oracle():
     assert sg.shape == (nt,)
     assert np.abs(sg - so).max() <= 1e-12 * np.abs(so).max()
     assert so.max() > 0.0
+
+
+def test_contact_force_query_matches_the_oracle():
+    """Normal contact forces of the squeezed cube at a pressed state, in the contact list's order:
+    GPU query and oracle agree to 1e-10 relative; the list matches the contacts query."""
+    env, x, v, step = pressed_cube_state()
+    p = S.scene_params(0.01)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    sc.set_state(eid, x, v, step)
+    fg = sc.contact_forces(eid)
+    o = O.OracleEnv(p, env)
+    fo = o.contact_forces(x)
+    assert len(fg) == len(sc.contacts(eid)) == len(fo) > 0
+    assert np.abs(fg - fo).max() <= 1e-10 * np.abs(fo).max()

@@ -48,6 +48,8 @@ def test_resting_body_contact_forces_balance_weight(body):
         m = e.soft_mass(len(env["soft"][0]["verts"])).sum()
     tol = 5e-5 if body == "block" else 1e-5
     assert abs(F / (m * G) - 1) < tol
+    # the contact-force query reports the same normal forces
+    assert abs(e.contact_forces(x).sum() / (m * G) - 1) < tol
 
 
 def _slope_velocity(e, env, incline_deg):
