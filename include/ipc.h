@@ -156,8 +156,12 @@ typedef enum {
   IPC_Q_KAPPA = 11,        /* double[1]: the env's barrier stiffness in its current (or last) step */
   IPC_Q_TET_STRESS = 12,   /* double[n_tets]: von Mises stress (Pa) of the Neo-Hookean Cauchy
                               stress of each of the env's tets at its current DOFs */
-  IPC_Q_CONTACT_FORCES = 13 /* double[n]: normal force kappa e |b'(d)| (N) of each contact at the
-                              env's current DOFs, in the order of IPC_Q_CONTACTS */
+  IPC_Q_CONTACT_FORCES = 13, /* double[n]: normal force kappa e |b'(d)| (N) of each contact at
+                              the env's current DOFs, in the order of IPC_Q_CONTACTS */
+  IPC_Q_FRICTION_FORCES = 14 /* double[n]: tangential force mu lambda f1(|u|) (N) of each lagged
+                              friction stencil of the env's current (or last) step at its
+                              current DOFs (u: tangential relative displacement since the step
+                              start); point-triangle stencils first */
 } ipc_query_kind;
 
 /* Create / destroy a scene on desc->device. */

@@ -1633,6 +1633,27 @@ int or_env_contact_forces(void* h, const double* q, double* out, int cap) {
   }
   return n;
 }
+// Tangential force of every lagged friction stencil of the current (or last) step at DOFs q:
+// mu lambda f1(|u|), u the tangential relative displacement since the step start (N).
+int or_env_friction_forces(void* h, const double* q, double* out, int cap) {
+  Env* e = (Env*)h;
+  std::vector<double> px;
+  point_positions(*e, q, px);
+  const double eh = e->P.eps_v * e->P.dt;
+  int n = 0;
+  for (const FrictionContact& f : e->fric) {
+    double rel[3] = {0, 0, 0};
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 3; ++k) rel[k] += f.c[a] * (px[3 * f.pts[a] + k] - e->ptx_t[3 * f.pts[a] + k]);
+    double nr = d3dot(f.n, rel);
+    double u[3] = {rel[0] - nr * f.n[0], rel[1] - nr * f.n[1], rel[2] - nr * f.n[2]};
+    double f0, f1, f2;
+    friction_f(std::sqrt(d3dot(u, u)), eh, &f0, &f1, &f2);
+    if (n < cap) out[n] = e->mu * f.lambda * f1;
+    ++n;
+  }
+  return n;
+}
 // world positions of all points at q (npoints x 3)
 void or_env_points(void* h, const double* q, double* out) {
   Env* e = (Env*)h;

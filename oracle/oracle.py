@@ -59,6 +59,7 @@ def lib():
         L.or_env_kappa.argtypes = [vp]
         L.or_env_tet_stress.argtypes = [vp, vp, vp]
         L.or_env_contact_forces.argtypes = [vp, vp, vp, C.c_int]
+        L.or_env_friction_forces.argtypes = [vp, vp, vp, C.c_int]
         L.or_env_trace_get.argtypes = [vp, vp, C.c_int]
         L.or_env_body_mass.argtypes = [vp, C.c_int, vp, vp]
         L.or_env_soft_mass.argtypes = [vp, vp]
@@ -197,6 +198,14 @@ class OracleEnv:
         n = lib().or_env_contact_forces(self.h, _p(q), None, 0)
         out = np.zeros(max(n, 1))
         lib().or_env_contact_forces(self.h, _p(q), _p(out), n)
+        return out[:n]
+
+    def friction_forces(self, q) -> np.ndarray:
+        """Tangential force (N) of every lagged friction stencil of the last step at DOFs q."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        n = lib().or_env_friction_forces(self.h, _p(q), None, 0)
+        out = np.zeros(max(n, 1))
+        lib().or_env_friction_forces(self.h, _p(q), _p(out), n)
         return out[:n]
 
     def kappa(self) -> float:

@@ -574,6 +574,18 @@ __device__ __noinline__ double friction_energy(const FrictionRec& f, const doubl
   return h2 * f.mu_lambda * f0;
 }
 
+// tangential force mu lambda f1(|u|) of every lagged friction stencil at positions ptx (N)
+__global__ void k_friction_force(int n_fr, const FrictionRec* __restrict__ fr, const double* __restrict__ ptx,
+                                 const double* __restrict__ ptx_t, double eh, double* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_fr) return;
+  const FrictionRec f = fr[k];
+  d3 u;
+  double y;
+  friction_energy(f, ptx, ptx_t, 0.0, eh, &u, &y);
+  out[k] = f.mu_lambda * (y < eh ? -y * y / (eh * eh) + 2.0 * y / eh : 1.0);
+}
+
 template <int MODE, class HT = double>
 __global__ void k_friction(int n_fr, const FrictionRec* __restrict__ fr, const uint8_t* __restrict__ act,
                            const double* __restrict__ ptx, const double* __restrict__ ptx_t, double h2, double eh,

@@ -2293,6 +2293,25 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       s->ttri.built = s->tedge.built = false;
       return copy_out(v.data(), n * sizeof(double), out, out_bytes, written);
     }
+    case IPC_Q_FRICTION_FORCES: {
+      const int n = s->n_fr;
+      s->launch(k_points, s->NP, 256, s->NP, (const int*)s->pt_node.p, (const double*)s->pt_xb.p,
+                (const int*)s->body_node.p, (const double*)s->x.p, s->ptx.p);
+      s->tet_vm.ensure((size_t)std::max(n, 1));
+      s->launch(k_friction_force, n, 128, n, (const FrictionRec*)s->fr.p, (const double*)s->ptx.p,
+                (const double*)s->ptx_t.p, s->desc.eps_v * s->desc.dt, s->tet_vm.p);
+      std::vector<double> v(std::max(n, 1));
+      std::vector<FrictionRec> recs(std::max(n, 1));
+      if (n) {
+        CK(cudaMemcpyAsync(v.data(), s->tet_vm.p, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(recs.data(), s->fr.p, n * sizeof(FrictionRec), cudaMemcpyDeviceToHost, s->stream));
+      }
+      CK(cudaStreamSynchronize(s->stream));
+      std::vector<double> mine;  // this env's records, in list order (point-triangle, then edge-edge)
+      for (int k = 0; k < n; ++k)
+        if (recs[k].env == li) mine.push_back(v[k]);
+      return copy_out(mine.data(), mine.size() * sizeof(double), out, out_bytes, written);
+    }
     case IPC_Q_TET_STRESS: {
       const int t0 = s->h_tet_off[li], nt = s->h_tet_off[li + 1] - t0;
       s->select(li);

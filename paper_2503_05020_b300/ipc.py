@@ -22,7 +22,7 @@ ENV_STATUS = {0: "ACTIVE", 1: "DONE", 2: "FAILED"}
 FAIL_REASON = {0: "none", 1: "newton_cap", 2: "line_search", 3: "non_finite", 4: "initial_intersection", 5: "internal"}
 FP64, MIXED = 0, 1
 Q_DOFS, Q_VELOCITIES, Q_STATUS, Q_STATS, Q_CANDIDATES, Q_CONTACTS, Q_POINTS, Q_SIZES, Q_INTERSECTIONS, \
-    Q_SCENE_COUNTERS, Q_ALL_STATUS, Q_KAPPA, Q_TET_STRESS, Q_CONTACT_FORCES = range(14)
+    Q_SCENE_COUNTERS, Q_ALL_STATUS, Q_KAPPA, Q_TET_STRESS, Q_CONTACT_FORCES, Q_FRICTION_FORCES = range(15)
 
 
 class IpcError(RuntimeError):
@@ -237,6 +237,11 @@ class Scene:
     def contact_forces(self, eid: int) -> np.ndarray:
         """Normal force (N) of each contact at the env's current DOFs, in the order of contacts()."""
         return self._query(eid, Q_CONTACT_FORCES, np.float64)
+
+    def friction_forces(self, eid: int) -> np.ndarray:
+        """Tangential force (N) of each lagged friction stencil of the env's last step at its
+        current DOFs."""
+        return self._query(eid, Q_FRICTION_FORCES, np.float64)
 
     def tet_stress(self, eid: int) -> np.ndarray:
         """Von Mises stress (Pa) of each of the env's tets at its current DOFs."""

@@ -433,3 +433,21 @@ def test_contact_force_query_matches_the_oracle():
     fo = o.contact_forces(x)
     assert len(fg) == len(sc.contacts(eid)) == len(fo) > 0
     assert np.abs(fg - fo).max() <= 1e-10 * np.abs(fo).max()
+
+
+def test_friction_force_query_matches_the_oracle():
+    """Friction forces of a rigid box sliding down a 20 deg incline (mu = 0.2) after 20 steps:
+    the GPU's and the oracle's lagged friction stencils give the same forces (compared sorted:
+    the two lists may order an env's stencils differently) to 1e-6 relative."""
+    p = S.scene_params(0.01, newton_tol=1e-8)
+    env = S.resting_env("rigid", n_steps=30, mu=0.2, incline_deg=20.0)
+    o = O.OracleEnv(p, env)
+    o.step(20)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    sc.step(20)
+    xo, _ = o.state()
+    fo = np.sort(o.friction_forces(xo))
+    fg = np.sort(sc.friction_forces(eid))
+    assert len(fg) == len(fo) >= 3
+    assert np.abs(fg - fo).max() <= 1e-6 * fo.max()

@@ -281,3 +281,20 @@ def test_adapted_stiffness_stays_in_its_bounds_and_keeps_the_invariants():
         assert inv["intersections"] == 0 and inv["inverted"] == 0
     assert min(ks) >= p["kappa"] and max(ks) <= 1000.0 * p["kappa"]
     assert max(ks) > p["kappa"]  # contact made the stiffness adapt
+
+
+def test_friction_forces_of_a_sliding_and_a_sticking_box():
+    """Rigid box on a 20 deg incline. Sliding (mu = 0.2 < tan 20 deg): every lagged friction
+    stencil is past the smoothing, so the friction forces add up to mu m g cos th (kinetic
+    friction). Sticking (mu = 0.5): they balance the slope component of the weight, m g sin th."""
+    th = math.radians(20.0)
+    p = S.scene_params(0.01, newton_tol=1e-8)
+    for mu, expect in ((0.2, lambda m: mu * m * G * math.cos(th)), (0.5, lambda m: m * G * math.sin(th))):
+        env = S.resting_env("rigid", n_steps=30, mu=mu, incline_deg=20.0)
+        e = O.OracleEnv(p, env)
+        e.step(30)
+        x, _ = e.state()
+        f = e.friction_forces(x)
+        M, _vol = e.body_mass(0)
+        assert len(f) >= 3
+        assert abs(f.sum() / expect(M[0, 0]) - 1.0) < 0.02, (mu, f.sum(), expect(M[0, 0]))
