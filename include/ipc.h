@@ -114,7 +114,9 @@ typedef struct {
                           (rigid links of a hand following joint targets); 0 = none */
 } ipc_affine_body_desc;
 
-/* One environment. gravity_on: n_steps bytes (gravity acts during step s when 1).
+/* One environment. gravity_on: n_steps bytes, the gravity of step s: 0 none, 1 the scene's
+ * gravity vector, 2..7 its magnitude along +x, -x, +y, -y, +z, -z (the axis-aligned phases of the
+ * grasp evaluation protocol, Sec. III-D); other values are rejected (IPC_ERR_ARG).
  * targets: n_steps * (n_soft + n_affine) * 12 doubles: for step s and body b (soft bodies
  * first) the affine map the body's kinematic vertices (soft, applied to their initial
  * positions) or the kinematic affine body itself must reach at the end of step s. */

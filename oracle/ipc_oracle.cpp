@@ -1143,13 +1143,22 @@ static void step_setup(Env& e) {
   const double h = e.P.dt;
   e.xt = e.x;
   e.xtilde.assign(e.ndof, 0.0);
-  double hh = e.gravity[std::min(e.step, e.n_steps - 1)] ? h * h : 0.0;
+  // gravity of the step: 0 none, 1 the scene's vector, 2..7 its magnitude along +x, -x, +y, -y,
+  // +z, -z (the axis-aligned phases of the grasp evaluation protocol, Sec. III-D)
+  const int code = e.gravity[std::min(e.step, e.n_steps - 1)];
+  double hh = code ? h * h : 0.0;
+  double g[3] = {e.P.gravity[0], e.P.gravity[1], e.P.gravity[2]};
+  if (code >= 2) {
+    const double gm = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    g[0] = g[1] = g[2] = 0.0;
+    g[(code - 2) / 2] = code % 2 == 0 ? gm : -gm;
+  }
   for (int i = 0; i < e.n_soft_verts; ++i)
-    for (int k = 0; k < 3; ++k) e.xtilde[3 * i + k] = (e.x[3 * i + k] + h * e.v[3 * i + k]) + hh * e.P.gravity[k];
+    for (int k = 0; k < 3; ++k) e.xtilde[3 * i + k] = (e.x[3 * i + k] + h * e.v[3 * i + k]) + hh * g[k];
   for (const Body& B : e.bodies)
     for (int k = 0; k < 12; ++k) {
       double r = e.x[B.dof + k] + h * e.v[B.dof + k];
-      if (k < 3) r = r + hh * e.P.gravity[k];
+      if (k < 3) r = r + hh * g[k];
       e.xtilde[B.dof + k] = r;
     }
   // friction lagged at x^t: normal force lambda = kappa e |b'(d)|, closest-point data

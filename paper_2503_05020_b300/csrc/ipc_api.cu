@@ -203,6 +203,8 @@ void build_env(HostEnv& h, const ipc_env_desc* D) {
   h.mu = D->friction_mu;
   h.n_steps = D->n_steps;
   h.grav.assign(D->gravity_on, D->gravity_on + D->n_steps);
+  for (uint8_t gcode : h.grav)
+    if (gcode > 7) fail_with(IPC_ERR_ARG, "env: gravity codes are 0..7");
   int nh = D->n_soft + D->n_affine;
   h.targets.assign(D->targets, D->targets + (size_t)D->n_steps * nh * 12);
   int nsv = 0;

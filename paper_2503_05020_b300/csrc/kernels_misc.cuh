@@ -58,10 +58,18 @@ __global__ void k_step_setup_nodes(int n_nodes, Layout L, EnvCtl C, const uint8_
   if (!act[e]) return;
   int step = C.step[e];
   if (step >= C.nsteps[e]) step = C.nsteps[e] - 1;
-  double hh = S.gravity[S.grav_off[e] + step] ? h * h : 0.0;
+  // gravity of this step: 0 none, 1 the scene's vector, 2..7 its magnitude along +x, -x, +y,
+  // -y, +z, -z (the axis-aligned phases of the grasp evaluation protocol)
+  const int code = S.gravity[S.grav_off[e] + step];
+  double hh = code ? h * h : 0.0;
   int b = L.node_body[i];
   bool grav_node = b < 0 || (i - L.body_node[b]) == 0;
   double g[3] = {gx, gy, gz};
+  if (code >= 2) {
+    const double gm = sqrt(gx * gx + gy * gy + gz * gz);
+    g[0] = g[1] = g[2] = 0.0;
+    g[(code - 2) / 2] = (code % 2 == 0) ? gm : -gm;
+  }
   for (int k = 0; k < 3; ++k) {
     double xv = x[3L * i + k];
     xt[3L * i + k] = xv;
