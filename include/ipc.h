@@ -160,10 +160,13 @@ typedef enum {
                               stress of each of the env's tets at its current DOFs */
   IPC_Q_CONTACT_FORCES = 13, /* double[n]: normal force kappa e |b'(d)| (N) of each contact at
                               the env's current DOFs, in the order of IPC_Q_CONTACTS */
-  IPC_Q_FRICTION_FORCES = 14 /* double[n]: tangential force mu lambda f1(|u|) (N) of each lagged
+  IPC_Q_FRICTION_FORCES = 14, /* double[n]: tangential force mu lambda f1(|u|) (N) of each lagged
                               friction stencil of the env's current (or last) step at its
                               current DOFs (u: tangential relative displacement since the step
                               start); point-triangle stencils first */
+  IPC_Q_CONTACT_HANDLES = 15 /* int32[n][2]: the bodies of the two sides of each contact (env-local
+                              handles: soft bodies first, then affine bodies), in the order of
+                              IPC_Q_CONTACTS */
 } ipc_query_kind;
 
 /* Create / destroy a scene on desc->device. */
@@ -215,6 +218,11 @@ ipc_status ipc_hessian_apply(ipc_scene* scene, int32_t env_id, const double* d, 
  * ipc_env_add), the kinematic targets of its next step from a host array laid out as
  * [env][body][12]. bytes must equal 12*8*sum over active envs of their body counts. */
 ipc_status ipc_set_next_targets(ipc_scene* scene, const double* targets, size_t bytes);
+/* Rewrite rows first_step .. first_step + n_steps - 1 of one env's schedule (targets: host array
+ * [n_steps][body][12], soft bodies first); kept across relayouts. IPC_ERR_ARG outside the
+ * schedule. */
+ipc_status ipc_env_set_targets(ipc_scene* scene, int32_t env_id, int32_t first_step, int32_t n_steps,
+                               const double* targets);
 
 /* Copy the DOFs of every ACTIVE-or-finished env, in env-id order, into one host array. */
 ipc_status ipc_get_all_dofs(ipc_scene* scene, double* out, size_t out_bytes, size_t* written);

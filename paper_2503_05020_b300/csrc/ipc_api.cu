@@ -2295,6 +2295,22 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       s->ttri.built = s->tedge.built = false;
       return copy_out(v.data(), n * sizeof(double), out, out_bytes, written);
     }
+    case IPC_Q_CONTACT_HANDLES: {
+      s->select(li);
+      s->launch(k_points, s->NP, 256, s->NP, (const int*)s->pt_node.p, (const double*)s->pt_xb.p,
+                (const int*)s->body_node.p, (const double*)s->x.p, s->ptx.p);
+      s->build_trees();
+      s->constraint_set(s->e_sel.p);
+      const int n = s->n_ct;
+      s->nflag.ensure(2 * (size_t)n + 2);
+      s->launch(k_contact_handles, n, 128, n, (const ContactRec*)s->ct.p, (const int*)s->pt_node.p,
+                (const int*)s->body_node.p, (const int*)s->node_handle.p, s->nflag.p);
+      std::vector<int> v(2 * (size_t)std::max(n, 1));
+      if (n) CK(cudaMemcpyAsync(v.data(), s->nflag.p, 2 * n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      s->ttri.built = s->tedge.built = false;
+      return copy_out(v.data(), 2 * n * sizeof(int), out, out_bytes, written);
+    }
     case IPC_Q_FRICTION_FORCES: {
       const int n = s->n_fr;
       s->launch(k_points, s->NP, 256, s->NP, (const int*)s->pt_node.p, (const double*)s->pt_xb.p,
@@ -2440,6 +2456,34 @@ ipc_status ipc_set_next_targets(ipc_scene* s, const double* targets, size_t byte
       src += nhb * 12;
     }
     so += (long)h.targets.size();
+  }
+  API_END
+}
+
+ipc_status ipc_env_set_targets(ipc_scene* s, int32_t env_id, int32_t first_step, int32_t n_steps,
+                               const double* targets) {
+  API_BEGIN
+  if (!s || !targets || n_steps < 0) fail_with(IPC_ERR_ARG, "bad argument");
+  auto it = s->envs.find(env_id);
+  if (it == s->envs.end()) fail_with(IPC_ERR_ARG, "unknown env id " + std::to_string(env_id));
+  HostEnv& h = it->second;
+  if (first_step < 0 || first_step + n_steps > h.n_steps) fail_with(IPC_ERR_ARG, "steps out of the schedule");
+  const size_t nh = h.soft.size() + h.aff.size(), row = nh * 12;
+  std::copy(targets, targets + (size_t)n_steps * row, h.targets.begin() + (size_t)first_step * row);
+  if (!s->dirty) {  // the laid-out schedule too (a relayout re-uploads the host copy)
+    CK(cudaSetDevice(s->device));
+    long so = 0;
+    for (int li = 0; li < s->E; ++li) {
+      HostEnv& o = s->envs[s->ids[li]];
+      if (s->ids[li] == env_id) {
+        if (n_steps)
+          CK(cudaMemcpyAsync(s->sched.p + so + (size_t)first_step * row, targets, (size_t)n_steps * row * 8,
+                             cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        break;
+      }
+      so += (long)o.targets.size();
+    }
   }
   API_END
 }

@@ -679,6 +679,23 @@ __global__ void k_compact_contacts(int n, const int* __restrict__ flag, const in
   if (flag[i]) out[off[i]] = tmp[i];
 }
 
+// the bodies (env-local handles: soft bodies first, then affine bodies) of the two sides of
+// every contact: the point and the triangle of a point-triangle pair, the two edges of an
+// edge-edge pair
+__global__ void k_contact_handles(int n_ct, const ContactRec* __restrict__ ct, const int* __restrict__ pt_node,
+                                  const int* __restrict__ body_node, const int* __restrict__ node_handle,
+                                  int* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_ct) return;
+  const ContactRec c = ct[k];
+  auto handle = [&](int p) {
+    const int nd = pt_node[p];
+    return node_handle[nd >= 0 ? nd : body_node[-1 - nd]];
+  };
+  out[2 * k] = handle(c.pts[0]);
+  out[2 * k + 1] = handle(c.pts[c.kind == 0 ? 1 : 2]);
+}
+
 // normal force of every contact: kappa e |b'(d)| (the friction lag's lambda), per env kappa
 __global__ void k_contact_force(int n_ct, const ContactRec* __restrict__ ct, const double* __restrict__ ptx,
                                 double dhat, const double* __restrict__ kappa_env, double* __restrict__ out) {

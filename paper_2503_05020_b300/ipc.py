@@ -22,7 +22,8 @@ ENV_STATUS = {0: "ACTIVE", 1: "DONE", 2: "FAILED"}
 FAIL_REASON = {0: "none", 1: "newton_cap", 2: "line_search", 3: "non_finite", 4: "initial_intersection", 5: "internal"}
 FP64, MIXED = 0, 1
 Q_DOFS, Q_VELOCITIES, Q_STATUS, Q_STATS, Q_CANDIDATES, Q_CONTACTS, Q_POINTS, Q_SIZES, Q_INTERSECTIONS, \
-    Q_SCENE_COUNTERS, Q_ALL_STATUS, Q_KAPPA, Q_TET_STRESS, Q_CONTACT_FORCES, Q_FRICTION_FORCES = range(15)
+    Q_SCENE_COUNTERS, Q_ALL_STATUS, Q_KAPPA, Q_TET_STRESS, Q_CONTACT_FORCES, Q_FRICTION_FORCES, \
+    Q_CONTACT_HANDLES = range(16)
 
 
 class IpcError(RuntimeError):
@@ -82,6 +83,7 @@ def lib() -> C.CDLL:
             "ipc_env_set_state": [vp, i32, vp, vp, i32], "ipc_eval": [vp, i32, vp, vp, vp],
             "ipc_newton_direction": [vp, i32, vp], "ipc_hessian_apply": [vp, i32, vp, vp],
             "ipc_set_next_targets": [vp, vp, sz], "ipc_get_all_dofs": [vp, vp, sz, vp],
+            "ipc_env_set_targets": [vp, i32, i32, i32, vp],
             "ipc_env_estimate_bytes": [vp, i32, vp], "ipc_launch_count": [vp, vp],
             "ipc_profile_enable": [vp, i32], "ipc_profile_read": [vp, i32, vp, vp, vp],
             "ipc_elastic_energy_noalloc": [i32, vp, vp, vp, i32, vp, C.c_double, vp, vp, vp],
@@ -284,6 +286,15 @@ class Scene:
         y = np.zeros_like(d)
         _check(lib().ipc_hessian_apply(self._h, eid, _p(d), _p(y)))
         return y
+
+    def set_env_targets(self, eid: int, first_step: int, targets: np.ndarray):
+        """Rewrite the env's schedule from first_step on with targets [n_steps][body][12]."""
+        t = np.ascontiguousarray(targets, dtype=np.float64)
+        _check(lib().ipc_env_set_targets(self._h, eid, first_step, t.shape[0], _p(t)))
+
+    def contact_handles(self, eid: int) -> np.ndarray:
+        """Bodies (soft first, then affine) of the two sides of each contact, in contacts() order."""
+        return self._query(eid, Q_CONTACT_HANDLES, np.int32, 2)
 
     def set_next_targets(self, targets: np.ndarray):
         t = np.ascontiguousarray(targets, dtype=np.float64)
