@@ -43,3 +43,20 @@ def test_env_validation_on_host():
         assert e.status == 6
     ok = S.cube_squeeze_env(0)
     assert ipc.estimate_bytes(ok) > 100_000
+
+
+def test_gravity_codes_are_validated_on_host():
+    """Per-step gravity codes 0..7 are accepted (none, the scene's vector, the six axis
+    phases); other values are rejected before anything reaches the GPU."""
+    import numpy as np
+    from paper_2503_05020_b300 import scenes as S
+
+    env = S.single_tet_env(n_steps=3)
+    env["gravity"] = np.array([0, 1, 7], dtype=np.uint8)
+    assert ipc.estimate_bytes(env) > 0
+    env["gravity"] = np.array([0, 7, 8], dtype=np.uint8)
+    try:
+        ipc.estimate_bytes(env)
+        raise AssertionError("gravity code 8 accepted")
+    except ipc.IpcError as e:
+        assert e.status == 1
