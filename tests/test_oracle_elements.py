@@ -352,6 +352,47 @@ def test_box_mass_properties_closed_form():
     assert np.allclose(M, M.T)
 
 
+def test_rotated_box_mass_properties_closed_form():
+    """A box turned by a random rotation R and moved to c: second moment
+    m (R diag(h^2/3) R^T + c c^T), whose off-diagonal entries are all nonzero, so a product of
+    inertia with a wrong sign or a swapped index fails here though not on the axis-aligned box."""
+    rng = np.random.default_rng(42)
+    h = np.array([0.04, 0.025, 0.01])
+    v, t = S.box_surface(tuple(h))
+    R = rand_rotation(rng)
+    c = np.array([-0.03, 0.07, 0.02])
+    rho = 1234.0
+    M, vol = O.mass_properties(v @ R.T + c, t, rho)
+    m = rho * 8 * h.prod()
+    assert math.isclose(vol, 8 * h.prod(), rel_tol=1e-12)
+    assert math.isclose(M[0, 0], m, rel_tol=1e-12)
+    assert np.allclose(M[0, 1:], m * c, rtol=1e-12)
+    assert np.allclose(M[1:, 0], m * c, rtol=1e-12)
+    second = m * (R @ np.diag(h * h / 3.0) @ R.T + np.outer(c, c))
+    assert np.abs(second - second.diagonal().mean() * np.eye(3)).min() > 0
+    assert np.allclose(M[1:, 1:], second, rtol=1e-11, atol=1e-14 * m)
+
+
+def test_tetrahedron_mass_properties_closed_form():
+    """One tetrahedron as a closed 4-triangle surface: volume |det|/6, first moment V s/4 and the
+    textbook second moment V/20 (sum_a x_a x_a^T + s s^T), s the sum of the corners."""
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        x = rng.uniform(-0.05, 0.05, size=(4, 3))
+        if np.linalg.det(np.stack([x[1] - x[0], x[2] - x[0], x[3] - x[0]])) < 0:
+            x[[1, 2]] = x[[2, 1]]
+        tris = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]], dtype=np.int32)
+        rho = 900.0
+        M, vol = O.mass_properties(x, tris, rho)
+        V = np.linalg.det(np.stack([x[1] - x[0], x[2] - x[0], x[3] - x[0]])) / 6.0
+        s = x.sum(axis=0)
+        assert math.isclose(vol, V, rel_tol=1e-11)
+        assert math.isclose(M[0, 0], rho * V, rel_tol=1e-11)
+        assert np.allclose(M[0, 1:], rho * V * s / 4.0, rtol=1e-10, atol=1e-16)
+        second = rho * V / 20.0 * (x.T @ x + np.outer(s, s))
+        assert np.allclose(M[1:, 1:], second, rtol=1e-10, atol=1e-18)
+
+
 def test_hull_mass_positive_definite():
     rng = S.SplitMix64(7)
     v, t = S.hull_object(rng, 200)
