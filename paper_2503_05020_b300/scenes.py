@@ -555,6 +555,23 @@ def resting_env(body: str = "tet", n_steps: int = 100, mu: float = 0.0, incline_
     return dict(soft=[soft], affine=[ground], mu=mu, gravity=np.ones(n_steps, dtype=np.uint8), targets=targets)
 
 
+def stacked_boxes_env(n_steps: int = 100, mu: float = 0.0, dhat: float = 1e-3, rho: float = 1000.0) -> dict:
+    """A free rigid cube (half side 0.01 m) resting, centred, on a fixed wider box (half sides
+    0.02, 0.02, 0.01 m) a gap dhat/2 above its top face. Both boxes split their horizontal faces
+    along the same (1, 1, 0) diagonal, so the cube's bottom diagonal lies exactly parallel to
+    the fixed box's top diagonal, straight above it: an edge-edge pair with parallel edges."""
+    gap = 0.5 * dhat
+    lv, lt = box_surface((0.02, 0.02, 0.01))
+    base = dict(verts=lv, tris=lt, rho=rho, q0=_q_from(np.eye(3), (0, 0, 0)), qdot0=np.zeros(12), kinematic=True)
+    cv, ct = box_surface((0.01, 0.01, 0.01))
+    q0 = _q_from(np.eye(3), (0, 0, 0.02 + gap))
+    cube = dict(verts=cv, tris=ct, rho=rho, q0=q0, qdot0=np.zeros(12), kinematic=False)
+    targets = np.zeros((n_steps, 2, 12))
+    targets[:, 0] = q0
+    targets[:, 1] = base["q0"]
+    return dict(soft=[], affine=[cube, base], mu=mu, gravity=np.ones(n_steps, dtype=np.uint8), targets=targets)
+
+
 def spinning_body_env(n_steps: int = 20, omega=(0.0, 0.0, 20.0)) -> dict:
     """A free rigid box spinning in free flight with gravity off (A A^T stays close to I)."""
     bv, btris = box_surface((0.02, 0.01, 0.005))

@@ -236,15 +236,18 @@ def test_env_gradient_fd_pd_target_term():
     _fd_check(e, q, list(range(12)))
 
 
-def test_adapted_stiffness_at_rest_balances_the_contact_vertices_weight():
+@pytest.mark.parametrize("floor", [1.0, 1e-2, 1e-4])
+def test_adapted_stiffness_at_rest_balances_the_contact_vertices_weight(floor):
     """Adapted barrier stiffness at a step start: the kappa that minimises |g_E + kappa G| over
     the free DOFs (g_E: gradient of every other term, G: the barrier's per unit kappa). A soft
     block at rest with its 9 bottom vertices a gap d above a fixed ground triangle, gravity on,
     has g_E = m_i h^2 g on each vertex and G = h^2 b'(d) on the bottom ones, so kappa equals
     g times the bottom vertices' mean mass over |b'(d)| (b' written out from
-    b(d) = -(d - dhat)^2 ln(d / dhat)). The scene's kappa (the clamp's floor) is set low."""
+    b(d) = -(d - dhat)^2 ln(d / dhat)), clamped to [floor, 1000 floor] with the scene's kappa
+    as the floor. The floors put that value near the bottom of the range, at about 250 times
+    the floor, and above the range (clamped to 1000 times the floor)."""
     h = 0.01
-    p = S.scene_params(h, kappa=1.0)
+    p = S.scene_params(h, kappa=floor)
     p["kappa_adapt"] = True
     gap = 0.5 * p["dhat"]
     env = S.resting_env("block", n_steps=2, gap=gap)
@@ -256,9 +259,12 @@ def test_adapted_stiffness_at_rest_balances_the_contact_vertices_weight():
     assert bottom.sum() == 9
     d, dh = gap, p["dhat"]
     b1 = -2.0 * (d - dh) * math.log(d / dh) - (d - dh) ** 2 / d
-    expect = G * m[bottom].mean() / abs(b1)
-    assert 1.0 < expect < 1000.0  # inside the clamp [kappa, 1000 kappa]
-    assert abs(e.kappa() / expect - 1.0) < 1e-9
+    balance = G * m[bottom].mean() / abs(b1)
+    if balance < 1000.0 * floor:
+        assert floor < balance
+        assert abs(e.kappa() / balance - 1.0) < 1e-9
+    else:
+        assert e.kappa() == 1000.0 * floor
 
 
 def test_adapted_stiffness_stays_in_its_bounds_and_keeps_the_invariants():
@@ -320,3 +326,56 @@ def test_axis_gravity_phase_free_fall(code):
     d = (x - x0).reshape(-1, 3)
     assert np.allclose(d[:, axis], z, rtol=1e-9)
     assert np.abs(np.delete(d, axis, axis=1)).max() <= 1e-12
+
+
+def test_friction_acts_on_tangential_motion_only_and_parallel_edges_carry_no_force():
+    """A rigid cube at rest on a wider fixed box, with one edge-edge contact between exactly
+    parallel edges (the two boxes' face diagonals, one above the other). The mollified barrier
+    of parallel edges vanishes with its gradient, so that pair carries no normal force and the
+    remaining lagged normal forces alone balance the weight (static equilibrium). Friction acts
+    on the tangential part of the relative motion only: moving the cube straight up draws no
+    friction force, moving it sideways by more than eps_v h draws mu times the normal forces,
+    i.e. mu m g in total (Coulomb's kinetic friction)."""
+    p = S.scene_params(0.01, newton_tol=1e-8)
+    mu = 0.5
+    env = S.stacked_boxes_env(n_steps=150, mu=mu)
+    e = O.OracleEnv(p, env)
+    assert e.step(150) == "DONE"
+    x, _ = e.state()
+    M, _vol = e.body_mass(0)
+    mg = M[0, 0] * G
+    pairs, _d2 = e.contacts(x)
+    cf = e.contact_forces(x)
+    assert len(cf) == len(pairs) >= 8 and (pairs[:, 0] == 1).any()
+    assert cf.min() < 1e-6 * cf.max()  # the parallel edge-edge pair
+    assert abs(cf.sum() / mg - 1.0) < 1e-5
+    shift = 10.0 * p["eps_v"] * p["dt"]
+    for axis, expect in ((2, 0.0), (0, mu * mg), (1, mu * mg)):
+        q = x.copy()
+        q[axis] += shift  # the cube's translation DOFs
+        f = e.friction_forces(q)
+        assert len(f) == len(pairs)
+        if expect == 0.0:
+            assert f.sum() < 1e-3 * mu * mg
+        else:
+            assert abs(f.sum() / expect - 1.0) < 1e-5
+
+
+def test_lumped_masses_carry_the_body_mass_and_centroid():
+    """Lumped vertex masses (a quarter of each tet's rho V_e to each of its corners) add up to
+    rho times the body's volume and have the body's centroid as their centre (a linear tet's
+    centroid is the mean of its corners). Checked on an L-shaped block of 3 unit cells, whose
+    volume and centroid follow from the cells alone."""
+    a, rho = 0.01, 1300.0
+    mask = np.ones((2, 2, 1), dtype=bool)
+    mask[1, 1, 0] = False
+    verts, tets, _ = S.kuhn_grid(2, 2, 1, (0.0, 0.0, 0.0), (2 * a, 2 * a, a), cell_mask=mask)
+    tris = S.boundary_tris(verts, tets)
+    soft = dict(verts=verts, tets=tets, tris=tris, E=1e5, nu=0.4, rho=rho, kin=np.zeros(len(verts), dtype=np.uint8))
+    env = dict(soft=[soft], affine=[], mu=0.0, gravity=np.zeros(1, dtype=np.uint8),
+               targets=np.tile(S.IDENTITY_Q, (1, 1, 1)))
+    e = O.OracleEnv(S.scene_params(0.01), env)
+    m = e.soft_mass(len(verts))
+    cells = np.array([[0.5, 0.5, 0.5], [1.5, 0.5, 0.5], [0.5, 1.5, 0.5]]) * a
+    assert abs(m.sum() / (rho * 3 * a ** 3) - 1.0) < 1e-12
+    assert np.allclose(m @ verts / m.sum(), cells.mean(axis=0), rtol=1e-12, atol=1e-15)
