@@ -314,6 +314,68 @@ def test_accd_is_conservative_against_bisection(kind):
     assert n_hit >= 10
 
 
+def first_crossing_time(kind, x, p):
+    """Exact first contact time in [0, 1] of four linearly moving points (Provot 1997): contact
+    needs the four points coplanar, i.e. a root of the cubic det[x1 - x0, x2 - x0, x3 - x0](t),
+    at which the point lies in the triangle (PT) or the two segments meet (EE). Plain numpy
+    geometry; none of the oracle's distance code. Returns inf when the primitives never meet."""
+    P = lambda t: (x + t * p).reshape(4, 3)
+
+    def vol(t):
+        q = P(t)
+        return np.linalg.det(np.stack([q[1] - q[0], q[2] - q[0], q[3] - q[0]]))
+
+    ts = np.array([0.0, 1 / 3, 2 / 3, 1.0])
+    coef = np.polyfit(ts, [vol(t) for t in ts], 3)
+    roots = sorted(r.real for r in np.roots(coef) if abs(r.imag) < 1e-9 and -1e-12 <= r.real <= 1 + 1e-12)
+    for t in roots:
+        q = P(t)
+        if kind == 0:  # barycentric coordinates of the point in the triangle's plane
+            A = np.stack([q[2] - q[1], q[3] - q[1]], axis=1)
+            uv, *_ = np.linalg.lstsq(A, q[0] - q[1], rcond=None)
+            if uv.min() >= -1e-9 and uv.sum() <= 1 + 1e-9:
+                return t
+        else:  # a0 + s (a1 - a0) = b0 + u (b1 - b0)
+            A = np.stack([q[1] - q[0], -(q[3] - q[2])], axis=1)
+            su, *_ = np.linalg.lstsq(A, q[2] - q[0], rcond=None)
+            if su.min() >= -1e-9 and su.max() <= 1 + 1e-9:
+                return t
+    return math.inf
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_accd_stops_before_primitives_pass_through_each_other(kind):
+    """Fast motions that carry one primitive straight through the other within the step (a
+    path that dense distance sampling can step over): the ACCD time is at most the exact first
+    crossing time, never past it, and the pair is still apart there."""
+    rng = np.random.default_rng(99 + kind)
+    n_cross = 0
+    for _ in range(200):
+        x = rng.normal(size=12) * 0.01
+        if kind == 0:  # the point goes through a random interior point of the triangle
+            w = rng.dirichlet([2.0, 2.0, 2.0])
+            through = w[0] * x[3:6] + w[1] * x[6:9] + w[2] * x[9:12]
+            src = x[0:3]
+        else:  # the first edge's midpoint goes through a random point of the second edge
+            u = rng.uniform(0.2, 0.8)
+            through = (1 - u) * x[6:9] + u * x[9:12]
+            src = 0.5 * (x[0:3] + x[3:6])
+        p = rng.normal(size=12) * 0.002
+        shift = (through - src) / rng.uniform(0.2, 0.6)  # crossing near t in [0.2, 0.6]
+        for i in range(2 if kind else 1):
+            p[3 * i:3 * i + 3] = shift + p[3 * i:3 * i + 3] * 0.1
+        if O.pair_dist2(kind, x)[0] < 1e-10:
+            continue
+        tc = first_crossing_time(kind, x, p)
+        t, _ = O.accd(kind, x, p)
+        assert 0 < t <= 1
+        assert O.pair_dist2(kind, x + t * p)[0] > 0
+        if tc <= 1:
+            n_cross += 1
+            assert t < tc, (t, tc)
+    assert n_cross >= 100
+
+
 def test_accd_returns_one_without_contact():
     x = np.array([0, 0, 0.1, 0, 0, 0, 1, 0, 0, 0, 1, 0], dtype=float)
     p = np.zeros(12)

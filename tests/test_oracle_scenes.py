@@ -379,3 +379,26 @@ def test_lumped_masses_carry_the_body_mass_and_centroid():
     cells = np.array([[0.5, 0.5, 0.5], [1.5, 0.5, 0.5], [0.5, 1.5, 0.5]]) * a
     assert abs(m.sum() / (rho * 3 * a ** 3) - 1.0) < 1e-12
     assert np.allclose(m @ verts / m.sum(), cells.mean(axis=0), rtol=1e-12, atol=1e-15)
+
+
+def test_thin_rigid_plate_has_no_self_contact():
+    """A free rigid plate thinner than dhat in free fall: its top and bottom faces are closer
+    than dhat, but points of one rigid body never meet, so the plate has no contact candidates,
+    falls by the implicit-Euler closed form and keeps A = I (no barrier pushes its faces apart)."""
+    h, n = 0.01, 10
+    p = S.scene_params(h)
+    pv, pt = S.box_surface((0.02, 0.015, 0.25 * p["dhat"]))
+    plate = dict(verts=pv, tris=pt, rho=900.0, q0=S.IDENTITY_Q.copy(), qdot0=np.zeros(12), kinematic=False)
+    env = dict(soft=[], affine=[plate], mu=0.5, gravity=np.ones(n, dtype=np.uint8),
+               targets=np.tile(S.IDENTITY_Q, (n, 1, 1)))
+    e = O.OracleEnv(p, env)
+    x0, _ = e.state()
+    assert len(e.candidates(x0)) == 0
+    assert e.step(n) == "DONE"
+    x, _ = e.state()
+    vz = z = 0.0
+    for _ in range(n):
+        vz -= h * G
+        z += h * vz
+    assert math.isclose(x[2] - x0[2], z, rel_tol=1e-9)
+    assert np.abs(x[3:12] - S.IDENTITY_Q[3:12]).max() < 1e-12
