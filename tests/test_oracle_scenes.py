@@ -402,3 +402,52 @@ def test_thin_rigid_plate_has_no_self_contact():
         z += h * vz
     assert math.isclose(x[2] - x0[2], z, rel_tol=1e-9)
     assert np.abs(x[3:12] - S.IDENTITY_Q[3:12]).max() < 1e-12
+
+
+def _fd_hessian(e, q, idx, step=1e-9):
+    cols = []
+    for i in idx:
+        qp, qm = q.copy(), q.copy()
+        qp[i] += step
+        qm[i] -= step
+        cols.append((e.eval(qp)[1] - e.eval(qm)[1]) / (2 * step))
+    return np.array(cols).T
+
+
+def test_hessian_matches_finite_differences_where_no_projection_acts():
+    """The assembled Hessian against central differences of the gradient, at states where every
+    element Hessian is already PSD, so that the projection leaves it as it is. (1) A rigid cube
+    lifted 3 dhat off the box it rested on: no barrier is active, its lagged friction stencils
+    are (the friction Hessian, PSD inside and past the eps_v h smoothing), and A = I (the
+    orthogonality Hessian is its PSD Gauss-Newton part there). (2) A free stiff soft block at a
+    strain of about 1e-6, where the Neo-Hookean Hessian is linear elasticity's up to a
+    projection of eigenvalues of the order of the strain."""
+    p = S.scene_params(0.01, newton_tol=1e-8)
+    e = O.OracleEnv(p, S.stacked_boxes_env(n_steps=150, mu=0.5))
+    assert e.step(150) == "DONE"
+    x, _ = e.state()
+    eh = p["eps_v"] * p["dt"]
+    for slide in (0.3 * eh, 3.0 * eh):
+        q = x.copy()
+        q[2] += 3.0 * p["dhat"]
+        q[0] += slide
+        q[1] += 0.5 * slide
+        assert len(e.contacts(q)[0]) == 0
+        H = e.hessian(q)[:12, :12]
+        Hf = _fd_hessian(e, q, range(12))[:12]
+        assert np.abs(H - Hf).max() <= 1e-6 * np.abs(H).max()
+
+    a = 0.01
+    verts, tets, _ = S.kuhn_grid(2, 2, 2, (0.0, 0.0, 0.0), (2 * a, 2 * a, 2 * a))
+    soft = dict(verts=verts, tets=tets, tris=S.boundary_tris(verts, tets), E=1e7, nu=0.4, rho=1000.0,
+                kin=np.zeros(len(verts), dtype=np.uint8))
+    env = dict(soft=[soft], affine=[], mu=0.0, gravity=np.zeros(2, dtype=np.uint8),
+               targets=np.tile(S.IDENTITY_Q, (2, 1, 1)))
+    e = O.OracleEnv(S.scene_params(0.01), env)
+    e.step(1)
+    x, _ = e.state()
+    q = x + np.random.default_rng(3).normal(size=x.size) * 1e-6 * a
+    H = e.hessian(q)
+    Hf = _fd_hessian(e, q, range(e.ndof))
+    elastic = H - np.diag(np.repeat(e.soft_mass(len(verts)), 3))
+    assert np.abs(H - Hf).max() <= 1e-5 * np.abs(elastic).max()
