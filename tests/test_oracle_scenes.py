@@ -451,3 +451,31 @@ def test_hessian_matches_finite_differences_where_no_projection_acts():
     Hf = _fd_hessian(e, q, range(e.ndof))
     elastic = H - np.diag(np.repeat(e.soft_mass(len(verts)), 3))
     assert np.abs(H - Hf).max() <= 1e-5 * np.abs(elastic).max()
+
+
+def test_invariant_checks_report_what_they_count():
+    """The invariants asserted after every step do report violations. A cube placed a gap g above
+    the box it rests on has no intersection and minimum distance g (its bottom corners over the
+    box's top face); pushed halfway into the box (off-centre, so that no crossing falls on a
+    triangle's boundary), its vertical edges pierce the box's top face. A tet with its apex
+    reflected through its base plane is inverted."""
+    p = S.scene_params(0.01)
+    e = O.OracleEnv(p, S.stacked_boxes_env(n_steps=2))
+    x, _ = e.state()
+    for gap in (0.3e-3, 2e-3):
+        q = x.copy()
+        q[2] = 0.02 + gap
+        inv = e.invariants(q)
+        assert inv["intersections"] == 0 and inv["inverted"] == 0
+        assert abs(inv["min_dist"] / gap - 1.0) < 1e-9
+    q = x.copy()
+    q[0:3] = [0.0031, -0.0017, 0.0137]
+    inv = e.invariants(q)
+    assert inv["intersections"] >= 4
+
+    e = O.OracleEnv(p, S.single_tet_env(n_steps=2))
+    x, _ = e.state()
+    assert e.invariants(x)["inverted"] == 0
+    q = x.copy()
+    q[11] = -q[11]  # apex (0, 0, 0.01) to (0, 0, -0.01): the base plane is z = 0
+    assert e.invariants(q)["inverted"] == 1
