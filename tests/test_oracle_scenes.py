@@ -479,3 +479,66 @@ def test_invariant_checks_report_what_they_count():
     q = x.copy()
     q[11] = -q[11]  # apex (0, 0, 0.01) to (0, 0, -0.01): the base plane is z = 0
     assert e.invariants(q)["inverted"] == 1
+
+
+def test_kinematic_bodies_sit_on_their_scheduled_poses():
+    """Kinematic parts take their scheduled pose of each step exactly: a soft tet whose four
+    vertices are all driven (x = p + A X0 for the step's handle pose q = (p, A)) and a
+    kinematic rigid box (q equals the step's entry), on a schedule that turns about z and
+    translates, one entry per step."""
+    n, h = 6, 0.01
+    tet = S.single_tet_env(n_steps=n)
+    soft = dict(tet["soft"][0], kin=np.ones(4, dtype=np.uint8))
+    bv, bt = S.box_surface((0.01, 0.01, 0.01))
+    box = dict(verts=bv, tris=bt, rho=700.0, q0=S.IDENTITY_Q.copy(), qdot0=np.zeros(12), kinematic=True)
+    targets = np.zeros((n, 2, 12))
+    for s in range(n):
+        c, sn = math.cos(0.1 * (s + 1)), math.sin(0.1 * (s + 1))
+        R = np.array([[c, -sn, 0.0], [sn, c, 0.0], [0.0, 0.0, 1.0]])
+        targets[s, 0] = np.concatenate([[0.001 * (s + 1), 0.0, 0.0], R[:, 0], R[:, 1], R[:, 2]])
+        targets[s, 1] = np.concatenate([[0.2, 0.002 * (s + 1), 0.0], R[:, 0], R[:, 1], R[:, 2]])
+    env = dict(soft=[soft], affine=[box], mu=0.0, gravity=np.ones(n, dtype=np.uint8), targets=targets)
+    e = O.OracleEnv(S.scene_params(h), env)
+    X0 = np.asarray(soft["verts"])
+    for s in range(n):
+        e.step(1)
+        x, _ = e.state()
+        q = targets[s, 0]
+        A = np.stack([q[3:6], q[6:9], q[9:12]], axis=1)
+        assert np.abs(x[:12].reshape(4, 3) - (X0 @ A.T + q[:3])).max() < 1e-15
+        assert np.abs(x[12:24] - targets[s, 1]).max() < 1e-15
+
+
+def test_pd_target_body_follows_the_implicit_euler_spring():
+    """Gravity off, a free box pulled by the PD potential toward targets that move over the
+    first steps: every step minimises 1/2 |q - q~|_M^2 + 1/2 h^2 k |q - q^|_M^2 (A stays at I,
+    so the orthogonality term is zero), whose minimiser is q = (q~ + h^2 k q^) / (1 + h^2 k)
+    with q~ = q + h v and q^ this step's target: the implicit-Euler recurrence of a spring."""
+    k, h, n = 900.0, 0.01, 12
+    env = S.pd_body_env(k_pd=k, n_steps=n, gravity=False, target_shift=(0.01, -0.02, 0.005), shift_steps=5)
+    e = O.OracleEnv(S.scene_params(h, newton_tol=1e-10), env)
+    q, v = S.IDENTITY_Q.copy(), np.zeros(12)
+    for s in range(n):
+        q_next = (q + h * v + h * h * k * env["targets"][s, 0]) / (1.0 + h * h * k)
+        v, q = (q_next - q) / h, q_next
+        assert e.step(1) in ("ACTIVE", "DONE")
+        x, _ = e.state()
+        assert np.abs(x - q).max() < 1e-9 * 0.02
+
+
+def test_gated_gravity_starts_with_its_schedule():
+    """Gravity gated per step (off for the first steps, as in the closing phase of a grasp): a
+    free tet does not move while gravity is off, then falls by the implicit-Euler closed form."""
+    h, n, off = 0.01, 8, 3
+    env = S.single_tet_env(n_steps=n)
+    env["gravity"] = np.array([0] * off + [1] * (n - off), dtype=np.uint8)
+    e = O.OracleEnv(S.scene_params(h), env)
+    x0, _ = e.state()
+    vz = z = 0.0
+    for s in range(n):
+        e.step(1)
+        if s >= off:
+            vz -= h * G
+            z += h * vz
+        x, _ = e.state()
+        assert np.allclose((x - x0).reshape(-1, 3)[:, 2], z, rtol=1e-9, atol=1e-15)
