@@ -231,9 +231,9 @@ ipc_status ipc_get_all_dofs(ipc_scene* scene, double* out, size_t out_bytes, siz
 ipc_status ipc_env_estimate_bytes(const ipc_env_desc* env, int32_t precision, uint64_t* bytes);
 
 /* Allocation-free Neo-Hookean energy (the paper has no counterpart; this is a deployment
- * convenience). For callers that cannot call cudaMalloc: code that runs while a CUDA graph is
- * being captured, real-time control loops where an allocation's latency or failure is not
- * acceptable, or hosts whose memory manager owns every device allocation. It computes, for each
+ * convenience). For callers that cannot call cudaMalloc: real-time control loops where an
+ * allocation's latency or failure is not acceptable, or hosts whose memory manager owns every
+ * device allocation and forbids others. It computes, for each
  * group g of tets [group_offsets[g], group_offsets[g+1]), h2 * sum V Psi(F) over the group with
  * the same per-tet energy code and the same fixed-order reduction as the scene path, and sets
  * inverted[g] = 1 when a tet of the group has J <= 0 (its energy then counts as 0).

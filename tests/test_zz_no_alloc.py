@@ -1,8 +1,8 @@
 """The allocation-free energy entry point against the scene path (needs a B300).
 
-Some callers of this library cannot allocate device memory: code running while a CUDA graph is
-captured, real-time control loops that must not pay for (or fail on) an allocation, and hosts
-whose memory manager owns every device allocation. ipc_elastic_energy_noalloc serves them: it
+Some callers of this library cannot allocate device memory: real-time control loops that must
+not pay for (or fail on) an allocation, and hosts whose memory manager owns every device
+allocation and forbids others. ipc_elastic_energy_noalloc serves them: it
 takes caller-owned device buffers and uses only a fixed scratch array inside the library. Here
 its result for a deformed soft cube must equal the energy ipc_eval reports for the same state
 (where inertia, contact and friction terms vanish), on two calls in a row.
