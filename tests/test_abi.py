@@ -26,7 +26,8 @@ def test_version_and_error_strings_without_gpu():
     assert b"sm_103a" in L.ipc_version()
     # a null scene is rejected on the host before any CUDA call
     st = L.ipc_step(None, 1)
-    assert st == 1 and b"null" in L.ipc_last_error() or b"bad" in L.ipc_last_error()
+    err = L.ipc_last_error()
+    assert st == 1 and (b"null" in err or b"bad" in err)
 
 
 def test_env_validation_on_host():
@@ -60,3 +61,52 @@ def test_gravity_codes_are_validated_on_host():
         raise AssertionError("gravity code 8 accepted")
     except ipc.IpcError as e:
         assert e.status == 1
+
+
+def _rejected(fn, status):
+    try:
+        fn()
+    except ipc.IpcError as e:
+        assert e.status == status, (e.status, e)
+        return str(e)
+    raise AssertionError("accepted")
+
+
+def test_scene_parameters_are_validated_on_host():
+    """A scene with a non-positive time step, contact distance or stiffness, an unknown
+    precision or an unsupported cluster size is rejected (IPC_ERR_ARG) before any CUDA call."""
+    from paper_2503_05020_b300 import scenes as S
+
+    good = S.scene_params(0.01)
+    for key, bad in (("dt", 0.0), ("dhat", -1e-3), ("kappa", 0.0), ("dt", float("nan"))):
+        _rejected(lambda: ipc.Scene(dict(good, **{key: bad})), 1)
+    _rejected(lambda: ipc.Scene(good, precision=5), 1)
+    _rejected(lambda: ipc.Scene(good, pcg_cluster=3), 1)
+
+
+def test_env_meshes_are_validated_on_host():
+    """Out-of-range tet and triangle indices, an empty soft body, an affine surface that encloses
+    no volume (triangles turned inward) and an empty schedule are rejected on the host."""
+    import numpy as np
+    from paper_2503_05020_b300 import scenes as S
+
+    env = S.single_tet_env(n_steps=2)
+    env["soft"][0]["tets"] = np.array([[0, 1, 2, 4]], dtype=np.int32)
+    assert "tet index" in _rejected(lambda: ipc.estimate_bytes(env), 1)
+
+    env = S.single_tet_env(n_steps=2)
+    env["soft"][0]["tris"] = np.array([[0, 1, 9]], dtype=np.int32)
+    assert "triangle index" in _rejected(lambda: ipc.estimate_bytes(env), 1)
+
+    env = S.resting_env("rigid", n_steps=2)
+    env["affine"][0]["tris"] = env["affine"][0]["tris"][:, [0, 2, 1]].copy()
+    assert "volume" in _rejected(lambda: ipc.estimate_bytes(env), 1)
+
+    env = S.resting_env("rigid", n_steps=2)
+    env["gravity"] = env["gravity"][:0]
+    env["targets"] = env["targets"][:0]
+    _rejected(lambda: ipc.estimate_bytes(env), 1)
+
+    env = S.single_tet_env(n_steps=2)
+    env["soft"][0]["tets"] = env["soft"][0]["tets"][:0]
+    assert "empty" in _rejected(lambda: ipc.estimate_bytes(env), 1)
