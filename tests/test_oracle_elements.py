@@ -227,6 +227,12 @@ def test_mollifier_continuity_and_limits():
         b1 = np.array([0.5 + math.cos(th + d), math.sin(th + d), 0.1])
         x = np.concatenate([a0, a1, [0.5, 0, 0.1], b1])
         assert abs(O.mollifier(x, eps) - 1.0) < 1e-6
+    # C1 at c = eps (the barrier's gradient stays continuous as edges turn through the threshold):
+    # just below it, 1 - e(c) vanishes to second order in (eps - c) / eps
+    for rel in (1e-2, 1e-3):
+        th = math.asin(math.sqrt(eps * (1.0 - rel)))
+        x = np.concatenate([a0, a1, [0.5, 0, 0.1], [0.5 + math.cos(th), math.sin(th), 0.1]])
+        assert abs((1.0 - O.mollifier(x, eps)) / rel ** 2 - 1.0) < 1e-6
 
 
 @pytest.mark.parametrize("kind", [0, 1])

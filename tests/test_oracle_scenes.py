@@ -328,15 +328,18 @@ def test_axis_gravity_phase_free_fall(code):
     assert np.abs(np.delete(d, axis, axis=1)).max() <= 1e-12
 
 
-def test_friction_acts_on_tangential_motion_only_and_parallel_edges_carry_no_force():
+@pytest.mark.parametrize("adapt", [False, True])
+def test_friction_acts_on_tangential_motion_only_and_parallel_edges_carry_no_force(adapt):
     """A rigid cube at rest on a wider fixed box, with one edge-edge contact between exactly
     parallel edges (the two boxes' face diagonals, one above the other). The mollified barrier
     of parallel edges vanishes with its gradient, so that pair carries no normal force and the
     remaining lagged normal forces alone balance the weight (static equilibrium). Friction acts
     on the tangential part of the relative motion only: moving the cube straight up draws no
     friction force, moving it sideways by more than eps_v h draws mu times the normal forces,
-    i.e. mu m g in total (Coulomb's kinetic friction)."""
+    i.e. mu m g in total (Coulomb's kinetic friction). With the adapted barrier stiffness the
+    lagged normal forces are those of the step's adapted kappa."""
     p = S.scene_params(0.01, newton_tol=1e-8)
+    p["kappa_adapt"] = adapt
     mu = 0.5
     env = S.stacked_boxes_env(n_steps=150, mu=mu)
     e = O.OracleEnv(p, env)
@@ -346,6 +349,7 @@ def test_friction_acts_on_tangential_motion_only_and_parallel_edges_carry_no_for
     mg = M[0, 0] * G
     pairs, _d2 = e.contacts(x)
     cf = e.contact_forces(x)
+    assert (e.kappa() > p["kappa"]) == adapt
     assert len(cf) == len(pairs) >= 8 and (pairs[:, 0] == 1).any()
     assert cf.min() < 1e-6 * cf.max()  # the parallel edge-edge pair
     assert abs(cf.sum() / mg - 1.0) < 1e-5
