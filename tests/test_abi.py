@@ -110,3 +110,36 @@ def test_env_meshes_are_validated_on_host():
     env = S.single_tet_env(n_steps=2)
     env["soft"][0]["tets"] = env["soft"][0]["tets"][:0]
     assert "empty" in _rejected(lambda: ipc.estimate_bytes(env), 1)
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The package never reaches the oracle (no import of it anywhere in the product modules),
+    and the binding fails loudly, instead of falling back to anything, when the library is
+    missing."""
+    import ast
+    import importlib
+
+    pkg = os.path.dirname(ipc.__file__)
+    for name in os.listdir(pkg):
+        if not name.endswith(".py"):
+            continue
+        tree = ast.parse(open(os.path.join(pkg, name)).read())
+        for node in ast.walk(tree):
+            mods = []
+            if isinstance(node, ast.Import):
+                mods = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                mods = [node.module or ""]
+            assert not any(m == "oracle" or m.startswith("oracle.") for m in mods), (name, mods)
+
+    fresh = importlib.import_module("paper_2503_05020_b300.ipc")
+    saved_path, saved_lib = fresh.LIB_PATH, fresh._lib
+    try:
+        fresh.LIB_PATH, fresh._lib = os.path.join(pkg, "missing", "libipc_b300.so"), None
+        try:
+            fresh.lib()
+            raise AssertionError("missing library did not raise")
+        except ImportError as e:
+            assert "not built" in str(e)
+    finally:
+        fresh.LIB_PATH, fresh._lib = saved_path, saved_lib
