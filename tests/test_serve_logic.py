@@ -130,3 +130,45 @@ def test_multi_step_calls_count_each_env_step_once():
     assert srv.env_steps == 13
     assert rep["batch_steps"] == 12  # three calls of four steps
     assert reqs[1].finished == 0.4 and reqs[0].finished == 1.2
+
+
+def test_slots_bound_the_batch_and_latency_includes_the_wait():
+    """At most max_envs requests are on the GPU at once; the next one is admitted when a slot
+    frees up, and its latency runs from its arrival (queue wait included), not its admission."""
+    reqs = [Request(i, env(f"r{i}", 5 + i), 0.0) for i in range(5)]
+    srv, sc, rep = serve(reqs, max_envs=2)
+    assert rep["completed"] == 5 and rep["max_active"] == 2
+    third = reqs[2]
+    assert third.admitted >= reqs[0].finished > 0.0
+    assert third.latency == third.finished - third.arrival
+    assert third.latency > third.finished - third.admitted
+
+
+def test_admission_rounds_fall_exactly_every_admission_period():
+    """Requests arriving every 0.1 s (one batch step) with an admission period of 8 steps are
+    admitted in rounds at t = 0, 0.8 and 1.6 s: a round as soon as the period has passed."""
+    reqs = [Request(i, env(f"r{i}", 20), 0.1 * i) for i in range(10)]
+    srv, sc, rep = serve(reqs, admit_period=8)
+    rounds = sorted(set(round(t, 6) for kind, _, t in sc.log if kind == "add"))
+    assert rounds == [0.0, 0.8, 1.6]
+
+
+def test_grasp_outcome_of_the_object_rows():
+    """The grasped object's rows in the point list come after every soft vertex and every
+    earlier affine body's vertices; its outcome is their mean displacement, and it counts as
+    held when it rose by more than half the scheduled lift."""
+    from paper_2503_05020_b300.serve import initial_points, object_points, object_result
+
+    soft = [dict(verts=np.zeros((4, 3))), dict(verts=np.ones((3, 3)))]
+    q = np.array([0.5, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1], dtype=np.float64)
+    aff = [dict(verts=np.zeros((6, 3)), q0=q), dict(verts=np.eye(3), q0=q), dict(verts=np.zeros((2, 3)), q0=q)]
+    e = {"soft": soft, "affine": aff, "object": ("affine", 1), "lift": 0.1}
+    assert object_points(e) == slice(13, 16)
+    p0 = initial_points(e)
+    assert p0.shape == (18, 3) and np.allclose(p0[13:16], np.eye(3) + [0.5, 0, 0])
+    for rise, held in ((0.03, False), (0.06, True)):
+        p = p0.copy()
+        p[13:16] += [0.01, 0.0, rise]
+        r = object_result(e, p, p0)
+        assert np.allclose(r["object_disp"], [0.01, 0.0, rise]) and r["held"] is held
+    assert object_points(dict(e, object=("soft", 1))) == slice(4, 7)
