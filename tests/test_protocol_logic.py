@@ -60,3 +60,40 @@ def test_finger_halt_and_label():
     out = P.evaluate_grasp(sc, 0, env, fingers=[0, 1], obj=2, obj_points=slice(0, 4), close_steps=5,
                            eps_v=1e-3, dt=0.01)
     assert out.in_contact and not out.stable
+
+
+class RateScene(FakeScene):
+    """FakeScene with chosen per-step force rates and contact pairs."""
+
+    def __init__(self, n_steps, drift, rates, handles):
+        super().__init__(n_steps, drift)
+        self.rates, self.handles = rates, np.asarray(handles, dtype=np.int32)
+
+    def contact_forces(self, eid):
+        return np.array([r * self.step_no for r in self.rates])
+
+    def contact_handles(self, eid):
+        return self.handles
+
+
+def _run(sc, close_steps=5):
+    T = np.zeros((20, 4, 12))
+    return P.evaluate_grasp(sc, 0, dict(targets=T), fingers=[0, 1], obj=2, obj_points=slice(0, 4),
+                            close_steps=close_steps, eps_v=1e-3, dt=0.01)
+
+
+def test_halt_needs_a_force_above_50_newton():
+    """A finger stops once its contact force exceeds 50 N: exactly 50 N (after the second step at
+    25 N per step) does not stop it, 75 N after the third does."""
+    out = _run(RateScene(20, 1e-7, rates=[25.0, 1.0], handles=[[0, 2], [1, 2]]))
+    assert out.halted == {0: 2}
+
+
+def test_stable_needs_gripper_contact_and_a_still_last_step():
+    """Stable means the object touches a finger (not merely another body, such as a table of
+    handle 3) at the last step, and its centre of mass moved less than eps_v dt over that last
+    step alone: 1.7e-6 m per step is still, although the hold's 15 steps add up to 2.6e-5 m."""
+    out = _run(RateScene(20, 1e-6, rates=[1.0, 1.0], handles=[[0, 2], [1, 2]]))
+    assert out.in_contact and out.stable and out.com_step < 2e-6
+    out = _run(RateScene(20, 1e-7, rates=[1.0, 1.0], handles=[[2, 3], [0, 1]]))
+    assert not out.in_contact and not out.stable
