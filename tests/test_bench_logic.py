@@ -1,0 +1,56 @@
+"""Host arithmetic of the benchmark line (no GPU): the roofline of the dominant kernel (bound
+chosen by the ridge point of its arithmetic intensity, achieved work over its event time, the
+fraction of the peak) and the clock record taken from nvidia-smi samples."""
+import os
+import tempfile
+
+import bench
+
+
+def _prof(ms, launches, work, flops):
+    z = {"ms": 0.0, "launches": 0, "work": 0.0}
+    return {"pcg_solve": {"ms": ms, "launches": launches, "work": work},
+            "pcg_flops": {"ms": 0.0, "launches": 0, "work": flops}, "spmv": dict(z)}
+
+
+def test_roofline_picks_the_bound_by_the_ridge_point():
+    hbm, _ = bench.peaks()
+    ridge = bench.FP64_PEAK_TFLOPS * 1e12 / (hbm * 1e9)  # flop per byte
+    # 2 GB and 0.3 flop/B above the ridge in 10 launches over 5 ms: FP64-arithmetic bound
+    work, flops = 2e9, 2e9 * (ridge * 1.5)
+    r = bench.roofline(_prof(5.0, 10, work, flops), "fp64")
+    assert r["bound"] == "alu"
+    assert abs(r["achieved"] - flops / 5e-3 / 1e12) < 1e-3
+    assert abs(r["frac"] - flops / 5e-3 / 1e12 / bench.FP64_PEAK_TFLOPS) < 1e-3
+    assert r["bytes_per_launch"] == work / 10 and abs(r["avg_launch_us"] - 500.0) < 1e-9
+    # below the ridge, or in mixed precision (FP32 arithmetic is far from its roof): HBM bound
+    for prec, fl in (("fp64", 2e9 * ridge * 0.5), ("mixed", flops)):
+        r = bench.roofline(_prof(5.0, 10, work, fl), prec)
+        assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == hbm
+        assert abs(r["achieved"] - work / 5e-3 / 1e9) < 0.1
+        assert abs(r["frac"] - work / 5e-3 / 1e9 / hbm) < 1e-4
+    assert bench.roofline(_prof(0.0, 0, 0.0, 0.0), "fp64") is None
+
+
+def test_clock_record_reports_median_clock_and_active_reasons():
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    rows = ["0, 1900, 2032, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2032, 2032, 1050.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 1965, 2032, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    with os.fdopen(fd, "w") as f:
+        f.write("\n".join(rows) + "\n")
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.proc, s.path = Done(), path
+    rec = s.stop()
+    assert rec["sm_mhz"] == 1965.0 and rec["sm_max_mhz"] == 2032.0 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]
+    assert not os.path.exists(path)
