@@ -48,3 +48,30 @@ def test_pad_grasp_recipe_and_seed_ranges():
     a, b = S.pad_grasp_env(3), S.pad_grasp_env(3)
     assert np.array_equal(a["soft"][0]["verts"], b["soft"][0]["verts"]) and a["mu"] == b["mu"]
     assert not np.array_equal(S.pad_grasp_env(4)["affine"][0]["verts"], a["affine"][0]["verts"])
+
+
+def test_hand_grasp_recipe():
+    """Rigid hand of 20 PD-driven affine links of about 500 triangles each, grasping a star-shaped
+    soft object of about 20k tets with E log-uniform over [1e4, 1e6] Pa and nu U(0.3, 0.48)."""
+    for k in range(2):
+        env = S.hand_grasp_env(k)
+        obj, links = env["soft"][0], env["affine"]
+        assert 18_000 <= len(obj["tets"]) <= 24_000
+        assert 1e4 <= obj["E"] <= 1e6 and 0.3 <= obj["nu"] <= 0.48
+        assert len(links) == 20 and all(450 <= len(a["tris"]) <= 550 for a in links)
+        assert all(a["pd"] > 0 and not a["kinematic"] for a in links)
+        assert len(env["targets"]) == 400 and np.all(env["gravity"][:200] == 0) and np.all(env["gravity"][200:] == 1)
+
+
+def test_request_schedule_closes_lifts_and_shakes_15_degrees_at_2_hz():
+    """A serving request: 80 closing steps with gravity off, 60 lifting 0.1 m, then 60 steps of a
+    +-15 deg shake about the grasp axis at 2 Hz (dt = 5 ms: the peak falls on the 25th step)."""
+    env = S.grasp_request_env(0)
+    T, g = env["targets"], env["gravity"]
+    assert len(T) == 200 and np.all(g[:80] == 0) and np.all(g[80:] == 1)
+    assert abs(T[139, 0, 2] - 0.1) < 1e-12
+    ang = []
+    for s in range(140, 200):
+        A = np.stack([T[s, 0, 3:6], T[s, 0, 6:9], T[s, 0, 9:12]], axis=1)
+        ang.append(np.degrees(np.arccos(np.clip((np.trace(A) - 1.0) / 2.0, -1.0, 1.0))))
+    assert abs(max(ang) - 15.0) < 1e-9 and int(np.argmax(ang)) == 24
