@@ -546,3 +546,35 @@ def test_gated_gravity_starts_with_its_schedule():
             z += h * vz
         x, _ = e.state()
         assert np.allclose((x - x0).reshape(-1, 3)[:, 2], z, rtol=1e-9, atol=1e-15)
+
+
+def test_failure_semantics_newton_cap_and_non_finite_state():
+    """An env that does not converge within its Newton cap is marked failed (Sec. III-D: after
+    N_iters iterations), as is one whose state is not finite; a failed env takes no further step."""
+    p = S.scene_params(0.01)
+    p["max_newton"] = 1
+    e = O.OracleEnv(p, S.cube_squeeze_env(0, n_steps=10, close_steps=5))
+    assert e.step(3) == "FAILED"
+    st = e.status()
+    assert st["reason"] == 1 and st["steps_done"] == 0 and st["newton_iters"] == 1
+    x, _ = e.state()
+    assert e.step(2) == "FAILED" and e.status()["newton_iters"] == 1
+    assert np.array_equal(e.state()[0], x)
+
+    e = O.OracleEnv(S.scene_params(0.01), S.resting_env("block", n_steps=5))
+    x, v = e.state()
+    v = v.copy()
+    v[4] = np.nan
+    e.set_state(x, v, 0)
+    assert e.step(1) == "FAILED" and e.status()["reason"] == 3
+
+
+def test_a_step_at_equilibrium_converges_in_one_newton_iteration():
+    """Stopping rule |p|_inf / h < tol: once a body rests in equilibrium, the first Newton step
+    of the next time step is already below the tolerance."""
+    p = S.scene_params(0.01, newton_tol=1e-6)
+    e = O.OracleEnv(p, S.resting_env("rigid", n_steps=200))
+    e.step(190)
+    n0 = e.status()["newton_iters"]
+    assert e.step(5) == "ACTIVE"
+    assert e.status()["newton_iters"] - n0 == 5
