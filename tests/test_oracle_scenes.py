@@ -182,6 +182,13 @@ def test_constraint_candidates_are_conservative():
     for r in contacts:
         assert (r[0], r[1], r[2]) in cand
     assert np.all(d2 < p["dhat"] ** 2)
+    # the list's form (what the GPU list must equal bit for bit): sorted by (kind, i, j), no
+    # duplicate, each edge-edge pair once with i < j; the same for the swept (CCD) list
+    for c in (e.candidates(x), e.candidates(x, e.newton_direction())):
+        rows = [tuple(r) for r in c]
+        assert rows == sorted(set(rows)) and len(rows) > 0
+        ee = c[c[:, 0] == 1]
+        assert len(ee) > 0 and np.all(ee[:, 1] < ee[:, 2])
 
 
 @pytest.mark.slow
