@@ -18,6 +18,10 @@
 // Jacobi eigensolver. The linear solve is conjugate gradients to 1e-12 relative residual.
 // Broad phase is all pairs. Built with -ffp-contract=off so that every expression rounds as
 // written.
+//
+// Parity unpinned: the in-step doubling of the adapted barrier stiffness (step_once; the
+// paper gives no rule, so its trigger and factor are a reading). Its bounds and the stepping
+// invariants are tested; no closed form fixes the values it produces.
 #include <algorithm>
 #include <array>
 #include <atomic>
