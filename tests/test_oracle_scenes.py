@@ -585,3 +585,61 @@ def test_a_step_at_equilibrium_converges_in_one_newton_iteration():
     n0 = e.status()["newton_iters"]
     assert e.step(5) == "ACTIVE"
     assert e.status()["newton_iters"] - n0 == 5
+
+
+def _sym_fd_hessian(e, q, step):
+    H = _fd_hessian(e, q, range(len(q)), step)
+    return 0.5 * (H + H.T)
+
+
+def _free_tet(v):
+    t = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    if np.linalg.det(np.stack([v[1] - v[0], v[2] - v[0], v[3] - v[0]])) < 0:
+        t = np.array([[0, 2, 1, 3]], dtype=np.int32)
+    return dict(verts=v, tets=t, tris=S.boundary_tris(v, t), E=1e5, nu=0.4, rho=1000.0, kin=np.zeros(4, dtype=np.uint8))
+
+
+def test_projection_makes_the_hessian_psd_where_the_raw_one_is_not():
+    """Projected Newton: every element Hessian is projected to PSD before assembly, so the
+    assembled Hessian is PSD even where the exact one (central differences of the gradient) is
+    indefinite. With dt = 1 s the element terms dominate the mass: a strongly compressed and
+    sheared tet (Neo-Hookean), a tet's vertex 0.3 dhat below another free tet's face (barrier),
+    and an affine body at A = I/2 (orthogonality)."""
+    p = S.scene_params(1.0)
+    env = S.single_tet_env(n_steps=2)
+    env["gravity"][:] = 0
+    e = O.OracleEnv(p, env)
+    e.step(1)
+    x, _ = e.state()
+    q = x.copy()
+    q[9:12] = [0.002, 0.001, 0.003]
+    cases = [(e, q, 1e-10)]
+
+    g = 0.3 * p["dhat"]
+    a = np.array([[0, 0, 0], [0.01, 0, 0], [0, 0.01, 0], [0, 0, 0.01]], dtype=np.float64)
+    b = np.array([[0.002, 0.002, -g], [-0.003, -0.003, -g - 0.01], [0.007, -0.003, -g - 0.01],
+                  [-0.003, 0.007, -g - 0.01]])
+    env = dict(soft=[_free_tet(a), _free_tet(b)], affine=[], mu=0.0, gravity=np.zeros(2, dtype=np.uint8),
+               targets=np.tile(S.IDENTITY_Q, (2, 2, 1)))
+    e = O.OracleEnv(p, env)
+    x, _ = e.state()
+    assert len(e.contacts(x)[0]) == 1
+    cases.append((e, x, 1e-11))
+
+    bv, bt = S.box_surface((0.02, 0.015, 0.01))
+    body = dict(verts=bv, tris=bt, rho=800.0, q0=S.IDENTITY_Q.copy(), qdot0=np.zeros(12), kinematic=False)
+    env = dict(soft=[], affine=[body], mu=0.0, gravity=np.zeros(2, dtype=np.uint8),
+               targets=np.tile(S.IDENTITY_Q, (2, 1, 1)))
+    e = O.OracleEnv(p, env)
+    e.step(1)
+    x, _ = e.state()
+    q = x.copy()
+    q[3:12] *= 0.5
+    cases.append((e, q, 1e-8))
+
+    for e, q, step in cases:
+        raw = _sym_fd_hessian(e, q, step)
+        assert np.linalg.eigvalsh(raw).min() < -1e-2 * np.abs(raw).max()
+        H = e.hessian(q)
+        assert np.allclose(H, H.T, atol=1e-12 * np.abs(H).max())
+        assert np.linalg.eigvalsh(H).min() > -1e-9 * np.abs(H).max()
