@@ -54,3 +54,17 @@ def test_clock_record_reports_median_clock_and_active_reasons():
     assert rec["sm_mhz"] == 1965.0 and rec["sm_max_mhz"] == 2032.0 and rec["samples"] == 3
     assert rec["reasons"] == ["sw_power_cap"]
     assert not os.path.exists(path)
+
+
+def test_reference_arm_runs_on_rank_0_only():
+    """Under torchrun the oracle arm runs and prints on rank 0 alone; any other rank exits 0
+    without work and without output."""
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True, env=env, cwd=root,
+                       timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == ""
