@@ -186,6 +186,33 @@ def test_distance_derivatives_match_finite_differences(kind):
             assert np.allclose((gp - gm) / 2e-7, H[i], atol=1e-5 * max(np.abs(H).max(), 1e-12))
 
 
+def test_distances_in_degenerate_configurations():
+    """Closed forms where the closest-feature selection is fragile: exactly parallel edges
+    (overlapping, offset along their line, and collinear with a gap), crossing edges, and a point
+    exactly on a triangle's face, edge and corner."""
+    E = lambda a0, a1, b0, b1: O.pair_dist2(1, np.concatenate([a0, a1, b0, b1]))[0]
+    P = lambda p, a, b, c: O.pair_dist2(0, np.concatenate([p, a, b, c]))[0]
+    z = np.zeros(3)
+    ex, ey = np.array([1.0, 0, 0]), np.array([0, 1.0, 0])
+    h = 0.003
+    # parallel, overlapping in projection: the perpendicular offset
+    assert math.isclose(E(z, ex, h * ey + 0.2 * ex, h * ey + 1.5 * ex), h * h, rel_tol=1e-12)
+    # parallel, no overlap: the distance between the nearest endpoints
+    assert math.isclose(E(z, ex, h * ey + 1.4 * ex, h * ey + 2.0 * ex), 0.4 ** 2 + h * h, rel_tol=1e-12)
+    # collinear with a gap of 0.25
+    assert math.isclose(E(z, ex, 1.25 * ex, 2.0 * ex), 0.25 ** 2, rel_tol=1e-12)
+    # antiparallel copy shifted by h: same as parallel
+    assert math.isclose(E(z, ex, h * ey + ex, h * ey), h * h, rel_tol=1e-12)
+    # crossing at right angles, h apart
+    ez = np.array([0, 0, 1.0])
+    assert math.isclose(E(z, ex, 0.5 * ex - 0.5 * ey + h * ez, 0.5 * ex + 0.5 * ey + h * ez), h * h, rel_tol=1e-12)
+    a, b, c = z, ex, ey
+    assert P(np.array([0.2, 0.3, 0.0]), a, b, c) == 0.0  # on the face
+    assert P(np.array([0.5, 0.0, 0.0]), a, b, c) == 0.0  # on an edge
+    assert P(b.copy(), a, b, c) == 0.0  # on a corner
+    assert math.isclose(P(np.array([0.7, 0.7, 0.0]), a, b, c), 2 * 0.2 ** 2, rel_tol=1e-12)  # beyond the hypotenuse
+
+
 def test_pt_distance_continuous_across_regions():
     """On the boundary between two regions both typed formulas give the same distance."""
     a, b, c = np.array([0.0, 0, 0]), np.array([1.0, 0, 0]), np.array([0.0, 1, 0])
