@@ -68,7 +68,7 @@ typedef struct {
   int32_t precision;     /* ipc_precision */
   uint64_t hbm_budget_bytes; /* 0 = no admission limit */
   int32_t device;        /* CUDA device ordinal */
-  int32_t pcg_cluster;   /* PCG launch shape: 0 = automatic, 1/2/4/8 = one persistent cluster of
+  int32_t pcg_cluster;   /* PCG launch shape: 0 = automatic, 1/2/4/8/16 = one persistent cluster of
                             that many CTAs per environment, -1 = one launch per PCG phase over
                             tiles of all environments */
   int32_t fresh_broad_phase; /* 0: inside a time step, the line-search trials and the later Newton

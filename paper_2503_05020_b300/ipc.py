@@ -160,7 +160,7 @@ class Scene:
             d.gravity[k] = params["gravity"][k]
         d.max_newton, d.max_ls_halvings, d.max_pcg_iters = params["max_newton"], params["max_ls"], params["max_pcg"]
         d.precision, d.hbm_budget_bytes, d.device = precision, hbm_budget_bytes, device
-        d.pcg_cluster = pcg_cluster  # 0 automatic, 1/2/4/8 CTAs per env cluster, -1 tiled multi-launch
+        d.pcg_cluster = pcg_cluster  # 0 automatic, 1/2/4/8/16 CTAs per env cluster, -1 tiled multi-launch
         d.fresh_broad_phase = int(bool(fresh_broad_phase))  # 1: a BVH traversal at every evaluation
         d.kappa_adapt = int(bool(params.get("kappa_adapt", False)))  # 1: adapted barrier stiffness per env
         d.cuda_stream = stream
