@@ -88,24 +88,21 @@ def kuhn_grid(nx: int, ny: int, nz: int, lo, hi, cell_mask: np.ndarray | None = 
     grid = np.stack([gi.ravel(), gj.ravel(), gk.ravel()], axis=1)
     verts = lo + (hi - lo) * grid / np.array([nx, ny, nz], dtype=np.float64)
 
-    def vid(i, j, k):
-        return (i * (ny + 1) + j) * (nz + 1) + k
-
+    # cells in (i, j, k) order, each cut into 6 tets: one per order in which the path from its
+    # lowest to its highest corner steps along the three axes
+    ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    cells = np.stack([ci.ravel(), cj.ravel(), ck.ravel()], axis=1)
+    if cell_mask is not None:
+        cells = cells[np.asarray(cell_mask, dtype=bool).ravel()]
+    strides = np.array([(ny + 1) * (nz + 1), nz + 1, 1], dtype=np.int64)
     perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
-    tets = []
-    for i in range(nx):
-        for j in range(ny):
-            for k in range(nz):
-                if cell_mask is not None and not cell_mask[i, j, k]:
-                    continue
-                for p in perms:
-                    c = [i, j, k]
-                    path = [tuple(c)]
-                    for ax in p:
-                        c[ax] += 1
-                        path.append(tuple(c))
-                    tets.append([vid(*q) for q in path])
-    tets = np.asarray(tets, dtype=np.int64)
+    corner = np.zeros((6, 4), dtype=np.int64)  # vertex-id offset of each path corner
+    for a, p in enumerate(perms):
+        c = np.zeros(3, dtype=np.int64)
+        for q, ax in enumerate(p):
+            c[ax] += 1
+            corner[a, q + 1] = c @ strides
+    tets = ((cells.astype(np.int64) @ strides)[:, None, None] + corner[None]).reshape(-1, 4)
     used = np.unique(tets)
     remap = -np.ones(len(verts), dtype=np.int64)
     remap[used] = np.arange(len(used))
@@ -117,27 +114,26 @@ def kuhn_grid(nx: int, ny: int, nz: int, lo, hi, cell_mask: np.ndarray | None = 
 
 
 def boundary_tris(verts: np.ndarray, tets: np.ndarray) -> np.ndarray:
-    """Faces used by exactly one tet, oriented so that the normal points out of that tet."""
-    faces = {}
-    for t in tets:
-        for f, opp in (((t[1], t[2], t[3]), t[0]), ((t[0], t[2], t[3]), t[1]),
-                       ((t[0], t[1], t[3]), t[2]), ((t[0], t[1], t[2]), t[3])):
-            key = tuple(sorted(f))
-            if key in faces:
-                faces[key] = None
-            else:
-                faces[key] = (f, opp)
-    out = []
-    for v in faces.values():
-        if v is None:
-            continue
-        (a, b, c), d = v
-        n = np.cross(verts[b] - verts[a], verts[c] - verts[a])
-        if np.dot(n, verts[d] - verts[a]) > 0:
-            b, c = c, b
-        out.append((a, b, c))
-    out.sort()
-    return np.asarray(out, dtype=np.int32)
+    """Faces used by exactly one tet, oriented so that the normal points out of that tet, sorted
+    by their vertex triples."""
+    tets = np.asarray(tets, dtype=np.int64)
+    if len(tets) == 0:
+        return np.zeros((0, 3), dtype=np.int32)
+    # face k of a tet leaves out its vertex k (kept vertices in tet order)
+    keep = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    faces = tets[:, keep].reshape(-1, 3)
+    opp = tets.reshape(-1)
+    s = np.sort(faces, axis=1)
+    nv = np.int64(max(len(verts), 1))
+    _, first, counts = np.unique((s[:, 0] * nv + s[:, 1]) * nv + s[:, 2], return_index=True, return_counts=True)
+    sel = first[counts == 1]
+    f, d = faces[sel], opp[sel]
+    a, b, c = verts[f[:, 0]], verts[f[:, 1]], verts[f[:, 2]]
+    n = np.cross(b - a, c - a)
+    inward = np.einsum("ij,ij->i", n, verts[d] - a) > 0
+    f[inward, 1], f[inward, 2] = f[inward, 2].copy(), f[inward, 1].copy()
+    f = f[np.lexsort((f[:, 2], f[:, 1], f[:, 0]))]
+    return f.astype(np.int32)
 
 
 def box_surface(half_extents) -> tuple[np.ndarray, np.ndarray]:
@@ -428,13 +424,10 @@ def pad_grasp_state_at(env: dict, step: int) -> tuple[np.ndarray, np.ndarray]:
     return x, np.zeros_like(x)
 
 
-def soft_object_grasp_env(env_id: int, base_seed: int = BASE_SEED, n_steps: int = 100,
-                          close_steps: int = 50, dt: float = 0.005, dhat: float = 1e-3,
-                          tets_lo: int = 2000, tets_hi: int = 60000, bimanual: bool | None = None,
-                          squeeze: float = 1.5e-3, lift: float = 0.05) -> dict:
-    """Uneven-batch scene: a star-shaped soft object of log-uniform size in [tets_lo, tets_hi]
-    held by rigid kinematic plates (one pair, or two pairs when bimanual)."""
-    rng = SplitMix64(base_seed + env_id)
+def star_object(rng: SplitMix64, tets_lo: int = 2000, tets_hi: int = 60000) -> dict:
+    """Soft star-shaped object of log-uniform size in [tets_lo, tets_hi] tets: radius U(0.02,
+    0.04) m, E log-uniform over 1e4-1e6 Pa, nu U(0.3, 0.45), rho 1000 kg/m^3 (Sec. III-B
+    randomises stiffness and scale per object)."""
     target_tets = math.exp(rng.uniform(math.log(tets_lo), math.log(tets_hi)))
     # a Kuhn ball of n^3 cells keeps about (pi/6) n^3 cells, 6 tets each
     n = max(4, int(round((target_tets / (6 * math.pi / 6)) ** (1 / 3))))
@@ -443,11 +436,22 @@ def soft_object_grasp_env(env_id: int, base_seed: int = BASE_SEED, n_steps: int 
     tris = boundary_tris(verts, tets)
     E = math.exp(rng.uniform(math.log(1e4), math.log(1e6)))
     nu = rng.uniform(0.3, 0.45)
+    return dict(verts=verts, tets=tets, tris=tris, E=E, nu=nu, rho=1000.0,
+                kin=np.zeros(len(verts), dtype=np.uint8))
+
+
+def soft_object_grasp_env(env_id: int, base_seed: int = BASE_SEED, n_steps: int = 100,
+                          close_steps: int = 50, dt: float = 0.005, dhat: float = 1e-3,
+                          tets_lo: int = 2000, tets_hi: int = 60000, bimanual: bool | None = None,
+                          squeeze: float = 1.5e-3, lift: float = 0.05) -> dict:
+    """Uneven-batch scene: a star-shaped soft object of log-uniform size in [tets_lo, tets_hi]
+    held by rigid kinematic plates (one pair, or two pairs when bimanual)."""
+    rng = SplitMix64(base_seed + env_id)
+    soft = star_object(rng, tets_lo, tets_hi)
+    verts = soft["verts"]
     mu = rng.uniform(0.3, 0.8)
     if bimanual is None:
         bimanual = rng.uniform() < 0.25
-    soft = dict(verts=verts, tets=tets, tris=tris, E=E, nu=nu, rho=1000.0,
-                kin=np.zeros(len(verts), dtype=np.uint8))
     gap = 1.5 * dhat
     pt = 0.004
     pv, ptris = box_surface((pt, 0.05, 0.05))
@@ -482,6 +486,95 @@ def soft_object_grasp_env(env_id: int, base_seed: int = BASE_SEED, n_steps: int 
     targets[:, 0] = IDENTITY_Q
     gravity = (np.arange(n_steps) >= close_steps).astype(np.uint8)
     return dict(soft=[soft], affine=affine, mu=mu, gravity=gravity, targets=targets)
+
+
+def _rot_z90(body: dict) -> dict:
+    """A soft body turned by +90 degrees about z: (x, y, z) -> (-y, x, z) (a proper rotation keeps
+    tet and triangle orientations)."""
+    b = dict(body)
+    v = body["verts"]
+    b["verts"] = np.ascontiguousarray(np.stack([-v[:, 1], v[:, 0], v[:, 2]], axis=1))
+    return b
+
+
+def soft_pad_grasp_env(env_id: int, base_seed: int = BASE_SEED + 65537, n_steps: int = 300,
+                       close_steps: int = 100, dt: float = 0.005, dhat: float = 1e-3, squeeze: float = 2e-3,
+                       lift: float = 0.1, tets_lo: int = 2000, tets_hi: int = 60000,
+                       bimanual: bool | None = None, pad_cells=(6, 8, 18)) -> dict:
+    """The pad grasp with a soft object: two soft wedge finger pads (~5k tets each, E=2e5 Pa,
+    nu=0.45; two pairs at right angles when bimanual) around a star-shaped soft object of
+    log-uniform 2k-60k tets. Close with gravity off, then lift with gravity on."""
+    rng = SplitMix64(base_seed + env_id)
+    obj = star_object(rng, tets_lo, tets_hi)
+    mu = rng.uniform(0.3, 0.8)
+    if bimanual is None:
+        bimanual = rng.uniform() < 0.25
+    ov = obj["verts"]
+    gap = 1.5 * dhat
+    ext = {(0, +1): ov[:, 0].max(), (0, -1): -ov[:, 0].min(), (1, +1): ov[:, 1].max(), (1, -1): -ov[:, 1].min()}
+    # two pairs: pads narrow enough that the x pair's edges stay clear of the y pair's faces
+    width = 0.04 if not bimanual else min(0.04, 1.6 * min(ext.values()))
+    pads, moves = [], []
+    for ax in ([0, 1] if bimanual else [0]):
+        for sgn in (+1, -1):
+            pad = finger_pad(rng, sgn, ext[(ax, sgn)] + gap, 2e5, 0.45, n=pad_cells, width=width)
+            pads.append(_rot_z90(pad) if ax == 1 else pad)
+            moves.append((ax, sgn))
+    speed = (gap + squeeze) / (close_steps * dt)
+    lift_speed = lift / (max(n_steps - close_steps, 1) * dt)
+    targets = np.zeros((n_steps, len(pads) + 1, 12))
+    for s in range(n_steps):
+        nc = min(s + 1, close_steps)
+        nl = max(s + 1 - close_steps, 0)
+        for b, (ax, sgn) in enumerate(moves):
+            d = np.zeros(3)
+            d[ax] = -sgn * speed * dt * nc
+            d[2] = lift_speed * dt * nl
+            targets[s, b] = _translation_q(d)
+        targets[s, len(pads)] = IDENTITY_Q
+    gravity = (np.arange(n_steps) >= close_steps).astype(np.uint8)
+    return dict(soft=pads + [obj], affine=[], mu=mu, gravity=gravity, targets=targets,
+                object=("soft", len(pads)), lift=lift)
+
+
+UNEVEN_SEED = BASE_SEED + 1048576
+
+
+def uneven_batch_env(env_id: int, base_seed: int = UNEVEN_SEED) -> dict:
+    """One environment of the uneven batch: with equal odds the plate squeeze (a soft object
+    between kinematic rigid plates: the single-env configuration's form) or the pad grasp (soft
+    finger pads: the pad configuration's form), each holding a star-shaped soft object of
+    log-uniform 2k-60k tets, with two gripper pairs in a quarter of the envs. dt = 5 ms. Every
+    env's schedule leaves its grippers 0.7-0.8 mm from the object at step UNEVEN_START_STEP."""
+    rng = SplitMix64(base_seed + env_id)
+    pads = rng.uniform() < 0.5
+    bimanual = rng.uniform() < 0.25
+    if pads:
+        return soft_pad_grasp_env(env_id, base_seed=base_seed + 7, bimanual=bimanual)
+    return soft_object_grasp_env(env_id, base_seed=base_seed + 7, n_steps=150, close_steps=75,
+                                 bimanual=bimanual)
+
+
+UNEVEN_START_STEP = 20
+
+
+def grasp_state_at(env: dict, step: int) -> tuple[np.ndarray, np.ndarray]:
+    """Synthetic start of a grasp env at schedule step `step`: every soft body with kinematic
+    vertices translated by the displacement its schedule reaches at the end of step-1, every
+    kinematic affine body at its scheduled coordinates, everything else at rest where it was
+    built. Returns (DOFs, zero velocities)."""
+    x = initial_dofs(env)
+    off = 0
+    for b, s in enumerate(env["soft"]):
+        n = len(s["verts"])
+        if step > 0 and np.any(s["kin"]):
+            x[3 * off: 3 * (off + n)].reshape(-1, 3)[:] += np.asarray(env["targets"][step - 1, b][:3])
+        off += n
+    ns = len(env["soft"])
+    for a, body in enumerate(env["affine"]):
+        if step > 0 and body["kinematic"]:
+            x[3 * off + 12 * a: 3 * off + 12 * (a + 1)] = env["targets"][step - 1, ns + a]
+    return x, np.zeros_like(x)
 
 
 # ---------------------------------------------------------------- small test scenes

@@ -494,3 +494,74 @@ def test_hull_mass_positive_definite():
     M, vol = O.mass_properties(v, t, 1000.0)
     assert vol > 0 and np.linalg.eigvalsh(M).min() > 0
     assert len(t) == 1584
+
+
+def exact_segment_d2(x):
+    """Exact squared distance between segments a0a1 and b0b1 of the given doubles, in rational
+    arithmetic: the minimum of the convex quadratic |a0 + s d1 - b0 - t d2|^2 over [0,1]^2 is at
+    the interior stationary point when that lies inside, else on one of the four sides, where it
+    is a clamped one-dimensional minimum."""
+    from fractions import Fraction as Fr
+
+    P = [[Fr(float(v)) for v in x[3 * i:3 * i + 3]] for i in range(4)]
+    d1 = [P[1][k] - P[0][k] for k in range(3)]
+    d2 = [P[3][k] - P[2][k] for k in range(3)]
+    r = [P[0][k] - P[2][k] for k in range(3)]
+    dot = lambda u, v: sum(ui * vi for ui, vi in zip(u, v))
+    a, b, e, c, f = dot(d1, d1), dot(d1, d2), dot(d2, d2), dot(d1, r), dot(d2, r)
+    q = lambda s, t: dot(*[[r[k] + s * d1[k] - t * d2[k] for k in range(3)]] * 2)
+    clamp = lambda v: min(max(v, Fr(0)), Fr(1))
+    cands = []
+    den = a * e - b * b
+    if den > 0:
+        s, t = (b * f - c * e) / den, (a * f - b * c) / den
+        if 0 <= s <= 1 and 0 <= t <= 1:
+            cands.append(q(s, t))
+    for s0 in (Fr(0), Fr(1)):
+        cands.append(q(s0, clamp((f + s0 * b) / e)))
+    for t0 in (Fr(0), Fr(1)):
+        cands.append(q(clamp((t0 * b - c) / a), t0))
+    return min(cands)
+
+
+def crossing_edges(rng, L1, L2, h, sin2):
+    """Two edges whose lines pass h apart at interior points of both, at angle theta with
+    sin^2 theta = sin2, in a random frame."""
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    u, w, n = Q[:, 0], Q[:, 1], Q[:, 2]
+    st = math.sqrt(sin2)
+    d1 = L1 * u
+    d2 = L2 * (math.sqrt(1.0 - sin2) * u + st * w)
+    a0 = rng.normal(size=3) * 0.01
+    s, t = rng.uniform(0.2, 0.8), rng.uniform(0.2, 0.8)
+    b0 = a0 + s * d1 + h * n - t * d2
+    return np.concatenate([a0, a0 + d1, b0, b0 + d2])
+
+
+def test_near_parallel_edge_band_within_its_error_bound():
+    """Reading 7's band: edges with sin^2 theta <= 1e-10 are treated as parallel, so their closest
+    pair is taken on an endpoint (never the interior line-line pair). Against the exact minimum
+    the oracle's distance can then only be too large, and by at most max(|e_a|, |e_b|) sin theta
+    (the separation of the two lines changes by at most that much along an edge). Just outside
+    the band (sin^2 theta from 1e-9 to 1e-7) the oracle must return the exact minimum, the
+    interior line-line distance, to 1e-9 relative."""
+    rng = np.random.default_rng(20250306)
+    for sin2 in (1e-12, 3e-12, 1e-11, 3e-11):
+        for _ in range(25):
+            L1, L2 = rng.uniform(0.004, 0.02, size=2)
+            h = rng.uniform(1e-5, 1e-3)
+            x = crossing_edges(rng, L1, L2, h, sin2)
+            d2, t, _, _ = O.pair_dist2(1, x)
+            ex = float(exact_segment_d2(x))
+            assert t != 8, "an edge pair inside the parallel band was typed line-line"
+            assert d2 >= ex * (1 - 1e-12)
+            assert math.sqrt(d2) - math.sqrt(ex) <= max(L1, L2) * math.sqrt(sin2) * (1 + 1e-6) + 1e-15
+    for sin2 in (1e-9, 1e-8, 1e-7):
+        for _ in range(25):
+            L1, L2 = rng.uniform(0.004, 0.02, size=2)
+            h = rng.uniform(1e-5, 1e-3)
+            x = crossing_edges(rng, L1, L2, h, sin2)
+            d2, t, _, _ = O.pair_dist2(1, x)
+            ex = float(exact_segment_d2(x))
+            assert t == 8
+            assert abs(d2 - ex) <= 1e-9 * ex, (sin2, d2, ex)
