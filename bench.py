@@ -1,14 +1,31 @@
 """Benchmark: IPC sim-steps per second summed over environments.
 
-Workload (N=1): 64 pad-grasp environments (two soft wedge finger pads of ~5k Neo-Hookean tets
-each squeezing a rigid affine-body convex hull of 1584 triangles, dt = 5 ms, FP64), stepped as
-one batch through the C ABI. Every run starts from the same synthetic contact-phase state
-(pads placed where the closing schedule puts them at step 20, 0.8 mm from the object), does W
-untimed steps and times K steps of every env. A "step" is one ipc_step over the whole batch:
-every active env advances one time step (its full Newton loop).
+Workload (N=1, default): the uneven batch, 1024 grasp environments stepped as one batch through
+the C ABI. Each env is, with equal odds, a soft star-shaped object of log-uniform 2k-60k
+Neo-Hookean tets squeezed between kinematic rigid plates, or the same kind of object grasped by
+two soft wedge finger pads (~5k tets each); a quarter of the envs have two gripper pairs. dt =
+5 ms, FP64, objects' E log-uniform 1e4-1e6 Pa. Every run starts from the same synthetic
+contact-phase state (grippers placed where their schedules put them at step 20, 0.7-0.8 mm from
+the object), does W untimed steps and times K steps of every env. A "step" is one ipc_step over
+the whole batch: every active env advances one time step (its full Newton loop).
+`--workload pads` selects the 64-env pad grasp of a rigid hull instead.
 
-Under torchrun every rank runs its own 64 envs (seeds offset by rank): independent replicas,
-weak scaling, no collective on the data path; the rank times are combined by max.
+Legs of the same JSON line:
+  value        FP64 batched, device-timed (CUDA events on the scene's stream)
+  e2e          the same K steps through the public API with host buffers (next targets up,
+               all DOFs down, every step)
+  plain_fp64   the same kernels one env at a time (a stated sample of the envs, from the same
+               states): the plain GPU stepper, and the paper-style ratio of N envs batched
+               over the same N envs run in sequence (Sec. IV-A)
+  mixed_precision  the same K steps in mixed precision, and the error of both precisions
+               against a converged FP64 solve of a sample
+  cpu_baseline the CPU oracle on a bounded sample, one env per host core
+  serving      grasp-evaluation requests served by continuous batching
+
+Under torchrun every rank runs its own batch: the global pool of world x N envs is split by
+greedy longest-processing-time bin-packing of their estimated costs (tets + surface size), so
+the ranks get equal work (weak scaling, no collective on the data path); rank times combine by
+max.
 
 --impl reference times the CPU oracle (plain FP64, no GPU) on a bounded sample of the same
 workload on the host cores.
@@ -17,12 +34,13 @@ from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mpc
 import os
+import platform
 import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -34,46 +52,104 @@ from paper_2503_05020_b300 import scenes as S  # noqa: E402
 
 METRIC = "IPC sim-steps/s summed over envs"
 UNIT = "env-steps/s"
-START_STEP = 20
 DT = 0.005
+
+
+class Workload:
+    def __init__(self, name: str):
+        self.name = name
+        if name == "uneven":
+            self.build, self.state_at, self.start = S.uneven_batch_env, S.grasp_state_at, S.UNEVEN_START_STEP
+            self.cost = S.uneven_batch_cost
+        else:
+            self.build, self.state_at, self.start = S.pad_grasp_env, S.pad_grasp_state_at, 20
+            self.cost = lambda i: 1.0
+
+    def config(self, n_env, tets, world):
+        if self.name == "uneven":
+            w = (f"uneven batch x{n_env} envs: soft star objects of log-uniform 2k-60k tets squeezed by rigid plates "
+                 f"or grasped by two soft pads (~5k tets each), 25% with two gripper pairs, dt={DT}s, FP64, "
+                 f"from schedule step {self.start}")
+            sched = "plates: close 75 steps, lift; pads: close 100 steps (gravity off), then lift (gravity on)"
+        else:
+            w = (f"pad-grasp x{n_env} envs (2 soft pads ~5k tets each + rigid hull 1584 tris), dt={DT}s, FP64, "
+                 f"from schedule step {self.start}")
+            sched = "close 100 steps (gravity off) then lift 0.1 m (gravity on)"
+        return {"workload": w, "envs_per_gpu": n_env, "tets_per_env_avg": tets, "start_step": self.start,
+                "schedule": sched, "l2": "inputs larger than L2 (BSR + element buffers of the batch exceed 126 MB)",
+                "parallelism": "replicas" if world == 1 else f"env-sharded x{world} (LPT by estimated cost)"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--envs", type=int, default=64)
+    ap.add_argument("--workload", default="uneven", choices=["uneven", "pads"])
+    ap.add_argument("--envs", type=int, default=None, help="envs per GPU (default 1024 uneven, 64 pads)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--pcg-cluster", type=int, default=0,
-                    help="PCG launch shape: 0 automatic, 1/2/4/8 CTAs per env cluster, -1 tiled multi-launch")
+                    help="PCG launch shape: 0 automatic, 1/2/4/8/16 CTAs per env cluster, -1 tiled multi-launch")
+    ap.add_argument("--plain-envs", type=int, default=16, help="envs of the one-env-at-a-time leg (0: none)")
+    ap.add_argument("--ref-envs", type=int, default=16, help="envs of the converged FP64 reference (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: none)")
     ap.add_argument("--serve-rate", type=float, default=1.5, help="Poisson arrival rate of the serving leg (1/s)")
     ap.add_argument("--no-mixed-leg", action="store_true",
                     help="skip the mixed-precision run of the same steps that the FP64 line reports beside it")
     ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle time for --impl reference")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.envs is None:
+        a.envs = 1024 if a.workload == "uneven" else 64
+    return a
 
 
-def workload_config(n_env, tets, start):
-    return {"workload": f"pad-grasp x{n_env} envs (2 soft pads ~5k tets each + rigid hull 1584 tris), "
-                        f"dt={DT}s, FP64, from schedule step {start}",
-            "envs_per_gpu": n_env, "tets_per_env_avg": tets, "start_step": start,
-            "schedule": "close 100 steps (gravity off) then lift 0.1 m (gravity on)",
-            "l2": "inputs larger than L2 (BSR + element buffers of the batch exceed 126 MB)",
-            "parallelism": "replicas"}
+def shard_env_ids(rank, world, n_env, cost=None):
+    """Env ids of one rank. The global pool holds world * n_env envs; it is split by greedy
+    longest-processing-time bin-packing of the envs' estimated costs, so each rank gets an equal
+    share of the work (the counts may differ by a few envs). Disjoint, and the same on every
+    rank without communication."""
+    ids = list(range(world * n_env))
+    if world == 1:
+        return ids
+    costs = [cost(i) if cost else 1.0 for i in ids]
+    return S.lpt_shards(costs, world)[rank]
 
 
-def shard_env_ids(rank, n_env):
-    """Env seeds of one rank: rank r steps envs r*n .. r*n + n - 1 (independent replicas with
-    disjoint envs; the batch shards across ranks with no data-path collective)."""
-    return [rank * n_env + i for i in range(n_env)]
+def _build_one(args):
+    name, i = args
+    return Workload(name).build(i)
 
 
-def make_envs(rank, n_env):
-    return [S.pad_grasp_env(i) for i in shard_env_ids(rank, n_env)]
+def make_envs(wl: Workload, ids):
+    """Build the envs (a spawned process pool: no CUDA context is ever forked)."""
+    n_proc = min(len(ids), os.cpu_count() or 1, 16)
+    if len(ids) < 64 or n_proc <= 1:
+        return [wl.build(i) for i in ids]
+    with mpc.get_context("spawn").Pool(n_proc) as pool:
+        return pool.map(_build_one, [(wl.name, i) for i in ids], chunksize=8)
+
+
+# The oracle's cost grows faster than linearly with an env's size (all-pairs broad phase, CG to
+# 1e-12): its timed sample takes envs of at most this many tets (the small end of the batch), so
+# that one step of the sample takes seconds, not hours.
+CPU_SAMPLE_MAX_TETS = 6000
+
+
+def cpu_sample(tets, n):
+    """Envs of the CPU oracle sample: n envs at evenly spaced size quantiles among the envs of at
+    most CPU_SAMPLE_MAX_TETS tets (all envs when none is that small)."""
+    small = [i for i, t in enumerate(tets) if t <= CPU_SAMPLE_MAX_TETS] or list(range(len(tets)))
+    return [small[j] for j in stratified([tets[i] for i in small], n)]
+
+
+def stratified(values, n):
+    """Indices of n items at evenly spaced quantiles (i + 0.5) / n of the given values (ties by
+    index): a sample that keeps the batch's size mix."""
+    order = sorted(range(len(values)), key=lambda i: (values[i], i))
+    n = min(n, len(order))
+    return sorted({order[int((k + 0.5) * len(order) / n)] for k in range(n)})
 
 
 def max_over_ranks(v, world, device):
@@ -88,9 +164,20 @@ def max_over_ranks(v, world, device):
     return float(t.item())
 
 
-def job_throughput(world, n_env, steps, seconds):
-    """Whole-job env-steps/s: the envs and steps of every rank over the slowest rank's time."""
-    return world * n_env * steps / seconds
+def sum_over_ranks(v, world, device):
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(env_steps, seconds):
+    """Whole-job env-steps/s: the env-steps of every rank over the slowest rank's time."""
+    return env_steps / seconds
 
 
 class ClockSampler:
@@ -147,6 +234,18 @@ def peaks():
     return 6400.0, "fallback"
 
 
+def host_info() -> dict:
+    model = platform.processor() or ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
 # FP64 peak of one B300 from its unit counts and clock: 148 SMs x 4 FP64 flop/clk (2 DFMA) x
 # 2.032 GHz (1.25 TFLOP/s nominal at the boost clock; 1.11 measured by an FMA loop at 2032 MHz).
 FP64_PEAK_TFLOPS = 148 * 4 * 2.032e9 / 1e12
@@ -186,17 +285,29 @@ def cpu_oracle_sample(envs, states, params, n_threads):
     """Time the oracle on n_threads envs x 1 step from the given states (bounded CPU sample)."""
     from oracle import oracle as O
 
-    sel = list(range(min(n_threads, len(envs))))
     oe = []
-    for i in sel:
-        o = O.OracleEnv(params, envs[i])
-        x, v, step = states[i]
+    for env, (x, v, step) in zip(envs, states):
+        o = O.OracleEnv(params, env)
         o.set_state(x, v, step)
         oe.append(o)
     t0 = time.perf_counter()
-    O.run_batch(oe, 1, len(oe))
+    O.run_batch(oe, 1, n_threads)
     dt = time.perf_counter() - t0
     return len(oe) / dt, len(oe), dt
+
+
+def timed_steps(sc, stream, k):
+    """Device time (ms) of one ipc_step(k) call: CUDA events on the scene's stream."""
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sc.step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
 
 
 def run_ours(args):
@@ -205,6 +316,9 @@ def run_ours(args):
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
+    wl = Workload(args.workload)
+    ids_global = shard_env_ids(rank, world, args.envs, wl.cost)
+    envs = make_envs(wl, ids_global)  # before the first CUDA call
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -213,15 +327,14 @@ def run_ours(args):
     from paper_2503_05020_b300 import ipc
 
     params = S.scene_params(DT)
-    envs = make_envs(rank, args.envs)
     stream = torch.cuda.Stream()  # a non-default stream: the library's kernels and the timing events share it
     torch.cuda.set_stream(stream)
     prec = ipc.MIXED if args.precision == "mixed" else ipc.FP64
     sc = ipc.Scene(params, precision=prec, device=local, stream=stream.cuda_stream, pcg_cluster=args.pcg_cluster)
     ids = [sc.add_env(e) for e in envs]
     for eid, env in zip(ids, envs):
-        x, v = S.pad_grasp_state_at(env, START_STEP)
-        sc.set_state(eid, x, v, START_STEP)
+        x, v = wl.state_at(env, wl.start)
+        sc.set_state(eid, x, v, wl.start)
     sc.step(args.warmup)
     snap = [(sc.dofs(e), sc.velocities(e), sc.status(e)["step"]) for e in ids]
     p_start = [sc.points(e) for e in ids]
@@ -236,26 +349,23 @@ def run_ours(args):
     clocks = ClockSampler(local)
     sc.profile(True)
     l0 = sc.launch_count()
+    st0 = [sc.status(e)["steps"] for e in ids]
     torch.cuda.synchronize()
     barrier()
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sc.step(args.steps)  # one call: every env runs its K steps at its own pace
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms = timed_steps(sc, stream, args.steps)  # one call: every env runs its K steps at its own pace
     barrier()
     clk = clocks.stop()
     launches = sc.launch_count() - l0
-    ms = e0.elapsed_time(e1)
     prof = sc.profile_read()
     sc.profile(False)
-    steps_done = sum(sc.status(e)["steps"] for e in ids)
-    failed = sum(sc.status(e)["status"] == "FAILED" for e in ids)
+    stats = [sc.status(e) for e in ids]
+    steps_done = sum(s["steps"] for s in stats) - sum(st0)
+    failed = sum(s["status"] == "FAILED" for s in stats)
     x_end = [sc.points(e) for e in ids]
     t_max = max_over_ranks(ms, world, "cuda")
-    value = job_throughput(world, args.envs, args.steps, t_max / 1000.0)
+    all_steps = sum_over_ranks(steps_done, world, "cuda")
+    value = job_throughput(all_steps, t_max / 1000.0)
 
     # ---- end to end through the public API with host buffers: per step, the next kinematic
     # targets of every env go host -> device and the DOFs of every env come back.
@@ -278,11 +388,21 @@ def run_ours(args):
         sc.all_dofs(h_out)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
-    e2e_value = job_throughput(world, args.envs, args.steps, e2e_s)
+    e2e_value = job_throughput(all_steps, e2e_s)
+    counters = sc.scene_counters(ids[0])
+    newton = sum(s["newton_iters"] for s in stats)
+    pcg_its = sum(s["pcg_iters"] for s in stats)
+    sc.close()
+    del sc
 
-    mixed = None
+    tets = [sum(len(s["tets"]) for s in e["soft"]) for e in envs]
+    plain = mixed = None
+    if world == 1 and args.plain_envs > 0:
+        plain = plain_leg(args, params, envs, snap, tets, stream, local, value)
     if world == 1 and args.precision == "fp64" and not args.no_mixed_leg:
-        mixed = mixed_leg(args, params, envs, snap, p_start, x_end, stream, local, t_max / args.steps)
+        mixed = mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, local, t_max / args.steps)
+        if plain:
+            plain["mixed_batched_over_plain"] = round(mixed["value"] / plain["value"], 2)
 
     if rank != 0:
         if world > 1:
@@ -294,32 +414,32 @@ def run_ours(args):
     # ---- roofline of the dominant kernel: the persistent per-env PCG when it runs, else the
     # tiled SpMV. Its bound is the roof its arithmetic intensity reaches first: FP64 arithmetic
     # (B300 runs FP64 at 1/58 of FP32) or HBM bandwidth.
-    fam = max(prof, key=lambda k: prof[k]["ms"])
     roof = roofline(prof, args.precision)
-    tets = int(np.mean([sum(len(s["tets"]) for s in e["soft"]) for e in envs]))
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        threads = min(os.cpu_count() or 1, 8)
-        v_cpu, n_cpu, dt_cpu = cpu_oracle_sample(envs, snap, params, threads)
-        cpu = {"value": round(v_cpu, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{n_cpu} envs x 1 step from the timed region's start state, one env per thread, "
-                         f"{dt_cpu:.1f} s wall"}
+        threads = min(os.cpu_count() or 1, 64)
+        sel = cpu_sample(tets, threads)
+        v_cpu, n_cpu, dt_cpu = cpu_oracle_sample([envs[i] for i in sel], [snap[i] for i in sel], params, threads)
+        cpu = {"value": round(v_cpu, 4), "unit": UNIT, "cores": min(threads, n_cpu), "kind": "oracle",
+               "sample": f"{n_cpu} envs at evenly spaced size quantiles among the envs of at most "
+                         f"{CPU_SAMPLE_MAX_TETS} tets (tets {min(tets[i] for i in sel)}-{max(tets[i] for i in sel)}; "
+                         f"the batch's envs average {int(np.mean(tets))}), 1 step each from the timed region's start "
+                         f"state, one env per thread, {dt_cpu:.1f} s wall", **host_info()}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
-        "data": "synthetic", "config": workload_config(args.envs, tets, START_STEP),
+        "data": "synthetic", "config": wl.config(len(envs), int(np.mean(tets)), world),
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h_tg.nbytes),
                 "d2h_bytes_per_step": int(h_out.nbytes)},
-        "gpu_launches": int(launches), "clocks": clk, "mixed_precision": mixed, "serving": None,
+        "gpu_launches": int(launches), "clocks": clk, "plain_fp64": plain, "mixed_precision": mixed, "serving": None,
         "env_steps_done": int(steps_done), "envs_failed": int(failed),
         "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k != "pcg_flops"},
-        "counters_last_iteration": sc.scene_counters(ids[0]),
-        "newton_iters_per_env_step": round(sum(sc.status(e)["newton_iters"] for e in ids) / max(steps_done, 1), 2),
-        "pcg_iters_per_newton": round(sum(sc.status(e)["pcg_iters"] for e in ids)
-                                      / max(sum(sc.status(e)["newton_iters"] for e in ids), 1), 1),
+        "counters_last_iteration": counters,
+        "newton_iters_per_env_step": round(newton / max(sum(s["steps"] for s in stats), 1), 2),
+        "pcg_iters_per_newton": round(pcg_its / max(newton, 1), 1),
     }
     if world == 1 and args.serve_requests > 0:
         line["serving"] = serving_leg(args, params, local)
@@ -330,51 +450,117 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def mixed_leg(args, params, envs, snap, p_start, x_end, stream, device, ms_fp64):
-    """The same K timed steps from the same state with FP32 Hessians and PCG (FP64 energies,
-    gradients, barrier, CCD and line search): throughput, speedup over the FP64 run, and the
-    largest difference of a point's world position from the FP64 run (all points, and the
-    grasped objects' points) relative to the largest FP64 point displacement of the run."""
-    import torch
+def plain_leg(args, params, envs, snap, tets, stream, device, batched_value):
+    """The plain FP64 GPU stepper: the same kernels, one env at a time (its own scene, automatic
+    PCG shape, which for a single env has one candidate and is never tuned), on a sample of the
+    envs at evenly spaced size quantiles, each from the timed region's start state for the same
+    K steps. Also the paper's comparison (Sec. IV-A): the sample's envs batched in one scene over
+    the same envs run one after another."""
+    from paper_2503_05020_b300 import ipc
 
+    sel = stratified(tets, args.plain_envs)
+    seq_ms, steps = 0.0, 0
+    for i in sel:
+        sc = ipc.Scene(params, precision=ipc.FP64, device=device, stream=stream.cuda_stream)
+        eid = sc.add_env(envs[i])
+        x, v, st = snap[i]
+        sc.set_state(eid, x, v, st)
+        sc.step(0)  # layout outside the timed call
+        s0 = sc.status(eid)["steps"]
+        seq_ms += timed_steps(sc, stream, args.steps)
+        steps += sc.status(eid)["steps"] - s0
+        sc.close()
+    value = steps / (seq_ms / 1000.0)
+    sc = ipc.Scene(params, precision=ipc.FP64, device=device, stream=stream.cuda_stream)
+    ids = [sc.add_env(envs[i]) for i in sel]
+    for eid, i in zip(ids, sel):
+        x, v, st = snap[i]
+        sc.set_state(eid, x, v, st)
+    sc.step(0)
+    s0 = sum(sc.status(e)["steps"] for e in ids)
+    b_ms = timed_steps(sc, stream, args.steps)
+    b_steps = sum(sc.status(e)["steps"] for e in ids) - s0
+    sc.close()
+    return {"value": round(value, 2), "unit": UNIT, "envs": len(sel),
+            "sample": f"{len(sel)} envs at evenly spaced size quantiles (tets {min(tets[i] for i in sel)}-"
+                      f"{max(tets[i] for i in sel)}), {args.steps} steps each from the timed region's start state",
+            "batched_over_plain": round(batched_value / value, 2),
+            "paper_style_ratio": {"n_envs": len(sel), "batched_ms": round(b_ms, 1), "sequential_ms": round(seq_ms, 1),
+                                  "ratio": round((b_steps / b_ms) / (steps / seq_ms), 2),
+                                  "paper": "16x (512 envs, LEAP hand), 40x / 48x (400 envs, UMI gripper); "
+                                           "1x H100, FP64 (Sec. I, IV-A)"}}
+
+
+def mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, device, ms_fp64):
+    """The same K timed steps from the same state with FP32 Hessians and PCG (FP64 energies,
+    gradients, barrier, CCD and line search): throughput and speedup over the FP64 run. Accuracy:
+    the largest difference of a point's world position from the FP64 run (all points, and the
+    grasped objects' points) relative to the largest FP64 point displacement of the run; and on
+    a sample of envs, both precisions against a converged FP64 solve of the same steps (PCG to
+    1e-10, Newton tolerance x1e-2)."""
     from paper_2503_05020_b300 import ipc
 
     sc = ipc.Scene(params, precision=ipc.MIXED, device=device, stream=stream.cuda_stream,
                    pcg_cluster=args.pcg_cluster)
     ids = [sc.add_env(e) for e in envs]
-    for eid, env in zip(ids, envs):
-        x, v = S.pad_grasp_state_at(env, START_STEP)
-        sc.set_state(eid, x, v, START_STEP)
-    sc.step(args.warmup)
+    for eid, (x, v, st) in zip(ids, snap):
+        sc.set_state(eid, x, v, st)
+    sc.step(1)  # warm-up (tuner, first-call costs), then back to the snapshot
     for eid, (x, v, st) in zip(ids, snap):
         sc.set_state(eid, x, v, st)
     sc.profile(True)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sc.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    s0 = sum(sc.status(e)["steps"] for e in ids)
+    ms = timed_steps(sc, stream, args.steps)
     prof = sc.profile_read()
     sc.profile(False)
-    # world positions of every point (soft vertices, then the object's vertices)
-    diff = max(float(np.abs(sc.points(e) - x).max()) for e, x in zip(ids, x_end))
-    disp = max(float(np.abs(x - x0).max()) for x, x0 in zip(x_end, p_start))
-    obj_diff = 0.0
-    for e, x, env in zip(ids, x_end, envs):
-        o = sum(len(s["verts"]) for s in env["soft"])
-        obj_diff = max(obj_diff, float(np.abs(sc.points(e)[o:] - x[o:]).max()))
+    steps = sum(sc.status(e)["steps"] for e in ids) - s0
+    x_mixed = [sc.points(e) for e in ids]
     failed = sum(sc.status(e)["status"] == "FAILED" for e in ids)
-    value = args.envs * args.steps / (ms / 1000.0)
-    return {"value": round(value, 2), "unit": UNIT, "ms_per_step": round(ms / args.steps, 3),
-            "speedup_vs_fp64": round((ms_fp64 * args.steps) / ms, 3), "max_displacement_diff_m": diff,
-            "rel_displacement_diff": diff / disp if disp > 0 else None,
-            "rel_object_displacement_diff": obj_diff / disp if disp > 0 else None, "envs_failed": int(failed),
-            "dtype": "f32 Hessians + PCG, f64 energies/gradients/barrier/CCD/line search",
-            "roofline": roofline(prof, "mixed"),
-            "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k != "pcg_flops"}}
+    sc.close()
+
+    def errors(xa, xb, rows):
+        disp = max(float(np.abs(xb[i] - p_start[i]).max()) for i in rows)
+        d_all = max(float(np.abs(xa[i] - xb[i]).max()) for i in rows)
+        d_obj = 0.0
+        for i in rows:
+            o = object_points(envs[i])
+            d_obj = max(d_obj, float(np.abs(xa[i][o] - xb[i][o]).max()))
+        return {"max_diff_m": d_all, "rel_all_points": d_all / disp if disp > 0 else None,
+                "rel_object_points": d_obj / disp if disp > 0 else None, "max_displacement_m": disp}
+
+    rows = list(range(len(envs)))
+    out = {"value": round(steps / (ms / 1000.0), 2), "unit": UNIT, "ms_per_step": round(ms / args.steps, 3),
+           "speedup_vs_fp64": round((ms_fp64 * args.steps) / ms, 3), "envs_failed": int(failed),
+           "vs_fp64": errors(x_mixed, x_end, rows),
+           "dtype": "f32 Hessians + PCG, f64 energies/gradients/barrier/CCD/line search",
+           "roofline": roofline(prof, "mixed"),
+           "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k != "pcg_flops"}}
+    if args.ref_envs > 0:
+        sel = stratified(tets, args.ref_envs)
+        pr = dict(params, pcg_rel_tol=1e-10, newton_tol=params["newton_tol"] * 1e-2, max_pcg=20000)
+        sc = ipc.Scene(pr, precision=ipc.FP64, device=device, stream=stream.cuda_stream)
+        rid = [sc.add_env(envs[i]) for i in sel]
+        for eid, i in zip(rid, sel):
+            x, v, st = snap[i]
+            sc.set_state(eid, x, v, st)
+        sc.step(args.steps)
+        x_ref = {i: sc.points(e) for e, i in zip(rid, sel)}
+        sc.close()
+        xr = [x_ref.get(i) for i in rows]
+        out["vs_converged_fp64"] = {"envs": len(sel), "mixed": errors(x_mixed, xr, sel),
+                                    "fp64": errors(x_end, xr, sel)}
+    return out
+
+
+def object_points(env):
+    """Indices of the grasped object's points among an env's points (soft vertices in body order,
+    then the affine bodies' rest vertices)."""
+    kind, k = env.get("object", ("soft", len(env["soft"]) - 1))
+    if kind == "soft":
+        o = sum(len(s["verts"]) for s in env["soft"][:k])
+        return np.arange(o, o + len(env["soft"][k]["verts"]))
+    o = sum(len(s["verts"]) for s in env["soft"]) + sum(len(a["verts"]) for a in env["affine"][:k])
+    return np.arange(o, o + len(env["affine"][k]["verts"]))
 
 
 def serving_leg(args, params, device):
@@ -409,14 +595,20 @@ def run_reference(args):
         return
     from oracle import oracle as O
 
+    wl = Workload(args.workload)
     params = S.scene_params(DT)
-    threads = min(os.cpu_count() or 1, 8)
-    envs = make_envs(0, threads)
+    threads = min(os.cpu_count() or 1, 64)
+    # the workload's config is the GPU arm's (all its envs); the timed sample is one env per core
+    # at evenly spaced size quantiles among the batch's small envs
+    all_envs = make_envs(wl, list(range(args.envs)))
+    all_tets = [sum(len(s["tets"]) for s in e["soft"]) for e in all_envs]
+    sel = cpu_sample(all_tets, threads)
+    envs = [all_envs[i] for i in sel]
     oe = []
     for env in envs:
         o = O.OracleEnv(params, env)
-        x, v = S.pad_grasp_state_at(env, START_STEP)
-        o.set_state(x, v, START_STEP)
+        x, v = wl.state_at(env, wl.start)
+        o.set_state(x, v, wl.start)
         oe.append(o)
     t_start = time.perf_counter()
     for _ in range(min(args.warmup, 1)):
@@ -430,15 +622,16 @@ def run_reference(args):
         t_timed += time.perf_counter() - t0
         done += 1
     value = len(oe) * done / t_timed
-    # the workload's config is the GPU arm's (all its envs); the timed sample is its first envs
-    tets = int(np.mean([sum(len(s["tets"]) for s in e["soft"]) for e in make_envs(0, args.envs)]))
+    tets = [sum(len(s["tets"]) for s in e["soft"]) for e in envs]
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": 0, "steps": done,
             "warmup": min(args.warmup, 1), "ms_per_step": round(1000 * t_timed / max(done, 1), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.envs, tets, START_STEP), "impl": "reference",
-            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{len(oe)} of the {args.envs} envs, {done} of {args.steps} steps "
-                                       f"(budget {args.cpu_budget:.0f} s), one env per thread"},
+            "data": "synthetic", "config": wl.config(args.envs, int(np.mean(all_tets)), 1), "impl": "reference",
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": min(threads, len(oe)), "kind": "oracle",
+                             "sample": f"{len(oe)} of the {args.envs} envs at evenly spaced size quantiles among the "
+                                       f"envs of at most {CPU_SAMPLE_MAX_TETS} tets (tets {min(tets)}-{max(tets)}; the "
+                                       f"batch's envs average {int(np.mean(all_tets))}), {done} of {args.steps} steps "
+                                       f"(budget {args.cpu_budget:.0f} s), one env per thread", **host_info()},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

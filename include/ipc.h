@@ -80,9 +80,8 @@ typedef struct {
   int32_t kappa_adapt;   /* 0: the barrier stiffness is kappa throughout (Sec. III-D). 1: adapted
                             per env: at each step start the least-squares balance of the barrier
                             gradient against the other terms' gradient over the free DOFs,
-                            -(g_E . G) / (G . G), clamped to [kappa, 1000 kappa]; inside a step
-                            doubled (up to 1000 kappa) at an iterate whose closest contact is
-                            nearer than 1e-2 dhat and nearer than at the previous iterate */
+                            -(g_E . G) / (G . G), clamped to [kappa, 1000 kappa], and held for
+                            the rest of the step */
   void* cuda_stream;     /* cudaStream_t to borrow, or NULL for a library-owned stream */
 } ipc_scene_desc;
 
@@ -114,6 +113,18 @@ typedef struct {
                           (rigid links of a hand following joint targets); 0 = none */
 } ipc_affine_body_desc;
 
+/* Point joint between two affine bodies of one environment (Sec. I: IPC coupled with affine body
+ * dynamics for articulated multibodies). The anchor of body a and the anchor of body b (each in
+ * its body's rest frame, x = p + A xbar) are held together by the potential 1/2 k |x_a - x_b|^2
+ * (k in N/m, scaled by h^2 like every potential of the incremental potential). Two joints
+ * between the same bodies on one axis make a hinge. */
+typedef struct {
+  int32_t body_a, body_b; /* indices among the env's affine bodies; distinct */
+  double anchor_a[3];     /* rest-frame anchor on body a (m) */
+  double anchor_b[3];     /* rest-frame anchor on body b (m) */
+  double stiffness;       /* k > 0 (N/m) */
+} ipc_joint_desc;
+
 /* One environment. gravity_on: n_steps bytes, the gravity of step s: 0 none, 1 the scene's
  * gravity vector, 2..7 its magnitude along +x, -x, +y, -y, +z, -z (the axis-aligned phases of the
  * grasp evaluation protocol, Sec. III-D); other values are rejected (IPC_ERR_ARG).
@@ -127,6 +138,8 @@ typedef struct {
   double friction_mu;
   const uint8_t* gravity_on;
   const double* targets;
+  int32_t n_joints, pad2;       /* point joints of the env (0: none) */
+  const ipc_joint_desc* joints; /* n_joints entries (may be NULL when n_joints = 0) */
 } ipc_env_desc;
 
 typedef enum {
@@ -142,7 +155,8 @@ typedef enum {
   IPC_Q_CONTACTS = 5,    /* int32[n][4]: (kind, i, j, distance type) of candidates closer than
                             dhat, sorted like CANDIDATES */
   IPC_Q_POINTS = 6,      /* double[n_points][3]: world positions of all surface-capable points
-                            (soft vertices, then affine rest vertices mapped by q) */
+                            (soft vertices, then affine rest vertices mapped by q; joint anchors
+                            are not among them) */
   IPC_Q_SIZES = 7,       /* int64[8]: ndof, points, surface vertices, edges, triangles, tets,
                             bodies, steps */
   IPC_Q_INTERSECTIONS = 8, /* int64[2]: segment-triangle intersections, inverted tets */
@@ -233,21 +247,29 @@ ipc_status ipc_env_estimate_bytes(const ipc_env_desc* env, int32_t precision, ui
 /* Allocation-free Neo-Hookean energy (the paper has no counterpart; this is a deployment
  * convenience). For callers that cannot call cudaMalloc: real-time control loops where an
  * allocation's latency or failure is not acceptable, or hosts whose memory manager owns every
- * device allocation and forbids others. It computes, for each
- * group g of tets [group_offsets[g], group_offsets[g+1]), h2 * sum V Psi(F) over the group with
- * the same per-tet energy code and the same fixed-order reduction as the scene path, and sets
- * inverted[g] = 1 when a tet of the group has J <= 0 (its energy then counts as 0).
- * All pointers are DEVICE pointers on the current device, owned by the caller:
+ * device allocation and forbids others. It computes, for each group g of tets
+ * [group_offsets[g], group_offsets[g+1]), h2 * sum V Psi(F) over the group with the same per-tet
+ * energy code and the same fixed-order reduction as the scene path, and sets inverted[g] = 1 when
+ * a tet of the group has J <= 0 (its energy then counts as 0).
+ * All pointers are DEVICE pointers on the current device, owned by the caller, each aligned to
+ * its element type (4 bytes for int32, 8 for double; IPC_ERR_ARG otherwise):
  *   tets: n_tets*4 int32 node indices into x; tet_params: n_tets*12 doubles per tet (row-major
  *   Dm^-1, rest volume, mu, lambda); x: node positions (3 doubles each); group_offsets:
- *   n_groups+1 int32 (ascending); energy: n_groups doubles (written); inverted: n_groups int32
- *   (written). stream: cudaStream_t or NULL for the legacy default stream.
+ *   n_groups+1 int32, non-decreasing, with group_offsets[0] = 0 and group_offsets[n_groups] =
+ *   n_tets; energy: n_groups doubles (written); inverted: n_groups int32 (written).
+ *   stream: cudaStream_t or NULL for the legacy default stream.
+ * The offsets are device data and are not read back: the kernels clamp each one to [0, n_tets],
+ * so every access stays in bounds whatever they hold, and tets outside [group_offsets[0],
+ * group_offsets[n_groups]) belong to no group (neither summed nor flagged); offsets that break
+ * the rules above give unspecified sums. Node indices must lie inside x.
  * Scratch lives in a file-scope device array of IPC_NOALLOC_MAX_TETS doubles (2 MiB), held by
  * every device that loads the library until the process exits. Calls with n_tets above that
  * maximum, or more than IPC_NOALLOC_MAX_GROUPS groups, return IPC_ERR_ARG. The first call on a
- * device looks the array up (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture. All calls share the array: calls that overlap on the GPU
- * (different streams, or different host threads) race on it. The call enqueues its work and
+ * device looks the array up (cudaGetSymbolAddress, with that device current) and keeps its
+ * address for the life of the process; make that first call before any stream capture, and do
+ * not call this entry point on a device after cudaDeviceReset (or any other destruction of its
+ * primary context) in the same process. All calls share the array: calls that overlap on the
+ * GPU (different streams, or different host threads) race on it. The call enqueues its work and
  * returns without synchronising; it performs no allocation of any kind. */
 #define IPC_NOALLOC_MAX_TETS 262144
 #define IPC_NOALLOC_MAX_GROUPS 65536

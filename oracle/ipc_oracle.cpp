@@ -19,9 +19,10 @@
 // Broad phase is all pairs. Built with -ffp-contract=off so that every expression rounds as
 // written.
 //
-// Parity unpinned: the in-step doubling of the adapted barrier stiffness (step_once; the
-// paper gives no rule, so its trigger and factor are a reading). Its bounds and the stepping
-// invariants are tested; no closed form fixes the values it produces.
+// Every function here is pinned by a test against closed forms, invariants, brute force or a
+// library routine (tests/test_oracle_*.py). The adapted barrier stiffness (an option; the paper
+// fixes kappa) is set once per step by a least-squares force balance that a resting body pins
+// in closed form; it is not changed inside a step.
 #include <algorithm>
 #include <array>
 #include <atomic>
@@ -484,6 +485,14 @@ struct AffineDesc {
   double qdot0[12];
   double pd_stiffness;  // k_pd (1/s^2); 0: no PD target potential
 };
+// A point joint between two affine bodies: the anchor of body a (its rest-frame coordinates) and
+// the anchor of body b are held together by the potential 1/2 k |x_a - x_b|^2 (k in N/m). Two
+// such joints on one axis make a hinge.
+struct JointDesc {
+  int32_t body_a, body_b;  // affine body indices of the env
+  double anchor_a[3], anchor_b[3];
+  double stiffness;
+};
 struct EnvDesc {
   int32_t n_soft, n_affine, n_steps, pad;
   const SoftDesc* soft;
@@ -491,6 +500,8 @@ struct EnvDesc {
   double mu;
   const uint8_t* gravity;
   const double* targets;
+  int32_t n_joints, pad2;
+  const JointDesc* joints;
 };
 
 enum { ST_ACTIVE = 0, ST_DONE = 1, ST_FAILED = 2 };
@@ -512,6 +523,11 @@ struct Body {
   double M4[16];
   double vol;
   double lo[3], hi[3];
+};
+struct Joint {
+  int a, b;  // affine body indices
+  double xa[3], xb[3];
+  double k;
 };
 struct Contact {
   int kind;
@@ -538,6 +554,7 @@ struct Env {
   std::vector<std::array<double, 9>> Dminv;
   std::vector<double> tvol, tmu, tlam;
   std::vector<Body> bodies;
+  std::vector<Joint> joints;
   std::vector<Point> pts;
   std::vector<int> sv;
   std::vector<std::array<int, 2>> edges;
@@ -551,7 +568,6 @@ struct Env {
   std::vector<FrictionContact> fric;
   std::vector<double> ptx_t;  // point positions at step start
   double kappa = 0.0;            // barrier stiffness of the current step (P.kappa unless adapted)
-  double prev_dmin2 = INFINITY;  // smallest squared contact distance at the previous iterate
   // per-iteration trace (optional)
   int trace = 0;
   std::vector<double> trace_E;
@@ -707,6 +723,15 @@ static Env* build_env(const Params& P, const EnvDesc& D) {
       e->v[B.dof + k] = A.qdot0[k];
     }
     e->bodies.push_back(B);
+  }
+  for (int j = 0; j < D.n_joints; ++j) {
+    const JointDesc& J = D.joints[j];
+    Joint jt;
+    jt.a = J.body_a;
+    jt.b = J.body_b;
+    for (int k = 0; k < 3; ++k) { jt.xa[k] = J.anchor_a[k]; jt.xb[k] = J.anchor_b[k]; }
+    jt.k = J.stiffness;
+    e->joints.push_back(jt);
   }
   // points: all soft vertices, then every affine rest vertex
   voff = 0;
@@ -905,7 +930,7 @@ static bool is_kin_dof(const Env& e, int d) {
 static double evaluate(Env& e, const std::vector<double>& q, const std::vector<Contact>& C, int want,
                        std::vector<double>* grad, Triplets* H) {
   const double h = e.P.dt, h2 = h * h;
-  double Einert = 0, Eelas = 0, Ebar = 0, Efric = 0, Eorth = 0, Epd = 0;
+  double Einert = 0, Eelas = 0, Ebar = 0, Efric = 0, Eorth = 0, Epd = 0, Ejoint = 0;
   if (grad) grad->assign(e.ndof, 0.0);
   // inertia of free soft vertices
   for (int i = 0; i < e.n_soft_verts; ++i) {
@@ -1017,6 +1042,40 @@ static double evaluate(Env& e, const std::vector<double>& q, const std::vector<C
         for (int b = 0; b < 9; ++b) H->add(qidx(a), qidx(b), w * HA[9 * a + b]);
     }
   }
+  // joints: 1/2 h^2 k |x_a - x_b|^2 with x = p + A xbar for each anchor. With the weights
+  // w = (1, xbar) of the blocks (p, a1, a2, a3) of q, x = sum_r w_r q_r, so the gradient on block
+  // r of body a is h^2 k w_r (x_a - x_b) and the Hessian block (r, s) is h^2 k w_r w_s I3 (with a
+  // minus sign between the two bodies): PSD as it stands, not projected.
+  for (const Joint& J : e.joints) {
+    const Body& Ba = e.bodies[J.a];
+    const Body& Bb = e.bodies[J.b];
+    const double wa[4] = {1.0, J.xa[0], J.xa[1], J.xa[2]}, wb[4] = {1.0, J.xb[0], J.xb[1], J.xb[2]};
+    double r[3];
+    for (int k = 0; k < 3; ++k) {
+      double xa = 0.0, xb = 0.0;
+      for (int m = 0; m < 4; ++m) {
+        xa += wa[m] * q[Ba.dof + 3 * m + k];
+        xb += wb[m] * q[Bb.dof + 3 * m + k];
+      }
+      r[k] = xa - xb;
+    }
+    const double c = h2 * J.k;
+    Ejoint += 0.5 * c * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    const int dofs[2] = {Ba.dof, Bb.dof};
+    const double* ws[2] = {wa, wb};
+    const double sg[2] = {1.0, -1.0};
+    if (want >= 1)
+      for (int side = 0; side < 2; ++side)
+        for (int m = 0; m < 4; ++m)
+          for (int k = 0; k < 3; ++k) (*grad)[dofs[side] + 3 * m + k] += sg[side] * c * ws[side][m] * r[k];
+    if (want >= 2)
+      for (int s1 = 0; s1 < 2; ++s1)
+        for (int s2 = 0; s2 < 2; ++s2)
+          for (int m = 0; m < 4; ++m)
+            for (int n = 0; n < 4; ++n)
+              for (int k = 0; k < 3; ++k)
+                H->add(dofs[s1] + 3 * m + k, dofs[s2] + 3 * n + k, sg[s1] * sg[s2] * c * ws[s1][m] * ws[s2][n]);
+  }
   // contacts: barrier
   std::vector<double> px;
   point_positions(e, q.data(), px);
@@ -1081,7 +1140,7 @@ static double evaluate(Env& e, const std::vector<double>& q, const std::vector<C
           for (int l = 0; l < 3; ++l) H12[(3 * i + k) * 12 + 3 * j + l] = f.c[i] * f.c[j] * M[3 * k + l];
     scatter(f.pts, g12, H12, s);
   }
-  return Einert + Eelas + Eorth + Epd + Ebar + Efric;
+  return Einert + Eelas + Eorth + Epd + Ejoint + Ebar + Efric;
 }
 
 // ---------------------------------------------------------------- step pieces
@@ -1105,24 +1164,12 @@ static void target_dofs(const Env& e, std::vector<double>& tgt) {
       for (int k = 0; k < 12; ++k) tgt[B.dof + k] = T[12 * B.handle + k];
 }
 
-// smallest squared distance over a contact set at point positions px (INFINITY when empty)
-static double min_contact_d2(const std::vector<double>& px, const std::vector<Contact>& C) {
-  double m = INFINITY;
-  for (const Contact& c : C) {
-    double x12[12];
-    gather12(px, c.pts, x12);
-    m = std::min(m, pair_dist2(c.kind, x12));
-  }
-  return m;
-}
-
 // Barrier stiffness at the start of a step (reading of the adapted-stiffness rule): with g_E the
 // gradient of every other term of the incremental potential at x^t and G the gradient of the
 // barrier term per unit stiffness, the kappa that minimises |g_E + kappa G| over the free DOFs,
 // -(g_E . G) / (G . G), clamped to [kappa, 1000 kappa] of the scene; the scene's kappa when no
 // pair is within dhat. Also records the smallest contact distance at x^t.
 static void kappa_start(Env& e, const std::vector<Contact>& C) {
-  e.prev_dmin2 = min_contact_d2(e.ptx_t, C);
   if (C.empty()) return;
   std::vector<double> g0(e.ndof, 0.0), g1(e.ndof, 0.0);
   e.kappa = 0.0;
@@ -1350,13 +1397,6 @@ static void step_once(Env& e) {
   for (int it = 0; it < e.P.max_newton; ++it) {
     point_positions(e, e.x.data(), px);
     constraint_set(e, px, C);
-    if (e.P.kappa_adapt && it > 0) {
-      // inside a step the stiffness doubles (up to 1000 times the scene's) while the smallest
-      // contact distance is below 1e-2 dhat and still shrinking from one iterate to the next
-      const double m = min_contact_d2(px, C), lim = 1e-2 * e.P.dhat;
-      if (m < lim * lim && m < e.prev_dmin2) e.kappa = std::min(2.0 * e.kappa, 1000.0 * e.P.kappa);
-      e.prev_dmin2 = m;
-    }
     Triplets T;
     double E0 = evaluate(e, e.x, C, 2, &grad, &T);
     if (!std::isfinite(E0)) { e.status = ST_FAILED; e.reason = FAIL_NAN; return; }

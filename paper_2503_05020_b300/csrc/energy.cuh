@@ -623,6 +623,45 @@ __global__ void k_friction(int n_fr, const FrictionRec* __restrict__ fr, const u
       sH[78 * (long)k + up_idx(i, j, 12)] = HT(s * f.c[i / 3] * f.c[j / 3] * M[3 * (i % 3) + (j % 3)]);
 }
 
+// ----------------------------------------------------------------- joints
+// A point joint between two affine bodies: its two anchors are points of the point table (on
+// their bodies, not on any surface). As a stencil its points are (a, b, a, b) with the last two
+// carrying nothing.
+struct JointRec {
+  int pts[2];
+  int env, pad;
+  double k;  // stiffness (N/m)
+};
+// 1/2 h^2 k |x_a - x_b|^2: gradient h^2 k (r, -r) on the two anchors, Hessian h^2 k [I, -I; -I, I]
+// (PSD as it stands).
+template <int MODE, class HT = double>
+__global__ void k_joint(int n_jt, const JointRec* __restrict__ jt, const uint8_t* __restrict__ act,
+                        const double* __restrict__ ptx, double h2, double* __restrict__ sE, double* __restrict__ sg,
+                        HT* __restrict__ sH) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_jt) return;
+  const JointRec J = jt[k];
+  if (!act[J.env]) return;
+  const d3 xa = ld3(ptx, J.pts[0]), xb = ld3(ptx, J.pts[1]);
+  const double r[3] = {xa.x - xb.x, xa.y - xb.y, xa.z - xb.z};
+  const double c = h2 * J.k;
+  sE[k] = 0.5 * c * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  if (MODE == MODE_ENERGY) return;
+  for (int i = 0; i < 3; ++i) {
+    sg[12 * (long)k + i] = c * r[i];
+    sg[12 * (long)k + 3 + i] = -c * r[i];
+    sg[12 * (long)k + 6 + i] = 0.0;
+    sg[12 * (long)k + 9 + i] = 0.0;
+  }
+  if (MODE == MODE_GRAD) return;
+  for (int i = 0; i < 12; ++i)
+    for (int j = i; j < 12; ++j) {
+      double v = 0.0;
+      if (i < 6 && j < 6 && (i % 3) == (j % 3)) v = (i / 3 == j / 3) ? c : -c;
+      sH[78 * (long)k + up_idx(i, j, 12)] = HT(v);
+    }
+}
+
 // ----------------------------------------------------------------- per-env energy sums
 // One block per env; every sub-range is summed by a fixed-order tree. Dynamic lists (contacts,
 // friction) are env-sorted; their env ranges are found by binary search.
@@ -638,7 +677,7 @@ struct EnergyLists {
   const double* nodeE; const int* node_off;     // soft-node inertia per node
   const double* tetE; const int* tet_off;
   const double* bodyE; const int* body_off;
-  const double* stE; const int* st_env; int n_pt, n_ee, n_frpt, n_fr;  // stencils: [pt|ee|frpt|free]
+  const double* stE; const int* st_env; int n_pt, n_ee, n_frpt, n_fr, n_jt;  // stencils: [pt|ee|frpt|free|joints]
 };
 __global__ void k_env_energy(int n_env, EnergyLists L, const uint8_t* __restrict__ act, double* __restrict__ out) {
   __shared__ double sh[256];
@@ -653,8 +692,9 @@ __global__ void k_env_energy(int n_env, EnergyLists L, const uint8_t* __restrict
   acc += range_sum(L.nodeE, L.node_off[e], L.node_off[e + 1]);
   acc += range_sum(L.tetE, L.tet_off[e], L.tet_off[e + 1]);
   acc += range_sum(L.bodyE, L.body_off[e], L.body_off[e + 1]);
-  int bounds[5] = {0, L.n_pt, L.n_pt + L.n_ee, L.n_pt + L.n_ee + L.n_frpt, L.n_pt + L.n_ee + L.n_fr};
-  for (int r = 0; r < 4; ++r) {
+  const int nc = L.n_pt + L.n_ee;
+  int bounds[6] = {0, L.n_pt, nc, nc + L.n_frpt, nc + L.n_fr, nc + L.n_fr + L.n_jt};
+  for (int r = 0; r < 5; ++r) {
     int b = lower_env(L.st_env, bounds[r], bounds[r + 1], e);
     int en = lower_env(L.st_env, bounds[r], bounds[r + 1], e + 1);
     acc += range_sum(L.stE, b, en);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -117,6 +118,13 @@ struct HostEnv {
   std::vector<uint8_t> pt_kin;
   std::vector<int> sv, edges, tris;  // point ids
   std::vector<double> edge_rest2;
+  // point joints: local anchor points (appended after the surface-capable points) and stiffness
+  struct Joint {
+    int pa, pb;
+    double k;
+  };
+  std::vector<Joint> joints;
+  int n_surf_pts = 0;  // points before the joint anchors
   // state
   std::vector<double> x, v;
   int step = 0, status = ST_ACTIVE, reason = FAIL_NONE;
@@ -387,6 +395,32 @@ void build_env(HostEnv& h, const ipc_env_desc* D) {
     }
     h.edge_rest2.push_back(s);
   }
+  // joint anchors: points on their bodies that belong to no surface (no contact)
+  h.n_surf_pts = (int)h.pt_node.size();
+  if (D->n_joints < 0 || (D->n_joints > 0 && !D->joints)) fail_with(IPC_ERR_ARG, "env: bad joint list");
+  for (int j = 0; j < D->n_joints; ++j) {
+    const ipc_joint_desc& J = D->joints[j];
+    if (J.body_a < 0 || J.body_a >= D->n_affine || J.body_b < 0 || J.body_b >= D->n_affine || J.body_a == J.body_b)
+      fail_with(IPC_ERR_ARG, "joint: bodies must be two distinct affine bodies of the env");
+    if (!(J.stiffness > 0.0) || !std::isfinite(J.stiffness)) fail_with(IPC_ERR_ARG, "joint: stiffness must be > 0");
+    HostEnv::Joint hj;
+    const int bodies[2] = {J.body_a, J.body_b};
+    const double* anchors[2] = {J.anchor_a, J.anchor_b};
+    for (int side = 0; side < 2; ++side) {
+      const int b = bodies[side];
+      (side == 0 ? hj.pa : hj.pb) = (int)h.pt_node.size();
+      h.pt_node.push_back(-1 - b);
+      for (int k = 0; k < 3; ++k) {
+        if (!std::isfinite(anchors[side][k])) fail_with(IPC_ERR_ARG, "joint: anchor not finite");
+        h.pt_xb.push_back(anchors[side][k]);
+        h.pt_rest.push_back(anchors[side][k]);
+      }
+      h.pt_body.push_back(b);
+      h.pt_kin.push_back(h.aff[b].kin ? 1 : 0);
+    }
+    hj.k = J.stiffness;
+    h.joints.push_back(hj);
+  }
 }
 
 }  // namespace
@@ -415,7 +449,7 @@ struct ipc_scene {
 
   // ---------------- layout sizes
   int E = 0, NN = 0, NB = 0, NT = 0, NP = 0, NSV = 0, NED = 0, NTR = 0, NTILE = 0, NNZB = 0;
-  int max_env_slices = 0, n_slices = 0;
+  int max_env_slices = 0, max_env_bodies = 0, n_slices = 0;
   int pcg_C = 0;  // CTAs per env cluster of the last solve's first persistent-PCG launch (0: tiled PCG)
   int pcg_resident[5] = {0, 0, 0, 0, 0};  // clusters of 1, 2, 4, 8, 16 CTAs resident at once
   long sell_nval = 0;
@@ -446,9 +480,8 @@ struct ipc_scene {
   // env control
   DBuf<int> e_status, e_reason, e_step, e_constrained, e_bad, e_nanp, e_halv, e_newton_it, e_count, e_rem;
   // barrier stiffness per env, its closest-contact tracking and the step-start sums
-  DBuf<double> e_kappa, e_kprev, e_kdots, g0buf;
+  DBuf<double> e_kappa, e_kdots, g0buf;
   DBuf<double> tet_vm;  // per-tet stress or per-contact force of a query
-  DBuf<unsigned long long> e_dmin2;
   DBuf<uint8_t> e_stepping, e_iter, e_ls, e_accept, e_sel, e_all, e_start, e_cover;
   DBuf<double> e_E0, e_Et, e_alpha;
   DBuf<unsigned long long> e_alpha_bits, e_pnorm_bits, e_inter, e_inv;
@@ -459,7 +492,7 @@ struct ipc_scene {
   // mixed precision: FP32 Hessians, sliced-ELL values, preconditioner blocks, stencil Hessians,
   // entry weights and every vector of the PCG (the FP64 twins above hold them otherwise)
   DBuf<float> f_tet_H, f_body_H, f_bsr_val, f_Ps, f_Pb, f_sH, f_ns_w, f_ns_xb, f_st_t, f_st_xb;
-  DBuf<float> f_r, f_z, f_d, f_y, f_x, f_part;
+  DBuf<float> f_r, f_z, f_d, f_y, f_x;
   bool mixed() const { return desc.precision == IPC_MIXED; }
   template <class T>
   static T* hp(DBuf<double>& d, DBuf<float>& f) {
@@ -468,7 +501,6 @@ struct ipc_scene {
   }
   DBuf<double> pcg_r, pcg_z, pcg_d, pcg_y, pcg_x, part_a, part_b, part_c, pcg_rz, pcg_bb;
   DBuf<int> pcg_it, pcg_active;
-  DBuf<double> pcg_part;  // per-slot partial sums of the persistent PCG
   DBuf<double> pcg_rzs, pcg_bbs, pcg_iterb, pcg_iterf;  // per-env state of the persistent PCG
   DBuf<unsigned long long> pcg_tune_iters;                 // env-iterations of a timed launch
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};
@@ -496,6 +528,9 @@ struct ipc_scene {
   DBuf<unsigned> fr_vals, fr_vals2;
   DBuf<int> fr_hist;
   int n_pt = 0, n_ee = 0, n_ct = 0, n_ct_pt = 0, n_fr = 0, n_fr_pt = 0, n_inc = 0;
+  DBuf<JointRec> jt;  // point joints of the batch, env-sorted (static per layout)
+  int n_jt = 0;
+  int n_st() const { return n_ct + n_fr + n_jt; }  // stencils: contacts, friction, joints
   DBuf<int> st_pts, st_env, st_cnt, st_off, ns_ptr, ns_src, ns_cnt;
   DBuf<unsigned long long> st_keys, st_keys2;
   DBuf<unsigned> st_vals, st_vals2;
@@ -709,6 +744,7 @@ struct ipc_scene {
     std::vector<int4> tets_h;
     std::vector<int> tet_env_h, pt_node_h, pt_body_h, pt_env_h, sv_pt_h, sv_env_h, ed_pt_h, ed_env_h, tri_pt_h, tri_env_h;
     std::vector<int> status_h, reason_h, step_h;
+    std::vector<JointRec> jt_h;
     std::vector<long long> stats_h;
     int body_base = 0, soft_body_base = 0;
     for (int li = 0; li < E; ++li) {
@@ -771,6 +807,15 @@ struct ipc_scene {
       for (size_t f = 0; f < h.tris.size() / 3; ++f) {
         for (int k = 0; k < 3; ++k) tri_pt_h.push_back(p0 + h.tris[3 * f + k]);
         tri_env_h.push_back(li);
+      }
+      for (const HostEnv::Joint& j : h.joints) {
+        JointRec r;
+        r.pts[0] = p0 + j.pa;
+        r.pts[1] = p0 + j.pb;
+        r.env = li;
+        r.pad = 0;
+        r.k = j.k;
+        jt_h.push_back(r);
       }
       nsteps_h.push_back(h.n_steps);
       grav_off_h.push_back((int)grav_h.size());
@@ -910,7 +955,8 @@ struct ipc_scene {
       pslice_off.upload(poff, s);
       pslice_row.upload(prow, s);
       pslice_sel.upload(psel, s);
-      pcg_part.alloc(mixed() ? 1 : 8 * ((size_t)n_slices + NB) + 8);
+      max_env_bodies = 0;
+      for (int li = 0; li < E; ++li) max_env_bodies = std::max(max_env_bodies, body_off_h[li + 1] - body_off_h[li]);
     }
     slice_w.upload(sw, s);
     slice_vbase.upload(svb, s);
@@ -957,6 +1003,8 @@ struct ipc_scene {
     ed_rest2.upload(ed_rest2_h, s);
     tri_pt.upload(tri_pt_h, s);
     tri_env.upload(tri_env_h, s);
+    n_jt = (int)jt_h.size();
+    jt.upload(jt_h, s);
     tile_env.upload(te, s);
     tile_kind.upload(tk, s);
     tile_begin.upload(tb, s);
@@ -975,19 +1023,8 @@ struct ipc_scene {
       pcg_iterf.alloc(E);
       pcg_its.alloc(E);
       pcg_runs.alloc(E);
-      if (mixed()) {
-        pcg_resident[0] = resident_clusters<1, float>();
-        pcg_resident[1] = resident_clusters<2, float>();
-        pcg_resident[2] = resident_clusters<4, float>();
-        pcg_resident[3] = resident_clusters<8, float>();
-        pcg_resident[4] = resident_clusters<16, float>();
-      } else {
-        pcg_resident[0] = resident_clusters<1, double>();
-        pcg_resident[1] = resident_clusters<2, double>();
-        pcg_resident[2] = resident_clusters<4, double>();
-        pcg_resident[3] = resident_clusters<8, double>();
-        pcg_resident[4] = resident_clusters<16, double>();
-      }
+      if (mixed()) pcg_shapes<float>();
+      else pcg_shapes<double>();
     }
     root_off_tri.upload(tri_off_h, s);
     root_off_ed.upload(ed_off_h, s);
@@ -1022,9 +1059,7 @@ struct ipc_scene {
     launch(k_fill_u8, E, 256, E, e_all.p, (uint8_t)1);
     for (DBuf<double>* b : {&e_E0, &e_Et, &e_alpha}) b->alloc(E);
     e_kappa.alloc(E);
-    e_kprev.alloc(E);
     e_kdots.alloc(2 * (size_t)E);
-    e_dmin2.alloc(E);
     launch(k_env_fill, E, 128, E, (const uint8_t*)nullptr, e_kappa.p, desc.kappa);
     for (DBuf<unsigned long long>* b : {&e_alpha_bits, &e_pnorm_bits, &e_inter, &e_inv}) b->alloc(E);
     nodeE.alloc(NN);
@@ -1043,7 +1078,6 @@ struct ipc_scene {
         b->alloc(n3);
         b->zero(s);  // kinematic soft rows are never written by the persistent PCG: d stays 0
       }
-      f_part.alloc(8 * ((size_t)n_slices + NB) + 8);
     } else {
       tet_H.alloc(90 * (size_t)NT);
       body_H.alloc(144 * (size_t)NB);
@@ -1241,7 +1275,7 @@ struct ipc_scene {
     else constraint_set(act);
   }
   void stencil_table() {
-    int ns = n_ct + n_fr;
+    int ns = n_st();
     st_pts.ensure(4 * (size_t)ns + 4);
     st_env.ensure(ns + 1);
     sE.ensure(ns + 1);
@@ -1256,7 +1290,8 @@ struct ipc_scene {
       sH.ensure(78 * (size_t)ns + 78);
       st_xb.ensure(12 * (size_t)ns + 12);
     }
-    launch(k_stencil_table, ns, 256, n_ct, n_fr, (const ContactRec*)ct.p, (const FrictionRec*)fr.p, st_pts.p, st_env.p);
+    launch(k_stencil_table, ns, 256, n_ct, n_fr, n_jt, (const ContactRec*)ct.p, (const FrictionRec*)fr.p,
+           (const JointRec*)jt.p, st_pts.p, st_env.p);
   }
   // ------------------------------------------------------------------ energy
   // energies (and derivatives) of the envs in act at DOFs q; positions/contacts at q are
@@ -1271,7 +1306,6 @@ struct ipc_scene {
   void evaluate_t(const double* q, const uint8_t* act, double* out) {
     launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p, q, ptx.p);
     contacts_at(act);
-    if (MODE == MODE_HESS && desc.kappa_adapt) kappa_iterate(act);
     stencil_table();
     // Hessian outputs (taken after stencil_table, which may grow the stencil buffers)
     HT* tH = MODE == MODE_HESS ? hp<HT>(tet_H, f_tet_H) : nullptr;
@@ -1298,7 +1332,7 @@ struct ipc_scene {
     if (fork) CK(cudaStreamWaitEvent(stream, join_ev, 0));
     else launch_contacts<MODE, HT>(act, q, h2, bH, sHp);
     EnergyLists L{nodeE.p, node_off.p, tetE.p, tet_off.p, bodyE.p, body_off.p, sE.p, st_env.p,
-                  n_ct_pt, n_ct - n_ct_pt, n_fr_pt, n_fr};
+                  n_ct_pt, n_ct - n_ct_pt, n_fr_pt, n_fr, n_jt};
     launch_grid(k_env_energy, E, 256, E, L, act, out);
   }
   // affine bodies, barrier and friction stencils of one evaluation
@@ -1324,18 +1358,13 @@ struct ipc_scene {
     launch(k_friction<MODE, HT>, n_fr, 128, n_fr, (const FrictionRec*)fr.p, act, (const double*)ptx.p,
            (const double*)ptx_t.p, h2, desc.eps_v * h, sE.p + n_ct, sg.p + 12 * (size_t)n_ct,
            sHp ? sHp + 78 * (size_t)n_ct : sHp);
+    const size_t j0 = (size_t)n_ct + n_fr;
+    launch(k_joint<MODE, HT>, n_jt, 128, n_jt, (const JointRec*)jt.p, act, (const double*)ptx.p, h2, sE.p + j0,
+           sg.p + 12 * j0, sHp ? sHp + 78 * j0 : sHp);
     pend(cfam);
   }
 
   // ------------------------------------------------------------------ adapted stiffness
-  // closest contact of every env in act (contacts ct at ptx), then the doubling test
-  void kappa_iterate(const uint8_t* act) {
-    CK(cudaMemsetAsync(e_dmin2.p, 0x7f, E * sizeof(unsigned long long), stream));  // > every finite d^2
-    launch(k_env_min_d2, n_ct, 128, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, e_dmin2.p);
-    const double lim = 1e-2 * desc.dhat;
-    launch(k_env_kappa_iter, E, 128, E, ctl(), act, (const unsigned long long*)e_dmin2.p, e_kprev.p, e_kappa.p,
-           1000.0 * desc.kappa, lim * lim);
-  }
   // gradient of the incremental potential at the DOFs x for the envs in act, into grad
   void gradient_at_x(const uint8_t* act) {
     evaluate<MODE_GRAD>(x.p, act, e_Et.p);
@@ -1360,7 +1389,7 @@ struct ipc_scene {
 
   // stencil -> node incidence (stable by stencil order within each node)
   void stencil_incidence(const uint8_t* act) {
-    int ns = n_ct + n_fr;
+    int ns = n_st();
     st_cnt.ensure(ns + 1);
     st_off.ensure(ns + 1);
     launch(k_stencil_nent, ns, 256, ns, (const int*)st_pts.p, (const int*)st_env.p, act, (const int*)pt_node.p, st_cnt.p);
@@ -1412,7 +1441,7 @@ struct ipc_scene {
   }
   template <class HT>
   void matvec_t(const uint8_t* run, const double* d, double* y, double* part) {
-    int ns = n_ct + n_fr;
+    int ns = n_st();
     launch(k_stencil_mv<HT, double>, 16L * ns, 128, ns, layout(), (const int*)st_env.p, (const int*)st_pts.p, run,
            (const HT*)hp<HT>(sH, f_sH), d, st_t.p);
     pbeg(IPC_PROF_SPMV);
@@ -1432,13 +1461,25 @@ struct ipc_scene {
     at.val.clusterDim.z = 1;
     return at;
   }
+  // Slot partials of the persistent PCG live in the CTAs' shared memory: slots one CTA of a
+  // C-cluster owns, and the dynamic shared memory that takes.
+  int ns_loc(int C) const { return (std::max(max_env_slices, 1) + C - 1) / C; }
+  int nb_loc(int C) const { return (std::max(max_env_bodies, 1) + C - 1) / C; }
+  template <class T>
+  size_t pcg_smem(int C) const { return pcg_smem_bytes<T>(ns_loc(C), nb_loc(C)); }
+  static constexpr size_t PCG_SMEM_CAP = 160 * 1024;  // leaves room for the static arrays
+  int pcg_c_min = 1;  // smallest cluster size whose slot partials fit PCG_SMEM_CAP
   template <int C, class T>
   int resident_clusters() {
     if (C > 8) CK(cudaFuncSetAttribute(k_pcg_cluster<C, T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    const size_t smem = pcg_smem<T>(C);
+    if (smem > PCG_SMEM_CAP) return 0;  // never chosen
+    CK(cudaFuncSetAttribute(k_pcg_cluster<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchAttribute at = cluster_attr<C>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(C * std::max(E, 1)));
     cfg.blockDim = dim3(PCG_THREADS);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cfg.attrs = &at;
     cfg.numAttrs = 1;
@@ -1449,16 +1490,31 @@ struct ipc_scene {
     }
     return n;
   }
+  template <class T>
+  void pcg_shapes() {
+    pcg_resident[0] = resident_clusters<1, T>();
+    pcg_resident[1] = resident_clusters<2, T>();
+    pcg_resident[2] = resident_clusters<4, T>();
+    pcg_resident[3] = resident_clusters<8, T>();
+    pcg_resident[4] = resident_clusters<16, T>();
+    pcg_c_min = 0;
+    for (int k = 0; k <= 4 && !pcg_c_min; ++k)
+      if (pcg_smem<T>(1 << k) <= PCG_SMEM_CAP) pcg_c_min = 1 << k;
+    if (!pcg_c_min)
+      fail_with(IPC_ERR_INTERNAL, "an environment has too many free soft rows for the persistent PCG (" +
+                                      std::to_string(32L * max_env_slices) + ")");
+  }
   // Cluster size for n running solves: the caller's choice, else the largest C <= 16 whose n
   // clusters are all resident at once and that still leaves each CTA two 32-row slices of the
-  // largest env. Fewer running solves get more SMs each; the bits do not depend on C.
+  // largest env; never below the smallest size whose slot partials fit in shared memory. Fewer
+  // running solves get more SMs each; the bits do not depend on C.
   int pick_cluster(int n) {
-    if (desc.pcg_cluster > 0) return desc.pcg_cluster;
+    if (desc.pcg_cluster > 0) return std::max(desc.pcg_cluster, pcg_c_min);
     for (int k = 4; k > 0; --k) {
       int C = 1 << k;
-      if (2 * C <= std::max(max_env_slices, 2) && n <= pcg_resident[k]) return C;
+      if (2 * C <= std::max(max_env_slices, 2) && n <= pcg_resident[k]) return std::max(C, pcg_c_min);
     }
-    return 1;
+    return pcg_c_min;
   }
   // Launch-shape autotuner of the persistent PCG. The running-env count of a launch falls in one
   // of three buckets (more than fit resident with 8-CTA clusters; more than fit with 16; fewer).
@@ -1505,11 +1561,19 @@ struct ipc_scene {
       b.best = (b.ms[1] / (double)b.its[1] < b.ms[0] / (double)b.its[0]) ? 1 : 0;
   }
   template <int C, class T>
-  void launch_pcg_cluster(const PcgClusterArgs<T>& a, int n) {
+  void launch_pcg_cluster(const PcgClusterArgs<T>& a0, int n) {
+    PcgClusterArgs<T> a = a0;
+    a.ns_loc = ns_loc(C);
+    a.nb_loc = nb_loc(C);
+    const size_t smem = pcg_smem_bytes<T>(a.ns_loc, a.nb_loc);
+    if (smem > PCG_SMEM_CAP) fail_with(IPC_ERR_INTERNAL, "PCG slot partials exceed shared memory");
+    if (C > 8) CK(cudaFuncSetAttribute(k_pcg_cluster<C, T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    CK(cudaFuncSetAttribute(k_pcg_cluster<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchAttribute at = cluster_attr<C>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(C * n));
     cfg.blockDim = dim3(PCG_THREADS);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cfg.attrs = &at;
     cfg.numAttrs = 1;
@@ -1549,8 +1613,8 @@ struct ipc_scene {
     a.body_off = body_off.p;
     a.st_env = st_env.p;
     a.sH = hp<T>(sH, f_sH);
-    int b[5] = {0, n_ct_pt, n_ct, n_ct + n_fr_pt, n_ct + n_fr};
-    for (int i = 0; i < 5; ++i) a.st_bounds[i] = b[i];
+    int b[6] = {0, n_ct_pt, n_ct, n_ct + n_fr_pt, n_ct + n_fr, n_st()};
+    for (int i = 0; i < 6; ++i) a.st_bounds[i] = b[i];
     a.Ps = hp<T>(Ps, f_Ps);
     a.Pb = hp<T>(Pb, f_Pb);
     a.act = act;
@@ -1562,9 +1626,6 @@ struct ipc_scene {
     a.st_t = st;
     a.tol2 = desc.pcg_rel_tol * desc.pcg_rel_tol;
     a.max_it = desc.max_pcg_iters;
-    a.part = hp<T>(pcg_part, f_part);
-    a.s_total = n_slices;
-    a.n_bodies = NB;
     a.env_list = env_iota.p;
     a.first = 1;
     a.chunk = pcg_chunk<T>();
@@ -2363,14 +2424,14 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       return copy_out(v, sizeof(v), out, out_bytes, written);
     }
     case IPC_Q_SIZES: {
-      long long v[8] = {h.ndof, (long long)h.pt_node.size(), (long long)h.sv.size(), (long long)h.edges.size() / 2,
+      long long v[8] = {h.ndof, (long long)h.n_surf_pts, (long long)h.sv.size(), (long long)h.edges.size() / 2,
                         (long long)h.tris.size() / 3, h.ntets, h.nbodies, h.n_steps};
       return copy_out(v, sizeof(v), out, out_bytes, written);
     }
     case IPC_Q_POINTS: {
       s->launch(k_points, s->NP, 256, s->NP, (const int*)s->pt_node.p, (const double*)s->pt_xb.p,
                 (const int*)s->body_node.p, (const double*)s->x.p, s->ptx.p);
-      int np = (int)h.pt_node.size();
+      int np = h.n_surf_pts;
       std::vector<double> buf(3 * (size_t)np);
       CK(cudaMemcpyAsync(buf.data(), s->ptx.p + 3 * (size_t)s->h_pt_off[li], buf.size() * 8, cudaMemcpyDeviceToHost,
                          s->stream));
@@ -2547,23 +2608,33 @@ static __device__ __align__(256) double g_noalloc_tet_energy[IPC_NOALLOC_MAX_TET
 static double* g_noalloc_ptr[256] = {nullptr};
 static std::mutex g_noalloc_mutex;
 
+// The group bound g as the kernels use it: the caller's offset clamped to [0, n_tets], so that
+// every access stays inside the tets and the scratch array whatever the offsets hold, and the
+// energy kernel and the group sum agree on which tets belong to which group.
+__device__ __forceinline__ int noalloc_bound(const int* __restrict__ goff, int g, int n_tets) {
+  return min(max(goff[g], 0), n_tets);
+}
 // per-tet energy into the scratch array (same tet_energy as the scene path); the group of a tet
-// is found by binary search in the offsets; an inverted tet flags its group
-__global__ void k_noalloc_tet_energy(int n_tets, const int4* __restrict__ tets, const double* __restrict__ prm,
+// is found by binary search in the clamped offsets; an inverted tet flags its group. Tets outside
+// [goff[0], goff[n_groups]) belong to no group: neither flagged nor summed. The tet's four node
+// indices are read as scalars (the caller's pointer need only be int-aligned).
+__global__ void k_noalloc_tet_energy(int n_tets, const int* __restrict__ tets, const double* __restrict__ prm,
                                      const double* __restrict__ x, int n_groups, const int* __restrict__ goff, double h2,
                                      double* __restrict__ tE, int* __restrict__ inverted) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tets) return;
-  int lo = 0, hi = n_groups - 1;  // last group g with goff[g] <= t
+  tE[t] = 0.0;
+  if (t < noalloc_bound(goff, 0, n_tets) || t >= noalloc_bound(goff, n_groups, n_tets)) return;
+  int lo = 0, hi = n_groups - 1;  // last group g with bound(g) <= t
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (goff[mid] <= t) lo = mid;
+    if (noalloc_bound(goff, mid, n_tets) <= t) lo = mid;
     else hi = mid - 1;
   }
-  int4 T = tets[t];
+  const int* T = tets + 4L * t;
   const double* P = prm + 12L * t;
   double F[9], cof[9], J;
-  double En = tet_energy(ld3(x, T.x), ld3(x, T.y), ld3(x, T.z), ld3(x, T.w), P, P[10], P[11], h2 * P[9], F, cof, &J);
+  double En = tet_energy(ld3(x, T[0]), ld3(x, T[1]), ld3(x, T[2]), ld3(x, T[3]), P, P[10], P[11], h2 * P[9], F, cof, &J);
   if (!(J > 0.0)) {
     inverted[lo] = 1;
     En = 0.0;
@@ -2574,14 +2645,16 @@ __global__ void k_noalloc_clear(int n, int* __restrict__ a) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = 0;
 }
-// one block per group, the same strided fixed-order block reduction as the scene path
-__global__ void k_noalloc_group_sum(int n_groups, const int* __restrict__ goff, const double* __restrict__ tE,
-                                    double* __restrict__ out) {
+// one block per group over its clamped range, the same strided fixed-order block reduction as
+// the scene path
+__global__ void k_noalloc_group_sum(int n_groups, int n_tets, const int* __restrict__ goff,
+                                    const double* __restrict__ tE, double* __restrict__ out) {
   __shared__ double sh[256];
   int g = blockIdx.x;
   if (g >= n_groups) return;
+  const int b0 = noalloc_bound(goff, g, n_tets), b1 = noalloc_bound(goff, g + 1, n_tets);
   double s = 0.0;
-  for (int i = goff[g] + threadIdx.x; i < goff[g + 1]; i += blockDim.x) s += tE[i];
+  for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += tE[i];
   s = block_sum(s, sh);
   if (threadIdx.x == 0) out[g] = s;
 }
@@ -2597,6 +2670,10 @@ ipc_status ipc_elastic_energy_noalloc(int32_t n_tets, const int32_t* tets, const
                                std::to_string(IPC_NOALLOC_MAX_TETS));
   if (n_groups > IPC_NOALLOC_MAX_GROUPS)
     fail_with(IPC_ERR_ARG, "ipc_elastic_energy_noalloc: more than " + std::to_string(IPC_NOALLOC_MAX_GROUPS) + " groups");
+  auto misaligned = [](const void* ptr, size_t a) { return ((uintptr_t)ptr) % a != 0; };
+  if (misaligned(tets, 4) || misaligned(group_offsets, 4) || misaligned(inverted, 4) || misaligned(tet_params, 8) ||
+      misaligned(x, 8) || misaligned(energy, 8))
+    fail_with(IPC_ERR_ARG, "ipc_elastic_energy_noalloc: a pointer is not aligned to its element type");
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) fail_with(IPC_ERR_ARG, "ipc_elastic_energy_noalloc: device ordinal out of range");
@@ -2614,11 +2691,11 @@ ipc_status ipc_elastic_energy_noalloc(int32_t n_tets, const int32_t* tets, const
   k_noalloc_clear<<<(n_groups + 255) / 256, 256, 0, st>>>(n_groups, inverted);
   CK(cudaGetLastError());
   if (n_tets > 0) {
-    k_noalloc_tet_energy<<<(n_tets + 127) / 128, 128, 0, st>>>(n_tets, (const int4*)tets, tet_params, x, n_groups,
-                                                               group_offsets, h2, scratch, inverted);
+    k_noalloc_tet_energy<<<(n_tets + 127) / 128, 128, 0, st>>>(n_tets, tets, tet_params, x, n_groups, group_offsets,
+                                                               h2, scratch, inverted);
     CK(cudaGetLastError());
   }
-  k_noalloc_group_sum<<<n_groups, 256, 0, st>>>(n_groups, group_offsets, scratch, energy);
+  k_noalloc_group_sum<<<n_groups, 256, 0, st>>>(n_groups, n_tets, group_offsets, scratch, energy);
   CK(cudaGetLastError());
   API_END
 }

@@ -754,10 +754,17 @@ __global__ void k_friction_setup(int n_ct, const ContactRec* __restrict__ ct, co
 }
 
 // stencil table [contacts | friction]: points and env of every 4-point stencil
-__global__ void k_stencil_table(int n_ct, int n_fr, const ContactRec* __restrict__ ct, const FrictionRec* __restrict__ fr,
+__global__ void k_stencil_table(int n_ct, int n_fr, int n_jt, const ContactRec* __restrict__ ct,
+                                const FrictionRec* __restrict__ fr, const JointRec* __restrict__ jt,
                                 int* __restrict__ st_pts, int* __restrict__ st_env) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n_ct + n_fr) return;
+  if (s >= n_ct + n_fr + n_jt) return;
+  if (s >= n_ct + n_fr) {  // a joint: points (a, b, a, b), the last two carry nothing
+    const JointRec& J = jt[s - n_ct - n_fr];
+    for (int k = 0; k < 4; ++k) st_pts[4 * s + k] = J.pts[k & 1];
+    st_env[s] = J.env;
+    return;
+  }
   const int* p;
   int e;
   if (s < n_ct) {
@@ -809,31 +816,6 @@ __global__ void k_count_keys(int n, const unsigned long long* __restrict__ keys,
 }
 
 // ---------------------------------------------------------------- adapted barrier stiffness
-// Squared distance of the closest contact of every env (non-negative doubles: their bit patterns
-// order like the values, so an integer atomic minimum gives the exact minimum in any order).
-__global__ void k_env_min_d2(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
-                             const double* __restrict__ ptx, unsigned long long* __restrict__ dmin2) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_ct) return;
-  const ContactRec c = ct[k];
-  if (!act[c.env]) return;
-  d3 X[4];
-  for (int i = 0; i < 4; ++i) X[i] = ld3(ptx, c.pts[i]);
-  int type;
-  const double d2 = pair_d2(c.kind, X, &type);
-  atomicMin(&dmin2[c.env], (unsigned long long)__double_as_longlong(d2));
-}
-// Inside a step the stiffness of an env doubles (up to kmax) at an iterate whose closest contact
-// is nearer than lim (squared: lim2) and nearer than at the previous iterate.
-__global__ void k_env_kappa_iter(int n_env, EnvCtl C, const uint8_t* __restrict__ act,
-                                 const unsigned long long* __restrict__ dmin2, double* __restrict__ prev,
-                                 double* __restrict__ kappa, double kmax, double lim2) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n_env || !act[e]) return;
-  const double m = __longlong_as_double((long long)dmin2[e]);
-  if (C.newton_it[e] > 0 && m < lim2 && m < prev[e]) kappa[e] = fmin(2.0 * kappa[e], kmax);
-  prev[e] = m;
-}
 // Start of a step: per env, over its free DOFs, g0 . G and G . G with g0 the gradient without the
 // barrier (stiffness 0) and G = g1 - g0 the barrier's gradient per unit stiffness; one block per
 // env, fixed-order block sums (the result does not depend on the batch).

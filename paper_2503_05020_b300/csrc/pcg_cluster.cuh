@@ -19,8 +19,11 @@
 // Determinism: every dot product is summed per slot (a slice: warp butterfly over its 32 rows; a
 // body: fixed CTA tree), and the env's slots are added in a fixed order that depends on the env
 // alone. So the results are the same bits for every cluster size and every batch the env is in.
-// Vectors that other CTAs write inside the kernel (d, t, the slot partials) are read with
-// L2-coherent loads after the cluster barrier that publishes them.
+// A slot's partial lives in the shared memory of the CTA that owns the slot; after the barrier
+// that publishes the partials every CTA reads all of the env's slots over distributed shared
+// memory (the SM-to-SM network of the cluster, no L2 round trip) in that fixed order. Vectors
+// that other CTAs write inside the kernel (d, t) are read with L2-coherent loads after the
+// cluster barrier that publishes them.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -30,6 +33,7 @@
 namespace cg = cooperative_groups;
 
 constexpr int PCG_THREADS = 256;
+constexpr int N_ST_LISTS = 5;  // stencil sublists: contacts pt, ee; friction pt, ee; joints
 constexpr int PCG_WARPS = PCG_THREADS / 32;
 // CTAs per SM the register budget must allow: the FP64 solve keeps 128 registers a thread (it
 // is bound by the FP64 pipe, and fewer registers spill); the FP32 solve is bound by memory
@@ -50,7 +54,7 @@ struct PcgClusterArgs {
   const int* body_off;    // per env: first body (n_env + 1 entries)
   const int* st_env;
   const T* sH;
-  int st_bounds[5];       // stencil sublists [pt | ee | friction pt | friction ee], each env-sorted
+  int st_bounds[6];       // stencil sublists [pt | ee | friction pt | friction ee | joints], each env-sorted
   const T* Ps;
   const T* Pb;
   const uint8_t* act;
@@ -62,9 +66,8 @@ struct PcgClusterArgs {
   T* st_t;                // stencil products (the same buffer SpmvArgs reads)
   double tol2;             // (relative tolerance)^2
   int max_it;
-  T* part;                    // slot partials: 2 x 4 values x (s_total + n_bodies)
-  int s_total;                // slices of the whole batch
-  int n_bodies;               // rigid bodies of the whole batch
+  int ns_loc;                 // slice slots one CTA owns at most (ceil(most slices of an env / C))
+  int nb_loc;                 // body slots one CTA owns at most (ceil(most bodies of an env / C))
   const int* env_list;        // env of each cluster
   int first;                  // 1: start the solves (z = M^-1 r, d = z, x = 0); 0: resume them
   int chunk;                  // iterations at most in this launch
@@ -80,22 +83,35 @@ struct PcgClusterArgs {
   unsigned long long* iters;  // env-iterations done by this launch (may be null)
 };
 
+// Dynamic shared memory of one CTA: per owned slot, one d.y partial, then four values (r.z, r.r
+// and, at the start, the algorithmic bytes and flops of one iteration). Slice slot j of the env
+// (j = slice - first slice) is owned by CTA j mod C at local index j / C; body slot j by CTA
+// j mod C at local index ns_loc + j / C.
+template <class T>
+constexpr size_t pcg_smem_bytes(int ns_loc, int nb_loc) {
+  return (size_t)5 * (ns_loc + nb_loc) * sizeof(T);
+}
+
 // Sum of an env's slot partials (its slices, then its bodies) in a fixed order that depends on
-// the env alone: lane l of warp 0 adds slots l, l + 32, ... and the lanes are combined by a fixed
-// butterfly. Every CTA of the cluster computes the same bits; the result is broadcast through
-// shared memory. Call after a cluster barrier that publishes the partials.
-template <int K, class T>
-DEV void env_sum(const T* part, int S0, int S1, int s_total, int b0, int b1, T* tot, T (&v)[K]) {
+// the env alone: lane l of warp 0 adds slots l, l + 32, ... (each read from its owner CTA's
+// shared memory) and the lanes are combined by a fixed butterfly. Every CTA of the cluster
+// computes the same bits; the result is broadcast through shared memory. Call after a cluster
+// barrier that publishes the partials. base: this CTA's copy of the array (stride values per
+// slot, the first K summed).
+template <int K, int C, class T>
+DEV void env_sum(const cg::cluster_group& cl, T* base, int stride, int ns, int nb, int ns_loc, T* tot, T (&v)[K]) {
   if (threadIdx.x < 32) {
-    const int lane = threadIdx.x, ns = S1 - S0, n = ns + (b1 - b0);
+    const int lane = threadIdx.x, n = ns + nb;
     T s[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) s[q] = T(0);
 #pragma unroll 4
     for (int j = lane; j < n; j += 32) {  // unrolled: the loads of several slots in flight at once
-      long slot = j < ns ? S0 + j : (long)s_total + b0 + (j - ns);
+      const int jj = j < ns ? j : j - ns;
+      const int li = j < ns ? jj / C : ns_loc + jj / C;
+      const T* src = C == 1 ? base : cl.map_shared_rank(base, (unsigned)(jj % C));
 #pragma unroll
-      for (int q = 0; q < K; ++q) s[q] += __ldcg(part + 4 * slot + q);
+      for (int q = 0; q < K; ++q) s[q] += src[stride * li + q];
     }
 #pragma unroll
     for (int q = 0; q < K; ++q) {
@@ -157,10 +173,11 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
     if (rank == 0 && threadIdx.x == 0) P.run[e] = 0;
     return;
   }
+  extern __shared__ __align__(16) unsigned char pcg_dyn[];
   __shared__ T wred[PCG_WARPS][12];
   __shared__ T tot[4];
   __shared__ T sbody[12];
-  __shared__ int srange[8];
+  __shared__ int srange[2 * N_ST_LISTS];
   __shared__ int grab[4];  // per phase: the next of this CTA's slices to hand to a warp
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // warps are interleaved over the cluster's CTAs, so consecutive slices land on different SMs
@@ -168,15 +185,15 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
   const Layout& L = P.L;
   const int S0 = P.pslice_off[e], S1 = P.pslice_off[e + 1];
   const int b0 = P.body_off[e], b1 = P.body_off[e + 1];
-  const int ST = P.s_total;
-  T* part_dy = P.part;                                  // 4 values per slot, [0] used
-  T* part_rz = P.part + 4L * (P.s_total + P.n_bodies);  // (r.z, r.r, bytes, flops) per slot
-  if (tid < 4) {  // this env's range in each stencil sublist
+  const int NSL = P.ns_loc;
+  T* part_dy = (T*)pcg_dyn;                      // 1 value per owned slot
+  T* part_rz = part_dy + (P.ns_loc + P.nb_loc);  // (r.z, r.r, bytes, flops) per owned slot
+  if (tid < N_ST_LISTS) {  // this env's range in each stencil sublist
     int lo = P.st_bounds[tid], hi = P.st_bounds[tid + 1];
     srange[2 * tid] = lower_env(P.st_env, lo, hi, e);
     srange[2 * tid + 1] = lower_env(P.st_env, lo, hi, e + 1);
-    grab[tid] = 0;
   }
+  if (tid < 4) grab[tid] = 0;
   __syncthreads();
   // Slices go to CTAs round-robin (slice S0 + rank + C j belongs to this CTA) and, inside the
   // CTA, to whichever warp asks next, so warps of uneven rows finish a phase together. A row
@@ -189,7 +206,8 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
     j = __shfl_sync(0xffffffffu, j, 0);
     return j < n_mine ? S0 + rank + C * j : -1;
   };
-  const int n_stencils = srange[1] - srange[0] + srange[3] - srange[2] + srange[5] - srange[4] + srange[7] - srange[6];
+  int n_stencils = 0;
+  for (int q = 0; q < N_ST_LISTS; ++q) n_stencils += srange[2 * q + 1] - srange[2 * q];
 
   T rz, bb;
   double iter_bytes, iter_flops;
@@ -216,10 +234,11 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
       nb = warp_sum(nb);
       nf = warp_sum(nf);
       if (lane == 0) {
-        part_rz[4L * sl] = a;
-        part_rz[4L * sl + 1] = c;
-        part_rz[4L * sl + 2] = nb;
-        part_rz[4L * sl + 3] = nf;
+        T* o = part_rz + 4 * ((sl - S0) / C);
+        o[0] = a;
+        o[1] = c;
+        o[2] = nb;
+        o[3] = nf;
       }
     }
     for (int b = b0; b < b1; ++b) {
@@ -237,18 +256,18 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
         a = warp_sum(a);
         c = warp_sum(c);
         if (lane == 0) {
-          long slot = (long)ST + b;
-          part_rz[4 * slot] = a;
-          part_rz[4 * slot + 1] = c;
-          part_rz[4 * slot + 2] = P.bytes ? T(body_iter_bytes(L, P.A, b)) : T(0);
-          part_rz[4 * slot + 3] = P.bytes ? T(body_iter_flops(L, P.A, b)) : T(0);
+          T* o = part_rz + 4 * (NSL + (b - b0) / C);
+          o[0] = a;
+          o[1] = c;
+          o[2] = P.bytes ? T(body_iter_bytes(L, P.A, b)) : T(0);
+          o[3] = P.bytes ? T(body_iter_flops(L, P.A, b)) : T(0);
         }
       }
       __syncthreads();
     }
     cl.sync();
     T v4[4];
-    env_sum<4>(part_rz, S0, S1, ST, b0, b1, tot, v4);
+    env_sum<4, C>(cl, part_rz, 4, S1 - S0, b1 - b0, NSL, tot, v4);
     rz = v4[0];
     bb = v4[1];
     iter_bytes = double(v4[2]) + (P.bytes ? stencil_iter_bytes<T>() * n_stencils : 0.0);
@@ -258,7 +277,7 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
     // ---- t_s = H_s (P_s d) for the env's stencils, one half-warp per stencil (d = z was
     // published by the barrier above)
     if (go)
-      for (int q = 0; q < 4; ++q)  // warp-uniform loop
+      for (int q = 0; q < N_ST_LISTS; ++q)  // warp-uniform loop
         for (int s0 = srange[2 * q] + 2 * gwarp; s0 < srange[2 * q + 1]; s0 += 2 * nwarps) {
           int s = s0 + (lane >> 4);
           stencil_product_nodes<true>(P.A, (const T*)P.d, P.st_t, s, s < srange[2 * q + 1]);
@@ -287,7 +306,7 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
         dy = soft_row<true>(P.A, sel >> 5, sel & 31, i, (const T*)P.d, P.y);
       }
       dy = warp_sum(dy);
-      if (lane == 0) part_dy[4L * sl] = dy;
+      if (lane == 0) part_dy[(sl - S0) / C] = dy;
     }
     // ---- rigid bodies on their owner CTA: stencil entries gathered by its threads in a fixed
     // partition, the dense 12x12 block, one partial d.y per body
@@ -338,13 +357,13 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
           dyb = v * __ldcg(P.d + 3 * base + lane);
         }
         dyb = warp_sum(dyb);
-        if (lane == 0) part_dy[4 * ((long)ST + b)] = dyb;
+        if (lane == 0) part_dy[NSL + (b - b0) / C] = dyb;
       }
       __syncthreads();
     }
     cl.sync();
     T dy[1];
-    env_sum<1>(part_dy, S0, S1, ST, b0, b1, tot, dy);
+    env_sum<1, C>(cl, part_dy, 1, S1 - S0, b1 - b0, NSL, tot, dy);
     const T alpha = dy[0] > T(0) ? rz / dy[0] : T(0);
     // ---- x += alpha d; r -= alpha y; z = M^-1 r (owner threads only)
     if (tid == 0) grab[1] = 0;  // every warp is past the product phase (barrier above)
@@ -361,8 +380,8 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
       a = warp_sum(a);
       c = warp_sum(c);
       if (lane == 0) {
-        part_rz[4L * sl] = a;
-        part_rz[4L * sl + 1] = c;
+        part_rz[4 * ((sl - S0) / C)] = a;
+        part_rz[4 * ((sl - S0) / C) + 1] = c;
       }
     }
     for (int b = b0; b < b1; ++b) {
@@ -382,15 +401,15 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
         a = warp_sum(a);
         c = warp_sum(c);
         if (lane == 0) {
-          part_rz[4 * ((long)ST + b)] = a;
-          part_rz[4 * ((long)ST + b) + 1] = c;
+          part_rz[4 * (NSL + (b - b0) / C)] = a;
+          part_rz[4 * (NSL + (b - b0) / C) + 1] = c;
         }
       }
       __syncthreads();
     }
     cl.sync();
     T u2[2];
-    env_sum<2>(part_rz, S0, S1, ST, b0, b1, tot, u2);
+    env_sum<2, C>(cl, part_rz, 4, S1 - S0, b1 - b0, NSL, tot, u2);
     const T rz_new = u2[0], rr = u2[1];
     ++it;
     if (rr <= tol2 * bb || it >= P.max_it || !(dy[0] > T(0)) || !isfinite(rr)) {
@@ -414,13 +433,16 @@ __global__ void __launch_bounds__(PCG_THREADS, pcg_min_ctas<T>()) k_pcg_cluster(
     // ---- the stencil products follow d by linearity, H_s P_s d_new = H_s P_s z + beta t_s,
     // so they need z (published by the barrier above) and not the d being written: the next
     // product phase waits on one barrier instead of two
-    for (int q = 0; q < 4; ++q)  // warp-uniform loop
+    for (int q = 0; q < N_ST_LISTS; ++q)  // warp-uniform loop
       for (int s0 = srange[2 * q] + 2 * gwarp; s0 < srange[2 * q + 1]; s0 += 2 * nwarps) {
         int s = s0 + (lane >> 4);
         stencil_product_nodes<true>(P.A, (const T*)P.z, P.st_t, s, s < srange[2 * q + 1], beta);
       }
   }
-  // every CTA read the slot partials before it got here; CTA 0 records the env's state
+  // the CTAs of the cluster read each other's shared memory up to the last sum: none may leave
+  // (and release its shared memory) before all are past it
+  if (C > 1) cl.sync();
+  // CTA 0 records the env's state
   if (rank == 0 && tid == 0) {
     P.rz_state[e] = double(rz);
     P.bb_state[e] = double(bb);

@@ -53,10 +53,16 @@ class AffineDesc(C.Structure):
                 ("q0", C.c_double * 12), ("qdot0", C.c_double * 12), ("pd_stiffness", C.c_double)]
 
 
+class JointDesc(C.Structure):
+    _fields_ = [("body_a", C.c_int32), ("body_b", C.c_int32), ("anchor_a", C.c_double * 3),
+                ("anchor_b", C.c_double * 3), ("stiffness", C.c_double)]
+
+
 class EnvDesc(C.Structure):
     _fields_ = [("n_soft", C.c_int32), ("n_affine", C.c_int32), ("n_steps", C.c_int32), ("pad", C.c_int32),
                 ("soft", C.c_void_p), ("affine", C.c_void_p), ("friction_mu", C.c_double),
-                ("gravity_on", C.c_void_p), ("targets", C.c_void_p)]
+                ("gravity_on", C.c_void_p), ("targets", C.c_void_p), ("n_joints", C.c_int32), ("pad2", C.c_int32),
+                ("joints", C.c_void_p)]
 
 
 _lib = None
@@ -138,6 +144,14 @@ class _EnvMarshal:
         d.n_soft, d.n_affine, d.n_steps = len(env["soft"]), len(env["affine"]), len(g)
         d.soft, d.affine = C.addressof(soft), C.addressof(aff)
         d.friction_mu, d.gravity_on, d.targets = env["mu"], g.ctypes.data, tg.ctypes.data
+        js = env.get("joints", [])
+        jt = (JointDesc * max(len(js), 1))()
+        for i, j in enumerate(js):
+            jt[i].body_a, jt[i].body_b, jt[i].stiffness = int(j["a"]), int(j["b"]), float(j["k"])
+            for k in range(3):
+                jt[i].anchor_a[k], jt[i].anchor_b[k] = j["anchor_a"][k], j["anchor_b"][k]
+        self.keep.append(jt)
+        d.n_joints, d.joints = len(js), C.addressof(jt)
         self.desc = d
 
 

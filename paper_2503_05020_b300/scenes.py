@@ -20,6 +20,9 @@ Env dict layout (all arrays numpy, C-contiguous):
     targets: (n_steps, n_soft + n_affine, 12) f64 — for each step s the affine map
              q = (p, a1, a2, a3) that a kinematic body (or a soft body's kinematic vertices,
              mapped from their initial positions) must reach at the end of step s.
+    joints:  (optional) list of {a, b: affine body indices, anchor_a, anchor_b: (3,) rest-frame
+             anchors, k: stiffness N/m} — point joints 1/2 k |x_a - x_b|^2; two on one axis
+             make a hinge.
 
 Affine coordinates q = (p, a1, a2, a3) place a rest point xb at p + xb[0] a1 + xb[1] a2 + xb[2] a3
 (the a_i are the columns of A).
@@ -558,6 +561,36 @@ def uneven_batch_env(env_id: int, base_seed: int = UNEVEN_SEED) -> dict:
 UNEVEN_START_STEP = 20
 
 
+def uneven_batch_cost(env_id: int, base_seed: int = UNEVEN_SEED) -> float:
+    """Estimated work of uneven_batch_env(env_id) without building it: its tet count (the object's
+    drawn size plus ~5k tets per soft pad) and its surface size, a proxy for its contacts (n_t +
+    n_c, the units the per-env stages scale with). Replays only the seeded draws that fix the
+    sizes."""
+    rng = SplitMix64(base_seed + env_id)
+    pads = rng.uniform() < 0.5
+    bimanual = rng.uniform() < 0.25
+    inner = SplitMix64(base_seed + 7 + env_id)
+    obj = math.exp(inner.uniform(math.log(2000), math.log(60000)))
+    n_pads = (4 if bimanual else 2) if pads else 0
+    tets = obj + 5000.0 * n_pads
+    surface = 6.0 * obj ** (2.0 / 3.0) + 2100.0 * n_pads
+    return tets + surface
+
+
+def lpt_shards(costs, world: int) -> list[list[int]]:
+    """Greedy longest-processing-time partition of items with the given costs over `world` bins:
+    items in decreasing cost (ties by index) each go to the bin with the least total so far
+    (ties to the lowest bin). Every bin's items are returned in ascending order."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    bins = [[] for _ in range(world)]
+    for i in order:
+        b = min(range(world), key=lambda r: (load[r], r))
+        load[b] += costs[i]
+        bins[b].append(i)
+    return [sorted(b) for b in bins]
+
+
 def grasp_state_at(env: dict, step: int) -> tuple[np.ndarray, np.ndarray]:
     """Synthetic start of a grasp env at schedule step `step`: every soft body with kinematic
     vertices translated by the displacement its schedule reaches at the end of step-1, every
@@ -700,13 +733,17 @@ def _q_pose(R: np.ndarray, c: np.ndarray) -> np.ndarray:
 
 def hand_grasp_env(env_id: int, base_seed: int = BASE_SEED + 104729, n_steps: int = 400, close_steps: int = 200,
                    dt: float = 0.005, dhat: float = 5e-4, cells: int = 19, k_pd: float = 3e3, lift: float = 0.05,
-                   link_points: int = 250) -> dict:
+                   link_points: int = 250, k_joint: float | None = 1e5) -> dict:
     """Rigid hand of 20 PD-driven affine links (5 fingers x 4; each link a ~500-triangle hull)
     grasping a seeded star-shaped soft object (Kuhn ball of `cells`^3 cells, about 21k tets for 19;
     E log-uniform in [1e4, 1e6] Pa, nu U(0.3, 0.48)). Finger f hangs in the vertical half-plane at
     azimuth 2 pi f / 5 above and outside the object; its four joint angles curl it toward the
     object over `close_steps` (gravity off), then every link target rises by `lift` (gravity on).
-    Links are free bodies pulled toward their targets by the PD target potential (k_pd 1/s^2)."""
+    Links are free bodies pulled toward their targets by the PD target potential (k_pd 1/s^2).
+    With k_joint (N/m) the hand is articulated: each finger's first link hangs from a kinematic
+    palm (a small box above the object, the last affine body) and each further link from the
+    previous one by a hinge on the finger's bending axis, two point joints at +/- the link
+    radius along it (20 hinges, 40 point joints); None leaves the links unjointed."""
     rng = SplitMix64(base_seed + env_id)
     E = math.exp(rng.uniform(math.log(1e4), math.log(1e6)))
     nu = rng.uniform(0.3, 0.48)
@@ -756,8 +793,60 @@ def hand_grasp_env(env_id: int, base_seed: int = BASE_SEED + 104729, n_steps: in
     for k in range(20):
         lv, lt = link_shapes[k]
         links.append(dict(verts=lv, tris=lt, rho=1200.0, q0=q_init[k], qdot0=np.zeros(12), kinematic=False, pd=k_pd))
-    return dict(soft=[soft], affine=links, mu=rng.uniform(0.5, 0.9), gravity=gravity, targets=targets,
-                object=("soft", 0), lift=lift)
+    mu = rng.uniform(0.5, 0.9)
+    if k_joint is None:
+        return dict(soft=[soft], affine=links, mu=mu, gravity=gravity, targets=targets, object=("soft", 0), lift=lift)
+    # palm: a kinematic box above the object (clear of it and of the fingers), rising with the lift
+    c_palm = np.array([0.0, 0.0, rmax + 0.02])
+    pv, ptr = box_surface((0.01, 0.01, 0.004))
+    palm = dict(verts=pv, tris=ptr, rho=1000.0, q0=_translation_q(c_palm), qdot0=np.zeros(12), kinematic=True)
+    tg = np.zeros((n_steps, 22, 12))
+    tg[:, :21] = targets
+    for s_ in range(n_steps):
+        dz = lift * max(0.0, (s_ + 1 - close_steps) / max(n_steps - close_steps, 1))
+        tg[s_, 21] = _translation_q(c_palm + np.array([0.0, 0.0, dz]))
+    joints = []
+    for f, phi in enumerate(phis):
+        er = np.array([math.cos(phi), math.sin(phi), 0.0])
+        et = np.array([-math.sin(phi), math.cos(phi), 0.0])
+        base = base_r * er + np.array([0.0, 0.0, base_z])
+        for sgn in (+1.0, -1.0):
+            joints.append(dict(a=20, b=4 * f, anchor_a=base + sgn * rw * et - c_palm,
+                               anchor_b=np.array([sgn * rw, 0.0, -0.5 * L]), k=k_joint))
+            for k in range(1, 4):
+                joints.append(dict(a=4 * f + k - 1, b=4 * f + k, anchor_a=np.array([sgn * rw, 0.0, 0.5 * L]),
+                                   anchor_b=np.array([sgn * rw, 0.0, -0.5 * L]), k=k_joint))
+    return dict(soft=[soft], affine=links + [palm], mu=mu, gravity=gravity, targets=tg, object=("soft", 0),
+                lift=lift, joints=joints)
+
+
+def pendulum_env(k_joint: float = 1e4, n_steps: int = 100, theta0: float = 0.0, arm: float = 0.1,
+                 half: float = 0.01, rho: float = 1000.0, gravity: bool = True, wall_y: float | None = None,
+                 mu: float = 0.0) -> dict:
+    """A rigid cube (half side `half`) hanging by a point joint from a fixed kinematic pivot: the
+    joint's anchor sits `arm` above the cube's centre in the cube's frame and at the world
+    origin in the pivot's; the cube starts at rest turned by theta0 about the x axis through the
+    joint. Pivot and cube are far apart (no contact). With wall_y, a fixed kinematic wall (a thin
+    box whose face is the plane y = wall_y, below the pivot) stands in the cube's swing."""
+    bv, bt = box_surface((half, half, half))
+    pv, pt_ = box_surface((half, half, half))
+    pivot_c = np.array([0.0, 0.0, 0.05])
+    pivot = dict(verts=pv, tris=pt_, rho=rho, q0=_translation_q(pivot_c), qdot0=np.zeros(12), kinematic=True)
+    R = _rot_x(math.degrees(theta0))
+    bob = dict(verts=bv, tris=bt, rho=rho, q0=_q_pose(R, R @ np.array([0.0, 0.0, -arm])), qdot0=np.zeros(12),
+               kinematic=False)
+    targets = np.zeros((n_steps, 2, 12))
+    targets[:, 0] = pivot["q0"]
+    targets[:, 1] = bob["q0"]
+    joint = dict(a=0, b=1, anchor_a=-pivot_c, anchor_b=np.array([0.0, 0.0, arm]), k=k_joint)
+    affine = [pivot, bob]
+    if wall_y is not None:
+        wv, wt = box_surface((0.05, 0.005, 0.03))
+        c = np.array([0.0, wall_y - 0.005 if wall_y < 0 else wall_y + 0.005, -arm])
+        affine.append(dict(verts=wv, tris=wt, rho=rho, q0=_translation_q(c), qdot0=np.zeros(12), kinematic=True))
+        targets = np.concatenate([targets, np.tile(affine[-1]["q0"], (n_steps, 1, 1))], axis=1)
+    return dict(soft=[], affine=affine, mu=mu, gravity=np.full(n_steps, 1 if gravity else 0, dtype=np.uint8),
+                targets=targets, joints=[joint])
 
 
 def pd_body_env(k_pd: float = 400.0, n_steps: int = 100, gravity: bool = True, target_shift=(0.0, 0.0, 0.0),

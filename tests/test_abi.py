@@ -143,3 +143,44 @@ def test_product_path_has_no_cpu_fallback():
             assert "not built" in str(e)
     finally:
         fresh.LIB_PATH, fresh._lib = saved_path, saved_lib
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every descriptor struct of the binding has the size and field offsets the C compiler gives
+    include/ipc.h (a layout mismatch would pass garbage through the ABI)."""
+    import ctypes as C
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"ipc_scene_desc": ipc.SceneDesc, "ipc_soft_body_desc": ipc.SoftDesc,
+               "ipc_affine_body_desc": ipc.AffineDesc, "ipc_joint_desc": ipc.JointDesc, "ipc_env_desc": ipc.EnvDesc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ipc.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_joint_descriptors_are_validated_on_host():
+    """A joint must join two distinct affine bodies of its env with a positive stiffness."""
+    from paper_2503_05020_b300 import scenes as S
+
+    env = S.pendulum_env()
+    assert ipc.estimate_bytes(env) > 0
+    for bad in (dict(b=2), dict(b=0), dict(k=0.0), dict(a=-1)):
+        e = dict(env, joints=[dict(env["joints"][0], **bad)])
+        try:
+            ipc.estimate_bytes(e)
+            raise AssertionError(f"bad joint accepted: {bad}")
+        except ipc.IpcError as err:
+            assert err.status == 1

@@ -383,16 +383,17 @@ def test_batched_pad_grasps_do_the_work_of_each_alone():
 
 
 def test_adapted_stiffness_trajectory_and_kappa_parity():
-    """The squeezed cube with the adapted barrier stiffness: per step, the GPU's kappa equals the
+    """The single-env configuration as written: the squeezed cube (close 50 steps, lift 50) with
+    the adapted barrier stiffness over all 100 steps. Per step, the GPU's kappa equals the
     oracle's (1e-9 relative: the step-start least squares sums in another order) and the
     trajectories agree within 1e-6 m; the stiffness did adapt."""
     p = dict(S.parity_params(S.scene_params(0.01)), kappa_adapt=True)
-    env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+    env = S.cube_squeeze_env(0, n_steps=100)
     o = O.OracleEnv(p, env)
     sc = ipc.Scene(p)
     eid = sc.add_env(env)
     ks = []
-    for k in range(40):
+    for k in range(100):
         o.step(1)
         sc.step(1)
         ks.append(o.kappa())
@@ -401,6 +402,7 @@ def test_adapted_stiffness_trajectory_and_kappa_parity():
             xo, _ = o.state()
             assert np.abs(sc.dofs(eid) - xo).max() <= TRAJ_TOL, k
     assert max(ks) > p["kappa"]
+    assert sc.status(eid)["status"] == "DONE" and o.status()["status"] == "DONE"
     assert sc.invariants(eid) == {"intersections": 0, "inverted": 0}
 
 

@@ -643,3 +643,75 @@ def test_projection_makes_the_hessian_psd_where_the_raw_one_is_not():
         H = e.hessian(q)
         assert np.allclose(H, H.T, atol=1e-12 * np.abs(H).max())
         assert np.linalg.eigvalsh(H).min() > -1e-9 * np.abs(H).max()
+
+
+def _bob_com(x):
+    return x[12:15]
+
+
+def test_joint_hangs_a_body_by_its_static_sag():
+    """A cube (side a, volume V) hanging by a point joint of stiffness k, anchored l above its
+    centre, settles with its joint stretched by m g / k straight down (the joint force balances
+    the weight) and neither turns nor sways. The joint pulls on the column a3 of A with the
+    generalized force l m g, which the orthogonality term h^2 kappa_A V |A A^T - I|^2 balances at
+    A = diag(1, 1, 1 + eps), 8 kappa_A V eps = l m g: the centre hangs l eps lower still."""
+    k, a, l = 1e3, 0.02, 0.1
+    p = S.scene_params(0.01, newton_tol=1e-6)
+    env = S.pendulum_env(k_joint=k, n_steps=200, arm=l, half=a / 2)
+    e = O.OracleEnv(p, env)
+    m, V = 1000.0 * a ** 3, a ** 3
+    assert e.step(200) == "DONE"
+    x, _ = e.state()
+    sag = m * G / k
+    eps = l * m * G / (8.0 * p["kappa_affine"] * V)
+    assert abs(_bob_com(x)[2] - (-l - sag - l * eps)) <= 3e-4 * sag
+    assert np.abs(_bob_com(x)[:2]).max() < 1e-12
+    A = x[15:24].reshape(3, 3).T
+    assert abs(A[2, 2] - (1.0 + eps)) <= 1e-2 * eps
+    assert np.abs(A - np.diag([1.0, 1.0, A[2, 2]])).max() < 1e-12
+
+
+def test_pendulum_swings_with_the_compound_pendulum_period():
+    """Released at 0.05 rad, the jointed cube swings about the joint with the small-amplitude
+    period of a compound pendulum, 2 pi sqrt(I_p / (m g l)), I_p = m a^2 / 6 + m l^2 (cube of
+    side a, centre l below the joint), within 0.5% (implicit Euler at h omega = 0.02 shifts the
+    period by far less; the joint's stretch m g / k lengthens l by 1e-5 relative)."""
+    dt, n = 0.002, 700
+    p = S.scene_params(dt)
+    env = S.pendulum_env(k_joint=1e5, n_steps=n, theta0=0.05)
+    e = O.OracleEnv(p, env)
+    ys = []
+    for _ in range(n):
+        e.step(1)
+        ys.append(_bob_com(e.state()[0])[1])
+    ys = np.array(ys)
+    t = (np.arange(n) + 1) * dt
+    # zero crossings of the sideways position, by linear interpolation
+    z = [t[i] - ys[i] * (t[i + 1] - t[i]) / (ys[i + 1] - ys[i]) for i in range(n - 1) if ys[i] * ys[i + 1] < 0]
+    assert len(z) >= 3
+    period = 2.0 * (z[2] - z[0]) / 2.0
+    a, l = 0.02, 0.1
+    T = 2 * math.pi * math.sqrt((a * a / 6 + l * l) / (G * l))
+    assert abs(period / T - 1.0) < 5e-3, (period, T)
+    # the swing stays in the y-z plane and the cube keeps its shape
+    xs, _ = e.state()
+    assert abs(_bob_com(xs)[0]) < 1e-12
+    A = xs[15:24].reshape(3, 3).T
+    assert np.abs(A @ A.T - np.eye(3)).max() < 1e-5  # affine stiffness keeps A near a rotation
+
+
+def test_env_gradient_and_hessian_fd_joint_term():
+    """The joint potential's gradient and Hessian against central differences at a state where
+    the joint is stretched and turned (no contacts; the joint term is quadratic, so its
+    Hessian is exact and unprojected)."""
+    p = S.scene_params(0.01)
+    env = S.pendulum_env(k_joint=3e3, n_steps=10, theta0=0.3)
+    e = O.OracleEnv(p, env)
+    e.step(2)
+    x, _ = e.state()
+    q = x.copy()
+    q[12:15] += np.array([2e-3, -1e-3, 3e-3])
+    _fd_check(e, q, list(range(24)))
+    H = e.hessian(q)
+    Hf = _fd_hessian(e, q, range(12, 24))
+    assert np.abs(H[:, 12:24] - Hf).max() <= 1e-6 * np.abs(H).max()

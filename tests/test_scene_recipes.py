@@ -52,15 +52,26 @@ def test_pad_grasp_recipe_and_seed_ranges():
 
 def test_hand_grasp_recipe():
     """Rigid hand of 20 PD-driven affine links of about 500 triangles each, grasping a star-shaped
-    soft object of about 20k tets with E log-uniform over [1e4, 1e6] Pa and nu U(0.3, 0.48)."""
+    soft object of about 20k tets with E log-uniform over [1e4, 1e6] Pa and nu U(0.3, 0.48). The
+    links hang from a kinematic palm in five chains of four, one hinge (two point joints on the
+    finger's bending axis) between neighbours; every joint's anchors coincide at the start."""
     for k in range(2):
         env = S.hand_grasp_env(k)
-        obj, links = env["soft"][0], env["affine"]
+        obj, links, palm = env["soft"][0], env["affine"][:20], env["affine"][20]
         assert 18_000 <= len(obj["tets"]) <= 24_000
         assert 1e4 <= obj["E"] <= 1e6 and 0.3 <= obj["nu"] <= 0.48
-        assert len(links) == 20 and all(450 <= len(a["tris"]) <= 550 for a in links)
-        assert all(a["pd"] > 0 and not a["kinematic"] for a in links)
+        assert len(env["affine"]) == 21 and all(450 <= len(a["tris"]) <= 550 for a in links)
+        assert all(a["pd"] > 0 and not a["kinematic"] for a in links) and palm["kinematic"]
         assert len(env["targets"]) == 400 and np.all(env["gravity"][:200] == 0) and np.all(env["gravity"][200:] == 1)
+        J = env["joints"]
+        assert len(J) == 40 and sorted((j["a"], j["b"]) for j in J) == sorted(
+            [(20, 4 * f) for f in range(5)] * 2 + [(4 * f + i, 4 * f + i + 1) for f in range(5) for i in range(3)] * 2)
+
+        def world(b, xb):
+            q = env["affine"][b]["q0"]
+            return q[:3] + xb[0] * q[3:6] + xb[1] * q[6:9] + xb[2] * q[9:12]
+
+        assert max(np.linalg.norm(world(j["a"], j["anchor_a"]) - world(j["b"], j["anchor_b"])) for j in J) < 1e-12
 
 
 def test_request_schedule_closes_lifts_and_shakes_15_degrees_at_2_hz():
