@@ -94,8 +94,9 @@ def parse():
     ap.add_argument("--plain-envs", type=int, default=16, help="envs of the one-env-at-a-time leg (0: none)")
     ap.add_argument("--ref-envs", type=int, default=16, help="envs of the converged FP64 reference (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: none)")
-    ap.add_argument("--serve-rate", type=float, default=1.5, help="Poisson arrival rate of the serving leg (1/s)")
+    ap.add_argument("--serve-requests", type=int, default=12, help="requests per arrival rate of the serving leg (0: none)")
+    ap.add_argument("--serve-rates", default="0.2,2,20", help="Poisson arrival rates of the serving leg (1/s)")
+    ap.add_argument("--serve-ref", type=int, default=3, help="requests of the serving leg's converged FP64 reference")
     ap.add_argument("--no-mixed-leg", action="store_true",
                     help="skip the mixed-precision run of the same steps that the FP64 line reports beside it")
     ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle time for --impl reference")
@@ -310,6 +311,18 @@ def timed_steps(sc, stream, k):
     return e0.elapsed_time(e1)
 
 
+def guarded(leg, *a):
+    """Run one secondary leg of the line; an error in it is recorded in its place (the headline
+    measurement already taken stays valid and is still printed)."""
+    try:
+        return leg(*a)
+    except Exception as ex:  # noqa: BLE001 - reported in the line, not swallowed
+        import traceback
+
+        traceback.print_exc()
+        return {"error": f"{type(ex).__name__}: {ex}"}
+
+
 def run_ours(args):
     import torch
 
@@ -373,17 +386,22 @@ def run_ours(args):
         sc.set_state(eid, x, v, st)
     n_all = sc.all_dofs_size()
     h_out = torch.empty(n_all, dtype=torch.float64, pin_memory=True).numpy()
-    tg_all = []
-    for k in range(args.steps):
-        tg_all.append(np.concatenate([env["targets"][min(st + k, len(env["targets"]) - 1)].reshape(-1)
-                                      for env, (_, _, st) in zip(envs, snap)]))
-    h_tg = torch.empty(len(tg_all[0]), dtype=torch.float64, pin_memory=True).numpy()
+    # the next targets of every env for each step (the API takes those of the envs still active)
+    rows = [[env["targets"][min(st + k, len(env["targets"]) - 1)].reshape(-1) for env, (_, _, st) in zip(envs, snap)]
+            for k in range(args.steps)]
+    h_tg = torch.empty(sum(len(r) for r in rows[0]), dtype=torch.float64, pin_memory=True).numpy()
+    h2d = 0
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
     for k in range(args.steps):
-        h_tg[:] = tg_all[k]
-        sc.set_next_targets(h_tg)
+        st = sc.all_status()
+        live = [r for eid, r in zip(ids, rows[k]) if st[eid][0] == "ACTIVE"]
+        n = sum(len(r) for r in live)
+        if n:
+            h_tg[:n] = np.concatenate(live)
+            sc.set_next_targets(h_tg[:n])
+        h2d += 8 * n
         sc.step(1)
         sc.all_dofs(h_out)
     torch.cuda.synchronize()
@@ -398,10 +416,10 @@ def run_ours(args):
     tets = [sum(len(s["tets"]) for s in e["soft"]) for e in envs]
     plain = mixed = None
     if world == 1 and args.plain_envs > 0:
-        plain = plain_leg(args, params, envs, snap, tets, stream, local, value)
+        plain = guarded(plain_leg, args, params, envs, snap, tets, stream, local, value)
     if world == 1 and args.precision == "fp64" and not args.no_mixed_leg:
-        mixed = mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, local, t_max / args.steps)
-        if plain:
+        mixed = guarded(mixed_leg, args, params, envs, snap, p_start, x_end, tets, stream, local, t_max / args.steps)
+        if plain and "value" in plain and "value" in mixed:
             plain["mixed_batched_over_plain"] = round(mixed["value"] / plain["value"], 2)
 
     if rank != 0:
@@ -432,17 +450,21 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic", "config": wl.config(len(envs), int(np.mean(tets)), world),
         "roofline": roof, "cpu_baseline": cpu,
-        "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h_tg.nbytes),
+        "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d // max(args.steps, 1)),
                 "d2h_bytes_per_step": int(h_out.nbytes)},
         "gpu_launches": int(launches), "clocks": clk, "plain_fp64": plain, "mixed_precision": mixed, "serving": None,
         "env_steps_done": int(steps_done), "envs_failed": int(failed),
-        "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k != "pcg_flops"},
+        "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k not in ("pcg_flops", "host_idle")},
+        "host_round_trips": {"count": int(prof["host_idle"]["launches"]), "gpu_idle_ms": round(prof["host_idle"]["ms"], 2),
+                             "gpu_idle_frac": round(prof["host_idle"]["ms"] / t_max, 4) if t_max > 0 else None,
+                             "note": "GPU idle time behind the host reads inside the timed ipc_step call: events "
+                                     "before each wait and at the next kernel launch, on the scene's stream"},
         "counters_last_iteration": counters,
         "newton_iters_per_env_step": round(newton / max(sum(s["steps"] for s in stats), 1), 2),
         "pcg_iters_per_newton": round(pcg_its / max(newton, 1), 1),
     }
     if world == 1 and args.serve_requests > 0:
-        line["serving"] = serving_leg(args, params, local)
+        line["serving"] = guarded(serving_leg, args, params, local)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -534,7 +556,7 @@ def mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, device, ms
            "vs_fp64": errors(x_mixed, x_end, rows),
            "dtype": "f32 Hessians + PCG, f64 energies/gradients/barrier/CCD/line search",
            "roofline": roofline(prof, "mixed"),
-           "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k != "pcg_flops"}}
+           "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k not in ("pcg_flops", "host_idle")}}
     if args.ref_envs > 0:
         sel = stratified(tets, args.ref_envs)
         pr = dict(params, pcg_rel_tol=1e-10, newton_tol=params["newton_tol"] * 1e-2, max_pcg=20000)
@@ -563,29 +585,74 @@ def object_points(env):
     return np.arange(o, o + len(env["affine"][k]["verts"]))
 
 
+SERVE_BUDGET = 180 * 10 ** 9  # HBM admission budget of the serving configuration (bytes)
+
+
 def serving_leg(args, params, device):
-    """Grasp-evaluation serving: a seeded Poisson stream of requests (one pad grasp each: close,
-    lift 0.1 m, shake +/-15 deg at 2 Hz; 200 steps; seeded objects of uneven size) served by
-    continuous batching on one device-resident scene, in FP64 and in mixed precision."""
+    """Grasp-evaluation serving (the serving configuration): seeded Poisson streams of requests,
+    each the plate squeeze or the soft-pad grasp of a soft object of log-uniform 1k-100k tets
+    (close, lift 5 cm, shake +/-15 deg at 2 Hz, hold still; 200 steps), served by continuous
+    batching on one device-resident scene admitted under a 180 GB HBM budget, at several arrival
+    rates, in FP64 and in mixed precision. Per rate: throughput, p50/p99 latency and queue wait.
+    Per request: the stability label of Sec. III-D at its last step, in both precisions; and, on a
+    subset, the final object points of both precisions against a converged FP64 run of the same
+    requests. A request's result does not depend on the rate (each env does exactly the work it
+    does alone), so labels and points are taken from the first rate."""
     from paper_2503_05020_b300 import ipc
-    from paper_2503_05020_b300.serve import GraspServer, Request, poisson_arrivals
+    from paper_2503_05020_b300.serve import GraspServer, Request, object_points, poisson_arrivals
 
     n = args.serve_requests
-    envs = [S.grasp_request_env(5000 + i) for i in range(n)]
-    arrivals = poisson_arrivals(args.serve_rate, n, 20250306)
-    out = {"requests": n, "rate_req_s": args.serve_rate, "steps_per_request": len(envs[0]["targets"]),
-           "request": "pad grasp: close 80 steps, lift 0.1 m in 60, shake +/-15 deg at 2 Hz for 60; dt 5 ms"}
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    envs = [S.serving_request_env(i) for i in range(n)]
+    tets = [sum(len(s["tets"]) for s in e["soft"]) for e in envs]
+    out = {"requests_per_rate": n, "rates_req_s": rates, "steps_per_request": len(envs[0]["targets"]),
+           "hbm_budget_bytes": SERVE_BUDGET, "object_tets": [min(tets), max(tets)],
+           "request": "plate squeeze or soft-pad grasp of a soft object (log-uniform 1k-100k tets): close 70 "
+                      "steps, lift 5 cm in 50, shake +/-15 deg at 2 Hz for 60, hold 20; dt 5 ms",
+           "per_rate": {}}
+    results = {}
     for name, prec in (("fp64", ipc.FP64), ("mixed", ipc.MIXED)):
-        reqs = [Request(i, e, t) for i, (e, t) in enumerate(zip(envs, arrivals))]
-        srv = GraspServer(params, precision=prec, device=device, max_envs=64, admit_period=8, steps_per_call=8)
-        rep = srv.run(reqs)
-        held = [bool(r.result.get("held")) for r in reqs]
-        out[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rep.items()}
-        out[name]["held"] = int(sum(held))
-        out.setdefault("held_labels", {})[name] = held
-        del srv
-    lab = out.pop("held_labels")
-    out["grasp_labels_agree"] = lab["fp64"] == lab["mixed"]
+        for k, rate in enumerate(rates):
+            reqs = [Request(i, e, t) for i, (e, t) in enumerate(zip(envs, poisson_arrivals(rate, n, 20250306)))]
+            srv = GraspServer(params, precision=prec, device=device, hbm_budget_bytes=SERVE_BUDGET, max_envs=1024,
+                              admit_period=8, steps_per_call=8)
+            rep = srv.run(reqs)
+            rec = {kk: (round(v, 4) if isinstance(v, float) else v) for kk, v in rep.items()}
+            rec["stable"] = int(sum(bool(r.result.get("stable")) for r in reqs))
+            out["per_rate"].setdefault(str(rate), {})[name] = rec
+            if k == 0:
+                results[name] = {r.rid: r.result for r in reqs}
+            srv.scene.close()
+    lab = {nm: [bool(results[nm][i].get("stable")) for i in range(n)] for nm in results}
+    out["stable_labels"] = lab
+    out["labels_agree"] = lab["fp64"] == lab["mixed"]
+    hi = str(rates[-1])
+    out["mixed_over_fp64_throughput"] = round(out["per_rate"][hi]["mixed"]["env_steps_s"]
+                                              / out["per_rate"][hi]["fp64"]["env_steps_s"], 3)
+    # converged FP64 reference of a subset: its final object points against both precisions,
+    # relative to the object's largest point displacement over the request
+    sub = stratified(tets, min(args.serve_ref, n))
+    pr = dict(params, pcg_rel_tol=1e-10, newton_tol=params["newton_tol"] * 1e-2, max_pcg=20000)
+    sc = ipc.Scene(pr, precision=ipc.FP64, device=device)
+    ids = [sc.add_env(envs[i]) for i in sub]
+    sc.step(len(envs[0]["targets"]))
+    from paper_2503_05020_b300.serve import initial_points
+
+    err = {"fp64": 0.0, "mixed": 0.0}
+    err_all = {"fp64": 0.0, "mixed": 0.0}
+    for eid, i in zip(ids, sub):
+        ref = sc.points(eid)
+        sl = object_points(envs[i])
+        disp = float(np.abs(ref[sl] - initial_points(envs[i])[sl]).max())
+        disp_all = float(np.abs(ref - initial_points(envs[i])).max())
+        for nm in err:
+            pts = results[nm][i]["points"]
+            err[nm] = max(err[nm], float(np.abs(pts[sl] - ref[sl]).max()) / disp)
+            err_all[nm] = max(err_all[nm], float(np.abs(pts - ref).max()) / disp_all)
+    sc.close()
+    out["vs_converged_fp64"] = {"requests": sub, "rel_object_points": err, "rel_all_points": err_all,
+                                "note": "largest point difference at the request's end over the largest point "
+                                        "displacement of the converged run (PCG 1e-10, Newton tolerance x1e-2)"}
     return out
 
 

@@ -83,6 +83,9 @@ typedef struct {
                             -(g_E . G) / (G . G), clamped to [kappa, 1000 kappa], and held for
                             the rest of the step */
   void* cuda_stream;     /* cudaStream_t to borrow, or NULL for a library-owned stream */
+  int32_t collect_slots; /* partners a collect traversal keeps per query (0 = 128; 1..4096); a
+                            query with more sends the pass to a count-then-fill traversal, with the
+                            same candidates in the same order */
 } ipc_scene_desc;
 
 /* Soft body: a Neo-Hookean tet mesh. verts: n_verts*3 doubles (rest = initial positions);
@@ -160,12 +163,13 @@ typedef enum {
   IPC_Q_SIZES = 7,       /* int64[8]: ndof, points, surface vertices, edges, triangles, tets,
                             bodies, steps */
   IPC_Q_INTERSECTIONS = 8, /* int64[2]: segment-triangle intersections, inverted tets */
-  IPC_Q_SCENE_COUNTERS = 9, /* int64[10] for the whole scene (env_id ignored), from the last Newton
+  IPC_Q_SCENE_COUNTERS = 9, /* int64[12] for the whole scene (env_id ignored), from the last Newton
                               iteration: contacts, point-triangle contacts, friction stencils,
                               stencil-node incidence entries, longest node incidence list,
                               candidates, BSR blocks, sliced-ELL padded blocks; then the PCG
-                              cluster size in use (0 = tiled multi-launch PCG) and the most
-                              32-row slices of one environment */
+                              cluster size in use (0 = tiled multi-launch PCG), the most 32-row
+                              slices of one environment, the point joints of the batch and the
+                              collect traversal passes that spilled since the scene was made */
   IPC_Q_ALL_STATUS = 10,   /* int32[4 * n_env] for the whole scene (env_id ignored): env id,
                               status, failure reason, next step of every environment, in one
                               read-back (a serving loop polls this once per step) */
@@ -294,7 +298,11 @@ typedef enum {
   IPC_PROF_PCG_SOLVE = 8,   /* persistent per-environment PCG (work: algorithmic bytes) */
   IPC_PROF_PCG_FLOPS = 9,   /* work only: floating-point operations of the persistent PCG (an FMA
                                counts 2); its launches and time are those of IPC_PROF_PCG_SOLVE */
-  IPC_PROF_COUNT = 10
+  IPC_PROF_HOST_IDLE = 10,  /* host round trips inside ipc_step (a count or flag read back before
+                               the next launch): "launches" counts them and the time is the GPU's
+                               idle time from the end of the work before each wait to the next
+                               kernel launch (events on the scene's stream) */
+  IPC_PROF_COUNT = 11
 } ipc_prof_family;
 /* Turn profiling on (1) or off (0); turning it on clears the counters. */
 ipc_status ipc_profile_enable(ipc_scene* scene, int32_t on);

@@ -1686,6 +1686,41 @@ int or_env_contact_forces(void* h, const double* q, double* out, int cap) {
   }
   return n;
 }
+// Bodies of the two sides of every contact at q, in or_env_contacts' order (env-local handles:
+// soft bodies first, then affine bodies): the point's and the triangle's, or the two edges'.
+int or_env_contact_bodies(void* h, const double* q, int32_t* out, int cap) {
+  Env* e = (Env*)h;
+  std::vector<double> px;
+  point_positions(*e, q, px);
+  std::vector<std::array<int, 3>> cands;
+  candidates(*e, px, nullptr, 0.5 * e->P.dhat, cands);
+  std::sort(cands.begin(), cands.end());
+  int n = 0;
+  for (auto& c : cands) {
+    int pts[4];
+    cand_points(*e, c, pts);
+    double x12[12];
+    gather12(px, pts, x12);
+    if (!(pair_dist2(c[0], x12) < e->P.dhat * e->P.dhat)) continue;
+    if (n < cap) {
+      out[2 * n] = e->pts[pts[0]].body;
+      out[2 * n + 1] = e->pts[pts[c[0] == 0 ? 1 : 2]].body;
+    }
+    ++n;
+  }
+  return n;
+}
+// Rewrite rows first .. first + n - 1 of the env's schedule of kinematic targets (n rows of
+// (soft + affine bodies) x 12 values); rows outside the schedule are ignored.
+void or_env_set_targets(void* h, int first, int n, const double* targets) {
+  Env* e = (Env*)h;
+  const size_t row = (size_t)e->n_handles * 12;
+  for (int r = 0; r < n; ++r) {
+    const int s = first + r;
+    if (s < 0 || s >= e->n_steps) continue;
+    std::copy(targets + r * row, targets + (r + 1) * row, e->targets.begin() + s * row);
+  }
+}
 // Tangential force of every lagged friction stencil of the current (or last) step at DOFs q:
 // mu lambda f1(|u|), u the tangential relative displacement since the step start (N).
 int or_env_friction_forces(void* h, const double* q, double* out, int cap) {

@@ -59,6 +59,8 @@ def lib():
         L.or_env_kappa.argtypes = [vp]
         L.or_env_tet_stress.argtypes = [vp, vp, vp]
         L.or_env_contact_forces.argtypes = [vp, vp, vp, C.c_int]
+        L.or_env_contact_bodies.argtypes = [vp, vp, vp, C.c_int]
+        L.or_env_set_targets.argtypes = [vp, C.c_int, C.c_int, vp]
         L.or_env_friction_forces.argtypes = [vp, vp, vp, C.c_int]
         L.or_env_trace_get.argtypes = [vp, vp, C.c_int]
         L.or_env_body_mass.argtypes = [vp, C.c_int, vp, vp]
@@ -213,6 +215,20 @@ class OracleEnv:
         out = np.zeros(max(n, 1))
         lib().or_env_contact_forces(self.h, _p(q), _p(out), n)
         return out[:n]
+
+    def contact_bodies(self, q) -> np.ndarray:
+        """Body handles (soft bodies first, then affine) of the two sides of every contact at q,
+        in the order of contacts(q)."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        n = lib().or_env_contact_bodies(self.h, _p(q), None, 0)
+        out = np.zeros((max(n, 1), 2), dtype=np.int32)
+        lib().or_env_contact_bodies(self.h, _p(q), _p(out), n)
+        return out[:n]
+
+    def set_targets(self, first_step: int, targets) -> None:
+        """Rewrite the schedule rows first_step .. first_step + len(targets) - 1."""
+        t = np.ascontiguousarray(targets, dtype=np.float64)
+        lib().or_env_set_targets(self.h, first_step, len(t), _p(t))
 
     def friction_forces(self, q) -> np.ndarray:
         """Tangential force (N) of every lagged friction stencil of the last step at DOFs q."""

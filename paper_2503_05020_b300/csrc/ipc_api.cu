@@ -521,7 +521,7 @@ struct ipc_scene {
   // candidates / contacts
   DBuf<int> cnt_pt, off_pt, cnt_ee, off_ee, cand_j, cand_q, nflag, noff, scan_tmp, overflow;
   DBuf<int> ccd_cnt_pt, ccd_off_pt, ccd_cnt_ee, ccd_off_ee, ccd_j, ccd_q;  // swept-box candidates
-  DBuf<int> slots_pt, slots_ee;  // partner slots of collect traversals (CAND_CAP per query)
+  DBuf<int> slots_pt, slots_ee;  // partner slots of collect traversals (cand_cap() per query)
   DBuf<ContactRec> ct_tmp, ct, cand_rec, ccd_rec;  // contacts; pair records of the two lists
   DBuf<FrictionRec> fr, fr_new, fr_tmp;
   DBuf<unsigned long long> fr_keys, fr_keys2;
@@ -621,6 +621,7 @@ struct ipc_scene {
   template <class K, class... Args>
   void launch(K kern, long n_threads, int block, Args... args) {
     if (n_threads <= 0) return;
+    mark_resume();
     long grid = (n_threads + block - 1) / block;
     kern<<<(unsigned)grid, block, 0, stream>>>(args...);
     if (capturing) ++captured_kernels;
@@ -630,19 +631,41 @@ struct ipc_scene {
   template <class K, class... Args>
   void launch_grid(K kern, long grid, int block, Args... args) {
     if (grid <= 0) return;
+    mark_resume();
     kern<<<(unsigned)grid, block, 0, stream>>>(args...);
     if (capturing) ++captured_kernels;
     else ++launches;
     CK(cudaGetLastError());
   }
+  // A host round trip inside the stepping loop (a count or flag the host needs before its next
+  // launch). With profiling on, an event recorded behind the work before the wait and one recorded
+  // at the next kernel launch bound the time the GPU sat idle because of it (family
+  // IPC_PROF_HOST_IDLE).
+  cudaEvent_t idle_from = nullptr;
+  void host_sync() {
+    if (prof_on && !capturing) {
+      if (idle_from) ev_pool.push_back(idle_from);
+      idle_from = take_event();
+      CK(cudaEventRecord(idle_from, stream));
+    }
+    CK(cudaStreamSynchronize(stream));
+  }
+  void mark_resume() {
+    if (!idle_from) return;
+    cudaEvent_t e = take_event();
+    CK(cudaEventRecord(e, stream));
+    prof_ev[IPC_PROF_HOST_IDLE].push_back({idle_from, e});
+    prof_launches[IPC_PROF_HOST_IDLE]++;
+    idle_from = nullptr;
+  }
   void read_ints(const int* dptr, int* out, int n) {
     CK(cudaMemcpyAsync(hpin, dptr, n * sizeof(int), cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
+    host_sync();
     for (int i = 0; i < n; ++i) out[i] = hpin[i];
   }
   int read_int(const int* dptr) {
     CK(cudaMemcpyAsync(hpin, dptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
+    host_sync();
     return *hpin;
   }
   int count_flags(const uint8_t* f) {
@@ -1170,13 +1193,16 @@ struct ipc_scene {
   // traversal had a query with more partners than its slots
   bool collect_spilled() {
     CK(cudaMemcpyAsync(hpin, overflow.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
+    host_sync();
     const int stack = hpin[0], spill = hpin[1];
     if (stack || spill) overflow.zero(stream);
     if (stack) fail_with(IPC_ERR_INTERNAL, "BVH traversal stack overflow");
     return spill != 0;
   }
-  static constexpr int CAND_CAP = CAND_SLOTS;
+  // partner slots per query of a collect traversal (a scene option; more partners send the pass
+  // to a count-then-fill traversal)
+  int cand_cap() const { return desc.collect_slots > 0 ? desc.collect_slots : CAND_SLOTS; }
+  long long spills = 0;  // collect passes that spilled into a fill traversal
   // the candidate totals of a pair of collect traversals (the last entries of their offset
   // scans) and the traversal flags, in one read-back; fails on a stack overflow, returns
   // whether a query had more partners than its slots
@@ -1184,12 +1210,13 @@ struct ipc_scene {
     CK(cudaMemcpyAsync(hpin, tot_pt, sizeof(int), cudaMemcpyDeviceToHost, stream));
     CK(cudaMemcpyAsync(hpin + 1, tot_ee, sizeof(int), cudaMemcpyDeviceToHost, stream));
     CK(cudaMemcpyAsync(hpin + 2, overflow.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
+    host_sync();
     *np = hpin[0];
     *ne = hpin[1];
     const int stack = hpin[2], spill = hpin[3];
     if (stack || spill) overflow.zero(stream);
     if (stack) fail_with(IPC_ERR_INTERNAL, "BVH traversal stack overflow");
+    spills += spill != 0;
     return spill != 0;
   }
 
@@ -1198,16 +1225,16 @@ struct ipc_scene {
   void constraint_set(const uint8_t* act) {
     double r = 0.5 * desc.dhat;
     boxes_and_refit(nullptr, r);
-    // one traversal per query kind keeps up to CAND_CAP partners per query (edge-edge queries
+    // one traversal per query kind keeps up to cand_cap() partners per query (edge-edge queries
     // on fine surfaces find a few dozen non-adjacent neighbours); a fill traversal
     // runs only if some query found more
-    slots_pt.ensure((size_t)NSV * CAND_CAP + 1);
-    slots_ee.ensure((size_t)NED * CAND_CAP + 1);
-    CandOut o{cnt_pt.p, nullptr, slots_pt.p, overflow.p, CAND_CAP};
+    slots_pt.ensure((size_t)NSV * cand_cap() + 1);
+    slots_ee.ensure((size_t)NED * cand_cap() + 1);
+    CandOut o{cnt_pt.p, nullptr, slots_pt.p, overflow.p, cand_cap()};
     pbeg(IPC_PROF_BROAD);
     launch(k_trav_pt<TRAV_COLLECT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
            (const double*)ptx.p, (const double*)nullptr, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), o);
-    CandOut oe{cnt_ee.p, nullptr, slots_ee.p, overflow.p, CAND_CAP};
+    CandOut oe{cnt_ee.p, nullptr, slots_ee.p, overflow.p, cand_cap()};
     launch(k_trav_ee<TRAV_COLLECT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
            (const double*)tedge.pbox.p, tree(tedge), ptinfo(), oe);
     pend(IPC_PROF_BROAD);
@@ -1225,9 +1252,9 @@ struct ipc_scene {
       launch(k_trav_ee<TRAV_FILL>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
              (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe);
     } else {
-      launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)cnt_pt.p, (const int*)slots_pt.p,
+      launch(k_gather_cands, NSV, 256, NSV, cand_cap(), (const int*)cnt_pt.p, (const int*)slots_pt.p,
              (const int*)off_pt.p, cand_j.p, cand_q.p, 1);
-      launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)cnt_ee.p, (const int*)slots_ee.p,
+      launch(k_gather_cands, NED, 256, NED, cand_cap(), (const int*)cnt_ee.p, (const int*)slots_ee.p,
              (const int*)off_ee.p, cand_j.p + n_pt, cand_q.p + n_pt, 1);
     }
     cand_rec.ensure(nc + 1);
@@ -1250,7 +1277,7 @@ struct ipc_scene {
     // the contacts' count and the point-triangle part of it, in one read-back
     CK(cudaMemcpyAsync(hpin, noff.p + np, sizeof(int), cudaMemcpyDeviceToHost, stream));
     CK(cudaMemcpyAsync(hpin + 1, noff.p + nc, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
+    host_sync();
     n_ct_pt = hpin[0];
     n_ct = hpin[1];
     ct.ensure(n_ct + 1);
@@ -1577,6 +1604,7 @@ struct ipc_scene {
     cfg.stream = stream;
     cfg.attrs = &at;
     cfg.numAttrs = 1;
+    mark_resume();
     CK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<C, T>, a));
     ++launches;
   }
@@ -1841,14 +1869,14 @@ struct ipc_scene {
     ccd_off_pt.ensure(NSV + 1);
     ccd_cnt_ee.ensure(NED + 1);
     ccd_off_ee.ensure(NED + 1);
-    slots_pt.ensure((size_t)NSV * CAND_CAP + 1);
-    slots_ee.ensure((size_t)NED * CAND_CAP + 1);
+    slots_pt.ensure((size_t)NSV * cand_cap() + 1);
+    slots_ee.ensure((size_t)NED * cand_cap() + 1);
     ccd_np = ccd_ne = 0;
     list_ok = false;
-    CandOut cp{ccd_cnt_pt.p, nullptr, slots_pt.p, overflow.p, CAND_CAP};
+    CandOut cp{ccd_cnt_pt.p, nullptr, slots_pt.p, overflow.p, cand_cap()};
     launch(k_trav_pt<TRAV_COLLECT>, NSV, 128, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act,
            (const double*)ptx.p, (const double*)pte.p, r, tree(ttri), (const int*)tri_pt.p, ptinfo(), cp);
-    CandOut ce{ccd_cnt_ee.p, nullptr, slots_ee.p, overflow.p, CAND_CAP};
+    CandOut ce{ccd_cnt_ee.p, nullptr, slots_ee.p, overflow.p, cand_cap()};
     launch(k_trav_ee<TRAV_COLLECT>, NED, 128, NED, (const int*)ed_pt.p, (const int*)ed_env.p, act,
            (const double*)tedge.pbox.p, tree(tedge), ptinfo(), ce);
     scan(ccd_cnt_pt.p, NSV, ccd_off_pt.p, false);
@@ -1875,9 +1903,9 @@ struct ipc_scene {
                  (const double*)tedge.pbox.p, tree(tedge), ptinfo(), fe);
         }
       } else {
-        launch(k_gather_cands, NSV, 256, NSV, CAND_CAP, (const int*)ccd_cnt_pt.p, (const int*)slots_pt.p,
+        launch(k_gather_cands, NSV, 256, NSV, cand_cap(), (const int*)ccd_cnt_pt.p, (const int*)slots_pt.p,
                (const int*)ccd_off_pt.p, ccd_j.p, ccd_q.p, keep ? 1 : 0);
-        launch(k_gather_cands, NED, 256, NED, CAND_CAP, (const int*)ccd_cnt_ee.p, (const int*)slots_ee.p,
+        launch(k_gather_cands, NED, 256, NED, cand_cap(), (const int*)ccd_cnt_ee.p, (const int*)slots_ee.p,
                (const int*)ccd_off_ee.p, ccd_j.p + np, ccd_q.p + np, keep ? 1 : 0);
       }
     }
@@ -2106,6 +2134,7 @@ ipc_status ipc_scene_create(const ipc_scene_desc* desc, ipc_scene** out) {
   if (!desc || !out) fail_with(IPC_ERR_ARG, "null argument");
   if (!(desc->dt > 0) || !(desc->dhat > 0) || !(desc->kappa > 0)) fail_with(IPC_ERR_ARG, "dt, dhat and kappa must be > 0");
   if (desc->precision != IPC_FP64 && desc->precision != IPC_MIXED) fail_with(IPC_ERR_ARG, "unknown precision");
+  if (desc->collect_slots < 0 || desc->collect_slots > 4096) fail_with(IPC_ERR_ARG, "collect_slots must be 0..4096");
   {
     int c = desc->pcg_cluster;
     if (c != -1 && c != 0 && c != 1 && c != 2 && c != 4 && c != 8 && c != 16)
@@ -2419,8 +2448,8 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       CK(cudaMemcpy(ptr.data(), s->ns_ptr.p, (s->NN + 1) * 4, cudaMemcpyDeviceToHost));
       long long mx = 0;
       for (int i = 0; i < s->NN; ++i) mx = std::max(mx, (long long)(ptr[i + 1] - ptr[i]));
-      long long v[10] = {s->n_ct, s->n_ct_pt, s->n_fr, s->n_inc, mx, (long long)s->n_pt + s->n_ee, s->NNZB,
-                         s->sell_nval / 288, s->pcg_C, s->max_env_slices};
+      long long v[12] = {s->n_ct, s->n_ct_pt, s->n_fr, s->n_inc, mx, (long long)s->n_pt + s->n_ee, s->NNZB,
+                         s->sell_nval / 288, s->pcg_C, s->max_env_slices, s->n_jt, s->spills};
       return copy_out(v, sizeof(v), out, out_bytes, written);
     }
     case IPC_Q_SIZES: {
@@ -2579,6 +2608,8 @@ ipc_status ipc_profile_enable(ipc_scene* s, int32_t on) {
   s->prof_units.ensure(IPC_PROF_COUNT);
   s->prof_units.zero(s->stream, IPC_PROF_COUNT);
   CK(cudaStreamSynchronize(s->stream));
+  if (s->idle_from) s->ev_pool.push_back(s->idle_from);
+  s->idle_from = nullptr;  // a wait before profiling started is not counted
   s->prof_on = on != 0;
   API_END
 }

@@ -38,7 +38,7 @@ class SceneDesc(C.Structure):
                 ("gravity", C.c_double * 3), ("max_newton", C.c_int32), ("max_ls_halvings", C.c_int32),
                 ("max_pcg_iters", C.c_int32), ("precision", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
                 ("device", C.c_int32), ("pcg_cluster", C.c_int32), ("fresh_broad_phase", C.c_int32),
-                ("kappa_adapt", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("kappa_adapt", C.c_int32), ("cuda_stream", C.c_void_p), ("collect_slots", C.c_int32)]
 
 
 class SoftDesc(C.Structure):
@@ -166,7 +166,8 @@ class Scene:
     """A batch of grasp environments stepped together on one GPU."""
 
     def __init__(self, params: dict, precision: int = FP64, device: int = 0, stream: int | None = None,
-                 hbm_budget_bytes: int = 0, pcg_cluster: int = 0, fresh_broad_phase: bool = False):
+                 hbm_budget_bytes: int = 0, pcg_cluster: int = 0, fresh_broad_phase: bool = False,
+                 collect_slots: int = 0):
         d = SceneDesc()
         d.dt, d.dhat, d.kappa, d.eps_v = params["dt"], params["dhat"], params["kappa"], params["eps_v"]
         d.newton_tol, d.pcg_rel_tol, d.kappa_affine = params["newton_tol"], params["pcg_rel_tol"], params["kappa_affine"]
@@ -178,6 +179,7 @@ class Scene:
         d.fresh_broad_phase = int(bool(fresh_broad_phase))  # 1: a BVH traversal at every evaluation
         d.kappa_adapt = int(bool(params.get("kappa_adapt", False)))  # 1: adapted barrier stiffness per env
         d.cuda_stream = stream
+        d.collect_slots = collect_slots  # partner slots per collect-traversal query (0: 128)
         self._h = C.c_void_p()
         _check(lib().ipc_scene_create(C.byref(d), C.byref(self._h)))
         self.params = dict(params)
@@ -247,7 +249,7 @@ class Scene:
     def scene_counters(self, eid: int) -> dict:
         v = self._query(eid, Q_SCENE_COUNTERS, np.int64)
         keys = ["contacts", "pt_contacts", "friction", "incidence_entries", "longest_list", "candidates",
-                "bsr_blocks", "sell_blocks", "pcg_cluster", "max_env_slices"]
+                "bsr_blocks", "sell_blocks", "pcg_cluster", "max_env_slices", "joints", "collect_spills"]
         return dict(zip(keys, map(int, v)))
 
     def contact_forces(self, eid: int) -> np.ndarray:
@@ -325,7 +327,7 @@ class Scene:
         return w.value // 8
 
     PROF_FAMILIES = ["spmv", "elastic", "contact", "ccd", "pcg_vector", "broad", "assembly", "ls_energy", "pcg_solve",
-                     "pcg_flops"]
+                     "pcg_flops", "host_idle"]
 
     def profile(self, on: bool = True):
         _check(lib().ipc_profile_enable(self._h, int(on)))

@@ -560,6 +560,52 @@ def uneven_batch_env(env_id: int, base_seed: int = UNEVEN_SEED) -> dict:
 
 UNEVEN_START_STEP = 20
 
+SERVE_SEED = BASE_SEED + 2097152
+
+
+def serving_request_env(req_id: int, base_seed: int = SERVE_SEED, close_steps: int = 70, lift_steps: int = 50,
+                        shake_steps: int = 60, hold_steps: int = 20, shake_deg: float = 15.0, shake_hz: float = 2.0,
+                        dt: float = 0.005, lift: float = 0.05, tets_lo: int = 1000, tets_hi: int = 100000) -> dict:
+    """A grasp-evaluation request of the serving workload: with equal odds the plate squeeze or the
+    soft-pad grasp of a star-shaped soft object of log-uniform tets_lo-tets_hi tets (one gripper
+    pair). The grippers close from 1.5 dhat away in `close_steps` (gravity off), lift by `lift`,
+    shake the object about the grasp (x) axis through its lifted centre by
+    shake_deg * sin(2 pi shake_hz t), then hold still for `hold_steps` (gravity on), at the end of
+    which the grasp is labelled (Sec. III-D: the object still touches a gripper and its centre of
+    mass moves less than eps_v dt in the last step)."""
+    rng = SplitMix64(base_seed + req_id)
+    pads = rng.uniform() < 0.5
+    cl = close_steps + lift_steps
+    if pads:
+        env = soft_pad_grasp_env(req_id, base_seed=base_seed + 7, n_steps=cl, close_steps=close_steps, dt=dt,
+                                 lift=lift, tets_lo=tets_lo, tets_hi=tets_hi, bimanual=False)
+    else:
+        env = soft_object_grasp_env(req_id, base_seed=base_seed + 7, n_steps=cl, close_steps=close_steps, dt=dt,
+                                    lift=lift, tets_lo=tets_lo, tets_hi=tets_hi, bimanual=False)
+    last = env["targets"][-1]
+    nb = last.shape[0]
+    grip = [b for b in range(nb) if not (len(env["soft"]) > b and not np.any(env["soft"][b]["kin"]))]
+    c = np.array([0.0, 0.0, lift])
+    frames = []
+    for k in range(1, shake_steps + hold_steps + 1):
+        ang = shake_deg * math.sin(2.0 * math.pi * shake_hz * min(k, shake_steps) * dt)
+        R = _rot_x(ang if k <= shake_steps else 0.0)
+        fr = last.copy()
+        for b in grip:  # a gripper q: x = R (A0 X + t - c) + c
+            A0 = np.stack([last[b, 3:6], last[b, 6:9], last[b, 9:12]], axis=1)
+            q = np.zeros(12)
+            q[:3] = R @ (last[b, :3] - c) + c
+            RA = R @ A0
+            q[3:6], q[6:9], q[9:12] = RA[:, 0], RA[:, 1], RA[:, 2]
+            fr[b] = q
+        frames.append(fr)
+    env["targets"] = np.concatenate([env["targets"], np.array(frames)], axis=0)
+    env["gravity"] = np.concatenate([env["gravity"], np.ones(shake_steps + hold_steps, dtype=np.uint8)])
+    if "object" not in env:
+        env["object"] = ("soft", 0)
+    env["lift"] = lift
+    return env
+
 
 def uneven_batch_cost(env_id: int, base_seed: int = UNEVEN_SEED) -> float:
     """Estimated work of uneven_batch_env(env_id) without building it: its tet count (the object's

@@ -92,15 +92,48 @@ def initial_points(env: dict) -> np.ndarray:
     return np.concatenate(parts, axis=0)
 
 
-def object_result(env: dict, points: np.ndarray, points0: np.ndarray) -> dict:
-    """Grasp outcome: mean displacement of the grasped object's points and whether it rose by
-    more than half the schedule's lift."""
+def object_handle(env: dict) -> int | None:
+    """Body handle of the grasped object (soft bodies first, then affine bodies)."""
+    if "object" not in env:
+        return None
+    kind, idx = env["object"]
+    return idx if kind == "soft" else len(env["soft"]) + idx
+
+
+def com_velocity(env: dict, v: np.ndarray) -> np.ndarray:
+    """Velocity of the grasped object's centre of mass (the mean of its points) from the env's DOF
+    rates: a soft object's vertex rates, or for an affine object p' + A' xbar averaged over its
+    rest vertices."""
+    kind, idx = env["object"]
+    if kind == "soft":
+        o = sum(len(s["verts"]) for s in env["soft"][:idx])
+        return v[3 * o: 3 * (o + len(env["soft"][idx]["verts"]))].reshape(-1, 3).mean(axis=0)
+    o = 3 * sum(len(s["verts"]) for s in env["soft"]) + 12 * idx
+    q = v[o: o + 12]
+    xb = np.asarray(env["affine"][idx]["verts"], dtype=np.float64).mean(axis=0)
+    return q[:3] + xb[0] * q[3:6] + xb[1] * q[6:9] + xb[2] * q[9:12]
+
+
+def object_result(env: dict, points: np.ndarray, points0: np.ndarray, v: np.ndarray | None = None,
+                  handles: np.ndarray | None = None, eps_v: float = 0.0, dt: float = 0.0,
+                  stable_factor: float = 1.0) -> dict:
+    """Grasp outcome: mean displacement of the grasped object's points, whether it rose by more
+    than half the schedule's lift, and the stability label of Sec. III-D at the last step (the
+    object touches another body, and its centre of mass moved less than stable_factor * eps_v * dt
+    in that step; the motion is dt times the centre's velocity, v = (x - x^t) / dt)."""
     sl = object_points(env)
     if sl is None or points0 is None:
         return {}
     disp = (points[sl] - points0[sl]).mean(axis=0)
     lift = float(env.get("lift", 0.0))
-    return {"object_disp": disp.tolist(), "held": bool(lift > 0 and disp[2] > 0.5 * lift)}
+    out = {"object_disp": disp.tolist(), "held": bool(lift > 0 and disp[2] > 0.5 * lift)}
+    if v is not None and handles is not None:
+        obj = object_handle(env)
+        in_contact = any((int(a) == obj) != (int(b) == obj) for a, b in handles)
+        com_step = float(np.linalg.norm(com_velocity(env, v))) * dt
+        out.update({"in_contact": bool(in_contact), "com_step": com_step,
+                    "stable": bool(in_contact and com_step < stable_factor * eps_v * dt)})
+    return out
 
 
 class GraspServer:
@@ -113,6 +146,7 @@ class GraspServer:
         self.steps_per_call = max(1, steps_per_call)
         self.clock = clock or time.perf_counter
         self.sleep = sleep or time.sleep
+        self.eps_v, self.dt = params.get("eps_v", 0.0), params.get("dt", 0.0)
         self.batch_steps = 0
         self.env_steps = 0
         self.relayouts = 0
@@ -175,7 +209,10 @@ class GraspServer:
                     req = active.pop(eid)
                     req.finished, req.status, req.reason, req.steps = t_now, st, reason, step
                     pts = sc.points(eid)
-                    req.result = {"dofs": sc.dofs(eid), "points": pts, **object_result(req.env, pts, start_pts.pop(eid))}
+                    v = sc.velocities(eid) if "object" in req.env else None
+                    hd = sc.contact_handles(eid) if "object" in req.env else None
+                    req.result = {"dofs": sc.dofs(eid), "points": pts,
+                                  **object_result(req.env, pts, start_pts.pop(eid), v, hd, self.eps_v, self.dt)}
                     done_in_scene.append(eid)
         for eid in done_in_scene:
             sc.remove_env(eid)

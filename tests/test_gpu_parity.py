@@ -472,3 +472,37 @@ def test_axis_gravity_phases_match_the_oracle():
         xo, _ = o.state()
         assert np.abs(sc.dofs(eid) - xo).max() <= TRAJ_TOL, k
     assert sc.status(eid)["status"] == "DONE"
+
+
+@pytest.mark.parametrize("slots", [1, 3])
+def test_spilled_collect_traversals_give_the_same_candidates_and_bits(slots):
+    """A collect traversal keeps up to `collect_slots` partners per query; a query with more sends
+    the pass to a count-then-fill traversal (the candidate-buffer overflow case). With 1 or 3
+    slots nearly every pass spills: the candidate and contact lists of the squeezed cube still
+    equal the oracle's, and ten steps of the pad grasp from its contact phase give the same bits,
+    Newton, line-search, PCG and ACCD counts as with the default 128 slots."""
+    p = S.scene_params(0.01)
+    env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+    o, x, v = oracle_state(p, env, 25)
+    sc = ipc.Scene(p, collect_slots=slots)
+    eid = sc.add_env(env)
+    sc.set_state(eid, x, v, 25)
+    assert np.array_equal(sc.candidates(eid), o.candidates(x))
+    ko, _ = o.contacts(x)
+    assert len(ko) > 10 and np.array_equal(sc.contacts(eid)[:, :3], ko[:, :3])
+    assert sc.scene_counters(eid)["collect_spills"] > 0
+
+    pp = S.scene_params(0.005)
+    pad = S.pad_grasp_env(0)
+    xs, vs = S.pad_grasp_state_at(pad, 20)
+    runs = []
+    for c in (0, slots):
+        s2 = ipc.Scene(pp, collect_slots=c)
+        e2 = s2.add_env(pad)
+        s2.set_state(e2, xs, vs, 20)
+        s2.step(10)
+        st = s2.status(e2)
+        runs.append((s2.dofs(e2), [st[k] for k in ("newton_iters", "pcg_iters", "ls_halvings", "accd_iters")],
+                     s2.scene_counters(e2)["collect_spills"]))
+    assert runs[0][2] == 0 and runs[1][2] > 0
+    assert np.array_equal(runs[0][0], runs[1][0]) and runs[0][1] == runs[1][1]

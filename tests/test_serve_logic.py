@@ -172,3 +172,29 @@ def test_grasp_outcome_of_the_object_rows():
         r = object_result(e, p, p0)
         assert np.allclose(r["object_disp"], [0.01, 0.0, rise]) and r["held"] is held
     assert object_points(dict(e, object=("soft", 1))) == slice(4, 7)
+
+
+def test_stability_label_of_a_finished_request():
+    """Sec. III-D's label at the last step: stable when the object touches another body and its
+    centre of mass (the mean of its points) moved less than eps_v dt in that step, the motion being
+    dt times the mean of the object's point velocities."""
+    from paper_2503_05020_b300 import scenes as S
+    from paper_2503_05020_b300.serve import object_result, initial_points
+
+    env = S.serving_request_env(4)  # plates squeezing a soft object (handle 0, plates 1 and 2)
+    assert env["object"] == ("soft", 0) and len(env["affine"]) == 2
+    pts = initial_points(env)
+    n = len(env["soft"][0]["verts"])
+    eps_v, dt = 1e-3, 0.005
+    v = np.zeros(3 * n + 24)
+    slow = v.copy()
+    slow[2:3 * n:3] = 0.5 * eps_v  # every object vertex at half the threshold speed
+    fast = v.copy()
+    fast[0:3 * n:3] = 2.0 * eps_v
+    touching = np.array([[0, 1], [2, 0]])
+    apart = np.array([[1, 2]])  # the plates touch each other, not the object
+    r = object_result(env, pts, pts, slow, touching, eps_v, dt)
+    assert r["stable"] and r["in_contact"] and abs(r["com_step"] - 0.5 * eps_v * dt) < 1e-18
+    assert not object_result(env, pts, pts, fast, touching, eps_v, dt)["stable"]
+    r = object_result(env, pts, pts, slow, apart, eps_v, dt)
+    assert not r["in_contact"] and not r["stable"]
