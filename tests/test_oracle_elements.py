@@ -565,3 +565,17 @@ def test_near_parallel_edge_band_within_its_error_bound():
             ex = float(exact_segment_d2(x))
             assert t == 8
             assert abs(d2 - ex) <= 1e-9 * ex, (sin2, d2, ex)
+
+
+def test_accd_common_translation_needs_no_advance():
+    """Additive CCD subtracts the pair's mean displacement: two primitives carried by the same
+    translation never approach each other, so the step is the whole [0, 1] with no advancement,
+    however large the translation (Li, Kaufman & Jiang 2021)."""
+    rng = np.random.default_rng(17)
+    for kind in (0, 1):
+        for _ in range(10):
+            x = rng.normal(size=12) * 0.01
+            d = rng.normal(size=3) * 0.05
+            p = np.tile(d, 4)
+            t, it = O.accd(kind, x, p)
+            assert t == 1.0 and it == 0, (kind, t, it)

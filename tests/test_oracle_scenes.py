@@ -715,3 +715,84 @@ def test_env_gradient_and_hessian_fd_joint_term():
     H = e.hessian(q)
     Hf = _fd_hessian(e, q, range(12, 24))
     assert np.abs(H[:, 12:24] - Hf).max() <= 1e-6 * np.abs(H).max()
+
+
+def test_elastic_energy_is_the_volume_weighted_strain_energy():
+    """A free soft block (side a) under a uniform deformation F has elastic energy h^2 a^3 Psi(F):
+    every tet has the same F, and their rest volumes add up to the block's. With the block at rest
+    and gravity off the predicted positions are the rest ones for any dt, so two time steps h1, h2
+    change only the elastic term: (E(h1) - E(h2)) / (h1^2 - h2^2) = a^3 Psi(F), with Psi the
+    (separately pinned) Neo-Hookean density of the element routine."""
+    a, E, nu = 0.02, 2e5, 0.35
+    verts, tets, _ = S.kuhn_grid(3, 3, 3, (0.0, 0.0, 0.0), (a, a, a))
+    soft = dict(verts=verts, tets=tets, tris=S.boundary_tris(verts, tets), E=E, nu=nu, rho=1000.0,
+                kin=np.zeros(len(verts), dtype=np.uint8))
+    env = dict(soft=[soft], affine=[], mu=0.0, gravity=np.zeros(2, dtype=np.uint8),
+               targets=np.tile(S.IDENTITY_Q, (2, 1, 1)))
+    F = np.array([[1.05, 0.02, 0.0], [-0.01, 0.97, 0.03], [0.0, 0.01, 1.02]])
+    q = (verts @ F.T).ravel()
+    Es = []
+    for h in (0.01, 0.02):
+        e = O.OracleEnv(S.scene_params(h), env)
+        Es.append(e.eval(q, grad=False))
+    mu, lam = E / (2 * (1 + nu)), E * nu / ((1 + nu) * (1 - 2 * nu))
+    psi, _, _ = O.neo_hookean(F, mu, lam)
+    assert abs((Es[0] - Es[1]) / (0.01 ** 2 - 0.02 ** 2) / (a ** 3 * psi) - 1.0) < 1e-10
+
+
+def test_edge_edge_contact_force_carries_the_rest_length_mollifier():
+    """Two thin rigid bars crossing at angle theta, 0.4 dhat apart: the edge-edge contacts' normal
+    forces are kappa e(c) |b'(d)| with c = |e_a x e_b|^2 and the mollifier threshold 1e-3 |rest e_a|^2
+    |rest e_b|^2 of IPC 2020 (e = 1 above it, 2 c/eps - (c/eps)^2 below). At 8 degrees the crossing
+    long edges are unmollified (sin^2 = 0.019 > 1e-3); at 1 degree (sin^2 = 3e-4) they carry
+    e = 2 r - r^2 with r = 0.30."""
+    dhat, g = 1e-3, 4e-4
+    p = S.scene_params(0.01)
+    hv, ht = S.box_surface((0.05, 0.002, 0.002))
+    for deg, mollified in ((8.0, False), (1.0, True)):
+        th = math.radians(deg)
+        R = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+        qa = S.IDENTITY_Q.copy()
+        qb = S.IDENTITY_Q.copy()
+        qb[:3] = [0.0, 0.0, 0.004 + g]
+        qb[3:6], qb[6:9], qb[9:12] = R[:, 0], R[:, 1], R[:, 2]
+        bars = [dict(verts=hv, tris=ht, rho=1000.0, q0=q, qdot0=np.zeros(12), kinematic=k)
+                for q, k in ((qa, True), (qb, False))]  # pairs of two kinematic bodies are skipped
+        env = dict(soft=[], affine=bars, mu=0.0, gravity=np.zeros(2, dtype=np.uint8),
+                   targets=np.stack([np.stack([qa, qb])] * 2))
+        e = O.OracleEnv(p, env)
+        x, _ = e.state()
+        pts = np.concatenate([hv, hv @ R.T + qb[:3]])
+        tris = np.concatenate([ht, ht + len(hv)])
+        ed = sorted({(min(a, b), max(a, b)) for t in tris for a, b in ((t[0], t[1]), (t[1], t[2]), (t[2], t[0]))})
+        rest = np.concatenate([hv, hv])
+        C, _ = e.contacts(x)
+        f = e.contact_forces(x)
+        rs = []
+        E_ref = 0.0  # at rest with gravity off and mu = 0 the potential is the barrier alone
+        for (kind, i, j, _), fk in zip(C, f):
+            if kind != 1:
+                v = sorted({int(t) for t in tris.ravel()})[i]
+                tri = tris[j]
+                x12 = np.concatenate([pts[v], pts[tri[0]], pts[tri[1]], pts[tri[2]]])
+                E_ref += p["dt"] ** 2 * p["kappa"] * O.barrier(math.sqrt(O.pair_dist2(0, x12)[0]), dhat)[0]
+                continue
+            (a0, a1), (b0, b1) = ed[i], ed[j]
+            x12 = np.concatenate([pts[a0], pts[a1], pts[b0], pts[b1]])
+            d = math.sqrt(O.pair_dist2(1, x12)[0])
+            cr = np.cross(pts[a1] - pts[a0], pts[b1] - pts[b0])
+            c = float(cr @ cr)
+            eps = 1e-3 * float((rest[a1] - rest[a0]) @ (rest[a1] - rest[a0])) * float((rest[b1] - rest[b0]) @ (rest[b1] - rest[b0]))
+            r = c / eps
+            m = 1.0 if r >= 1.0 else 2.0 * r - r * r
+            ref = p["kappa"] * m * abs(O.barrier(d, dhat)[1])
+            assert abs(fk - ref) <= 1e-9 * ref, (deg, i, j, fk, ref)
+            E_ref += p["dt"] ** 2 * p["kappa"] * m * O.barrier(d, dhat)[0]
+            rs.append(r)
+        assert len(rs) > 0
+        E = e.eval(x, grad=False)
+        assert abs(E - E_ref) <= 1e-9 * E_ref, (deg, E, E_ref)
+        # at 8 degrees every crossing (long edges, top-face diagonals) is above the threshold; at 1
+        # degree the long edges' crossing sits at r = sin^2(1 deg) / 1e-3 = 0.30
+        assert any(r < 1.0 for r in rs) == mollified
+        assert not mollified or any(abs(r - 0.30) < 0.01 for r in rs)
