@@ -243,7 +243,7 @@ def test_env_gradient_fd_pd_target_term():
     _fd_check(e, q, list(range(12)))
 
 
-@pytest.mark.parametrize("floor", [1.0, 1e-2, 1e-4])
+@pytest.mark.parametrize("floor", [1.0, 1e-2, 1e-4, 1e3])
 def test_adapted_stiffness_at_rest_balances_the_contact_vertices_weight(floor):
     """Adapted barrier stiffness at a step start: the kappa that minimises |g_E + kappa G| over
     the free DOFs (g_E: gradient of every other term, G: the barrier's per unit kappa). A soft
@@ -252,7 +252,8 @@ def test_adapted_stiffness_at_rest_balances_the_contact_vertices_weight(floor):
     g times the bottom vertices' mean mass over |b'(d)| (b' written out from
     b(d) = -(d - dhat)^2 ln(d / dhat)), clamped to [floor, 1000 floor] with the scene's kappa
     as the floor. The floors put that value near the bottom of the range, at about 250 times
-    the floor, and above the range (clamped to 1000 times the floor)."""
+    the floor, above the range (clamped to 1000 times the floor) and below it (held at the
+    floor)."""
     h = 0.01
     p = S.scene_params(h, kappa=floor)
     p["kappa_adapt"] = True
@@ -267,8 +268,9 @@ def test_adapted_stiffness_at_rest_balances_the_contact_vertices_weight(floor):
     d, dh = gap, p["dhat"]
     b1 = -2.0 * (d - dh) * math.log(d / dh) - (d - dh) ** 2 / d
     balance = G * m[bottom].mean() / abs(b1)
-    if balance < 1000.0 * floor:
-        assert floor < balance
+    if balance <= floor:
+        assert e.kappa() == floor
+    elif balance < 1000.0 * floor:
         assert abs(e.kappa() / balance - 1.0) < 1e-9
     else:
         assert e.kappa() == 1000.0 * floor
