@@ -252,7 +252,14 @@ def host_info() -> dict:
 FP64_PEAK_TFLOPS = 148 * 4 * 2.032e9 / 1e12
 
 
-def roofline(prof, precision):
+# DRAM bytes per launch of k_pcg_cluster measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum over every launch of a run of this workload, averaged per launch; the
+# command is in profiles/k_pcg_cluster_uneven_1024env_dram.md). Keyed by (workload, envs,
+# precision); a workload without a capture of the current kernel reports null.
+PCG_DRAM_BYTES_PER_LAUNCH = {("uneven", 1024, "fp64"): 21.154e9}
+
+
+def roofline(prof, precision, traffic=None):
     kern = {"pcg_solve": "k_pcg_cluster (persistent per-environment PCG, whole solve per launch)",
             "spmv": "k_spmv (PCG matrix-vector product)"}
     solve = "pcg_solve" if prof["pcg_solve"]["launches"] > 0 else "spmv"
@@ -268,7 +275,8 @@ def roofline(prof, precision):
     # ridge point: intensity (flop/B) above peak_flops / peak_bandwidth is arithmetic-bound
     intensity = flops / sp["work"] if sp["work"] > 0 else 0.0
     alu_bound = fp64 and flops > 0 and intensity > FP64_PEAK_TFLOPS * 1e12 / (hbm * 1e9)
-    base = {"kernel": kern[solve], "traffic": None, "bytes_per_launch": sp["work"] / sp["launches"],
+    base = {"kernel": kern[solve], "traffic": traffic if solve == "pcg_solve" else None,
+            "bytes_per_launch": sp["work"] / sp["launches"],
             "flops_per_launch": flops / sp["launches"], "intensity_flop_per_byte": round(intensity, 4),
             "avg_launch_us": 1000.0 * sp["ms"] / sp["launches"], "launches": sp["launches"],
             "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4), "hbm_peak_source": f"{hbm_kind} hbm_gbs"}
@@ -433,7 +441,8 @@ def run_ours(args):
     # ---- roofline of the dominant kernel: the persistent per-env PCG when it runs, else the
     # tiled SpMV. Its bound is the roof its arithmetic intensity reaches first: FP64 arithmetic
     # (B300 runs FP64 at 1/58 of FP32) or HBM bandwidth.
-    roof = roofline(prof, args.precision)
+    roof = roofline(prof, args.precision,
+                    PCG_DRAM_BYTES_PER_LAUNCH.get((args.workload, args.envs, args.precision)) if world == 1 else None)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
