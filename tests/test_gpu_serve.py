@@ -48,3 +48,37 @@ def test_hbm_budget_bounds_the_resident_batch():
     rep = srv.run(reqs)
     assert rep["completed"] == 4 and rep["rejected"] == 0
     assert rep["max_active"] == 2
+
+
+@pytest.mark.slow
+def test_served_labels_and_held_object_match_the_oracle():
+    """Two requests of the serving configuration (plates squeezing soft objects of 1.7k and 2.3k
+    tets: close, lift 5 cm, shake +/-15 deg at 2 Hz, hold), served together in FP64 and in mixed
+    precision at the default tolerances, against the FP64 oracle running each request alone:
+    the same Sec. III-D label (the smaller object is dropped, the larger held), and the held
+    object's points end within 1e-4 of its displacement of the oracle's."""
+    from oracle import oracle as O
+    from paper_2503_05020_b300.serve import initial_points, object_points, object_result
+
+    p = S.scene_params(0.005)
+    ids = (4, 5)
+    envs = [S.serving_request_env(i) for i in ids]
+    ref = []
+    for env in envs:
+        o = O.OracleEnv(p, env)
+        assert o.step(len(env["targets"])) == "DONE"
+        x, v = o.state()
+        pts = o.points(x)
+        ref.append((pts, object_result(env, pts, initial_points(env), v, o.contact_bodies(x), p["eps_v"], p["dt"])))
+    assert [r[1]["stable"] for r in ref] == [False, True]
+    for prec in (ipc.FP64, ipc.MIXED):
+        reqs = [Request(k, e, 0.0) for k, e in enumerate(envs)]
+        GraspServer(p, precision=prec, max_envs=8, admit_period=8, steps_per_call=8).run(reqs)
+        for r, (pts_o, res_o), env in zip(reqs, ref, envs):
+            assert r.status == "DONE"
+            assert r.result["stable"] == res_o["stable"] and r.result["in_contact"] == res_o["in_contact"]
+            if res_o["stable"]:
+                sl = object_points(env)
+                disp = float(np.abs(pts_o[sl] - initial_points(env)[sl]).max())
+                err = float(np.abs(r.result["points"][sl] - pts_o[sl]).max())
+                assert err <= 1e-4 * disp, (prec, err, disp)
