@@ -358,6 +358,9 @@ def run_ours(args):
         sc.set_state(eid, x, v, wl.start)
     sc.step(args.warmup)
     snap = [(sc.dofs(e), sc.velocities(e), sc.status(e)["step"]) for e in ids]
+    # envs that stopped during the warm-up (Newton cap, or their schedule's end) take no part in the
+    # later legs: restoring their state would make them active again and repeat their last step
+    live = [i for i, e in enumerate(ids) if sc.status(e)["status"] == "ACTIVE"]
     p_start = [sc.points(e) for e in ids]
 
     def barrier():
@@ -390,8 +393,9 @@ def run_ours(args):
 
     # ---- end to end through the public API with host buffers: per step, the next kinematic
     # targets of every env go host -> device and the DOFs of every env come back.
-    for eid, (x, v, st) in zip(ids, snap):
-        sc.set_state(eid, x, v, st)
+    for i in live:
+        x, v, st = snap[i]
+        sc.set_state(ids[i], x, v, st)
     n_all = sc.all_dofs_size()
     h_out = torch.empty(n_all, dtype=torch.float64, pin_memory=True).numpy()
     # the next targets of every env for each step (the API takes those of the envs still active)
@@ -424,10 +428,10 @@ def run_ours(args):
     tets = [sum(len(s["tets"]) for s in e["soft"]) for e in envs]
     plain = mixed = None
     if world == 1 and args.plain_envs > 0:
-        plain = guarded(plain_leg, args, params, envs, snap, tets, stream, local, value)
+        plain = guarded(plain_leg, args, params, envs, snap, tets, stream, local, value, live)
     if world == 1 and args.precision == "fp64" and not args.no_mixed_leg:
         mixed = guarded(mixed_leg, args, params, envs, snap, p_start, x_end, tets, stream, local, t_max / args.steps,
-                        {i for i, s_ in enumerate(stats) if s_["status"] == "FAILED"})
+                        {i for i, s_ in enumerate(stats) if s_["status"] == "FAILED"}, live)
         if plain and "value" in plain and "value" in mixed:
             plain["mixed_batched_over_plain"] = round(mixed["value"] / plain["value"], 2)
 
@@ -447,7 +451,7 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         threads = min(os.cpu_count() or 1, 64)
-        sel = cpu_sample(tets, threads)
+        sel = [live[j] for j in cpu_sample([tets[i] for i in live], threads)]
         v_cpu, n_cpu, dt_cpu = cpu_oracle_sample([envs[i] for i in sel], [snap[i] for i in sel], params, threads)
         cpu = {"value": round(v_cpu, 4), "unit": UNIT, "cores": min(threads, n_cpu), "kind": "oracle",
                "sample": f"{n_cpu} envs at evenly spaced size quantiles among the envs of at most "
@@ -482,7 +486,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def plain_leg(args, params, envs, snap, tets, stream, device, batched_value):
+def plain_leg(args, params, envs, snap, tets, stream, device, batched_value, live=None):
     """The plain FP64 GPU stepper: the same kernels, one env at a time (its own scene, automatic
     PCG shape, which for a single env has one candidate and is never tuned), on a sample of the
     envs at evenly spaced size quantiles, each from the timed region's start state for the same
@@ -490,7 +494,8 @@ def plain_leg(args, params, envs, snap, tets, stream, device, batched_value):
     the same envs run one after another."""
     from paper_2503_05020_b300 import ipc
 
-    sel = stratified(tets, args.plain_envs)
+    live = list(range(len(envs))) if live is None else live
+    sel = [live[j] for j in stratified([tets[i] for i in live], args.plain_envs)]
     seq_ms, steps = 0.0, 0
     for i in sel:
         sc = ipc.Scene(params, precision=ipc.FP64, device=device, stream=stream.cuda_stream)
@@ -523,7 +528,7 @@ def plain_leg(args, params, envs, snap, tets, stream, device, batched_value):
                                            "1x H100, FP64 (Sec. I, IV-A)"}}
 
 
-def mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, device, ms_fp64, failed_fp64=()):
+def mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, device, ms_fp64, failed_fp64=(), live=None):
     """The same K timed steps from the same state with FP32 Hessians and PCG (FP64 energies,
     gradients, barrier, CCD and line search): throughput and speedup over the FP64 run. Accuracy:
     the largest difference of a point's world position from the FP64 run (all points, and the
@@ -534,12 +539,13 @@ def mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, device, ms
 
     sc = ipc.Scene(params, precision=ipc.MIXED, device=device, stream=stream.cuda_stream,
                    pcg_cluster=args.pcg_cluster)
-    ids = [sc.add_env(e) for e in envs]
-    for eid, (x, v, st) in zip(ids, snap):
-        sc.set_state(eid, x, v, st)
+    live = list(range(len(envs))) if live is None else live
+    ids = [sc.add_env(envs[i]) for i in live]
+    for eid, i in zip(ids, live):
+        sc.set_state(eid, *snap[i])
     sc.step(1)  # warm-up (tuner, first-call costs), then back to the snapshot
-    for eid, (x, v, st) in zip(ids, snap):
-        sc.set_state(eid, x, v, st)
+    for eid, i in zip(ids, live):
+        sc.set_state(eid, *snap[i])
     sc.profile(True)
     s0 = sum(sc.status(e)["steps"] for e in ids)
     ms = timed_steps(sc, stream, args.steps)
@@ -547,8 +553,10 @@ def mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, device, ms
     sc.profile(False)
     sts = [sc.status(e) for e in ids]
     steps = sum(st["steps"] for st in sts) - s0
-    x_mixed = [sc.points(e) for e in ids]
-    failed_m = {i for i, st in enumerate(sts) if st["status"] == "FAILED"}
+    x_mixed = [None] * len(envs)
+    for eid, i in zip(ids, live):
+        x_mixed[i] = sc.points(eid)
+    failed_m = {i for i, st in zip(live, sts) if st["status"] == "FAILED"}
     failed = len(failed_m)
     newton = sum(st["newton_iters"] for st in sts)
     pcg_its = sum(st["pcg_iters"] for st in sts)
@@ -565,7 +573,7 @@ def mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, device, ms
                 "rel_object_points": d_obj / disp if disp > 0 else None, "max_displacement_m": disp}
 
     # envs that failed in either precision stop at different points: compared only where both ran
-    rows = [i for i in range(len(envs)) if i not in failed_m and i not in failed_fp64]
+    rows = [i for i in live if i not in failed_m and i not in failed_fp64]
     out = {"value": round(steps / (ms / 1000.0), 2), "unit": UNIT, "ms_per_step": round(ms / args.steps, 3),
            "speedup_vs_fp64": round((ms_fp64 * args.steps) / ms, 3), "envs_failed": int(failed),
            "pcg_iters_per_newton": round(pcg_its / max(newton, 1), 1),

@@ -160,8 +160,8 @@ typedef enum {
   IPC_Q_POINTS = 6,      /* double[n_points][3]: world positions of all surface-capable points
                             (soft vertices, then affine rest vertices mapped by q; joint anchors
                             are not among them) */
-  IPC_Q_SIZES = 7,       /* int64[8]: ndof, points, surface vertices, edges, triangles, tets,
-                            bodies, steps */
+  IPC_Q_SIZES = 7,       /* int64[8]: ndof, points (those of IPC_Q_POINTS), surface vertices,
+                            edges, triangles, tets, bodies, steps */
   IPC_Q_INTERSECTIONS = 8, /* int64[2]: segment-triangle intersections, inverted tets */
   IPC_Q_SCENE_COUNTERS = 9, /* int64[12] for the whole scene (env_id ignored), from the last Newton
                               iteration: contacts, point-triangle contacts, friction stencils,
