@@ -182,9 +182,12 @@ typedef enum {
                               friction stencil of the env's current (or last) step at its
                               current DOFs (u: tangential relative displacement since the step
                               start); point-triangle stencils first */
-  IPC_Q_CONTACT_HANDLES = 15 /* int32[n][2]: the bodies of the two sides of each contact (env-local
+  IPC_Q_CONTACT_HANDLES = 15, /* int32[n][2]: the bodies of the two sides of each contact (env-local
                               handles: soft bodies first, then affine bodies), in the order of
                               IPC_Q_CONTACTS */
+  IPC_Q_ENERGY_TRACE = 16  /* double[n]: the incremental potential (J) at each Newton iterate of the
+                              env's current (or last) step, in iteration order, n <= max_newton
+                              (Sec. II-C projected Newton: a diagnostic trace for parity checks) */
 } ipc_query_kind;
 
 /* Create / destroy a scene on desc->device. */

@@ -481,6 +481,9 @@ struct ipc_scene {
   DBuf<int> e_status, e_reason, e_step, e_constrained, e_bad, e_nanp, e_halv, e_newton_it, e_count, e_rem;
   // barrier stiffness per env, its closest-contact tracking and the step-start sums
   DBuf<double> e_kappa, e_kdots, g0buf;
+  DBuf<double> e_trace;  // per env: the incremental potential at each Newton iterate of its step
+  DBuf<int> e_trace_n;
+  int trace_cap() const { return std::max(desc.max_newton, 1); }
   DBuf<double> tet_vm;  // per-tet stress or per-contact force of a query
   DBuf<uint8_t> e_stepping, e_iter, e_ls, e_accept, e_sel, e_all, e_start, e_cover;
   DBuf<double> e_E0, e_Et, e_alpha;
@@ -1082,6 +1085,9 @@ struct ipc_scene {
     launch(k_fill_u8, E, 256, E, e_all.p, (uint8_t)1);
     for (DBuf<double>* b : {&e_E0, &e_Et, &e_alpha}) b->alloc(E);
     e_kappa.alloc(E);
+    e_trace.alloc((size_t)E * trace_cap());
+    e_trace_n.alloc(E);
+    e_trace_n.zero(s);
     e_kdots.alloc(2 * (size_t)E);
     launch(k_env_fill, E, 128, E, (const uint8_t*)nullptr, e_kappa.p, desc.kappa);
     for (DBuf<unsigned long long>* b : {&e_alpha_bits, &e_pnorm_bits, &e_inter, &e_inv}) b->alloc(E);
@@ -2015,6 +2021,7 @@ struct ipc_scene {
   void newton_round(EnvCtl C) {
     launch(k_env_iter_begin, E, 128, E, C);
     evaluate<MODE_HESS>(x.p, e_iter.p, e_E0.p);
+    launch(k_trace_record, E, 128, E, C, (const double*)e_E0.p, e_trace.p, e_trace_n.p, trace_cap());
     assemble(e_iter.p);
     // kinematic step and the reduced right-hand side -g - H pbar
     launch(k_pbar, NN, 256, NN, layout(), C, (const double*)x.p, (const double*)xtarget.p, pbar.p);
@@ -2451,6 +2458,17 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       long long v[12] = {s->n_ct, s->n_ct_pt, s->n_fr, s->n_inc, mx, (long long)s->n_pt + s->n_ee, s->NNZB,
                          s->sell_nval / 288, s->pcg_C, s->max_env_slices, s->n_jt, s->spills};
       return copy_out(v, sizeof(v), out, out_bytes, written);
+    }
+    case IPC_Q_ENERGY_TRACE: {
+      int n = 0;
+      CK(cudaMemcpyAsync(&n, s->e_trace_n.p + li, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      std::vector<double> buf(std::max(n, 0));
+      if (n > 0)
+        CK(cudaMemcpyAsync(buf.data(), s->e_trace.p + (size_t)li * s->trace_cap(), n * sizeof(double),
+                           cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      return copy_out(buf.data(), buf.size() * 8, out, out_bytes, written);
     }
     case IPC_Q_SIZES: {
       long long v[8] = {h.ndof, (long long)h.n_surf_pts, (long long)h.sv.size(), (long long)h.edges.size() / 2,

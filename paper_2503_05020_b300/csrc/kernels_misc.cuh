@@ -302,6 +302,17 @@ __global__ void k_env_ls_decide(int n_env, EnvCtl C, int max_ls) {
   C.stats[5 * e + STAT_LS] += 1;
   C.alpha[e] = C.alpha[e] / 2.0;
 }
+// the incremental potential at the iterate of each env still iterating, at its place in the env's
+// trace of the current step (index = Newton iterations already done in the step)
+__global__ void k_trace_record(int n_env, EnvCtl C, const double* __restrict__ E0, double* __restrict__ trace,
+                               int* __restrict__ trace_n, int cap) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_env || !C.iter[e]) return;
+  const int k = C.newton_it[e];
+  if (k < 0 || k >= cap) return;
+  trace[(long)e * cap + k] = E0[e];
+  trace_n[e] = k + 1;
+}
 __global__ void k_env_newton_end(int n_env, EnvCtl C, int max_newton) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_env) return;

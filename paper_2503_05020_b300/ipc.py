@@ -23,7 +23,7 @@ FAIL_REASON = {0: "none", 1: "newton_cap", 2: "line_search", 3: "non_finite", 4:
 FP64, MIXED = 0, 1
 Q_DOFS, Q_VELOCITIES, Q_STATUS, Q_STATS, Q_CANDIDATES, Q_CONTACTS, Q_POINTS, Q_SIZES, Q_INTERSECTIONS, \
     Q_SCENE_COUNTERS, Q_ALL_STATUS, Q_KAPPA, Q_TET_STRESS, Q_CONTACT_FORCES, Q_FRICTION_FORCES, \
-    Q_CONTACT_HANDLES = range(16)
+    Q_CONTACT_HANDLES, Q_ENERGY_TRACE = range(17)
 
 
 class IpcError(RuntimeError):
@@ -264,6 +264,10 @@ class Scene:
     def tet_stress(self, eid: int) -> np.ndarray:
         """Von Mises stress (Pa) of each of the env's tets at its current DOFs."""
         return self._query(eid, Q_TET_STRESS, np.float64)
+
+    def energy_trace(self, eid: int) -> np.ndarray:
+        """Incremental potential at each Newton iterate of the env's current (or last) step."""
+        return self._query(eid, Q_ENERGY_TRACE, np.float64)
 
     def kappa(self, eid: int) -> float:
         """The env's barrier stiffness in its current (or last) step."""

@@ -506,3 +506,29 @@ def test_spilled_collect_traversals_give_the_same_candidates_and_bits(slots):
                      s2.scene_counters(e2)["collect_spills"]))
     assert runs[0][2] == 0 and runs[1][2] > 0
     assert np.array_equal(runs[0][0], runs[1][0]) and runs[0][1] == runs[1][1]
+
+
+def test_energy_trace_query_matches_the_oracle_trace():
+    """IPC_Q_ENERGY_TRACE: the incremental potential at every Newton iterate of a step, as the
+    oracle records it, for the squeezed cube's 12th step (in contact, eight iterations, the first
+    with the plates still off target; parity settings): same number of iterates, energies within
+    1e-9 relative."""
+    p = S.parity_params(S.scene_params(0.01))
+    env = S.cube_squeeze_env(0, n_steps=40, close_steps=20)
+    o = O.OracleEnv(p, env)
+    o.trace(True)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    for k in range(12):
+        o.step(1)
+        sc.step(1)
+    rows = o.trace_energies()
+    last = rows[rows[:, 0] == rows[:, 0].max()]
+    eo = last[:, 3]
+    eg = sc.energy_trace(eid)
+    assert len(eo) >= 2 and len(eg) == len(eo), (len(eg), len(eo))
+    assert np.all(np.abs(eg - eo) <= 1e-9 * np.abs(eo)), (eg, eo)
+    # once the kinematic parts sit on their targets (the oracle's flag), the line search never
+    # raises the energy
+    free = eg[last[:, 2] == 0]
+    assert len(free) >= 2 and np.all(np.diff(free) <= 1e-12 * np.abs(free[:-1]))
