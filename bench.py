@@ -408,10 +408,10 @@ def run_ours(args):
     t0 = time.perf_counter()
     for k in range(args.steps):
         st = sc.all_status()
-        live = [r for eid, r in zip(ids, rows[k]) if st[eid][0] == "ACTIVE"]
-        n = sum(len(r) for r in live)
+        act_rows = [r for eid, r in zip(ids, rows[k]) if st[eid][0] == "ACTIVE"]
+        n = sum(len(r) for r in act_rows)
         if n:
-            h_tg[:n] = np.concatenate(live)
+            h_tg[:n] = np.concatenate(act_rows)
             sc.set_next_targets(h_tg[:n])
         h2d += 8 * n
         sc.step(1)
@@ -450,14 +450,7 @@ def run_ours(args):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        threads = min(os.cpu_count() or 1, 64)
-        sel = [live[j] for j in cpu_sample([tets[i] for i in live], threads)]
-        v_cpu, n_cpu, dt_cpu = cpu_oracle_sample([envs[i] for i in sel], [snap[i] for i in sel], params, threads)
-        cpu = {"value": round(v_cpu, 4), "unit": UNIT, "cores": min(threads, n_cpu), "kind": "oracle",
-               "sample": f"{n_cpu} envs at evenly spaced size quantiles among the envs of at most "
-                         f"{CPU_SAMPLE_MAX_TETS} tets (tets {min(tets[i] for i in sel)}-{max(tets[i] for i in sel)}; "
-                         f"the batch's envs average {int(np.mean(tets))}), 1 step each from the timed region's start "
-                         f"state, one env per thread, {dt_cpu:.1f} s wall", **host_info()}
+        cpu = guarded(cpu_leg, envs, snap, tets, live, params)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
@@ -484,6 +477,19 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def cpu_leg(envs, snap, tets, live, params):
+    """The CPU oracle on the host cores: one env per thread, 1 step each from the timed region's
+    start state, on envs of the batch's small end (CPU_SAMPLE_MAX_TETS)."""
+    threads = min(os.cpu_count() or 1, 64)
+    sel = [live[j] for j in cpu_sample([tets[i] for i in live], threads)]
+    v_cpu, n_cpu, dt_cpu = cpu_oracle_sample([envs[i] for i in sel], [snap[i] for i in sel], params, threads)
+    return {"value": round(v_cpu, 4), "unit": UNIT, "cores": min(threads, n_cpu), "kind": "oracle",
+            "sample": f"{n_cpu} envs at evenly spaced size quantiles among the envs of at most "
+                      f"{CPU_SAMPLE_MAX_TETS} tets (tets {min(tets[i] for i in sel)}-{max(tets[i] for i in sel)}; "
+                      f"the batch's envs average {int(np.mean(tets))}), 1 step each from the timed region's start "
+                      f"state, one env per thread, {dt_cpu:.1f} s wall", **host_info()}
 
 
 def plain_leg(args, params, envs, snap, tets, stream, device, batched_value, live=None):

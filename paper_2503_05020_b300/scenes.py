@@ -778,14 +778,16 @@ def _q_pose(R: np.ndarray, c: np.ndarray) -> np.ndarray:
 
 
 def hand_grasp_env(env_id: int, base_seed: int = BASE_SEED + 104729, n_steps: int = 400, close_steps: int = 200,
-                   dt: float = 0.005, dhat: float = 5e-4, cells: int = 19, k_pd: float = 3e3, lift: float = 0.05,
+                   dt: float = 0.005, dhat: float = 5e-4, cells: int = 19, k_pd: float = 2.5e5, lift: float = 0.05,
                    link_points: int = 250, k_joint: float | None = 1e5) -> dict:
     """Rigid hand of 20 PD-driven affine links (5 fingers x 4; each link a ~500-triangle hull)
     grasping a seeded star-shaped soft object (Kuhn ball of `cells`^3 cells, about 21k tets for 19;
     E log-uniform in [1e4, 1e6] Pa, nu U(0.3, 0.48)). Finger f hangs in the vertical half-plane at
     azimuth 2 pi f / 5 above and outside the object; its four joint angles curl it toward the
     object over `close_steps` (gravity off), then every link target rises by `lift` (gravity on).
-    Links are free bodies pulled toward their targets by the PD target potential (k_pd 1/s^2).
+    Links are free bodies pulled toward their targets by the PD target potential (k_pd 1/s^2; the
+    default makes a finger press about k_pd m_link (4 mm) = 2 N into the object, enough for five
+    fingers to hold its ~1 N weight by friction).
     With k_joint (N/m) the hand is articulated: each finger's first link hangs from a kinematic
     palm (a small box above the object, the last affine body) and each further link from the
     previous one by a hinge on the finger's bending axis, two point joints at +/- the link

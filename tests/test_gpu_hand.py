@@ -50,9 +50,7 @@ def test_hand_candidates_energy_and_newton_direction_match_the_oracle():
 
 def test_hand_batch_closes_on_the_object_without_failure():
     """Eight hands curl onto their objects (gravity off): every environment finishes the closing
-    schedule intersection-free and without inverted tets, with the fingers in contact. (Holding
-    the object under gravity needs a stiffer contact than the fixed kappa gives at dhat = 5e-4;
-    the oracle fails there too, so the hold is not part of this test.)"""
+    schedule intersection-free and without inverted tets, with the fingers in contact."""
     p = params()
     n_close = 120
     envs = [S.hand_grasp_env(i, n_steps=n_close, close_steps=n_close) for i in range(8)]
@@ -65,3 +63,21 @@ def test_hand_batch_closes_on_the_object_without_failure():
         inv = sc.invariants(eid)
         assert inv["intersections"] == 0 and inv["inverted"] == 0
         assert len(sc.contacts(eid)) > 0  # the fingers are on the object
+
+
+def test_hinged_hands_hold_and_lift_their_objects():
+    """The third configuration's grasp with the hinged hand: close 200 steps (gravity off), then
+    lift the palm and the finger targets 5 cm over 100 steps with gravity on. Every object rises
+    with its hand (its mean height within 1 cm of the 5 cm lift), no environment fails, crosses or
+    inverts."""
+    p = params()
+    envs = [S.hand_grasp_env(i, n_steps=300, close_steps=200) for i in range(4)]
+    sc = ipc.Scene(p)
+    ids = [sc.add_env(e) for e in envs]
+    sc.step(300)
+    for e, eid in zip(envs, ids):
+        assert sc.status(eid)["status"] == "DONE", sc.status(eid)
+        assert sc.invariants(eid) == {"intersections": 0, "inverted": 0}
+        n = len(e["soft"][0]["verts"])
+        dz = sc.points(eid)[:n, 2].mean() - np.asarray(e["soft"][0]["verts"])[:, 2].mean()
+        assert abs(dz - e["lift"]) < 0.01, dz

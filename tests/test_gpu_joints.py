@@ -84,5 +84,7 @@ def test_hinged_hands_close_with_their_joints_held():
         nsd = 3 * len(env["soft"][0]["verts"])
         gap = max(np.linalg.norm(_anchor(x, nsd, j["a"], j["anchor_a"]) - _anchor(x, nsd, j["b"], j["anchor_b"]))
                   for j in env["joints"])
-        assert gap < 1e-5, gap  # a joint of 1e5 N/m opens by force / k: far below a link's size
+        # a joint of 1e5 N/m opens by force / k: a few newtons of grip open it by tens of microns,
+        # far below the links' 5.5 mm radius
+        assert gap < 1e-4, gap
         assert sc.invariants(eid) == {"intersections": 0, "inverted": 0}
