@@ -143,6 +143,9 @@ typedef struct {
   const double* targets;
   int32_t n_joints, pad2;       /* point joints of the env (0: none) */
   const ipc_joint_desc* joints; /* n_joints entries (may be NULL when n_joints = 0) */
+  int32_t grasped_object;       /* 1 + the handle of the grasped object (soft bodies first, then
+                                   affine bodies), for IPC_Q_GRASP_RESULT; 0 = none */
+  int32_t pad3;
 } ipc_env_desc;
 
 typedef enum {
@@ -185,9 +188,15 @@ typedef enum {
   IPC_Q_CONTACT_HANDLES = 15, /* int32[n][2]: the bodies of the two sides of each contact (env-local
                               handles: soft bodies first, then affine bodies), in the order of
                               IPC_Q_CONTACTS */
-  IPC_Q_ENERGY_TRACE = 16  /* double[n]: the incremental potential (J) at each Newton iterate of the
+  IPC_Q_ENERGY_TRACE = 16, /* double[n]: the incremental potential (J) at each Newton iterate of the
                               env's current (or last) step, in iteration order, n <= max_newton
                               (Sec. II-C projected Newton: a diagnostic trace for parity checks) */
+  IPC_Q_GRASP_RESULT = 17  /* double[4] for an env that names its grasped object: in contact with
+                              another body at the current DOFs (0/1); the motion of the object's
+                              centre of mass (the mean of its points) over the last step, dt times
+                              its velocity (m); the stability label of Sec. III-D (1 when in contact
+                              and that motion is below eps_v dt); the rise of the centre since the
+                              env's initial state (m). IPC_ERR_ARG when the env names no object */
 } ipc_query_kind;
 
 /* Create / destroy a scene on desc->device. */

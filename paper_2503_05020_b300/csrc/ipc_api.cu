@@ -125,6 +125,10 @@ struct HostEnv {
   };
   std::vector<Joint> joints;
   int n_surf_pts = 0;  // points before the joint anchors
+  // the grasped object named by the descriptor (-1: none): a soft body's node range, or an
+  // affine body with the mean of its rest vertices; its centre of mass at the initial state
+  int obj = -1, obj_affine = 0, obj_first = 0, obj_count = 0;
+  double obj_xbar[3] = {0, 0, 0}, obj_com0[3] = {0, 0, 0};
   // state
   std::vector<double> x, v;
   int step = 0, status = ST_ACTIVE, reason = FAIL_NONE;
@@ -420,6 +424,30 @@ void build_env(HostEnv& h, const ipc_env_desc* D) {
     }
     hj.k = J.stiffness;
     h.joints.push_back(hj);
+  }
+  if (D->grasped_object < 0 || D->grasped_object > D->n_soft + D->n_affine)
+    fail_with(IPC_ERR_ARG, "env: grasped_object out of range");
+  h.obj = D->grasped_object - 1;
+  if (h.obj >= 0) {
+    if (h.obj < D->n_soft) {
+      int first = 0;
+      for (int b = 0; b < h.obj; ++b) first += D->soft[b].n_verts;
+      h.obj_first = first;
+      h.obj_count = D->soft[h.obj].n_verts;
+      for (int i = 0; i < h.obj_count; ++i)
+        for (int k = 0; k < 3; ++k) h.obj_com0[k] += h.x[3 * (first + i) + k] / h.obj_count;
+    } else {
+      const int a = h.obj - D->n_soft;
+      h.obj_affine = 1;
+      h.obj_first = a;
+      const auto& av = h.aff[a].verts;
+      const int nv = (int)av.size() / 3;
+      for (int i = 0; i < nv; ++i)
+        for (int k = 0; k < 3; ++k) h.obj_xbar[k] += av[3 * i + k] / nv;
+      const double* q = h.aff[a].q0;
+      for (int k = 0; k < 3; ++k)
+        h.obj_com0[k] = q[k] + h.obj_xbar[0] * q[3 + k] + h.obj_xbar[1] * q[6 + k] + h.obj_xbar[2] * q[9 + k];
+    }
   }
 }
 
@@ -2110,6 +2138,23 @@ struct ipc_scene {
     fail_with(IPC_ERR_ARG, "unknown env id " + std::to_string(id));
   }
   void select(int li) { launch(k_set_single, E, 128, E, e_sel.p, li); }
+  // the bodies of the two sides of each contact of env li at its current DOFs (env-local handles)
+  std::vector<int> contact_handles(int li) {
+    select(li);
+    launch(k_points, NP, 256, NP, (const int*)pt_node.p, (const double*)pt_xb.p, (const int*)body_node.p,
+           (const double*)x.p, ptx.p);
+    build_trees();
+    constraint_set(e_sel.p);
+    const int n = n_ct;
+    nflag.ensure(2 * (size_t)n + 2);
+    launch(k_contact_handles, n, 128, n, (const ContactRec*)ct.p, (const int*)pt_node.p, (const int*)body_node.p,
+           (const int*)node_handle.p, nflag.p);
+    std::vector<int> v(2 * (size_t)n);
+    if (n) CK(cudaMemcpyAsync(v.data(), nflag.p, 2 * n * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    ttri.built = tedge.built = false;
+    return v;
+  }
 };
 
 
@@ -2393,20 +2438,36 @@ ipc_status ipc_query(ipc_scene* s, int32_t env_id, int32_t kind, void* out, size
       return copy_out(v.data(), n * sizeof(double), out, out_bytes, written);
     }
     case IPC_Q_CONTACT_HANDLES: {
-      s->select(li);
-      s->launch(k_points, s->NP, 256, s->NP, (const int*)s->pt_node.p, (const double*)s->pt_xb.p,
-                (const int*)s->body_node.p, (const double*)s->x.p, s->ptx.p);
-      s->build_trees();
-      s->constraint_set(s->e_sel.p);
-      const int n = s->n_ct;
-      s->nflag.ensure(2 * (size_t)n + 2);
-      s->launch(k_contact_handles, n, 128, n, (const ContactRec*)s->ct.p, (const int*)s->pt_node.p,
-                (const int*)s->body_node.p, (const int*)s->node_handle.p, s->nflag.p);
-      std::vector<int> v(2 * (size_t)std::max(n, 1));
-      if (n) CK(cudaMemcpyAsync(v.data(), s->nflag.p, 2 * n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+      std::vector<int> v = s->contact_handles(li);
+      return copy_out(v.data(), v.size() * sizeof(int), out, out_bytes, written);
+    }
+    case IPC_Q_GRASP_RESULT: {
+      if (h.obj < 0) fail_with(IPC_ERR_ARG, "the env names no grasped object");
+      std::vector<double> xs(h.ndof), vs(h.ndof);
+      CK(cudaMemcpyAsync(xs.data(), s->x.p + o, h.ndof * 8, cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaMemcpyAsync(vs.data(), s->v.p + o, h.ndof * 8, cudaMemcpyDeviceToHost, s->stream));
       CK(cudaStreamSynchronize(s->stream));
-      s->ttri.built = s->tedge.built = false;
-      return copy_out(v.data(), 2 * n * sizeof(int), out, out_bytes, written);
+      double com[3] = {0, 0, 0}, vel[3] = {0, 0, 0};
+      if (!h.obj_affine) {
+        for (int i = 0; i < h.obj_count; ++i)
+          for (int k = 0; k < 3; ++k) {
+            com[k] += xs[3 * (h.obj_first + i) + k] / h.obj_count;
+            vel[k] += vs[3 * (h.obj_first + i) + k] / h.obj_count;
+          }
+      } else {
+        const size_t d = 3 * (size_t)h.nsv_verts + 12 * (size_t)h.obj_first;
+        for (int k = 0; k < 3; ++k) {
+          com[k] = xs[d + k] + h.obj_xbar[0] * xs[d + 3 + k] + h.obj_xbar[1] * xs[d + 6 + k] + h.obj_xbar[2] * xs[d + 9 + k];
+          vel[k] = vs[d + k] + h.obj_xbar[0] * vs[d + 3 + k] + h.obj_xbar[1] * vs[d + 6 + k] + h.obj_xbar[2] * vs[d + 9 + k];
+        }
+      }
+      std::vector<int> hd = s->contact_handles(li);
+      bool touch = false;
+      for (size_t c = 0; c + 1 < hd.size(); c += 2) touch |= (hd[c] == h.obj) != (hd[c + 1] == h.obj);
+      const double step = s->desc.dt * std::sqrt(vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+      double r[4] = {touch ? 1.0 : 0.0, step, (touch && step < s->desc.eps_v * s->desc.dt) ? 1.0 : 0.0,
+                     com[2] - h.obj_com0[2]};
+      return copy_out(r, sizeof(r), out, out_bytes, written);
     }
     case IPC_Q_FRICTION_FORCES: {
       const int n = s->n_fr;

@@ -23,7 +23,7 @@ FAIL_REASON = {0: "none", 1: "newton_cap", 2: "line_search", 3: "non_finite", 4:
 FP64, MIXED = 0, 1
 Q_DOFS, Q_VELOCITIES, Q_STATUS, Q_STATS, Q_CANDIDATES, Q_CONTACTS, Q_POINTS, Q_SIZES, Q_INTERSECTIONS, \
     Q_SCENE_COUNTERS, Q_ALL_STATUS, Q_KAPPA, Q_TET_STRESS, Q_CONTACT_FORCES, Q_FRICTION_FORCES, \
-    Q_CONTACT_HANDLES, Q_ENERGY_TRACE = range(17)
+    Q_CONTACT_HANDLES, Q_ENERGY_TRACE, Q_GRASP_RESULT = range(18)
 
 
 class IpcError(RuntimeError):
@@ -62,7 +62,7 @@ class EnvDesc(C.Structure):
     _fields_ = [("n_soft", C.c_int32), ("n_affine", C.c_int32), ("n_steps", C.c_int32), ("pad", C.c_int32),
                 ("soft", C.c_void_p), ("affine", C.c_void_p), ("friction_mu", C.c_double),
                 ("gravity_on", C.c_void_p), ("targets", C.c_void_p), ("n_joints", C.c_int32), ("pad2", C.c_int32),
-                ("joints", C.c_void_p)]
+                ("joints", C.c_void_p), ("grasped_object", C.c_int32), ("pad3", C.c_int32)]
 
 
 _lib = None
@@ -152,6 +152,9 @@ class _EnvMarshal:
                 jt[i].anchor_a[k], jt[i].anchor_b[k] = j["anchor_a"][k], j["anchor_b"][k]
         self.keep.append(jt)
         d.n_joints, d.joints = len(js), C.addressof(jt)
+        if "object" in env:  # 1 + the object's handle (soft bodies first, then affine bodies)
+            kind, k = env["object"]
+            d.grasped_object = 1 + (k if kind == "soft" else len(env["soft"]) + k)
         self.desc = d
 
 
@@ -264,6 +267,12 @@ class Scene:
     def tet_stress(self, eid: int) -> np.ndarray:
         """Von Mises stress (Pa) of each of the env's tets at its current DOFs."""
         return self._query(eid, Q_TET_STRESS, np.float64)
+
+    def grasp_result(self, eid: int) -> dict:
+        """Sec. III-D outcome of an env that names its grasped object: contact, the centre of
+        mass's motion over the last step (m), the stability label and the centre's rise (m)."""
+        v = self._query(eid, Q_GRASP_RESULT, np.float64)
+        return {"in_contact": bool(v[0]), "com_step": float(v[1]), "stable": bool(v[2]), "com_rise": float(v[3])}
 
     def energy_trace(self, eid: int) -> np.ndarray:
         """Incremental potential at each Newton iterate of the env's current (or last) step."""

@@ -209,10 +209,10 @@ class GraspServer:
                     req = active.pop(eid)
                     req.finished, req.status, req.reason, req.steps = t_now, st, reason, step
                     pts = sc.points(eid)
-                    v = sc.velocities(eid) if "object" in req.env else None
-                    hd = sc.contact_handles(eid) if "object" in req.env else None
                     req.result = {"dofs": sc.dofs(eid), "points": pts,
-                                  **object_result(req.env, pts, start_pts.pop(eid), v, hd, self.eps_v, self.dt)}
+                                  **object_result(req.env, pts, start_pts.pop(eid))}
+                    if "object" in req.env and hasattr(sc, "grasp_result"):
+                        req.result.update(sc.grasp_result(eid))  # the library's Sec. III-D label
                     done_in_scene.append(eid)
         for eid in done_in_scene:
             sc.remove_env(eid)

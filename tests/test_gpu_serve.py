@@ -82,3 +82,24 @@ def test_served_labels_and_held_object_match_the_oracle():
                 disp = float(np.abs(pts_o[sl] - initial_points(env)[sl]).max())
                 err = float(np.abs(r.result["points"][sl] - pts_o[sl]).max())
                 assert err <= 1e-4 * disp, (prec, err, disp)
+
+
+def test_grasp_result_query_matches_its_definition():
+    """IPC_Q_GRASP_RESULT of a finished serving request (the held 2.3k-tet object) against the
+    Sec. III-D outcome computed from the env's own point, velocity and contact queries: same
+    contact flag and label, the same centre-of-mass motion over the last step and rise."""
+    from paper_2503_05020_b300.serve import initial_points, object_result
+
+    p = S.scene_params(0.005)
+    env = S.serving_request_env(5)
+    sc = ipc.Scene(p)
+    eid = sc.add_env(env)
+    sc.step(len(env["targets"]))
+    assert sc.status(eid)["status"] == "DONE"
+    g = sc.grasp_result(eid)
+    ref = object_result(env, sc.points(eid), initial_points(env), sc.velocities(eid), sc.contact_handles(eid),
+                        p["eps_v"], p["dt"])
+    assert (g["in_contact"], g["stable"]) == (ref["in_contact"], ref["stable"]) == (True, True)
+    assert abs(g["com_step"] - ref["com_step"]) <= 1e-12 + 1e-9 * ref["com_step"]
+    assert abs(g["com_rise"] - ref["object_disp"][2]) <= 1e-12
+    assert abs(g["com_rise"] - env["lift"]) < 0.01  # held through the shake: it rose with the grippers

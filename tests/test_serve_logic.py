@@ -198,3 +198,13 @@ def test_stability_label_of_a_finished_request():
     assert not object_result(env, pts, pts, fast, touching, eps_v, dt)["stable"]
     r = object_result(env, pts, pts, slow, apart, eps_v, dt)
     assert not r["in_contact"] and not r["stable"]
+
+
+def test_binding_names_the_grasped_object_by_its_handle():
+    """The env descriptor's grasped_object is 1 + the object's handle (soft bodies first, then
+    affine bodies), 0 when the env names none."""
+    from paper_2503_05020_b300 import scenes as S
+
+    assert ipc._EnvMarshal(S.serving_request_env(4)).desc.grasped_object == 1  # soft body 0
+    assert ipc._EnvMarshal(S.pad_grasp_env(0)).desc.grasped_object == 3  # after two soft pads: affine 0
+    assert ipc._EnvMarshal(S.single_tet_env()).desc.grasped_object == 0
