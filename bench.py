@@ -373,7 +373,8 @@ def run_ours(args):
     clocks = ClockSampler(local)
     sc.profile(True)
     l0 = sc.launch_count()
-    st0 = [sc.status(e)["steps"] for e in ids]
+    st_before = [sc.status(e) for e in ids]
+    st0 = [s["steps"] for s in st_before]
     torch.cuda.synchronize()
     barrier()
     clocks.start()
@@ -420,8 +421,9 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
     e2e_value = job_throughput(all_steps, e2e_s)
     counters = sc.scene_counters(ids[0])
-    newton = sum(s["newton_iters"] for s in stats)
-    pcg_its = sum(s["pcg_iters"] for s in stats)
+    # iteration counts of the timed region only (the status counters are cumulative)
+    newton = sum(s["newton_iters"] for s in stats) - sum(s["newton_iters"] for s in st_before)
+    pcg_its = sum(s["pcg_iters"] for s in stats) - sum(s["pcg_iters"] for s in st_before)
     sc.close()
     del sc
 
@@ -467,7 +469,7 @@ def run_ours(args):
                              "note": "GPU idle time behind the host reads inside the timed ipc_step call: events "
                                      "before each wait and at the next kernel launch, on the scene's stream"},
         "counters_last_iteration": counters,
-        "newton_iters_per_env_step": round(newton / max(sum(s["steps"] for s in stats), 1), 2),
+        "newton_iters_per_env_step": round(newton / max(steps_done, 1), 2),
         "pcg_iters_per_newton": round(pcg_its / max(newton, 1), 1),
     }
     if world == 1 and args.serve_requests > 0:
@@ -553,7 +555,8 @@ def mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, device, ms
     for eid, i in zip(ids, live):
         sc.set_state(eid, *snap[i])
     sc.profile(True)
-    s0 = sum(sc.status(e)["steps"] for e in ids)
+    sts0 = [sc.status(e) for e in ids]
+    s0 = sum(st["steps"] for st in sts0)
     ms = timed_steps(sc, stream, args.steps)
     prof = sc.profile_read()
     sc.profile(False)
@@ -564,8 +567,8 @@ def mixed_leg(args, params, envs, snap, p_start, x_end, tets, stream, device, ms
         x_mixed[i] = sc.points(eid)
     failed_m = {i for i, st in zip(live, sts) if st["status"] == "FAILED"}
     failed = len(failed_m)
-    newton = sum(st["newton_iters"] for st in sts)
-    pcg_its = sum(st["pcg_iters"] for st in sts)
+    newton = sum(st["newton_iters"] for st in sts) - sum(st["newton_iters"] for st in sts0)
+    pcg_its = sum(st["pcg_iters"] for st in sts) - sum(st["pcg_iters"] for st in sts0)
     sc.close()
 
     def errors(xa, xb, rows):

@@ -124,9 +124,9 @@ def main() -> int:
     todo = [m for m in MUTATIONS if not a.names or m[0] in a.names]
     survived = 0
     with ThreadPoolExecutor(max(1, a.j)) as ex:
-        for name, verdict, detail in ex.map(lambda m: run_one(*m), todo):
-            survived += verdict != "KILLED"
-            print(f"{verdict:8s} {name:28s} {detail[:120]}", flush=True)
+        for name, outcome, detail in ex.map(lambda m: run_one(*m), todo):
+            survived += outcome != "KILLED"
+            print(f"{outcome:8s} {name:28s} {detail[:120]}", flush=True)
     print(f"{len(todo) - survived} of {len(todo)} killed")
     return 1 if survived else 0
 
