@@ -516,29 +516,39 @@ __global__ void k_barrier(int n_ct, const ContactRec* __restrict__ ct, const uin
     for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = g[i];
 }
 
-// Hessian mode: one block of BARRIER_HESS_THREADS per contact (a Newton iteration has a few
-// hundred contacts, so their latency, not the GPU's FP64 throughput, sets the time). Thread 0
-// forms the energy, gradient and 12x12 Hessian (FP64) in shared memory, the block projects it to
-// PSD in FP64 (FP32-warm-started Jacobi, one or two matrix elements per thread per round), and
-// its packed upper triangle is stored in the precision HT.
+// Hessian mode, in two launches. First one thread per contact forms the energy, gradient and
+// unprojected 12x12 Hessian (FP64; row-major into the scratch Hl, 144 values per contact): a
+// long dependent FP64 chain, so every contact of the batch gets its own thread and the chains
+// overlap. Then one block of BARRIER_HESS_THREADS per contact projects its Hessian to PSD in
+// FP64 (FP32-warm-started Jacobi, one or two matrix elements per thread per round) and stores
+// the packed upper triangle in the precision HT. The split keeps the chain's registers out of
+// the projection's blocks, so many contacts are projected per SM at once.
+constexpr int BARRIER_LOCAL_THREADS = 64;
+__global__ void __launch_bounds__(BARRIER_LOCAL_THREADS)
+    k_barrier_local(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
+                    const double* __restrict__ ptx, double h2, double dhat, const double* __restrict__ kappa,
+                    double* __restrict__ sE, double* __restrict__ sg, double* __restrict__ Hl) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_ct) return;
+  const ContactRec c = ct[k];
+  if (!act[c.env]) return;
+  double g[12];
+  sE[k] = barrier_eval<MODE_HESS>(c, ptx, h2, dhat, kappa[c.env], g, Hl + 144 * (long)k);
+  for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = g[i];
+}
+
 constexpr int BARRIER_HESS_THREADS = 128;
 template <class HT>
-__global__ void __launch_bounds__(BARRIER_HESS_THREADS)
+__global__ void __launch_bounds__(BARRIER_HESS_THREADS, 12)
     k_barrier_hess(int n_ct, const ContactRec* __restrict__ ct, const uint8_t* __restrict__ act,
-                   const double* __restrict__ ptx, double h2, double dhat, const double* __restrict__ kappa,
-                   double* __restrict__ sE, double* __restrict__ sg, HT* __restrict__ sH) {
+                   const double* __restrict__ Hl, HT* __restrict__ sH) {
   static_assert(144 <= 2 * BARRIER_HESS_THREADS, "two matrix elements per thread at most");
   __shared__ double A[144], V[144], W[144], R[36];
   __shared__ float Af[144], Vf[144], Rf[36];
   const int k = blockIdx.x, t = threadIdx.x;
   if (k >= n_ct) return;  // uniform over the block
-  const ContactRec c = ct[k];
-  if (!act[c.env]) return;
-  if (t == 0) {
-    double g[12];
-    sE[k] = barrier_eval<MODE_HESS>(c, ptx, h2, dhat, kappa[c.env], g, A);
-    for (int i = 0; i < 12; ++i) sg[12 * (long)k + i] = g[i];
-  }
+  if (!act[ct[k].env]) return;
+  for (int e = t; e < 144; e += BARRIER_HESS_THREADS) A[e] = Hl[144 * (long)k + e];
   __syncthreads();
   project_psd_block_warm<12>(A, V, W, R, Af, Vf, Rf);
   for (int e = t; e < 144; e += BARRIER_HESS_THREADS) {

@@ -566,6 +566,7 @@ struct ipc_scene {
   DBuf<unsigned long long> st_keys, st_keys2;
   DBuf<unsigned> st_vals, st_vals2;
   DBuf<double> sE, sg, sH, st_t, ns_w, ns_xb, st_xb;
+  DBuf<double> ct_Hl;  // unprojected 12x12 barrier Hessians of one evaluation (144 per contact)
   DBuf<int> st_node;  // per stencil point: its node, or -1 - the p node of its affine body
   DBuf<long long> pcg_iters;
   DBuf<int> st_hist, root_off_tri, root_off_ed;
@@ -1343,6 +1344,7 @@ struct ipc_scene {
     sg.ensure(12 * (size_t)ns + 12);
     st_t.ensure(12 * (size_t)ns + 12);
     st_node.ensure(4 * (size_t)ns + 4);
+    ct_Hl.ensure(144 * (size_t)n_ct + 144);
     if (mixed()) {
       f_sH.ensure(78 * (size_t)ns + 78);
       f_st_t.ensure(12 * (size_t)ns + 12);
@@ -1411,8 +1413,12 @@ struct ipc_scene {
     int cfam = MODE == MODE_ENERGY ? IPC_PROF_LS_ENERGY : IPC_PROF_CONTACT;
     pbeg(cfam);
     if constexpr (MODE == MODE_HESS)
+    {
+      launch(k_barrier_local, n_ct, BARRIER_LOCAL_THREADS, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p,
+             h2, desc.dhat, (const double*)e_kappa.p, sE.p, sg.p, ct_Hl.p);
       launch(k_barrier_hess<HT>, (long)BARRIER_HESS_THREADS * n_ct, BARRIER_HESS_THREADS, n_ct, (const ContactRec*)ct.p,
-             act, (const double*)ptx.p, h2, desc.dhat, (const double*)e_kappa.p, sE.p, sg.p, sHp);
+             act, (const double*)ct_Hl.p, sHp);
+    }
     else
       launch(k_barrier<MODE>, n_ct, 64, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p, h2, desc.dhat,
              (const double*)e_kappa.p, sE.p, sg.p);
