@@ -46,7 +46,8 @@ __global__ void k_points(int n_pts, const int* __restrict__ pt_node, const doubl
 //   twist (i,j):   mu + (lam lnJ - mu)/(s_i s_j),  U (e_i e_j^T - e_j e_i^T) V^T / sqrt 2,
 //   flip (i,j):    mu + (mu - lam lnJ)/(s_i s_j),  U (e_i e_j^T + e_j e_i^T) V^T / sqrt 2.
 // Negative eigenvalues are dropped (projected Newton); the 12x12 Hessian is
-// h^2 V sum_m lam_m^+ w_m w_m^T with w_m[a] = Q_m b_a (b_a: shape-function gradients).
+// h^2 V sum_m lam_m^+ w_m w_m^T with w_m[a] = Q_m b_a (b_a: shape-function gradients), formed
+// blockwise in the frame of the SVD (tet_hessian).
 // F = Ds Dm^-1, its cofactor, J and the weighted energy h^2 V Psi(F). Not inlined: every mode
 // calls the same machine code, so Newton and line-search energies round identically.
 __device__ __noinline__ double tet_energy(d3 x0, d3 x1, d3 x2, d3 x3, const double* __restrict__ Bm, double mu,
@@ -119,56 +120,70 @@ DEV void tet_hessian(const double* F64, double mu64, double lam64, double lnJ64,
   HT cb[4][3];
   for (int a = 0; a < 4; ++a)
     for (int k = 0; k < 3; ++k) cb[a][k] = V[k] * b[a][0] + V[3 + k] * b[a][1] + V[6 + k] * b[a][2];
-  HT Hb[90];
-  for (int i = 0; i < 90; ++i) Hb[i] = HT(0);
-  // accumulate lam * w w^T over the 10 upper 3x3 blocks; w_a = U m_a where m_a = M c_a
-  auto add_mode = [&](HT lm, const HT (*m)[3]) {
-    if (!(lm > HT(0))) return;
-    HT wv[4][3];
-    for (int a = 0; a < 4; ++a)
-      for (int r = 0; r < 3; ++r) wv[a][r] = U[3 * r] * m[a][0] + U[3 * r + 1] * m[a][1] + U[3 * r + 2] * m[a][2];
-    int blk = 0;
-    for (int a = 0; a < 4; ++a)
-      for (int bb = a; bb < 4; ++bb, ++blk)
-        for (int r = 0; r < 3; ++r)
-          for (int c = 0; c < 3; ++c) Hb[9 * blk + 3 * r + c] += lm * wv[a][r] * wv[bb][c];
-  };
-  // scaling modes
+  // The projected d2Psi/dF2 in the frame of the SVD (F^ = U^T F V = diag(s)) is block-diagonal:
+  // the scaling block on the (ii, kk) entries, projected to S+ (its eigenpairs with positive
+  // eigenvalue; the block itself when it is positive definite, the common case, which needs no
+  // eigen-decomposition), and for each pair i < j the 2x2 block of the twist and flip modes on
+  // the (ij, ji) entries, (lt+ + lf+)/2 on its diagonal and (lf+ - lt+)/2 off it. With
+  // dF^ = sum_a dx^_a c_a^T (x^ = U^T x, c_a = V^T b_a), the 3x3 block (a, b) of the tet Hessian
+  // in that frame is
+  //   H^_ab[i][i] = S+_ii ca_i cb_i + sum_{j != i} P_ij ca_j cb_j,
+  //   H^_ab[i][k] = S+_ik ca_i cb_k + Q_ik ca_k cb_i   (i != k),
+  // and H_ab = U H^_ab U^T: the same sum of the nine clamped modes as lam_m w_m w_m^T, without
+  // forming each mode.
   HT A[9];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j)
       A[3 * i + j] = (i == j) ? mu + (mu - lam * lnJ + lam) / (s[i] * s[i]) : lam / (s[i] * s[j]);
-  HT la[3], av[9];
-  eig_sym3<HT>(A, la, av);
-  for (int k = 0; k < 3; ++k) {
-    HT m[4][3];
-    for (int a = 0; a < 4; ++a) {
-      m[a][0] = av[k] * cb[a][0];
-      m[a][1] = av[3 + k] * cb[a][1];
-      m[a][2] = av[6 + k] * cb[a][2];
+  HT Sp[9];
+  const HT m2 = A[0] * A[4] - A[1] * A[1];
+  const HT det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                 A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (A[0] > HT(0) && m2 > HT(0) && det > HT(0)) {  // leading minors positive: A is its own projection
+    for (int i = 0; i < 9; ++i) Sp[i] = A[i];
+  } else {
+    HT la[3], av[9];
+    eig_sym3<HT>(A, la, av);
+    for (int i = 0; i < 9; ++i) Sp[i] = HT(0);
+    for (int k = 0; k < 3; ++k) {
+      if (!(la[k] > HT(0))) continue;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Sp[3 * i + j] += la[k] * av[3 * i + k] * av[3 * j + k];
     }
-    add_mode(la[k], m);
   }
-  // twist and flip modes of each pair: (e_i e_j^T -/+ e_j e_i^T) c = e_i c_j -/+ e_j c_i
-  const HT r2 = HT(0.70710678118654752440);
+  // twist (lt) and flip (lf) eigenvalues of the pairs (0,1), (1,2), (0,2), clamped at zero
+  HT Pp[3], Qp[3];
   for (int pr = 0; pr < 3; ++pr) {
-    int i = pr == 2 ? 0 : pr, j = pr == 2 ? 2 : pr + 1;
-    HT ss = s[i] * s[j];
-    HT lt = mu + (lam * lnJ - mu) / ss, lf = mu + (mu - lam * lnJ) / ss;
-    HT mt[4][3], mf[4][3];
-    for (int a = 0; a < 4; ++a) {
-      HT ci = cb[a][i], cj = cb[a][j];
-      for (int k = 0; k < 3; ++k) mt[a][k] = mf[a][k] = HT(0);
-      mt[a][i] = r2 * cj;
-      mt[a][j] = -r2 * ci;
-      mf[a][i] = r2 * cj;
-      mf[a][j] = r2 * ci;
-    }
-    add_mode(lt, mt);
-    add_mode(lf, mf);
+    const int i = pr == 2 ? 0 : pr, j = pr == 2 ? 2 : pr + 1;
+    const HT ss = s[i] * s[j];
+    const HT lt = fmax(mu + (lam * lnJ - mu) / ss, HT(0)), lf = fmax(mu + (mu - lam * lnJ) / ss, HT(0));
+    Pp[pr] = HT(0.5) * (lt + lf);
+    Qp[pr] = HT(0.5) * (lf - lt);
   }
   const HT w = HT(w64);
-  for (int i = 0; i < 90; ++i) out[i] = w * Hb[i];
+  int blk = 0;
+  for (int a = 0; a < 4; ++a)
+    for (int bb = a; bb < 4; ++bb, ++blk) {
+      const HT* ca = cb[a];
+      const HT* cc = cb[bb];
+      const HT p0 = ca[0] * cc[0], p1 = ca[1] * cc[1], p2 = ca[2] * cc[2];
+      HT Hh[9];
+      Hh[0] = Sp[0] * p0 + Pp[0] * p1 + Pp[2] * p2;
+      Hh[4] = Sp[4] * p1 + Pp[0] * p0 + Pp[1] * p2;
+      Hh[8] = Sp[8] * p2 + Pp[2] * p0 + Pp[1] * p1;
+      Hh[1] = Sp[1] * ca[0] * cc[1] + Qp[0] * ca[1] * cc[0];
+      Hh[3] = Sp[3] * ca[1] * cc[0] + Qp[0] * ca[0] * cc[1];
+      Hh[5] = Sp[5] * ca[1] * cc[2] + Qp[1] * ca[2] * cc[1];
+      Hh[7] = Sp[7] * ca[2] * cc[1] + Qp[1] * ca[1] * cc[2];
+      Hh[2] = Sp[2] * ca[0] * cc[2] + Qp[2] * ca[2] * cc[0];
+      Hh[6] = Sp[6] * ca[2] * cc[0] + Qp[2] * ca[0] * cc[2];
+      HT T[9];  // U H^
+      for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) T[3 * r + k] = U[3 * r] * Hh[k] + U[3 * r + 1] * Hh[3 + k] + U[3 * r + 2] * Hh[6 + k];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+          out[9 * blk + 3 * r + c] = w * (T[3 * r] * U[3 * c] + T[3 * r + 1] * U[3 * c + 1] + T[3 * r + 2] * U[3 * c + 2]);
+    }
 }
 
 template <int MODE, class HT = double>
