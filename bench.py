@@ -290,6 +290,41 @@ def roofline(prof, precision, traffic=None):
     return base
 
 
+# Algorithmic bytes per tet of a Neo-Hookean Hessian evaluation: the tet (int4), its 12
+# parameters, env id and 4 gathered nodes in; energy, 12 gradient and 78 Hessian entries out
+# (the Hessian in FP32 under mixed precision).
+ELASTIC_BYTES_PER_TET = {"fp64": 16 + 96 + 4 + 96 + 8 + 96 + 78 * 8, "mixed": 16 + 96 + 4 + 96 + 8 + 96 + 78 * 4}
+
+# kernels of each profiled family, as the library groups them
+FAMILY_KERNELS = {
+    "pcg_solve": "k_pcg_cluster (persistent per-environment PCG)",
+    "elastic": "k_elastic<HESS> (Neo-Hookean energy, gradient, projected Hessian)",
+    "contact": "k_barrier_local + k_barrier_hess + k_friction + k_joint (Hessian evaluations; side stream)",
+    "assembly": "stencil incidence sort, k_assemble_grad, k_assemble_bsr, k_precond_soft, k_precond_body",
+    "ccd": "step filter: swept-box cover test or collect traversals, k_accd_pairs",
+    "broad": "constraint-set collect traversals (k_trav_pt, k_trav_ee)",
+}
+
+
+def kernel_fractions(prof, precision):
+    """Achieved algorithmic HBM bandwidth of every profiled kernel family over the timed region:
+    the family's algorithmic bytes (counted by the library from each launch's sizes, or on the
+    device; elastic: tets x bytes per tet) over the summed CUDA-event time of its launches, and
+    that as a fraction of the measured HBM copy rate."""
+    hbm, kind = peaks()
+    out = {}
+    for fam, what in FAMILY_KERNELS.items():
+        p = prof.get(fam)
+        if not p or p["ms"] <= 0 or p["work"] <= 0:
+            continue
+        work = p["work"] * (ELASTIC_BYTES_PER_TET[precision] if fam == "elastic" else 1.0)
+        gbs = work / (p["ms"] / 1000.0) / 1e9
+        out[fam] = {"kernels": what, "launches": int(p["launches"]), "ms": round(p["ms"], 2),
+                    "bytes": float(f"{work:.4g}"), "gb_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+    out["peak"] = {"hbm_gbs": hbm, "source": f"{kind} hbm_gbs"}
+    return out
+
+
 def cpu_oracle_sample(envs, states, params, n_threads):
     """Time the oracle on n_threads envs x 1 step from the given states (bounded CPU sample)."""
     from oracle import oracle as O
@@ -464,6 +499,7 @@ def run_ours(args):
         "gpu_launches": int(launches), "clocks": clk, "plain_fp64": plain, "mixed_precision": mixed, "serving": None,
         "env_steps_done": int(steps_done), "envs_failed": int(failed),
         "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k not in ("pcg_flops", "host_idle")},
+        "kernel_roofline": kernel_fractions(prof, args.precision),
         "host_round_trips": {"count": int(prof["host_idle"]["launches"]), "gpu_idle_ms": round(prof["host_idle"]["ms"], 2),
                              "gpu_idle_frac": round(prof["host_idle"]["ms"] / t_max, 4) if t_max > 0 else None,
                              "note": "GPU idle time behind the host reads inside the timed ipc_step call: events "

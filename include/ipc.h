@@ -320,7 +320,11 @@ typedef enum {
 ipc_status ipc_profile_enable(ipc_scene* scene, int32_t on);
 /* Launches, summed event time (ms) and algorithmic work of one family since profiling was
  * turned on. work: SPMV = algorithmic bytes (BSR blocks 76 B, node vectors 56 B, stencil
- * entries 28 B, body blocks 1344 B), ELASTIC = tets processed, others 0. Synchronises. */
+ * entries 28 B, body blocks 1344 B); PCG_SOLVE = algorithmic bytes and PCG_FLOPS = operations,
+ * both counted on the device; ELASTIC = tets processed by the Hessian evaluations; CONTACT,
+ * CCD, BROAD, ASSEMBLY = algorithmic bytes counted on the host from the sizes of each launch
+ * (records, gathered points and outputs once each, over the launch's whole extent); others 0.
+ * Synchronises. */
 ipc_status ipc_profile_read(ipc_scene* scene, int32_t family, int64_t* launches, double* ms, double* work);
 
 const char* ipc_last_error(void);

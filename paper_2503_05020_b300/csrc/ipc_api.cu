@@ -628,6 +628,19 @@ struct ipc_scene {
     graph_ev.clear();
   }
   unsigned long long* punits(int fam) { return prof_on ? prof_units.p + fam : nullptr; }
+  // algorithmic bytes of a family's launches that the host can count from the sizes it launches
+  // with (the launch's whole extent: records, gathered points and outputs, each once)
+  double prof_host_work[IPC_PROF_COUNT] = {0};
+  void pwork(int fam, double bytes) {
+    if (prof_on && !capturing) prof_host_work[fam] += bytes;
+  }
+  // one pair of collect traversals (point-triangle, edge-edge) that listed np + ne candidates:
+  // query records (surface vertex ids and point, edge ids and box), the leaf boxes and the FP32
+  // node boxes with child links of both trees, the per-query counts and the listed partners
+  double traversal_bytes(int np, int ne) const {
+    return (double)NSV * (4 + 4 + 24) + (double)NED * (8 + 4 + 48) + (double)(NTR + NED) * 48 +
+           2.0 * (NTR + NED) * 40 + (double)(NSV + NED) * 4 + (double)(np + ne) * 4;
+  }
   // pinned host scratch
   int* hpin = nullptr;
 
@@ -1276,6 +1289,7 @@ struct ipc_scene {
     scan(cnt_pt.p, NSV, off_pt.p, false);
     scan(cnt_ee.p, NED, off_ee.p, false);
     const bool spilled = read_totals(off_pt.p + NSV, off_ee.p + NED, &n_pt, &n_ee);
+    pwork(IPC_PROF_BROAD, traversal_bytes(n_pt, n_ee));
     int nc = n_pt + n_ee;
     cand_j.ensure(nc + 1);
     cand_q.ensure(nc + 1);
@@ -1412,6 +1426,13 @@ struct ipc_scene {
              (const double*)body_pd.p, h2, h2 * desc.kappa_affine, bodyE.p, body_g.p);
     int cfam = MODE == MODE_ENERGY ? IPC_PROF_LS_ENERGY : IPC_PROF_CONTACT;
     pbeg(cfam);
+    if constexpr (MODE != MODE_ENERGY) {
+      // per stencil: record, gathered points (friction: at x and x^t), barrier stiffness; energy,
+      // 12 gradient and (Hessian evaluations) 78 packed Hessian entries out
+      const double hb = MODE == MODE_HESS ? 78.0 * sizeof(HT) : 0.0;
+      pwork(IPC_PROF_CONTACT, (double)n_ct * (40 + 96 + 8 + 8 + 96 + hb) + (double)n_fr * (88 + 192 + 8 + 96 + hb) +
+                                  (double)n_jt * (24 + 48 + 8 + 96 + hb));
+    }
     if constexpr (MODE == MODE_HESS)
     {
       launch(k_barrier_local, n_ct, BARRIER_LOCAL_THREADS, n_ct, (const ContactRec*)ct.p, act, (const double*)ptx.p,
@@ -1816,6 +1837,15 @@ struct ipc_scene {
     if (mixed()) assemble_h<float>(act);
     else assemble_h<double>(act);
     pend(IPC_PROF_ASSEMBLY);
+    // gradient gather (per node: x, x~, mass, offsets, the gradient out; per tet corner and per
+    // stencil entry: index and 3 gradient values), sliced-ELL gather (per block: row, column,
+    // offsets, position and 9 values out; per tet-block contribution: index and 9 values), the
+    // soft and body preconditioner blocks (read and written once); the incidence sort is not
+    // counted
+    const double b = mixed() ? 4.0 : 8.0;
+    pwork(IPC_PROF_ASSEMBLY, (double)NN * 88 + 4.0 * NT * 28 + (double)n_inc * 32 + (double)NNZB * (24 + 9 * b) +
+                                 16.0 * NT * (4 + 9 * b) + (double)NN * (8 + 18 * b) + (double)n_inc * (4 + 9 * b) +
+                                 (double)NB * 288 * b);
   }
   // sliced-ELL values and block-Jacobi blocks in the Hessian precision HT
   template <class HT>
@@ -1888,6 +1918,7 @@ struct ipc_scene {
            (const double*)pte.p, r, (const double*)keep_ed.p, e_count.p + 2);
     launch(k_swept_inside<1>, NSV, 256, NSV, (const int*)sv_pt.p, (const int*)sv_env.p, act, (const double*)ptx.p,
            (const double*)pte.p, r, (const double*)keep_sv.p, e_count.p + 2);
+    pwork(IPC_PROF_CCD, (double)NTR * (3 * 48 + 48) + (double)NED * (2 * 48 + 48) + (double)NSV * (48 + 48));
     return read_int(e_count.p + 2) == 0;
   }
   // CCD step filter on the envs in act: swept-box candidates at [x, x + p] (ptx, pte current),
@@ -1923,6 +1954,7 @@ struct ipc_scene {
     scan(ccd_cnt_ee.p, NED, ccd_off_ee.p, false);
     int np = 0, ne = 0;
     const bool spilled = read_totals(ccd_off_pt.p + NSV, ccd_off_ee.p + NED, &np, &ne);
+    pwork(IPC_PROF_CCD, traversal_bytes(np, ne));
     ccd_np = np;
     ccd_ne = ne;
     ccd_j.ensure(np + ne + 1);
@@ -1969,6 +2001,7 @@ struct ipc_scene {
   // overlap are tested
   void accd_all(EnvCtl C, bool keep) {
     if (ccd_np + ccd_ne == 0) return;
+    pwork(IPC_PROF_CCD, (double)(ccd_np + ccd_ne) * (40 + 4 * 48));  // pair record, x and p of 4 points
     launch(k_accd_pairs, ccd_np + ccd_ne, 128, ccd_np + ccd_ne, (const ContactRec*)ccd_rec.p, (const double*)ptx.p,
            (const double*)ptp.p, keep ? (const double*)pte.p : nullptr, C);
   }
@@ -2689,6 +2722,7 @@ ipc_status ipc_profile_enable(ipc_scene* s, int32_t on) {
     s->prof_ev[f].clear();
     s->prof_launches[f] = 0;
     s->prof_graph_ms[f] = 0.0;
+    s->prof_host_work[f] = 0.0;
   }
   s->prof_units.ensure(IPC_PROF_COUNT);
   s->prof_units.zero(s->stream, IPC_PROF_COUNT);
@@ -2715,7 +2749,7 @@ ipc_status ipc_profile_read(ipc_scene* s, int32_t fam, int64_t* launches, double
   if (s->prof_units.p) CK(cudaMemcpy(u, s->prof_units.p, sizeof(u), cudaMemcpyDeviceToHost));
   if (launches) *launches = s->prof_launches[tf];
   if (ms) *ms = t;
-  if (work) *work = (double)u[fam];
+  if (work) *work = (double)u[fam] + s->prof_host_work[fam];
   API_END
 }
 

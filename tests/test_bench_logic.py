@@ -32,6 +32,26 @@ def test_roofline_picks_the_bound_by_the_ridge_point():
     assert bench.roofline(_prof(0.0, 0, 0.0, 0.0), "fp64") is None
 
 
+def test_kernel_fractions_divide_each_family_s_bytes_by_its_event_time():
+    hbm, _ = bench.peaks()
+    z = {"ms": 0.0, "launches": 0, "work": 0.0}
+    prof = {k: dict(z) for k in ("spmv", "pcg_vector", "ls_energy", "pcg_flops", "host_idle")}
+    prof["pcg_solve"] = {"ms": 100.0, "launches": 4, "work": 3e11}
+    prof["elastic"] = {"ms": 20.0, "launches": 2, "work": 1e6}  # tets
+    prof["contact"] = {"ms": 5.0, "launches": 2, "work": 2e9}
+    prof["assembly"] = dict(z)  # no launch in the window: left out
+    prof["ccd"] = {"ms": 1.0, "launches": 5, "work": 1e8}
+    prof["broad"] = {"ms": 0.0, "launches": 0, "work": 0.0}
+    for prec, per_tet in (("fp64", 940), ("mixed", 628)):
+        t = bench.kernel_fractions(prof, prec)
+        assert set(t) == {"pcg_solve", "elastic", "contact", "ccd", "peak"}
+        assert abs(t["pcg_solve"]["gb_s"] - 3e11 / 0.1 / 1e9) < 0.1
+        assert t["elastic"]["bytes"] == 1e6 * per_tet
+        assert abs(t["elastic"]["gb_s"] - 1e6 * per_tet / 0.02 / 1e9) < 0.1
+        assert abs(t["contact"]["hbm_frac"] - 2e9 / 5e-3 / 1e9 / hbm) < 1e-4
+        assert t["ccd"]["launches"] == 5 and t["peak"]["hbm_gbs"] == hbm
+
+
 def test_clock_record_reports_median_clock_and_active_reasons():
     fd, path = tempfile.mkstemp(suffix=".csv")
     rows = ["0, 1900, 2032, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
