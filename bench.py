@@ -498,6 +498,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(h_out.nbytes)},
         "gpu_launches": int(launches), "clocks": clk, "plain_fp64": plain, "mixed_precision": mixed, "serving": None,
         "env_steps_done": int(steps_done), "envs_failed": int(failed),
+        "failed_envs": [{"env": int(ids_global[i]), "tets": int(tets[i]), "reason": stats[i]["reason"],
+                         "step": int(stats[i]["step"])} for i in range(len(ids)) if stats[i]["status"] == "FAILED"],
         "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items() if k not in ("pcg_flops", "host_idle")},
         "kernel_roofline": kernel_fractions(prof, args.precision),
         "host_round_trips": {"count": int(prof["host_idle"]["launches"]), "gpu_idle_ms": round(prof["host_idle"]["ms"], 2),
