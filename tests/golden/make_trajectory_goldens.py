@@ -2,7 +2,7 @@
 
 Each case steps one seeded grasp environment on the plain FP64 CPU oracle for 100 steps or more
 in the parity settings (Newton tolerance x1e-3, CG to 1e-12), from the contact-phase start state
-its schedule reaches at step 20 (the pad grasp: from its open pads at step 0),
+its schedule reaches at step 20 (the pad grasp and the hand: from their open grippers at step 0),
 and stores a sample of its DOFs every 20 steps. The pad grasp's window stops at the end of its
 closing: at this tolerance the oracle's Newton loop reaches its iteration cap at the first
 lifting step, its line search halving the step down to 3e-11. One oracle step of
@@ -59,6 +59,12 @@ CASES = {
         scene="scenes.uneven_batch_env(22): a 4.4k-tet star-shaped soft object between one pair of kinematic "
               "plates (the uneven batch's env 22), dt 5 ms, from the step-20 contact state",
         build=lambda: S.uneven_batch_env(22), params=lambda: _params(), start=START_STEP, steps=N_STEPS),
+    "hand_0": dict(
+        scene="scenes.hand_grasp_env(0, n_steps=300, close_steps=200): 20 hinged PD-driven affine links "
+              "curling onto a ~22k-tet star-shaped soft object, dhat 5e-4 m, dt 5 ms, from the open hand "
+              "(step 0) through the first 200 steps of the closing",
+        build=lambda: S.hand_grasp_env(0, n_steps=300, close_steps=200), params=lambda: _params(5e-4),
+        start=0, steps=200),
 }
 
 

@@ -12,7 +12,8 @@ the generators is refused, not compared.
 Cases: the pad configuration's env 0 (two ~5k-tet soft pads closing on a rigid hull, steps
 0-100, gravity off); two small envs of the uneven batch stepped together from their contact
 state at step 20 to step 120 (a 2.3k-tet object between two pairs of plates, lifted, and a
-4.4k-tet object between one pair, which slips out and falls once gravity is on).
+4.4k-tet object between one pair, which slips out and falls once gravity is on). The hinged
+hand's case is in `tests/test_gpu_zz_hand_trajectory.py`.
 """
 import importlib.util
 import json
