@@ -35,3 +35,71 @@ def test_golden_matches_its_generators(case):
     # the env is still stepping at the end of the window (not failed, schedule not finished)
     assert gold["final_status"]["status"] == "ACTIVE"
     assert gold["final_status"]["step"] == c["start"] + c["steps"]
+
+
+def _checkpoints(case):
+    """(env, start DOFs, sampled indices, [(steps, DOFs with the sampled entries of that
+    checkpoint)]) of a stored trajectory."""
+    with open(G.golden_path(case)) as f:
+        gold = json.load(f)
+    c = G.CASES[case]
+    env = c["build"]()
+    x0, _ = G.S.grasp_state_at(env, c["start"])
+    idx = np.asarray(gold["dof_indices"])
+    out = []
+    for chk in gold["checkpoints"]:
+        x = x0.copy()
+        x[idx] = chk["dofs"]
+        out.append((chk["steps"], x))
+    return env, x0, idx, out
+
+
+def _soft0_mean_shift(env, x0, idx, x):
+    n0 = len(env["soft"][0]["verts"])
+    sel = idx[idx < 3 * n0]
+    return (x[sel] - x0[sel]).reshape(-1, 3).mean(axis=0)
+
+
+def test_stored_uneven_envs_hold_or_drop_their_objects():
+    """The oracle's plate squeezes end the way their scenes make them: env 8's object rises with
+    its two plate pairs (3 cm by step 120) within 1%; env 22's object, between one pair, slips out
+    once gravity is on and has fallen more than 10 cm while the plates rose 3 cm."""
+    for case, held in (("uneven_8", True), ("uneven_22", False)):
+        env, x0, idx, chks = _checkpoints(case)
+        steps, x = chks[-1]
+        base = 3 * sum(len(s["verts"]) for s in env["soft"])
+        plate_rise = x[base + 2] - x0[base + 2]  # first plate's translation z
+        assert abs(plate_rise - 0.03) < 1e-9, plate_rise
+        dz = _soft0_mean_shift(env, x0, idx, x)[2]
+        if held:
+            assert abs(dz - plate_rise) < 0.01 * plate_rise, dz
+        else:
+            assert dz < -0.1, dz
+
+
+def test_stored_pad_closing_squeezes_the_hull_in_place():
+    """With gravity off the two pads close 3.5 mm each from opposite sides: the rigid hull
+    between them moves less than 0.5 mm and its A stays within 1e-2 of a rotation's."""
+    env, x0, idx, chks = _checkpoints("pad_grasp_0")
+    base = 3 * sum(len(s["verts"]) for s in env["soft"])
+    for steps, x in chks:
+        assert np.abs(x[base:base + 3] - x0[base:base + 3]).max() < 5e-4, steps
+        A = x[base + 3:base + 12].reshape(3, 3).T
+        assert np.abs(A @ A.T - np.eye(3)).max() < 1e-2, steps
+    shift = _soft0_mean_shift(env, x0, idx, chks[-1][1])
+    assert abs(shift[0] + 3.5e-3) < 5e-4, shift  # the first pad's mean moves with its base layer
+
+
+def test_stored_hand_leaves_the_object_at_rest_until_the_fingers_arrive():
+    """Gravity is off while the hand closes: no force acts on the free soft object until a finger
+    reaches it, so its sampled vertices stay where they started (to rounding) through step 180,
+    and the fingers have moved it by step 200."""
+    env, x0, idx, chks = _checkpoints("hand_0")
+    n0 = len(env["soft"][0]["verts"])
+    sel = idx[idx < 3 * n0]
+    for steps, x in chks:
+        moved = np.abs(x[sel] - x0[sel]).max()
+        if steps <= 180:
+            assert moved < 1e-12, (steps, moved)
+        else:
+            assert moved > 1e-3, (steps, moved)
