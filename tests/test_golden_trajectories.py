@@ -103,3 +103,23 @@ def test_stored_hand_leaves_the_object_at_rest_until_the_fingers_arrive():
             assert moved < 1e-12, (steps, moved)
         else:
             assert moved > 1e-3, (steps, moved)
+
+
+@pytest.mark.slow
+def test_oracle_still_computes_the_first_stored_checkpoint():
+    """The fingerprints tie a golden to its inputs; this ties it to the oracle's code: the first
+    20 steps of the smallest case, rerun now, give the stored DOFs bit for bit."""
+    from oracle import oracle as O
+
+    case = "uneven_8"
+    with open(G.golden_path(case)) as f:
+        gold = json.load(f)
+    c = G.CASES[case]
+    env, params = c["build"](), c["params"]()
+    x0, v0 = G.S.grasp_state_at(env, c["start"])
+    o = O.OracleEnv(params, env)
+    o.set_state(x0, v0, c["start"])
+    o.step(G.EVERY)
+    x, _ = o.state()
+    idx = np.asarray(gold["dof_indices"])
+    assert np.array_equal(x[idx], np.asarray(gold["checkpoints"][0]["dofs"]))
