@@ -41,6 +41,12 @@ MUTATIONS = [
     ("friction_f0_constant", "+ y * y / eh + eh / 3.0;", "+ y * y / eh;"),
     ("friction_f1_slope", "*f1 = -y * y / (eh * eh) + 2.0 * y / eh;", "*f1 = -y * y / (eh * eh) + y / eh;"),
     ("friction_lambda_kappa", "f.lambda = e.kappa * moll * std::fabs(b1);", "f.lambda = moll * std::fabs(b1);"),
+    ("friction_mu", "double s = h2 * e.mu * f.lambda;", "double s = h2 * f.lambda;"),
+    ("friction_no_tangent_projection",
+     "double u[3] = {rel[0] - nr * f.n[0], rel[1] - nr * f.n[1], rel[2] - nr * f.n[2]};",
+     "double u[3] = {rel[0], rel[1], rel[2]};"),
+    ("barrier_energy_h2", "Ebar += h2 * E.v;", "Ebar += E.v;"),
+    ("barrier_derivatives_h2", "scatter(c.pts, E.g.data(), H12, h2);", "scatter(c.pts, E.g.data(), H12, 1.0);"),
     # distances
     ("pe_distance_norm", "return dot(c, c) / dot(e, e);", "return dot(c, c);"),
     ("pt_plane_square", "return e * e / dot(n, n);", "return e * e;"),
@@ -60,11 +66,14 @@ MUTATIONS = [
     ("lumped_mass_share", "e->mass[tt[k]] += S.rho * vol / 4.0;", "e->mass[tt[k]] += S.rho * vol / 3.0;"),
     ("abd_mass_second_moment", "I2[3 * i + j] += det / 120.0 *", "I2[3 * i + j] += det / 60.0 *"),
     ("predict_gravity_h", "+ hh * g[k];", "+ h * g[k];"),
+    ("inertia_soft_half", "Einert += 0.5 * e.mass[i] * d * d;", "Einert += e.mass[i] * d * d;"),
     ("velocity_update", "e.v[d] = (e.x[d] - e.xt[d]) / h;", "e.v[d] = (e.x[d] - e.xt[d]);"),
     # affine body terms
     ("abd_orth_identity", "if (i == j) s = s - Dual<9>(1.0);", "if (i == j) s = s - Dual<9>(0.5);"),
     ("abd_orth_volume", "double w = h2 * e.P.kappa_affine * B.vol;", "double w = h2 * e.P.kappa_affine;"),
     ("pd_weight_h2", "const double w = h2 * B.kpd;", "const double w = B.kpd;"),
+    ("pd_target_next_step", "const int st = std::min(e.step, e.n_steps - 1);",
+     "const int st = std::min(e.step + 1, e.n_steps - 1);"),
     # joints
     ("joint_h2", "const double c = h2 * J.k;", "const double c = J.k;"),
     ("joint_anchor_swap", "jt.xa[k] = J.anchor_a[k]; jt.xb[k] = J.anchor_b[k];",

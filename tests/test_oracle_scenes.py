@@ -798,3 +798,80 @@ def test_edge_edge_contact_force_carries_the_rest_length_mollifier():
         # degree the long edges' crossing sits at r = sin^2(1 deg) / 1e-3 = 0.30
         assert any(r < 1.0 for r in rs) == mollified
         assert not mollified or any(abs(r - 0.30) < 0.01 for r in rs)
+
+
+def _head_on_cube(gap, speed, n_steps=1):
+    """A free rigid cube a gap above the fixed ground triangle, falling straight down at `speed`
+    with gravity off (no friction): the predicted pose is x~ = x^t + h v, a pure translation."""
+    env = S.resting_env("rigid", n_steps=n_steps, gap=gap)
+    env["gravity"][:] = 0
+    env["affine"][0]["qdot0"] = np.zeros(12)
+    env["affine"][0]["qdot0"][2] = -speed
+    return env
+
+
+def _first_two_iterate_energies(p, env):
+    e = O.OracleEnv(p, env)
+    e.trace(True)
+    e.step(1)
+    tr = e.trace_energies()
+    assert tr[0][:3].tolist() == [0, 0, 0] and tr[1][:3].tolist() == [0, 1, 0]
+    return tr[0][3], tr[1][3]
+
+
+def test_step_filter_stops_short_of_impact_by_the_accd_gap_fraction():
+    """Step filter (ACCD, Li et al. 2021, gap fraction s = 0.1): for a cube translating head-on
+    toward the ground, every closest pair (the four bottom corners over the ground triangle) has
+    relative speed l_p = |p| after the mean shift, so ACCD's first advance (1 - s) d0 / l_p is
+    already within s d0 of contact and the bound is alpha = (1 - s) d0 / (h V). With the gap
+    large enough that the trial point is still farther than d^ from the ground, the step is
+    accepted as it is, and the energy of the next iterate is the inertia term alone:
+    E1 = (1 - alpha)^2 E0 (the Newton direction is exactly h v: the orthogonality term has zero
+    gradient at A = I and its Hessian does not couple to the translation)."""
+    h = 0.01
+    p = S.scene_params(h)
+    d0 = 20 * p["dhat"]
+    V = 2 * d0 / h  # the free step would carry the cube a full gap past the ground
+    E0, E1 = _first_two_iterate_energies(p, _head_on_cube(d0, V))
+    alpha = (1 - 0.1) * d0 / (h * V)
+    assert E0 > 0
+    assert abs(E1 / E0 - (1 - alpha) ** 2) < 1e-9, (E1 / E0, (1 - alpha) ** 2)
+
+
+def test_line_search_halves_a_trial_that_meets_the_barrier():
+    """Backtracking by halving: from a gap of 3 d^ the step filter's bound 0.45 leaves the cube
+    0.3 d^ above the ground, where the barrier energy (four point-triangle contacts at
+    kappa = 3e6) exceeds the inertia decrease, so the trial is rejected; the halved step leaves
+    it 1.65 d^ above, out of contact, and is accepted: E1 = (1 - 0.225)^2 E0."""
+    h = 0.01
+    p = S.scene_params(h)
+    d0 = 3 * p["dhat"]
+    V = 2 * d0 / h
+    E0, E1 = _first_two_iterate_energies(p, _head_on_cube(d0, V))
+    alpha = (1 - 0.1) * d0 / (h * V)
+    gap_trial = d0 - alpha * h * V
+    assert gap_trial < p["dhat"] < d0 - 0.5 * alpha * h * V
+    barrier = 4 * h * h * p["kappa"] * O.barrier(gap_trial, p["dhat"])[0]
+    assert (1 - alpha) ** 2 * E0 + barrier > E0  # the first trial must fail the decrease test
+    assert abs(E1 / E0 - (1 - 0.5 * alpha) ** 2) < 1e-9, (E1 / E0, (1 - 0.5 * alpha) ** 2)
+
+
+def test_incremental_potential_of_a_body_at_rest_above_the_ground_is_its_barrier_sum():
+    """With gravity off and zero velocity, x~ = x^t, so at x^t the inertia term vanishes and an
+    undeformed rigid cube (A = I, no orthogonality energy, no friction) a gap d above the ground
+    has the incremental potential h^2 kappa sum_k b(d_k) over its four bottom corners, each a
+    point-triangle contact at d (no mollifier). The energy-only evaluation (the line search's)
+    and the one with derivatives (the Newton iterate's) must both give it."""
+    h = 0.01
+    p = S.scene_params(h)
+    gap = 0.4 * p["dhat"]
+    env = S.resting_env("rigid", n_steps=2, gap=gap)
+    env["gravity"][:] = 0
+    e = O.OracleEnv(p, env)
+    x, _ = e.state()
+    want = 4 * h * h * p["kappa"] * O.barrier(gap, p["dhat"])[0]
+    assert want > 0
+    E_only = e.eval(x, grad=False)
+    E_full, _ = e.eval(x)
+    assert abs(E_only / want - 1) < 1e-9, (E_only, want)
+    assert abs(E_full / want - 1) < 1e-9, (E_full, want)
