@@ -100,6 +100,9 @@ def parse():
     ap.add_argument("--no-mixed-leg", action="store_true",
                     help="skip the mixed-precision run of the same steps that the FP64 line reports beside it")
     ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle time for --impl reference")
+    ap.add_argument("--leg-budget", type=float, default=1100.0,
+                    help="seconds since the start of the run after which secondary legs not yet begun are skipped "
+                         "(the headline line is always printed)")
     a = ap.parse_args()
     if a.envs is None:
         a.envs = 1024 if a.workload == "uneven" else 64
@@ -366,9 +369,19 @@ def guarded(leg, *a):
         return {"error": f"{type(ex).__name__}: {ex}"}
 
 
+def budgeted(t_run0, budget, leg, *a):
+    """A secondary leg, run through `guarded` unless the run has already spent `budget` seconds
+    since `t_run0`; a leg that is not started is recorded as skipped with the time spent."""
+    spent = time.perf_counter() - t_run0
+    if spent > budget:
+        return {"skipped": f"not started: {spent:.0f} s of the run's {budget:.0f} s leg budget spent"}
+    return guarded(leg, *a)
+
+
 def run_ours(args):
     import torch
 
+    t_run0 = time.perf_counter()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -465,10 +478,10 @@ def run_ours(args):
     tets = [sum(len(s["tets"]) for s in e["soft"]) for e in envs]
     plain = mixed = None
     if world == 1 and args.plain_envs > 0:
-        plain = guarded(plain_leg, args, params, envs, snap, tets, stream, local, value, live)
+        plain = budgeted(t_run0, args.leg_budget, plain_leg, args, params, envs, snap, tets, stream, local, value, live)
     if world == 1 and args.precision == "fp64" and not args.no_mixed_leg:
-        mixed = guarded(mixed_leg, args, params, envs, snap, p_start, x_end, tets, stream, local, t_max / args.steps,
-                        {i for i, s_ in enumerate(stats) if s_["status"] == "FAILED"}, live)
+        mixed = budgeted(t_run0, args.leg_budget, mixed_leg, args, params, envs, snap, p_start, x_end, tets, stream,
+                         local, t_max / args.steps, {i for i, s_ in enumerate(stats) if s_["status"] == "FAILED"}, live)
         if plain and "value" in plain and "value" in mixed:
             plain["mixed_batched_over_plain"] = round(mixed["value"] / plain["value"], 2)
 
@@ -487,7 +500,7 @@ def run_ours(args):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = guarded(cpu_leg, envs, snap, tets, live, params)
+        cpu = budgeted(t_run0, args.leg_budget, cpu_leg, envs, snap, tets, live, params)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
@@ -511,7 +524,7 @@ def run_ours(args):
         "pcg_iters_per_newton": round(pcg_its / max(newton, 1), 1),
     }
     if world == 1 and args.serve_requests > 0:
-        line["serving"] = guarded(serving_leg, args, params, local)
+        line["serving"] = budgeted(t_run0, args.leg_budget, serving_leg, args, params, local)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -88,3 +88,23 @@ def test_reference_arm_runs_on_rank_0_only():
                         "--steps", "1", "--warmup", "1"], capture_output=True, text=True, env=env, cwd=root,
                        timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_secondary_legs_past_the_leg_budget_are_skipped_and_errors_are_recorded():
+    import time
+
+    calls = []
+
+    def leg(x):
+        calls.append(x)
+        return {"value": x}
+
+    def broken():
+        raise RuntimeError("leg failed")
+
+    now = time.perf_counter()
+    assert bench.budgeted(now, 60.0, leg, 3) == {"value": 3}
+    skipped = bench.budgeted(now - 100.0, 60.0, leg, 4)
+    assert "value" not in skipped and skipped["skipped"].startswith("not started")
+    assert calls == [3]
+    assert bench.budgeted(now, 60.0, broken) == {"error": "RuntimeError: leg failed"}
