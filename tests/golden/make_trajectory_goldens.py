@@ -11,6 +11,10 @@ would take most of an hour; the GPU side of the test runs the same 100 steps liv
 with these values. Only `oracle/` and the seeded scene generators are called here: no value
 comes from the CUDA path.
 
+Cases marked with the configuration's own settings are not parity windows: they run a whole
+grasp schedule (closing, then lifting under gravity) as the configuration states it, to show
+that the oracle itself holds and lifts the object; CPU tests check the stored outcome.
+
 Usage: python tests/golden/make_trajectory_goldens.py [case ...]   (default: every case; each
 case runs in its own process)
 """
@@ -21,6 +25,7 @@ import json
 import multiprocessing as mp
 import os
 import sys
+import time
 
 import numpy as np
 
@@ -38,11 +43,15 @@ EVERY = 20
 SAMPLED_SOFT_VERTS = 240  # soft vertices kept per checkpoint (evenly strided), all affine DOFs
 
 
-def _params(dhat=None):
+def _params(dhat=None, parity=True):
     p = S.scene_params(DT)
     if dhat is not None:
         p["dhat"] = dhat
-    return S.parity_params(p)
+    return S.parity_params(p) if parity else p
+
+
+PARITY_SETTINGS = "parity settings (Newton tolerance x1e-3, CG to 1e-12)"
+CONFIG_SETTINGS = "the configuration's settings (Newton tolerance 1e-2 dt in m/s; the oracle's CG to 1e-12)"
 
 
 # case name -> recipe text, env builder, parameters, first step, steps (checkpoints every EVERY)
@@ -65,6 +74,13 @@ CASES = {
               "(step 0) through the first 200 steps of the closing",
         build=lambda: S.hand_grasp_env(0, n_steps=300, close_steps=200), params=lambda: _params(5e-4),
         start=0, steps=200),
+    # not a parity case: the pad configuration's env 0 as configured, closing and lifting, to show
+    # that the oracle itself holds and lifts the hull (its schedule ends with the window)
+    "pad_grasp_0_lift": dict(
+        scene="scenes.pad_grasp_env(0): the pad configuration's env 0 through its whole schedule: close 100 "
+              "steps (gravity off), then lift 0.1 m in 200 (gravity on), dt 5 ms, from the open pads",
+        build=lambda: S.pad_grasp_env(0), params=lambda: _params(parity=False),
+        start=0, steps=300, final="DONE", settings=CONFIG_SETTINGS),
 }
 
 
@@ -132,17 +148,18 @@ def make(case: str) -> str:
     o = O.OracleEnv(params, env)
     o.set_state(x0, v0, start)
     checkpoints = []
+    t0 = time.perf_counter()
     for k in range(EVERY, n_steps + 1, EVERY):
         o.step(EVERY)
         x, _ = o.state()
         checkpoints.append({"steps": k, "dofs": [float(v) for v in x[idx]]})
         st = o.status()
-        print(f"{case}: step {start + k} {st}", flush=True)
+        print(f"{case}: step {start + k} {st} ({time.perf_counter() - t0:.0f} s)", flush=True)
     out = {
         "what": "plain FP64 CPU oracle trajectory (oracle/ipc_oracle.cpp), sampled DOFs every "
                 f"{EVERY} steps; written by tests/golden/make_trajectory_goldens.py",
-        "method": "IPC step of Sec. II-C with the per-environment solve of Sec. III-A, parity settings "
-                  "(Newton tolerance x1e-3, CG to 1e-12)",
+        "method": "IPC step of Sec. II-C with the per-environment solve of Sec. III-A, "
+                  + c.get("settings", PARITY_SETTINGS),
         "scene": c["scene"],
         "params": {k: (list(v) if isinstance(v, tuple) else v) for k, v in params.items()},
         "start_step": start,

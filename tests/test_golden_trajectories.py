@@ -32,8 +32,9 @@ def test_golden_matches_its_generators(case):
     assert steps == list(range(G.EVERY, c["steps"] + 1, G.EVERY))
     for chk in gold["checkpoints"]:
         assert len(chk["dofs"]) == len(idx) and np.all(np.isfinite(chk["dofs"]))
-    # the env is still stepping at the end of the window (not failed, schedule not finished)
-    assert gold["final_status"]["status"] == "ACTIVE"
+    # the env is still stepping at the end of the window (not failed; a window that ends with its
+    # schedule finishes it)
+    assert gold["final_status"]["status"] == c.get("final", "ACTIVE")
     assert gold["final_status"]["step"] == c["start"] + c["steps"]
 
 
@@ -103,6 +104,26 @@ def test_stored_hand_leaves_the_object_at_rest_until_the_fingers_arrive():
             assert moved < 1e-12, (steps, moved)
         else:
             assert moved > 1e-3, (steps, moved)
+
+
+def test_stored_pad_grasp_lifts_the_hull_with_the_pads():
+    """The pad configuration's env 0 as configured: the pads close on the rigid hull with gravity
+    off (100 steps), then their bases rise 0.1 m in 200 steps with gravity on. The hull is held:
+    its translation follows the pads' rise within 1 mm at every checkpoint (the squeeze moves it
+    0.3 mm) and ends within 1 mm of 0.1 m, its A stays within 1e-3 of a rotation's, and the run
+    finishes its schedule without failing."""
+    with open(G.golden_path("pad_grasp_0_lift")) as f:
+        gold = json.load(f)
+    assert gold["final_status"]["status"] == "DONE" and gold["final_status"]["reason"] == 0
+    env, x0, idx, chks = _checkpoints("pad_grasp_0_lift")
+    base = 3 * sum(len(s["verts"]) for s in env["soft"])
+    for steps, x in chks:
+        rise = env["lift"] * max(0, steps - 100) / 200
+        dz = x[base + 2] - x0[base + 2]
+        assert abs(dz - rise) < 1e-3, (steps, dz, rise)
+        A = x[base + 3:base + 12].reshape(3, 3).T
+        assert np.abs(A @ A.T - np.eye(3)).max() < 1e-3, steps
+    assert abs(dz - env["lift"]) < 1e-3, dz
 
 
 @pytest.mark.slow
