@@ -256,9 +256,9 @@ FP64_PEAK_TFLOPS = 148 * 4 * 2.032e9 / 1e12
 
 
 # DRAM bytes per launch of k_pcg_cluster measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum over every launch of a run of this workload, averaged per launch; the
-# command is in profiles/k_pcg_cluster_uneven_1024env_dram.md). Keyed by (workload, envs,
-# precision); a workload without a capture of the current kernel reports null.
+# dram__bytes_write.sum over every launch of `bench.py --steps 2 --warmup 3 --plain-envs 0
+# --no-mixed-leg --no-cpu-baseline --serve-requests 0`, averaged per launch). Keyed by (workload,
+# envs, precision); a workload without a capture of the current kernel reports null.
 PCG_DRAM_BYTES_PER_LAUNCH = {("uneven", 1024, "fp64"): 21.154e9}
 
 
