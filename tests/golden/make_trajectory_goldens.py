@@ -74,6 +74,13 @@ CASES = {
               "(step 0) through the first 200 steps of the closing",
         build=lambda: S.hand_grasp_env(0, n_steps=300, close_steps=200), params=lambda: _params(5e-4),
         start=0, steps=200),
+    # not a parity case: the hand's whole grasp in the configuration's own settings, to show that
+    # the oracle itself closes, holds and lifts the object (its schedule ends with the window)
+    "hand_0_hold": dict(
+        scene="scenes.hand_grasp_env(0, n_steps=300, close_steps=200): the same hinged hand and object, all "
+              "300 steps: close 200 (gravity off), then palm and finger targets rise 5 cm in 100 (gravity on)",
+        build=lambda: S.hand_grasp_env(0, n_steps=300, close_steps=200), params=lambda: _params(5e-4, parity=False),
+        start=0, steps=300, final="DONE", settings=CONFIG_SETTINGS),
     # not a parity case: the pad configuration's env 0 as configured, closing and lifting, to show
     # that the oracle itself holds and lifts the hull (its schedule ends with the window)
     "pad_grasp_0_lift": dict(

@@ -106,6 +106,27 @@ def test_stored_hand_leaves_the_object_at_rest_until_the_fingers_arrive():
             assert moved > 1e-3, (steps, moved)
 
 
+def test_stored_hand_grasp_holds_and_lifts_the_object():
+    """The oracle's whole hand grasp in the configuration's settings: the fingers close on the
+    object with gravity off (steps 0-200), then palm and finger targets rise 5 cm in 100 steps
+    with gravity on. The object rises with the hand: its sampled vertices' mean height follows
+    the palm's (the last affine body's) rise within 1 mm at every checkpoint of the lift (the
+    closing fingers have pushed it up 2.2 mm by step 200; under its weight it then trails the palm
+    by 0.5 mm) and ends within 1 mm of the full 5 cm, and the run finishes its schedule without
+    failing."""
+    with open(G.golden_path("hand_0_hold")) as f:
+        gold = json.load(f)
+    assert gold["final_status"]["status"] == "DONE" and gold["final_status"]["reason"] == 0
+    env, x0, idx, chks = _checkpoints("hand_0_hold")
+    palm = 3 * sum(len(s["verts"]) for s in env["soft"]) + 12 * (len(env["affine"]) - 1)
+    for steps, x in chks:
+        rise = x[palm + 2] - x0[palm + 2]
+        dz = _soft0_mean_shift(env, x0, idx, x)[2]
+        if steps > 200:
+            assert rise > 0 and abs(dz - rise) < 1e-3, (steps, dz, rise)
+    assert abs(rise - env["lift"]) < 1e-9 and abs(dz - env["lift"]) < 1e-3, (dz, rise)
+
+
 def test_stored_pad_grasp_lifts_the_hull_with_the_pads():
     """The pad configuration's env 0 as configured: the pads close on the rigid hull with gravity
     off (100 steps), then their bases rise 0.1 m in 200 steps with gravity on. The hull is held:
