@@ -108,3 +108,25 @@ def test_secondary_legs_past_the_leg_budget_are_skipped_and_errors_are_recorded(
     assert "value" not in skipped and skipped["skipped"].startswith("not started")
     assert calls == [3]
     assert bench.budgeted(now, 60.0, broken) == {"error": "RuntimeError: leg failed"}
+
+
+def test_cpu_leg_times_the_oracle_on_the_batch_s_small_envs():
+    """The CPU baseline leg, on the first 24 envs of the uneven batch from their start state: one
+    oracle step per env on a sample of the envs of at most CPU_SAMPLE_MAX_TETS tets, one env per
+    host thread, with the host's core count and CPU model in the record."""
+    from paper_2503_05020_b300 import scenes as S
+
+    wl = bench.Workload("uneven")
+    envs = [wl.build(i) for i in range(24)]
+    snap = []
+    for e in envs:
+        x, v = wl.state_at(e, wl.start)
+        snap.append((x, v, wl.start))
+    tets = [sum(len(s["tets"]) for s in e["soft"]) for e in envs]
+    live = [i for i in range(len(envs)) if i != 1]  # an env stopped in the warm-up is left out
+    out = bench.cpu_leg(envs, snap, tets, live, S.scene_params(bench.DT))
+    assert out["kind"] == "oracle" and out["unit"] == bench.UNIT and out["value"] > 0
+    assert 1 <= out["cores"] <= (os.cpu_count() or 1)
+    assert out["nproc"] == os.cpu_count() and out["cpu_model"]
+    lo, hi = (int(t) for t in out["sample"].split("(tets ")[1].split(";")[0].split("-"))
+    assert hi <= bench.CPU_SAMPLE_MAX_TETS and lo >= min(tets[i] for i in live)
