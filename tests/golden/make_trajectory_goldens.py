@@ -88,6 +88,13 @@ CASES = {
               "steps (gravity off), then lift 0.1 m in 200 (gravity on), dt 5 ms, from the open pads",
         build=lambda: S.pad_grasp_env(0), params=lambda: _params(parity=False),
         start=0, steps=300, final="DONE", settings=CONFIG_SETTINGS),
+    # not a parity case: a soft-pad grasp of a soft object from the uneven batch as configured
+    "uneven_4_lift": dict(
+        scene="scenes.uneven_batch_env(4): two ~4.8k-tet soft pads around a 3.3k-tet star-shaped soft object "
+              "(the uneven batch's env 4), its whole schedule from the open pads: close 100 steps (gravity off), "
+              "then lift 0.1 m in 200 (gravity on), dt 5 ms",
+        build=lambda: S.uneven_batch_env(4), params=lambda: _params(parity=False),
+        start=0, steps=300, final="DONE", settings=CONFIG_SETTINGS),
 }
 
 

@@ -147,6 +147,37 @@ def test_stored_pad_grasp_lifts_the_hull_with_the_pads():
     assert abs(dz - env["lift"]) < 1e-3, dz
 
 
+def test_stored_soft_pad_grasp_lifts_the_soft_object():
+    """The uneven batch's env 4 as configured: two soft pads close on a 3.3k-tet soft object with
+    gravity off (100 steps), then their bases rise 0.1 m in 200 steps with gravity on. The object
+    is held: when gravity comes on it settles into the soft pads over the first 40 lifting steps
+    (its sampled vertices' mean height then trails the pads' rise by about 3 mm, never by 5 mm),
+    then it sticks: from one later lift checkpoint to the next its lag grows by less than
+    eps_v dt per step, the friction model's static/dynamic transition speed; it ends above 95%
+    of the lift, and the run finishes its schedule without failing."""
+    with open(G.golden_path("uneven_4_lift")) as f:
+        gold = json.load(f)
+    assert gold["final_status"]["status"] == "DONE" and gold["final_status"]["reason"] == 0
+    env, x0, idx, chks = _checkpoints("uneven_4_lift")
+    p = G.CASES["uneven_4_lift"]["params"]()
+    lo = 3 * sum(len(s["verts"]) for s in env["soft"][:-1])
+    hi = lo + 3 * len(env["soft"][-1]["verts"])
+    sel = idx[(idx >= lo) & (idx < hi)]
+    assert len(sel) > 30
+    lags = []
+    for steps, x in chks:
+        rise = 0.1 * max(0, steps - 100) / 200
+        dz = (x[sel] - x0[sel]).reshape(-1, 3).mean(axis=0)[2]
+        if steps <= 100:
+            assert abs(dz) < 1e-4, (steps, dz)  # gravity off: the closing pads do not lift it
+        else:
+            assert 0 <= rise - dz < 5e-3, (steps, dz, rise)
+            lags.append(rise - dz)
+    creep = np.diff(lags[1:])  # settled from the second lift checkpoint (step 140) on
+    assert np.all(creep < p["eps_v"] * p["dt"] * G.EVERY), creep
+    assert dz > 0.095, dz
+
+
 @pytest.mark.slow
 def test_oracle_still_computes_the_first_stored_checkpoint():
     """The fingerprints tie a golden to its inputs; this ties it to the oracle's code: the first
