@@ -42,6 +42,7 @@ MUTATIONS = [
     ("friction_f1_slope", "*f1 = -y * y / (eh * eh) + 2.0 * y / eh;", "*f1 = -y * y / (eh * eh) + y / eh;"),
     ("friction_lambda_kappa", "f.lambda = e.kappa * moll * std::fabs(b1);", "f.lambda = moll * std::fabs(b1);"),
     ("friction_mu", "double s = h2 * e.mu * f.lambda;", "double s = h2 * f.lambda;"),
+    ("friction_eps_without_h", "const double eh = e.P.eps_v * h;", "const double eh = e.P.eps_v;"),
     ("friction_no_tangent_projection",
      "double u[3] = {rel[0] - nr * f.n[0], rel[1] - nr * f.n[1], rel[2] - nr * f.n[2]};",
      "double u[3] = {rel[0], rel[1], rel[2]};"),
