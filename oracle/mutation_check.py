@@ -67,6 +67,10 @@ MUTATIONS = [
     ("lumped_mass_share", "e->mass[tt[k]] += S.rho * vol / 4.0;", "e->mass[tt[k]] += S.rho * vol / 3.0;"),
     ("abd_mass_second_moment", "I2[3 * i + j] += det / 120.0 *", "I2[3 * i + j] += det / 60.0 *"),
     ("predict_gravity_h", "+ hh * g[k];", "+ h * g[k];"),
+    ("gravity_gate_ignored", "double hh = code ? h * h : 0.0;", "double hh = h * h;"),
+    ("gravity_gate_next_step", "const int code = e.gravity[std::min(e.step, e.n_steps - 1)];",
+     "const int code = e.gravity[std::min(e.step + 1, e.n_steps - 1)];"),
+    ("axis_gravity_sign", "g[(code - 2) / 2] = code % 2 == 0 ? gm : -gm;", "g[(code - 2) / 2] = code % 2 == 0 ? -gm : gm;"),
     ("inertia_soft_half", "Einert += 0.5 * e.mass[i] * d * d;", "Einert += e.mass[i] * d * d;"),
     ("velocity_update", "e.v[d] = (e.x[d] - e.xt[d]) / h;", "e.v[d] = (e.x[d] - e.xt[d]);"),
     # affine body terms
